@@ -1,0 +1,179 @@
+"""Plain FP64 CPU oracle of the DMN material-point update (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path.
+The arithmetic lives in ``dmn_oracle.c`` (plain C + OpenMP over points); this
+module builds it with gcc and marshals numpy arrays through ctypes.
+
+Every function states the passage of the paper it follows in the C source.
+Parity is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``
+against closed forms, textbook routines and the depth-3 operator printed in the
+paper.  Pinned-status of each function is listed in the module docstring of
+those tests; nothing here is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dmn_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle_dmn.so")
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host gcc (-O2, OpenMP); returns the .so path."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.oracle_update.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_long, _D, _D, _D, _D, _D, _D, _D, _D, _I, _I, _D,
+                                      ctypes.c_int]
+        lib.oracle_normals.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double, _D]
+        lib.oracle_barycentric.argtypes = [ctypes.c_double, ctypes.c_double, _D]
+        lib.oracle_gradient_operator.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, ctypes.c_double,
+                                                 ctypes.c_double, _D]
+        lib.oracle_newton_system.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_double,
+                                             ctypes.c_double, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+        lib.oracle_phase_law.argtypes = [_D, _D, _D, _D, _D, _D]
+        lib.oracle_rotate.argtypes = [_D, _D, _D, _D, _D]
+        lib.oracle_interp_orientation.argtypes = [ctypes.c_long, _D, _D, _D]
+        lib.oracle_state_size.argtypes = [ctypes.c_int, _D]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def phases_array(phases) -> np.ndarray:
+    """(kind, E, nu, sigma0, H) of phase 1 then phase 2."""
+    return np.array([[ph.kind, ph.E, ph.nu, ph.sigma0, ph.H] for ph in phases], dtype=np.float64).reshape(10)
+
+
+def state_size(K: int, phases) -> int:
+    m = phases_array(phases)
+    return int(_load().oracle_state_size(K, _p(m)))
+
+
+def update(tree, lam, Q, E_n, dE, state_in, tol=1e-12, max_iter=50, line_search=False, nthreads=None):
+    """One material-point update of n points (Sec. 3.2): returns
+    (state_out, stress [n,6], tangent [n,6,6], iters [n], status [n], yield_gap [n]).
+
+    state_in is field-major [S, n]; stress/tangent are in the global frame."""
+    lib = _load()
+    lam = _f64(lam); Q = _f64(Q); E_n = _f64(E_n); dE = _f64(dE); state_in = _f64(state_in)
+    n = lam.shape[0]
+    S = state_size(tree.K, tree.phases)
+    assert state_in.shape == (S, n), (state_in.shape, S, n)
+    p = _f64(tree.p); q = _f64(tree.q); w = _f64(tree.w); m = phases_array(tree.phases)
+    state_out = np.empty_like(state_in)
+    stress = np.empty((n, 6)); tangent = np.empty((n, 6, 6))
+    iters = np.empty(n, dtype=np.int32); status = np.empty(n, dtype=np.int32); gap = np.empty(n)
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    rc = lib.oracle_update(tree.K, tree.M, _p(p), _p(q), _p(w), _p(m), float(tol), int(max_iter),
+                           int(bool(line_search)), n, _p(lam), _p(Q), _p(E_n), _p(dE), _p(state_in),
+                           _p(state_out), _p(stress), _p(tangent), iters.ctypes.data_as(_I),
+                           status.ctypes.data_as(_I), _p(gap), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_update rejected its arguments (rc=%d)" % rc)
+    return state_out, stress, tangent, iters, status, gap
+
+
+def normals(tree, lam1, lam2):
+    """Normals of all laminates [N, 3] in the paper's ordering (Sec. 2.3)."""
+    N = (1 << tree.K) - 1
+    out = np.empty((N, 3))
+    p = _f64(tree.p); q = _f64(tree.q)
+    rc = _load().oracle_normals(tree.K, tree.M, _p(p), _p(q), float(lam1), float(lam2), _p(out))
+    assert rc == 0
+    return out
+
+
+def barycentric(lam1, lam2):
+    out = np.empty(3)
+    _load().oracle_barycentric(float(lam1), float(lam2), _p(out))
+    return out
+
+
+def gradient_operator(tree, lam1, lam2):
+    """Dense A [6 * 2^K, 3 * (2^K - 1)] (Sec. 3.2)."""
+    L = 1 << tree.K
+    N = L - 1
+    A = np.empty((6 * L, 3 * N))
+    p = _f64(tree.p); q = _f64(tree.q); w = _f64(tree.w)
+    rc = _load().oracle_gradient_operator(tree.K, tree.M, _p(p), _p(q), _p(w), float(lam1), float(lam2), _p(A))
+    assert rc == 0
+    return A
+
+
+def newton_system(tree, lam1, lam2, E_loc, a, z_n):
+    """J (dense), R, da = -J^{-1} R (oracle's Cholesky), leaf eps, sigma and
+    sigma_bar at one iterate.  z_n: [2^K, 7] per leaf (alpha_bar, ep6)."""
+    L = 1 << tree.K
+    N = L - 1
+    J = np.empty((3 * N, 3 * N)); R = np.empty(3 * N); da = np.empty(3 * N)
+    eps = np.empty((L, 6)); sig = np.empty((L, 6)); sbar = np.empty(6)
+    p = _f64(tree.p); q = _f64(tree.q); w = _f64(tree.w); m = phases_array(tree.phases)
+    rc = _load().oracle_newton_system(tree.K, tree.M, _p(p), _p(q), _p(w), _p(m), float(lam1), float(lam2),
+                                      _p(_f64(E_loc)), _p(_f64(a)), _p(_f64(z_n)), _p(J), _p(R), _p(da),
+                                      _p(eps), _p(sig), _p(sbar))
+    return dict(J=J, R=R, da=da, eps=eps, sig=sig, sbar=sbar, rc=rc)
+
+
+def phase_law(phase, eps, z_n=None):
+    """One leaf: (sigma [6], D [6,6], z_new [7]); z = (alpha_bar, ep6 Mandel)."""
+    ph = np.array([phase.kind, phase.E, phase.nu, phase.sigma0, phase.H], dtype=np.float64)
+    z = np.zeros(7) if z_n is None else _f64(z_n)
+    sig = np.empty(6); D = np.empty((6, 6)); zn = np.empty(7)
+    _load().oracle_phase_law(_p(ph), _p(_f64(eps)), _p(z), _p(sig), _p(D), _p(zn))
+    return sig, D, zn
+
+
+def rotate(Q, C_loc, v_loc):
+    """Global-frame Mandel stiffness and symmetric tensor from local ones."""
+    Cg = np.empty((6, 6)); vg = np.empty(6)
+    _load().oracle_rotate(_p(_f64(Q)), _p(_f64(C_loc)), _p(_f64(v_loc)), _p(Cg), _p(vg))
+    return Cg, vg
+
+
+def interp_orientation(A2):
+    """(lam [n,2], Q [n,9]) from A2 [n,6] (Eq. of the eigen decomposition)."""
+    A2 = _f64(A2)
+    n = A2.shape[0]
+    lam = np.empty((n, 2)); Q = np.empty((n, 9))
+    _load().oracle_interp_orientation(n, _p(A2), _p(lam), _p(Q))
+    return lam, Q
+
+
+__all__ = ["build", "update", "normals", "barycentric", "gradient_operator", "newton_system", "phase_law",
+           "rotate", "interp_orientation", "state_size", "phases_array"]
+if "--build" in sys.argv[1:]:  # pragma: no cover
+    print(build(force=True))

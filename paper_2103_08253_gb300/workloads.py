@@ -1,0 +1,229 @@
+"""Seeded synthetic inputs for the DMN material-point update.
+
+This module only draws inputs: tree parameters (angle coefficients p, q and leaf
+weights w), fiber-orientation fields (A2 with its eigenvalues and frames) and
+macro strain paths.  It contains none of the method's arithmetic (no normals,
+no laminate algebra, no material law), so both the CUDA path and the CPU oracle
+can be fed from it.
+
+Conventions shared by every consumer:
+
+* symmetric 3x3 tensors are 6-vectors ordered (11, 22, 33, 23, 13, 12);
+  strains and stresses use the Mandel form (shear entries times sqrt(2)),
+  the orientation tensor A2 uses plain components;
+* frames Q are row-major 3x3 with the eigenvectors of A2 as columns,
+  so that A2 = Q diag(lam1, lam2, lam3) Q^T;
+* tree parameters follow the paper's ordering of laminates: the nodes of the
+  deepest level K first, then level K-1, ..., the root last (Sec. 3.1);
+  leaf weights are listed leaf 1 .. leaf 2^K;
+* moduli are in MPa.
+
+The paper's workloads (SAM microstructures, FFT training data, the drone-arm
+orientation field) are not available; the generators below stand in for them
+with the sizes and value distributions described in the module functions.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SQRT2 = math.sqrt(2.0)
+
+# Corners of the fiber-orientation triangle in (lam1, lam2): unidirectional,
+# isotropic, planar isotropic (Sec. 2.2, Fig. of the orientation triangle).
+TRIANGLE_CORNERS = np.array([[1.0, 0.0], [1.0 / 3.0, 1.0 / 3.0], [0.5, 0.5]])
+
+
+@dataclass
+class Phase:
+    """One constituent: kind 0 = linear elastic, kind 1 = J2 plasticity with
+    linear isotropic hardening sigma_Y = sigma0 + H * alpha_bar."""
+    kind: int
+    E: float
+    nu: float
+    sigma0: float = 0.0
+    H: float = 0.0
+
+
+# Materials of the synthetic workloads: glass fiber and a J2 matrix with linear
+# hardening (the fiber data are those of the paper's Tab. of material parameters;
+# the matrix law is the linear-hardening stand-in for its exp-linear law).
+FIBER = Phase(kind=0, E=72000.0, nu=0.22)
+MATRIX = Phase(kind=1, E=3000.0, nu=0.35, sigma0=40.0, H=300.0)
+
+
+@dataclass
+class TreeParams:
+    K: int
+    M: int
+    p: np.ndarray  # [2^K - 1, M] (rad), paper ordering
+    q: np.ndarray  # [2^K - 1, M] (rad), paper ordering
+    w: np.ndarray  # [2^K] leaf weights, >= 0
+    phases: tuple = field(default_factory=lambda: (FIBER, MATRIX))
+
+
+def n_nodes(K: int) -> int:
+    return (1 << K) - 1
+
+
+def n_leaves(K: int) -> int:
+    return 1 << K
+
+
+def d10_barycentric() -> np.ndarray:
+    """The ten sampling points of the once-split orientation triangle (Sec. 4.3):
+    the three corners, the three edge midpoints and the centres of the four
+    sub-triangles, as weights on the (UD, ISO, PI) corners."""
+    c = [(1, 0, 0), (0, 1, 0), (0, 0, 1),
+         (0.5, 0.5, 0), (0.5, 0, 0.5), (0, 0.5, 0.5),
+         (2 / 3, 1 / 6, 1 / 6), (1 / 6, 2 / 3, 1 / 6), (1 / 6, 1 / 6, 2 / 3),
+         (1 / 3, 1 / 3, 1 / 3)]
+    return np.array(c, dtype=np.float64)
+
+
+def _uniform_sphere_angles(rng, size):
+    alpha = np.arccos(rng.uniform(-1.0, 1.0, size=size))
+    beta = rng.uniform(0.0, 2.0 * np.pi, size=size)
+    return alpha, beta
+
+
+def tree_constant_normals(K: int, seed: int, M: int = 3, phases=(FIBER, MATRIX)) -> TreeParams:
+    """Uniformly random unit normals that do not vary over the orientation
+    triangle, and Dirichlet(1, ..., 1) leaf weights.
+
+    The shape functions of every interpolation order sum to one, so constant
+    angles are represented by p_j = alpha_j * (1, ..., 1)."""
+    rng = np.random.default_rng(seed)
+    N = n_nodes(K)
+    alpha, beta = _uniform_sphere_angles(rng, N)
+    p = np.repeat(alpha[:, None], M, axis=1)
+    q = np.repeat(beta[:, None], M, axis=1)
+    w = rng.dirichlet(np.ones(n_leaves(K)))
+    return TreeParams(K=K, M=M, p=p, q=q, w=w, phases=tuple(phases))
+
+
+def tree_d10_fit(K: int, seed: int, spread: float = 0.35, phases=(FIBER, MATRIX)) -> TreeParams:
+    """Linear (M = 3) angle coefficients fitted to seeded angles at the ten D10
+    sampling points.
+
+    Per laminate a base direction is drawn uniformly on the sphere; at each D10
+    point its angles are perturbed by N(0, spread^2).  p, q are the least-squares
+    coefficients of the linear interpolant through those ten samples: for linear
+    interpolation the design matrix is the barycentric coordinates of the D10
+    points themselves.  Leaf weights are Dirichlet(1, ..., 1)."""
+    rng = np.random.default_rng(seed)
+    N = n_nodes(K)
+    alpha0, beta0 = _uniform_sphere_angles(rng, N)
+    phi = d10_barycentric()                      # [10, 3]
+    a_s = alpha0[:, None] + spread * rng.standard_normal((N, 10))
+    b_s = beta0[:, None] + spread * rng.standard_normal((N, 10))
+    pinv = np.linalg.pinv(phi)                   # [3, 10]
+    p = a_s @ pinv.T
+    q = b_s @ pinv.T
+    w = rng.dirichlet(np.ones(n_leaves(K)))
+    return TreeParams(K=K, M=3, p=p, q=q, w=w, phases=tuple(phases))
+
+
+def haar_rotations(rng, n: int) -> np.ndarray:
+    """n Haar-distributed rotation matrices [n, 3, 3] (QR of Gaussian matrices
+    with the sign of R's diagonal fixed, then det forced to +1)."""
+    g = rng.standard_normal((n, 3, 3))
+    Qm, R = np.linalg.qr(g)
+    d = np.sign(np.diagonal(R, axis1=1, axis2=2))
+    d[d == 0] = 1.0
+    Qm = Qm * d[:, None, :]
+    det = np.linalg.det(Qm)
+    Qm[:, :, 2] *= np.sign(det)[:, None]
+    return Qm
+
+
+def orientation_field(n: int, seed: int):
+    """Orientation tensors whose eigenvalue pairs are uniform over the fiber
+    orientation triangle, with Haar-random principal frames.
+
+    Returns (A2 [n,6] plain components, lam [n,2], Q [n,9] row-major with the
+    eigenvectors as columns, sorted lam1 >= lam2 >= lam3)."""
+    rng = np.random.default_rng(seed)
+    wts = rng.dirichlet(np.ones(3), size=n)      # uniform over the triangle
+    lam = wts @ TRIANGLE_CORNERS                 # [n, 2]
+    lam3 = 1.0 - lam[:, 0] - lam[:, 1]
+    Qm = haar_rotations(rng, n)
+    L = np.stack([lam[:, 0], lam[:, 1], lam3], axis=1)
+    A = np.einsum("nij,nj,nkj->nik", Qm, L, Qm)
+    A2 = np.stack([A[:, 0, 0], A[:, 1, 1], A[:, 2, 2], A[:, 1, 2], A[:, 0, 2], A[:, 0, 1]], axis=1)
+    return np.ascontiguousarray(A2), np.ascontiguousarray(lam), np.ascontiguousarray(Qm.reshape(n, 9))
+
+
+def identity_orientation(n: int):
+    """Identity frames and the isotropic corner, for trees whose normals do not
+    depend on the orientation."""
+    lam = np.tile(np.array([1.0 / 3.0, 1.0 / 3.0]), (n, 1))
+    Q = np.tile(np.eye(3).reshape(1, 9), (n, 1))
+    return lam, Q
+
+
+def tensor_to_mandel(T: np.ndarray) -> np.ndarray:
+    """[..., 3, 3] symmetric -> [..., 6] Mandel."""
+    return np.stack([T[..., 0, 0], T[..., 1, 1], T[..., 2, 2],
+                     SQRT2 * T[..., 1, 2], SQRT2 * T[..., 0, 2], SQRT2 * T[..., 0, 1]], axis=-1)
+
+
+def uniaxial_path_final(n: int, eps_max: float, seed: int) -> np.ndarray:
+    """Final macro strain of a uniaxial-strain ramp eps_max * R e1 (x) e1 R^T with
+    a Haar-random R per point (Mandel, [n, 6])."""
+    rng = np.random.default_rng(seed)
+    R = haar_rotations(rng, n)
+    d = R[:, :, 0]
+    T = eps_max * np.einsum("ni,nj->nij", d, d)
+    return tensor_to_mandel(T)
+
+
+def random6_path_final(n: int, eps_eq_max: float, seed: int, min_dev_fraction: float = 0.5) -> np.ndarray:
+    """Final macro strain of a proportional path along a random Gaussian Mandel
+    direction, rejected while the deviatoric part carries less than
+    `min_dev_fraction` of its norm, scaled so that the equivalent strain
+    sqrt(2/3 E':E') reaches eps_eq_max ([n, 6])."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((n, 6))
+    todo = np.arange(n)
+    while todo.size:
+        d = rng.standard_normal((todo.size, 6))
+        tr = d[:, 0] + d[:, 1] + d[:, 2]
+        dev = d.copy()
+        dev[:, :3] -= tr[:, None] / 3.0
+        ndev = np.linalg.norm(dev, axis=1)
+        ok = ndev >= min_dev_fraction * np.linalg.norm(d, axis=1)
+        eq = np.sqrt(2.0 / 3.0) * ndev[ok]
+        out[todo[ok]] = d[ok] * (eps_eq_max / eq)[:, None]
+        todo = todo[~ok]
+    return out
+
+
+def proportional_increment(E_final: np.ndarray, step: int, n_steps: int):
+    """(E_n, dE) of increment `step` (1-based) of a proportional ramp to E_final."""
+    E_n = E_final * ((step - 1) / n_steps)
+    dE = E_final * (step / n_steps) - E_n
+    return np.ascontiguousarray(E_n), np.ascontiguousarray(dE)
+
+
+def triangle_wave(step: int, n_steps: int, amp: float, periods: float = 1.0) -> float:
+    """Amplitude of a triangle wave 0 -> +amp -> -amp -> 0 ... after `step` of
+    `n_steps` increments (periods full cycles)."""
+    t = periods * step / n_steps
+    f = t - math.floor(t)
+    if f < 0.25:
+        return amp * 4.0 * f
+    if f < 0.75:
+        return amp * (2.0 - 4.0 * f)
+    return amp * (4.0 * f - 4.0)
+
+
+def state_size(K: int, phases=(FIBER, MATRIX)) -> int:
+    """Doubles of state per point: 6 per inelastic leaf (alpha_bar and the five
+    independent components of the deviatoric plastic strain), then 3 jumps per
+    laminate."""
+    L = n_leaves(K)
+    n_inel = sum(1 for i in range(L) if phases[i % 2].kind == 1)
+    return 6 * n_inel + 3 * n_nodes(K)
