@@ -1,0 +1,465 @@
+#!/usr/bin/env python
+"""DMN Gauss-point updates/s at depth 8 on one GB300, FP64 and mixed forms.
+
+Workload (one "step" = one increment of the load path over the whole batch:
+orientation set-up + material-point update, all through the C ABI):
+  * K = 8 DMN (256 leaves, 255 laminates), linear angle interpolation fitted to
+    seeded angles at the ten D10 points of the orientation triangle,
+    Dirichlet(1) leaf weights; glass fiber (E 72 GPa, nu 0.22) and a J2 matrix
+    (E 3 GPa, nu 0.35, sigma0 40 MPa, H 300 MPa);
+  * 2^20 Gauss points per GPU whose orientation eigenvalues are uniform over
+    the triangle, Haar-random principal frames;
+  * random proportional 6-component macro strain paths reaching 3 %
+    equivalent strain after 50 increments; step s of the run is increment s.
+The state (12.9 GB per buffer at 2^20 points) is far larger than L2, so no
+flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2103_08253_gb300 import workloads as W  # noqa: E402
+
+METRIC = "DMN Gauss-point updates/s at depth 8 on 1 GB300 (FP64 vs mixed) at stated stress error"
+UNIT = "GP-updates/s"
+K_DEPTH = 8
+N_INCREMENTS = 50
+EPS_EQ = 0.03
+SEED_TREE, SEED_ORI, SEED_PATH = 2103, 8253, 1208
+WORKLOAD = "K=8 D10-interpolated DMN, 2^20 points/GPU, random 6-comp paths, 50 increments to 3% eq. strain"
+
+# FP64 peak: 152 SMs x 4 sub-partitions x 0.5 DFMA/clk x 2 flop x 2.07 GHz
+PEAK_F64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.07
+# FP32 peak: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
+PEAK_F32_GFLOPS = 152 * 128 * 2 * 2.07
+
+# ---------------------------------------------------------------------------------------------
+# Algorithmic flop counts (add/sub/mul/div/sqrt = 1, fma = 2) per Newton pass over a depth-K
+# tree, counted from the arithmetic of csrc/dmn_device.cuh (see the design doc for the breakdown).
+# Per laminate: jump correction da = g + H d_eps (36, precision T), a += da (3, FP64), N a and
+# the children's strains (39, FP64), children's strain corrections (36, T, not at the bottom
+# level), the laminate's residual share and plain stress average (52, FP64), the
+# condensation (745, T).  Per leaf: elastic law with tangent 75 (FP64 stress 17 + T tangent
+# 58), J2 law with consistent tangent 128 (FP64 70 + T 58).  T = FP64 in the FP64 form and
+# FP32 in the mixed form.
+def pass_flops(K):
+    """(FP64 flops, T flops) of one Newton pass."""
+    N, L = (1 << K) - 1, 1 << K
+    nb = (1 << (K - 1)) - 1
+    f64 = N * (3 + 39 + 52) + (L // 2) * 17 + (L // 2) * 70
+    ft = N * (36 + 745) + nb * 36 + L * 58
+    return f64, ft
+
+
+F_POINT_NEWTON = 1470   # per point: strain rotation (300), stress and tangent rotation (1150), test (20)
+F_STATE_NODE = 39       # state pass: per laminate (strains from the jumps)
+F_STATE_J2 = 75         # state pass: per J2 leaf (return mapping + new state)
+
+
+def newton_flops(K, iters_sum, npts, mixed):
+    """(FP64, FP32) flops of the Newton kernel over npts points with iters_sum corrections."""
+    f64, ft = pass_flops(K)
+    passes = iters_sum + npts
+    F64 = passes * f64 + npts * F_POINT_NEWTON
+    return (F64, passes * ft) if mixed else (F64 + passes * ft, 0.0)
+
+
+def final_flops(K, npts, mixed):
+    """FP64 flops of the final kernel (state pass; mixed form: plus one FP64 sweep)."""
+    N, L = (1 << K) - 1, 1 << K
+    f = npts * (300 + N * F_STATE_NODE + (L // 2) * F_STATE_J2)
+    if mixed:
+        f64, ft = pass_flops(K)
+        f += npts * (f64 + ft + 1150)
+    return f
+
+
+# ---------------------------------------------------------------------------------------------
+def src_hash():
+    h = hashlib.sha256()
+    for f in ("paper_2103_08253_gb300/csrc/dmn.cu", "paper_2103_08253_gb300/csrc/dmn_device.cuh"):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, npts_launch):
+    """DRAM bytes per launch from a committed ncu summary of the same sources (scaled by points)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("src_hash") != src_hash():
+        return None
+    return e["dram_bytes_per_point"] * npts_launch
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+def make_workload(n, rank):
+    tree = W.tree_d10_fit(K_DEPTH, seed=SEED_TREE)
+    A2, lam, Q = W.orientation_field(n, seed=SEED_ORI + 1000 * rank)
+    Ef = W.random6_path_final(n, EPS_EQ, seed=SEED_PATH + 1000 * rank)
+    return tree, A2, lam, Q, Ef
+
+
+def oracle_baseline(tree, A2, Ef, idx, warmup, steps, threads):
+    """Time the oracle (as it stands) on the points idx over increments warmup+1..warmup+steps."""
+    import oracle
+    A2s = A2[idx]
+    lam, Q = oracle.interp_orientation(A2s)
+    S = W.state_size(K_DEPTH)
+    st = np.zeros((S, len(idx)))
+    for s in range(1, warmup + 1):
+        En, dE = W.proportional_increment(Ef[idx], s, N_INCREMENTS)
+        st = oracle.update(tree, lam, Q, En, dE, st, nthreads=threads)[0]
+    t0 = time.perf_counter()
+    for s in range(warmup + 1, warmup + steps + 1):
+        lam, Q = oracle.interp_orientation(A2s)
+        En, dE = W.proportional_increment(Ef[idx], s, N_INCREMENTS)
+        st = oracle.update(tree, lam, Q, En, dE, st, nthreads=threads)[0]
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    tree, A2, lam, Q, Ef = make_workload(args.points, 0)
+    cores = os.cpu_count() or 1
+    m = args.ref_points
+    idx = np.arange(m)
+    t = oracle_baseline(tree, A2, Ef, idx, args.warmup, args.steps, cores)
+    v = m * args.steps / t
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "K": K_DEPTH, "points_per_step": m,
+                       "increments": [args.warmup + 1, args.warmup + args.steps]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "first %d points of the workload, increments %d..%d (after %d untimed)"
+                                       % (m, args.warmup + 1, args.warmup + args.steps, args.warmup)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def rel_rows(a, b):
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
+
+
+def run_form(form, ctx, args, dist):
+    """Warm-up increments, then the timed increments; returns timings and the last outputs."""
+    import torch
+    from paper_2103_08253_gb300 import dmn
+    dev, n = ctx["dev"], ctx["n"]
+    m = dmn.DMN(ctx["tree"], precision=form)
+    S = m.state_size
+    st = [torch.zeros((S, n), dtype=torch.float64, device=dev), torch.zeros((S, n), dtype=torch.float64, device=dev)]
+    lam = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    Q = torch.empty((n, 9), dtype=torch.float64, device=dev)
+    out = m.alloc_outputs(n, dev)
+    iters_steps = torch.zeros((args.steps, n), dtype=torch.int32, device=dev)
+    cur = 0
+
+    def step(s, cur, iters_buf=None):
+        m.interp_orientation(ctx["A2"], lam, Q)
+        out["state_out"] = st[1 - cur]
+        if iters_buf is not None:
+            out["iters"] = iters_buf
+        m.update(lam, Q, ctx["En"][s - 1], ctx["dE"][s - 1], st[cur], out=out)
+        return 1 - cur
+
+    for s in range(1, args.warmup + 1):
+        cur = step(s, cur)
+    torch.cuda.synchronize()
+    host_state = None
+    if form == "f64" and args.e2e_steps > 0:
+        host_state = torch.empty((S, n), dtype=torch.float64, pin_memory=True)
+        host_state.copy_(st[cur])
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(ctx["smi_id"]) if ctx["rank"] == 0 else None
+    m.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for j, s in enumerate(range(args.warmup + 1, args.warmup + args.steps + 1)):
+        cur = step(s, cur, iters_steps[j])
+    e1.record()
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    kms, cnt = m.profile_read()
+    m.profile(False)
+    its = iters_steps.to(torch.int64).sum().item()
+    hist = torch.bincount(iters_steps.reshape(-1).to(torch.int64), minlength=1).cpu().numpy()
+    res = dict(t_ms=t_ms, kms=kms, updates=cnt, clocks=clk, iters_sum=int(its), iters_hist=hist.tolist(),
+               stress=out["stress"], tangent=out["tangent"], status=out["status"], state=st[cur],
+               host_state=host_state, m=m, lam=lam, Q=Q, S=S, st=st)
+    return res
+
+
+def parity_sample(form, r, ctx, args, pidx):
+    """Oracle on the sampled points through increments 1..warmup+steps, compared with the GPU."""
+    import oracle
+    tree, A2, Ef = ctx["tree"], ctx["A2_np"], ctx["Ef_np"]
+    lam, Q = oracle.interp_orientation(A2[pidx])
+    S = W.state_size(K_DEPTH)
+    st = np.zeros((S, len(pidx)))
+    for s in range(1, args.warmup + args.steps + 1):
+        En, dE = W.proportional_increment(Ef[pidx], s, N_INCREMENTS)
+        st, sig, C, it, stat, gap = oracle.update(tree, lam, Q, En, dE, st)
+    sig_g = r["stress"][pidx].cpu().numpy()
+    C_g = r["tangent"][pidx].cpu().numpy()
+    st_g = r["state"][:, pidx].cpu().numpy()
+    ok = (stat == 0) & (r["status"][pidx].cpu().numpy() == 0)
+    scale = np.abs(st).max(axis=1, keepdims=True) + 1e-300
+    return {"points": int(len(pidx)), "max_rel_stress": float(rel_rows(sig_g[ok], sig[ok]).max(initial=0)),
+            "max_rel_tangent": float(rel_rows(C_g[ok], C[ok]).max(initial=0)),
+            "max_rel_state": float((np.abs(st_g - st) / scale).max()), "status_ok": int(ok.sum())}
+
+
+def run_e2e(r, ctx, args, dist):
+    """Same increments through the public API with host buffers: H2D of the step's inputs and
+    D2H of its results inside the timed region (FP64 form)."""
+    import torch
+    dev, n, S = ctx["dev"], ctx["n"], r["S"]
+    m = r["m"]
+    steps = min(args.e2e_steps, args.steps)
+    pin = dict(dtype=torch.float64, pin_memory=True)
+    A2_h = torch.from_numpy(ctx["A2_np"]).pin_memory()
+    En_h = [ctx["En"][s - 1].cpu().pin_memory() for s in range(args.warmup + 1, args.warmup + steps + 1)]
+    dE_h = [ctx["dE"][s - 1].cpu().pin_memory() for s in range(args.warmup + 1, args.warmup + steps + 1)]
+    hs = [r["host_state"], torch.empty((S, n), **pin)]
+    out_h = dict(stress=torch.empty((n, 6), **pin), tangent=torch.empty((n, 6, 6), **pin),
+                 iters=torch.empty(n, dtype=torch.int32, pin_memory=True),
+                 status=torch.empty(n, dtype=torch.int32, pin_memory=True))
+    A2_d = torch.empty((n, 6), dtype=torch.float64, device=dev)
+    En_d = torch.empty((n, 6), dtype=torch.float64, device=dev)
+    dE_d = torch.empty((n, 6), dtype=torch.float64, device=dev)
+    st_in, st_out = r["st"][0], r["st"][1]
+    out = m.alloc_outputs(n, dev)
+    out["state_out"] = st_out
+    lam, Q = r["lam"], r["Q"]
+    h2d = A2_h.nbytes + En_h[0].nbytes + dE_h[0].nbytes + hs[0].nbytes
+    d2h = out_h["stress"].nbytes + out_h["tangent"].nbytes + hs[1].nbytes + out_h["iters"].nbytes + out_h["status"].nbytes
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    cur = 0
+    for j in range(steps):
+        A2_d.copy_(A2_h, non_blocking=True)
+        En_d.copy_(En_h[j], non_blocking=True)
+        dE_d.copy_(dE_h[j], non_blocking=True)
+        st_in.copy_(hs[cur], non_blocking=True)
+        m.interp_orientation(A2_d, lam, Q)
+        m.update(lam, Q, En_d, dE_d, st_in, out=out)
+        for k in ("stress", "tangent", "iters", "status"):
+            out_h[k].copy_(out[k], non_blocking=True)
+        hs[1 - cur].copy_(st_out, non_blocking=True)
+        cur = 1 - cur
+    e1.record()
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    world = dist.get_world_size() if dist else 1
+    return {"value": world * n * steps / (t_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "form": "f64"}
+
+
+def roofline_f64(r, n, steps):
+    F, _ = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=False)
+    t = r["kms"]["newton"] * 1e-3
+    ach = F / t / 1e9
+    tr = ncu_traffic("k_newton_f64", n)
+    return {"bound": "alu", "kernel": "k_newton<double>", "achieved": ach, "peak": PEAK_F64_GFLOPS,
+            "unit": "GFLOP/s (FP64)", "frac": ach / PEAK_F64_GFLOPS, "traffic": tr,
+            "flops_per_launch": F / steps, "launch_ms": r["kms"]["newton"] / steps,
+            "peak_note": "derived: 152 SM x 4 SMSP x 0.5 DFMA/clk x 2 flop x 2.07 GHz"}
+
+
+def roofline_mixed(r, n, steps):
+    F64, F32 = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=True)
+    t = r["kms"]["newton"] * 1e-3
+    tb = F64 / (PEAK_F64_GFLOPS * 1e9) + F32 / (PEAK_F32_GFLOPS * 1e9)
+    Ff = final_flops(K_DEPTH, n * steps, mixed=True)
+    tf = r["kms"]["final"] * 1e-3
+    fin = {"kernel": "k_final<sweep>", "achieved": Ff / tf / 1e9, "peak": PEAK_F64_GFLOPS, "unit": "GFLOP/s (FP64)",
+           "frac": Ff / tf / 1e9 / PEAK_F64_GFLOPS, "launch_ms": r["kms"]["final"] / steps}
+    return {"bound": "alu", "kernel": "k_newton<float>", "achieved": tb / t * PEAK_F64_GFLOPS,
+            "peak": PEAK_F64_GFLOPS, "unit": "GFLOP/s (FP64-equivalent: F64/P64 + F32/P32)", "frac": tb / t,
+            "traffic": ncu_traffic("k_newton_mixed", n), "flops_f64_per_launch": F64 / steps,
+            "flops_f32_per_launch": F32 / steps, "launch_ms": r["kms"]["newton"] / steps, "final_kernel": fin}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--points", type=int, default=1 << 20)
+    ap.add_argument("--forms", default="f64,mixed")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-points", type=int, default=1024)
+    ap.add_argument("--cpu-points", type=int, default=1024)
+    ap.add_argument("--parity-points", type=int, default=16)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.warmup + args.steps > N_INCREMENTS:
+        raise SystemExit("warmup + steps must not exceed the %d increments of the load path" % N_INCREMENTS)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+def run_gpu(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    from paper_2103_08253_gb300 import dmn
+    dmn.load_library()
+    n = args.points
+    tree, A2, lam_np, Q_np, Ef = make_workload(n, rank)
+    try:
+        smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        smi_id = str(local)
+    A2_d = torch.from_numpy(A2).to(dev)
+    Ef_d = torch.from_numpy(Ef).to(dev)
+    total = args.warmup + args.steps
+    En = [Ef_d * ((s - 1) / N_INCREMENTS) for s in range(1, total + 1)]
+    dE = [Ef_d * (s / N_INCREMENTS) - En[s - 1] for s in range(1, total + 1)]
+    ctx = dict(dev=dev, n=n, tree=tree, A2=A2_d, En=En, dE=dE, smi_id=smi_id, rank=rank, A2_np=A2, Ef_np=Ef)
+    forms = [f for f in args.forms.split(",") if f]
+    rng = np.random.default_rng(7)
+    pidx = np.sort(rng.choice(n, size=min(args.parity_points, n), replace=False))
+    results, e2e = {}, None
+    for form in forms:
+        r = run_form(form, ctx, args, dist)
+        if rank == 0 and args.parity_points > 0:
+            r["parity"] = parity_sample(form, r, ctx, args, pidx)
+        if form == "f64" and args.e2e_steps > 0:
+            e2e = run_e2e(r, ctx, args, dist)
+        r["m"].close()
+        for k in ("stress", "tangent", "status", "state", "host_state", "st", "lam", "Q", "m"):
+            r.pop(k, None)
+        torch.cuda.empty_cache()
+        results[form] = r
+    if rank != 0:
+        return 0
+    steps = args.steps
+    forms_out = {}
+    for form, r in results.items():
+        v = world * n * steps / (r["t_ms"] * 1e-3)
+        forms_out[form] = {"value": v, "unit": UNIT, "ms_per_step": r["t_ms"] / steps,
+                           "kernel_ms_per_step": {k: x / steps for k, x in r["kms"].items()},
+                           "newton_iters_per_update": r["iters_sum"] / (n * steps), "iters_hist": r["iters_hist"],
+                           "roofline": roofline_f64(r, n, steps) if form == "f64" else roofline_mixed(r, n, steps),
+                           "parity_vs_oracle": r.get("parity"), "clocks": r["clocks"]}
+    main_form = "f64" if "f64" in results else forms[0]
+    mr = results[main_form]
+    cpu = None
+    if world == 1 and args.cpu_points > 0:
+        cores = os.cpu_count() or 1
+        idx = np.arange(min(args.cpu_points, n))
+        t = oracle_baseline(tree, A2, Ef, idx, args.warmup, min(3, steps), cores)
+        cpu = {"value": len(idx) * min(3, steps) / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "first %d points, increments %d..%d after %d untimed, orientation set-up included"
+                         % (len(idx), args.warmup + 1, args.warmup + min(3, steps), args.warmup)}
+    line = {"metric": METRIC, "value": forms_out[main_form]["value"], "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": mr["t_ms"] / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_form == "f64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "K": K_DEPTH, "points_per_gpu": n, "increments": N_INCREMENTS,
+                       "timed_increments": [args.warmup + 1, args.warmup + steps],
+                       "l2": "no flush: per-step inputs (state %.1f GB) exceed L2" % (W.state_size(K_DEPTH) * n * 8e-9),
+                       "parallelism": "independent point shards per GPU, no collective"},
+            "roofline": forms_out[main_form]["roofline"], "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 4 * steps, "clocks": mr["clocks"], "forms": forms_out}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,163 @@
+/*
+ * dmn.h - C ABI of the batched DMN material-point update on GB300 (sm_103a).
+ *
+ * A direct deep material network (DMN) is a perfect binary tree of depth K of
+ * rank-one laminates (Gajek, Schneider, Boehlke, "An FE-DMN method for the
+ * multiscale analysis of fiber reinforced plastic components", Sec. 2.1).
+ * Leaves alternate between phase 1 (odd leaves, e.g. elastic glass fiber) and
+ * phase 2 (even leaves, e.g. a J2-elastoplastic matrix).  Lamination normals
+ * are interpolated over the fiber-orientation triangle (Sec. 2.3).  For every
+ * Gauss point the update solves the DMN's Euler-Lagrange equation
+ * A^T W sigma(E + A a, z^n) = 0 for the displacement jumps a by Newton's
+ * method and returns the effective stress, the algorithmic tangent and the
+ * new state (Sec. 3.2; criterion and tolerance of Sec. 4.6).
+ *
+ * Conventions used by every entry point
+ *   - Symmetric tensors are 6-vectors ordered (11, 22, 33, 23, 13, 12).
+ *     Strains and stresses are Mandel vectors (shear entries times sqrt(2)),
+ *     so the Euclidean norm is the Frobenius norm.  The orientation tensor A2
+ *     uses plain components.  Tangents are Mandel 6x6, row-major.
+ *   - Frames Q are row-major 3x3 with the eigenvectors of A2 as columns
+ *     (A2 = Q diag(lam1, lam2, lam3) Q^T, det Q = +1).  Strains are rotated
+ *     into that frame before the DMN is evaluated, stress and tangent back.
+ *   - Per-point arrays are point-major ([n][6] means element c of point i at
+ *     index 6*i + c).  The state is field-major: field f of point i lives at
+ *     state[f * n + i].  Per inelastic leaf, in leaf order, six fields
+ *     (alpha_bar, ep11, ep22, sqrt2*ep23, sqrt2*ep13, sqrt2*ep12) of the
+ *     equivalent plastic strain and the deviatoric plastic strain
+ *     (ep33 = -ep11 - ep22); then three jump components per laminate in the
+ *     paper's ordering (level K first, root last; Sec. 3.2, Eq. of the normal
+ *     ordering).  A zero state is the virgin state.
+ *   - Pointers named "dev" are CUDA device pointers; "host" are host
+ *     pointers.  The caller owns every array passed in; the handle owns its
+ *     parameters and work space.  Device calls are asynchronous on the given
+ *     stream (a cudaStream_t passed as void*, NULL = legacy default stream).
+ *   - Return codes: 0 = success; DMN_ERR_ARG (-1) invalid argument, nothing
+ *     launched; DMN_ERR_CUDA (-2) a CUDA call failed (dmn_last_error has the
+ *     message).  Kernels never trap: per-point failures are reported in the
+ *     status array.
+ *   - One handle may have one update in flight at a time: concurrent calls
+ *     on the same handle share its work space and race.
+ */
+#ifndef DMN_H
+#define DMN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmn_handle dmn_handle;
+
+enum { DMN_OK = 0, DMN_ERR_ARG = -1, DMN_ERR_CUDA = -2 };
+
+/* phase laws: linear elastic (sigma = 3K P1 eps + 2G P2 eps) and J2
+ * plasticity with linear isotropic hardening sigma_Y = sigma0 + H alpha_bar,
+ * integrated by implicit Euler (radial return; Sec. 4.1 takes the J2 law with
+ * isotropic hardening from Simo-Hughes ch. 3) */
+enum { DMN_PHASE_ELASTIC = 0, DMN_PHASE_J2_LINEAR = 1 };
+
+/* DMN_PREC_F64: every step in FP64.
+ * DMN_PREC_MIXED: leaf tangents, laminate condensation and jump corrections
+ * in FP32; leaf stresses, strains, jumps, the Newton residual and the final
+ * sweep that yields stress and tangent in FP64. */
+enum { DMN_PREC_F64 = 0, DMN_PREC_MIXED = 1 };
+
+/* per-point status */
+enum { DMN_STATUS_OK = 0, DMN_STATUS_MAXITER = 1, DMN_STATUS_NONFINITE = 2 };
+
+typedef struct {
+  int32_t kind;    /* DMN_PHASE_* */
+  double E, nu;    /* Young's modulus (MPa), Poisson's ratio */
+  double sigma0;   /* J2: initial yield stress (MPa) */
+  double H;        /* J2: linear hardening modulus (MPa) */
+} dmn_phase;
+
+typedef struct {
+  int32_t K;         /* depth, 1..8: 2^K - 1 laminates, 2^K leaves (Sec. 2.1) */
+  int32_t M;         /* shape functions: 3 linear, 4 tri-linear, 6 quadratic (Tab. of shape functions) */
+  const double* p;   /* host [(2^K-1) * M]: alpha_j = p_j . phi(lam1, lam2) (rad), paper ordering (Sec. 3.1) */
+  const double* q;   /* host [(2^K-1) * M]: beta_j  = q_j . phi(lam1, lam2) (rad) */
+  const double* w;   /* host [2^K]: leaf weights, all > 0; normalised to sum 1 (Sec. 2.1) */
+  dmn_phase phase[2];/* phase 1 = odd leaves, phase 2 = even leaves (Sec. 2.1) */
+} dmn_tree_desc;
+
+typedef struct {
+  double tol;          /* ||A^T W sigma|| / ((2^K - 1) ||sigma_bar||) <= tol (Sec. 4.6); <= 0 selects 1e-12 */
+  int32_t max_iter;    /* Newton corrections before status MAXITER; <= 0 selects 50 */
+  int32_t precision;   /* DMN_PREC_F64 or DMN_PREC_MIXED */
+  int32_t block;       /* threads per CTA of the Newton kernel (multiple of 32); 0 selects 128 */
+  int32_t ctas_per_sm; /* resident CTAs per SM of the persistent Newton kernel; 0 selects 2 */
+} dmn_options;
+
+/* Create a handle for n_trees DMNs (n_trees = 1 in this version).  Copies the
+ * parameters to the device, propagates the leaf weights to the laminate
+ * volume fractions (Sec. 2.1) and allocates the work space of the persistent
+ * Newton kernel on the current CUDA device.  opt may be NULL (defaults).
+ * Errors: DMN_ERR_ARG for K outside 1..8, M not in {3,4,6}, a weight <= 0 or
+ * non-finite, an unknown phase kind or non-positive moduli; DMN_ERR_CUDA if
+ * an allocation fails.  On error *out is NULL. */
+int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* opt, dmn_handle** out);
+
+/* Free the handle and its device memory (synchronises the device).  NULL is a no-op. */
+void dmn_destroy(dmn_handle* h);
+
+/* Doubles of state per point for tree tree_id: 6 per inelastic leaf plus
+ * 3 per laminate (1533 for K = 8 with one inelastic phase; the paper counts
+ * the same 128 x (1 + 5) + 255 x 3 scalars, Sec. 4.7).  -1 on a bad argument. */
+int64_t dmn_state_size(const dmn_handle* h, int32_t tree_id);
+
+/* Orientation set-up (Sec. 2.2, Eq. of the eigen decomposition of A2):
+ * A2 dev [n][6] (plain components, symmetric positive semi-definite, unit
+ * trace) -> lam dev [n][2] = (lam1, lam2), the two largest eigenvalues,
+ * lam1 >= lam2 >= lam3, and Q dev [n][9], the eigenvectors as columns of a
+ * rotation; each of the first two columns is signed so that its entry of
+ * largest magnitude is positive, the third is their cross product.
+ * n = 0 is a no-op.  Errors: DMN_ERR_ARG for n < 0 or NULL arrays with n > 0. */
+int dmn_interp_orientation(dmn_handle* h, int64_t n, const double* A2, double* lam, double* Q, void* stream);
+
+/* One implicit material-point update of n points (Sec. 3.2):
+ *   lam      dev [n][2]   orientation eigenvalues (from dmn_interp_orientation)
+ *   Q        dev [n][9]   principal frames
+ *   E_n, dE  dev [n][6]   macro strain at the start of the increment and its
+ *                          increment (Mandel, global frame); E = E_n + dE
+ *   state_in dev [S][n]   z^n and the last converged jumps a^n (read only)
+ *   state_out dev [S][n]  z^{n+1}, a^{n+1}; must not overlap state_in
+ *   stress   dev [n][6]   effective stress sigma_bar = sum_i w_i sigma_i (Mandel, global)
+ *   tangent  dev [n][36]  algorithmic tangent d sigma_bar / d E (Eq. lin_system_da_dE)
+ *   iters    dev [n]      Newton corrections applied
+ *   status   dev [n]      DMN_STATUS_*; NONFINITE writes NaN to stress,
+ *                          tangent and the point's state_out
+ * tree_id must be NULL (one tree).  The Newton iteration starts from a^n
+ * (Sec. 4.7) and stops when the criterion of Sec. 4.6 holds.  The first call
+ * with a larger n than any earlier call allocates per-point work space
+ * (cudaMalloc, synchronous).  Errors: DMN_ERR_ARG for n < 0, NULL arrays with
+ * n > 0, state_in == state_out, a non-NULL tree_id. */
+int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam, const double* Q,
+               const double* E_n, const double* dE, const double* state_in, double* state_out, double* stress,
+               double* tangent, int32_t* iters, int32_t* status, void* stream);
+
+/* Per-kernel timing of dmn_update, for measurement: while enabled, CUDA
+ * events are recorded on the update's stream before and after each of its
+ * kernels.  enable != 0 clears the totals and starts recording; 0 stops.
+ * Errors: DMN_ERR_ARG for a NULL handle. */
+int dmn_profile_enable(dmn_handle* h, int32_t enable);
+
+/* Totals since dmn_profile_enable(h, 1): ms[0] orientation normals kernel,
+ * ms[1] Newton kernel, ms[2] final-sweep kernel (milliseconds, summed over
+ * the timed updates), *updates = number of timed updates.  Waits for the
+ * recorded events.  Errors: DMN_ERR_ARG for NULL arguments, DMN_ERR_CUDA if
+ * an event query fails. */
+int dmn_profile_read(dmn_handle* h, double ms[3], int64_t* updates);
+
+/* Message of the last failed call on this handle (or of the last failed
+ * dmn_create when h is NULL); "" if none.  Valid until the next call. */
+const char* dmn_last_error(const dmn_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMN_H */

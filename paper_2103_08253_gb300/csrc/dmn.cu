@@ -1,0 +1,600 @@
+// Kernels and C ABI of the batched DMN material-point update (include/dmn.h).
+//
+// Per update three kernels run on the caller's stream:
+//   k_normals  one thread per point: lamination normals of every laminate from
+//              the orientation (barycentric coordinates, shape functions,
+//              interpolated angles, spherical normal; Sec. 2.3);
+//   k_newton   persistent, one thread per point slot: the Newton loop of
+//              Sec. 3.2.  A lane that converges writes its results and takes
+//              the next point from a global counter at once, so lanes stay busy
+//              although points need different numbers of Newton steps;
+//   k_final    one thread per point: the return mapping at the converged jumps
+//              writes z^{n+1}; in the mixed form also the FP64 sweep that
+//              yields stress and algorithmic tangent.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <array>
+
+#include "../../include/dmn.h"
+#include "dmn_device.cuh"
+
+using namespace dmn;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Tree {
+  int K, M, N, L, nz, z_both, S;
+  double* d_p = nullptr;
+  double* d_q = nullptr;
+  double* d_c1 = nullptr;
+  double* d_c2 = nullptr;
+  double* d_W = nullptr;
+  PhaseDev ph[2];
+};
+
+}  // namespace
+
+struct dmn_handle {
+  Tree tree;
+  dmn_options opt;
+  int device = 0, n_sm = 0;
+  int64_t nslots = 0;
+  double* scr_d = nullptr;      // per slot: normals [3N] + jumps [3N] (FP64)
+  void* scr_t = nullptr;        // per slot: g [3N] + H [18N] (FP64 or FP32)
+  unsigned long long* counter = nullptr;
+  double* nbuf = nullptr;       // per point normals [3N][n]
+  int64_t nbuf_cap = 0;
+  bool profiling = false;
+  std::vector<std::array<cudaEvent_t, 4>> events;  // per timed update: before/after each kernel
+  size_t events_used = 0;
+  std::string err;
+};
+
+namespace {
+
+int fail(dmn_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(dmn_handle* h, cudaError_t e, const char* what) {
+  return fail(h, DMN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+TreeDev tree_dev(const Tree& t) {
+  TreeDev d;
+  d.K = t.K; d.M = t.M; d.N = t.N; d.L = t.L; d.nz = t.nz; d.z_both = t.z_both;
+  d.p = t.d_p; d.q = t.d_q; d.c1 = t.d_c1; d.c2 = t.d_c2; d.W = t.d_W;
+  d.ph[0] = t.ph[0]; d.ph[1] = t.ph[1];
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// Weights (Sec. 2.1): w normalised to sum 1; w^i_k = w^{2i-1}_{k+1} + w^{2i}_{k+1};
+// c1 = w_left / (w_left + w_right), c2 = 1 - c1.  Heap order.  One thread.
+__global__ void k_setup_tree(int K, const double* w_raw, double* W, double* c1, double* c2) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int L = 1 << K, N = L - 1;
+  double s = 0.0;
+  for (int l = 0; l < L; ++l) s += w_raw[l];
+  for (int h = N; h >= 1; --h) {
+    double wl, wr;
+    if (h >= (1 << (K - 1))) {
+      const int m = h - (1 << (K - 1));
+      wl = w_raw[2 * m] / s;
+      wr = w_raw[2 * m + 1] / s;
+    } else {
+      wl = W[2 * h - 1];
+      wr = W[2 * h];
+    }
+    W[h - 1] = wl + wr;
+    c1[h - 1] = wl / (wl + wr);
+    c2[h - 1] = 1.0 - c1[h - 1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Orientation set-up: cyclic Jacobi rotations on the symmetric 3x3 A2,
+// eigenvalues sorted descending, eigenvector signs normalised (see dmn.h).
+__global__ void k_interp(int64_t n, const double* __restrict__ A2, double* __restrict__ lam, double* __restrict__ Q) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* a = A2 + 6 * i;
+  double S[3][3] = {{a[0], a[5], a[4]}, {a[5], a[1], a[3]}, {a[4], a[3], a[2]}};
+  double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int sweep = 0; sweep < 32; ++sweep) {
+    const double off = fabs(S[0][1]) + fabs(S[0][2]) + fabs(S[1][2]);
+    const double dia = fabs(S[0][0]) + fabs(S[1][1]) + fabs(S[2][2]);
+    if (off <= 1e-30 * dia) break;
+#pragma unroll
+    for (int pr = 0; pr < 3; ++pr) {
+      const int p = pr == 2 ? 1 : 0, q = pr == 0 ? 1 : 2;
+      const double apq = S[p][q];
+      if (apq == 0.0) continue;
+      // rotation angle that annihilates S[p][q]: t = tan(phi), |phi| <= pi/4
+      const double tau = (S[q][q] - S[p][p]) / (2.0 * apq);
+      const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      const double c = rsqrt(1.0 + t * t), s = t * c;
+      for (int k = 0; k < 3; ++k) {
+        const double skp = S[k][p], skq = S[k][q];
+        S[k][p] = c * skp - s * skq;
+        S[k][q] = s * skp + c * skq;
+      }
+      for (int k = 0; k < 3; ++k) {
+        const double spk = S[p][k], sqk = S[q][k];
+        S[p][k] = c * spk - s * sqk;
+        S[q][k] = s * spk + c * sqk;
+      }
+      for (int k = 0; k < 3; ++k) {
+        const double vkp = V[k][p], vkq = V[k][q];
+        V[k][p] = c * vkp - s * vkq;
+        V[k][q] = s * vkp + c * vkq;
+      }
+    }
+  }
+  double l[3] = {S[0][0], S[1][1], S[2][2]};
+  int o[3] = {0, 1, 2};
+  // order indices by descending eigenvalue
+  if (l[o[1]] > l[o[0]]) { int x = o[0]; o[0] = o[1]; o[1] = x; }
+  if (l[o[2]] > l[o[1]]) { int x = o[1]; o[1] = o[2]; o[2] = x; }
+  if (l[o[1]] > l[o[0]]) { int x = o[0]; o[0] = o[1]; o[1] = x; }
+  double v[2][3];
+  for (int c = 0; c < 2; ++c) {
+    int m = 0;
+    for (int k = 1; k < 3; ++k)
+      if (fabs(V[k][o[c]]) > fabs(V[m][o[c]])) m = k;
+    const double sg = V[m][o[c]] < 0.0 ? -1.0 : 1.0;
+    for (int k = 0; k < 3; ++k) v[c][k] = sg * V[k][o[c]];
+  }
+  const double w3[3] = {v[0][1] * v[1][2] - v[0][2] * v[1][1], v[0][2] * v[1][0] - v[0][0] * v[1][2],
+                        v[0][0] * v[1][1] - v[0][1] * v[1][0]};
+  lam[2 * i] = l[o[0]];
+  lam[2 * i + 1] = l[o[1]];
+  double* Qi = Q + 9 * i;
+  for (int k = 0; k < 3; ++k) { Qi[3 * k + 0] = v[0][k]; Qi[3 * k + 1] = v[1][k]; Qi[3 * k + 2] = w3[k]; }
+}
+
+// ---------------------------------------------------------------------------
+// Normals of every laminate (Sec. 2.3): phi = barycentric coordinates of
+// (lam1, lam2) in the triangle UD (1,0), ISO (1/3,1/3), PI (1/2,1/2), i.e.
+// phi = (lam1 - lam2, 3 lam3, 2 lam1 + 4 lam2 - 2); shape functions of order M;
+// alpha = p.phi, beta = q.phi; n = (sin a cos b, sin a sin b, cos a).
+__global__ void k_normals(TreeDev t, int64_t n, const double* __restrict__ lam, double* __restrict__ nbuf) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double l1 = lam[2 * i], l2 = lam[2 * i + 1];
+  const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
+  double ph[6];
+  if (t.M == 3) {
+    ph[0] = v[0]; ph[1] = v[1]; ph[2] = v[2];
+  } else if (t.M == 4) {
+    const double b = v[0] * v[1] * v[2];
+    ph[0] = v[0] - 9.0 * b; ph[1] = v[1] - 9.0 * b; ph[2] = v[2] - 9.0 * b; ph[3] = 27.0 * b;
+  } else {
+    ph[0] = v[0] * (2.0 * v[0] - 1.0); ph[1] = v[1] * (2.0 * v[1] - 1.0); ph[2] = v[2] * (2.0 * v[2] - 1.0);
+    ph[3] = 4.0 * v[0] * v[1]; ph[4] = 4.0 * v[0] * v[2]; ph[5] = 4.0 * v[1] * v[2];
+  }
+  for (int j = 0; j < t.N; ++j) {
+    double al = 0.0, be = 0.0;
+    for (int m = 0; m < t.M; ++m) {
+      al += __ldg(t.p + j * t.M + m) * ph[m];
+      be += __ldg(t.q + j * t.M + m) * ph[m];
+    }
+    double sa, ca, sb, cb;
+    sincos(al, &sa, &ca);
+    sincos(be, &sb, &cb);
+    nbuf[(size_t)(3 * j + 0) * n + i] = sa * cb;
+    nbuf[(size_t)(3 * j + 1) * n + i] = sa * sb;
+    nbuf[(size_t)(3 * j + 2) * n + i] = ca;
+  }
+}
+
+__device__ __forceinline__ void local_strain(const double* Q, const double* En, const double* dE, double Eloc[6]) {
+  double R[6][6], Eg[6];
+  mandel_rotation(Q, R);
+#pragma unroll
+  for (int I = 0; I < 6; ++I) Eg[I] = En[I] + dE[I];
+#pragma unroll
+  for (int J = 0; J < 6; ++J) {
+    double s = 0.0;
+#pragma unroll
+    for (int I = 0; I < 6; ++I) s += R[I][J] * Eg[I];
+    Eloc[J] = s;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void write_stress_tangent(const double* Q, const double sb[6], const T C[21], double* stress,
+                                                     double* tangent) {
+  double R[6][6];
+  mandel_rotation(Q, R);
+#pragma unroll
+  for (int I = 0; I < 6; ++I) {
+    double s = 0.0;
+#pragma unroll
+    for (int J = 0; J < 6; ++J) s += R[I][J] * sb[J];
+    stress[I] = s;
+  }
+  double RC[6][6];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = 0; J < 6; ++J) {
+      double s = 0.0;
+#pragma unroll
+      for (int P = 0; P < 6; ++P) s += R[I][P] * (double)C[sidx(P, J)];
+      RC[I][J] = s;
+    }
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = 0; J < 6; ++J) {
+      double s = 0.0;
+#pragma unroll
+      for (int P = 0; P < 6; ++P) s += RC[I][P] * R[J][P];
+      tangent[6 * I + J] = s;
+    }
+}
+
+template <typename T>
+struct NewtonParams {
+  TreeDev t;
+  int64_t n, nslots;
+  const double *Q, *En, *dE, *state_in;
+  double *state_out, *stress, *tangent;
+  int32_t *iters, *status;
+  const double* nbuf;
+  double* scr_d;
+  T* scr_t;
+  unsigned long long* counter;
+  double tol;
+  int max_iter;
+  int write_outputs;  // FP64 form: stress and tangent come from the converged Newton pass
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_newton(NewtonParams<T> P) {
+  const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const TreeDev& t = P.t;
+  const int N = t.N;
+  double* my_nrm = P.scr_d + slot;
+  PointArrays A;
+  A.nrm = my_nrm; A.ns = (size_t)P.nslots;
+  A.a = P.scr_d + (size_t)(3 * N) * P.nslots + slot; A.as = (size_t)P.nslots;
+  A.paper = false;
+  A.z = nullptr; A.zs = (size_t)P.n;
+  GH<T> gh{P.scr_t + slot, (size_t)P.nslots};
+  const int nzf = 6 * t.nz;
+  int64_t pt = -1;
+  int it = 0;
+  double Eloc[6];
+  for (;;) {
+    const bool need = pt < 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, need);
+    if (mask) {
+      const int leader = __ffs(mask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(P.counter, (unsigned long long)__popc(mask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        pt = (int64_t)(base + __popc(mask & ((1u << lane) - 1u)));
+        if (pt < P.n) {
+          local_strain(P.Q + 9 * pt, P.En + 6 * pt, P.dE + 6 * pt, Eloc);
+          for (int f = 0; f < 3 * N; ++f) {
+            const int node = f / 3, c = f - 3 * node;
+            // heap node -> paper index of its jumps
+            const int lvl = 32 - __clz(node + 1);
+            const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+            A.a[(size_t)f * A.as] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
+            my_nrm[(size_t)f * A.ns] = P.nbuf[(size_t)f * P.n + pt];
+          }
+          A.z = P.state_in + pt;
+          it = 0;
+        }
+      }
+    }
+    const bool active = pt >= 0 && pt < P.n;
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (!active) continue;
+    Sub<T> root;
+    double r2;
+    tree_pass<T, true>(t, Eloc, A, gh, it > 0, root, r2, nullptr);
+    const double rn = sqrt(r2);
+    double sn2 = 0.0;
+#pragma unroll
+    for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
+    const double sn = sqrt(sn2);
+    int st = -1;
+    if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
+    else if (rn <= P.tol * (double)N * sn) st = DMN_STATUS_OK;
+    else if (it >= P.max_iter) st = DMN_STATUS_MAXITER;
+    if (st < 0) { ++it; continue; }
+    // finished point: jumps (paper ordering), counters, and in the FP64 form stress + tangent
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int f = 0; f < 3 * N; ++f) {
+      const int node = f / 3, c = f - 3 * node;
+      const int lvl = 32 - __clz(node + 1);
+      const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+      P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt] = st == DMN_STATUS_NONFINITE ? qnan : A.a[(size_t)f * A.as];
+    }
+    P.iters[pt] = it;
+    P.status[pt] = st;
+    if (P.write_outputs) {
+      if (st == DMN_STATUS_NONFINITE) {
+        for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
+        for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
+      } else {
+        write_stress_tangent<T>(P.Q + 9 * pt, root.sb, root.C, P.stress + 6 * pt, P.tangent + 36 * pt);
+      }
+    }
+    pt = -1;
+  }
+}
+
+struct FinalParams {
+  TreeDev t;
+  int64_t n;
+  const double *Q, *En, *dE, *state_in;
+  double *state_out, *stress, *tangent;
+  const int32_t* status;
+  const double* nbuf;
+};
+
+template <bool SWEEP>
+__global__ void __launch_bounds__(128) k_final(FinalParams P) {
+  const int64_t pt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pt >= P.n) return;
+  const TreeDev& t = P.t;
+  const int st = P.status[pt];
+  double Eloc[6];
+  local_strain(P.Q + 9 * pt, P.En + 6 * pt, P.dE + 6 * pt, Eloc);
+  PointArrays A;
+  A.nrm = P.nbuf + pt; A.ns = (size_t)P.n;
+  A.a = P.state_out + (size_t)(6 * t.nz) * P.n + pt; A.as = (size_t)P.n;
+  A.paper = true;
+  A.z = P.state_in + pt; A.zs = (size_t)P.n;
+  if (SWEEP) {
+    if (st == DMN_STATUS_NONFINITE) {
+      const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+      for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
+      for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
+    } else {
+      Sub<double> root;
+      double r2;
+      GH<double> gh{nullptr, 0};
+      tree_pass<double, false>(t, Eloc, A, gh, false, root, r2, nullptr);
+      write_stress_tangent<double>(P.Q + 9 * pt, root.sb, root.C, P.stress + 6 * pt, P.tangent + 36 * pt);
+    }
+  }
+  write_leaf_states(t, Eloc, A, P.state_out + pt, (size_t)P.n, st == DMN_STATUS_NONFINITE);
+}
+
+int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+
+extern "C" {
+
+int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* opt, dmn_handle** out) {
+  if (!out) return fail(nullptr, DMN_ERR_ARG, "dmn_create: out is NULL");
+  *out = nullptr;
+  g_create_error.clear();
+  if (!trees || n_trees != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: exactly one tree is supported");
+  const dmn_tree_desc& d = trees[0];
+  if (d.K < 1 || d.K > KMAX) return fail(nullptr, DMN_ERR_ARG, "dmn_create: K must be in 1..8");
+  if (d.M != 3 && d.M != 4 && d.M != 6) return fail(nullptr, DMN_ERR_ARG, "dmn_create: M must be 3, 4 or 6");
+  if (!d.p || !d.q || !d.w) return fail(nullptr, DMN_ERR_ARG, "dmn_create: p, q, w must be non-NULL");
+  const int K = d.K, M = d.M, N = (1 << K) - 1, L = 1 << K;
+  for (int l = 0; l < L; ++l)
+    if (!(d.w[l] > 0.0) || !std::isfinite(d.w[l]))
+      return fail(nullptr, DMN_ERR_ARG, "dmn_create: leaf weights must be finite and > 0");
+  for (int j = 0; j < N * M; ++j)
+    if (!std::isfinite(d.p[j]) || !std::isfinite(d.q[j]))
+      return fail(nullptr, DMN_ERR_ARG, "dmn_create: p, q must be finite");
+  Tree t;
+  t.K = K; t.M = M; t.N = N; t.L = L;
+  int n_inel_phase = 0;
+  for (int f = 0; f < 2; ++f) {
+    const dmn_phase& p = d.phase[f];
+    if (p.kind != DMN_PHASE_ELASTIC && p.kind != DMN_PHASE_J2_LINEAR)
+      return fail(nullptr, DMN_ERR_ARG, "dmn_create: unknown phase kind");
+    if (!(p.E > 0.0) || !(p.nu > -1.0) || !(p.nu < 0.5))
+      return fail(nullptr, DMN_ERR_ARG, "dmn_create: need E > 0 and -1 < nu < 0.5");
+    if (p.kind == DMN_PHASE_J2_LINEAR && (!(p.sigma0 > 0.0) || !(p.H >= 0.0)))
+      return fail(nullptr, DMN_ERR_ARG, "dmn_create: J2 phase needs sigma0 > 0 and H >= 0");
+    t.ph[f].kind = p.kind;
+    t.ph[f].K = p.E / (3.0 * (1.0 - 2.0 * p.nu));
+    t.ph[f].G = p.E / (2.0 * (1.0 + p.nu));
+    t.ph[f].s0 = p.sigma0;
+    t.ph[f].H = p.H;
+    n_inel_phase += p.kind == DMN_PHASE_J2_LINEAR;
+  }
+  t.z_both = n_inel_phase == 2;
+  t.nz = n_inel_phase * (L / 2);
+  t.S = 6 * t.nz + 3 * N;
+
+  dmn_options o;
+  o.tol = 1e-12; o.max_iter = 50; o.precision = DMN_PREC_F64; o.block = 128; o.ctas_per_sm = 2;
+  if (opt) {
+    if (opt->tol > 0.0) o.tol = opt->tol;
+    if (opt->max_iter > 0) o.max_iter = opt->max_iter;
+    o.precision = opt->precision;
+    if (opt->block > 0) o.block = opt->block;
+    if (opt->ctas_per_sm > 0) o.ctas_per_sm = opt->ctas_per_sm;
+  }
+  if (o.precision != DMN_PREC_F64 && o.precision != DMN_PREC_MIXED)
+    return fail(nullptr, DMN_ERR_ARG, "dmn_create: unknown precision");
+  if (o.block % 32 != 0 || o.block > 128)
+    return fail(nullptr, DMN_ERR_ARG, "dmn_create: block must be a multiple of 32 and at most 128");
+  if (o.ctas_per_sm > 16) return fail(nullptr, DMN_ERR_ARG, "dmn_create: ctas_per_sm must be at most 16");
+
+  dmn_handle* h = new dmn_handle();
+  h->tree = t;
+  h->opt = o;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "dmn_create: device query"); }
+
+  // parameters in heap order
+  std::vector<double> ph(N * M), qh(N * M);
+  for (int k = 1; k <= K; ++k)
+    for (int i = 1; i <= (1 << (k - 1)); ++i) {
+      const int j = (1 << K) - (1 << k) + (i - 1);   // paper ordering
+      const int hn = (1 << (k - 1)) + i - 1;        // heap node index
+      for (int m = 0; m < M; ++m) { ph[hn * M + m] = d.p[j * M + m]; qh[hn * M + m] = d.q[j * M + m]; }
+    }
+  double* d_w = nullptr;
+  Tree& T = h->tree;
+  e = cudaMalloc(&T.d_p, sizeof(double) * N * M);
+  if (e == cudaSuccess) e = cudaMalloc(&T.d_q, sizeof(double) * N * M);
+  if (e == cudaSuccess) e = cudaMalloc(&T.d_c1, sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&T.d_c2, sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&T.d_W, sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&d_w, sizeof(double) * L);
+  if (e == cudaSuccess) e = cudaMemcpy(T.d_p, ph.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(T.d_q, qh.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_w, d.w, sizeof(double) * L, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_setup_tree<<<1, 1>>>(K, d_w, T.d_W, T.d_c1, T.d_c2);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d_w);
+  h->nslots = (int64_t)h->n_sm * o.ctas_per_sm * o.block;
+  if (e == cudaSuccess) e = cudaMalloc(&h->scr_d, sizeof(double) * (size_t)(6 * N) * h->nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&h->scr_t, sizeof(double) * (size_t)(21 * N) * h->nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&h->counter, sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    dmn_destroy(h);
+    return cuda_fail(nullptr, e, "dmn_create");
+  }
+  *out = h;
+  return DMN_OK;
+}
+
+void dmn_destroy(dmn_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (auto& a : h->events)
+    for (auto& x : a) cudaEventDestroy(x);
+  cudaFree(h->tree.d_p); cudaFree(h->tree.d_q); cudaFree(h->tree.d_c1); cudaFree(h->tree.d_c2);
+  cudaFree(h->tree.d_W); cudaFree(h->scr_d); cudaFree(h->scr_t); cudaFree(h->counter); cudaFree(h->nbuf);
+  delete h;
+}
+
+int64_t dmn_state_size(const dmn_handle* h, int32_t tree_id) {
+  if (!h || tree_id != 0) return -1;
+  return h->tree.S;
+}
+
+int dmn_profile_enable(dmn_handle* h, int32_t enable) {
+  if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_profile_enable: NULL handle");
+  h->profiling = enable != 0;
+  if (enable) h->events_used = 0;
+  return DMN_OK;
+}
+
+int dmn_profile_read(dmn_handle* h, double ms[3], int64_t* updates) {
+  if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_profile_read: NULL handle");
+  if (!ms || !updates) return fail(h, DMN_ERR_ARG, "dmn_profile_read: NULL output");
+  ms[0] = ms[1] = ms[2] = 0.0;
+  for (size_t i = 0; i < h->events_used; ++i) {
+    const auto& a = h->events[i];
+    cudaError_t e = cudaEventSynchronize(a[3]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_profile_read");
+    for (int k = 0; k < 3; ++k) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, a[k], a[k + 1]);
+      if (e != cudaSuccess) return cuda_fail(h, e, "dmn_profile_read");
+      ms[k] += t;
+    }
+  }
+  *updates = (int64_t)h->events_used;
+  return DMN_OK;
+}
+
+const char* dmn_last_error(const dmn_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int dmn_interp_orientation(dmn_handle* h, int64_t n, const double* A2, double* lam, double* Q, void* stream) {
+  if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_interp_orientation: NULL handle");
+  if (n < 0) return fail(h, DMN_ERR_ARG, "dmn_interp_orientation: n < 0");
+  if (n == 0) return DMN_OK;
+  if (!A2 || !lam || !Q) return fail(h, DMN_ERR_ARG, "dmn_interp_orientation: NULL array");
+  cudaStream_t s = (cudaStream_t)stream;
+  k_interp<<<(unsigned)div_up(n, 128), 128, 0, s>>>(n, A2, lam, Q);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DMN_OK : cuda_fail(h, e, "dmn_interp_orientation");
+}
+
+int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam, const double* Q,
+               const double* E_n, const double* dE, const double* state_in, double* state_out, double* stress,
+               double* tangent, int32_t* iters, int32_t* status, void* stream) {
+  if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_update: NULL handle");
+  if (n < 0) return fail(h, DMN_ERR_ARG, "dmn_update: n < 0");
+  if (tree_id) return fail(h, DMN_ERR_ARG, "dmn_update: tree_id must be NULL (one tree)");
+  if (n == 0) return DMN_OK;
+  if (!lam || !Q || !E_n || !dE || !state_in || !state_out || !stress || !tangent || !iters || !status)
+    return fail(h, DMN_ERR_ARG, "dmn_update: NULL array");
+  if (state_in == state_out) return fail(h, DMN_ERR_ARG, "dmn_update: state_in and state_out must differ");
+  const Tree& t = h->tree;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (n > h->nbuf_cap) {
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) { cudaFree(h->nbuf); h->nbuf = nullptr; h->nbuf_cap = 0; }
+    if (e == cudaSuccess) e = cudaMalloc(&h->nbuf, sizeof(double) * (size_t)(3 * t.N) * n);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: normals buffer");
+    h->nbuf_cap = n;
+  }
+  const TreeDev td = tree_dev(t);
+  const unsigned g1 = (unsigned)div_up(n, 128);
+  cudaEvent_t* ev = nullptr;
+  if (h->profiling) {
+    if (h->events_used == h->events.size()) {
+      std::array<cudaEvent_t, 4> a;
+      for (auto& x : a) {
+        e = cudaEventCreate(&x);
+        if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: profiling event");
+      }
+      h->events.push_back(a);
+    }
+    ev = h->events[h->events_used++].data();
+    cudaEventRecord(ev[0], s);
+  }
+  k_normals<<<g1, 128, 0, s>>>(td, n, lam, h->nbuf);
+  if (ev) cudaEventRecord(ev[1], s);
+  e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: counter reset");
+  // the Newton interval includes the counter reset (a few hundred ns)
+  const unsigned grid = (unsigned)(h->n_sm * h->opt.ctas_per_sm);
+  const bool mixed = h->opt.precision == DMN_PREC_MIXED;
+  if (!mixed) {
+    NewtonParams<double> P{td, n, h->nslots, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status,
+                           h->nbuf, h->scr_d, (double*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 1};
+    k_newton<double><<<grid, h->opt.block, 0, s>>>(P);
+  } else {
+    NewtonParams<float> P{td, n, h->nslots, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status,
+                          h->nbuf, h->scr_d, (float*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 0};
+    k_newton<float><<<grid, h->opt.block, 0, s>>>(P);
+  }
+  if (ev) cudaEventRecord(ev[2], s);
+  FinalParams F{td, n, Q, E_n, dE, state_in, state_out, stress, tangent, status, h->nbuf};
+  if (mixed) k_final<true><<<g1, 128, 0, s>>>(F);
+  else k_final<false><<<g1, 128, 0, s>>>(F);
+  if (ev) cudaEventRecord(ev[3], s);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? DMN_OK : cuda_fail(h, e, "dmn_update: launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,446 @@
+// Device code of the DMN material-point update (sm_103a).
+//
+// One thread owns one Gauss point.  The tree is traversed depth first with an
+// explicit per-thread stack: on the way down the laminate jumps are corrected
+// (top-down redistribution of the previous Newton step) and the leaf strains
+// are formed; at the leaves the phase laws give stress and tangent; on the way
+// up every laminate is condensed (bottom-up homogenisation of the linearised
+// problem) and its share of the Newton residual is accumulated.  All threads
+// of a warp walk the same tree in lock step, so tree parameters are read at
+// warp-uniform addresses.
+//
+// Laminates are indexed in heap order inside this file (root h = 1, children
+// 2h and 2h + 1, array index h - 1); the paper's ordering (level K first, root
+// last) is used only at the ABI (state jumps, p, q).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dmn {
+
+constexpr int KMAX = 8;
+constexpr int NMAX = (1 << KMAX) - 1;
+constexpr double RS2 = 0.70710678118654752440;   // 1/sqrt(2)
+constexpr double SQ23 = 0.81649658092772603273;  // sqrt(2/3)
+
+struct PhaseDev {
+  int kind;        // 0 elastic, 1 J2 with linear hardening
+  double K, G;     // bulk and shear modulus
+  double s0, H;    // yield stress and hardening modulus
+};
+
+struct TreeDev {
+  int K, M, N, L;
+  int nz;          // inelastic leaves
+  int z_both;      // 1 if both phases are inelastic (slot = leaf), else slot = leaf / 2
+  const double* p;   // [N][M] heap order
+  const double* q;   // [N][M]
+  const double* c1;  // [N] volume fraction of the left child
+  const double* c2;  // [N] volume fraction of the right child
+  const double* W;   // [N] subtree weight (normalised, root = 1)
+  PhaseDev ph[2];
+};
+
+// packed symmetric 6x6: upper triangle row by row
+__host__ __device__ constexpr int sidx(int i, int j) {
+  return i <= j ? i * 6 - (i * (i - 1)) / 2 + (j - i) : j * 6 - (j * (j - 1)) / 2 + (i - j);
+}
+
+// Result of a subtree: plain weighted-average stress (FP64, for the residual),
+// and the affine response of the linearised subtree, s + C d_eps (precision T).
+template <typename T>
+struct Sub {
+  double sb[6];
+  T s[6];
+  T C[21];
+};
+
+// ---------------------------------------------------------------------------
+// Phase laws (Sec. 3.2 two-potential GSM leaves; J2 radial return with linear
+// isotropic hardening).  z = (alpha_bar, ep11, ep22, ep23M, ep13M, ep12M).
+template <typename T>
+__device__ __forceinline__ void leaf_law(const PhaseDev& ph, const double e[6], const double z[6], double sig[6],
+                                         T D[21], double* znew, double* gap) {
+  const double tr = e[0] + e[1] + e[2];
+  const double m = tr * (1.0 / 3.0);
+  double dev[6] = {e[0] - m, e[1] - m, e[2] - m, e[3], e[4], e[5]};
+  const double twoG = 2.0 * ph.G;
+  double th = 1.0, thb = 0.0, nh[6] = {0, 0, 0, 0, 0, 0};
+  if (ph.kind == 0) {
+#pragma unroll
+    for (int I = 0; I < 6; ++I) sig[I] = twoG * dev[I];
+    if (gap) *gap = 1e300;
+  } else {
+    const double ep[6] = {z[1], z[2], -(z[1] + z[2]), z[3], z[4], z[5]};
+    double st[6], n2 = 0.0;
+#pragma unroll
+    for (int I = 0; I < 6; ++I) { st[I] = twoG * (dev[I] - ep[I]); n2 += st[I] * st[I]; }
+    const double ns = sqrt(n2);
+    const double sy = ph.s0 + ph.H * z[0];
+    const double f = ns - SQ23 * sy;
+    if (gap) *gap = fabs(f) / sy;
+    if (f > 0.0) {
+      const double dg = f / (twoG + (2.0 / 3.0) * ph.H);
+      const double ins = 1.0 / ns;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { nh[I] = st[I] * ins; sig[I] = st[I] - twoG * dg * nh[I]; }
+      th = 1.0 - twoG * dg * ins;
+      thb = 1.0 / (1.0 + ph.H / (3.0 * ph.G)) - (1.0 - th);
+      if (znew) {
+        znew[0] = z[0] + SQ23 * dg;
+        znew[1] = z[1] + dg * nh[0]; znew[2] = z[2] + dg * nh[1];
+        znew[3] = z[3] + dg * nh[3]; znew[4] = z[4] + dg * nh[4]; znew[5] = z[5] + dg * nh[5];
+      }
+    } else {
+#pragma unroll
+      for (int I = 0; I < 6; ++I) sig[I] = st[I];
+      if (znew) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) znew[c] = z[c];
+      }
+    }
+  }
+  const double Kt = ph.K * tr;
+  sig[0] += Kt; sig[1] += Kt; sig[2] += Kt;
+  if (D) {
+    // D = K 1(x)1 + 2G th Idev - 2G thb nh(x)nh
+    const T a = (T)(twoG * th), b = (T)(ph.K - twoG * th * (1.0 / 3.0)), c = (T)(twoG * thb);
+    T n[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) n[I] = (T)nh[I];
+#pragma unroll
+    for (int I = 0; I < 6; ++I)
+#pragma unroll
+      for (int J = I; J < 6; ++J) {
+        T v = -c * n[I] * n[J];
+        if (I == J) v += a;
+        if (I < 3 && J < 3) v += b;
+        D[sidx(I, J)] = v;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// N(n) a = sym(a (x) n) in Mandel form, and N^T v = v n (as a tensor).
+template <typename T>
+__device__ __forceinline__ void N_apply(const T n[3], const T nr[3], const T a[3], T out[6]) {
+  out[0] = n[0] * a[0];
+  out[1] = n[1] * a[1];
+  out[2] = n[2] * a[2];
+  out[3] = nr[2] * a[1] + nr[1] * a[2];
+  out[4] = nr[2] * a[0] + nr[0] * a[2];
+  out[5] = nr[1] * a[0] + nr[0] * a[1];
+}
+template <typename T>
+__device__ __forceinline__ void Nt_apply(const T n[3], const T nr[3], const T v[6], T out[3]) {
+  out[0] = n[0] * v[0] + nr[2] * v[4] + nr[1] * v[5];
+  out[1] = n[1] * v[1] + nr[2] * v[3] + nr[0] * v[5];
+  out[2] = n[2] * v[2] + nr[1] * v[3] + nr[0] * v[4];
+}
+// S N for packed symmetric S: 6x3
+template <typename T>
+__device__ __forceinline__ void SN_apply(const T S[21], const T n[3], const T nr[3], T out[6][3]) {
+#pragma unroll
+  for (int I = 0; I < 6; ++I) {
+    out[I][0] = S[sidx(I, 0)] * n[0] + S[sidx(I, 4)] * nr[2] + S[sidx(I, 5)] * nr[1];
+    out[I][1] = S[sidx(I, 1)] * n[1] + S[sidx(I, 3)] * nr[2] + S[sidx(I, 5)] * nr[0];
+    out[I][2] = S[sidx(I, 2)] * n[2] + S[sidx(I, 3)] * nr[1] + S[sidx(I, 4)] * nr[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Condensation of one laminate with children L (fraction c1) and R (c2) and
+// normal n.  Jumps perturb the children as d_eps_L = d_eps - c2 N da,
+// d_eps_R = d_eps + c1 N da (Sec. 3.2, gradient operator); equilibrium
+// N^T (sigma_R - sigma_L) = 0 of the linearised children gives
+//   Kn da = -N^T (s_R - s_L) - B^T d_eps,  Kn = N^T (c2 C_L + c1 C_R) N,
+//   B = (C_R - C_L) N,
+// i.e. da = g + H d_eps with g = -Kn^-1 N^T (s_R - s_L), H = -Kn^-1 B^T, and
+// the laminate's affine response
+//   s = c1 s_L + c2 s_R + c1 c2 B g,  C = c1 C_L + c2 C_R + c1 c2 B H.
+// For constant child tangents this is the laminate homogenisation of Sec. 3.1;
+// eliminating laminates leaves-to-root is Gaussian elimination of the Newton
+// system A^T W D A da = -A^T W sigma of Sec. 3.2 (no fill in that order).
+// The FP64 residual of the laminate, (A^T W sigma)_j = W c1 c2 N^T
+// (sb_R - sb_L), is added to r2 as a squared norm.
+template <typename T, bool STORE>
+__device__ __forceinline__ void condense(const double nd[3], double c1d, double c2d, double Wd, const Sub<T>& L,
+                                         const Sub<T>& R, Sub<T>& out, T* g_out, T* H_out, size_t gstride,
+                                         double& r2) {
+  {
+    double d[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) d[I] = R.sb[I] - L.sb[I];
+    const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+    double t[3];
+    Nt_apply<double>(nd, ndr, d, t);
+    const double sc = Wd * c1d * c2d;
+    r2 += sc * sc * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+#pragma unroll
+    for (int I = 0; I < 6; ++I) out.sb[I] = c1d * L.sb[I] + c2d * R.sb[I];
+  }
+  const T c1 = (T)c1d, c2 = (T)c2d, c12 = (T)(c1d * c2d);
+  const T n[3] = {(T)nd[0], (T)nd[1], (T)nd[2]};
+  const T nr[3] = {(T)(nd[0] * RS2), (T)(nd[1] * RS2), (T)(nd[2] * RS2)};
+  T Ch[21], dC[21];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) { Ch[k] = c2 * L.C[k] + c1 * R.C[k]; dC[k] = R.C[k] - L.C[k]; }
+  T ChN[6][3], B[6][3];
+  SN_apply<T>(Ch, n, nr, ChN);
+  SN_apply<T>(dC, n, nr, B);
+  // Kn = N^T Ch N (symmetric 3x3)
+  T k[3][3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    T col[6] = {ChN[0][m], ChN[1][m], ChN[2][m], ChN[3][m], ChN[4][m], ChN[5][m]};
+    T r[3];
+    Nt_apply<T>(n, nr, col, r);
+    k[0][m] = r[0]; k[1][m] = r[1]; k[2][m] = r[2];
+  }
+  // inverse by cofactors (Kn is symmetric positive definite); symmetrised entries
+  const T k01 = (T)0.5 * (k[0][1] + k[1][0]), k02 = (T)0.5 * (k[0][2] + k[2][0]), k12 = (T)0.5 * (k[1][2] + k[2][1]);
+  const T i00 = k[1][1] * k[2][2] - k12 * k12;
+  const T i01 = k02 * k12 - k01 * k[2][2];
+  const T i02 = k01 * k12 - k02 * k[1][1];
+  const T i11 = k[0][0] * k[2][2] - k02 * k02;
+  const T i12 = k01 * k02 - k[0][0] * k12;
+  const T i22 = k[0][0] * k[1][1] - k01 * k01;
+  const T idet = (T)1 / (k[0][0] * i00 + k01 * i01 + k02 * i02);
+  const T Ki[3][3] = {{i00 * idet, i01 * idet, i02 * idet},
+                      {i01 * idet, i11 * idet, i12 * idet},
+                      {i02 * idet, i12 * idet, i22 * idet}};
+  // H = -Ki B^T (3x6),  g = -Ki N^T (s_R - s_L)
+  T H[3][6];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int I = 0; I < 6; ++I) H[m][I] = -(Ki[m][0] * B[I][0] + Ki[m][1] * B[I][1] + Ki[m][2] * B[I][2]);
+  T ds[6], u[3], g[3];
+#pragma unroll
+  for (int I = 0; I < 6; ++I) ds[I] = R.s[I] - L.s[I];
+  Nt_apply<T>(n, nr, ds, u);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
+  // s, C of the laminate
+#pragma unroll
+  for (int I = 0; I < 6; ++I) {
+    const T bg = B[I][0] * g[0] + B[I][1] * g[1] + B[I][2] * g[2];
+    out.s[I] = c1 * L.s[I] + c2 * R.s[I] + c12 * bg;
+  }
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = I; J < 6; ++J) {
+      const T bh = B[I][0] * H[0][J] + B[I][1] * H[1][J] + B[I][2] * H[2][J];
+      const int s = sidx(I, J);
+      out.C[s] = c1 * L.C[s] + c2 * R.C[s] + c12 * bh;
+    }
+  if (STORE) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) g_out[m * gstride] = g[m];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int I = 0; I < 6; ++I) H_out[(6 * m + I) * gstride] = H[m][I];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-thread views of strided arrays.
+struct PointArrays {
+  const double* nrm; size_t ns;  // normals: element (3*node + c) at nrm[(3*node+c)*ns]
+  double* a; size_t as;          // jumps: a[(3*j+c)*as], j = node (heap) or the paper's index
+  bool paper;                    // jumps stored in the paper's ordering (level K first, root last)
+  const double* z; size_t zs;    // leaf state z^n of the inelastic slots: z[(6*slot+c)*zs]
+};
+
+// array index of the jumps of heap node `node` at level lvl
+__device__ __forceinline__ int jump_index(const PointArrays& P, int K, int lvl, int node) {
+  return P.paper ? (1 << K) - 3 * (1 << (lvl - 1)) + node + 1 : node;
+}
+
+template <typename T>
+struct GH {
+  T* p; size_t s;  // g and H of laminate node: p[(21*node + c)*s], c = 0..2 g, 3..20 H
+};
+
+__device__ __forceinline__ void load_z(const TreeDev& t, const PointArrays& P, int leaf, int phase, double z[6]) {
+  if (t.ph[phase].kind == 1) {
+    const int slot = t.z_both ? leaf : (leaf >> 1);
+    const double* b = P.z + (size_t)(6 * slot) * P.zs;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) z[c] = b[c * P.zs];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) z[c] = 0.0;
+  }
+}
+
+// One pass over the tree for one point.
+//   STORE:  Newton pass.  When `apply` is set, first apply the previous Newton
+//           step on the way down, da = g + H d_eps with the g, H stored by the
+//           previous pass, a += da (top-down redistribution); then store this
+//           pass's g, H for the next step.
+//   !STORE: evaluation at the given jumps only (final sweep).
+// Returns the root's subtree result (sb = effective stress, C = tangent of the
+// linearised DMN) and the squared norm of A^T W sigma at the (updated) jumps.
+template <typename T, bool STORE>
+__device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArrays& P, GH<T> gh, bool apply,
+                          Sub<T>& root, double& r2, double* gap_min) {
+  const int K = t.K;
+  double epsR[KMAX + 1][6];
+  T depsR[KMAX + 1][6];
+  Sub<T> pend[KMAX + 1];
+  r2 = 0.0;
+  const int nbottom = 1 << (K - 1);
+  for (int m = 0; m < nbottom; ++m) {
+    const int top = (m == 0) ? 1 : K - __ffs(m) + 1;
+    double e[6];
+    T de[6];
+    if (m == 0) {
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { e[I] = Eloc[I]; de[I] = (T)0; }
+    } else {
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { e[I] = epsR[top][I]; de[I] = depsR[top][I]; }
+    }
+    double eL[6], eR[6];
+    for (int lvl = top; lvl <= K; ++lvl) {
+      const int node = (1 << (lvl - 1)) + (m >> (K - lvl)) - 1;
+      const double nd[3] = {P.nrm[(3 * node) * P.ns], P.nrm[(3 * node + 1) * P.ns], P.nrm[(3 * node + 2) * P.ns]};
+      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      double* ap = P.a + (size_t)(3 * jump_index(P, K, lvl, node)) * P.as;
+      double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
+      T da[3] = {(T)0, (T)0, (T)0};
+      if (STORE) {   // only the Newton kernel corrects jumps; `apply` is false on a point's first pass
+        const T* gp = gh.p + (size_t)(21 * node) * gh.s;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T v = gp[c * gh.s];
+#pragma unroll
+          for (int I = 0; I < 6; ++I) v += gp[(3 + 6 * c + I) * gh.s] * de[I];
+          da[c] = apply ? v : (T)0;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { a[c] += (double)da[c]; ap[c * P.as] = a[c]; }
+      }
+      const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+      double Na[6];
+      N_apply<double>(nd, ndr, a, Na);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { eL[I] = e[I] - c2 * Na[I]; eR[I] = e[I] + c1 * Na[I]; }
+      if (lvl < K) {
+        T dR[6];
+        if (STORE) {
+          const T nt[3] = {(T)nd[0], (T)nd[1], (T)nd[2]}, ntr[3] = {(T)ndr[0], (T)ndr[1], (T)ndr[2]};
+          T Nda[6];
+          N_apply<T>(nt, ntr, da, Nda);
+#pragma unroll
+          for (int I = 0; I < 6; ++I) { dR[I] = de[I] + (T)c1 * Nda[I]; de[I] = de[I] - (T)c2 * Nda[I]; }
+        } else {
+#pragma unroll
+          for (int I = 0; I < 6; ++I) dR[I] = (T)0;
+        }
+#pragma unroll
+        for (int I = 0; I < 6; ++I) { epsR[lvl + 1][I] = eR[I]; depsR[lvl + 1][I] = dR[I]; e[I] = eL[I]; }
+      }
+    }
+    // leaves 2m (phase 1) and 2m + 1 (phase 2)
+    Sub<T> A, B;
+    {
+      double z[6], g;
+      load_z(t, P, 2 * m, 0, z);
+      leaf_law<T>(t.ph[0], eL, z, A.sb, A.C, nullptr, gap_min ? &g : nullptr);
+      if (gap_min) *gap_min = fmin(*gap_min, g);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) A.s[I] = (T)A.sb[I];
+      load_z(t, P, 2 * m + 1, 1, z);
+      leaf_law<T>(t.ph[1], eR, z, B.sb, B.C, nullptr, gap_min ? &g : nullptr);
+      if (gap_min) *gap_min = fmin(*gap_min, g);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) B.s[I] = (T)B.sb[I];
+    }
+    // condense upwards while the finished laminate is a right child
+    int lvl = K, idx = m;
+    for (;;) {
+      const int node = (1 << (lvl - 1)) + idx - 1;
+      const double nd[3] = {P.nrm[(3 * node) * P.ns], P.nrm[(3 * node + 1) * P.ns], P.nrm[(3 * node + 2) * P.ns]};
+      Sub<T> res;
+      T* gp = STORE ? gh.p + (size_t)(21 * node) * gh.s : nullptr;
+      condense<T, STORE>(nd, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.W + node), A, B, res, gp,
+                         STORE ? gp + 3 * gh.s : nullptr, gh.s, r2);
+      if (lvl == 1) { root = res; break; }
+      if (idx & 1) {
+        A = pend[lvl];
+        B = res;
+        idx >>= 1;
+        --lvl;
+      } else {
+        pend[lvl] = res;
+        break;
+      }
+    }
+  }
+}
+
+// Leaf strains from the jumps (top-down) and the return mapping at the final
+// iterate: writes z^{n+1} of the inelastic leaves.
+__device__ inline void write_leaf_states(const TreeDev& t, const double Eloc[6], const PointArrays& P, double* zout,
+                                         size_t zos, bool nan_out) {
+  const int K = t.K;
+  double epsR[KMAX + 1][6];
+  const int nbottom = 1 << (K - 1);
+  for (int m = 0; m < nbottom; ++m) {
+    const int top = (m == 0) ? 1 : K - __ffs(m) + 1;
+    double e[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) e[I] = (m == 0) ? Eloc[I] : epsR[top][I];
+    double eL[6], eR[6];
+    for (int lvl = top; lvl <= K; ++lvl) {
+      const int node = (1 << (lvl - 1)) + (m >> (K - lvl)) - 1;
+      const double nd[3] = {P.nrm[(3 * node) * P.ns], P.nrm[(3 * node + 1) * P.ns], P.nrm[(3 * node + 2) * P.ns]};
+      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      const double* ap = P.a + (size_t)(3 * jump_index(P, K, lvl, node)) * P.as;
+      const double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
+      const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+      double Na[6];
+      N_apply<double>(nd, ndr, a, Na);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { eL[I] = e[I] - c2 * Na[I]; eR[I] = e[I] + c1 * Na[I]; }
+      if (lvl < K) {
+#pragma unroll
+        for (int I = 0; I < 6; ++I) { epsR[lvl + 1][I] = eR[I]; e[I] = eL[I]; }
+      }
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (t.ph[side].kind != 1) continue;
+      const int leaf = 2 * m + side;
+      double z[6], zn[6], sig[6];
+      load_z(t, P, leaf, side, z);
+      leaf_law<double>(t.ph[side], side ? eR : eL, z, sig, nullptr, zn, nullptr);
+      const int slot = t.z_both ? leaf : (leaf >> 1);
+      double* b = zout + (size_t)(6 * slot) * zos;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) b[c * zos] = nan_out ? __longlong_as_double(0x7ff8000000000000LL) : zn[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mandel rotation R_IJ = (w_I w_J / 2)(Q_ia Q_jb + Q_ib Q_ja) for index pairs
+// I = (i, j), J = (a, b), w = 1 (normal) or sqrt 2 (shear): sigma_glob =
+// R sigma_loc, E_loc = R^T E_glob, C_glob = R C_loc R^T.
+__device__ __forceinline__ void mandel_rotation(const double Q[9], double R[6][6]) {
+  const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = 0; J < 6; ++J) {
+      const int i = pi[I], j = pj[I], a = pi[J], b = pj[J];
+      const double wIJ = ((I < 3) ? 1.0 : 1.41421356237309504880) * ((J < 3) ? 1.0 : 1.41421356237309504880) * 0.5;
+      R[I][J] = wIJ * (Q[3 * i + a] * Q[3 * j + b] + Q[3 * i + b] * Q[3 * j + a]);
+    }
+}
+
+}  // namespace dmn

@@ -1,0 +1,204 @@
+"""Python binding of the DMN C ABI (include/dmn.h).
+
+Argument marshalling only: every step of the update runs in the CUDA library
+``_build/libdmn.so``.  PyTorch provides device memory and the current stream.
+There is no CPU fallback: if the library or a CUDA device is missing, the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+_lib = None
+
+# ABI symbols declared in include/dmn.h
+EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_interp_orientation", "dmn_update",
+           "dmn_profile_enable", "dmn_profile_read", "dmn_last_error")
+
+PREC_F64 = 0
+PREC_MIXED = 1
+STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE = 0, 1, 2
+
+
+class Phase_(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("E", ctypes.c_double), ("nu", ctypes.c_double),
+                ("sigma0", ctypes.c_double), ("H", ctypes.c_double)]
+
+
+class TreeDesc_(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("M", ctypes.c_int32), ("p", ctypes.POINTER(ctypes.c_double)),
+                ("q", ctypes.POINTER(ctypes.c_double)), ("w", ctypes.POINTER(ctypes.c_double)),
+                ("phase", Phase_ * 2)]
+
+
+class Options_(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("DMN CUDA library not built: run __graft_entry__.build() or "
+                           "python -m paper_2103_08253_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    lib.dmn_create.argtypes = [ctypes.POINTER(TreeDesc_), i32, ctypes.POINTER(Options_), ctypes.POINTER(vp)]
+    lib.dmn_create.restype = ctypes.c_int
+    lib.dmn_destroy.argtypes = [vp]
+    lib.dmn_destroy.restype = None
+    lib.dmn_state_size.argtypes = [vp, i32]
+    lib.dmn_state_size.restype = i64
+    lib.dmn_interp_orientation.argtypes = [vp, i64, vp, vp, vp, vp]
+    lib.dmn_interp_orientation.restype = ctypes.c_int
+    lib.dmn_update.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.dmn_update.restype = ctypes.c_int
+    lib.dmn_profile_enable.argtypes = [vp, i32]
+    lib.dmn_profile_enable.restype = ctypes.c_int
+    lib.dmn_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+    lib.dmn_profile_read.restype = ctypes.c_int
+    lib.dmn_last_error.argtypes = [vp]
+    lib.dmn_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check_dev(name, t, dtype, shape):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+
+
+class DMN:
+    """A DMN on the current CUDA device.
+
+    tree: object with K, M, p [N, M], q [N, M], w [2^K] (numpy, paper
+    ordering) and phases (two objects with kind, E, nu, sigma0, H)."""
+
+    def __init__(self, tree, precision: str = "f64", tol: float = 1e-12, max_iter: int = 50, block: int = 0,
+                 ctas_per_sm: int = 0):
+        import numpy as np
+        self._lib = load_library()
+        self.K, self.M = int(tree.K), int(tree.M)
+        self._p = np.ascontiguousarray(tree.p, dtype=np.float64).reshape(-1)
+        self._q = np.ascontiguousarray(tree.q, dtype=np.float64).reshape(-1)
+        self._w = np.ascontiguousarray(tree.w, dtype=np.float64).reshape(-1)
+        dp = ctypes.POINTER(ctypes.c_double)
+        desc = TreeDesc_()
+        desc.K, desc.M = self.K, self.M
+        desc.p = self._p.ctypes.data_as(dp)
+        desc.q = self._q.ctypes.data_as(dp)
+        desc.w = self._w.ctypes.data_as(dp)
+        for f, ph in enumerate(tree.phases):
+            desc.phase[f] = Phase_(int(ph.kind), float(ph.E), float(ph.nu), float(ph.sigma0), float(ph.H))
+        opt = Options_(float(tol), int(max_iter), PREC_MIXED if precision == "mixed" else PREC_F64, int(block),
+                       int(ctas_per_sm))
+        if precision not in ("f64", "mixed"):
+            raise ValueError("precision must be 'f64' or 'mixed'")
+        self.precision = precision
+        h = ctypes.c_void_p()
+        rc = self._lib.dmn_create(ctypes.byref(desc), 1, ctypes.byref(opt), ctypes.byref(h))
+        if rc != 0:
+            raise ValueError("dmn_create failed (%d): %s" % (rc, self._lib.dmn_last_error(None).decode()))
+        self._h = h
+        self.state_size = int(self._lib.dmn_state_size(h, 0))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dmn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _err(self, what, rc):
+        msg = self._lib.dmn_last_error(self._h).decode()
+        raise RuntimeError("%s failed (%d): %s" % (what, rc, msg))
+
+    def interp_orientation(self, A2, lam=None, Q=None):
+        """A2 [n, 6] float64 CUDA -> (lam [n, 2], Q [n, 9])."""
+        import torch
+        n = A2.shape[0]
+        _check_dev("A2", A2, torch.float64, (n, 6))
+        lam = torch.empty((n, 2), dtype=torch.float64, device=A2.device) if lam is None else lam
+        Q = torch.empty((n, 9), dtype=torch.float64, device=A2.device) if Q is None else Q
+        _check_dev("lam", lam, torch.float64, (n, 2))
+        _check_dev("Q", Q, torch.float64, (n, 9))
+        s = torch.cuda.current_stream(A2.device).cuda_stream
+        rc = self._lib.dmn_interp_orientation(self._h, n, _ptr(A2), _ptr(lam), _ptr(Q), ctypes.c_void_p(s))
+        if rc != 0:
+            self._err("dmn_interp_orientation", rc)
+        return lam, Q
+
+    def profile(self, enable: bool):
+        """Start (clearing the totals) or stop per-kernel event timing of update()."""
+        rc = self._lib.dmn_profile_enable(self._h, 1 if enable else 0)
+        if rc != 0:
+            self._err("dmn_profile_enable", rc)
+
+    def profile_read(self):
+        """(ms of the normals, Newton and final kernels summed over the timed updates, number of updates)."""
+        ms = (ctypes.c_double * 3)()
+        cnt = ctypes.c_int64()
+        rc = self._lib.dmn_profile_read(self._h, ms, ctypes.byref(cnt))
+        if rc != 0:
+            self._err("dmn_profile_read", rc)
+        return dict(normals=ms[0], newton=ms[1], final=ms[2]), int(cnt.value)
+
+    def alloc_outputs(self, n, device):
+        import torch
+        return dict(state_out=torch.empty((self.state_size, n), dtype=torch.float64, device=device),
+                    stress=torch.empty((n, 6), dtype=torch.float64, device=device),
+                    tangent=torch.empty((n, 6, 6), dtype=torch.float64, device=device),
+                    iters=torch.empty(n, dtype=torch.int32, device=device),
+                    status=torch.empty(n, dtype=torch.int32, device=device))
+
+    def update(self, lam, Q, E_n, dE, state_in, out=None):
+        """One material-point update; returns dict(state_out, stress, tangent, iters, status)."""
+        import torch
+        n = lam.shape[0]
+        dev = lam.device
+        _check_dev("lam", lam, torch.float64, (n, 2))
+        _check_dev("Q", Q, torch.float64, (n, 9))
+        _check_dev("E_n", E_n, torch.float64, (n, 6))
+        _check_dev("dE", dE, torch.float64, (n, 6))
+        _check_dev("state_in", state_in, torch.float64, (self.state_size, n))
+        out = self.alloc_outputs(n, dev) if out is None else out
+        _check_dev("state_out", out["state_out"], torch.float64, (self.state_size, n))
+        _check_dev("stress", out["stress"], torch.float64, (n, 6))
+        _check_dev("tangent", out["tangent"], torch.float64, (n, 6, 6))
+        _check_dev("iters", out["iters"], torch.int32, (n,))
+        _check_dev("status", out["status"], torch.int32, (n,))
+        s = torch.cuda.current_stream(dev).cuda_stream
+        rc = self._lib.dmn_update(self._h, n, None, _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE), _ptr(state_in),
+                                  _ptr(out["state_out"]), _ptr(out["stress"]), _ptr(out["tangent"]),
+                                  _ptr(out["iters"]), _ptr(out["status"]), ctypes.c_void_p(s))
+        if rc != 0:
+            self._err("dmn_update", rc)
+        return out

@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/dmn.h; argument errors are reported before any CUDA work (no GPU
+needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2103_08253_gb300 import dmn, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "dmn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dmn_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = dmn.load_library()
+    syms = declared_symbols()
+    assert "dmn_update" in syms and "dmn_create" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(dmn.EXPORTS) == set(syms)
+
+
+def _desc(K=3, M=3, w=None, kind=1):
+    tree = W.tree_d10_fit(K, seed=1)
+    p = np.ascontiguousarray(tree.p.reshape(-1)); q = np.ascontiguousarray(tree.q.reshape(-1))
+    w = np.ascontiguousarray(tree.w if w is None else w, dtype=np.float64)
+    d = dmn.TreeDesc_()
+    dp = ctypes.POINTER(ctypes.c_double)
+    d.K, d.M = K, M
+    d.p, d.q, d.w = p.ctypes.data_as(dp), q.ctypes.data_as(dp), w.ctypes.data_as(dp)
+    d.phase[0] = dmn.Phase_(0, 72000.0, 0.22, 0.0, 0.0)
+    d.phase[1] = dmn.Phase_(kind, 3000.0, 0.35, 40.0, 300.0)
+    return d, (p, q, w)
+
+
+@pytest.mark.parametrize("case,msg", [
+    (dict(K=9), "K must be"), (dict(K=0), "K must be"), (dict(M=5), "M must be"),
+    (dict(w=np.r_[np.ones(7), 0.0]), "weights"), (dict(w=np.r_[np.ones(7), np.nan]), "weights"),
+    (dict(kind=7), "phase kind")])
+def test_create_rejects_bad_arguments_without_touching_the_gpu(case, msg):
+    lib = dmn.load_library()
+    d, keep = _desc(**case)
+    h = ctypes.c_void_p(123)
+    rc = lib.dmn_create(ctypes.byref(d), 1, None, ctypes.byref(h))
+    assert rc == -1
+    assert h.value is None
+    assert msg in lib.dmn_last_error(None).decode()
+
+
+def test_calls_on_null_handle_are_argument_errors():
+    lib = dmn.load_library()
+    assert lib.dmn_update(None, 4, None, *([None] * 10), None) == -1
+    assert lib.dmn_interp_orientation(None, 4, None, None, None, None) == -1
+    assert lib.dmn_state_size(None, 0) == -1
+    lib.dmn_destroy(None)
+
+
+def test_state_size_formula():
+    # 6 per inelastic leaf + 3 per laminate; the paper's count for K = 8 is 1533
+    assert W.state_size(8) == 1533
+    assert W.state_size(4) == 6 * 8 + 3 * 15
+    assert W.state_size(3, (W.MATRIX, W.MATRIX)) == 6 * 8 + 3 * 7
