@@ -451,7 +451,7 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   for (int k = 1; k <= K; ++k)
     for (int i = 1; i <= (1 << (k - 1)); ++i) {
       const int j = (1 << K) - (1 << k) + (i - 1);   // paper ordering
-      const int hn = (1 << (k - 1)) + i - 1;        // heap node index
+      const int hn = (1 << (k - 1)) + i - 2;        // array index (heap number - 1)
       for (int m = 0; m < M; ++m) { ph[hn * M + m] = d.p[j * M + m]; qh[hn * M + m] = d.q[j * M + m]; }
     }
   double* d_w = nullptr;

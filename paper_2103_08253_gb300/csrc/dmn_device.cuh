@@ -13,8 +13,11 @@
 // 2h and 2h + 1, array index h - 1); the paper's ordering (level K first, root
 // last) is used only at the ABI (state jumps, p, q).
 #pragma once
+#include <cmath>
 #include <cstdint>
+#ifndef DMN_HOST_EMULATION
 #include <cuda_runtime.h>
+#endif
 
 namespace dmn {
 
@@ -46,12 +49,16 @@ __host__ __device__ constexpr int sidx(int i, int j) {
   return i <= j ? i * 6 - (i * (i - 1)) / 2 + (j - i) : j * 6 - (j * (j - 1)) / 2 + (i - j);
 }
 
-// Result of a subtree: plain weighted-average stress (FP64, for the residual),
-// and the affine response of the linearised subtree, s + C d_eps (precision T).
+// Result of a subtree.  Its linearised response to a strain perturbation d_eps,
+// with its inner jumps re-equilibrated, is sb + ds + C d_eps: sb is the plain
+// weighted-average stress at the current iterate (FP64; it also feeds the
+// residual), ds the change that the inner Newton corrections add (precision
+// T), C the condensed tangent (T).  Keeping sb apart in FP64 lets the FP32
+// form see the residual, a small difference of large stresses, exactly.
 template <typename T>
 struct Sub {
   double sb[6];
-  T s[6];
+  T ds[6];
   T C[21];
 };
 
@@ -157,7 +164,9 @@ __device__ __forceinline__ void SN_apply(const T S[21], const T n[3], const T nr
 //   B = (C_R - C_L) N,
 // i.e. da = g + H d_eps with g = -Kn^-1 N^T (s_R - s_L), H = -Kn^-1 B^T, and
 // the laminate's affine response
-//   s = c1 s_L + c2 s_R + c1 c2 B g,  C = c1 C_L + c2 C_R + c1 c2 B H.
+//   s = c1 s_L + c2 s_R + c1 c2 B g,  C = c1 C_L + c2 C_R + c1 c2 B H,
+// with s = sb + ds split as in Sub: N^T (s_R - s_L) = t + N^T (ds_R - ds_L),
+// t = N^T (sb_R - sb_L) taken from the FP64 residual.
 // For constant child tangents this is the laminate homogenisation of Sec. 3.1;
 // eliminating laminates leaves-to-root is Gaussian elimination of the Newton
 // system A^T W D A da = -A^T W sigma of Sec. 3.2 (no fill in that order).
@@ -167,6 +176,7 @@ template <typename T, bool STORE>
 __device__ __forceinline__ void condense(const double nd[3], double c1d, double c2d, double Wd, const Sub<T>& L,
                                          const Sub<T>& R, Sub<T>& out, T* g_out, T* H_out, size_t gstride,
                                          double& r2) {
+  T u[3];
   {
     double d[6];
 #pragma unroll
@@ -178,6 +188,7 @@ __device__ __forceinline__ void condense(const double nd[3], double c1d, double 
     r2 += sc * sc * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
 #pragma unroll
     for (int I = 0; I < 6; ++I) out.sb[I] = c1d * L.sb[I] + c2d * R.sb[I];
+    u[0] = (T)t[0]; u[1] = (T)t[1]; u[2] = (T)t[2];
   }
   const T c1 = (T)c1d, c2 = (T)c2d, c12 = (T)(c1d * c2d);
   const T n[3] = {(T)nd[0], (T)nd[1], (T)nd[2]};
@@ -215,17 +226,19 @@ __device__ __forceinline__ void condense(const double nd[3], double c1d, double 
   for (int m = 0; m < 3; ++m)
 #pragma unroll
     for (int I = 0; I < 6; ++I) H[m][I] = -(Ki[m][0] * B[I][0] + Ki[m][1] * B[I][1] + Ki[m][2] * B[I][2]);
-  T ds[6], u[3], g[3];
+  T dds[6], v[3], g[3];
 #pragma unroll
-  for (int I = 0; I < 6; ++I) ds[I] = R.s[I] - L.s[I];
-  Nt_apply<T>(n, nr, ds, u);
+  for (int I = 0; I < 6; ++I) dds[I] = R.ds[I] - L.ds[I];
+  Nt_apply<T>(n, nr, dds, v);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) u[m] += v[m];
 #pragma unroll
   for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
-  // s, C of the laminate
+  // ds, C of the laminate
 #pragma unroll
   for (int I = 0; I < 6; ++I) {
     const T bg = B[I][0] * g[0] + B[I][1] * g[1] + B[I][2] * g[2];
-    out.s[I] = c1 * L.s[I] + c2 * R.s[I] + c12 * bg;
+    out.ds[I] = c1 * L.ds[I] + c2 * R.ds[I] + c12 * bg;
   }
 #pragma unroll
   for (int I = 0; I < 6; ++I)
@@ -353,12 +366,12 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
       leaf_law<T>(t.ph[0], eL, z, A.sb, A.C, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
 #pragma unroll
-      for (int I = 0; I < 6; ++I) A.s[I] = (T)A.sb[I];
+      for (int I = 0; I < 6; ++I) A.ds[I] = (T)0;
       load_z(t, P, 2 * m + 1, 1, z);
       leaf_law<T>(t.ph[1], eR, z, B.sb, B.C, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
 #pragma unroll
-      for (int I = 0; I < 6; ++I) B.s[I] = (T)B.sb[I];
+      for (int I = 0; I < 6; ++I) B.ds[I] = (T)0;
     }
     // condense upwards while the finished laminate is a right child
     int lvl = K, idx = m;

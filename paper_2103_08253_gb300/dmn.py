@@ -132,6 +132,11 @@ class DMN:
             self._h = None
 
     def __del__(self):
+        # at interpreter exit the CUDA runtime may already be torn down; the
+        # process releases the device memory anyway
+        import sys
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
