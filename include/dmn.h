@@ -152,6 +152,36 @@ int dmn_profile_enable(dmn_handle* h, int32_t enable);
  * an event query fails. */
 int dmn_profile_read(dmn_handle* h, double ms[3], int64_t* updates);
 
+/* The same FP64 update as dmn_update, for callers that cannot allocate device
+ * memory -- for example code whose device memory is all handed out by an
+ * application's own pool or arena, or that runs under a policy forbidding
+ * cudaMalloc once it has started.  The paper has no counterpart: this is an
+ * interface choice of this library.
+ *
+ * It needs no handle and allocates nothing (no cudaMalloc, cudaFree or other
+ * allocating call).  Its work space -- tree parameters, a work counter and the
+ * per-lane scratch of the Newton kernel -- is one static device array of
+ * 64 MiB inside this library, which every GPU that loads the library holds
+ * until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) once; make that first call before
+ * any stream capture.  Every call shares the array: calls that overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  Each call re-uploads the tree and clears the counter.
+ *
+ * Arguments are those of dmn_create (tree, opt) and dmn_update (n and the
+ * arrays, same layouts and ownership).  Only the FP64 form is offered
+ * (opt->precision must be DMN_PREC_F64; opt may be NULL); opt->block and
+ * opt->ctas_per_sm are ignored.  The static work space limits parallelism:
+ * 1152 lanes at K = 8 (more for shallower trees), so it is slower than
+ * dmn_update.  Errors: DMN_ERR_ARG for the argument errors of dmn_create and
+ * dmn_update and for a tree whose parameters or one CTA of scratch do not fit
+ * the 64 MiB; DMN_ERR_CUDA if a CUDA call fails.  Messages are returned by
+ * dmn_last_error(NULL). */
+int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* opt, int64_t n, const double* lam,
+                       const double* Q, const double* E_n, const double* dE, const double* state_in,
+                       double* state_out, double* stress, double* tangent, int32_t* iters, int32_t* status,
+                       void* stream);
+
 /* Message of the last failed call on this handle (or of the last failed
  * dmn_create when h is NULL); "" if none.  Valid until the next call. */
 const char* dmn_last_error(const dmn_handle* h);

@@ -19,6 +19,7 @@
 #include <string>
 #include <vector>
 #include <array>
+#include <mutex>
 
 #include "../../include/dmn.h"
 #include "dmn_device.cuh"
@@ -598,3 +599,256 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Update without any allocation (dmn_update_noalloc).
+//
+// Some callers cannot allocate device memory: code that runs where every byte of
+// the device is handed out by someone else's pool or arena, or under policies that
+// forbid cudaMalloc after start-up.  For them the update below keeps its whole work
+// space -- tree parameters, the work counter and the per-lane scratch of the
+// persistent Newton kernel -- in one file-scope device array of fixed size,
+// DMN_NOALLOC_BYTES.  Every GPU that loads this library holds that array until the
+// process exits.  The caller passes inputs and outputs as for dmn_update.
+
+namespace {
+
+constexpr size_t DMN_NOALLOC_BYTES = size_t(64) << 20;  // 64 MiB
+constexpr size_t NOALLOC_PARAM_DOUBLES = 4096;          // p, q, w, c1, c2, W for K <= 8, M <= 6
+constexpr int NOALLOC_BLOCK = 128;
+
+// [0, 256): work counter; [256, 256 + 8 * NOALLOC_PARAM_DOUBLES): tree parameters;
+// the rest: per-lane scratch (normals, jumps, g and H of every laminate).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DMN_NOALLOC_BYTES];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[256] = {nullptr};  // device address of g_noalloc_scratch, per device
+
+struct NoAllocParams {
+  TreeDev t;
+  int64_t n, nslots;
+  const double *lam, *Q, *En, *dE, *state_in;
+  double *state_out, *stress, *tangent;
+  int32_t *iters, *status;
+  double* slots;  // per-lane scratch, field-major over lanes
+  unsigned long long* counter;
+  double tol;
+  int max_iter;
+};
+
+// normals of every laminate of one point, written to strided scratch
+__device__ void point_normals(const TreeDev& t, double l1, double l2, double* out, size_t stride) {
+  const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
+  double ph[6];
+  if (t.M == 3) {
+    ph[0] = v[0]; ph[1] = v[1]; ph[2] = v[2];
+  } else if (t.M == 4) {
+    const double b = v[0] * v[1] * v[2];
+    ph[0] = v[0] - 9.0 * b; ph[1] = v[1] - 9.0 * b; ph[2] = v[2] - 9.0 * b; ph[3] = 27.0 * b;
+  } else {
+    ph[0] = v[0] * (2.0 * v[0] - 1.0); ph[1] = v[1] * (2.0 * v[1] - 1.0); ph[2] = v[2] * (2.0 * v[2] - 1.0);
+    ph[3] = 4.0 * v[0] * v[1]; ph[4] = 4.0 * v[0] * v[2]; ph[5] = 4.0 * v[1] * v[2];
+  }
+  for (int j = 0; j < t.N; ++j) {
+    double al = 0.0, be = 0.0;
+    for (int m = 0; m < t.M; ++m) {
+      al += t.p[j * t.M + m] * ph[m];
+      be += t.q[j * t.M + m] * ph[m];
+    }
+    double sa, ca, sb, cb;
+    sincos(al, &sa, &ca);
+    sincos(be, &sb, &cb);
+    out[(size_t)(3 * j + 0) * stride] = sa * cb;
+    out[(size_t)(3 * j + 1) * stride] = sa * sb;
+    out[(size_t)(3 * j + 2) * stride] = ca;
+  }
+}
+
+// FP64 Newton kernel of dmn_update, with the orientation normals and the new leaf
+// states computed by the lane that owns the point (no per-point buffers).
+__global__ void __launch_bounds__(NOALLOC_BLOCK) k_newton_noalloc(NoAllocParams P) {
+  const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const TreeDev& t = P.t;
+  const int N = t.N;
+  double* my_nrm = P.slots + slot;
+  PointArrays A;
+  A.nrm = my_nrm; A.ns = (size_t)P.nslots;
+  A.a = P.slots + (size_t)(3 * N) * P.nslots + slot; A.as = (size_t)P.nslots;
+  A.paper = false;
+  A.z = nullptr; A.zs = (size_t)P.n;
+  GH<double> gh{P.slots + (size_t)(6 * N) * P.nslots + slot, (size_t)P.nslots};
+  const int nzf = 6 * t.nz;
+  int64_t pt = -1;
+  int it = 0;
+  double Eloc[6];
+  for (;;) {
+    const bool need = pt < 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, need);
+    if (mask) {
+      const int leader = __ffs(mask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(P.counter, (unsigned long long)__popc(mask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        pt = (int64_t)(base + __popc(mask & ((1u << lane) - 1u)));
+        if (pt < P.n) {
+          local_strain(P.Q + 9 * pt, P.En + 6 * pt, P.dE + 6 * pt, Eloc);
+          point_normals(t, P.lam[2 * pt], P.lam[2 * pt + 1], my_nrm, A.ns);
+          for (int f = 0; f < 3 * N; ++f) {
+            const int node = f / 3, c = f - 3 * node;
+            const int lvl = 32 - __clz(node + 1);
+            const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+            A.a[(size_t)f * A.as] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
+          }
+          A.z = P.state_in + pt;
+          it = 0;
+        }
+      }
+    }
+    const bool active = pt >= 0 && pt < P.n;
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (!active) continue;
+    Sub<double> root;
+    double r2;
+    tree_pass<double, true>(t, Eloc, A, gh, it > 0, root, r2, nullptr);
+    const double rn = sqrt(r2);
+    double sn2 = 0.0;
+#pragma unroll
+    for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
+    const double sn = sqrt(sn2);
+    int st = -1;
+    if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
+    else if (rn <= P.tol * (double)N * sn) st = DMN_STATUS_OK;
+    else if (it >= P.max_iter) st = DMN_STATUS_MAXITER;
+    if (st < 0) { ++it; continue; }
+    const bool bad = st == DMN_STATUS_NONFINITE;
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int f = 0; f < 3 * N; ++f) {
+      const int node = f / 3, c = f - 3 * node;
+      const int lvl = 32 - __clz(node + 1);
+      const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+      P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt] = bad ? qnan : A.a[(size_t)f * A.as];
+    }
+    P.iters[pt] = it;
+    P.status[pt] = st;
+    if (bad) {
+      for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
+      for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
+    } else {
+      write_stress_tangent<double>(P.Q + 9 * pt, root.sb, root.C, P.stress + 6 * pt, P.tangent + 36 * pt);
+    }
+    write_leaf_states(t, Eloc, A, P.state_out + pt, (size_t)P.n, bad);
+    pt = -1;
+  }
+}
+
+}  // namespace
+
+extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* opt, int64_t n, const double* lam,
+                                  const double* Q, const double* E_n, const double* dE, const double* state_in,
+                                  double* state_out, double* stress, double* tangent, int32_t* iters,
+                                  int32_t* status, void* stream) {
+  if (!tree) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: tree is NULL");
+  const dmn_tree_desc& d = *tree;
+  if (d.K < 1 || d.K > KMAX) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: K must be in 1..8");
+  if (d.M != 3 && d.M != 4 && d.M != 6) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: M must be 3, 4 or 6");
+  if (!d.p || !d.q || !d.w) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: p, q, w must be non-NULL");
+  if (n < 0) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: n < 0");
+  const int K = d.K, M = d.M, N = (1 << K) - 1, L = 1 << K;
+  for (int l = 0; l < L; ++l)
+    if (!(d.w[l] > 0.0) || !std::isfinite(d.w[l]))
+      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: leaf weights must be finite and > 0");
+  for (int j = 0; j < N * M; ++j)
+    if (!std::isfinite(d.p[j]) || !std::isfinite(d.q[j]))
+      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: p, q must be finite");
+  double tol = 1e-12;
+  int max_iter = 50;
+  if (opt) {
+    if (opt->precision != DMN_PREC_F64)
+      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: only the FP64 form is available without allocation");
+    if (opt->tol > 0.0) tol = opt->tol;
+    if (opt->max_iter > 0) max_iter = opt->max_iter;
+  }
+  TreeDev td;
+  td.K = K; td.M = M; td.N = N; td.L = L;
+  int n_inel = 0;
+  for (int f = 0; f < 2; ++f) {
+    const dmn_phase& p = d.phase[f];
+    if (p.kind != DMN_PHASE_ELASTIC && p.kind != DMN_PHASE_J2_LINEAR)
+      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: unknown phase kind");
+    if (!(p.E > 0.0) || !(p.nu > -1.0) || !(p.nu < 0.5))
+      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: need E > 0 and -1 < nu < 0.5");
+    if (p.kind == DMN_PHASE_J2_LINEAR && (!(p.sigma0 > 0.0) || !(p.H >= 0.0)))
+      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: J2 phase needs sigma0 > 0 and H >= 0");
+    td.ph[f].kind = p.kind;
+    td.ph[f].K = p.E / (3.0 * (1.0 - 2.0 * p.nu));
+    td.ph[f].G = p.E / (2.0 * (1.0 + p.nu));
+    td.ph[f].s0 = p.sigma0;
+    td.ph[f].H = p.H;
+    n_inel += p.kind == DMN_PHASE_J2_LINEAR;
+  }
+  td.z_both = n_inel == 2;
+  td.nz = n_inel * (L / 2);
+  // sizes against the fixed work space: parameters, then whole CTAs of lane scratch
+  const size_t param_doubles = (size_t)2 * N * M + (size_t)L + 3 * (size_t)N;
+  const size_t lane_bytes = sizeof(double) * (size_t)27 * N;
+  const size_t avail = DMN_NOALLOC_BYTES - 256 - sizeof(double) * NOALLOC_PARAM_DOUBLES;
+  const int64_t nslots = (int64_t)(avail / lane_bytes) / NOALLOC_BLOCK * NOALLOC_BLOCK;
+  if (param_doubles > NOALLOC_PARAM_DOUBLES || nslots < NOALLOC_BLOCK)
+    return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: tree too large for the 64 MiB static work space");
+  if (n == 0) return DMN_OK;
+  if (!lam || !Q || !E_n || !dE || !state_in || !state_out || !stress || !tangent || !iters || !status)
+    return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: NULL array");
+  if (state_in == state_out) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: state_in and state_out must differ");
+
+  // device address of the static work space, looked up once per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= 256) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: device ordinal out of range");
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: cudaGetSymbolAddress");
+      g_noalloc_addr[dev] = ptr;
+    }
+    base = (unsigned char*)g_noalloc_addr[dev];
+  }
+  unsigned long long* counter = (unsigned long long*)base;
+  double* prm = (double*)(base + 256);
+  double* d_p = prm;
+  double* d_q = d_p + N * M;
+  double* d_w = d_q + N * M;
+  double* d_c1 = d_w + L;
+  double* d_c2 = d_c1 + N;
+  double* d_W = d_c2 + N;
+  double* slots = (double*)(base + 256 + sizeof(double) * NOALLOC_PARAM_DOUBLES);
+
+  // parameters in heap order, staged on the host stack (no heap allocation)
+  double ph[NMAX * 6], qh[NMAX * 6];
+  for (int k = 1; k <= K; ++k)
+    for (int i = 1; i <= (1 << (k - 1)); ++i) {
+      const int j = (1 << K) - (1 << k) + (i - 1);  // paper ordering
+      const int hn = (1 << (k - 1)) + i - 2;       // array index (heap number - 1)
+      for (int m = 0; m < M; ++m) { ph[hn * M + m] = d.p[j * M + m]; qh[hn * M + m] = d.q[j * M + m]; }
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  e = cudaMemcpyAsync(d_p, ph, sizeof(double) * N * M, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_q, qh, sizeof(double) * N * M, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, d.w, sizeof(double) * L, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: parameter upload");
+  k_setup_tree<<<1, 1, 0, s>>>(K, d_w, d_W, d_c1, d_c2);
+  // the counter keeps the previous call's value: clear it
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: counter reset");
+  td.p = d_p; td.q = d_q; td.c1 = d_c1; td.c2 = d_c2; td.W = d_W;
+  NoAllocParams P{td, n, nslots, lam, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status, slots,
+                  counter, tol, max_iter};
+  k_newton_noalloc<<<(unsigned)(nslots / NOALLOC_BLOCK), NOALLOC_BLOCK, 0, s>>>(P);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? DMN_OK : cuda_fail(nullptr, e, "dmn_update_noalloc: launch");
+}

@@ -16,7 +16,7 @@ _lib = None
 
 # ABI symbols declared in include/dmn.h
 EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_interp_orientation", "dmn_update",
-           "dmn_profile_enable", "dmn_profile_read", "dmn_last_error")
+           "dmn_profile_enable", "dmn_profile_read", "dmn_update_noalloc", "dmn_last_error")
 
 PREC_F64 = 0
 PREC_MIXED = 1
