@@ -1,25 +1,27 @@
 // Kernels and C ABI of the batched DMN material-point update (include/dmn.h).
 //
 // Per update three kernels run on the caller's stream:
-//   k_normals  one thread per point: lamination normals of every laminate from
+//   k_prepare  one thread per point: lamination normals of every laminate from
 //              the orientation (barycentric coordinates, shape functions,
-//              interpolated angles, spherical normal; Sec. 2.3);
+//              interpolated angles, spherical normal; Sec. 2.3) and the macro
+//              strain in the principal frame;
 //   k_newton   persistent, one thread per point slot: the Newton loop of
 //              Sec. 3.2.  A lane that converges writes its results and takes
 //              the next point from a global counter at once, so lanes stay busy
 //              although points need different numbers of Newton steps;
 //   k_final    one thread per point: the return mapping at the converged jumps
-//              writes z^{n+1}; in the mixed form also the FP64 sweep that
-//              yields stress and algorithmic tangent.
+//              writes z^{n+1}, and stress and tangent are rotated back to the
+//              global frame; in the mixed form this kernel first runs the FP64
+//              sweep that yields them.
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
-#include <array>
-#include <mutex>
 
 #include "../../include/dmn.h"
 #include "dmn_device.cuh"
@@ -34,9 +36,8 @@ struct Tree {
   int K, M, N, L, nz, z_both, S;
   double* d_p = nullptr;
   double* d_q = nullptr;
-  double* d_c1 = nullptr;
-  double* d_c2 = nullptr;
-  double* d_W = nullptr;
+  double* d_c = nullptr;   // c1 [N], c2 [N], sc [N]
+  float* d_cf = nullptr;   // c1f [N], c2f [N], c12f [N]
   PhaseDev ph[2];
 };
 
@@ -48,9 +49,9 @@ struct dmn_handle {
   int device = 0, n_sm = 0;
   int64_t nslots = 0;
   double* scr_d = nullptr;      // per slot: normals [3N] + jumps [3N] (FP64)
-  void* scr_t = nullptr;        // per slot: g [3N] + H [18N] (FP64 or FP32)
+  void* scr_t = nullptr;        // per slot: g, H [21N] (FP64 or FP32) + FP32 normals [3N]
   unsigned long long* counter = nullptr;
-  double* nbuf = nullptr;       // per point normals [3N][n]
+  double* nbuf = nullptr;       // per point: normals [3N] + local macro strain [6], field-major
   int64_t nbuf_cap = 0;
   bool profiling = false;
   std::vector<std::array<cudaEvent_t, 4>> events;  // per timed update: before/after each kernel
@@ -72,17 +73,38 @@ int cuda_fail(dmn_handle* h, cudaError_t e, const char* what) {
 TreeDev tree_dev(const Tree& t) {
   TreeDev d;
   d.K = t.K; d.M = t.M; d.N = t.N; d.L = t.L; d.nz = t.nz; d.z_both = t.z_both;
-  d.p = t.d_p; d.q = t.d_q; d.c1 = t.d_c1; d.c2 = t.d_c2; d.W = t.d_W;
+  d.p = t.d_p; d.q = t.d_q;
+  d.c1 = t.d_c; d.c2 = t.d_c + t.N; d.sc = t.d_c + 2 * t.N;
+  d.c1f = t.d_cf; d.c2f = t.d_cf + t.N; d.c12f = t.d_cf + 2 * t.N;
   d.ph[0] = t.ph[0]; d.ph[1] = t.ph[1];
   return d;
 }
 
+// Checks one phase of a tree description and derives its device constants.
+const char* make_phase(const dmn_phase& p, PhaseDev& out) {
+  if (p.kind != DMN_PHASE_ELASTIC && p.kind != DMN_PHASE_J2_LINEAR) return "unknown phase kind";
+  if (!(p.E > 0.0) || !(p.nu > -1.0) || !(p.nu < 0.5)) return "need E > 0 and -1 < nu < 0.5";
+  if (p.kind == DMN_PHASE_J2_LINEAR && (!(p.sigma0 > 0.0) || !(p.H >= 0.0)))
+    return "J2 phase needs sigma0 > 0 and H >= 0";
+  out.kind = p.kind;
+  out.K = p.E / (3.0 * (1.0 - 2.0 * p.nu));
+  out.G = p.E / (2.0 * (1.0 + p.nu));
+  out.s0 = p.sigma0;
+  out.H = p.H;
+  out.lam = out.K - 2.0 * out.G / 3.0;
+  out.inv_den = 1.0 / (2.0 * out.G + 2.0 * p.H / 3.0);
+  out.thb0 = 1.0 / (1.0 + p.H / (3.0 * out.G));
+  return nullptr;
+}
+
 // ---------------------------------------------------------------------------
 // Weights (Sec. 2.1): w normalised to sum 1; w^i_k = w^{2i-1}_{k+1} + w^{2i}_{k+1};
-// c1 = w_left / (w_left + w_right), c2 = 1 - c1.  Heap order.  One thread.
-__global__ void k_setup_tree(int K, const double* w_raw, double* W, double* c1, double* c2) {
+// c1 = w_left / (w_left + w_right), c2 = 1 - c1; sc = W c1 c2 scales the
+// laminate's residual.  Heap order.  One thread.
+__global__ void k_setup_tree(int K, const double* w_raw, double* c, float* cf) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   const int L = 1 << K, N = L - 1;
+  double W[NMAX];
   double s = 0.0;
   for (int l = 0; l < L; ++l) s += w_raw[l];
   for (int h = N; h >= 1; --h) {
@@ -96,8 +118,13 @@ __global__ void k_setup_tree(int K, const double* w_raw, double* W, double* c1, 
       wr = W[2 * h];
     }
     W[h - 1] = wl + wr;
-    c1[h - 1] = wl / (wl + wr);
-    c2[h - 1] = 1.0 - c1[h - 1];
+    const double c1 = wl / (wl + wr), c2 = 1.0 - c1;
+    c[h - 1] = c1;
+    c[N + h - 1] = c2;
+    c[2 * N + h - 1] = W[h - 1] * c1 * c2;
+    cf[h - 1] = (float)c1;
+    cf[N + h - 1] = (float)c2;
+    cf[2 * N + h - 1] = (float)(c1 * c2);
   }
 }
 
@@ -163,14 +190,12 @@ __global__ void k_interp(int64_t n, const double* __restrict__ A2, double* __res
 }
 
 // ---------------------------------------------------------------------------
-// Normals of every laminate (Sec. 2.3): phi = barycentric coordinates of
-// (lam1, lam2) in the triangle UD (1,0), ISO (1/3,1/3), PI (1/2,1/2), i.e.
-// phi = (lam1 - lam2, 3 lam3, 2 lam1 + 4 lam2 - 2); shape functions of order M;
-// alpha = p.phi, beta = q.phi; n = (sin a cos b, sin a sin b, cos a).
-__global__ void k_normals(TreeDev t, int64_t n, const double* __restrict__ lam, double* __restrict__ nbuf) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double l1 = lam[2 * i], l2 = lam[2 * i + 1];
+// Normals of every laminate of one point (Sec. 2.3): phi = barycentric
+// coordinates of (lam1, lam2) in the triangle UD (1,0), ISO (1/3,1/3),
+// PI (1/2,1/2), i.e. phi = (lam1 - lam2, 3 lam3, 2 lam1 + 4 lam2 - 2); shape
+// functions of order M; alpha = p.phi, beta = q.phi;
+// n = (sin a cos b, sin a sin b, cos a).  Written to strided storage.
+__device__ void point_normals(const TreeDev& t, double l1, double l2, double* out, size_t stride) {
   const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
   double ph[6];
   if (t.M == 3) {
@@ -191,9 +216,9 @@ __global__ void k_normals(TreeDev t, int64_t n, const double* __restrict__ lam, 
     double sa, ca, sb, cb;
     sincos(al, &sa, &ca);
     sincos(be, &sb, &cb);
-    nbuf[(size_t)(3 * j + 0) * n + i] = sa * cb;
-    nbuf[(size_t)(3 * j + 1) * n + i] = sa * sb;
-    nbuf[(size_t)(3 * j + 2) * n + i] = ca;
+    out[(size_t)(3 * j + 0) * stride] = sa * cb;
+    out[(size_t)(3 * j + 1) * stride] = sa * sb;
+    out[(size_t)(3 * j + 2) * stride] = ca;
   }
 }
 
@@ -211,11 +236,26 @@ __device__ __forceinline__ void local_strain(const double* Q, const double* En, 
   }
 }
 
+// per point: normals and the macro strain in the principal frame
+__global__ void k_prepare(TreeDev t, int64_t n, const double* __restrict__ lam, const double* __restrict__ Q,
+                          const double* __restrict__ En, const double* __restrict__ dE, double* __restrict__ nbuf) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  point_normals(t, lam[2 * i], lam[2 * i + 1], nbuf + i, (size_t)n);
+  double E[6];
+  local_strain(Q + 9 * i, En + 6 * i, dE + 6 * i, E);
+#pragma unroll
+  for (int I = 0; I < 6; ++I) nbuf[(size_t)(3 * t.N + I) * n + i] = E[I];
+}
+
 template <typename T>
 __device__ __forceinline__ void write_stress_tangent(const double* Q, const double sb[6], const T C[21], double* stress,
                                                      double* tangent) {
   double R[6][6];
   mandel_rotation(Q, R);
+  double Cl[21];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) Cl[k] = (double)C[k];
 #pragma unroll
   for (int I = 0; I < 6; ++I) {
     double s = 0.0;
@@ -230,7 +270,7 @@ __device__ __forceinline__ void write_stress_tangent(const double* Q, const doub
     for (int J = 0; J < 6; ++J) {
       double s = 0.0;
 #pragma unroll
-      for (int P = 0; P < 6; ++P) s += R[I][P] * (double)C[sidx(P, J)];
+      for (int P = 0; P < 6; ++P) s += R[I][P] * Cl[sidx(P, J)];
       RC[I][J] = s;
     }
 #pragma unroll
@@ -248,7 +288,7 @@ template <typename T>
 struct NewtonParams {
   TreeDev t;
   int64_t n, nslots;
-  const double *Q, *En, *dE, *state_in;
+  const double* state_in;
   double *state_out, *stress, *tangent;
   int32_t *iters, *status;
   const double* nbuf;
@@ -257,7 +297,7 @@ struct NewtonParams {
   unsigned long long* counter;
   double tol;
   int max_iter;
-  int write_outputs;  // FP64 form: stress and tangent come from the converged Newton pass
+  int write_outputs;  // FP64 form: stress and tangent (local frame) come from the converged Newton pass
 };
 
 template <typename T>
@@ -267,8 +307,10 @@ __global__ void __launch_bounds__(128) k_newton(NewtonParams<T> P) {
   const TreeDev& t = P.t;
   const int N = t.N;
   double* my_nrm = P.scr_d + slot;
+  float* my_nrmf = (float*)(P.scr_t + (size_t)(21 * N) * P.nslots) + slot;
   PointArrays A;
   A.nrm = my_nrm; A.ns = (size_t)P.nslots;
+  A.nrmf = my_nrmf;
   A.a = P.scr_d + (size_t)(3 * N) * P.nslots + slot; A.as = (size_t)P.nslots;
   A.paper = false;
   A.z = nullptr; A.zs = (size_t)P.n;
@@ -288,14 +330,17 @@ __global__ void __launch_bounds__(128) k_newton(NewtonParams<T> P) {
       if (need) {
         pt = (int64_t)(base + __popc(mask & ((1u << lane) - 1u)));
         if (pt < P.n) {
-          local_strain(P.Q + 9 * pt, P.En + 6 * pt, P.dE + 6 * pt, Eloc);
+#pragma unroll
+          for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * N + I) * P.n + pt];
           for (int f = 0; f < 3 * N; ++f) {
             const int node = f / 3, c = f - 3 * node;
             // heap node -> paper index of its jumps
             const int lvl = 32 - __clz(node + 1);
             const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
             A.a[(size_t)f * A.as] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
-            my_nrm[(size_t)f * A.ns] = P.nbuf[(size_t)f * P.n + pt];
+            const double nv = P.nbuf[(size_t)f * P.n + pt];
+            my_nrm[(size_t)f * A.ns] = nv;
+            if (sizeof(T) == 4) my_nrmf[(size_t)f * A.ns] = (float)nv;
           }
           A.z = P.state_in + pt;
           it = 0;
@@ -318,7 +363,8 @@ __global__ void __launch_bounds__(128) k_newton(NewtonParams<T> P) {
     else if (rn <= P.tol * (double)N * sn) st = DMN_STATUS_OK;
     else if (it >= P.max_iter) st = DMN_STATUS_MAXITER;
     if (st < 0) { ++it; continue; }
-    // finished point: jumps (paper ordering), counters, and in the FP64 form stress + tangent
+    // finished point: jumps (paper ordering), counters, and in the FP64 form the
+    // local-frame stress and packed tangent for k_final to rotate
     const double qnan = __longlong_as_double(0x7ff8000000000000LL);
     for (int f = 0; f < 3 * N; ++f) {
       const int node = f / 3, c = f - 3 * node;
@@ -329,12 +375,10 @@ __global__ void __launch_bounds__(128) k_newton(NewtonParams<T> P) {
     P.iters[pt] = it;
     P.status[pt] = st;
     if (P.write_outputs) {
-      if (st == DMN_STATUS_NONFINITE) {
-        for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
-        for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
-      } else {
-        write_stress_tangent<T>(P.Q + 9 * pt, root.sb, root.C, P.stress + 6 * pt, P.tangent + 36 * pt);
-      }
+#pragma unroll
+      for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = root.sb[I];
+#pragma unroll
+      for (int k = 0; k < 21; ++k) P.tangent[36 * pt + k] = (double)root.C[k];
     }
     pt = -1;
   }
@@ -343,7 +387,7 @@ __global__ void __launch_bounds__(128) k_newton(NewtonParams<T> P) {
 struct FinalParams {
   TreeDev t;
   int64_t n;
-  const double *Q, *En, *dE, *state_in;
+  const double *Q, *state_in;
   double *state_out, *stress, *tangent;
   const int32_t* status;
   const double* nbuf;
@@ -356,29 +400,59 @@ __global__ void __launch_bounds__(128) k_final(FinalParams P) {
   const TreeDev& t = P.t;
   const int st = P.status[pt];
   double Eloc[6];
-  local_strain(P.Q + 9 * pt, P.En + 6 * pt, P.dE + 6 * pt, Eloc);
+#pragma unroll
+  for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * t.N + I) * P.n + pt];
   PointArrays A;
   A.nrm = P.nbuf + pt; A.ns = (size_t)P.n;
+  A.nrmf = nullptr;
   A.a = P.state_out + (size_t)(6 * t.nz) * P.n + pt; A.as = (size_t)P.n;
   A.paper = true;
   A.z = P.state_in + pt; A.zs = (size_t)P.n;
-  if (SWEEP) {
-    if (st == DMN_STATUS_NONFINITE) {
-      const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-      for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
-      for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
-    } else {
-      Sub<double> root;
-      double r2;
-      GH<double> gh{nullptr, 0};
-      tree_pass<double, false>(t, Eloc, A, gh, false, root, r2, nullptr);
-      write_stress_tangent<double>(P.Q + 9 * pt, root.sb, root.C, P.stress + 6 * pt, P.tangent + 36 * pt);
-    }
+  if (st == DMN_STATUS_NONFINITE) {
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
+    for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
+  } else if (SWEEP) {
+    Sub<double> root;
+    double r2;
+    GH<double> gh{nullptr, 0};
+    tree_pass<double, false>(t, Eloc, A, gh, false, root, r2, nullptr);
+    write_stress_tangent<double>(P.Q + 9 * pt, root.sb, root.C, P.stress + 6 * pt, P.tangent + 36 * pt);
+  } else {
+    double sb[6], C[21];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) sb[I] = P.stress[6 * pt + I];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) C[k] = P.tangent[36 * pt + k];
+    write_stress_tangent<double>(P.Q + 9 * pt, sb, C, P.stress + 6 * pt, P.tangent + 36 * pt);
   }
   write_leaf_states(t, Eloc, A, P.state_out + pt, (size_t)P.n, st == DMN_STATUS_NONFINITE);
 }
 
 int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// parameters of a tree description in heap order (array index = heap number - 1)
+void heap_params(const dmn_tree_desc& d, double* ph, double* qh) {
+  const int K = d.K, M = d.M;
+  for (int k = 1; k <= K; ++k)
+    for (int i = 1; i <= (1 << (k - 1)); ++i) {
+      const int j = (1 << K) - (1 << k) + (i - 1);  // paper ordering
+      const int hn = (1 << (k - 1)) + i - 2;       // array index (heap number - 1)
+      for (int m = 0; m < M; ++m) { ph[hn * M + m] = d.p[j * M + m]; qh[hn * M + m] = d.q[j * M + m]; }
+    }
+}
+
+const char* check_tree(const dmn_tree_desc& d) {
+  if (d.K < 1 || d.K > KMAX) return "K must be in 1..8";
+  if (d.M != 3 && d.M != 4 && d.M != 6) return "M must be 3, 4 or 6";
+  if (!d.p || !d.q || !d.w) return "p, q, w must be non-NULL";
+  const int N = (1 << d.K) - 1, L = 1 << d.K;
+  for (int l = 0; l < L; ++l)
+    if (!(d.w[l] > 0.0) || !std::isfinite(d.w[l])) return "leaf weights must be finite and > 0";
+  for (int j = 0; j < N * d.M; ++j)
+    if (!std::isfinite(d.p[j]) || !std::isfinite(d.q[j])) return "p, q must be finite";
+  return nullptr;
+}
 
 }  // namespace
 
@@ -393,33 +467,15 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   g_create_error.clear();
   if (!trees || n_trees != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: exactly one tree is supported");
   const dmn_tree_desc& d = trees[0];
-  if (d.K < 1 || d.K > KMAX) return fail(nullptr, DMN_ERR_ARG, "dmn_create: K must be in 1..8");
-  if (d.M != 3 && d.M != 4 && d.M != 6) return fail(nullptr, DMN_ERR_ARG, "dmn_create: M must be 3, 4 or 6");
-  if (!d.p || !d.q || !d.w) return fail(nullptr, DMN_ERR_ARG, "dmn_create: p, q, w must be non-NULL");
+  if (const char* m = check_tree(d)) return fail(nullptr, DMN_ERR_ARG, std::string("dmn_create: ") + m);
   const int K = d.K, M = d.M, N = (1 << K) - 1, L = 1 << K;
-  for (int l = 0; l < L; ++l)
-    if (!(d.w[l] > 0.0) || !std::isfinite(d.w[l]))
-      return fail(nullptr, DMN_ERR_ARG, "dmn_create: leaf weights must be finite and > 0");
-  for (int j = 0; j < N * M; ++j)
-    if (!std::isfinite(d.p[j]) || !std::isfinite(d.q[j]))
-      return fail(nullptr, DMN_ERR_ARG, "dmn_create: p, q must be finite");
   Tree t;
   t.K = K; t.M = M; t.N = N; t.L = L;
   int n_inel_phase = 0;
   for (int f = 0; f < 2; ++f) {
-    const dmn_phase& p = d.phase[f];
-    if (p.kind != DMN_PHASE_ELASTIC && p.kind != DMN_PHASE_J2_LINEAR)
-      return fail(nullptr, DMN_ERR_ARG, "dmn_create: unknown phase kind");
-    if (!(p.E > 0.0) || !(p.nu > -1.0) || !(p.nu < 0.5))
-      return fail(nullptr, DMN_ERR_ARG, "dmn_create: need E > 0 and -1 < nu < 0.5");
-    if (p.kind == DMN_PHASE_J2_LINEAR && (!(p.sigma0 > 0.0) || !(p.H >= 0.0)))
-      return fail(nullptr, DMN_ERR_ARG, "dmn_create: J2 phase needs sigma0 > 0 and H >= 0");
-    t.ph[f].kind = p.kind;
-    t.ph[f].K = p.E / (3.0 * (1.0 - 2.0 * p.nu));
-    t.ph[f].G = p.E / (2.0 * (1.0 + p.nu));
-    t.ph[f].s0 = p.sigma0;
-    t.ph[f].H = p.H;
-    n_inel_phase += p.kind == DMN_PHASE_J2_LINEAR;
+    if (const char* m = make_phase(d.phase[f], t.ph[f]))
+      return fail(nullptr, DMN_ERR_ARG, std::string("dmn_create: ") + m);
+    n_inel_phase += d.phase[f].kind == DMN_PHASE_J2_LINEAR;
   }
   t.z_both = n_inel_phase == 2;
   t.nz = n_inel_phase * (L / 2);
@@ -447,34 +503,27 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "dmn_create: device query"); }
 
-  // parameters in heap order
   std::vector<double> ph(N * M), qh(N * M);
-  for (int k = 1; k <= K; ++k)
-    for (int i = 1; i <= (1 << (k - 1)); ++i) {
-      const int j = (1 << K) - (1 << k) + (i - 1);   // paper ordering
-      const int hn = (1 << (k - 1)) + i - 2;        // array index (heap number - 1)
-      for (int m = 0; m < M; ++m) { ph[hn * M + m] = d.p[j * M + m]; qh[hn * M + m] = d.q[j * M + m]; }
-    }
+  heap_params(d, ph.data(), qh.data());
   double* d_w = nullptr;
   Tree& T = h->tree;
   e = cudaMalloc(&T.d_p, sizeof(double) * N * M);
   if (e == cudaSuccess) e = cudaMalloc(&T.d_q, sizeof(double) * N * M);
-  if (e == cudaSuccess) e = cudaMalloc(&T.d_c1, sizeof(double) * N);
-  if (e == cudaSuccess) e = cudaMalloc(&T.d_c2, sizeof(double) * N);
-  if (e == cudaSuccess) e = cudaMalloc(&T.d_W, sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&T.d_c, sizeof(double) * 3 * N);
+  if (e == cudaSuccess) e = cudaMalloc(&T.d_cf, sizeof(float) * 3 * N);
   if (e == cudaSuccess) e = cudaMalloc(&d_w, sizeof(double) * L);
   if (e == cudaSuccess) e = cudaMemcpy(T.d_p, ph.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(T.d_q, qh.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_w, d.w, sizeof(double) * L, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    k_setup_tree<<<1, 1>>>(K, d_w, T.d_W, T.d_c1, T.d_c2);
+    k_setup_tree<<<1, 1>>>(K, d_w, T.d_c, T.d_cf);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(d_w);
   h->nslots = (int64_t)h->n_sm * o.ctas_per_sm * o.block;
   if (e == cudaSuccess) e = cudaMalloc(&h->scr_d, sizeof(double) * (size_t)(6 * N) * h->nslots);
-  if (e == cudaSuccess) e = cudaMalloc(&h->scr_t, sizeof(double) * (size_t)(21 * N) * h->nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&h->scr_t, sizeof(double) * (size_t)(24 * N) * h->nslots);
   if (e == cudaSuccess) e = cudaMalloc(&h->counter, sizeof(unsigned long long));
   if (e != cudaSuccess) {
     dmn_destroy(h);
@@ -489,8 +538,8 @@ void dmn_destroy(dmn_handle* h) {
   cudaDeviceSynchronize();
   for (auto& a : h->events)
     for (auto& x : a) cudaEventDestroy(x);
-  cudaFree(h->tree.d_p); cudaFree(h->tree.d_q); cudaFree(h->tree.d_c1); cudaFree(h->tree.d_c2);
-  cudaFree(h->tree.d_W); cudaFree(h->scr_d); cudaFree(h->scr_t); cudaFree(h->counter); cudaFree(h->nbuf);
+  cudaFree(h->tree.d_p); cudaFree(h->tree.d_q); cudaFree(h->tree.d_c); cudaFree(h->tree.d_cf);
+  cudaFree(h->scr_d); cudaFree(h->scr_t); cudaFree(h->counter); cudaFree(h->nbuf);
   delete h;
 }
 
@@ -554,8 +603,8 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
   if (n > h->nbuf_cap) {
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) { cudaFree(h->nbuf); h->nbuf = nullptr; h->nbuf_cap = 0; }
-    if (e == cudaSuccess) e = cudaMalloc(&h->nbuf, sizeof(double) * (size_t)(3 * t.N) * n);
-    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: normals buffer");
+    if (e == cudaSuccess) e = cudaMalloc(&h->nbuf, sizeof(double) * (size_t)(3 * t.N + 6) * n);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: per-point buffer");
     h->nbuf_cap = n;
   }
   const TreeDev td = tree_dev(t);
@@ -573,24 +622,24 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
     ev = h->events[h->events_used++].data();
     cudaEventRecord(ev[0], s);
   }
-  k_normals<<<g1, 128, 0, s>>>(td, n, lam, h->nbuf);
+  k_prepare<<<g1, 128, 0, s>>>(td, n, lam, Q, E_n, dE, h->nbuf);
   if (ev) cudaEventRecord(ev[1], s);
+  // the Newton interval includes the counter reset (a few hundred ns)
   e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: counter reset");
-  // the Newton interval includes the counter reset (a few hundred ns)
   const unsigned grid = (unsigned)(h->n_sm * h->opt.ctas_per_sm);
   const bool mixed = h->opt.precision == DMN_PREC_MIXED;
   if (!mixed) {
-    NewtonParams<double> P{td, n, h->nslots, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status,
+    NewtonParams<double> P{td, n, h->nslots, state_in, state_out, stress, tangent, iters, status,
                            h->nbuf, h->scr_d, (double*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 1};
     k_newton<double><<<grid, h->opt.block, 0, s>>>(P);
   } else {
-    NewtonParams<float> P{td, n, h->nslots, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status,
+    NewtonParams<float> P{td, n, h->nslots, state_in, state_out, stress, tangent, iters, status,
                           h->nbuf, h->scr_d, (float*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 0};
     k_newton<float><<<grid, h->opt.block, 0, s>>>(P);
   }
   if (ev) cudaEventRecord(ev[2], s);
-  FinalParams F{td, n, Q, E_n, dE, state_in, state_out, stress, tangent, status, h->nbuf};
+  FinalParams F{td, n, Q, state_in, state_out, stress, tangent, status, h->nbuf};
   if (mixed) k_final<true><<<g1, 128, 0, s>>>(F);
   else k_final<false><<<g1, 128, 0, s>>>(F);
   if (ev) cudaEventRecord(ev[3], s);
@@ -614,7 +663,7 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
 namespace {
 
 constexpr size_t DMN_NOALLOC_BYTES = size_t(64) << 20;  // 64 MiB
-constexpr size_t NOALLOC_PARAM_DOUBLES = 4096;          // p, q, w, c1, c2, W for K <= 8, M <= 6
+constexpr size_t NOALLOC_PARAM_DOUBLES = 6144;          // p, q, w, c, cf for K <= 8, M <= 6
 constexpr int NOALLOC_BLOCK = 128;
 
 // [0, 256): work counter; [256, 256 + 8 * NOALLOC_PARAM_DOUBLES): tree parameters;
@@ -636,36 +685,9 @@ struct NoAllocParams {
   int max_iter;
 };
 
-// normals of every laminate of one point, written to strided scratch
-__device__ void point_normals(const TreeDev& t, double l1, double l2, double* out, size_t stride) {
-  const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
-  double ph[6];
-  if (t.M == 3) {
-    ph[0] = v[0]; ph[1] = v[1]; ph[2] = v[2];
-  } else if (t.M == 4) {
-    const double b = v[0] * v[1] * v[2];
-    ph[0] = v[0] - 9.0 * b; ph[1] = v[1] - 9.0 * b; ph[2] = v[2] - 9.0 * b; ph[3] = 27.0 * b;
-  } else {
-    ph[0] = v[0] * (2.0 * v[0] - 1.0); ph[1] = v[1] * (2.0 * v[1] - 1.0); ph[2] = v[2] * (2.0 * v[2] - 1.0);
-    ph[3] = 4.0 * v[0] * v[1]; ph[4] = 4.0 * v[0] * v[2]; ph[5] = 4.0 * v[1] * v[2];
-  }
-  for (int j = 0; j < t.N; ++j) {
-    double al = 0.0, be = 0.0;
-    for (int m = 0; m < t.M; ++m) {
-      al += t.p[j * t.M + m] * ph[m];
-      be += t.q[j * t.M + m] * ph[m];
-    }
-    double sa, ca, sb, cb;
-    sincos(al, &sa, &ca);
-    sincos(be, &sb, &cb);
-    out[(size_t)(3 * j + 0) * stride] = sa * cb;
-    out[(size_t)(3 * j + 1) * stride] = sa * sb;
-    out[(size_t)(3 * j + 2) * stride] = ca;
-  }
-}
-
-// FP64 Newton kernel of dmn_update, with the orientation normals and the new leaf
-// states computed by the lane that owns the point (no per-point buffers).
+// FP64 Newton kernel of dmn_update, with the orientation normals, the local
+// strain, the rotation of the results and the new leaf states computed by the
+// lane that owns the point (no per-point buffers).
 __global__ void __launch_bounds__(NOALLOC_BLOCK) k_newton_noalloc(NoAllocParams P) {
   const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -674,6 +696,7 @@ __global__ void __launch_bounds__(NOALLOC_BLOCK) k_newton_noalloc(NoAllocParams 
   double* my_nrm = P.slots + slot;
   PointArrays A;
   A.nrm = my_nrm; A.ns = (size_t)P.nslots;
+  A.nrmf = nullptr;
   A.a = P.slots + (size_t)(3 * N) * P.nslots + slot; A.as = (size_t)P.nslots;
   A.paper = false;
   A.z = nullptr; A.zs = (size_t)P.n;
@@ -751,17 +774,9 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
                                   int32_t* status, void* stream) {
   if (!tree) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: tree is NULL");
   const dmn_tree_desc& d = *tree;
-  if (d.K < 1 || d.K > KMAX) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: K must be in 1..8");
-  if (d.M != 3 && d.M != 4 && d.M != 6) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: M must be 3, 4 or 6");
-  if (!d.p || !d.q || !d.w) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: p, q, w must be non-NULL");
+  if (const char* m = check_tree(d)) return fail(nullptr, DMN_ERR_ARG, std::string("dmn_update_noalloc: ") + m);
   if (n < 0) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: n < 0");
   const int K = d.K, M = d.M, N = (1 << K) - 1, L = 1 << K;
-  for (int l = 0; l < L; ++l)
-    if (!(d.w[l] > 0.0) || !std::isfinite(d.w[l]))
-      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: leaf weights must be finite and > 0");
-  for (int j = 0; j < N * M; ++j)
-    if (!std::isfinite(d.p[j]) || !std::isfinite(d.q[j]))
-      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: p, q must be finite");
   double tol = 1e-12;
   int max_iter = 50;
   if (opt) {
@@ -774,24 +789,14 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   td.K = K; td.M = M; td.N = N; td.L = L;
   int n_inel = 0;
   for (int f = 0; f < 2; ++f) {
-    const dmn_phase& p = d.phase[f];
-    if (p.kind != DMN_PHASE_ELASTIC && p.kind != DMN_PHASE_J2_LINEAR)
-      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: unknown phase kind");
-    if (!(p.E > 0.0) || !(p.nu > -1.0) || !(p.nu < 0.5))
-      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: need E > 0 and -1 < nu < 0.5");
-    if (p.kind == DMN_PHASE_J2_LINEAR && (!(p.sigma0 > 0.0) || !(p.H >= 0.0)))
-      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: J2 phase needs sigma0 > 0 and H >= 0");
-    td.ph[f].kind = p.kind;
-    td.ph[f].K = p.E / (3.0 * (1.0 - 2.0 * p.nu));
-    td.ph[f].G = p.E / (2.0 * (1.0 + p.nu));
-    td.ph[f].s0 = p.sigma0;
-    td.ph[f].H = p.H;
-    n_inel += p.kind == DMN_PHASE_J2_LINEAR;
+    if (const char* m = make_phase(d.phase[f], td.ph[f]))
+      return fail(nullptr, DMN_ERR_ARG, std::string("dmn_update_noalloc: ") + m);
+    n_inel += d.phase[f].kind == DMN_PHASE_J2_LINEAR;
   }
   td.z_both = n_inel == 2;
   td.nz = n_inel * (L / 2);
   // sizes against the fixed work space: parameters, then whole CTAs of lane scratch
-  const size_t param_doubles = (size_t)2 * N * M + (size_t)L + 3 * (size_t)N;
+  const size_t param_doubles = (size_t)2 * N * M + (size_t)L + 3 * (size_t)N + (3 * (size_t)N + 1) / 2;
   const size_t lane_bytes = sizeof(double) * (size_t)27 * N;
   const size_t avail = DMN_NOALLOC_BYTES - 256 - sizeof(double) * NOALLOC_PARAM_DOUBLES;
   const int64_t nslots = (int64_t)(avail / lane_bytes) / NOALLOC_BLOCK * NOALLOC_BLOCK;
@@ -823,29 +828,25 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   double* d_p = prm;
   double* d_q = d_p + N * M;
   double* d_w = d_q + N * M;
-  double* d_c1 = d_w + L;
-  double* d_c2 = d_c1 + N;
-  double* d_W = d_c2 + N;
+  double* d_c = d_w + L;
+  float* d_cf = (float*)(d_c + 3 * N);
   double* slots = (double*)(base + 256 + sizeof(double) * NOALLOC_PARAM_DOUBLES);
 
   // parameters in heap order, staged on the host stack (no heap allocation)
   double ph[NMAX * 6], qh[NMAX * 6];
-  for (int k = 1; k <= K; ++k)
-    for (int i = 1; i <= (1 << (k - 1)); ++i) {
-      const int j = (1 << K) - (1 << k) + (i - 1);  // paper ordering
-      const int hn = (1 << (k - 1)) + i - 2;       // array index (heap number - 1)
-      for (int m = 0; m < M; ++m) { ph[hn * M + m] = d.p[j * M + m]; qh[hn * M + m] = d.q[j * M + m]; }
-    }
+  heap_params(d, ph, qh);
   cudaStream_t s = (cudaStream_t)stream;
   e = cudaMemcpyAsync(d_p, ph, sizeof(double) * N * M, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_q, qh, sizeof(double) * N * M, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, d.w, sizeof(double) * L, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: parameter upload");
-  k_setup_tree<<<1, 1, 0, s>>>(K, d_w, d_W, d_c1, d_c2);
+  k_setup_tree<<<1, 1, 0, s>>>(K, d_w, d_c, d_cf);
   // the counter keeps the previous call's value: clear it
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: counter reset");
-  td.p = d_p; td.q = d_q; td.c1 = d_c1; td.c2 = d_c2; td.W = d_W;
+  td.p = d_p; td.q = d_q;
+  td.c1 = d_c; td.c2 = d_c + N; td.sc = d_c + 2 * N;
+  td.c1f = d_cf; td.c2f = d_cf + N; td.c12f = d_cf + 2 * N;
   NoAllocParams P{td, n, nslots, lam, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status, slots,
                   counter, tol, max_iter};
   k_newton_noalloc<<<(unsigned)(nslots / NOALLOC_BLOCK), NOALLOC_BLOCK, 0, s>>>(P);

@@ -26,23 +26,48 @@ constexpr int NMAX = (1 << KMAX) - 1;
 constexpr double RS2 = 0.70710678118654752440;   // 1/sqrt(2)
 constexpr double SQ23 = 0.81649658092772603273;  // sqrt(2/3)
 
+// Isotropic phase: elastic (kind 0) or J2 with linear isotropic hardening
+// (kind 1).  Constants derived once on the host.
 struct PhaseDev {
-  int kind;        // 0 elastic, 1 J2 with linear hardening
-  double K, G;     // bulk and shear modulus
-  double s0, H;    // yield stress and hardening modulus
+  int kind;
+  double K, G;       // bulk and shear modulus
+  double s0, H;      // yield stress and hardening modulus
+  double lam;        // K - 2G/3: sigma = lam tr(eps) 1 + 2G eps when elastic
+  double inv_den;    // 1 / (2G + 2H/3): plastic multiplier per unit overstress
+  double thb0;       // 1 / (1 + H / (3G))
 };
 
+// Per-laminate constants, heap order.
 struct TreeDev {
   int K, M, N, L;
-  int nz;          // inelastic leaves
-  int z_both;      // 1 if both phases are inelastic (slot = leaf), else slot = leaf / 2
-  const double* p;   // [N][M] heap order
+  int nz;            // inelastic leaves
+  int z_both;        // 1 if both phases are inelastic (slot = leaf), else slot = leaf / 2
+  const double* p;   // [N][M]
   const double* q;   // [N][M]
   const double* c1;  // [N] volume fraction of the left child
   const double* c2;  // [N] volume fraction of the right child
-  const double* W;   // [N] subtree weight (normalised, root = 1)
+  const double* sc;  // [N] W c1 c2: scale of the laminate's residual (W = subtree weight)
+  const float* c1f;  // [N] FP32 copies of c1, c2, c1 c2
+  const float* c2f;
+  const float* c12f;
   PhaseDev ph[2];
 };
+
+template <typename T>
+struct NodeC {
+  T c1, c2, c12;
+};
+template <typename T>
+__device__ __forceinline__ NodeC<T> node_c(const TreeDev& t, int node);
+template <>
+__device__ __forceinline__ NodeC<double> node_c<double>(const TreeDev& t, int node) {
+  const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+  return {c1, c2, c1 * c2};
+}
+template <>
+__device__ __forceinline__ NodeC<float> node_c<float>(const TreeDev& t, int node) {
+  return {__ldg(t.c1f + node), __ldg(t.c2f + node), __ldg(t.c12f + node)};
+}
 
 // packed symmetric 6x6: upper triangle row by row
 __host__ __device__ constexpr int sidx(int i, int j) {
@@ -62,68 +87,72 @@ struct Sub {
   T C[21];
 };
 
-// ---------------------------------------------------------------------------
-// Phase laws (Sec. 3.2 two-potential GSM leaves; J2 radial return with linear
-// isotropic hardening).  z = (alpha_bar, ep11, ep22, ep23M, ep13M, ep12M).
+// Tangent of an isotropic leaf: D = lam 1(x)1 + 2 mu I - c m(x)m.
 template <typename T>
-__device__ __forceinline__ void leaf_law(const PhaseDev& ph, const double e[6], const double z[6], double sig[6],
-                                         T D[21], double* znew, double* gap) {
+struct LeafTan {
+  T lam, mu, c;
+  T m[6];
+};
+
+// ---------------------------------------------------------------------------
+// Phase law (Sec. 3.2 condensed GSM leaf; Sec. 4.1 J2 radial return, here with
+// linear isotropic hardening).  z = (alpha_bar, ep11, ep22, ep23M, ep13M, ep12M).
+//   s_tr = 2G (dev eps - ep), f = |s_tr| - sqrt(2/3) (s0 + H alpha_bar);
+//   f > 0: dg = f / (2G + 2H/3), n = s_tr / |s_tr|, s = s_tr - 2G dg n,
+//          ep += dg n, alpha_bar += sqrt(2/3) dg,
+//          D = K 1(x)1 + 2G th Idev - 2G thb n(x)n, th = 1 - 2G dg / |s_tr|,
+//          thb = 1/(1 + H/(3G)) - (1 - th).
+// Written without branches: an elastic step is the plastic formula with dg = 0.
+template <typename T>
+__device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], const double z[6], double sig[6],
+                                         LeafTan<T>* D, double* znew, double* gap) {
   const double tr = e[0] + e[1] + e[2];
-  const double m = tr * (1.0 / 3.0);
-  double dev[6] = {e[0] - m, e[1] - m, e[2] - m, e[3], e[4], e[5]};
   const double twoG = 2.0 * ph.G;
-  double th = 1.0, thb = 0.0, nh[6] = {0, 0, 0, 0, 0, 0};
   if (ph.kind == 0) {
+    const double lt = ph.lam * tr;
 #pragma unroll
-    for (int I = 0; I < 6; ++I) sig[I] = twoG * dev[I];
-    if (gap) *gap = 1e300;
-  } else {
-    const double ep[6] = {z[1], z[2], -(z[1] + z[2]), z[3], z[4], z[5]};
-    double st[6], n2 = 0.0;
+    for (int I = 0; I < 6; ++I) sig[I] = twoG * e[I];
+    sig[0] += lt; sig[1] += lt; sig[2] += lt;
+    if (D) {
+      D->lam = (T)ph.lam; D->mu = (T)ph.G; D->c = (T)0;
 #pragma unroll
-    for (int I = 0; I < 6; ++I) { st[I] = twoG * (dev[I] - ep[I]); n2 += st[I] * st[I]; }
-    const double ns = sqrt(n2);
-    const double sy = ph.s0 + ph.H * z[0];
-    const double f = ns - SQ23 * sy;
-    if (gap) *gap = fabs(f) / sy;
-    if (f > 0.0) {
-      const double dg = f / (twoG + (2.0 / 3.0) * ph.H);
-      const double ins = 1.0 / ns;
-#pragma unroll
-      for (int I = 0; I < 6; ++I) { nh[I] = st[I] * ins; sig[I] = st[I] - twoG * dg * nh[I]; }
-      th = 1.0 - twoG * dg * ins;
-      thb = 1.0 / (1.0 + ph.H / (3.0 * ph.G)) - (1.0 - th);
-      if (znew) {
-        znew[0] = z[0] + SQ23 * dg;
-        znew[1] = z[1] + dg * nh[0]; znew[2] = z[2] + dg * nh[1];
-        znew[3] = z[3] + dg * nh[3]; znew[4] = z[4] + dg * nh[4]; znew[5] = z[5] + dg * nh[5];
-      }
-    } else {
-#pragma unroll
-      for (int I = 0; I < 6; ++I) sig[I] = st[I];
-      if (znew) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) znew[c] = z[c];
-      }
+      for (int I = 0; I < 6; ++I) D->m[I] = (T)0;
     }
+    if (gap) *gap = 1e300;
+    return;
   }
+  const double m3 = tr * (1.0 / 3.0);
+  const double ep2 = -(z[1] + z[2]);
+  double st[6] = {twoG * (e[0] - m3 - z[1]), twoG * (e[1] - m3 - z[2]), twoG * (e[2] - m3 - ep2),
+                  twoG * (e[3] - z[3]),      twoG * (e[4] - z[4]),      twoG * (e[5] - z[5])};
+  double n2 = 0.0;
+#pragma unroll
+  for (int I = 0; I < 6; ++I) n2 += st[I] * st[I];
+  const double ins = rsqrt(fmax(n2, 1e-300));
+  const double ns = n2 * ins;
+  const double sy = ph.s0 + ph.H * z[0];
+  const double f = ns - SQ23 * sy;
+  const bool plastic = f > 0.0;
+  if (gap) *gap = fabs(f) / sy;
+  const double dg = plastic ? f * ph.inv_den : 0.0;
+  const double k2 = twoG * dg * ins;        // 2G dg / |s_tr| = 1 - th
   const double Kt = ph.K * tr;
+#pragma unroll
+  for (int I = 0; I < 6; ++I) sig[I] = st[I] - k2 * st[I];
   sig[0] += Kt; sig[1] += Kt; sig[2] += Kt;
   if (D) {
-    // D = K 1(x)1 + 2G th Idev - 2G thb nh(x)nh
-    const T a = (T)(twoG * th), b = (T)(ph.K - twoG * th * (1.0 / 3.0)), c = (T)(twoG * thb);
-    T n[6];
+    const double mu = ph.G * (1.0 - k2);
+    D->mu = (T)mu;
+    D->lam = (T)(ph.K - (2.0 / 3.0) * mu);
+    D->c = (T)(plastic ? twoG * (ph.thb0 - k2) : 0.0);
 #pragma unroll
-    for (int I = 0; I < 6; ++I) n[I] = (T)nh[I];
-#pragma unroll
-    for (int I = 0; I < 6; ++I)
-#pragma unroll
-      for (int J = I; J < 6; ++J) {
-        T v = -c * n[I] * n[J];
-        if (I == J) v += a;
-        if (I < 3 && J < 3) v += b;
-        D[sidx(I, J)] = v;
-      }
+    for (int I = 0; I < 6; ++I) D->m[I] = (T)(st[I] * ins);
+  }
+  if (znew) {
+    const double di = dg * ins;
+    znew[0] = z[0] + SQ23 * dg;
+    znew[1] = z[1] + di * st[0]; znew[2] = z[2] + di * st[1];
+    znew[3] = z[3] + di * st[3]; znew[4] = z[4] + di * st[4]; znew[5] = z[5] + di * st[5];
   }
 }
 
@@ -154,6 +183,48 @@ __device__ __forceinline__ void SN_apply(const T S[21], const T n[3], const T nr
     out[I][2] = S[sidx(I, 2)] * n[2] + S[sidx(I, 3)] * nr[1] + S[sidx(I, 4)] * nr[0];
   }
 }
+// structural non-zeros of N: (I, I) for I < 3 and two entries in each shear row
+__host__ __device__ constexpr bool N_nonzero(int I, int j) {
+  return I < 3 ? I == j : !((I == 3 && j == 0) || (I == 4 && j == 1) || (I == 5 && j == 2));
+}
+// entry (I, j) of N: column j of sym(e_j (x) n)
+template <typename T>
+__device__ __forceinline__ T N_entry(const T n[3], const T nr[3], int I, int j) {
+  if (I < 3) return I == j ? n[j] : (T)0;
+  const int a = I == 3 ? 1 : 0, b = I == 5 ? 1 : 2;  // index pair of shear component I
+  if (j == a) return nr[b];
+  if (j == b) return nr[a];
+  return (T)0;
+}
+
+// Symmetric 3x3 inverse by cofactors (the matrix is positive definite).
+template <typename T>
+__device__ __forceinline__ void inv3_sym(T k00, T k01, T k02, T k11, T k12, T k22, T Ki[3][3]) {
+  const T i00 = k11 * k22 - k12 * k12;
+  const T i01 = k02 * k12 - k01 * k22;
+  const T i02 = k01 * k12 - k02 * k11;
+  const T i11 = k00 * k22 - k02 * k02;
+  const T i12 = k01 * k02 - k00 * k12;
+  const T i22 = k00 * k11 - k01 * k01;
+  const T idet = (T)1 / (k00 * i00 + k01 * i01 + k02 * i02);
+  Ki[0][0] = i00 * idet; Ki[0][1] = i01 * idet; Ki[0][2] = i02 * idet;
+  Ki[1][0] = Ki[0][1];   Ki[1][1] = i11 * idet; Ki[1][2] = i12 * idet;
+  Ki[2][0] = Ki[0][2];   Ki[2][1] = Ki[1][2];   Ki[2][2] = i22 * idet;
+}
+
+// The laminate's FP64 residual share (A^T W sigma)_j = W c1 c2 N^T (sb_R - sb_L),
+// added to r2, the plain average sb = c1 sb_L + c2 sb_R, and t = N^T (sb_R - sb_L).
+__device__ __forceinline__ void residual_share(const double nd[3], double c1, double c2, double sc, const double sL[6],
+                                               const double sR[6], double sb[6], double t[3], double& r2) {
+  double d[6];
+#pragma unroll
+  for (int I = 0; I < 6; ++I) d[I] = sR[I] - sL[I];
+  const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+  Nt_apply<double>(nd, ndr, d, t);
+  r2 += sc * sc * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+#pragma unroll
+  for (int I = 0; I < 6; ++I) sb[I] = c1 * sL[I] + c2 * sR[I];
+}
 
 // ---------------------------------------------------------------------------
 // Condensation of one laminate with children L (fraction c1) and R (c2) and
@@ -170,57 +241,35 @@ __device__ __forceinline__ void SN_apply(const T S[21], const T n[3], const T nr
 // For constant child tangents this is the laminate homogenisation of Sec. 3.1;
 // eliminating laminates leaves-to-root is Gaussian elimination of the Newton
 // system A^T W D A da = -A^T W sigma of Sec. 3.2 (no fill in that order).
-// The FP64 residual of the laminate, (A^T W sigma)_j = W c1 c2 N^T
-// (sb_R - sb_L), is added to r2 as a squared norm.
 template <typename T, bool STORE>
-__device__ __forceinline__ void condense(const double nd[3], double c1d, double c2d, double Wd, const Sub<T>& L,
-                                         const Sub<T>& R, Sub<T>& out, T* g_out, T* H_out, size_t gstride,
-                                         double& r2) {
+__device__ __forceinline__ void condense(const double nd[3], const T n[3], double c1d, double c2d, double sc,
+                                         NodeC<T> cc, const Sub<T>& L, const Sub<T>& R, Sub<T>& out, T* gp,
+                                         size_t gstride, double& r2) {
   T u[3];
   {
-    double d[6];
-#pragma unroll
-    for (int I = 0; I < 6; ++I) d[I] = R.sb[I] - L.sb[I];
-    const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
     double t[3];
-    Nt_apply<double>(nd, ndr, d, t);
-    const double sc = Wd * c1d * c2d;
-    r2 += sc * sc * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-#pragma unroll
-    for (int I = 0; I < 6; ++I) out.sb[I] = c1d * L.sb[I] + c2d * R.sb[I];
+    residual_share(nd, c1d, c2d, sc, L.sb, R.sb, out.sb, t, r2);
     u[0] = (T)t[0]; u[1] = (T)t[1]; u[2] = (T)t[2];
   }
-  const T c1 = (T)c1d, c2 = (T)c2d, c12 = (T)(c1d * c2d);
-  const T n[3] = {(T)nd[0], (T)nd[1], (T)nd[2]};
-  const T nr[3] = {(T)(nd[0] * RS2), (T)(nd[1] * RS2), (T)(nd[2] * RS2)};
+  const T c1 = cc.c1, c2 = cc.c2, c12 = cc.c12;
+  const T nr[3] = {n[0] * (T)RS2, n[1] * (T)RS2, n[2] * (T)RS2};
   T Ch[21], dC[21];
 #pragma unroll
   for (int k = 0; k < 21; ++k) { Ch[k] = c2 * L.C[k] + c1 * R.C[k]; dC[k] = R.C[k] - L.C[k]; }
   T ChN[6][3], B[6][3];
   SN_apply<T>(Ch, n, nr, ChN);
   SN_apply<T>(dC, n, nr, B);
-  // Kn = N^T Ch N (symmetric 3x3)
   T k[3][3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    T col[6] = {ChN[0][m], ChN[1][m], ChN[2][m], ChN[3][m], ChN[4][m], ChN[5][m]};
+    const T col[6] = {ChN[0][m], ChN[1][m], ChN[2][m], ChN[3][m], ChN[4][m], ChN[5][m]};
     T r[3];
     Nt_apply<T>(n, nr, col, r);
     k[0][m] = r[0]; k[1][m] = r[1]; k[2][m] = r[2];
   }
-  // inverse by cofactors (Kn is symmetric positive definite); symmetrised entries
-  const T k01 = (T)0.5 * (k[0][1] + k[1][0]), k02 = (T)0.5 * (k[0][2] + k[2][0]), k12 = (T)0.5 * (k[1][2] + k[2][1]);
-  const T i00 = k[1][1] * k[2][2] - k12 * k12;
-  const T i01 = k02 * k12 - k01 * k[2][2];
-  const T i02 = k01 * k12 - k02 * k[1][1];
-  const T i11 = k[0][0] * k[2][2] - k02 * k02;
-  const T i12 = k01 * k02 - k[0][0] * k12;
-  const T i22 = k[0][0] * k[1][1] - k01 * k01;
-  const T idet = (T)1 / (k[0][0] * i00 + k01 * i01 + k02 * i02);
-  const T Ki[3][3] = {{i00 * idet, i01 * idet, i02 * idet},
-                      {i01 * idet, i11 * idet, i12 * idet},
-                      {i02 * idet, i12 * idet, i22 * idet}};
-  // H = -Ki B^T (3x6),  g = -Ki N^T (s_R - s_L)
+  T Ki[3][3];
+  inv3_sym<T>(k[0][0], (T)0.5 * (k[0][1] + k[1][0]), (T)0.5 * (k[0][2] + k[2][0]), k[1][1],
+              (T)0.5 * (k[1][2] + k[2][1]), k[2][2], Ki);
   T H[3][6];
 #pragma unroll
   for (int m = 0; m < 3; ++m)
@@ -234,27 +283,113 @@ __device__ __forceinline__ void condense(const double nd[3], double c1d, double 
   for (int m = 0; m < 3; ++m) u[m] += v[m];
 #pragma unroll
   for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
-  // ds, C of the laminate
 #pragma unroll
-  for (int I = 0; I < 6; ++I) {
-    const T bg = B[I][0] * g[0] + B[I][1] * g[1] + B[I][2] * g[2];
-    out.ds[I] = c1 * L.ds[I] + c2 * R.ds[I] + c12 * bg;
-  }
+  for (int I = 0; I < 6; ++I)
+    out.ds[I] = c1 * L.ds[I] + c2 * R.ds[I] + c12 * (B[I][0] * g[0] + B[I][1] * g[1] + B[I][2] * g[2]);
 #pragma unroll
   for (int I = 0; I < 6; ++I)
 #pragma unroll
     for (int J = I; J < 6; ++J) {
-      const T bh = B[I][0] * H[0][J] + B[I][1] * H[1][J] + B[I][2] * H[2][J];
       const int s = sidx(I, J);
-      out.C[s] = c1 * L.C[s] + c2 * R.C[s] + c12 * bh;
+      out.C[s] = c1 * L.C[s] + c2 * R.C[s] + c12 * (B[I][0] * H[0][J] + B[I][1] * H[1][J] + B[I][2] * H[2][J]);
     }
   if (STORE) {
 #pragma unroll
-    for (int m = 0; m < 3; ++m) g_out[m * gstride] = g[m];
+    for (int m = 0; m < 3; ++m) gp[m * gstride] = g[m];
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
-      for (int I = 0; I < 6; ++I) H_out[(6 * m + I) * gstride] = H[m][I];
+      for (int I = 0; I < 6; ++I) gp[(3 + 6 * m + I) * gstride] = H[m][I];
+  }
+}
+
+// Condensation of a bottom laminate, whose children are leaves with isotropic
+// tangents D_X = lam_X 1(x)1 + 2 mu_X I - c_X m_X (x) m_X (X = L, R).  With
+// N^T 1 = n and N^T N = (I + n (x) n) / 2 the laminate algebra above reduces to
+//   Kn = a I + b n (x) n - c2 c_L u_L (x) u_L - c1 c_R u_R (x) u_R,
+//        a = c2 mu_L + c1 mu_R, b = c2 (lam_L + mu_L) + c1 (lam_R + mu_R), u_X = N^T m_X,
+//   B  = (lam_R - lam_L) 1 (x) n + 2 (mu_R - mu_L) N - c_R m_R (x) u_R + c_L m_L (x) u_L,
+//   C  = (c1 lam_L + c2 lam_R) 1(x)1 + 2 (c1 mu_L + c2 mu_R) I
+//        - c1 c_L m_L (x) m_L - c2 c_R m_R (x) m_R + c1 c2 B H,
+// and, the leaves having no inner corrections, ds = c1 c2 B g with g = -Kn^-1 t.
+template <typename T, bool STORE>
+__device__ __forceinline__ void condense_bottom(const double nd[3], const T n[3], double c1d, double c2d, double sc,
+                                                NodeC<T> cc, const double sL[6], const LeafTan<T>& DL,
+                                                const double sR[6], const LeafTan<T>& DR, Sub<T>& out, T* gp,
+                                                size_t gstride, double& r2) {
+  T u[3];
+  {
+    double t[3];
+    residual_share(nd, c1d, c2d, sc, sL, sR, out.sb, t, r2);
+    u[0] = (T)t[0]; u[1] = (T)t[1]; u[2] = (T)t[2];
+  }
+  const T c1 = cc.c1, c2 = cc.c2, c12 = cc.c12;
+  const T nr[3] = {n[0] * (T)RS2, n[1] * (T)RS2, n[2] * (T)RS2};
+  T uL[3], uR[3];
+  Nt_apply<T>(n, nr, DL.m, uL);
+  Nt_apply<T>(n, nr, DR.m, uR);
+  const T a = c2 * DL.mu + c1 * DR.mu;
+  const T b = c2 * (DL.lam + DL.mu) + c1 * (DR.lam + DR.mu);
+  const T wL = c2 * DL.c, wR = c1 * DR.c;
+  T k[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) k[i][j] = b * n[i] * n[j] - wL * uL[i] * uL[j] - wR * uR[i] * uR[j] + (i == j ? a : (T)0);
+  T Ki[3][3];
+  inv3_sym<T>(k[0][0], k[0][1], k[0][2], k[1][1], k[1][2], k[2][2], Ki);
+  const T dlam = DR.lam - DL.lam, dmu2 = (T)2 * (DR.mu - DL.mu);
+  T cmL[6], cmR[6];
+#pragma unroll
+  for (int I = 0; I < 6; ++I) { cmL[I] = DL.c * DL.m[I]; cmR[I] = DR.c * DR.m[I]; }
+  T B[6][3];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T v = cmL[I] * uL[j] - cmR[I] * uR[j];
+      if (I < 3) v += dlam * n[j];
+      if (N_nonzero(I, j)) v += dmu2 * N_entry<T>(n, nr, I, j);
+      B[I][j] = v;
+    }
+  T H[3][6];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int I = 0; I < 6; ++I) H[m][I] = -(Ki[m][0] * B[I][0] + Ki[m][1] * B[I][1] + Ki[m][2] * B[I][2]);
+  T g[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
+  const T g12[3] = {c12 * g[0], c12 * g[1], c12 * g[2]};
+#pragma unroll
+  for (int I = 0; I < 6; ++I) out.ds[I] = B[I][0] * g12[0] + B[I][1] * g12[1] + B[I][2] * g12[2];
+  const T lamC = c1 * DL.lam + c2 * DR.lam, mu2C = (T)2 * (c1 * DL.mu + c2 * DR.mu);
+  T hL[6], hR[6];
+#pragma unroll
+  for (int I = 0; I < 6; ++I) { hL[I] = c1 * cmL[I]; hR[I] = c2 * cmR[I]; }
+  T H12[3][6];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int I = 0; I < 6; ++I) H12[m][I] = c12 * H[m][I];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = I; J < 6; ++J) {
+      T v = B[I][0] * H12[0][J] + B[I][1] * H12[1][J] + B[I][2] * H12[2][J];
+      v -= hL[I] * DL.m[J];
+      v -= hR[I] * DR.m[J];
+      if (I < 3 && J < 3) v += lamC;
+      if (I == J) v += mu2C;
+      out.C[sidx(I, J)] = v;
+    }
+  if (STORE) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) gp[m * gstride] = g[m];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int I = 0; I < 6; ++I) gp[(3 + 6 * m + I) * gstride] = H[m][I];
   }
 }
 
@@ -262,6 +397,7 @@ __device__ __forceinline__ void condense(const double nd[3], double c1d, double 
 // Per-thread views of strided arrays.
 struct PointArrays {
   const double* nrm; size_t ns;  // normals: element (3*node + c) at nrm[(3*node+c)*ns]
+  const float* nrmf;             // FP32 copy of the normals (same indexing; FP32 form only)
   double* a; size_t as;          // jumps: a[(3*j+c)*as], j = node (heap) or the paper's index
   bool paper;                    // jumps stored in the paper's ordering (level K first, root last)
   const double* z; size_t zs;    // leaf state z^n of the inelastic slots: z[(6*slot+c)*zs]
@@ -276,6 +412,19 @@ template <typename T>
 struct GH {
   T* p; size_t s;  // g and H of laminate node: p[(21*node + c)*s], c = 0..2 g, 3..20 H
 };
+
+template <typename T>
+__device__ __forceinline__ void load_n(const PointArrays& P, int node, double nd[3], T n[3]);
+template <>
+__device__ __forceinline__ void load_n<double>(const PointArrays& P, int node, double nd[3], double n[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { nd[c] = P.nrm[(3 * node + c) * P.ns]; n[c] = nd[c]; }
+}
+template <>
+__device__ __forceinline__ void load_n<float>(const PointArrays& P, int node, double nd[3], float n[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { nd[c] = P.nrm[(3 * node + c) * P.ns]; n[c] = P.nrmf[(3 * node + c) * P.ns]; }
+}
 
 __device__ __forceinline__ void load_z(const TreeDev& t, const PointArrays& P, int leaf, int phase, double z[6]) {
   if (t.ph[phase].kind == 1) {
@@ -320,7 +469,9 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
     double eL[6], eR[6];
     for (int lvl = top; lvl <= K; ++lvl) {
       const int node = (1 << (lvl - 1)) + (m >> (K - lvl)) - 1;
-      const double nd[3] = {P.nrm[(3 * node) * P.ns], P.nrm[(3 * node + 1) * P.ns], P.nrm[(3 * node + 2) * P.ns]};
+      double nd[3];
+      T nt[3];
+      load_n<T>(P, node, nd, nt);
       const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
       double* ap = P.a + (size_t)(3 * jump_index(P, K, lvl, node)) * P.as;
       double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
@@ -345,11 +496,12 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
       if (lvl < K) {
         T dR[6];
         if (STORE) {
-          const T nt[3] = {(T)nd[0], (T)nd[1], (T)nd[2]}, ntr[3] = {(T)ndr[0], (T)ndr[1], (T)ndr[2]};
+          const NodeC<T> cc = node_c<T>(t, node);
+          const T ntr[3] = {nt[0] * (T)RS2, nt[1] * (T)RS2, nt[2] * (T)RS2};
           T Nda[6];
           N_apply<T>(nt, ntr, da, Nda);
 #pragma unroll
-          for (int I = 0; I < 6; ++I) { dR[I] = de[I] + (T)c1 * Nda[I]; de[I] = de[I] - (T)c2 * Nda[I]; }
+          for (int I = 0; I < 6; ++I) { dR[I] = de[I] + cc.c1 * Nda[I]; de[I] = de[I] - cc.c2 * Nda[I]; }
         } else {
 #pragma unroll
           for (int I = 0; I < 6; ++I) dR[I] = (T)0;
@@ -358,40 +510,40 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
         for (int I = 0; I < 6; ++I) { epsR[lvl + 1][I] = eR[I]; depsR[lvl + 1][I] = dR[I]; e[I] = eL[I]; }
       }
     }
-    // leaves 2m (phase 1) and 2m + 1 (phase 2)
-    Sub<T> A, B;
+    // leaves 2m (phase 1) and 2m + 1 (phase 2), condensed by their bottom laminate
+    Sub<T> res;
     {
-      double z[6], g;
+      const int node = nbottom + m - 1;
+      double z[6], g, sL[6], sR[6];
+      LeafTan<T> DL, DR;
       load_z(t, P, 2 * m, 0, z);
-      leaf_law<T>(t.ph[0], eL, z, A.sb, A.C, nullptr, gap_min ? &g : nullptr);
+      leaf_iso<T>(t.ph[0], eL, z, sL, &DL, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
-#pragma unroll
-      for (int I = 0; I < 6; ++I) A.ds[I] = (T)0;
       load_z(t, P, 2 * m + 1, 1, z);
-      leaf_law<T>(t.ph[1], eR, z, B.sb, B.C, nullptr, gap_min ? &g : nullptr);
+      leaf_iso<T>(t.ph[1], eR, z, sR, &DR, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
-#pragma unroll
-      for (int I = 0; I < 6; ++I) B.ds[I] = (T)0;
+      double nd[3];
+      T nt[3];
+      load_n<T>(P, node, nd, nt);
+      T* gp = STORE ? gh.p + (size_t)(21 * node) * gh.s : nullptr;
+      condense_bottom<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node),
+                                node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2);
     }
     // condense upwards while the finished laminate is a right child
     int lvl = K, idx = m;
     for (;;) {
-      const int node = (1 << (lvl - 1)) + idx - 1;
-      const double nd[3] = {P.nrm[(3 * node) * P.ns], P.nrm[(3 * node + 1) * P.ns], P.nrm[(3 * node + 2) * P.ns]};
-      Sub<T> res;
-      T* gp = STORE ? gh.p + (size_t)(21 * node) * gh.s : nullptr;
-      condense<T, STORE>(nd, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.W + node), A, B, res, gp,
-                         STORE ? gp + 3 * gh.s : nullptr, gh.s, r2);
       if (lvl == 1) { root = res; break; }
-      if (idx & 1) {
-        A = pend[lvl];
-        B = res;
-        idx >>= 1;
-        --lvl;
-      } else {
-        pend[lvl] = res;
-        break;
-      }
+      if (!(idx & 1)) { pend[lvl] = res; break; }
+      idx >>= 1;
+      --lvl;
+      const int node = (1 << (lvl - 1)) + idx - 1;
+      double nd[3];
+      T nt[3];
+      load_n<T>(P, node, nd, nt);
+      T* gp = STORE ? gh.p + (size_t)(21 * node) * gh.s : nullptr;
+      const Sub<T> B = res;
+      condense<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node), node_c<T>(t, node),
+                         pend[lvl + 1], B, res, gp, gh.s, r2);
     }
   }
 }
@@ -431,7 +583,7 @@ __device__ inline void write_leaf_states(const TreeDev& t, const double Eloc[6],
       const int leaf = 2 * m + side;
       double z[6], zn[6], sig[6];
       load_z(t, P, leaf, side, z);
-      leaf_law<double>(t.ph[side], side ? eR : eL, z, sig, nullptr, zn, nullptr);
+      leaf_iso<double>(t.ph[side], side ? eR : eL, z, sig, nullptr, zn, nullptr);
       const int slot = t.z_both ? leaf : (leaf >> 1);
       double* b = zout + (size_t)(6 * slot) * zos;
 #pragma unroll
