@@ -206,12 +206,36 @@ def rel_rows(a, b):
     return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
 
 
+def tune_shape(form, ctx, args):
+    """Launch shape of the Newton kernel from the autotuner, tuned on the first 2^18 points at the
+    first timed increment (after the warm-up increments)."""
+    import torch
+    from paper_2103_08253_gb300 import autotune, dmn
+    dev = ctx["dev"]
+    m = min(ctx["n"], 1 << 18)
+    A2 = ctx["A2"][:m].contiguous()
+    h = dmn.DMN(ctx["tree"], precision=form)
+    lam, Q = h.interp_orientation(A2)
+    st = torch.zeros((h.state_size, m), dtype=torch.float64, device=dev)
+    for s in range(1, args.warmup + 1):
+        st = h.update(lam, Q, ctx["En"][s - 1][:m].contiguous(), ctx["dE"][s - 1][:m].contiguous(), st)["state_out"]
+    h.close()
+    s = args.warmup + 1
+    res = autotune.tune(ctx["tree"], form, lam, Q, ctx["En"][s - 1][:m].contiguous(),
+                        ctx["dE"][s - 1][:m].contiguous(), st, reps=1)
+    del st
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_form(form, ctx, args, dist):
     """Warm-up increments, then the timed increments; returns timings and the last outputs."""
     import torch
     from paper_2103_08253_gb300 import dmn
     dev, n = ctx["dev"], ctx["n"]
-    m = dmn.DMN(ctx["tree"], precision=form)
+    shape = tune_shape(form, ctx, args) if args.autotune else None
+    m = dmn.DMN(ctx["tree"], precision=form, block=shape["block"] if shape else 0,
+                ctas_per_sm=shape["ctas_per_sm"] if shape else 0)
     S = m.state_size
     st = [torch.zeros((S, n), dtype=torch.float64, device=dev), torch.zeros((S, n), dtype=torch.float64, device=dev)]
     lam = torch.empty((n, 2), dtype=torch.float64, device=dev)
@@ -258,6 +282,8 @@ def run_form(form, ctx, args, dist):
     its = iters_steps.to(torch.int64).sum().item()
     hist = torch.bincount(iters_steps.reshape(-1).to(torch.int64), minlength=1).cpu().numpy()
     res = dict(t_ms=t_ms, kms=kms, updates=cnt, clocks=clk, iters_sum=int(its), iters_hist=hist.tolist(),
+               launch=(dict(block=shape["block"], ctas_per_sm=shape["ctas_per_sm"], tuned_on_points=shape["points"],
+                            table=shape["table"]) if shape else "defaults"),
                stress=out["stress"], tangent=out["tangent"], status=out["status"], state=st[cur],
                host_state=host_state, m=m, lam=lam, Q=Q, S=S, st=st)
     return res
@@ -373,6 +399,8 @@ def main():
     ap.add_argument("--ref-points", type=int, default=1024)
     ap.add_argument("--cpu-points", type=int, default=1024)
     ap.add_argument("--parity-points", type=int, default=16)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use the library's default launch shape instead of autotuning it")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -434,6 +462,7 @@ def run_gpu(args):
                            "kernel_ms_per_step": {k: x / steps for k, x in r["kms"].items()},
                            "newton_iters_per_update": r["iters_sum"] / (n * steps), "iters_hist": r["iters_hist"],
                            "roofline": roofline_f64(r, n, steps) if form == "f64" else roofline_mixed(r, n, steps),
+                           "launch": r["launch"],
                            "parity_vs_oracle": r.get("parity"), "clocks": r["clocks"]}
     main_form = "f64" if "f64" in results else forms[0]
     mr = results[main_form]

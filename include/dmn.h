@@ -89,7 +89,9 @@ typedef struct {
   int32_t max_iter;    /* Newton corrections before status MAXITER; <= 0 selects 50 */
   int32_t precision;   /* DMN_PREC_F64 or DMN_PREC_MIXED */
   int32_t block;       /* threads per CTA of the Newton kernel (multiple of 32); 0 selects 128 */
-  int32_t ctas_per_sm; /* resident CTAs per SM of the persistent Newton kernel; 0 selects 2 */
+  int32_t ctas_per_sm; /* resident CTAs per SM of the persistent Newton kernel; 0 selects 384 threads
+                        * per SM for DMN_PREC_F64 and 512 for DMN_PREC_MIXED;
+                        * block * ctas_per_sm <= 512 (registers are capped to fit) */
 } dmn_options;
 
 /* Create a handle for n_trees DMNs (n_trees = 1 in this version).  Copies the

@@ -1,0 +1,78 @@
+"""Autotuner for the launch shape of the persistent Newton kernel.
+
+The Newton kernel runs one Gauss point per thread; its launch shape is the CTA
+size (points per CTA) and the number of resident CTAs per SM.  The FP64 form is
+bound by the FP64 pipe once each SM holds a few warps, the FP32 form hides
+latency with more resident warps, and both trade occupancy against registers.
+`tune` times every candidate shape on a caller-provided batch through the C ABI
+(per-kernel CUDA events of the Newton kernel) and returns the fastest; results
+are cached per (GPU, SM count, depth, shape functions, phases, precision) in
+`_build/autotune.json` next to this file.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import dmn
+
+CANDIDATES = ((128, 2), (128, 3), (128, 4), (64, 4), (64, 6), (64, 8), (96, 4), (32, 12), (32, 16))
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+def _key(tree, precision, device):
+    import torch
+    p = torch.cuda.get_device_properties(device)
+    kinds = "".join(str(int(ph.kind)) for ph in tree.phases)
+    return "%s|sm%d|K%d|M%d|ph%s|%s" % (p.name, p.multi_processor_count, tree.K, tree.M, kinds, precision)
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cached(tree, precision, device=None):
+    """(block, ctas_per_sm) from the cache, or None."""
+    import torch
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    e = _load().get(_key(tree, precision, device))
+    return (int(e["block"]), int(e["ctas_per_sm"])) if e else None
+
+
+def tune(tree, precision, lam, Q, E_n, dE, state_in, reps=2, candidates=CANDIDATES, save=True):
+    """Time the Newton kernel of every candidate shape on this batch; returns
+    dict(block, ctas_per_sm, newton_ms, table)."""
+    import torch
+    dev = lam.device
+    n = lam.shape[0]
+    table = []
+    for block, cps in candidates:
+        m = dmn.DMN(tree, precision=precision, block=block, ctas_per_sm=cps)
+        out = m.alloc_outputs(n, dev)
+        m.update(lam, Q, E_n, dE, state_in, out=out)
+        torch.cuda.synchronize()
+        m.profile(True)
+        for _ in range(reps):
+            m.update(lam, Q, E_n, dE, state_in, out=out)
+        kms, cnt = m.profile_read()
+        m.profile(False)
+        m.close()
+        del out
+        table.append((block, cps, kms["newton"] / cnt))
+    torch.cuda.empty_cache()
+    block, cps, ms = min(table, key=lambda r: r[2])
+    res = dict(block=block, ctas_per_sm=cps, newton_ms=ms, points=n,
+               table=[dict(block=b, ctas_per_sm=c, newton_ms=t) for b, c, t in table])
+    if save:
+        data = _load()
+        data[_key(tree, precision, dev)] = res
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1)
+        os.replace(tmp, CACHE)
+    return res

@@ -300,8 +300,10 @@ struct NewtonParams {
   int write_outputs;  // FP64 form: stress and tangent (local frame) come from the converged Newton pass
 };
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_newton(NewtonParams<T> P) {
+// MINB: resident CTAs per SM the register allocation is sized for (255, 170 or
+// 128 registers per thread at 2, 3 or 4 CTAs of 128 threads).
+template <typename T, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const TreeDev& t = P.t;
@@ -482,7 +484,7 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   t.S = 6 * t.nz + 3 * N;
 
   dmn_options o;
-  o.tol = 1e-12; o.max_iter = 50; o.precision = DMN_PREC_F64; o.block = 128; o.ctas_per_sm = 2;
+  o.tol = 1e-12; o.max_iter = 50; o.precision = DMN_PREC_F64; o.block = 128; o.ctas_per_sm = 0;
   if (opt) {
     if (opt->tol > 0.0) o.tol = opt->tol;
     if (opt->max_iter > 0) o.max_iter = opt->max_iter;
@@ -490,11 +492,15 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     if (opt->block > 0) o.block = opt->block;
     if (opt->ctas_per_sm > 0) o.ctas_per_sm = opt->ctas_per_sm;
   }
+  // default occupancy: the FP64 form is bound by the FP64 pipe from 256 threads per SM on;
+  // the FP32 form hides latency with 512
+  if (o.ctas_per_sm <= 0) o.ctas_per_sm = (o.precision == DMN_PREC_MIXED ? 512 : 384) / o.block;
   if (o.precision != DMN_PREC_F64 && o.precision != DMN_PREC_MIXED)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: unknown precision");
   if (o.block % 32 != 0 || o.block > 128)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: block must be a multiple of 32 and at most 128");
-  if (o.ctas_per_sm > 16) return fail(nullptr, DMN_ERR_ARG, "dmn_create: ctas_per_sm must be at most 16");
+  if (o.block * o.ctas_per_sm > 512)
+    return fail(nullptr, DMN_ERR_ARG, "dmn_create: block * ctas_per_sm must be at most 512 threads per SM");
 
   dmn_handle* h = new dmn_handle();
   h->tree = t;
@@ -629,14 +635,20 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
   if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: counter reset");
   const unsigned grid = (unsigned)(h->n_sm * h->opt.ctas_per_sm);
   const bool mixed = h->opt.precision == DMN_PREC_MIXED;
+  const int threads_per_sm = h->opt.block * h->opt.ctas_per_sm;
+  const int minb = threads_per_sm > 384 ? 4 : threads_per_sm > 256 ? 3 : 2;
   if (!mixed) {
     NewtonParams<double> P{td, n, h->nslots, state_in, state_out, stress, tangent, iters, status,
                            h->nbuf, h->scr_d, (double*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 1};
-    k_newton<double><<<grid, h->opt.block, 0, s>>>(P);
+    if (minb == 2) k_newton<double, 2><<<grid, h->opt.block, 0, s>>>(P);
+    else if (minb == 3) k_newton<double, 3><<<grid, h->opt.block, 0, s>>>(P);
+    else k_newton<double, 4><<<grid, h->opt.block, 0, s>>>(P);
   } else {
     NewtonParams<float> P{td, n, h->nslots, state_in, state_out, stress, tangent, iters, status,
                           h->nbuf, h->scr_d, (float*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 0};
-    k_newton<float><<<grid, h->opt.block, 0, s>>>(P);
+    if (minb == 2) k_newton<float, 2><<<grid, h->opt.block, 0, s>>>(P);
+    else if (minb == 3) k_newton<float, 3><<<grid, h->opt.block, 0, s>>>(P);
+    else k_newton<float, 4><<<grid, h->opt.block, 0, s>>>(P);
   }
   if (ev) cudaEventRecord(ev[2], s);
   FinalParams F{td, n, Q, state_in, state_out, stress, tangent, status, h->nbuf};

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 
 from . import build as _build
 
@@ -134,8 +135,7 @@ class DMN:
     def __del__(self):
         # at interpreter exit the CUDA runtime may already be torn down; the
         # process releases the device memory anyway
-        import sys
-        if sys.is_finalizing():
+        if sys is None or sys.is_finalizing():
             return
         try:
             self.close()

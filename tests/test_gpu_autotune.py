@@ -1,0 +1,34 @@
+"""The autotuner times candidate launch shapes through the C ABI and caches the fastest."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2103_08253_gb300 import autotune, dmn, workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def test_autotune_picks_a_candidate_and_caches_it(tmp_path, monkeypatch):
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
+    K, n = 5, 4096
+    tree = W.tree_d10_fit(K, seed=3)
+    A2, lam, Q = W.orientation_field(n, seed=4)
+    Ef = W.random6_path_final(n, 0.03, seed=5)
+    En, dE = W.proportional_increment(Ef, 10, 20)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+    st = torch.zeros((W.state_size(K), n), dtype=torch.float64, device=DEV)
+    cands = ((128, 2), (64, 4))
+    res = autotune.tune(tree, "mixed", d(lam), d(Q), d(En), d(dE), st, reps=1, candidates=cands)
+    assert (res["block"], res["ctas_per_sm"]) in cands
+    assert len(res["table"]) == 2 and all(r["newton_ms"] > 0 for r in res["table"])
+    assert autotune.cached(tree, "mixed", DEV) == (res["block"], res["ctas_per_sm"])
+    data = json.load(open(autotune.CACHE))
+    assert len(data) == 1
+    # a tuned handle computes the same result as a default one, bit for bit
+    a = dmn.DMN(tree, precision="f64").update(d(lam), d(Q), d(En), d(dE), st)
+    b = dmn.DMN(tree, precision="f64", block=64, ctas_per_sm=6).update(d(lam), d(Q), d(En), d(dE), st)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
