@@ -66,7 +66,10 @@ enum { DMN_PHASE_ELASTIC = 0, DMN_PHASE_J2_LINEAR = 1 };
 enum { DMN_PREC_F64 = 0, DMN_PREC_MIXED = 1 };
 
 /* per-point status */
-enum { DMN_STATUS_OK = 0, DMN_STATUS_MAXITER = 1, DMN_STATUS_NONFINITE = 2 };
+enum { DMN_STATUS_OK = 0, DMN_STATUS_MAXITER = 1, DMN_STATUS_NONFINITE = 2, DMN_STATUS_BAD_TREE = 4 };
+
+/* trees per handle */
+enum { DMN_MAX_TREES = 8 };
 
 typedef struct {
   int32_t kind;    /* DMN_PHASE_* */
@@ -94,13 +97,15 @@ typedef struct {
                         * block * ctas_per_sm <= 512 (registers are capped to fit) */
 } dmn_options;
 
-/* Create a handle for n_trees DMNs (n_trees = 1 in this version).  Copies the
- * parameters to the device, propagates the leaf weights to the laminate
- * volume fractions (Sec. 2.1) and allocates the work space of the persistent
- * Newton kernel on the current CUDA device.  opt may be NULL (defaults).
- * Errors: DMN_ERR_ARG for K outside 1..8, M not in {3,4,6}, a weight <= 0 or
- * non-finite, an unknown phase kind or non-positive moduli; DMN_ERR_CUDA if
- * an allocation fails.  On error *out is NULL. */
+/* Create a handle for n_trees DMNs (1 <= n_trees <= DMN_MAX_TREES; trees may
+ * differ in depth, shape functions, weights and phases, e.g. a batch mixing
+ * depths 5 to 8).  Copies the parameters to the device, propagates the leaf
+ * weights to the laminate volume fractions (Sec. 2.1) and allocates the work
+ * space of the persistent Newton kernel on the current CUDA device.  opt may
+ * be NULL (defaults).  Errors: DMN_ERR_ARG for n_trees out of range, K outside
+ * 1..8, M not in {3,4,6}, a weight <= 0 or non-finite, an unknown phase kind
+ * or non-positive moduli; DMN_ERR_CUDA if an allocation fails.  On error *out
+ * is NULL. */
 int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* opt, dmn_handle** out);
 
 /* Free the handle and its device memory (synchronises the device).  NULL is a no-op. */
@@ -108,7 +113,10 @@ void dmn_destroy(dmn_handle* h);
 
 /* Doubles of state per point for tree tree_id: 6 per inelastic leaf plus
  * 3 per laminate (1533 for K = 8 with one inelastic phase; the paper counts
- * the same 128 x (1 + 5) + 255 x 3 scalars, Sec. 4.7).  -1 on a bad argument. */
+ * the same 128 x (1 + 5) + 255 x 3 scalars, Sec. 4.7).  tree_id = -1 gives
+ * the maximum over the handle's trees: the number of fields S of the state
+ * arrays passed to dmn_update (a point of tree t uses the first
+ * dmn_state_size(h, t) of them).  -1 on a bad argument. */
 int64_t dmn_state_size(const dmn_handle* h, int32_t tree_id);
 
 /* Orientation set-up (Sec. 2.2, Eq. of the eigen decomposition of A2):
@@ -132,11 +140,17 @@ int dmn_interp_orientation(dmn_handle* h, int64_t n, const double* A2, double* l
  *   iters    dev [n]      Newton corrections applied
  *   status   dev [n]      DMN_STATUS_*; NONFINITE writes NaN to stress,
  *                          tangent and the point's state_out
- * tree_id must be NULL (one tree).  The Newton iteration starts from a^n
- * (Sec. 4.7) and stops when the criterion of Sec. 4.6 holds.  The first call
- * with a larger n than any earlier call allocates per-point work space
- * (cudaMalloc, synchronous).  Errors: DMN_ERR_ARG for n < 0, NULL arrays with
- * n > 0, state_in == state_out, a non-NULL tree_id. */
+ *   tree_id  dev [n]      tree of each point (0 .. n_trees-1), or NULL for
+ *                          tree 0 everywhere; a point with another value gets
+ *                          status BAD_TREE, NaN stress and tangent, and its
+ *                          state_out is left untouched
+ * With several trees the points are first sorted by tree on the device so
+ * that the lanes of a warp walk the same tree.  The Newton iteration starts
+ * from a^n (Sec. 4.7) and stops when the criterion of Sec. 4.6 holds.  The
+ * first call with a larger n than any earlier call allocates per-point work
+ * space (cudaMalloc, synchronous); calls with at most that n allocate nothing
+ * and may be captured in a CUDA graph.  Errors: DMN_ERR_ARG for n < 0, NULL
+ * arrays with n > 0, state_in == state_out. */
 int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam, const double* Q,
                const double* E_n, const double* dE, const double* state_in, double* state_out, double* stress,
                double* tangent, int32_t* iters, int32_t* status, void* stream);

@@ -15,6 +15,7 @@
 //              sweep that yields them.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstdio>
@@ -44,14 +45,17 @@ struct Tree {
 }  // namespace
 
 struct dmn_handle {
-  Tree tree;
+  std::vector<Tree> trees;
+  int N_max = 0;                // laminates of the deepest tree
+  int64_t S_max = 0;            // state fields of the largest tree
   dmn_options opt;
   int device = 0, n_sm = 0;
   int64_t nslots = 0;
   double* scr_d = nullptr;      // per slot: normals [3N] + jumps [3N] (FP64)
   void* scr_t = nullptr;        // per slot: g, H [21N] (FP64 or FP32) + FP32 normals [3N]
-  unsigned long long* counter = nullptr;
+  unsigned long long* counter = nullptr;  // [0] work counter, [1..9] points per tree, [10..18] cursors
   double* nbuf = nullptr;       // per point: normals [3N] + local macro strain [6], field-major
+  int64_t* perm = nullptr;      // points sorted by tree (several trees)
   int64_t nbuf_cap = 0;
   bool profiling = false;
   std::vector<std::array<cudaEvent_t, 4>> events;  // per timed update: before/after each kernel
@@ -236,16 +240,72 @@ __device__ __forceinline__ void local_strain(const double* Q, const double* En, 
   }
 }
 
+// All trees of a handle, passed by value to the kernels.
+struct Forest {
+  TreeDev t[DMN_MAX_TREES];
+  int n;
+};
+
+// point handled by thread/work item i and its tree (n_trees = invalid)
+__device__ __forceinline__ void point_of(const int64_t* perm, const int32_t* tid, int n_trees, int64_t i,
+                                         int64_t& p, int& tree) {
+  p = perm ? perm[i] : i;
+  const int t = tid ? tid[p] : 0;
+  tree = (t >= 0 && t < n_trees) ? t : n_trees;
+}
+
+// Sorting points by tree (several trees): count per tree, exclusive offsets,
+// scatter.  Lanes of a warp with the same tree share one atomic.  The order
+// inside a tree is not deterministic; results do not depend on it.
+__global__ void k_tree_count(int64_t n, const int32_t* __restrict__ tid, int n_trees, unsigned long long* cnt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int b = -1;
+  if (i < n) {
+    const int t = tid[i];
+    b = (t >= 0 && t < n_trees) ? t : n_trees;
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, b);
+  if (b >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + b, (unsigned long long)__popc(peers));
+}
+
+__global__ void k_tree_offsets(int n_trees, const unsigned long long* cnt, unsigned long long* cursor) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  unsigned long long s = 0;
+  for (int b = 0; b <= n_trees; ++b) { cursor[b] = s; s += cnt[b]; }
+}
+
+__global__ void k_tree_scatter(int64_t n, const int32_t* __restrict__ tid, int n_trees, unsigned long long* cursor,
+                               int64_t* __restrict__ perm) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int b = -1;
+  if (i < n) {
+    const int t = tid[i];
+    b = (t >= 0 && t < n_trees) ? t : n_trees;
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, b);
+  const int leader = __ffs(peers) - 1;
+  unsigned long long base = 0;
+  if (b >= 0 && lane == leader) base = atomicAdd(cursor + b, (unsigned long long)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  if (b >= 0) perm[base + __popc(peers & ((1u << lane) - 1u))] = i;
+}
+
 // per point: normals and the macro strain in the principal frame
-__global__ void k_prepare(TreeDev t, int64_t n, const double* __restrict__ lam, const double* __restrict__ Q,
-                          const double* __restrict__ En, const double* __restrict__ dE, double* __restrict__ nbuf) {
+__global__ void k_prepare(Forest F, int64_t n, const int32_t* __restrict__ tid, const int64_t* __restrict__ perm,
+                          const double* __restrict__ lam, const double* __restrict__ Q, const double* __restrict__ En,
+                          const double* __restrict__ dE, double* __restrict__ nbuf, int N_max) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  point_normals(t, lam[2 * i], lam[2 * i + 1], nbuf + i, (size_t)n);
+  int64_t p;
+  int tr;
+  point_of(perm, tid, F.n, i, p, tr);
+  if (tr >= F.n) return;
+  point_normals(F.t[tr], lam[2 * p], lam[2 * p + 1], nbuf + p, (size_t)n);
   double E[6];
-  local_strain(Q + 9 * i, En + 6 * i, dE + 6 * i, E);
+  local_strain(Q + 9 * p, En + 6 * p, dE + 6 * p, E);
 #pragma unroll
-  for (int I = 0; I < 6; ++I) nbuf[(size_t)(3 * t.N + I) * n + i] = E[I];
+  for (int I = 0; I < 6; ++I) nbuf[(size_t)(3 * N_max + I) * n + p] = E[I];
 }
 
 template <typename T>
@@ -286,8 +346,11 @@ __device__ __forceinline__ void write_stress_tangent(const double* Q, const doub
 
 template <typename T>
 struct NewtonParams {
-  TreeDev t;
+  Forest F;
   int64_t n, nslots;
+  int N_max;
+  const int32_t* tid;
+  const int64_t* perm;
   const double* state_in;
   double *state_out, *stress, *tangent;
   int32_t *iters, *status;
@@ -306,19 +369,19 @@ template <typename T, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const TreeDev& t = P.t;
-  const int N = t.N;
+  const int NM = P.N_max;
   double* my_nrm = P.scr_d + slot;
-  float* my_nrmf = (float*)(P.scr_t + (size_t)(21 * N) * P.nslots) + slot;
+  float* my_nrmf = (float*)(P.scr_t + (size_t)(21 * NM) * P.nslots) + slot;
   PointArrays A;
   A.nrm = my_nrm; A.ns = (size_t)P.nslots;
   A.nrmf = my_nrmf;
-  A.a = P.scr_d + (size_t)(3 * N) * P.nslots + slot; A.as = (size_t)P.nslots;
+  A.a = P.scr_d + (size_t)(3 * NM) * P.nslots + slot; A.as = (size_t)P.nslots;
   A.paper = false;
   A.z = nullptr; A.zs = (size_t)P.n;
   GH<T> gh{P.scr_t + slot, (size_t)P.nslots};
-  const int nzf = 6 * t.nz;
-  int64_t pt = -1;
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  int64_t pt = -1;   // point of this lane; -1: needs work; >= n: no work left
+  int tr = 0;        // its tree
   int it = 0;
   double Eloc[6];
   for (;;) {
@@ -330,28 +393,45 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
       if (lane == leader) base = atomicAdd(P.counter, (unsigned long long)__popc(mask));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
-        pt = (int64_t)(base + __popc(mask & ((1u << lane) - 1u)));
-        if (pt < P.n) {
+        const int64_t i = (int64_t)(base + __popc(mask & ((1u << lane) - 1u)));
+        if (i >= P.n) {
+          pt = P.n;
+        } else {
+          point_of(P.perm, P.tid, P.F.n, i, pt, tr);
+          if (tr >= P.F.n) {      // unknown tree: report and take the next point
+            P.iters[pt] = 0;
+            P.status[pt] = DMN_STATUS_BAD_TREE;
+            for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
+            for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
+            pt = -1;
+          } else {
+            const TreeDev& t = P.F.t[tr];
+            const int nzf = 6 * t.nz;
 #pragma unroll
-          for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * N + I) * P.n + pt];
-          for (int f = 0; f < 3 * N; ++f) {
-            const int node = f / 3, c = f - 3 * node;
-            // heap node -> paper index of its jumps
-            const int lvl = 32 - __clz(node + 1);
-            const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
-            A.a[(size_t)f * A.as] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
-            const double nv = P.nbuf[(size_t)f * P.n + pt];
-            my_nrm[(size_t)f * A.ns] = nv;
-            if (sizeof(T) == 4) my_nrmf[(size_t)f * A.ns] = (float)nv;
+            for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * NM + I) * P.n + pt];
+            for (int f = 0; f < 3 * t.N; ++f) {
+              const int node = f / 3, c = f - 3 * node;
+              // heap node -> paper index of its jumps
+              const int lvl = 32 - __clz(node + 1);
+              const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+              A.a[(size_t)f * A.as] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
+              const double nv = P.nbuf[(size_t)f * P.n + pt];
+              my_nrm[(size_t)f * A.ns] = nv;
+              if (sizeof(T) == 4) my_nrmf[(size_t)f * A.ns] = (float)nv;
+            }
+            A.z = P.state_in + pt;
+            it = 0;
           }
-          A.z = P.state_in + pt;
-          it = 0;
         }
       }
     }
     const bool active = pt >= 0 && pt < P.n;
-    if (!__any_sync(0xffffffffu, active)) break;
+    if (!__any_sync(0xffffffffu, active)) {
+      if (!__any_sync(0xffffffffu, pt < 0)) break;
+      continue;
+    }
     if (!active) continue;
+    const TreeDev& t = P.F.t[tr];
     Sub<T> root;
     double r2;
     tree_pass<T, true>(t, Eloc, A, gh, it > 0, root, r2, nullptr);
@@ -362,13 +442,13 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
     const double sn = sqrt(sn2);
     int st = -1;
     if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
-    else if (rn <= P.tol * (double)N * sn) st = DMN_STATUS_OK;
+    else if (rn <= P.tol * (double)t.N * sn) st = DMN_STATUS_OK;
     else if (it >= P.max_iter) st = DMN_STATUS_MAXITER;
     if (st < 0) { ++it; continue; }
     // finished point: jumps (paper ordering), counters, and in the FP64 form the
     // local-frame stress and packed tangent for k_final to rotate
-    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-    for (int f = 0; f < 3 * N; ++f) {
+    const int nzf = 6 * t.nz;
+    for (int f = 0; f < 3 * t.N; ++f) {
       const int node = f / 3, c = f - 3 * node;
       const int lvl = 32 - __clz(node + 1);
       const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
@@ -387,8 +467,11 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
 }
 
 struct FinalParams {
-  TreeDev t;
+  Forest F;
   int64_t n;
+  int N_max;
+  const int32_t* tid;
+  const int64_t* perm;
   const double *Q, *state_in;
   double *state_out, *stress, *tangent;
   const int32_t* status;
@@ -397,13 +480,17 @@ struct FinalParams {
 
 template <bool SWEEP>
 __global__ void __launch_bounds__(128) k_final(FinalParams P) {
-  const int64_t pt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (pt >= P.n) return;
-  const TreeDev& t = P.t;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= P.n) return;
+  int64_t pt;
+  int tr;
+  point_of(P.perm, P.tid, P.F.n, i, pt, tr);
+  if (tr >= P.F.n) return;  // unknown tree: reported by the Newton kernel
+  const TreeDev& t = P.F.t[tr];
   const int st = P.status[pt];
   double Eloc[6];
 #pragma unroll
-  for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * t.N + I) * P.n + pt];
+  for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * P.N_max + I) * P.n + pt];
   PointArrays A;
   A.nrm = P.nbuf + pt; A.ns = (size_t)P.n;
   A.nrmf = nullptr;
@@ -467,21 +554,28 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   if (!out) return fail(nullptr, DMN_ERR_ARG, "dmn_create: out is NULL");
   *out = nullptr;
   g_create_error.clear();
-  if (!trees || n_trees != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: exactly one tree is supported");
-  const dmn_tree_desc& d = trees[0];
-  if (const char* m = check_tree(d)) return fail(nullptr, DMN_ERR_ARG, std::string("dmn_create: ") + m);
-  const int K = d.K, M = d.M, N = (1 << K) - 1, L = 1 << K;
-  Tree t;
-  t.K = K; t.M = M; t.N = N; t.L = L;
-  int n_inel_phase = 0;
-  for (int f = 0; f < 2; ++f) {
-    if (const char* m = make_phase(d.phase[f], t.ph[f]))
-      return fail(nullptr, DMN_ERR_ARG, std::string("dmn_create: ") + m);
-    n_inel_phase += d.phase[f].kind == DMN_PHASE_J2_LINEAR;
+  if (!trees || n_trees < 1 || n_trees > DMN_MAX_TREES)
+    return fail(nullptr, DMN_ERR_ARG, "dmn_create: n_trees must be in 1..8 and trees non-NULL");
+  std::vector<Tree> tv(n_trees);
+  int N_max = 0;
+  int64_t S_max = 0;
+  for (int k = 0; k < n_trees; ++k) {
+    const dmn_tree_desc& d = trees[k];
+    if (const char* m = check_tree(d)) return fail(nullptr, DMN_ERR_ARG, std::string("dmn_create: ") + m);
+    Tree& t = tv[k];
+    t.K = d.K; t.M = d.M; t.N = (1 << d.K) - 1; t.L = 1 << d.K;
+    int n_inel_phase = 0;
+    for (int f = 0; f < 2; ++f) {
+      if (const char* m = make_phase(d.phase[f], t.ph[f]))
+        return fail(nullptr, DMN_ERR_ARG, std::string("dmn_create: ") + m);
+      n_inel_phase += d.phase[f].kind == DMN_PHASE_J2_LINEAR;
+    }
+    t.z_both = n_inel_phase == 2;
+    t.nz = n_inel_phase * (t.L / 2);
+    t.S = 6 * t.nz + 3 * t.N;
+    N_max = std::max(N_max, t.N);
+    S_max = std::max<int64_t>(S_max, t.S);
   }
-  t.z_both = n_inel_phase == 2;
-  t.nz = n_inel_phase * (L / 2);
-  t.S = 6 * t.nz + 3 * N;
 
   dmn_options o;
   o.tol = 1e-12; o.max_iter = 50; o.precision = DMN_PREC_F64; o.block = 128; o.ctas_per_sm = 0;
@@ -492,45 +586,51 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     if (opt->block > 0) o.block = opt->block;
     if (opt->ctas_per_sm > 0) o.ctas_per_sm = opt->ctas_per_sm;
   }
-  // default occupancy: the FP64 form is bound by the FP64 pipe from 256 threads per SM on;
-  // the FP32 form hides latency with 512
-  if (o.ctas_per_sm <= 0) o.ctas_per_sm = (o.precision == DMN_PREC_MIXED ? 512 : 384) / o.block;
   if (o.precision != DMN_PREC_F64 && o.precision != DMN_PREC_MIXED)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: unknown precision");
   if (o.block % 32 != 0 || o.block > 128)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: block must be a multiple of 32 and at most 128");
+  // default occupancy: the FP64 form is bound by the FP64 pipe from 256 threads per SM on;
+  // the FP32 form hides latency with 512
+  if (o.ctas_per_sm <= 0) o.ctas_per_sm = (o.precision == DMN_PREC_MIXED ? 512 : 384) / o.block;
   if (o.block * o.ctas_per_sm > 512)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: block * ctas_per_sm must be at most 512 threads per SM");
 
   dmn_handle* h = new dmn_handle();
-  h->tree = t;
+  h->trees = tv;
+  h->N_max = N_max;
+  h->S_max = S_max;
   h->opt = o;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) { delete h; return cuda_fail(nullptr, e, "dmn_create: device query"); }
 
-  std::vector<double> ph(N * M), qh(N * M);
-  heap_params(d, ph.data(), qh.data());
   double* d_w = nullptr;
-  Tree& T = h->tree;
-  e = cudaMalloc(&T.d_p, sizeof(double) * N * M);
-  if (e == cudaSuccess) e = cudaMalloc(&T.d_q, sizeof(double) * N * M);
-  if (e == cudaSuccess) e = cudaMalloc(&T.d_c, sizeof(double) * 3 * N);
-  if (e == cudaSuccess) e = cudaMalloc(&T.d_cf, sizeof(float) * 3 * N);
-  if (e == cudaSuccess) e = cudaMalloc(&d_w, sizeof(double) * L);
-  if (e == cudaSuccess) e = cudaMemcpy(T.d_p, ph.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(T.d_q, qh.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_w, d.w, sizeof(double) * L, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
-    k_setup_tree<<<1, 1>>>(K, d_w, T.d_c, T.d_cf);
-    e = cudaGetLastError();
+  e = cudaMalloc(&d_w, sizeof(double) * (1 << KMAX));
+  for (int k = 0; k < n_trees && e == cudaSuccess; ++k) {
+    const dmn_tree_desc& d = trees[k];
+    Tree& T = h->trees[k];
+    const int N = T.N, M = T.M, L = T.L;
+    std::vector<double> ph(N * M), qh(N * M);
+    heap_params(d, ph.data(), qh.data());
+    e = cudaMalloc(&T.d_p, sizeof(double) * N * M);
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_q, sizeof(double) * N * M);
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_c, sizeof(double) * 3 * N);
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_cf, sizeof(float) * 3 * N);
+    if (e == cudaSuccess) e = cudaMemcpy(T.d_p, ph.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(T.d_q, qh.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_w, d.w, sizeof(double) * L, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      k_setup_tree<<<1, 1>>>(T.K, d_w, T.d_c, T.d_cf);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(d_w);
   h->nslots = (int64_t)h->n_sm * o.ctas_per_sm * o.block;
-  if (e == cudaSuccess) e = cudaMalloc(&h->scr_d, sizeof(double) * (size_t)(6 * N) * h->nslots);
-  if (e == cudaSuccess) e = cudaMalloc(&h->scr_t, sizeof(double) * (size_t)(24 * N) * h->nslots);
-  if (e == cudaSuccess) e = cudaMalloc(&h->counter, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->scr_d, sizeof(double) * (size_t)(6 * N_max) * h->nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&h->scr_t, sizeof(double) * (size_t)(24 * N_max) * h->nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&h->counter, sizeof(unsigned long long) * 32);
   if (e != cudaSuccess) {
     dmn_destroy(h);
     return cuda_fail(nullptr, e, "dmn_create");
@@ -544,14 +644,16 @@ void dmn_destroy(dmn_handle* h) {
   cudaDeviceSynchronize();
   for (auto& a : h->events)
     for (auto& x : a) cudaEventDestroy(x);
-  cudaFree(h->tree.d_p); cudaFree(h->tree.d_q); cudaFree(h->tree.d_c); cudaFree(h->tree.d_cf);
-  cudaFree(h->scr_d); cudaFree(h->scr_t); cudaFree(h->counter); cudaFree(h->nbuf);
+  for (auto& t : h->trees) { cudaFree(t.d_p); cudaFree(t.d_q); cudaFree(t.d_c); cudaFree(t.d_cf); }
+  cudaFree(h->scr_d); cudaFree(h->scr_t); cudaFree(h->counter); cudaFree(h->nbuf); cudaFree(h->perm);
   delete h;
 }
 
 int64_t dmn_state_size(const dmn_handle* h, int32_t tree_id) {
-  if (!h || tree_id != 0) return -1;
-  return h->tree.S;
+  if (!h) return -1;
+  if (tree_id == -1) return h->S_max;
+  if (tree_id < 0 || tree_id >= (int)h->trees.size()) return -1;
+  return h->trees[tree_id].S;
 }
 
 int dmn_profile_enable(dmn_handle* h, int32_t enable) {
@@ -598,22 +700,28 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
                double* tangent, int32_t* iters, int32_t* status, void* stream) {
   if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_update: NULL handle");
   if (n < 0) return fail(h, DMN_ERR_ARG, "dmn_update: n < 0");
-  if (tree_id) return fail(h, DMN_ERR_ARG, "dmn_update: tree_id must be NULL (one tree)");
   if (n == 0) return DMN_OK;
   if (!lam || !Q || !E_n || !dE || !state_in || !state_out || !stress || !tangent || !iters || !status)
     return fail(h, DMN_ERR_ARG, "dmn_update: NULL array");
   if (state_in == state_out) return fail(h, DMN_ERR_ARG, "dmn_update: state_in and state_out must differ");
-  const Tree& t = h->tree;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
+  const int NM = h->N_max;
+  const bool sort = tree_id && h->trees.size() > 1;
   if (n > h->nbuf_cap) {
     e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) { cudaFree(h->nbuf); h->nbuf = nullptr; h->nbuf_cap = 0; }
-    if (e == cudaSuccess) e = cudaMalloc(&h->nbuf, sizeof(double) * (size_t)(3 * t.N + 6) * n);
+    if (e == cudaSuccess) {
+      cudaFree(h->nbuf); cudaFree(h->perm);
+      h->nbuf = nullptr; h->perm = nullptr; h->nbuf_cap = 0;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->nbuf, sizeof(double) * (size_t)(3 * NM + 6) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&h->perm, sizeof(int64_t) * (size_t)n);
     if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: per-point buffer");
     h->nbuf_cap = n;
   }
-  const TreeDev td = tree_dev(t);
+  Forest F;
+  F.n = (int)h->trees.size();
+  for (int k = 0; k < F.n; ++k) F.t[k] = tree_dev(h->trees[k]);
   const unsigned g1 = (unsigned)div_up(n, 128);
   cudaEvent_t* ev = nullptr;
   if (h->profiling) {
@@ -628,32 +736,39 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
     ev = h->events[h->events_used++].data();
     cudaEventRecord(ev[0], s);
   }
-  k_prepare<<<g1, 128, 0, s>>>(td, n, lam, Q, E_n, dE, h->nbuf);
-  if (ev) cudaEventRecord(ev[1], s);
-  // the Newton interval includes the counter reset (a few hundred ns)
-  e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned long long), s);
+  // counters: [0] work, [1..9] points per tree, [10..18] cursors
+  e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned long long) * 32, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: counter reset");
+  const int64_t* perm = nullptr;
+  if (sort) {
+    k_tree_count<<<g1, 128, 0, s>>>(n, tree_id, F.n, h->counter + 1);
+    k_tree_offsets<<<1, 1, 0, s>>>(F.n, h->counter + 1, h->counter + 10);
+    k_tree_scatter<<<g1, 128, 0, s>>>(n, tree_id, F.n, h->counter + 10, h->perm);
+    perm = h->perm;
+  }
+  k_prepare<<<g1, 128, 0, s>>>(F, n, tree_id, perm, lam, Q, E_n, dE, h->nbuf, NM);
+  if (ev) cudaEventRecord(ev[1], s);
   const unsigned grid = (unsigned)(h->n_sm * h->opt.ctas_per_sm);
   const bool mixed = h->opt.precision == DMN_PREC_MIXED;
   const int threads_per_sm = h->opt.block * h->opt.ctas_per_sm;
   const int minb = threads_per_sm > 384 ? 4 : threads_per_sm > 256 ? 3 : 2;
   if (!mixed) {
-    NewtonParams<double> P{td, n, h->nslots, state_in, state_out, stress, tangent, iters, status,
+    NewtonParams<double> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                            h->nbuf, h->scr_d, (double*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 1};
     if (minb == 2) k_newton<double, 2><<<grid, h->opt.block, 0, s>>>(P);
     else if (minb == 3) k_newton<double, 3><<<grid, h->opt.block, 0, s>>>(P);
     else k_newton<double, 4><<<grid, h->opt.block, 0, s>>>(P);
   } else {
-    NewtonParams<float> P{td, n, h->nslots, state_in, state_out, stress, tangent, iters, status,
+    NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                           h->nbuf, h->scr_d, (float*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 0};
     if (minb == 2) k_newton<float, 2><<<grid, h->opt.block, 0, s>>>(P);
     else if (minb == 3) k_newton<float, 3><<<grid, h->opt.block, 0, s>>>(P);
     else k_newton<float, 4><<<grid, h->opt.block, 0, s>>>(P);
   }
   if (ev) cudaEventRecord(ev[2], s);
-  FinalParams F{td, n, Q, state_in, state_out, stress, tangent, status, h->nbuf};
-  if (mixed) k_final<true><<<g1, 128, 0, s>>>(F);
-  else k_final<false><<<g1, 128, 0, s>>>(F);
+  FinalParams FP{F, n, NM, tree_id, perm, Q, state_in, state_out, stress, tangent, status, h->nbuf};
+  if (mixed) k_final<true><<<g1, 128, 0, s>>>(FP);
+  else k_final<false><<<g1, 128, 0, s>>>(FP);
   if (ev) cudaEventRecord(ev[3], s);
   e = cudaGetLastError();
   return e == cudaSuccess ? DMN_OK : cuda_fail(h, e, "dmn_update: launch");

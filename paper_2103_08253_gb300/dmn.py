@@ -21,7 +21,8 @@ EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_interp_orientatio
 
 PREC_F64 = 0
 PREC_MIXED = 1
-STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE = 0, 1, 2
+STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE, STATUS_BAD_TREE = 0, 1, 2, 4
+MAX_TREES = 8
 
 
 class Phase_(ctypes.Structure):
@@ -94,38 +95,44 @@ def _check_dev(name, t, dtype, shape):
 
 
 class DMN:
-    """A DMN on the current CUDA device.
+    """One or several DMNs (up to 8, e.g. of different depths) on the current CUDA device.
 
-    tree: object with K, M, p [N, M], q [N, M], w [2^K] (numpy, paper
-    ordering) and phases (two objects with kind, E, nu, sigma0, H)."""
+    tree: an object with K, M, p [N, M], q [N, M], w [2^K] (numpy, paper
+    ordering) and phases (two objects with kind, E, nu, sigma0, H), or a list
+    of such objects (tree i is selected by tree_id == i in update())."""
 
     def __init__(self, tree, precision: str = "f64", tol: float = 1e-12, max_iter: int = 50, block: int = 0,
                  ctas_per_sm: int = 0):
         import numpy as np
         self._lib = load_library()
-        self.K, self.M = int(tree.K), int(tree.M)
-        self._p = np.ascontiguousarray(tree.p, dtype=np.float64).reshape(-1)
-        self._q = np.ascontiguousarray(tree.q, dtype=np.float64).reshape(-1)
-        self._w = np.ascontiguousarray(tree.w, dtype=np.float64).reshape(-1)
+        trees = list(tree) if isinstance(tree, (list, tuple)) else [tree]
+        self.n_trees = len(trees)
+        self.K, self.M = int(trees[0].K), int(trees[0].M)
         dp = ctypes.POINTER(ctypes.c_double)
-        desc = TreeDesc_()
-        desc.K, desc.M = self.K, self.M
-        desc.p = self._p.ctypes.data_as(dp)
-        desc.q = self._q.ctypes.data_as(dp)
-        desc.w = self._w.ctypes.data_as(dp)
-        for f, ph in enumerate(tree.phases):
-            desc.phase[f] = Phase_(int(ph.kind), float(ph.E), float(ph.nu), float(ph.sigma0), float(ph.H))
-        opt = Options_(float(tol), int(max_iter), PREC_MIXED if precision == "mixed" else PREC_F64, int(block),
-                       int(ctas_per_sm))
+        descs = (TreeDesc_ * len(trees))()
+        self._keep = []
+        for k, tr in enumerate(trees):
+            p = np.ascontiguousarray(tr.p, dtype=np.float64).reshape(-1)
+            q = np.ascontiguousarray(tr.q, dtype=np.float64).reshape(-1)
+            w = np.ascontiguousarray(tr.w, dtype=np.float64).reshape(-1)
+            self._keep += [p, q, w]
+            descs[k].K, descs[k].M = int(tr.K), int(tr.M)
+            descs[k].p, descs[k].q, descs[k].w = p.ctypes.data_as(dp), q.ctypes.data_as(dp), w.ctypes.data_as(dp)
+            for f, ph in enumerate(tr.phases):
+                descs[k].phase[f] = Phase_(int(ph.kind), float(ph.E), float(ph.nu), float(ph.sigma0), float(ph.H))
         if precision not in ("f64", "mixed"):
             raise ValueError("precision must be 'f64' or 'mixed'")
+        opt = Options_(float(tol), int(max_iter), PREC_MIXED if precision == "mixed" else PREC_F64, int(block),
+                       int(ctas_per_sm))
         self.precision = precision
         h = ctypes.c_void_p()
-        rc = self._lib.dmn_create(ctypes.byref(desc), 1, ctypes.byref(opt), ctypes.byref(h))
+        rc = self._lib.dmn_create(descs, len(trees), ctypes.byref(opt), ctypes.byref(h))
         if rc != 0:
             raise ValueError("dmn_create failed (%d): %s" % (rc, self._lib.dmn_last_error(None).decode()))
         self._h = h
-        self.state_size = int(self._lib.dmn_state_size(h, 0))
+        # state fields of the arrays passed to update(); tree i uses the first tree_state_sizes[i]
+        self.state_size = int(self._lib.dmn_state_size(h, -1))
+        self.tree_state_sizes = [int(self._lib.dmn_state_size(h, k)) for k in range(len(trees))]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -184,11 +191,14 @@ class DMN:
                     iters=torch.empty(n, dtype=torch.int32, device=device),
                     status=torch.empty(n, dtype=torch.int32, device=device))
 
-    def update(self, lam, Q, E_n, dE, state_in, out=None):
-        """One material-point update; returns dict(state_out, stress, tangent, iters, status)."""
+    def update(self, lam, Q, E_n, dE, state_in, out=None, tree_id=None):
+        """One material-point update; returns dict(state_out, stress, tangent, iters, status).
+        tree_id: int32 CUDA tensor [n] selecting each point's tree, or None (tree 0)."""
         import torch
         n = lam.shape[0]
         dev = lam.device
+        if tree_id is not None:
+            _check_dev("tree_id", tree_id, torch.int32, (n,))
         _check_dev("lam", lam, torch.float64, (n, 2))
         _check_dev("Q", Q, torch.float64, (n, 9))
         _check_dev("E_n", E_n, torch.float64, (n, 6))
@@ -201,7 +211,7 @@ class DMN:
         _check_dev("iters", out["iters"], torch.int32, (n,))
         _check_dev("status", out["status"], torch.int32, (n,))
         s = torch.cuda.current_stream(dev).cuda_stream
-        rc = self._lib.dmn_update(self._h, n, None, _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE), _ptr(state_in),
+        rc = self._lib.dmn_update(self._h, n, _ptr(tree_id), _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE), _ptr(state_in),
                                   _ptr(out["state_out"]), _ptr(out["stress"]), _ptr(out["tangent"]),
                                   _ptr(out["iters"]), _ptr(out["status"]), ctypes.c_void_p(s))
         if rc != 0:

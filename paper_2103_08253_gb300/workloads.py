@@ -227,3 +227,22 @@ def state_size(K: int, phases=(FIBER, MATRIX)) -> int:
     L = n_leaves(K)
     n_inel = sum(1 for i in range(L) if phases[i % 2].kind == 1)
     return 6 * n_inel + 3 * n_nodes(K)
+
+
+def cyclic_increment(E_amp: np.ndarray, step: int, n_steps: int, periods: float = 1.0):
+    """(E_n, dE) of increment `step` (1-based) of a triangle-wave path
+    0 -> +E_amp -> -E_amp -> 0 repeated `periods` times over n_steps."""
+    a0 = triangle_wave(step - 1, n_steps, 1.0, periods)
+    a1 = triangle_wave(step, n_steps, 1.0, periods)
+    return np.ascontiguousarray(E_amp * a0), np.ascontiguousarray(E_amp * (a1 - a0))
+
+
+def mixed_depth_batch(n: int, seed: int, depths=(5, 6, 7, 8)):
+    """Tree ids of n points, equal shares of the given depths, shuffled, plus a
+    per-point flag selecting the elastic-range half (True) or the cyclic half."""
+    rng = np.random.default_rng(seed)
+    tid = np.arange(n) % len(depths)
+    rng.shuffle(tid)
+    elastic = np.zeros(n, dtype=bool)
+    elastic[rng.permutation(n)[: n // 2]] = True
+    return tid.astype(np.int32), elastic
