@@ -66,7 +66,13 @@ enum { DMN_PHASE_ELASTIC = 0, DMN_PHASE_J2_LINEAR = 1 };
 enum { DMN_PREC_F64 = 0, DMN_PREC_MIXED = 1 };
 
 /* per-point status */
-enum { DMN_STATUS_OK = 0, DMN_STATUS_MAXITER = 1, DMN_STATUS_NONFINITE = 2, DMN_STATUS_BAD_TREE = 4 };
+enum {
+  DMN_STATUS_OK = 0,
+  DMN_STATUS_MAXITER = 1,     /* max_iter corrections without meeting the criterion */
+  DMN_STATUS_NONFINITE = 2,   /* NaN or Inf in the inputs or the iterates */
+  DMN_STATUS_LINESEARCH = 3,  /* line search: 8 halvings did not lower the residual norm */
+  DMN_STATUS_BAD_TREE = 4     /* tree id outside 0 .. n_trees-1 */
+};
 
 /* trees per handle */
 enum { DMN_MAX_TREES = 8 };
@@ -95,6 +101,10 @@ typedef struct {
   int32_t ctas_per_sm; /* resident CTAs per SM of the persistent Newton kernel; 0 selects 384 threads
                         * per SM for DMN_PREC_F64 and 512 for DMN_PREC_MIXED;
                         * block * ctas_per_sm <= 512 (registers are capped to fit) */
+  int32_t line_search; /* 0: full Newton steps; 1: backtracking (Sec. 3.2 allows a step in (0, 1]):
+                        * a trial step is accepted when it lowers ||A^T W sigma||, else halved, at
+                        * most 8 times (then status LINESEARCH and the last accepted iterate).
+                        * Needs 2x the per-lane scratch and at most 256 threads per SM. */
 } dmn_options;
 
 /* Create a handle for n_trees DMNs (1 <= n_trees <= DMN_MAX_TREES; trees may

@@ -365,24 +365,37 @@ struct NewtonParams {
 
 // MINB: resident CTAs per SM the register allocation is sized for (255, 170 or
 // 128 registers per thread at 2, 3 or 4 CTAs of 128 threads).
-template <typename T, int MINB>
+// LS: backtracking line search (Sec. 3.2 allows a step s in (0, 1]): a trial
+// step is accepted when it lowers the residual norm, else it is halved, at
+// most 8 times.  Jumps and g, H are then kept in two buffers per lane: a pass
+// reads the accepted ones and writes the trial's, so a rejected trial leaves
+// the accepted iterate intact.
+template <typename T, int MINB, bool LS>
 __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int NM = P.N_max;
+  const size_t ns = (size_t)P.nslots;
   double* my_nrm = P.scr_d + slot;
-  float* my_nrmf = (float*)(P.scr_t + (size_t)(21 * NM) * P.nslots) + slot;
+  float* my_nrmf = (float*)(P.scr_t + (size_t)((LS ? 42 : 21) * NM) * ns) + slot;
+  double* abuf[2] = {P.scr_d + (size_t)(3 * NM) * ns + slot, P.scr_d + (size_t)((LS ? 6 : 3) * NM) * ns + slot};
+  T* gbuf[2] = {P.scr_t + slot, P.scr_t + (size_t)((LS ? 21 : 0) * NM) * ns + slot};
   PointArrays A;
-  A.nrm = my_nrm; A.ns = (size_t)P.nslots;
+  A.nrm = my_nrm; A.ns = ns;
   A.nrmf = my_nrmf;
-  A.a = P.scr_d + (size_t)(3 * NM) * P.nslots + slot; A.as = (size_t)P.nslots;
+  A.as = ns;
   A.paper = false;
   A.z = nullptr; A.zs = (size_t)P.n;
-  GH<T> gh{P.scr_t + slot, (size_t)P.nslots};
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
   int64_t pt = -1;   // point of this lane; -1: needs work; >= n: no work left
   int tr = 0;        // its tree
   int it = 0;
+  int cur = 0;       // buffer holding the accepted jumps and g, H
+  bool first = true; // the next pass evaluates the starting jumps
+  T step = (T)1;     // line search: scale of the trial step
+  int halvings = 0;
+  double rn_acc = 0.0;
+  Sub<T> root_acc;   // line search: results at the accepted iterate
   double Eloc[6];
   for (;;) {
     const bool need = pt < 0;
@@ -407,6 +420,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
           } else {
             const TreeDev& t = P.F.t[tr];
             const int nzf = 6 * t.nz;
+            cur = 0;
 #pragma unroll
             for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * NM + I) * P.n + pt];
             for (int f = 0; f < 3 * t.N; ++f) {
@@ -414,13 +428,16 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
               // heap node -> paper index of its jumps
               const int lvl = 32 - __clz(node + 1);
               const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
-              A.a[(size_t)f * A.as] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
+              abuf[0][(size_t)f * ns] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
               const double nv = P.nbuf[(size_t)f * P.n + pt];
-              my_nrm[(size_t)f * A.ns] = nv;
-              if (sizeof(T) == 4) my_nrmf[(size_t)f * A.ns] = (float)nv;
+              my_nrm[(size_t)f * ns] = nv;
+              if (sizeof(T) == 4) my_nrmf[(size_t)f * ns] = (float)nv;
             }
             A.z = P.state_in + pt;
             it = 0;
+            first = true;
+            step = (T)1;
+            halvings = 0;
           }
         }
       }
@@ -432,27 +449,55 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
     }
     if (!active) continue;
     const TreeDev& t = P.F.t[tr];
+    A.a = abuf[cur];
+    A.a_out = abuf[LS ? 1 - cur : cur];
+    GH<T> gh{gbuf[cur], ns, gbuf[LS ? 1 - cur : cur]};
     Sub<T> root;
     double r2;
-    tree_pass<T, true>(t, Eloc, A, gh, it > 0, root, r2, nullptr);
+    tree_pass<T, true>(t, Eloc, A, gh, !first, step, root, r2, nullptr);
     const double rn = sqrt(r2);
     double sn2 = 0.0;
 #pragma unroll
     for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
     const double sn = sqrt(sn2);
     int st = -1;
-    if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
-    else if (rn <= P.tol * (double)t.N * sn) st = DMN_STATUS_OK;
-    else if (it >= P.max_iter) st = DMN_STATUS_MAXITER;
-    if (st < 0) { ++it; continue; }
+    if (!LS) {
+      first = false;
+      if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
+      else if (rn <= P.tol * (double)t.N * sn) st = DMN_STATUS_OK;
+      else if (it >= P.max_iter) st = DMN_STATUS_MAXITER;
+      if (st < 0) { ++it; continue; }
+    } else {
+      bool accepted = first || rn < rn_acc;
+      if (accepted) {
+        first = false;
+        cur = 1 - cur;
+        rn_acc = rn;
+        root_acc = root;
+        step = (T)1;
+        halvings = 0;
+        if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
+        else if (rn <= P.tol * (double)t.N * sn) st = DMN_STATUS_OK;
+        else if (it >= P.max_iter) st = DMN_STATUS_MAXITER;
+        if (st < 0) { ++it; continue; }
+      } else if (++halvings > 8) {
+        st = DMN_STATUS_LINESEARCH;   // no halving lowered the residual: keep the accepted iterate
+        ++it;
+        root = root_acc;
+      } else {
+        step *= (T)0.5;
+        continue;
+      }
+    }
     // finished point: jumps (paper ordering), counters, and in the FP64 form the
     // local-frame stress and packed tangent for k_final to rotate
+    const double* afin = abuf[cur];
     const int nzf = 6 * t.nz;
     for (int f = 0; f < 3 * t.N; ++f) {
       const int node = f / 3, c = f - 3 * node;
       const int lvl = 32 - __clz(node + 1);
       const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
-      P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt] = st == DMN_STATUS_NONFINITE ? qnan : A.a[(size_t)f * A.as];
+      P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt] = st == DMN_STATUS_NONFINITE ? qnan : afin[(size_t)f * ns];
     }
     P.iters[pt] = it;
     P.status[pt] = st;
@@ -495,6 +540,7 @@ __global__ void __launch_bounds__(128) k_final(FinalParams P) {
   A.nrm = P.nbuf + pt; A.ns = (size_t)P.n;
   A.nrmf = nullptr;
   A.a = P.state_out + (size_t)(6 * t.nz) * P.n + pt; A.as = (size_t)P.n;
+  A.a_out = A.a;
   A.paper = true;
   A.z = P.state_in + pt; A.zs = (size_t)P.n;
   if (st == DMN_STATUS_NONFINITE) {
@@ -504,8 +550,8 @@ __global__ void __launch_bounds__(128) k_final(FinalParams P) {
   } else if (SWEEP) {
     Sub<double> root;
     double r2;
-    GH<double> gh{nullptr, 0};
-    tree_pass<double, false>(t, Eloc, A, gh, false, root, r2, nullptr);
+    GH<double> gh{nullptr, 0, nullptr};
+    tree_pass<double, false>(t, Eloc, A, gh, false, 1.0, root, r2, nullptr);
     write_stress_tangent<double>(P.Q + 9 * pt, root.sb, root.C, P.stress + 6 * pt, P.tangent + 36 * pt);
   } else {
     double sb[6], C[21];
@@ -578,14 +624,18 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   }
 
   dmn_options o;
-  o.tol = 1e-12; o.max_iter = 50; o.precision = DMN_PREC_F64; o.block = 128; o.ctas_per_sm = 0;
+  o.tol = 1e-12; o.max_iter = 50; o.precision = DMN_PREC_F64; o.block = 128; o.ctas_per_sm = 0; o.line_search = 0;
   if (opt) {
     if (opt->tol > 0.0) o.tol = opt->tol;
     if (opt->max_iter > 0) o.max_iter = opt->max_iter;
     o.precision = opt->precision;
     if (opt->block > 0) o.block = opt->block;
     if (opt->ctas_per_sm > 0) o.ctas_per_sm = opt->ctas_per_sm;
+    o.line_search = opt->line_search;
   }
+  if (o.line_search != 0 && o.line_search != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: line_search must be 0 or 1");
+  // the line-search kernel keeps two buffers per lane and is built for 256 threads per SM
+  if (o.line_search && o.ctas_per_sm <= 0) o.ctas_per_sm = 256 / o.block;
   if (o.precision != DMN_PREC_F64 && o.precision != DMN_PREC_MIXED)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: unknown precision");
   if (o.block % 32 != 0 || o.block > 128)
@@ -593,8 +643,9 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   // default occupancy: the FP64 form is bound by the FP64 pipe from 256 threads per SM on;
   // the FP32 form hides latency with 512
   if (o.ctas_per_sm <= 0) o.ctas_per_sm = (o.precision == DMN_PREC_MIXED ? 512 : 384) / o.block;
-  if (o.block * o.ctas_per_sm > 512)
-    return fail(nullptr, DMN_ERR_ARG, "dmn_create: block * ctas_per_sm must be at most 512 threads per SM");
+  if (o.block * o.ctas_per_sm > (o.line_search ? 256 : 512))
+    return fail(nullptr, DMN_ERR_ARG, "dmn_create: block * ctas_per_sm must be at most 512 threads per SM "
+                                      "(256 with the line search)");
 
   dmn_handle* h = new dmn_handle();
   h->trees = tv;
@@ -628,8 +679,10 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   }
   cudaFree(d_w);
   h->nslots = (int64_t)h->n_sm * o.ctas_per_sm * o.block;
-  if (e == cudaSuccess) e = cudaMalloc(&h->scr_d, sizeof(double) * (size_t)(6 * N_max) * h->nslots);
-  if (e == cudaSuccess) e = cudaMalloc(&h->scr_t, sizeof(double) * (size_t)(24 * N_max) * h->nslots);
+  // per slot: normals + one or two jump buffers (FP64); one or two g, H buffers + FP32 normals
+  const size_t sd = o.line_search ? 9 : 6, stt = o.line_search ? 45 : 24;
+  if (e == cudaSuccess) e = cudaMalloc(&h->scr_d, sizeof(double) * (size_t)(sd * N_max) * h->nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&h->scr_t, sizeof(double) * (size_t)(stt * N_max) * h->nslots);
   if (e == cudaSuccess) e = cudaMalloc(&h->counter, sizeof(unsigned long long) * 32);
   if (e != cudaSuccess) {
     dmn_destroy(h);
@@ -752,18 +805,21 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
   const bool mixed = h->opt.precision == DMN_PREC_MIXED;
   const int threads_per_sm = h->opt.block * h->opt.ctas_per_sm;
   const int minb = threads_per_sm > 384 ? 4 : threads_per_sm > 256 ? 3 : 2;
+  const bool ls = h->opt.line_search != 0;
   if (!mixed) {
     NewtonParams<double> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                            h->nbuf, h->scr_d, (double*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 1};
-    if (minb == 2) k_newton<double, 2><<<grid, h->opt.block, 0, s>>>(P);
-    else if (minb == 3) k_newton<double, 3><<<grid, h->opt.block, 0, s>>>(P);
-    else k_newton<double, 4><<<grid, h->opt.block, 0, s>>>(P);
+    if (ls) k_newton<double, 2, true><<<grid, h->opt.block, 0, s>>>(P);
+    else if (minb == 2) k_newton<double, 2, false><<<grid, h->opt.block, 0, s>>>(P);
+    else if (minb == 3) k_newton<double, 3, false><<<grid, h->opt.block, 0, s>>>(P);
+    else k_newton<double, 4, false><<<grid, h->opt.block, 0, s>>>(P);
   } else {
     NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                           h->nbuf, h->scr_d, (float*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 0};
-    if (minb == 2) k_newton<float, 2><<<grid, h->opt.block, 0, s>>>(P);
-    else if (minb == 3) k_newton<float, 3><<<grid, h->opt.block, 0, s>>>(P);
-    else k_newton<float, 4><<<grid, h->opt.block, 0, s>>>(P);
+    if (ls) k_newton<float, 2, true><<<grid, h->opt.block, 0, s>>>(P);
+    else if (minb == 2) k_newton<float, 2, false><<<grid, h->opt.block, 0, s>>>(P);
+    else if (minb == 3) k_newton<float, 3, false><<<grid, h->opt.block, 0, s>>>(P);
+    else k_newton<float, 4, false><<<grid, h->opt.block, 0, s>>>(P);
   }
   if (ev) cudaEventRecord(ev[2], s);
   FinalParams FP{F, n, NM, tree_id, perm, Q, state_in, state_out, stress, tangent, status, h->nbuf};
@@ -825,9 +881,11 @@ __global__ void __launch_bounds__(NOALLOC_BLOCK) k_newton_noalloc(NoAllocParams 
   A.nrm = my_nrm; A.ns = (size_t)P.nslots;
   A.nrmf = nullptr;
   A.a = P.slots + (size_t)(3 * N) * P.nslots + slot; A.as = (size_t)P.nslots;
+  A.a_out = A.a;
   A.paper = false;
   A.z = nullptr; A.zs = (size_t)P.n;
-  GH<double> gh{P.slots + (size_t)(6 * N) * P.nslots + slot, (size_t)P.nslots};
+  GH<double> gh{P.slots + (size_t)(6 * N) * P.nslots + slot, (size_t)P.nslots,
+                P.slots + (size_t)(6 * N) * P.nslots + slot};
   const int nzf = 6 * t.nz;
   int64_t pt = -1;
   int it = 0;
@@ -861,7 +919,7 @@ __global__ void __launch_bounds__(NOALLOC_BLOCK) k_newton_noalloc(NoAllocParams 
     if (!active) continue;
     Sub<double> root;
     double r2;
-    tree_pass<double, true>(t, Eloc, A, gh, it > 0, root, r2, nullptr);
+    tree_pass<double, true>(t, Eloc, A, gh, it > 0, 1.0, root, r2, nullptr);
     const double rn = sqrt(r2);
     double sn2 = 0.0;
 #pragma unroll

@@ -399,6 +399,7 @@ struct PointArrays {
   const double* nrm; size_t ns;  // normals: element (3*node + c) at nrm[(3*node+c)*ns]
   const float* nrmf;             // FP32 copy of the normals (same indexing; FP32 form only)
   double* a; size_t as;          // jumps: a[(3*j+c)*as], j = node (heap) or the paper's index
+  double* a_out;                 // where corrected jumps are written (same indexing; == a: in place)
   bool paper;                    // jumps stored in the paper's ordering (level K first, root last)
   const double* z; size_t zs;    // leaf state z^n of the inelastic slots: z[(6*slot+c)*zs]
 };
@@ -410,7 +411,8 @@ __device__ __forceinline__ int jump_index(const PointArrays& P, int K, int lvl, 
 
 template <typename T>
 struct GH {
-  T* p; size_t s;  // g and H of laminate node: p[(21*node + c)*s], c = 0..2 g, 3..20 H
+  T* p; size_t s;  // g and H of laminate node read by a pass: p[(21*node + c)*s], c = 0..2 g, 3..20 H
+  T* q;            // where the pass stores the new g and H (== p: in place)
 };
 
 template <typename T>
@@ -440,15 +442,16 @@ __device__ __forceinline__ void load_z(const TreeDev& t, const PointArrays& P, i
 
 // One pass over the tree for one point.
 //   STORE:  Newton pass.  When `apply` is set, first apply the previous Newton
-//           step on the way down, da = g + H d_eps with the g, H stored by the
-//           previous pass, a += da (top-down redistribution); then store this
-//           pass's g, H for the next step.
+//           step scaled by `step` on the way down, da = step g + H d_eps with the
+//           g, H stored by the previous pass, a_out = a + da (top-down
+//           redistribution; the scaled step is the same linear map applied to
+//           step g); then store this pass's g, H for the next step.
 //   !STORE: evaluation at the given jumps only (final sweep).
 // Returns the root's subtree result (sb = effective stress, C = tangent of the
 // linearised DMN) and the squared norm of A^T W sigma at the (updated) jumps.
 template <typename T, bool STORE>
 __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArrays& P, GH<T> gh, bool apply,
-                          Sub<T>& root, double& r2, double* gap_min) {
+                          T step, Sub<T>& root, double& r2, double* gap_min) {
   const int K = t.K;
   double epsR[KMAX + 1][6];
   T depsR[KMAX + 1][6];
@@ -473,20 +476,22 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
       T nt[3];
       load_n<T>(P, node, nd, nt);
       const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
-      double* ap = P.a + (size_t)(3 * jump_index(P, K, lvl, node)) * P.as;
+      const size_t aoff = (size_t)(3 * jump_index(P, K, lvl, node)) * P.as;
+      const double* ap = P.a + aoff;
       double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
       T da[3] = {(T)0, (T)0, (T)0};
       if (STORE) {   // only the Newton kernel corrects jumps; `apply` is false on a point's first pass
         const T* gp = gh.p + (size_t)(21 * node) * gh.s;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          T v = gp[c * gh.s];
+          T v = step * gp[c * gh.s];
 #pragma unroll
           for (int I = 0; I < 6; ++I) v += gp[(3 + 6 * c + I) * gh.s] * de[I];
           da[c] = apply ? v : (T)0;
         }
+        double* aw = P.a_out + aoff;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) { a[c] += (double)da[c]; ap[c * P.as] = a[c]; }
+        for (int c = 0; c < 3; ++c) { a[c] += (double)da[c]; aw[c * P.as] = a[c]; }
       }
       const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
       double Na[6];
@@ -525,7 +530,7 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
       double nd[3];
       T nt[3];
       load_n<T>(P, node, nd, nt);
-      T* gp = STORE ? gh.p + (size_t)(21 * node) * gh.s : nullptr;
+      T* gp = STORE ? gh.q + (size_t)(21 * node) * gh.s : nullptr;
       condense_bottom<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node),
                                 node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2);
     }
@@ -540,7 +545,7 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
       double nd[3];
       T nt[3];
       load_n<T>(P, node, nd, nt);
-      T* gp = STORE ? gh.p + (size_t)(21 * node) * gh.s : nullptr;
+      T* gp = STORE ? gh.q + (size_t)(21 * node) * gh.s : nullptr;
       const Sub<T> B = res;
       condense<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node), node_c<T>(t, node),
                          pend[lvl + 1], B, res, gp, gh.s, r2);

@@ -21,7 +21,7 @@ EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_interp_orientatio
 
 PREC_F64 = 0
 PREC_MIXED = 1
-STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE, STATUS_BAD_TREE = 0, 1, 2, 4
+STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE, STATUS_LINESEARCH, STATUS_BAD_TREE = 0, 1, 2, 3, 4
 MAX_TREES = 8
 
 
@@ -38,7 +38,7 @@ class TreeDesc_(ctypes.Structure):
 
 class Options_(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("line_search", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -102,7 +102,7 @@ class DMN:
     of such objects (tree i is selected by tree_id == i in update())."""
 
     def __init__(self, tree, precision: str = "f64", tol: float = 1e-12, max_iter: int = 50, block: int = 0,
-                 ctas_per_sm: int = 0):
+                 ctas_per_sm: int = 0, line_search: bool = False):
         import numpy as np
         self._lib = load_library()
         trees = list(tree) if isinstance(tree, (list, tuple)) else [tree]
@@ -123,7 +123,7 @@ class DMN:
         if precision not in ("f64", "mixed"):
             raise ValueError("precision must be 'f64' or 'mixed'")
         opt = Options_(float(tol), int(max_iter), PREC_MIXED if precision == "mixed" else PREC_F64, int(block),
-                       int(ctas_per_sm))
+                       int(ctas_per_sm), int(bool(line_search)))
         self.precision = precision
         h = ctypes.c_void_p()
         rc = self._lib.dmn_create(descs, len(trees), ctypes.byref(opt), ctypes.byref(h))
