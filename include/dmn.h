@@ -165,6 +165,36 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
                const double* E_n, const double* dE, const double* state_in, double* state_out, double* stress,
                double* tangent, int32_t* iters, int32_t* status, void* stream);
 
+/* Replace the parameters of tree tree_id (host arrays laid out as in
+ * dmn_tree_desc: p, q [(2^K-1) * M] in the paper's ordering, w [2^K] > 0),
+ * e.g. after an optimiser step of the offline training (Sec. 3.1).  Depth,
+ * shape functions and phases stay.  Synchronises the device.  Errors:
+ * DMN_ERR_ARG for a bad tree_id or parameters (as dmn_create). */
+int dmn_set_params(dmn_handle* h, int32_t tree_id, const double* p, const double* q, const double* w);
+
+/* Adjoint of the converged update (FP64): for a loss L with g_stress =
+ * dL/d sigma_bar (dev [n][6], global frame), adds to
+ *   g_p, g_q  dev [(2^K-1) * M]  dL/dp, dL/dq (paper ordering, Sec. 3.1),
+ *   g_w       dev [2^K]          dL/dw for the leaf weights as given to
+ *                                dmn_create / dmn_set_params (before their
+ *                                normalisation to sum 1),
+ * summed over the n points, and writes g_E dev [n][6] = dL/dE = C^T g_stress
+ * (may be NULL).  The gradient is the implicit-function derivative of the
+ * converged Newton solution of the Euler-Lagrange equation (Sec. 3.2):
+ * dL/dtheta = g.d sigma_bar/d theta + mu.dR/d theta with mu = (da/dE) g, the
+ * response of the condensed tree to a macro perturbation g (no extra solve);
+ * the condensation at the converged jumps is recomputed, nothing from the
+ * Newton iterations is stored.  Inputs are those of the dmn_update call that
+ * produced state_out (its output, read only) from state_in; points whose
+ * update did not converge should get g_stress = 0.  One tree per handle
+ * (tree_id must be NULL).  The first call with a larger n than any earlier
+ * call (up to 16384 points per chunk) allocates work space.  Errors:
+ * DMN_ERR_ARG for NULL arrays, n < 0, a non-NULL tree_id or a handle with
+ * several trees. */
+int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam, const double* Q, const double* E_n,
+             const double* dE, const double* state_in, const double* state_out, const double* g_stress, double* g_p,
+             double* g_q, double* g_w, double* g_E, void* stream);
+
 /* Per-kernel timing of dmn_update, for measurement: while enabled, CUDA
  * events are recorded on the update's stream before and after each of its
  * kernels.  enable != 0 clears the totals and starts recording; 0 stops.

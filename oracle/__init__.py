@@ -177,3 +177,89 @@ __all__ = ["build", "update", "normals", "barycentric", "gradient_operator", "ne
            "rotate", "interp_orientation", "state_size", "phases_array"]
 if "--build" in sys.argv[1:]:  # pragma: no cover
     print(build(force=True))
+
+
+def _with_params(tree, p=None, q=None, w=None):
+    import copy
+    t = copy.copy(tree)
+    if p is not None:
+        t.p = p
+    if q is not None:
+        t.q = q
+    if w is not None:
+        t.w = w
+    return t
+
+
+def gradient_ift(tree, lam, Q, E_glob, a_star, z_leaf, g_glob, directions=None, h=1e-6):
+    """Gradient of g . sigma_bar at the converged jumps a_star of one point by the
+    implicit function theorem applied to R(a, theta) = A^T W sigma = 0 (Sec. 3.2):
+        dL/dtheta = g . d sigma_bar/d theta|_a - lambda . dR/d theta|_a,
+        J lambda = (d sigma_bar / d a)^T g,   J = A^T W D A (the oracle's dense matrix).
+    The partial derivatives at fixed jumps are central differences of the oracle's
+    own evaluation (step h), the solve is numpy's dense solve.  theta = (p, q, w) with w
+    the leaf weights before normalisation.
+
+    directions: None for the full gradient (dict with 'p', 'q', 'w'), or a list of
+    (dp, dq, dw) triples for directional derivatives.  Also returns dL/dE = C g with C
+    from the oracle's update tangent (global frame) when the caller passes it in."""
+    lam = np.asarray(lam, dtype=np.float64)
+    Qm = np.asarray(Q, dtype=np.float64).reshape(3, 3)
+    _, E_loc = rotate(Qm.T, np.zeros((6, 6)), E_glob)
+    _, g_loc = rotate(Qm.T, np.zeros((6, 6)), g_glob)
+    p0, q0, w0 = (np.array(x, dtype=np.float64) for x in (tree.p, tree.q, tree.w))
+
+    def ev(tr, a):
+        s = newton_system(tr, lam[0], lam[1], E_loc, a, z_leaf)
+        return s["sbar"], s["R"], s["J"]
+
+    s0, R0, J = ev(tree, a_star)
+    n_a = a_star.size
+    dsda = np.empty((6, n_a))
+    for k in range(n_a):
+        e = np.zeros(n_a)
+        e[k] = h
+        dsda[:, k] = (ev(tree, a_star + e)[0] - ev(tree, a_star - e)[0]) / (2 * h)
+    lamv = np.linalg.solve(J, dsda.T @ g_loc)
+
+    def partial(dp, dq, dw, step):
+        sp, Rp, _ = ev(_with_params(tree, p0 + step * dp, q0 + step * dq, w0 + step * dw), a_star)
+        sm, Rm, _ = ev(_with_params(tree, p0 - step * dp, q0 - step * dq, w0 - step * dw), a_star)
+        return g_loc @ (sp - sm) / (2 * step) - lamv @ (Rp - Rm) / (2 * step)
+
+    hw = h * w0.max()
+    if directions is not None:
+        return [partial(dp, dq, dw, h) for dp, dq, dw in directions]
+    gp = np.zeros_like(p0)
+    gq = np.zeros_like(q0)
+    gw = np.zeros_like(w0)
+    for idx in np.ndindex(p0.shape):
+        e = np.zeros_like(p0)
+        e[idx] = 1.0
+        gp[idx] = partial(e, 0 * q0, 0 * w0, h)
+        gq[idx] = partial(0 * p0, e, 0 * w0, h)
+    for l in range(w0.size):
+        e = np.zeros_like(w0)
+        e[l] = 1.0
+        gw[l] = partial(0 * p0, 0 * q0, e, hw)
+    return dict(p=gp, q=gq, w=gw)
+
+
+def leaf_states(tree, state, i):
+    """z^n of every leaf of point i, [2^K, 7] (alpha_bar, ep6), from a field-major state."""
+    L = 1 << tree.K
+    z = np.zeros((L, 7))
+    slot = 0
+    for l in range(L):
+        if tree.phases[l % 2].kind == 1:
+            b = state[6 * slot:6 * slot + 6, i]
+            z[l] = [b[0], b[1], b[2], -(b[1] + b[2]), b[3], b[4], b[5]]
+            slot += 1
+    return z
+
+
+def jumps(tree, state, i):
+    """a of point i (paper ordering) from a field-major state."""
+    L = 1 << tree.K
+    nz = sum(1 for l in range(L) if tree.phases[l % 2].kind == 1)
+    return np.array(state[6 * nz:, i])

@@ -1,0 +1,99 @@
+"""torch.autograd bindings of the DMN update and its adjoint (dmn_grad).
+
+`dmn_stress(m, lam, Q, E_n, dE, state_in, p, q, w)` returns the converged
+effective stress of an update and, in the backward pass, gradients with
+respect to the DMN parameters p, q (angle coefficients, Sec. 2.3), w (leaf
+weights) and the macro strain, from the implicit-function adjoint of the
+converged Newton solution (the condensation at the converged jumps is
+recomputed; nothing from the iterations is stored).
+
+`dmn_stiffness(m, lam, Q, p, q, w)` returns the effective stiffness of a DMN
+with linear elastic phases (the offline-training quantity of Sec. 3.1); its
+backward pass uses that sigma_bar = C_bar E holds exactly, so
+<G, C_bar> = sum_k G[:, k] . sigma_bar(E = e_k): six stress adjoints at the
+Mandel unit strains.
+
+Both run every step through the C ABI; the parameters are uploaded with
+dmn_set_params when they differ from the ones the handle holds.
+"""
+from __future__ import annotations
+
+import torch
+
+
+def _sync_params(m, p, q, w):
+    key = tuple(x.detach().double().cpu().numpy().tobytes() for x in (p, q, w))
+    if getattr(m, "_param_key", None) != key:
+        m.set_params(p.detach().double().cpu().numpy(), q.detach().double().cpu().numpy(),
+                     w.detach().double().cpu().numpy())
+        m._param_key = key
+
+
+class _Stress(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, m, lam, Q, E_n, dE, state_in, p, q, w):
+        _sync_params(m, p, q, w)
+        out = m.update(lam, Q, E_n.detach(), dE.detach(), state_in)
+        ctx.m = m
+        ctx.save_for_backward(lam, Q, E_n.detach(), dE.detach(), state_in, out["state_out"], out["status"])
+        ctx.shapes = (p.shape, q.shape, w.shape)
+        ctx.mark_non_differentiable(out["state_out"], out["status"])
+        return out["stress"], out["state_out"], out["status"]
+
+    @staticmethod
+    def backward(ctx, g_stress, _g_state, _g_status):
+        lam, Q, E_n, dE, state_in, state_out, status = ctx.saved_tensors
+        g = torch.where((status == 0)[:, None], g_stress, torch.zeros_like(g_stress)).contiguous()
+        g_p, g_q, g_w, g_E = ctx.m.grad(lam, Q, E_n, dE, state_in, state_out, g)
+        sp, sq, sw = ctx.shapes
+        return (None, None, None, g_E, g_E, None, g_p.reshape(sp), g_q.reshape(sq), g_w.reshape(sw))
+
+
+def dmn_stress(m, lam, Q, E_n, dE, state_in, p, q, w):
+    """(stress [n, 6], state_out, status) of one update; differentiable in E_n, dE, p, q, w."""
+    return _Stress.apply(m, lam, Q, E_n, dE, state_in, p, q, w)
+
+
+class _Stiffness(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, m, lam, Q, p, q, w):
+        _sync_params(m, p, q, w)
+        n = lam.shape[0]
+        dev = lam.device
+        S = m.state_size
+        zero_state = torch.zeros((S, 6 * n), dtype=torch.float64, device=dev)
+        lam6, Q6 = lam.repeat(6, 1), Q.repeat(6, 1)
+        E0 = torch.zeros((6 * n, 6), dtype=torch.float64, device=dev)
+        dE = torch.eye(6, dtype=torch.float64, device=dev).repeat_interleave(n, dim=0)
+        out = m.update(lam6, Q6, E0, dE, zero_state)
+        C = out["stress"].reshape(6, n, 6).permute(1, 2, 0).contiguous()   # C[:, :, k] = sigma(e_k)
+        ctx.m = m
+        ctx.save_for_backward(lam6, Q6, E0, dE, zero_state, out["state_out"])
+        ctx.n = n
+        ctx.shapes = (p.shape, q.shape, w.shape)
+        return C
+
+    @staticmethod
+    def backward(ctx, G):
+        lam6, Q6, E0, dE, st_in, st_out = ctx.saved_tensors
+        n = ctx.n
+        g = G.permute(2, 0, 1).reshape(6 * n, 6).contiguous()   # row block k: G[:, :, k]
+        g_p, g_q, g_w, _ = ctx.m.grad(lam6, Q6, E0, dE, st_in, st_out, g, want_E=False)
+        sp, sq, sw = ctx.shapes
+        return None, None, None, g_p.reshape(sp), g_q.reshape(sq), g_w.reshape(sw)
+
+
+def dmn_stiffness(m, lam, Q, p, q, w):
+    """Effective stiffness [n, 6, 6] (global frame) of a DMN with elastic phases; differentiable in p, q, w."""
+    for ph in m.phases:
+        if ph.kind != 0:
+            raise ValueError("dmn_stiffness needs linear elastic phases")
+    return _Stiffness.apply(m, lam, Q, p, q, w)
+
+
+def macaulay(v):
+    """w = <v>_+ = max(v, 0): the weight parametrisation of Sec. 3.1."""
+    return torch.clamp(v, min=0.0)
+
+
+__all__ = ["dmn_stress", "dmn_stiffness", "macaulay"]

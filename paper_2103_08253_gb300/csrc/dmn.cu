@@ -37,8 +37,9 @@ struct Tree {
   int K, M, N, L, nz, z_both, S;
   double* d_p = nullptr;
   double* d_q = nullptr;
-  double* d_c = nullptr;   // c1 [N], c2 [N], sc [N]
+  double* d_c = nullptr;   // c1 [N], c2 [N], sc [N], normalised leaf weights [L]
   float* d_cf = nullptr;   // c1f [N], c2f [N], c12f [N]
+  double wsum = 1.0;       // sum of the leaf weights as given
   PhaseDev ph[2];
 };
 
@@ -56,6 +57,8 @@ struct dmn_handle {
   unsigned long long* counter = nullptr;  // [0] work counter, [1..9] points per tree, [10..18] cursors
   double* nbuf = nullptr;       // per point: normals [3N] + local macro strain [6], field-major
   int64_t* perm = nullptr;      // points sorted by tree (several trees)
+  double* gwork = nullptr;      // dmn_grad per-point work, one chunk
+  int64_t gwork_cap = 0;
   int64_t nbuf_cap = 0;
   bool profiling = false;
   std::vector<std::array<cudaEvent_t, 4>> events;  // per timed update: before/after each kernel
@@ -80,6 +83,7 @@ TreeDev tree_dev(const Tree& t) {
   d.p = t.d_p; d.q = t.d_q;
   d.c1 = t.d_c; d.c2 = t.d_c + t.N; d.sc = t.d_c + 2 * t.N;
   d.c1f = t.d_cf; d.c2f = t.d_cf + t.N; d.c12f = t.d_cf + 2 * t.N;
+  d.wl = t.d_c + 3 * t.N; d.wsum = t.wsum;
   d.ph[0] = t.ph[0]; d.ph[1] = t.ph[1];
   return d;
 }
@@ -130,6 +134,7 @@ __global__ void k_setup_tree(int K, const double* w_raw, double* c, float* cf) {
     cf[N + h - 1] = (float)c2;
     cf[2 * N + h - 1] = (float)(c1 * c2);
   }
+  for (int l = 0; l < L; ++l) c[3 * N + l] = w_raw[l] / s;
 }
 
 // ---------------------------------------------------------------------------
@@ -564,6 +569,140 @@ __global__ void __launch_bounds__(128) k_final(FinalParams P) {
   write_leaf_states(t, Eloc, A, P.state_out + pt, (size_t)P.n, st == DMN_STATUS_NONFINITE);
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint kernels (dmn_grad).  One thread per point of a chunk; per-point work
+// arrays are field-major over the chunk.
+struct GradParams {
+  TreeDev t;
+  int64_t n, n0, nc;   // points in the batch, first point of the chunk, chunk size
+  const double *lam, *Q, *En, *dE, *state_in, *state_out, *g_stress;
+  double* g_E;
+  double* work;
+};
+
+// work fields per point
+__host__ __device__ inline size_t grad_fields(int N, int L) { return (size_t)33 * N + 2 * L + 6; }
+
+__global__ void __launch_bounds__(128) k_grad(GradParams P) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= P.nc) return;
+  const int64_t pt = P.n0 + i;
+  const TreeDev& t = P.t;
+  const int N = t.N, L = t.L;
+  const size_t ws = (size_t)P.nc;
+  double* w = P.work + i;
+  double* nrm = w;
+  double* a = w + (size_t)(3 * N) * ws;
+  double* gh = w + (size_t)(6 * N) * ws;
+  AdjWork Wk;
+  Wk.H = gh; Wk.hs = ws;
+  Wk.mu = w + (size_t)(27 * N) * ws;
+  Wk.xi = w + (size_t)(30 * N) * ws;
+  Wk.gab = w + (size_t)(31 * N) * ws;
+  Wk.direct = w + (size_t)(33 * N) * ws;
+  Wk.ws = ws;
+  double* gw = w + (size_t)(33 * N + L) * ws;
+  double* phv = w + (size_t)(33 * N + 2 * L) * ws;
+  // orientation: normals and shape functions
+  const double l1 = P.lam[2 * pt], l2 = P.lam[2 * pt + 1];
+  point_normals(t, l1, l2, nrm, ws);
+  const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
+  double ph[6] = {0, 0, 0, 0, 0, 0};
+  if (t.M == 3) {
+    ph[0] = v[0]; ph[1] = v[1]; ph[2] = v[2];
+  } else if (t.M == 4) {
+    const double b = v[0] * v[1] * v[2];
+    ph[0] = v[0] - 9.0 * b; ph[1] = v[1] - 9.0 * b; ph[2] = v[2] - 9.0 * b; ph[3] = 27.0 * b;
+  } else {
+    ph[0] = v[0] * (2.0 * v[0] - 1.0); ph[1] = v[1] * (2.0 * v[1] - 1.0); ph[2] = v[2] * (2.0 * v[2] - 1.0);
+    ph[3] = 4.0 * v[0] * v[1]; ph[4] = 4.0 * v[0] * v[2]; ph[5] = 4.0 * v[1] * v[2];
+  }
+  for (int m = 0; m < 6; ++m) phv[(size_t)m * ws] = ph[m];
+  // converged jumps (paper ordering in the state -> heap order here)
+  const int nzf = 6 * t.nz;
+  for (int f = 0; f < 3 * N; ++f) {
+    const int node = f / 3, c = f - 3 * node;
+    const int lvl = 32 - __clz(node + 1);
+    const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+    a[(size_t)f * ws] = P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt];
+  }
+  double Eloc[6];
+  local_strain(P.Q + 9 * pt, P.En + 6 * pt, P.dE + 6 * pt, Eloc);
+  PointArrays A;
+  A.nrm = nrm; A.ns = ws; A.nrmf = nullptr;
+  A.a = a; A.a_out = a; A.as = ws; A.paper = false;
+  A.z = P.state_in + pt; A.zs = (size_t)P.n;
+  // condensation at the converged jumps: H of every laminate and the tangent
+  Sub<double> root;
+  double r2;
+  GH<double> g{gh, ws, gh};
+  tree_pass<double, true>(t, Eloc, A, g, false, 1.0, root, r2, nullptr);
+  // loss gradient into the local frame: sigma_glob = R sigma_loc  =>  g_loc = R^T g_glob
+  double R[6][6], gl[6];
+  mandel_rotation(P.Q + 9 * pt, R);
+#pragma unroll
+  for (int J = 0; J < 6; ++J) {
+    double s = 0.0;
+#pragma unroll
+    for (int I = 0; I < 6; ++I) s += R[I][J] * P.g_stress[6 * pt + I];
+    gl[J] = s;
+  }
+  adjoint_pass(t, Eloc, gl, ph, A, Wk);
+  adjoint_weights(t, t.wl, t.wsum, Wk, gw, ws);
+  if (P.g_E) {   // dL/dE = C^T g (C symmetric), rotated back
+    double ge[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) {
+      double s = 0.0;
+#pragma unroll
+      for (int J = 0; J < 6; ++J) s += root.C[sidx(I, J)] * gl[J];
+      ge[I] = s;
+    }
+#pragma unroll
+    for (int I = 0; I < 6; ++I) {
+      double s = 0.0;
+#pragma unroll
+      for (int J = 0; J < 6; ++J) s += R[I][J] * ge[J];
+      P.g_E[6 * pt + I] = s;
+    }
+  }
+}
+
+// Sums the per-point gradients of a chunk into the parameter gradients (added to
+// g_p, g_q, g_w in the paper's ordering): one CTA per parameter, fixed-order
+// reduction, so results are repeatable bit for bit.
+__global__ void __launch_bounds__(256) k_grad_reduce(TreeDev t, int64_t nc, const double* __restrict__ work,
+                                                     double* g_p, double* g_q, double* g_w) {
+  const int r = blockIdx.x;
+  const int N = t.N, M = t.M, L = t.L;
+  const size_t ws = (size_t)nc;
+  const double* base;
+  const double* fac = nullptr;
+  double* out;
+  if (r < 2 * N * M) {
+    const int which = r / (N * M), rr = r % (N * M), node = rr / M, m = rr % M;
+    base = work + (size_t)(31 * N + which * N + node) * ws;
+    fac = work + (size_t)(33 * N + 2 * L + m) * ws;
+    const int lvl = 32 - __clz(node + 1);
+    const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+    out = (which ? g_q : g_p) + j * M + m;
+  } else {
+    const int l = r - 2 * N * M;
+    base = work + (size_t)(33 * N + L + l) * ws;
+    out = g_w + l;
+  }
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) s += fac ? base[i] * fac[i] : base[i];
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out += red[0];
+}
+
 int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // parameters of a tree description in heap order (array index = heap number - 1)
@@ -664,9 +803,11 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     const int N = T.N, M = T.M, L = T.L;
     std::vector<double> ph(N * M), qh(N * M);
     heap_params(d, ph.data(), qh.data());
+    T.wsum = 0.0;
+    for (int l = 0; l < L; ++l) T.wsum += d.w[l];
     e = cudaMalloc(&T.d_p, sizeof(double) * N * M);
     if (e == cudaSuccess) e = cudaMalloc(&T.d_q, sizeof(double) * N * M);
-    if (e == cudaSuccess) e = cudaMalloc(&T.d_c, sizeof(double) * 3 * N);
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_c, sizeof(double) * (3 * N + L));
     if (e == cudaSuccess) e = cudaMalloc(&T.d_cf, sizeof(float) * 3 * N);
     if (e == cudaSuccess) e = cudaMemcpy(T.d_p, ph.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(T.d_q, qh.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
@@ -699,6 +840,7 @@ void dmn_destroy(dmn_handle* h) {
     for (auto& x : a) cudaEventDestroy(x);
   for (auto& t : h->trees) { cudaFree(t.d_p); cudaFree(t.d_q); cudaFree(t.d_c); cudaFree(t.d_cf); }
   cudaFree(h->scr_d); cudaFree(h->scr_t); cudaFree(h->counter); cudaFree(h->nbuf); cudaFree(h->perm);
+  cudaFree(h->gwork);
   delete h;
 }
 
@@ -828,6 +970,66 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
   if (ev) cudaEventRecord(ev[3], s);
   e = cudaGetLastError();
   return e == cudaSuccess ? DMN_OK : cuda_fail(h, e, "dmn_update: launch");
+}
+
+int dmn_set_params(dmn_handle* h, int32_t tree_id, const double* p, const double* q, const double* w) {
+  if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_set_params: NULL handle");
+  if (tree_id < 0 || tree_id >= (int)h->trees.size()) return fail(h, DMN_ERR_ARG, "dmn_set_params: bad tree_id");
+  Tree& T = h->trees[tree_id];
+  dmn_tree_desc d;
+  d.K = T.K; d.M = T.M; d.p = p; d.q = q; d.w = w;
+  if (const char* m = check_tree(d)) return fail(h, DMN_ERR_ARG, std::string("dmn_set_params: ") + m);
+  std::vector<double> ph(T.N * T.M), qh(T.N * T.M);
+  heap_params(d, ph.data(), qh.data());
+  cudaError_t e = cudaDeviceSynchronize();
+  double* d_w = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&d_w, sizeof(double) * T.L);
+  if (e == cudaSuccess) e = cudaMemcpy(T.d_p, ph.data(), sizeof(double) * T.N * T.M, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(T.d_q, qh.data(), sizeof(double) * T.N * T.M, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_w, w, sizeof(double) * T.L, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_setup_tree<<<1, 1>>>(T.K, d_w, T.d_c, T.d_cf);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d_w);
+  if (e != cudaSuccess) return cuda_fail(h, e, "dmn_set_params");
+  T.wsum = 0.0;
+  for (int l = 0; l < T.L; ++l) T.wsum += w[l];
+  return DMN_OK;
+}
+
+int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam, const double* Q, const double* E_n,
+             const double* dE, const double* state_in, const double* state_out, const double* g_stress,
+             double* g_p, double* g_q, double* g_w, double* g_E, void* stream) {
+  if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_grad: NULL handle");
+  if (n < 0) return fail(h, DMN_ERR_ARG, "dmn_grad: n < 0");
+  if (tree_id || h->trees.size() != 1) return fail(h, DMN_ERR_ARG, "dmn_grad: one tree only (tree_id must be NULL)");
+  if (n == 0) return DMN_OK;
+  if (!lam || !Q || !E_n || !dE || !state_in || !state_out || !g_stress || !g_p || !g_q || !g_w)
+    return fail(h, DMN_ERR_ARG, "dmn_grad: NULL array");
+  const Tree& T = h->trees[0];
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t chunk = std::min<int64_t>(n, 16384);
+  const size_t fields = grad_fields(T.N, T.L);
+  cudaError_t e;
+  if (chunk > h->gwork_cap) {
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) { cudaFree(h->gwork); h->gwork = nullptr; h->gwork_cap = 0; }
+    if (e == cudaSuccess) e = cudaMalloc(&h->gwork, sizeof(double) * fields * chunk);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_grad: work buffer");
+    h->gwork_cap = chunk;
+  }
+  const TreeDev td = tree_dev(T);
+  const int n_params = 2 * T.N * T.M + T.L;
+  for (int64_t n0 = 0; n0 < n; n0 += chunk) {
+    const int64_t nc = std::min(chunk, n - n0);
+    GradParams P{td, n, n0, nc, lam, Q, E_n, dE, state_in, state_out, g_stress, g_E, h->gwork};
+    k_grad<<<(unsigned)div_up(nc, 128), 128, 0, s>>>(P);
+    k_grad_reduce<<<n_params, 256, 0, s>>>(td, nc, h->gwork, g_p, g_q, g_w);
+  }
+  e = cudaGetLastError();
+  return e == cudaSuccess ? DMN_OK : cuda_fail(h, e, "dmn_grad: launch");
 }
 
 }  // extern "C"
@@ -981,7 +1183,7 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   td.z_both = n_inel == 2;
   td.nz = n_inel * (L / 2);
   // sizes against the fixed work space: parameters, then whole CTAs of lane scratch
-  const size_t param_doubles = (size_t)2 * N * M + (size_t)L + 3 * (size_t)N + (3 * (size_t)N + 1) / 2;
+  const size_t param_doubles = (size_t)2 * N * M + (size_t)L + 3 * (size_t)N + (size_t)L + (3 * (size_t)N + 1) / 2;
   const size_t lane_bytes = sizeof(double) * (size_t)27 * N;
   const size_t avail = DMN_NOALLOC_BYTES - 256 - sizeof(double) * NOALLOC_PARAM_DOUBLES;
   const int64_t nslots = (int64_t)(avail / lane_bytes) / NOALLOC_BLOCK * NOALLOC_BLOCK;
@@ -1014,7 +1216,7 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   double* d_q = d_p + N * M;
   double* d_w = d_q + N * M;
   double* d_c = d_w + L;
-  float* d_cf = (float*)(d_c + 3 * N);
+  float* d_cf = (float*)(d_c + 3 * N + L);
   double* slots = (double*)(base + 256 + sizeof(double) * NOALLOC_PARAM_DOUBLES);
 
   // parameters in heap order, staged on the host stack (no heap allocation)
@@ -1032,6 +1234,9 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   td.p = d_p; td.q = d_q;
   td.c1 = d_c; td.c2 = d_c + N; td.sc = d_c + 2 * N;
   td.c1f = d_cf; td.c2f = d_cf + N; td.c12f = d_cf + 2 * N;
+  td.wl = d_c + 3 * N;
+  td.wsum = 0.0;
+  for (int l = 0; l < L; ++l) td.wsum += d.w[l];
   NoAllocParams P{td, n, nslots, lam, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status, slots,
                   counter, tol, max_iter};
   k_newton_noalloc<<<(unsigned)(nslots / NOALLOC_BLOCK), NOALLOC_BLOCK, 0, s>>>(P);

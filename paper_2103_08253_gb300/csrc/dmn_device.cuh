@@ -50,6 +50,8 @@ struct TreeDev {
   const float* c1f;  // [N] FP32 copies of c1, c2, c1 c2
   const float* c2f;
   const float* c12f;
+  const double* wl;  // [L] normalised leaf weights
+  double wsum;       // sum of the leaf weights as given
   PhaseDev ph[2];
 };
 
@@ -595,6 +597,204 @@ __device__ inline void write_leaf_states(const TreeDev& t, const double Eloc[6],
       for (int c = 0; c < 6; ++c) b[c * zos] = nan_out ? __longlong_as_double(0x7ff8000000000000LL) : zn[c];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the converged update (implicit function theorem, applied to the
+// Euler-Lagrange equation R(a, theta) = A^T W sigma = 0 of Sec. 3.2).
+//
+// For a loss with gradient g = dL/d sigma_bar (local frame) the parameter
+// gradient is dL/dtheta = d/dtheta [g . sigma_bar + mu . R] at fixed a = a* and
+// fixed mu, where mu = (da/dE) g is the jump response to a macro strain
+// perturbation g: the top-down map of the condensation, mu_j = H_j d_eps_j with
+// d_eps_root = g (no extra solve; J is symmetric).  Writing g_i = g + (A mu)_i
+// for the leaf strain perturbations and tau = average of D_i g_i over a
+// subtree, the lagrangian is sum_i w_i g_i . sigma_i and its partial
+// derivatives are
+//   laminate normal: W c1 c2 [N(a)^T (tau_R - tau_L) + N(mu)^T (sb_R - sb_L)]
+//                    (N(n) a = N(a) n), chained to the angles alpha, beta;
+//   volume fractions through the subtree weights: with
+//     Gam_X = (N mu)^T sb_X + (N a)^T tau_X,  Xi = (W_R Gam_R + W_L Gam_L) / W^2,
+//   d/dW_L = W_R Xi, d/dW_R = -W_L Xi, and W_X is the sum of the leaf weights
+//   below; leaf weight w_i directly: g_i . sigma_i.
+struct AdjWork {
+  const double* H; size_t hs;   // g, H of every laminate at a* (as stored by a Newton pass): [(21*node+c)*hs]
+  double* mu;                   // [3*node + c] jump response, stride ws
+  double* xi;                   // [node] weight term Xi, stride ws
+  double* direct;               // [leaf] g_i . sigma_i, stride ws
+  double* gab;                  // [node] dL/dalpha, [N + node] dL/dbeta, stride ws
+  size_t ws;
+};
+
+// angles of laminate `node` from the point's shape-function values
+__device__ __forceinline__ void node_angles(const TreeDev& t, int node, const double ph[6], double& al, double& be) {
+  al = 0.0; be = 0.0;
+  for (int m = 0; m < t.M; ++m) {
+    al += __ldg(t.p + node * t.M + m) * ph[m];
+    be += __ldg(t.q + node * t.M + m) * ph[m];
+  }
+}
+
+__device__ void adjoint_pass(const TreeDev& t, const double Eloc[6], const double gl[6], const double ph[6],
+                             const PointArrays& P, const AdjWork& Wk) {
+  const int K = t.K;
+  double epsR[KMAX + 1][6], gR[KMAX + 1][6];
+  double pend_s[KMAX + 1][6], pend_t[KMAX + 1][6];
+  const int nbottom = 1 << (K - 1);
+  const size_t ws = Wk.ws;
+  for (int m = 0; m < nbottom; ++m) {
+    const int top = (m == 0) ? 1 : K - __ffs(m) + 1;
+    double e[6], ge[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) {
+      e[I] = (m == 0) ? Eloc[I] : epsR[top][I];
+      ge[I] = (m == 0) ? gl[I] : gR[top][I];
+    }
+    double eL[6], eR[6], gL[6], gRr[6];
+    for (int lvl = top; lvl <= K; ++lvl) {
+      const int node = (1 << (lvl - 1)) + (m >> (K - lvl)) - 1;
+      double nd[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) nd[c] = P.nrm[(3 * node + c) * P.ns];
+      const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      const double* ap = P.a + (size_t)(3 * jump_index(P, K, lvl, node)) * P.as;
+      const double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
+      const double* Hp = Wk.H + (size_t)(21 * node + 3) * Wk.hs;
+      double mu[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double v = 0.0;
+#pragma unroll
+        for (int I = 0; I < 6; ++I) v += Hp[(6 * c + I) * Wk.hs] * ge[I];
+        mu[c] = v;
+        Wk.mu[(size_t)(3 * node + c) * ws] = v;
+      }
+      double Na[6], Nm[6];
+      N_apply<double>(nd, ndr, a, Na);
+      N_apply<double>(nd, ndr, mu, Nm);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) {
+        eL[I] = e[I] - c2 * Na[I]; eR[I] = e[I] + c1 * Na[I];
+        gL[I] = ge[I] - c2 * Nm[I]; gRr[I] = ge[I] + c1 * Nm[I];
+      }
+      if (lvl < K) {
+#pragma unroll
+        for (int I = 0; I < 6; ++I) { epsR[lvl + 1][I] = eR[I]; gR[lvl + 1][I] = gRr[I]; e[I] = eL[I]; ge[I] = gL[I]; }
+      }
+    }
+    // leaves: stress, D g_i, direct weight term
+    double sb[6], tb[6], sbL[6], tbL[6];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int leaf = 2 * m + side;
+      double z[6], sig[6];
+      LeafTan<double> D;
+      load_z(t, P, leaf, side, z);
+      leaf_iso<double>(t.ph[side], side ? eR : eL, z, sig, &D, nullptr, nullptr);
+      const double* gi = side ? gRr : gL;
+      const double tr = gi[0] + gi[1] + gi[2];
+      double mg = 0.0, gs = 0.0;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { mg += D.m[I] * gi[I]; gs += gi[I] * sig[I]; }
+      double tv[6];
+#pragma unroll
+      for (int I = 0; I < 6; ++I) tv[I] = 2.0 * D.mu * gi[I] - D.c * mg * D.m[I] + (I < 3 ? D.lam * tr : 0.0);
+      Wk.direct[(size_t)leaf * ws] = gs;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) {
+        if (side) { sb[I] = sig[I]; tb[I] = tv[I]; } else { sbL[I] = sig[I]; tbL[I] = tv[I]; }
+      }
+    }
+    // laminates upwards while the finished one is a right child
+    int lvl = K, idx = m;
+    for (;;) {
+      const int node = (1 << (lvl - 1)) + idx - 1;
+      double nd[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) nd[c] = P.nrm[(3 * node + c) * P.ns];
+      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      const double W = __ldg(t.sc + node) / (c1 * c2);
+      const double* ap = P.a + (size_t)(3 * jump_index(P, K, lvl, node)) * P.as;
+      const double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
+      double mu[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mu[c] = Wk.mu[(size_t)(3 * node + c) * ws];
+      const double ar[3] = {a[0] * RS2, a[1] * RS2, a[2] * RS2}, mr[3] = {mu[0] * RS2, mu[1] * RS2, mu[2] * RS2};
+      double ds[6], dt[6];
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { ds[I] = sb[I] - sbL[I]; dt[I] = tb[I] - tbL[I]; }
+      double u1[3], u2[3];
+      Nt_apply<double>(a, ar, dt, u1);    // N(a)^T (tau_R - tau_L)
+      Nt_apply<double>(mu, mr, ds, u2);   // N(mu)^T (sb_R - sb_L)
+      const double sc = W * c1 * c2;
+      const double gn[3] = {sc * (u1[0] + u2[0]), sc * (u1[1] + u2[1]), sc * (u1[2] + u2[2])};
+      double al, be, sa, ca, sbeta, cbeta;
+      node_angles(t, node, ph, al, be);
+      sincos(al, &sa, &ca);
+      sincos(be, &sbeta, &cbeta);
+      Wk.gab[(size_t)node * ws] = gn[0] * ca * cbeta + gn[1] * ca * sbeta - gn[2] * sa;
+      Wk.gab[(size_t)(t.N + node) * ws] = -gn[0] * sa * sbeta + gn[1] * sa * cbeta;
+      // weight terms: Gam_X = (N mu)^T sb_X + (N a)^T tau_X
+      const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+      double Nm[6], Na[6];
+      N_apply<double>(nd, ndr, mu, Nm);
+      N_apply<double>(nd, ndr, a, Na);
+      double GL = 0.0, GR = 0.0;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) {
+        GL += Nm[I] * sbL[I] + Na[I] * tbL[I];
+        GR += Nm[I] * sb[I] + Na[I] * tb[I];
+      }
+      const double WL = c1 * W, WR = c2 * W;
+      Wk.xi[(size_t)node * ws] = (WR * GR + WL * GL) / (W * W);
+      double so[6], to[6];
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { so[I] = c1 * sbL[I] + c2 * sb[I]; to[I] = c1 * tbL[I] + c2 * tb[I]; }
+      if (lvl == 1) break;
+      if (!(idx & 1)) {
+#pragma unroll
+        for (int I = 0; I < 6; ++I) { pend_s[lvl][I] = so[I]; pend_t[lvl][I] = to[I]; }
+        break;
+      }
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { sb[I] = so[I]; tb[I] = to[I]; sbL[I] = pend_s[lvl][I]; tbL[I] = pend_t[lvl][I]; }
+      idx >>= 1;
+      --lvl;
+    }
+  }
+}
+
+// Leaf-weight gradient: each leaf collects the direct term and, from every
+// laminate above it, +W_R Xi (left subtree) or -W_L Xi (right subtree); then the
+// normalisation w~ = w / S is undone: dL/dw_k = (G_k - sum_l G_l w~_l) / S.
+__device__ void adjoint_weights(const TreeDev& t, const double* wl, double S, const AdjWork& Wk, double* gw,
+                                size_t gws) {
+  const int K = t.K, L = t.L;
+  const size_t ws = Wk.ws;
+  double accR[KMAX + 2];
+  double sum_gw = 0.0;
+  const int nbottom = 1 << (K - 1);
+  for (int m = 0; m < nbottom; ++m) {
+    const int top = (m == 0) ? 1 : K - __ffs(m) + 1;
+    double acc = (m == 0) ? 0.0 : accR[top];
+    double aL = 0.0, aR = 0.0;
+    for (int lvl = top; lvl <= K; ++lvl) {
+      const int node = (1 << (lvl - 1)) + (m >> (K - lvl)) - 1;
+      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      const double W = __ldg(t.sc + node) / (c1 * c2);
+      const double xi = Wk.xi[(size_t)node * ws];
+      aL = acc + c2 * W * xi;   // left subtree: + W_R Xi
+      aR = acc - c1 * W * xi;   // right subtree: - W_L Xi
+      if (lvl < K) { accR[lvl + 1] = aR; acc = aL; }
+    }
+    const double G0 = Wk.direct[(size_t)(2 * m) * ws] + aL;
+    const double G1 = Wk.direct[(size_t)(2 * m + 1) * ws] + aR;
+    gw[(size_t)(2 * m) * gws] = G0;
+    gw[(size_t)(2 * m + 1) * gws] = G1;
+    sum_gw += G0 * __ldg(wl + 2 * m) + G1 * __ldg(wl + 2 * m + 1);
+  }
+  for (int l = 0; l < L; ++l) gw[(size_t)l * gws] = (gw[(size_t)l * gws] - sum_gw) / S;
 }
 
 // ---------------------------------------------------------------------------

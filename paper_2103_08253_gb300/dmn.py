@@ -17,7 +17,8 @@ _lib = None
 
 # ABI symbols declared in include/dmn.h
 EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_interp_orientation", "dmn_update",
-           "dmn_profile_enable", "dmn_profile_read", "dmn_update_noalloc", "dmn_last_error")
+           "dmn_set_params", "dmn_grad", "dmn_profile_enable", "dmn_profile_read", "dmn_update_noalloc",
+           "dmn_last_error")
 
 PREC_F64 = 0
 PREC_MIXED = 1
@@ -68,6 +69,11 @@ def load_library(build_if_missing: bool = True):
     lib.dmn_interp_orientation.restype = ctypes.c_int
     lib.dmn_update.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.dmn_update.restype = ctypes.c_int
+    lib.dmn_set_params.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]
+    lib.dmn_set_params.restype = ctypes.c_int
+    lib.dmn_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.dmn_grad.restype = ctypes.c_int
     lib.dmn_profile_enable.argtypes = [vp, i32]
     lib.dmn_profile_enable.restype = ctypes.c_int
     lib.dmn_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
@@ -108,6 +114,7 @@ class DMN:
         trees = list(tree) if isinstance(tree, (list, tuple)) else [tree]
         self.n_trees = len(trees)
         self.K, self.M = int(trees[0].K), int(trees[0].M)
+        self.phases = tuple(trees[0].phases)
         dp = ctypes.POINTER(ctypes.c_double)
         descs = (TreeDesc_ * len(trees))()
         self._keep = []
@@ -167,6 +174,39 @@ class DMN:
         if rc != 0:
             self._err("dmn_interp_orientation", rc)
         return lam, Q
+
+    def set_params(self, p, q, w, tree_id: int = 0):
+        """Replace p, q, w of one tree (numpy or CPU tensors, paper ordering)."""
+        import numpy as np
+        arrs = [np.ascontiguousarray(np.asarray(x, dtype=np.float64)).reshape(-1) for x in (p, q, w)]
+        dp = ctypes.POINTER(ctypes.c_double)
+        rc = self._lib.dmn_set_params(self._h, int(tree_id), *(a.ctypes.data_as(dp) for a in arrs))
+        if rc != 0:
+            self._err("dmn_set_params", rc)
+
+    def grad(self, lam, Q, E_n, dE, state_in, state_out, g_stress, g_p=None, g_q=None, g_w=None, want_E=True):
+        """Adjoint of a converged update: returns (g_p [N, M], g_q [N, M], g_w [2^K], g_E [n, 6] or None),
+        with g_p, g_q, g_w accumulated into the given tensors if passed."""
+        import torch
+        n = lam.shape[0]
+        dev = lam.device
+        N = (1 << self.K) - 1
+        for name, t, shape in (("lam", lam, (n, 2)), ("Q", Q, (n, 9)), ("E_n", E_n, (n, 6)), ("dE", dE, (n, 6)),
+                               ("state_in", state_in, (self.state_size, n)),
+                               ("state_out", state_out, (self.state_size, n)), ("g_stress", g_stress, (n, 6))):
+            _check_dev(name, t, torch.float64, shape)
+        z = lambda *sh: torch.zeros(sh, dtype=torch.float64, device=dev)
+        g_p = z(N, self.M) if g_p is None else g_p
+        g_q = z(N, self.M) if g_q is None else g_q
+        g_w = z(1 << self.K) if g_w is None else g_w
+        g_E = torch.empty((n, 6), dtype=torch.float64, device=dev) if want_E else None
+        s = torch.cuda.current_stream(dev).cuda_stream
+        rc = self._lib.dmn_grad(self._h, n, None, _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE), _ptr(state_in),
+                                _ptr(state_out), _ptr(g_stress), _ptr(g_p), _ptr(g_q), _ptr(g_w), _ptr(g_E),
+                                ctypes.c_void_p(s))
+        if rc != 0:
+            self._err("dmn_grad", rc)
+        return g_p, g_q, g_w, g_E
 
     def profile(self, enable: bool):
         """Start (clearing the totals) or stop per-kernel event timing of update()."""

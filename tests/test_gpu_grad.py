@@ -1,0 +1,142 @@
+"""Adjoint (dmn_grad) and the torch.autograd bindings.
+
+* GPU gradient vs the oracle's implicit-function gradient (dense J, partial
+  derivatives by central differences at fixed jumps), full parameter vectors;
+* GPU gradient vs central finite differences (h = 1e-6) of the converged
+  solve, along random parameter directions (target: <= 1e-5 relative);
+* dL/dE = C^T g against the tangent;
+* depth-8 training loss of elastic stiffnesses and elastoplastic stresses
+  against a seeded target DMN, through torch.autograd, vs finite differences.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2103_08253_gb300 import autograd as ag, dmn, workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+EL_MATRIX = W.Phase(0, 3000.0, 0.35)
+
+
+def d(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def states(tree, lam, Q, Ef, steps, n_steps):
+    """GPU run of `steps` increments; returns (state before the last, state after, E_n, dE of the last)."""
+    m = dmn.DMN(tree)
+    n = lam.shape[0]
+    st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+    prev = st
+    for s in range(1, steps + 1):
+        En, dE = W.proportional_increment(Ef, s, n_steps)
+        prev = st
+        st = m.update(d(lam), d(Q), d(En), d(dE), st)["state_out"]
+    return m, prev, st, En, dE
+
+
+@pytest.mark.parametrize("K,steps", [(3, 1), (3, 6), (5, 7)])
+def test_adjoint_matches_oracle_ift_gradient(K, steps):
+    n = 3
+    tree = W.tree_d10_fit(K, seed=60 + K)
+    A2, lam, Q = W.orientation_field(n, seed=61 + K)
+    Ef = W.random6_path_final(n, 0.03, seed=62 + K)
+    m, prev, st, En, dE = states(tree, lam, Q, Ef, steps, 10)
+    g = np.random.default_rng(K).standard_normal((n, 6))
+    g_p, g_q, g_w, g_E = m.grad(d(lam), d(Q), d(En), d(dE), prev, st, d(g))
+    # oracle on its own states
+    S = oracle.state_size(K, tree.phases)
+    so = np.zeros((S, n))
+    so_prev = so
+    for s in range(1, steps + 1):
+        E1, d1 = W.proportional_increment(Ef, s, 10)
+        so_prev = so
+        so = oracle.update(tree, lam, Q, E1, d1, so)[0]
+    tot = dict(p=0.0, q=0.0, w=0.0)
+    for i in range(n):
+        gi = oracle.gradient_ift(tree, lam[i], Q[i], (En + dE)[i], oracle.jumps(tree, so, i),
+                                 oracle.leaf_states(tree, so_prev, i), g[i])
+        for k in tot:
+            tot[k] = tot[k] + gi[k]
+    for k, gg in (("p", g_p), ("q", g_q), ("w", g_w)):
+        ref = tot[k]
+        err = np.abs(gg.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err < 1e-6, (k, err)
+    # dL/dE = C^T g with C the algorithmic tangent of the update
+    C = m.update(d(lam), d(Q), d(En), d(dE), prev)["tangent"].cpu().numpy()
+    np.testing.assert_allclose(g_E.cpu().numpy(), np.einsum("nji,nj->ni", C, g), rtol=1e-10, atol=1e-10)
+
+
+def test_adjoint_matches_finite_differences_of_the_solve():
+    K, n = 6, 16
+    tree = W.tree_d10_fit(K, seed=70)
+    A2, lam, Q = W.orientation_field(n, seed=71)
+    Ef = W.random6_path_final(n, 0.03, seed=72)
+    m, prev, st, En, dE = states(tree, lam, Q, Ef, 5, 10)
+    g = np.random.default_rng(5).standard_normal((n, 6))
+    g_p, g_q, g_w, _ = m.grad(d(lam), d(Q), d(En), d(dE), prev, st, d(g))
+    rng = np.random.default_rng(6)
+    h = 1e-6
+    for _ in range(3):
+        dp, dq = rng.standard_normal(tree.p.shape), rng.standard_normal(tree.q.shape)
+        dw = rng.standard_normal(tree.w.shape) * tree.w
+        pred = (g_p.cpu().numpy() * dp).sum() + (g_q.cpu().numpy() * dq).sum() + (g_w.cpu().numpy() * dw).sum()
+        vals = []
+        for sc in (h, -h):
+            m.set_params(tree.p + sc * dp, tree.q + sc * dq, tree.w + sc * dw)
+            sig = m.update(d(lam), d(Q), d(En), d(dE), prev)["stress"].cpu().numpy()
+            vals.append((g * sig).sum())
+        m.set_params(tree.p, tree.q, tree.w)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(pred - fd) <= 1e-5 * abs(fd), (pred, fd)
+
+
+def test_training_loss_through_autograd_depth8():
+    """Depth-8 DMN with trainable angle coefficients and leaf weights: relative
+    Frobenius errors of elastic stiffnesses and of elastoplastic stresses
+    (one increment from the virgin state, 1-3 % equivalent strain) against a
+    seeded target DMN; autograd gradient vs finite differences."""
+    K, ne, npl = 8, 64, 64
+    base = W.tree_d10_fit(K, seed=80)
+    target = W.tree_d10_fit(K, seed=81)
+    el = W.TreeParams(K, 3, base.p, base.q, base.w, (W.FIBER, EL_MATRIX))
+    A2e, lame, Qe = W.orientation_field(ne, seed=82)
+    A2p, lamp, Qp = W.orientation_field(npl, seed=83)
+    rng = np.random.default_rng(84)
+    Ep = W.random6_path_final(npl, 1.0, seed=85) * rng.uniform(0.01, 0.03, (npl, 1))
+    # one large increment from the virgin state: the line search keeps Newton convergent
+    m_el, m_pl = dmn.DMN(el), dmn.DMN(base, line_search=True)
+    t_el = dmn.DMN(W.TreeParams(K, 3, target.p, target.q, target.w, (W.FIBER, EL_MATRIX)))
+    t_pl = dmn.DMN(target, line_search=True)
+    z = lambda nn: torch.zeros((m_pl.state_size, nn), dtype=torch.float64, device=DEV)
+    zE = torch.zeros((npl, 6), dtype=torch.float64, device=DEV)
+    with torch.no_grad():
+        C_t = ag.dmn_stiffness(t_el, d(lame), d(Qe), d(target.p), d(target.q), d(target.w))
+        s_t = ag.dmn_stress(t_pl, d(lamp), d(Qp), zE, d(Ep), z(npl), d(target.p), d(target.q), d(target.w))[0]
+
+    def loss(p, q, w):
+        C = ag.dmn_stiffness(m_el, d(lame), d(Qe), p, q, w)
+        s, _, stat = ag.dmn_stress(m_pl, d(lamp), d(Qp), zE, d(Ep), z(npl), p, q, w)
+        assert (stat == 0).all()
+        le = (torch.linalg.norm((C - C_t).reshape(ne, -1), dim=1) / torch.linalg.norm(C_t.reshape(ne, -1), dim=1)).mean()
+        lp = (torch.linalg.norm(s - s_t, dim=1) / torch.linalg.norm(s_t, dim=1)).mean()
+        return le + lp
+
+    p = d(base.p).requires_grad_()
+    q = d(base.q).requires_grad_()
+    w = d(base.w).requires_grad_()
+    L = loss(p, q, w)
+    L.backward()
+    h = 1e-6
+    for trial in range(3):
+        dp, dq = rng.standard_normal(base.p.shape), rng.standard_normal(base.q.shape)
+        dw = rng.standard_normal(base.w.shape) * base.w
+        pred = float((p.grad.cpu().numpy() * dp).sum() + (q.grad.cpu().numpy() * dq).sum()
+                     + (w.grad.cpu().numpy() * dw).sum())
+        with torch.no_grad():
+            Lp = loss(d(base.p + h * dp), d(base.q + h * dq), d(base.w + h * dw)).item()
+            Lm = loss(d(base.p - h * dp), d(base.q - h * dq), d(base.w - h * dw)).item()
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(pred - fd) <= 1e-5 * abs(fd), (trial, pred, fd)
