@@ -387,6 +387,127 @@ def roofline_mixed(r, n, steps):
             "flops_f32_per_launch": F32 / steps, "launch_ms": r["kms"]["newton"] / steps, "final_kernel": fin}
 
 
+# ---------------------------------------------------------------------------------------------
+# Mixed-depth batch: 4M points, depths 5/6/7/8 (25 % each), half loaded in the elastic range
+# (proportional ramp to 0.1 % equivalent strain), half cyclic +-2 % (one triangle period over
+# 40 increments), shuffled; one persistent launch per increment, a CUDA graph over a block of
+# increments, autotuned launch shape.  A secondary measurement (not the headline line).
+MD_DEPTHS = (5, 6, 7, 8)
+MD_INCREMENTS = 40
+
+
+def run_mixed_depth(args):
+    import torch
+    from paper_2103_08253_gb300 import autotune, dmn
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n = args.points
+    trees = [W.tree_d10_fit(K, seed=SEED_TREE + K) for K in MD_DEPTHS]
+    tid, elastic = W.mixed_depth_batch(n, SEED_ORI + 7, MD_DEPTHS)
+    A2, lam_np, Q_np = W.orientation_field(n, seed=SEED_ORI + 8)
+    Edir = W.random6_path_final(n, 1.0, seed=SEED_PATH + 9)
+    amp = np.where(elastic, 0.001, 0.02)[:, None] * Edir
+    G = args.steps                      # increments per graph replay
+    first = args.warmup + 1
+    inc = list(range(first, first + G))
+
+    def inputs(k):
+        En_c, dE_c = W.cyclic_increment(amp, k, MD_INCREMENTS)
+        En_r, dE_r = W.proportional_increment(amp, k, MD_INCREMENTS)
+        e = elastic[:, None]
+        return (torch.from_numpy(np.where(e, En_r, En_c)).to(dev), torch.from_numpy(np.where(e, dE_r, dE_c)).to(dev))
+
+    A2_d, tid_d = torch.from_numpy(A2).to(dev), torch.from_numpy(tid).to(dev)
+    line = {"metric": "DMN Gauss-point updates/s, mixed depths 5-8, cyclic + elastic-range batch", "unit": UNIT,
+            "n_gpus": 1, "steps": G, "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "4M points, depths 5/6/7/8 x 25%%, half elastic-range 0.1%%, half cyclic +-2%% over "
+                                   "%d increments, shuffled" % MD_INCREMENTS, "points": n,
+                       "timed_increments": [inc[0], inc[-1]], "graph": "one CUDA graph of %d increments" % G},
+            "forms": {}}
+    for form in [f for f in args.forms.split(",") if f]:
+        # autotuned shape on 2^18 points of the batch at the first timed increment
+        m0 = dmn.DMN(trees, precision=form)
+        msub = min(n, 1 << 18)
+        lam_s, Q_s = m0.interp_orientation(A2_d[:msub].contiguous())
+        st = torch.zeros((m0.state_size, msub), dtype=torch.float64, device=dev)
+        for k in range(1, first):
+            En, dE = inputs(k)
+            st = m0.update(lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st,
+                           tree_id=tid_d[:msub].contiguous())["state_out"]
+        m0.close()
+        # autotune over the single-tree API is not available for several trees: time the candidates here
+        best = None
+        En, dE = inputs(first)
+        for block, cps in ((128, 2), (128, 3), (128, 4), (64, 6)):
+            mm = dmn.DMN(trees, precision=form, block=block, ctas_per_sm=cps)
+            o = mm.update(lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st, tree_id=tid_d[:msub].contiguous())
+            torch.cuda.synchronize()
+            mm.profile(True)
+            mm.update(lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st, out=o, tree_id=tid_d[:msub].contiguous())
+            kms, _ = mm.profile_read()
+            mm.close()
+            del o
+            if best is None or kms["newton"] < best[2]:
+                best = (block, cps, kms["newton"])
+        del st
+        torch.cuda.empty_cache()
+        m = dmn.DMN(trees, precision=form, block=best[0], ctas_per_sm=best[1])
+        lam, Q = m.interp_orientation(A2_d)
+        S = m.state_size
+        bufs = [torch.zeros((S, n), dtype=torch.float64, device=dev) for _ in range(2)]
+        outs = [None] * G
+        for j in range(G):
+            outs[j] = dict(stress=torch.empty((n, 6), dtype=torch.float64, device=dev),
+                           tangent=torch.empty((n, 6, 6), dtype=torch.float64, device=dev),
+                           iters=torch.empty(n, dtype=torch.int32, device=dev),
+                           status=torch.empty(n, dtype=torch.int32, device=dev))
+        for k in range(1, first):       # warm-up increments, eager
+            En, dE = inputs(k)
+            o = dict(outs[0], state_out=bufs[k % 2])
+            m.update(lam, Q, En, dE, bufs[(k - 1) % 2], out=o, tree_id=tid_d)
+        En_all, dE_all = zip(*[inputs(k) for k in inc])
+        base = (first - 1) % 2
+        for j in range(G):
+            outs[j]["state_out"] = bufs[(base + j + 1) % 2]
+        # the graph: increments first .. first+G-1, state ping-pong between the two buffers
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                for j in range(G):
+                    m.update(lam, Q, En_all[j], dE_all[j], bufs[(base + j) % 2], out=outs[j], tree_id=tid_d)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        clocks = ClockSampler("0")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        t_ms = e0.elapsed_time(e1)
+        its = torch.stack([o["iters"] for o in outs]).to(torch.int64)
+        stat = torch.stack([o["status"] for o in outs])
+        el = torch.from_numpy(elastic).to(dev)
+        line["forms"][form] = {
+            "value": n * G / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms / G,
+            "launch": {"block": best[0], "ctas_per_sm": best[1]},
+            "iters_elastic_half": torch.bincount(its[:, el].reshape(-1)).cpu().tolist(),
+            "iters_cyclic_half": torch.bincount(its[:, ~el].reshape(-1)).cpu().tolist(),
+            "status_counts": torch.bincount(stat.reshape(-1).to(torch.int64)).cpu().tolist(),
+            "clocks": clk}
+        del g, outs, bufs, En_all, dE_all
+        m.close()
+        torch.cuda.empty_cache()
+    main_form = "f64" if "f64" in line["forms"] else next(iter(line["forms"]))
+    line["value"] = line["forms"][main_form]["value"]
+    line["dtype"] = "f64" if main_form == "f64" else "f32+f64"
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,7 +522,13 @@ def main():
     ap.add_argument("--parity-points", type=int, default=16)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the library's default launch shape instead of autotuning it")
+    ap.add_argument("--workload", default="k8", choices=["k8", "mixed-depth"],
+                    help="k8: the headline depth-8 batch; mixed-depth: 4M points of depths 5-8 (secondary)")
     args = ap.parse_args()
+    if args.workload == "mixed-depth":
+        if args.points == 1 << 20:
+            args.points = 1 << 22
+        return run_mixed_depth(args)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.warmup + args.steps > N_INCREMENTS:
