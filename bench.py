@@ -310,56 +310,40 @@ def parity_sample(form, r, ctx, args, pidx):
 
 
 def run_e2e(r, ctx, args, dist):
-    """Same increments through the public API with host buffers: H2D of the step's inputs and
-    D2H of its results inside the timed region (FP64 form)."""
+    """Same increments through the public API with host buffers (dmn_update_host, FP64 form): every
+    step copies its inputs (orientation, strains, state) from pinned host memory and its results
+    (stress, tangent, iterations, status, state) back; the chunked pipeline of the library overlaps
+    those copies with the updates.  Wall-clock time of the blocking calls."""
     import torch
-    dev, n, S = ctx["dev"], ctx["n"], r["S"]
+    n, S = ctx["n"], r["S"]
     m = r["m"]
     steps = min(args.e2e_steps, args.steps)
-    pin = dict(dtype=torch.float64, pin_memory=True)
-    A2_h = torch.from_numpy(ctx["A2_np"]).pin_memory()
+    lam_h = r["lam"].cpu().pin_memory()
+    Q_h = r["Q"].cpu().pin_memory()
     En_h = [ctx["En"][s - 1].cpu().pin_memory() for s in range(args.warmup + 1, args.warmup + steps + 1)]
     dE_h = [ctx["dE"][s - 1].cpu().pin_memory() for s in range(args.warmup + 1, args.warmup + steps + 1)]
-    hs = [r["host_state"], torch.empty((S, n), **pin)]
-    out_h = dict(stress=torch.empty((n, 6), **pin), tangent=torch.empty((n, 6, 6), **pin),
-                 iters=torch.empty(n, dtype=torch.int32, pin_memory=True),
-                 status=torch.empty(n, dtype=torch.int32, pin_memory=True))
-    A2_d = torch.empty((n, 6), dtype=torch.float64, device=dev)
-    En_d = torch.empty((n, 6), dtype=torch.float64, device=dev)
-    dE_d = torch.empty((n, 6), dtype=torch.float64, device=dev)
-    st_in, st_out = r["st"][0], r["st"][1]
-    out = m.alloc_outputs(n, dev)
-    out["state_out"] = st_out
-    lam, Q = r["lam"], r["Q"]
-    h2d = A2_h.nbytes + En_h[0].nbytes + dE_h[0].nbytes + hs[0].nbytes
-    d2h = out_h["stress"].nbytes + out_h["tangent"].nbytes + hs[1].nbytes + out_h["iters"].nbytes + out_h["status"].nbytes
+    st_h = r["host_state"]                        # state after the warm-up increments, updated in place
+    out_h = m.alloc_host_outputs(n)
+    out_h["state_out"] = st_h
+    h2d = lam_h.nbytes + Q_h.nbytes + En_h[0].nbytes + dE_h[0].nbytes + st_h.nbytes
+    d2h = (out_h["stress"].nbytes + out_h["tangent"].nbytes + st_h.nbytes + out_h["iters"].nbytes
+           + out_h["status"].nbytes)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    cur = 0
+    t0 = time.perf_counter()
     for j in range(steps):
-        A2_d.copy_(A2_h, non_blocking=True)
-        En_d.copy_(En_h[j], non_blocking=True)
-        dE_d.copy_(dE_h[j], non_blocking=True)
-        st_in.copy_(hs[cur], non_blocking=True)
-        m.interp_orientation(A2_d, lam, Q)
-        m.update(lam, Q, En_d, dE_d, st_in, out=out)
-        for k in ("stress", "tangent", "iters", "status"):
-            out_h[k].copy_(out[k], non_blocking=True)
-        hs[1 - cur].copy_(st_out, non_blocking=True)
-        cur = 1 - cur
-    e1.record()
-    torch.cuda.synchronize()
-    t_ms = e0.elapsed_time(e1)
+        m.update_host(lam_h, Q_h, En_h[j], dE_h[j], st_h, out=out_h, chunk=args.e2e_chunk)
+    t_ms = 1e3 * (time.perf_counter() - t0)
     if dist:
-        t = torch.tensor([t_ms], device=dev)
+        t = torch.tensor([t_ms], device=ctx["dev"])
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_ms = float(t.item())
     world = dist.get_world_size() if dist else 1
     return {"value": world * n * steps / (t_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": steps, "form": "f64"}
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "form": "f64", "ms_per_step": t_ms / steps,
+            "api": "dmn_update_host", "chunk": args.e2e_chunk or "default",
+            "status_ok": int((out_h["status"] == 0).sum().item())}
 
 
 def roofline_f64(r, n, steps):
@@ -516,6 +500,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--points", type=int, default=1 << 20)
     ap.add_argument("--forms", default="f64,mixed")
+    ap.add_argument("--e2e-chunk", type=int, default=0,
+                    help="points per chunk of dmn_update_host (0: the library's default)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-points", type=int, default=1024)
     ap.add_argument("--cpu-points", type=int, default=1024)

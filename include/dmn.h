@@ -165,6 +165,32 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
                const double* E_n, const double* dE, const double* state_in, double* state_out, double* stress,
                double* tangent, int32_t* iters, int32_t* status, void* stream);
 
+/* The update of dmn_update for arrays in HOST memory, the form a finite-element
+ * code calls per Gauss-point batch (the UMAT call of Sec. 5).  Same arguments,
+ * layouts and results as dmn_update, all arrays host arrays:
+ *   tree_id [n] or NULL, lam [n][2], Q [n][9], E_n, dE [n][6] in;
+ *   state_in, state_out [S][n] with S = dmn_state_size(h, -1), row pitch n;
+ *   stress [n][6], tangent [n][36], iters, status [n] out.
+ * Unlike dmn_update, state_out may be state_in itself (each point's state is
+ * read before it is written), and a point of an unknown tree (status
+ * BAD_TREE) gets its state_in as state_out.  The points are processed in chunks of `chunk`
+ * points (<= 0: twice the resident lanes of the Newton kernel) through two
+ * stages of device buffers owned by the handle, on streams of the handle: the
+ * copy-in of chunk j+1 and the copy-out of chunk j-1 overlap the update of
+ * chunk j, and the updates of consecutive chunks may overlap (the two stages
+ * use separate work space).  Work queued earlier on `stream` is waited for;
+ * the call returns when every copy has ended, so the host arrays may be
+ * reused at once.  Pinned host memory (cudaHostAlloc / cudaHostRegister)
+ * gives overlapped copies; pageable memory works, slower.  The first call,
+ * and a call with a larger chunk than any before, allocate the stage buffers
+ * (about 2 x chunk x (2 S + 67) x 8 bytes) and a second Newton work space.
+ * Not for stream capture.  Errors: DMN_ERR_ARG for n < 0 or NULL arrays with
+ * n > 0; DMN_ERR_CUDA if a CUDA call fails (the call still waits for the
+ * copies it queued). */
+int dmn_update_host(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam, const double* Q,
+                    const double* E_n, const double* dE, const double* state_in, double* state_out, double* stress,
+                    double* tangent, int32_t* iters, int32_t* status, int64_t chunk, void* stream);
+
 /* Replace the parameters of tree tree_id (host arrays laid out as in
  * dmn_tree_desc: p, q [(2^K-1) * M] in the paper's ordering, w [2^K] > 0),
  * e.g. after an optimiser step of the offline training (Sec. 3.1).  Depth,

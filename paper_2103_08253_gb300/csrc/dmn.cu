@@ -45,6 +45,28 @@ struct Tree {
 
 }  // namespace
 
+// Work space of one update in flight: the per-lane scratch of the persistent
+// Newton kernel, its counters and the per-point buffers.  Updates that may run at
+// the same time (the two stages of dmn_update_host) use separate work sets.
+struct WorkSet {
+  double* scr_d = nullptr;      // per slot: normals [3N] + jumps [3N] (FP64)
+  void* scr_t = nullptr;        // per slot: g, H [21N] (FP64 or FP32) + FP32 normals [3N]
+  unsigned long long* counter = nullptr;  // [0] work counter, [1..9] points per tree, [10..18] cursors
+  double* nbuf = nullptr;       // per point: normals [3N] + local macro strain [6], field-major
+  int64_t* perm = nullptr;      // points sorted by tree (several trees)
+  int64_t nbuf_cap = 0;
+};
+
+// Device buffers, streams and events of dmn_update_host: two stages, each with
+// room for one chunk of points.
+struct HostPipe {
+  int64_t cap = 0;              // points per stage
+  char* buf[2] = {nullptr, nullptr};
+  cudaStream_t up = nullptr, down = nullptr, comp[2] = {nullptr, nullptr};
+  cudaEvent_t start = nullptr, h2d[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr},
+              d2h[2] = {nullptr, nullptr};
+};
+
 struct dmn_handle {
   std::vector<Tree> trees;
   int N_max = 0;                // laminates of the deepest tree
@@ -52,14 +74,10 @@ struct dmn_handle {
   dmn_options opt;
   int device = 0, n_sm = 0;
   int64_t nslots = 0;
-  double* scr_d = nullptr;      // per slot: normals [3N] + jumps [3N] (FP64)
-  void* scr_t = nullptr;        // per slot: g, H [21N] (FP64 or FP32) + FP32 normals [3N]
-  unsigned long long* counter = nullptr;  // [0] work counter, [1..9] points per tree, [10..18] cursors
-  double* nbuf = nullptr;       // per point: normals [3N] + local macro strain [6], field-major
-  int64_t* perm = nullptr;      // points sorted by tree (several trees)
+  WorkSet ws[2];                // [0]: dmn_update; [1]: second stage of dmn_update_host
+  HostPipe hp;
   double* gwork = nullptr;      // dmn_grad per-point work, one chunk
   int64_t gwork_cap = 0;
-  int64_t nbuf_cap = 0;
   bool profiling = false;
   std::vector<std::array<cudaEvent_t, 4>> events;  // per timed update: before/after each kernel
   size_t events_used = 0;
@@ -733,6 +751,179 @@ const char* check_tree(const dmn_tree_desc& d) {
 // ============================================================================
 // C ABI
 
+namespace {
+
+// Per-slot scratch and counters of one work set (per-point buffers come with the first update).
+cudaError_t alloc_ws(const dmn_handle* h, WorkSet& w) {
+  // per slot: normals + one or two jump buffers (FP64); one or two g, H buffers + FP32 normals
+  const size_t sd = h->opt.line_search ? 9 : 6, stt = h->opt.line_search ? 45 : 24;
+  cudaError_t e = cudaMalloc(&w.scr_d, sizeof(double) * (size_t)(sd * h->N_max) * h->nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&w.scr_t, sizeof(double) * (size_t)(stt * h->N_max) * h->nslots);
+  if (e == cudaSuccess) e = cudaMalloc(&w.counter, sizeof(unsigned long long) * 32);
+  return e;
+}
+
+void free_ws(WorkSet& w) {
+  cudaFree(w.scr_d); cudaFree(w.scr_t); cudaFree(w.counter); cudaFree(w.nbuf); cudaFree(w.perm);
+  w = WorkSet();
+}
+
+void free_pipe(HostPipe& p) {
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(p.buf[b]);
+    if (p.comp[b]) cudaStreamDestroy(p.comp[b]);
+    if (p.h2d[b]) cudaEventDestroy(p.h2d[b]);
+    if (p.done[b]) cudaEventDestroy(p.done[b]);
+    if (p.d2h[b]) cudaEventDestroy(p.d2h[b]);
+  }
+  if (p.up) cudaStreamDestroy(p.up);
+  if (p.down) cudaStreamDestroy(p.down);
+  if (p.start) cudaEventDestroy(p.start);
+  p = HostPipe();
+}
+
+// One update on work set w and stream s (the body of dmn_update; arguments checked by the caller).
+int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, const double* lam, const double* Q,
+              const double* E_n, const double* dE, const double* state_in, double* state_out, double* stress,
+              double* tangent, int32_t* iters, int32_t* status, cudaStream_t s) {
+  cudaError_t e;
+  const int NM = h->N_max;
+  const bool sort = tree_id && h->trees.size() > 1;
+  if (n > w.nbuf_cap) {
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      cudaFree(w.nbuf); cudaFree(w.perm);
+      w.nbuf = nullptr; w.perm = nullptr; w.nbuf_cap = 0;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&w.nbuf, sizeof(double) * (size_t)(3 * NM + 6) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&w.perm, sizeof(int64_t) * (size_t)n);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: per-point buffer");
+    w.nbuf_cap = n;
+  }
+  Forest F;
+  F.n = (int)h->trees.size();
+  for (int k = 0; k < F.n; ++k) F.t[k] = tree_dev(h->trees[k]);
+  const unsigned g1 = (unsigned)div_up(n, 128);
+  cudaEvent_t* ev = nullptr;
+  if (h->profiling) {
+    if (h->events_used == h->events.size()) {
+      std::array<cudaEvent_t, 4> a;
+      for (auto& x : a) {
+        e = cudaEventCreate(&x);
+        if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: profiling event");
+      }
+      h->events.push_back(a);
+    }
+    ev = h->events[h->events_used++].data();
+    cudaEventRecord(ev[0], s);
+  }
+  // counters: [0] work, [1..9] points per tree, [10..18] cursors
+  e = cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long) * 32, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: counter reset");
+  const int64_t* perm = nullptr;
+  if (sort) {
+    k_tree_count<<<g1, 128, 0, s>>>(n, tree_id, F.n, w.counter + 1);
+    k_tree_offsets<<<1, 1, 0, s>>>(F.n, w.counter + 1, w.counter + 10);
+    k_tree_scatter<<<g1, 128, 0, s>>>(n, tree_id, F.n, w.counter + 10, w.perm);
+    perm = w.perm;
+  }
+  k_prepare<<<g1, 128, 0, s>>>(F, n, tree_id, perm, lam, Q, E_n, dE, w.nbuf, NM);
+  if (ev) cudaEventRecord(ev[1], s);
+  const unsigned grid = (unsigned)(h->n_sm * h->opt.ctas_per_sm);
+  const bool mixed = h->opt.precision == DMN_PREC_MIXED;
+  const int threads_per_sm = h->opt.block * h->opt.ctas_per_sm;
+  const int minb = threads_per_sm > 384 ? 4 : threads_per_sm > 256 ? 3 : 2;
+  const bool ls = h->opt.line_search != 0;
+  if (!mixed) {
+    NewtonParams<double> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
+                           w.nbuf, w.scr_d, (double*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 1};
+    if (ls) k_newton<double, 2, true><<<grid, h->opt.block, 0, s>>>(P);
+    else if (minb == 2) k_newton<double, 2, false><<<grid, h->opt.block, 0, s>>>(P);
+    else if (minb == 3) k_newton<double, 3, false><<<grid, h->opt.block, 0, s>>>(P);
+    else k_newton<double, 4, false><<<grid, h->opt.block, 0, s>>>(P);
+  } else {
+    NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
+                          w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 0};
+    if (ls) k_newton<float, 2, true><<<grid, h->opt.block, 0, s>>>(P);
+    else if (minb == 2) k_newton<float, 2, false><<<grid, h->opt.block, 0, s>>>(P);
+    else if (minb == 3) k_newton<float, 3, false><<<grid, h->opt.block, 0, s>>>(P);
+    else k_newton<float, 4, false><<<grid, h->opt.block, 0, s>>>(P);
+  }
+  if (ev) cudaEventRecord(ev[2], s);
+  FinalParams FP{F, n, NM, tree_id, perm, Q, state_in, state_out, stress, tangent, status, w.nbuf};
+  if (mixed) k_final<true><<<g1, 128, 0, s>>>(FP);
+  else k_final<false><<<g1, 128, 0, s>>>(FP);
+  if (ev) cudaEventRecord(ev[3], s);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? DMN_OK : cuda_fail(h, e, "dmn_update: launch");
+}
+
+// Device buffers of one dmn_update_host stage, carved out of one allocation.
+struct StageView {
+  int32_t *tid, *iters, *status;
+  double *lam, *Q, *E_n, *dE, *state_in, *state_out, *stress, *tangent;
+};
+
+size_t stage_layout(int64_t cap, int64_t S, char* base, StageView* v) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off += (bytes + 255) & ~size_t(255);
+    return p;
+  };
+  const size_t c = (size_t)cap;
+  StageView t;
+  t.tid = (int32_t*)take(4 * c);
+  t.iters = (int32_t*)take(4 * c);
+  t.status = (int32_t*)take(4 * c);
+  t.lam = (double*)take(16 * c);
+  t.Q = (double*)take(72 * c);
+  t.E_n = (double*)take(48 * c);
+  t.dE = (double*)take(48 * c);
+  t.stress = (double*)take(48 * c);
+  t.tangent = (double*)take(288 * c);
+  t.state_in = (double*)take(8 * c * (size_t)S);
+  t.state_out = (double*)take(8 * c * (size_t)S);
+  if (v) *v = t;
+  return off;
+}
+
+// Streams, events, the second work set and stage buffers for chunks of `cap` points.
+cudaError_t pipe_ready(dmn_handle* h, int64_t cap) {
+  HostPipe& P = h->hp;
+  cudaError_t e = cudaSuccess;
+  if (!P.up) {
+    e = cudaStreamCreateWithFlags(&P.up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P.down, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaStreamCreateWithFlags(&P.comp[b], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.h2d[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.done[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.d2h[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.start, cudaEventDisableTiming);
+    if (e != cudaSuccess) { free_pipe(P); return e; }
+  }
+  if (!h->ws[1].scr_d) {
+    e = alloc_ws(h, h->ws[1]);
+    if (e != cudaSuccess) { free_ws(h->ws[1]); return e; }
+  }
+  if (cap > P.cap) {
+    for (int b = 0; b < 2; ++b) { cudaFree(P.buf[b]); P.buf[b] = nullptr; }
+    P.cap = 0;
+    const size_t bytes = stage_layout(cap, h->S_max, nullptr, nullptr);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&P.buf[b], bytes);
+    if (e != cudaSuccess) {
+      for (int b = 0; b < 2; ++b) { cudaFree(P.buf[b]); P.buf[b] = nullptr; }
+      return e;
+    }
+    P.cap = cap;
+  }
+  return e;
+}
+
+}  // namespace
+
 extern "C" {
 
 int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* opt, dmn_handle** out) {
@@ -820,11 +1011,7 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   }
   cudaFree(d_w);
   h->nslots = (int64_t)h->n_sm * o.ctas_per_sm * o.block;
-  // per slot: normals + one or two jump buffers (FP64); one or two g, H buffers + FP32 normals
-  const size_t sd = o.line_search ? 9 : 6, stt = o.line_search ? 45 : 24;
-  if (e == cudaSuccess) e = cudaMalloc(&h->scr_d, sizeof(double) * (size_t)(sd * N_max) * h->nslots);
-  if (e == cudaSuccess) e = cudaMalloc(&h->scr_t, sizeof(double) * (size_t)(stt * N_max) * h->nslots);
-  if (e == cudaSuccess) e = cudaMalloc(&h->counter, sizeof(unsigned long long) * 32);
+  if (e == cudaSuccess) e = alloc_ws(h, h->ws[0]);
   if (e != cudaSuccess) {
     dmn_destroy(h);
     return cuda_fail(nullptr, e, "dmn_create");
@@ -839,7 +1026,8 @@ void dmn_destroy(dmn_handle* h) {
   for (auto& a : h->events)
     for (auto& x : a) cudaEventDestroy(x);
   for (auto& t : h->trees) { cudaFree(t.d_p); cudaFree(t.d_q); cudaFree(t.d_c); cudaFree(t.d_cf); }
-  cudaFree(h->scr_d); cudaFree(h->scr_t); cudaFree(h->counter); cudaFree(h->nbuf); cudaFree(h->perm);
+  for (auto& w : h->ws) free_ws(w);
+  free_pipe(h->hp);
   cudaFree(h->gwork);
   delete h;
 }
@@ -899,77 +1087,84 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
   if (!lam || !Q || !E_n || !dE || !state_in || !state_out || !stress || !tangent || !iters || !status)
     return fail(h, DMN_ERR_ARG, "dmn_update: NULL array");
   if (state_in == state_out) return fail(h, DMN_ERR_ARG, "dmn_update: state_in and state_out must differ");
+  return update_on(h, h->ws[0], n, tree_id, lam, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status,
+                   (cudaStream_t)stream);
+}
+
+int dmn_update_host(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam, const double* Q,
+                    const double* E_n, const double* dE, const double* state_in, double* state_out, double* stress,
+                    double* tangent, int32_t* iters, int32_t* status, int64_t chunk, void* stream) {
+  if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_update_host: NULL handle");
+  if (n < 0) return fail(h, DMN_ERR_ARG, "dmn_update_host: n < 0");
+  if (n == 0) return DMN_OK;
+  if (!lam || !Q || !E_n || !dE || !state_in || !state_out || !stress || !tangent || !iters || !status)
+    return fail(h, DMN_ERR_ARG, "dmn_update_host: NULL array");
+  if (chunk <= 0) chunk = 2 * h->nslots;
+  chunk = std::min(chunk, n);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e;
-  const int NM = h->N_max;
-  const bool sort = tree_id && h->trees.size() > 1;
-  if (n > h->nbuf_cap) {
-    e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) {
-      cudaFree(h->nbuf); cudaFree(h->perm);
-      h->nbuf = nullptr; h->perm = nullptr; h->nbuf_cap = 0;
-    }
-    if (e == cudaSuccess) e = cudaMalloc(&h->nbuf, sizeof(double) * (size_t)(3 * NM + 6) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&h->perm, sizeof(int64_t) * (size_t)n);
-    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: per-point buffer");
-    h->nbuf_cap = n;
+  // the stage buffers may still be read by the copies of an earlier call that failed
+  HostPipe& P = h->hp;
+  if (P.up && chunk > P.cap) {
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t x : {P.up, P.comp[0], P.comp[1], P.down})
+      if (e == cudaSuccess) e = cudaStreamSynchronize(x);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update_host: pipeline");
   }
-  Forest F;
-  F.n = (int)h->trees.size();
-  for (int k = 0; k < F.n; ++k) F.t[k] = tree_dev(h->trees[k]);
-  const unsigned g1 = (unsigned)div_up(n, 128);
-  cudaEvent_t* ev = nullptr;
-  if (h->profiling) {
-    if (h->events_used == h->events.size()) {
-      std::array<cudaEvent_t, 4> a;
-      for (auto& x : a) {
-        e = cudaEventCreate(&x);
-        if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: profiling event");
-      }
-      h->events.push_back(a);
-    }
-    ev = h->events[h->events_used++].data();
-    cudaEventRecord(ev[0], s);
+  cudaError_t e = pipe_ready(h, chunk);
+  if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update_host: pipeline buffers");
+  StageView v[2];
+  for (int b = 0; b < 2; ++b) stage_layout(P.cap, h->S_max, P.buf[b], &v[b]);
+  const int64_t S = h->S_max;
+  const size_t host_pitch = sizeof(double) * (size_t)n;
+  // work already queued on the caller's stream (an update on work set 0) comes first
+  e = cudaEventRecord(P.start, s);
+  for (cudaStream_t x : {P.up, P.comp[0], P.comp[1]})
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(x, P.start, 0);
+  int rc = e == cudaSuccess ? DMN_OK : cuda_fail(h, e, "dmn_update_host: stream order");
+  const auto H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
+  for (int64_t j = 0, n0 = 0; rc == DMN_OK && n0 < n; ++j, n0 += chunk) {
+    const int b = (int)(j & 1);
+    const int64_t c = std::min(chunk, n - n0);
+    const size_t c8 = sizeof(double) * (size_t)c;
+    const StageView& V = v[b];
+    // inputs of chunk j, once the update of chunk j - 2 (same stage) has read its own
+    if (j >= 2) e = cudaStreamWaitEvent(P.up, P.done[b], 0);
+    if (e == cudaSuccess && tree_id) e = cudaMemcpyAsync(V.tid, tree_id + n0, 4 * (size_t)c, H2D, P.up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(V.lam, lam + 2 * n0, 2 * c8, H2D, P.up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(V.Q, Q + 9 * n0, 9 * c8, H2D, P.up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(V.E_n, E_n + 6 * n0, 6 * c8, H2D, P.up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(V.dE, dE + 6 * n0, 6 * c8, H2D, P.up);
+    if (e == cudaSuccess) e = cudaMemcpy2DAsync(V.state_in, c8, state_in + n0, host_pitch, c8, (size_t)S, H2D, P.up);
+    if (e == cudaSuccess) e = cudaEventRecord(P.h2d[b], P.up);
+    // the update, once its inputs are in and the outputs of chunk j - 2 are out
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.comp[b], P.h2d[b], 0);
+    if (e == cudaSuccess && j >= 2) e = cudaStreamWaitEvent(P.comp[b], P.d2h[b], 0);
+    // a point of an unknown tree leaves its state_out untouched: give it state_in, so that
+    // the copy-out returns the point's state unchanged rather than stale stage contents
+    if (e == cudaSuccess && tree_id)
+      e = cudaMemcpyAsync(V.state_out, V.state_in, c8 * (size_t)S, cudaMemcpyDeviceToDevice, P.comp[b]);
+    if (e != cudaSuccess) { rc = cuda_fail(h, e, "dmn_update_host: copy in"); break; }
+    rc = update_on(h, h->ws[b], c, tree_id ? V.tid : nullptr, V.lam, V.Q, V.E_n, V.dE, V.state_in, V.state_out,
+                   V.stress, V.tangent, V.iters, V.status, P.comp[b]);
+    if (rc != DMN_OK) break;
+    e = cudaEventRecord(P.done[b], P.comp[b]);
+    // outputs of chunk j
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.down, P.done[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stress + 6 * n0, V.stress, 6 * c8, D2H, P.down);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tangent + 36 * n0, V.tangent, 36 * c8, D2H, P.down);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(iters + n0, V.iters, 4 * (size_t)c, D2H, P.down);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status + n0, V.status, 4 * (size_t)c, D2H, P.down);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(state_out + n0, host_pitch, V.state_out, c8, c8, (size_t)S, D2H, P.down);
+    if (e == cudaSuccess) e = cudaEventRecord(P.d2h[b], P.down);
+    if (e != cudaSuccess) rc = cuda_fail(h, e, "dmn_update_host: copy out");
   }
-  // counters: [0] work, [1..9] points per tree, [10..18] cursors
-  e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned long long) * 32, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: counter reset");
-  const int64_t* perm = nullptr;
-  if (sort) {
-    k_tree_count<<<g1, 128, 0, s>>>(n, tree_id, F.n, h->counter + 1);
-    k_tree_offsets<<<1, 1, 0, s>>>(F.n, h->counter + 1, h->counter + 10);
-    k_tree_scatter<<<g1, 128, 0, s>>>(n, tree_id, F.n, h->counter + 10, h->perm);
-    perm = h->perm;
+  // the host arrays are in use until every copy has ended: wait for all four streams
+  for (cudaStream_t x : {P.up, P.comp[0], P.comp[1], P.down}) {
+    e = cudaStreamSynchronize(x);
+    if (e != cudaSuccess && rc == DMN_OK) rc = cuda_fail(h, e, "dmn_update_host: pipeline");
   }
-  k_prepare<<<g1, 128, 0, s>>>(F, n, tree_id, perm, lam, Q, E_n, dE, h->nbuf, NM);
-  if (ev) cudaEventRecord(ev[1], s);
-  const unsigned grid = (unsigned)(h->n_sm * h->opt.ctas_per_sm);
-  const bool mixed = h->opt.precision == DMN_PREC_MIXED;
-  const int threads_per_sm = h->opt.block * h->opt.ctas_per_sm;
-  const int minb = threads_per_sm > 384 ? 4 : threads_per_sm > 256 ? 3 : 2;
-  const bool ls = h->opt.line_search != 0;
-  if (!mixed) {
-    NewtonParams<double> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
-                           h->nbuf, h->scr_d, (double*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 1};
-    if (ls) k_newton<double, 2, true><<<grid, h->opt.block, 0, s>>>(P);
-    else if (minb == 2) k_newton<double, 2, false><<<grid, h->opt.block, 0, s>>>(P);
-    else if (minb == 3) k_newton<double, 3, false><<<grid, h->opt.block, 0, s>>>(P);
-    else k_newton<double, 4, false><<<grid, h->opt.block, 0, s>>>(P);
-  } else {
-    NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
-                          h->nbuf, h->scr_d, (float*)h->scr_t, h->counter, h->opt.tol, h->opt.max_iter, 0};
-    if (ls) k_newton<float, 2, true><<<grid, h->opt.block, 0, s>>>(P);
-    else if (minb == 2) k_newton<float, 2, false><<<grid, h->opt.block, 0, s>>>(P);
-    else if (minb == 3) k_newton<float, 3, false><<<grid, h->opt.block, 0, s>>>(P);
-    else k_newton<float, 4, false><<<grid, h->opt.block, 0, s>>>(P);
-  }
-  if (ev) cudaEventRecord(ev[2], s);
-  FinalParams FP{F, n, NM, tree_id, perm, Q, state_in, state_out, stress, tangent, status, h->nbuf};
-  if (mixed) k_final<true><<<g1, 128, 0, s>>>(FP);
-  else k_final<false><<<g1, 128, 0, s>>>(FP);
-  if (ev) cudaEventRecord(ev[3], s);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? DMN_OK : cuda_fail(h, e, "dmn_update: launch");
+  return rc;
 }
 
 int dmn_set_params(dmn_handle* h, int32_t tree_id, const double* p, const double* q, const double* w) {

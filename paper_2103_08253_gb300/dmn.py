@@ -18,7 +18,7 @@ _lib = None
 # ABI symbols declared in include/dmn.h
 EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_interp_orientation", "dmn_update",
            "dmn_set_params", "dmn_grad", "dmn_profile_enable", "dmn_profile_read", "dmn_update_noalloc",
-           "dmn_last_error")
+           "dmn_update_host", "dmn_last_error")
 
 PREC_F64 = 0
 PREC_MIXED = 1
@@ -69,6 +69,8 @@ def load_library(build_if_missing: bool = True):
     lib.dmn_interp_orientation.restype = ctypes.c_int
     lib.dmn_update.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.dmn_update.restype = ctypes.c_int
+    lib.dmn_update_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp]
+    lib.dmn_update_host.restype = ctypes.c_int
     lib.dmn_set_params.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]
     lib.dmn_set_params.restype = ctypes.c_int
@@ -92,6 +94,18 @@ def _check_dev(name, t, dtype, shape):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+
+
+def _check_host(name, t, dtype, shape):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise TypeError("%s must be a CPU tensor" % name)
     if t.dtype != dtype:
         raise TypeError("%s must be %s" % (name, dtype))
     if not t.is_contiguous():
@@ -256,4 +270,41 @@ class DMN:
                                   _ptr(out["iters"]), _ptr(out["status"]), ctypes.c_void_p(s))
         if rc != 0:
             self._err("dmn_update", rc)
+        return out
+
+    def alloc_host_outputs(self, n, pin=True):
+        """Output arrays of update_host in (pinned) host memory."""
+        import torch
+        return dict(state_out=torch.empty((self.state_size, n), dtype=torch.float64, pin_memory=pin),
+                    stress=torch.empty((n, 6), dtype=torch.float64, pin_memory=pin),
+                    tangent=torch.empty((n, 6, 6), dtype=torch.float64, pin_memory=pin),
+                    iters=torch.empty(n, dtype=torch.int32, pin_memory=pin),
+                    status=torch.empty(n, dtype=torch.int32, pin_memory=pin))
+
+    def update_host(self, lam, Q, E_n, dE, state_in, out=None, tree_id=None, chunk=0):
+        """dmn_update_host: the update of `update` with every array in host memory (CPU tensors, pinned
+        for overlapped copies).  out["state_out"] may be state_in itself.  Blocks until the results are
+        in the host arrays; returns out."""
+        import torch
+        n = lam.shape[0]
+        if tree_id is not None:
+            _check_host("tree_id", tree_id, torch.int32, (n,))
+        _check_host("lam", lam, torch.float64, (n, 2))
+        _check_host("Q", Q, torch.float64, (n, 9))
+        _check_host("E_n", E_n, torch.float64, (n, 6))
+        _check_host("dE", dE, torch.float64, (n, 6))
+        _check_host("state_in", state_in, torch.float64, (self.state_size, n))
+        out = self.alloc_host_outputs(n) if out is None else out
+        _check_host("state_out", out["state_out"], torch.float64, (self.state_size, n))
+        _check_host("stress", out["stress"], torch.float64, (n, 6))
+        _check_host("tangent", out["tangent"], torch.float64, (n, 6, 6))
+        _check_host("iters", out["iters"], torch.int32, (n,))
+        _check_host("status", out["status"], torch.int32, (n,))
+        s = torch.cuda.current_stream().cuda_stream
+        rc = self._lib.dmn_update_host(self._h, n, _ptr(tree_id), _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE),
+                                       _ptr(state_in), _ptr(out["state_out"]), _ptr(out["stress"]),
+                                       _ptr(out["tangent"]), _ptr(out["iters"]), _ptr(out["status"]),
+                                       int(chunk), ctypes.c_void_p(s))
+        if rc != 0:
+            self._err("dmn_update_host", rc)
         return out

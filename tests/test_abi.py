@@ -58,6 +58,9 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(case, msg):
 def test_calls_on_null_handle_are_argument_errors():
     lib = dmn.load_library()
     assert lib.dmn_update(None, 4, None, *([None] * 10), None) == -1
+    lib.dmn_update_host.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 11 + [ctypes.c_int64,
+                                                                                            ctypes.c_void_p]
+    assert lib.dmn_update_host(None, 4, *([None] * 11), 0, None) == -1
     assert lib.dmn_interp_orientation(None, 4, None, None, None, None) == -1
     assert lib.dmn_state_size(None, 0) == -1
     lib.dmn_destroy(None)
