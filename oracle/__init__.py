@@ -73,8 +73,12 @@ def _f64(a, shape=None):
 
 
 def phases_array(phases) -> np.ndarray:
-    """(kind, E, nu, sigma0, H) of phase 1 then phase 2."""
-    return np.array([[ph.kind, ph.E, ph.nu, ph.sigma0, ph.H] for ph in phases], dtype=np.float64).reshape(10)
+    """(kind, E, nu, sigma0, H, sigma_inf, k0) of phase 1 then phase 2."""
+    return np.array([_phase_row(ph) for ph in phases], dtype=np.float64).reshape(14)
+
+
+def _phase_row(ph):
+    return [ph.kind, ph.E, ph.nu, ph.sigma0, ph.H, getattr(ph, "sigma_inf", 0.0), getattr(ph, "k0", 0.0)]
 
 
 def state_size(K: int, phases) -> int:
@@ -150,7 +154,7 @@ def newton_system(tree, lam1, lam2, E_loc, a, z_n):
 
 def phase_law(phase, eps, z_n=None):
     """One leaf: (sigma [6], D [6,6], z_new [7]); z = (alpha_bar, ep6 Mandel)."""
-    ph = np.array([phase.kind, phase.E, phase.nu, phase.sigma0, phase.H], dtype=np.float64)
+    ph = np.array(_phase_row(phase), dtype=np.float64)
     z = np.zeros(7) if z_n is None else _f64(z_n)
     sig = np.empty(6); D = np.empty((6, 6)); zn = np.empty(7)
     _load().oracle_phase_law(_p(ph), _p(_f64(eps)), _p(z), _p(sig), _p(D), _p(zn))
@@ -251,7 +255,7 @@ def leaf_states(tree, state, i):
     z = np.zeros((L, 7))
     slot = 0
     for l in range(L):
-        if tree.phases[l % 2].kind == 1:
+        if tree.phases[l % 2].kind != 0:
             b = state[6 * slot:6 * slot + 6, i]
             z[l] = [b[0], b[1], b[2], -(b[1] + b[2]), b[3], b[4], b[5]]
             slot += 1
@@ -261,5 +265,5 @@ def leaf_states(tree, state, i):
 def jumps(tree, state, i):
     """a of point i (paper ordering) from a field-major state."""
     L = 1 << tree.K
-    nz = sum(1 for l in range(L) if tree.phases[l % 2].kind == 1)
+    nz = sum(1 for l in range(L) if tree.phases[l % 2].kind != 0)
     return np.array(state[6 * nz:, i])

@@ -66,7 +66,8 @@ static int leaf_side(int K, int k, int i, int l) {
 }
 
 /* ------------------------------------------------------------------ */
-typedef struct { int kind; double E, nu, s0, H; } or_phase;
+typedef struct { int kind; double E, nu, s0, H, sinf, k0; } or_phase;
+#define OR_MAT 7   /* doubles per phase: kind, E, nu, sigma0, H (k_inf), sigma_inf, k0 */
 
 typedef struct {
   int K, M, N, L;
@@ -98,8 +99,10 @@ static int tree_init(or_tree* t, int K, int M, const double* p, const double* q,
   t->K = K; t->M = M; t->N = (1 << K) - 1; t->L = 1 << K; t->p = p; t->q = q;
   t->tol = tol; t->max_iter = max_iter; t->line_search = line_search;
   for (int f = 0; f < 2; ++f) {
-    t->ph[f].kind = (int)mat[5 * f + 0]; t->ph[f].E = mat[5 * f + 1]; t->ph[f].nu = mat[5 * f + 2];
-    t->ph[f].s0 = mat[5 * f + 3]; t->ph[f].H = mat[5 * f + 4];
+    const double* m = mat + OR_MAT * f;
+    t->ph[f].kind = (int)m[0]; t->ph[f].E = m[1]; t->ph[f].nu = m[2];
+    t->ph[f].s0 = m[3]; t->ph[f].H = m[4]; t->ph[f].sinf = m[5]; t->ph[f].k0 = m[6];
+    if (t->ph[f].kind < 0 || t->ph[f].kind > 2) return -1;
   }
   double sw = 0.0;
   for (int l = 0; l < t->L; ++l) { if (!(w[l] > 0.0)) return -2; sw += w[l]; }
@@ -143,7 +146,7 @@ static int tree_init(or_tree* t, int K, int M, const double* p, const double* q,
   t->nz = 0;
   for (int l = 0; l < t->L; ++l) {
     int f = l % 2;   /* leaf l+1 odd -> phase 1, even -> phase 2 */
-    t->z_slot[l] = (t->ph[f].kind == 1) ? t->nz++ : -1;
+    t->z_slot[l] = (t->ph[f].kind != 0) ? t->nz++ : -1;
   }
   return 0;
 }
@@ -223,14 +226,34 @@ static void sym_operator(const double n[3], double Nm[6][3]) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Phase laws.  Elastic: sigma = 3K P1 eps + 2G P2 eps.  J2 with linear
- * isotropic hardening, implicit Euler = radial return (Simo-Hughes ch. 3):
- *   s_tr = 2G (dev eps - ep_n), f = |s_tr| - sqrt(2/3) (s0 + H ab_n);
- *   f > 0: dg = f / (2G + 2H/3), nhat = s_tr/|s_tr|, s = s_tr - 2G dg nhat,
+/* Phase laws.  Elastic: sigma = 3K P1 eps + 2G P2 eps.  J2 plasticity with
+ * isotropic hardening sigma_Y(ab), ab the equivalent plastic strain,
+ * integrated by implicit Euler = radial return (Simo-Hughes ch. 3):
+ *   s_tr = 2G (dev eps - ep_n), f = |s_tr| - sqrt(2/3) sigma_Y(ab_n);
+ *   f > 0: dg solves |s_tr| - 2G dg - sqrt(2/3) sigma_Y(ab_n + sqrt(2/3) dg) = 0,
+ *          nhat = s_tr/|s_tr|, s = s_tr - 2G dg nhat,
  *          ep = ep_n + dg nhat, ab = ab_n + sqrt(2/3) dg,
  *          D = K 1(x)1 + 2G th Idev - 2G thb nhat(x)nhat,
- *          th = 1 - 2G dg/|s_tr|, thb = 1/(1 + H/(3G)) - (1 - th).
+ *          th = 1 - 2G dg/|s_tr|, thb = 1/(1 + H'/(3G)) - (1 - th),
+ *          H' = d sigma_Y / d ab at the new ab.
+ * kind 1, linear hardening: sigma_Y = s0 + H ab, so dg = f / (2G + 2H/3).
+ * kind 2, exponential-linear hardening (Sec. 4.1, the matrix law of the
+ *   paper's material table): sigma_Y = s0 + H ab + (sinf - s0)(1 - exp(-(k0 - H)/(sinf - s0) ab))
+ *   with H = k_inf; dg by Newton's method on the scalar equation above,
+ *   started at 0 (the equation is convex and decreasing in dg, so the
+ *   iterates increase monotonically to the root).
  * z = (ab, ep in Mandel, 6 comps with ep33 = -ep11-ep22).  gap = |f| / sigma_Y. */
+static double yield_stress(const or_phase* ph, double ab, double* slope) {
+  if (ph->kind == 2 && ph->sinf > ph->s0) {
+    double ds = ph->sinf - ph->s0, r = (ph->k0 - ph->H) / ds;
+    double e = exp(-r * ab);
+    if (slope) *slope = ph->H + (ph->k0 - ph->H) * e;
+    return ph->s0 + ph->H * ab + ds * (1.0 - e);
+  }
+  if (slope) *slope = ph->H;
+  return ph->s0 + ph->H * ab;
+}
+
 static void phase_law(const or_phase* ph, const double eps[6], const double z_n[7],
                       double sig[6], double D[6][6], double z_new[7], double* gap) {
   double K = ph->E / (3.0 * (1.0 - 2.0 * ph->nu));
@@ -253,7 +276,7 @@ static void phase_law(const or_phase* ph, const double eps[6], const double z_n[
   double str[6], nrm2 = 0.0;
   for (int I = 0; I < 6; ++I) { str[I] = 2.0 * G * (dev[I] - ep_n[I]); nrm2 += str[I] * str[I]; }
   double ns = sqrt(nrm2);
-  double sy = ph->s0 + ph->H * ab_n;
+  double sy = yield_stress(ph, ab_n, NULL);
   double f = ns - sqrt(2.0 / 3.0) * sy;
   if (gap) *gap = fabs(f) / sy;
   if (f <= 0.0) {
@@ -263,11 +286,24 @@ static void phase_law(const or_phase* ph, const double eps[6], const double z_n[
     if (z_new) for (int c = 0; c < 7; ++c) z_new[c] = z_n[c];
     return;
   }
-  double dg = f / (2.0 * G + 2.0 * ph->H / 3.0);
+  double dg, Hp;
+  if (ph->kind == 1) {
+    dg = f / (2.0 * G + 2.0 * ph->H / 3.0);
+    Hp = ph->H;
+  } else {
+    dg = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double slope, r = ns - 2.0 * G * dg - sqrt(2.0 / 3.0) * yield_stress(ph, ab_n + sqrt(2.0 / 3.0) * dg, &slope);
+      double step = r / (2.0 * G + (2.0 / 3.0) * slope);
+      dg += step;
+      if (fabs(step) <= 1e-15 * dg) break;
+    }
+    yield_stress(ph, ab_n + sqrt(2.0 / 3.0) * dg, &Hp);
+  }
   double nh[6];
   for (int I = 0; I < 6; ++I) nh[I] = str[I] / ns;
   double th = 1.0 - 2.0 * G * dg / ns;
-  double thb = 1.0 / (1.0 + ph->H / (3.0 * G)) - (1.0 - th);
+  double thb = 1.0 / (1.0 + Hp / (3.0 * G)) - (1.0 - th);
   for (int I = 0; I < 6; ++I) sig[I] = (I < 3 ? K * tr : 0.0) + str[I] - 2.0 * G * dg * nh[I];
   for (int I = 0; I < 6; ++I)
     for (int J = 0; J < 6; ++J)
@@ -603,8 +639,8 @@ static or_work* work_alloc(const or_tree* t) {
 static void work_free(or_work* ws) { free(ws->J); free(ws); }
 
 /* ================================================================== */
-/* Exported entry points (ctypes).  mat = (kind, E, nu, sigma0, H) for phase 1
- * then phase 2.  Return 0 on success, < 0 on invalid arguments.           */
+/* Exported entry points (ctypes).  mat = (kind, E, nu, sigma0, H, sigma_inf, k0)
+ * for phase 1 then phase 2 (H is k_inf for kind 2).  Return 0 on success, < 0 on invalid arguments.           */
 
 int oracle_state_size(int K, const double* mat) {
   or_tree t;
@@ -641,7 +677,7 @@ int oracle_update(int K, int M, const double* p, const double* q, const double* 
 int oracle_normals(int K, int M, const double* p, const double* q, double lam1, double lam2, double* out) {
   or_tree t;
   double w[OR_LMAX];
-  double mat[10] = {0, 1, 0.2, 0, 0, 0, 1, 0.2, 0, 0};
+  double mat[2 * OR_MAT] = {0, 1, 0.2, 0, 0, 0, 0, 0, 1, 0.2, 0, 0, 0, 0};
   if (K < 1 || K > OR_KMAX) return -1;
   for (int l = 0; l < (1 << K); ++l) w[l] = 1.0;
   if (tree_init(&t, K, M, p, q, w, mat, 1e-12, 1, 0) != 0) return -1;
@@ -659,7 +695,7 @@ int oracle_barycentric(double lam1, double lam2, double* phi) { barycentric(lam1
 int oracle_gradient_operator(int K, int M, const double* p, const double* q, const double* w,
                              double lam1, double lam2, double* A) {
   or_tree t;
-  double mat[10] = {0, 1, 0.2, 0, 0, 0, 1, 0.2, 0, 0};
+  double mat[2 * OR_MAT] = {0, 1, 0.2, 0, 0, 0, 0, 0, 1, 0.2, 0, 0, 0, 0};
   if (tree_init(&t, K, M, p, q, w, mat, 1e-12, 1, 0) != 0) return -1;
   or_work* ws = work_alloc(&t);
   normals(&t, lam1, lam2, ws->nrm);
@@ -703,10 +739,10 @@ int oracle_newton_system(int K, int M, const double* p, const double* q, const d
   return rc;
 }
 
-/* one leaf law evaluation: phase = (kind, E, nu, sigma0, H); z = (alpha_bar, ep6) */
+/* one leaf law evaluation: phase = (kind, E, nu, sigma0, H, sigma_inf, k0); z = (alpha_bar, ep6) */
 int oracle_phase_law(const double* phase, const double* eps, const double* z_n, double* sig, double* D,
                      double* z_new) {
-  or_phase ph = {(int)phase[0], phase[1], phase[2], phase[3], phase[4]};
+  or_phase ph = {(int)phase[0], phase[1], phase[2], phase[3], phase[4], phase[5], phase[6]};
   double Dm[6][6], zz[7];
   phase_law(&ph, eps, z_n, sig, Dm, zz, NULL);
   for (int I = 0; I < 6; ++I) for (int J = 0; J < 6; ++J) D[6 * I + J] = Dm[I][J];

@@ -39,12 +39,17 @@ TRIANGLE_CORNERS = np.array([[1.0, 0.0], [1.0 / 3.0, 1.0 / 3.0], [0.5, 0.5]])
 @dataclass
 class Phase:
     """One constituent: kind 0 = linear elastic, kind 1 = J2 plasticity with
-    linear isotropic hardening sigma_Y = sigma0 + H * alpha_bar."""
+    linear isotropic hardening sigma_Y = sigma0 + H * alpha_bar, kind 2 = J2
+    plasticity with exponential-linear hardening
+    sigma_Y = sigma0 + H alpha_bar + (sigma_inf - sigma0)(1 - exp(-(k0 - H)/(sigma_inf - sigma0) alpha_bar))
+    (H = k_inf; Sec. 4.1)."""
     kind: int
     E: float
     nu: float
     sigma0: float = 0.0
     H: float = 0.0
+    sigma_inf: float = 0.0
+    k0: float = 0.0
 
 
 # Materials of the synthetic workloads: glass fiber and a J2 matrix with linear
@@ -52,6 +57,8 @@ class Phase:
 # the matrix law is the linear-hardening stand-in for its exp-linear law).
 FIBER = Phase(kind=0, E=72000.0, nu=0.22)
 MATRIX = Phase(kind=1, E=3000.0, nu=0.35, sigma0=40.0, H=300.0)
+# The paper's polyamide matrix (its table of material parameters): exponential-linear hardening.
+MATRIX_EXPLIN = Phase(kind=2, E=2100.0, nu=0.3, sigma0=29.0, H=139.0, sigma_inf=61.7, k0=10600.0)
 
 
 @dataclass
@@ -225,7 +232,7 @@ def state_size(K: int, phases=(FIBER, MATRIX)) -> int:
     independent components of the deviatoric plastic strain), then 3 jumps per
     laminate."""
     L = n_leaves(K)
-    n_inel = sum(1 for i in range(L) if phases[i % 2].kind == 1)
+    n_inel = sum(1 for i in range(L) if phases[i % 2].kind != 0)
     return 6 * n_inel + 3 * n_nodes(K)
 
 

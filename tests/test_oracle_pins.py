@@ -17,6 +17,8 @@ Each test checks the oracle against something other than itself:
 """
 import os
 
+import math
+
 import numpy as np
 import pytest
 
@@ -278,6 +280,99 @@ def test_j2_matches_closed_form_under_proportional_loading(seed):
             assert abs(np.linalg.norm(sdev) - np.sqrt(2 / 3) * (ph.sigma0 + ph.H * z[0])) < 1e-10
             # elastic law holds on the elastic part of the strain
             np.testing.assert_allclose(sdev, 2 * G * (eps - eps[:3].sum() / 3 * ONE - z[1:]), atol=1e-10)
+
+
+# ----------------------------------------------------------------------------- J2, exponential-linear hardening
+
+
+def explin_yield(ph, ab):
+    """sigma_Y of the exponential-linear law (Sec. 4.1), written out."""
+    return ph.sigma0 + ph.H * ab + (ph.sigma_inf - ph.sigma0) * (
+        1.0 - math.exp(-(ph.k0 - ph.H) / (ph.sigma_inf - ph.sigma0) * ab))
+
+
+def test_explin_law_with_k0_equal_kinf_is_the_linear_law():
+    """k0 = k_inf removes the exponential term: the law is the linear-hardening one."""
+    rng = np.random.default_rng(31)
+    lin = W.MATRIX
+    ex = W.Phase(kind=2, E=lin.E, nu=lin.nu, sigma0=lin.sigma0, H=lin.H, sigma_inf=2 * lin.sigma0, k0=lin.H)
+    z1 = np.zeros(7)
+    z2 = np.zeros(7)
+    for s in range(1, 6):
+        eps = 0.01 * s * rng.standard_normal(6)
+        s1, D1, z1 = oracle.phase_law(lin, eps, z1)
+        s2, D2, z2 = oracle.phase_law(ex, eps, z2)
+        np.testing.assert_allclose(s2, s1, rtol=0, atol=1e-12 * np.abs(s1).max())
+        np.testing.assert_allclose(D2, D1, rtol=0, atol=1e-12 * np.abs(D1).max())
+        np.testing.assert_allclose(z2, z1, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_explin_radial_return_against_bisection_and_path_independence(seed):
+    """Proportional deviatoric loading from the virgin state: the stress deviator
+    stays along the strain deviator d and |s| = 2G (|e| - dg), with dg the root of
+    2G (|e| - dg) = sqrt(2/3) sigma_Y(sqrt(2/3) dg), found here by bisection.
+    Radial return is exact for proportional loading, so 1 and 25 increments agree."""
+    rng = np.random.default_rng(40 + seed)
+    ph = W.MATRIX_EXPLIN
+    G = ph.E / (2 * (1 + ph.nu))
+    d = rng.standard_normal(6)
+    d[:3] -= d[:3].sum() / 3
+    d /= np.linalg.norm(d)
+    for e in (0.005, 0.02, 0.08):
+        lo, hi = 0.0, e
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if 2 * G * (e - mid) - math.sqrt(2 / 3) * explin_yield(ph, math.sqrt(2 / 3) * mid) > 0:
+                lo = mid
+            else:
+                hi = mid
+        dg = 0.5 * (lo + hi)
+        sig1, _, z1 = oracle.phase_law(ph, e * d, np.zeros(7))
+        np.testing.assert_allclose(sig1, 2 * G * (e - dg) * d, rtol=0, atol=1e-11 * 2 * G * e)
+        assert abs(z1[0] - math.sqrt(2 / 3) * dg) < 1e-14
+        z = np.zeros(7)
+        for s in range(1, 26):
+            sig, _, z = oracle.phase_law(ph, e * s / 25 * d, z)
+        np.testing.assert_allclose(sig, sig1, rtol=0, atol=1e-11 * 2 * G * e)
+        np.testing.assert_allclose(z, z1, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("plastic", [False, True])
+def test_explin_tangent_matches_finite_differences(plastic):
+    """The consistent tangent takes the hardening slope at the new alpha_bar."""
+    rng = np.random.default_rng(15 + plastic)
+    ph = W.MATRIX_EXPLIN
+    z_n = np.zeros(7)
+    if plastic:
+        for s in range(1, 5):
+            _, _, z_n = oracle.phase_law(ph, 0.01 * s * rng.standard_normal(6), z_n)
+        assert z_n[0] > 0.002
+    eps = z_n[1:] + (0.02 if plastic else 0.001) * rng.standard_normal(6)
+    sig, D, _ = oracle.phase_law(ph, eps, z_n)
+    h = 1e-7
+    Dfd = np.zeros((6, 6))
+    for j in range(6):
+        e = np.zeros(6)
+        e[j] = h
+        Dfd[:, j] = (oracle.phase_law(ph, eps + e, z_n)[0] - oracle.phase_law(ph, eps - e, z_n)[0]) / (2 * h)
+    np.testing.assert_allclose(D, Dfd, rtol=0, atol=1e-6 * np.abs(D).max())
+
+
+def test_identical_explin_phases_return_the_phase_law():
+    ph = W.MATRIX_EXPLIN
+    tree = W.tree_d10_fit(3, seed=32, phases=(ph, ph))
+    A2, lam, Q = W.orientation_field(4, seed=33)
+    Ef = W.random6_path_final(4, 0.03, seed=34)
+    st, sig, C, it, stat, _ = run_path(tree, lam, Q, Ef, 6)
+    assert np.all(stat == 0)
+    for i in range(4):
+        z = np.zeros(7)
+        for s in range(1, 7):
+            En, dE = W.proportional_increment(Ef[i:i + 1], s, 6)
+            s1, D1, z = oracle.phase_law(ph, (En + dE)[0], z)
+        np.testing.assert_allclose(sig[i], s1, atol=1e-10 * np.abs(s1).max())
+        np.testing.assert_allclose(C[i], D1, atol=1e-10 * np.abs(D1).max())
 
 
 @pytest.mark.parametrize("plastic", [False, True])
