@@ -49,43 +49,56 @@ PEAK_F64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.07
 PEAK_F32_GFLOPS = 152 * 128 * 2 * 2.07
 
 # ---------------------------------------------------------------------------------------------
-# Algorithmic flop counts (add/sub/mul/div/sqrt = 1, fma = 2) per Newton pass over a depth-K
-# tree, counted from the arithmetic of csrc/dmn_device.cuh (see the design doc for the breakdown).
-# Per laminate: jump correction da = g + H d_eps (36, precision T), a += da (3, FP64), N a and
-# the children's strains (39, FP64), children's strain corrections (36, T, not at the bottom
-# level), the laminate's residual share and plain stress average (52, FP64), the
-# condensation (745, T).  Per leaf: elastic law with tangent 75 (FP64 stress 17 + T tangent
-# 58), J2 law with consistent tangent 128 (FP64 70 + T 58).  T = FP64 in the FP64 form and
-# FP32 in the mixed form.
+# Algorithmic flop counts (add/sub/mul/div/sqrt/rsqrt = 1, fma = 2) of the tree-condensed Newton
+# method, counted from the arithmetic of csrc/dmn_device.cuh.  T = FP64 in the FP64 form, FP32
+# in the mixed form.
+#   per laminate, every pass:  N a and the children's strains 39 (FP64); residual share and
+#                              plain stress average 50 (FP64); condensation 747 (T), or 605 (T)
+#                              for a bottom laminate (leaf tangents D = lam 1(x)1 + 2 mu I - c m(x)m)
+#   per inner laminate:        children's strain corrections 39 (T)
+#   per laminate, per Newton correction: da = g + H d_eps 39 (T), a += da 3 (FP64)
+#   per leaf:                  elastic stress 13; J2 stress 56 + tangent scalars 12 (FP64)
+#   per pass:                  convergence test 15 (FP64)
+F_NODE_F64, F_RES, F_COND, F_COND_BOTTOM, F_DEPS, F_DA, F_A = 39, 50, 747, 605, 39, 39, 3
+F_LEAF_EL, F_LEAF_J2, F_TEST = 13, 56 + 12, 15
+F_ROTATE = 1150         # per point: stress and tangent back to the global frame (k_final)
+F_STATE_NODE = 39       # state pass: per laminate (strains from the jumps)
+F_STATE_J2 = 68         # state pass: per J2 leaf (return mapping and new state)
+
+
 def pass_flops(K):
-    """(FP64 flops, T flops) of one Newton pass."""
+    """(FP64 flops, T flops) of one Newton pass without the jump correction."""
     N, L = (1 << K) - 1, 1 << K
-    nb = (1 << (K - 1)) - 1
-    f64 = N * (3 + 39 + 52) + (L // 2) * 17 + (L // 2) * 70
-    ft = N * (36 + 745) + nb * 36 + L * 58
+    nbot = L // 2
+    f64 = N * (F_NODE_F64 + F_RES) + nbot * (F_LEAF_EL + F_LEAF_J2) + F_TEST
+    ft = (N - nbot) * (F_COND + F_DEPS) + nbot * F_COND_BOTTOM
     return f64, ft
 
 
-F_POINT_NEWTON = 1470   # per point: strain rotation (300), stress and tangent rotation (1150), test (20)
-F_STATE_NODE = 39       # state pass: per laminate (strains from the jumps)
-F_STATE_J2 = 75         # state pass: per J2 leaf (return mapping + new state)
+def corr_flops(K):
+    """(FP64 flops, T flops) of one jump correction of all laminates."""
+    N = (1 << K) - 1
+    return N * F_A, N * F_DA
 
 
 def newton_flops(K, iters_sum, npts, mixed):
-    """(FP64, FP32) flops of the Newton kernel over npts points with iters_sum corrections."""
+    """(FP64, FP32) flops of the Newton kernel over npts points with iters_sum corrections:
+    one pass per point evaluates the starting jumps, one more per correction."""
     f64, ft = pass_flops(K)
+    c64, ct = corr_flops(K)
     passes = iters_sum + npts
-    F64 = passes * f64 + npts * F_POINT_NEWTON
-    return (F64, passes * ft) if mixed else (F64 + passes * ft, 0.0)
+    F64 = passes * f64 + iters_sum * c64
+    FT = passes * ft + iters_sum * ct
+    return (F64, FT) if mixed else (F64 + FT, 0.0)
 
 
 def final_flops(K, npts, mixed):
-    """FP64 flops of the final kernel (state pass; mixed form: plus one FP64 sweep)."""
+    """FP64 flops of the final kernel (state pass and rotation; mixed form: plus one FP64 pass)."""
     N, L = (1 << K) - 1, 1 << K
-    f = npts * (300 + N * F_STATE_NODE + (L // 2) * F_STATE_J2)
+    f = npts * (F_ROTATE + N * F_STATE_NODE + (L // 2) * F_STATE_J2)
     if mixed:
         f64, ft = pass_flops(K)
-        f += npts * (f64 + ft + 1150)
+        f += npts * (f64 + ft)
     return f
 
 
@@ -256,7 +269,7 @@ def run_form(form, ctx, args, dist):
         cur = step(s, cur)
     torch.cuda.synchronize()
     host_state = None
-    if form == "f64" and args.e2e_steps > 0:
+    if form == "f64" and args.e2e_steps != 0:
         host_state = torch.empty((S, n), dtype=torch.float64, pin_memory=True)
         host_state.copy_(st[cur])
     if dist:
@@ -317,13 +330,15 @@ def run_e2e(r, ctx, args, dist):
     import torch
     n, S = ctx["n"], r["S"]
     m = r["m"]
-    steps = min(args.e2e_steps, args.steps)
+    steps = args.steps if args.e2e_steps < 0 else min(args.e2e_steps, args.steps)
     lam_h = r["lam"].cpu().pin_memory()
     Q_h = r["Q"].cpu().pin_memory()
     En_h = [ctx["En"][s - 1].cpu().pin_memory() for s in range(args.warmup + 1, args.warmup + steps + 1)]
     dE_h = [ctx["dE"][s - 1].cpu().pin_memory() for s in range(args.warmup + 1, args.warmup + steps + 1)]
     st_h = r["host_state"]                        # state after the warm-up increments, updated in place
     out_h = m.alloc_host_outputs(n)
+    # untimed call (its own state_out): allocates the library's stage buffers and second work set
+    m.update_host(lam_h, Q_h, En_h[0], dE_h[0], st_h, out=out_h, chunk=args.e2e_chunk)
     out_h["state_out"] = st_h
     h2d = lam_h.nbytes + Q_h.nbytes + En_h[0].nbytes + dE_h[0].nbytes + st_h.nbytes
     d2h = (out_h["stress"].nbytes + out_h["tangent"].nbytes + st_h.nbytes + out_h["iters"].nbytes
@@ -502,7 +517,8 @@ def main():
     ap.add_argument("--forms", default="f64,mixed")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="points per chunk of dmn_update_host (0: the library's default)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="increments timed through dmn_update_host (-1: the same increments as the device timing)")
     ap.add_argument("--ref-points", type=int, default=1024)
     ap.add_argument("--cpu-points", type=int, default=1024)
     ap.add_argument("--parity-points", type=int, default=16)
@@ -558,7 +574,7 @@ def run_gpu(args):
         r = run_form(form, ctx, args, dist)
         if rank == 0 and args.parity_points > 0:
             r["parity"] = parity_sample(form, r, ctx, args, pidx)
-        if form == "f64" and args.e2e_steps > 0:
+        if form == "f64" and args.e2e_steps != 0:
             e2e = run_e2e(r, ctx, args, dist)
         r["m"].close()
         for k in ("stress", "tangent", "status", "state", "host_state", "st", "lam", "Q", "m"):
