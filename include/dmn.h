@@ -54,10 +54,15 @@ typedef struct dmn_handle dmn_handle;
 enum { DMN_OK = 0, DMN_ERR_ARG = -1, DMN_ERR_CUDA = -2 };
 
 /* phase laws: linear elastic (sigma = 3K P1 eps + 2G P2 eps) and J2
- * plasticity with linear isotropic hardening sigma_Y = sigma0 + H alpha_bar,
- * integrated by implicit Euler (radial return; Sec. 4.1 takes the J2 law with
- * isotropic hardening from Simo-Hughes ch. 3) */
-enum { DMN_PHASE_ELASTIC = 0, DMN_PHASE_J2_LINEAR = 1 };
+ * plasticity with isotropic hardening, integrated by implicit Euler (radial
+ * return; Sec. 4.1 takes the J2 law from Simo-Hughes ch. 3):
+ *   DMN_PHASE_J2_LINEAR  sigma_Y = sigma0 + H alpha_bar;
+ *   DMN_PHASE_J2_EXPLIN  sigma_Y = sigma0 + H alpha_bar
+ *                          + (sigma_inf - sigma0) (1 - exp(-(k0 - H) / (sigma_inf - sigma0) alpha_bar)),
+ *                        the exponential-linear law of Sec. 4.1 (H = k_inf); the
+ *                        plastic multiplier is found by a scalar Newton iteration.
+ * alpha_bar is the equivalent plastic strain. */
+enum { DMN_PHASE_ELASTIC = 0, DMN_PHASE_J2_LINEAR = 1, DMN_PHASE_J2_EXPLIN = 2 };
 
 /* DMN_PREC_F64: every step in FP64.
  * DMN_PREC_MIXED: leaf tangents, laminate condensation and jump corrections
@@ -78,10 +83,12 @@ enum {
 enum { DMN_MAX_TREES = 8 };
 
 typedef struct {
-  int32_t kind;    /* DMN_PHASE_* */
-  double E, nu;    /* Young's modulus (MPa), Poisson's ratio */
-  double sigma0;   /* J2: initial yield stress (MPa) */
-  double H;        /* J2: linear hardening modulus (MPa) */
+  int32_t kind;      /* DMN_PHASE_* */
+  double E, nu;      /* Young's modulus (MPa), Poisson's ratio */
+  double sigma0;     /* J2: initial yield stress (MPa), > 0 */
+  double H;          /* J2: linear hardening modulus (MPa), >= 0 (k_inf of the exponential-linear law) */
+  double sigma_inf;  /* DMN_PHASE_J2_EXPLIN: saturation stress (MPa), >= sigma0 */
+  double k0;         /* DMN_PHASE_J2_EXPLIN: initial hardening modulus (MPa), >= H */
 } dmn_phase;
 
 typedef struct {
@@ -113,8 +120,8 @@ typedef struct {
  * weights to the laminate volume fractions (Sec. 2.1) and allocates the work
  * space of the persistent Newton kernel on the current CUDA device.  opt may
  * be NULL (defaults).  Errors: DMN_ERR_ARG for n_trees out of range, K outside
- * 1..8, M not in {3,4,6}, a weight <= 0 or non-finite, an unknown phase kind
- * or non-positive moduli; DMN_ERR_CUDA if an allocation fails.  On error *out
+ * 1..8, M not in {3,4,6}, a weight <= 0 or non-finite, an unknown phase kind,
+ * non-positive moduli or hardening parameters outside the ranges above; DMN_ERR_CUDA if an allocation fails.  On error *out
  * is NULL. */
 int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* opt, dmn_handle** out);
 

@@ -1,7 +1,8 @@
 """Build of the CUDA library (in-tree, sm_103a only).
 
-``python -m paper_2103_08253_gb300.build`` compiles ``csrc/dmn.cu`` with nvcc
-into ``_build/libdmn.so`` next to this file.
+``python -m paper_2103_08253_gb300.build`` compiles ``csrc/dmn.cu`` (the DMN
+update) and ``csrc/fe.cu`` (the hexahedral FE operator and PCG) with nvcc, in
+parallel, and links them into ``_build/libdmn.so`` next to this file.
 """
 from __future__ import annotations
 
@@ -12,8 +13,9 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = [os.path.join(HERE, "csrc", "dmn.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "dmn_device.cuh"), os.path.join(ROOT, "include", "dmn.h")]
+SOURCES = [os.path.join(HERE, "csrc", "dmn.cu"), os.path.join(HERE, "csrc", "fe.cu")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", "dmn_device.cuh"), os.path.join(ROOT, "include", "dmn.h"),
+                  os.path.join(ROOT, "include", "fe.h")]
 LIB = os.path.join(HERE, "_build", "libdmn.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -36,12 +38,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if all(os.path.getmtime(d) <= t for d in DEPS):
             return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), flush=True)
-    subprocess.check_call(cmd)
+        flags.insert(0, "-Xptxas=-v")
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(os.path.dirname(LIB), os.path.basename(src) + ".tmp%d.o" % os.getpid())
+        cmd = [nvcc(), *flags, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        objs.append(obj)
+        procs.append(subprocess.Popen(cmd))
+    rcs = [p.wait() for p in procs]
+    try:
+        for src, rc in zip(SOURCES, rcs):
+            if rc != 0:
+                raise subprocess.CalledProcessError(rc, "nvcc " + src)
+        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

@@ -108,11 +108,25 @@ TreeDev tree_dev(const Tree& t) {
 
 // Checks one phase of a tree description and derives its device constants.
 const char* make_phase(const dmn_phase& p, PhaseDev& out) {
-  if (p.kind != DMN_PHASE_ELASTIC && p.kind != DMN_PHASE_J2_LINEAR) return "unknown phase kind";
+  if (p.kind != DMN_PHASE_ELASTIC && p.kind != DMN_PHASE_J2_LINEAR && p.kind != DMN_PHASE_J2_EXPLIN)
+    return "unknown phase kind";
   if (!(p.E > 0.0) || !(p.nu > -1.0) || !(p.nu < 0.5)) return "need E > 0 and -1 < nu < 0.5";
-  if (p.kind == DMN_PHASE_J2_LINEAR && (!(p.sigma0 > 0.0) || !(p.H >= 0.0)))
+  if (p.kind != DMN_PHASE_ELASTIC && (!(p.sigma0 > 0.0) || !(p.H >= 0.0) || !std::isfinite(p.H)))
     return "J2 phase needs sigma0 > 0 and H >= 0";
+  if (p.kind == DMN_PHASE_J2_EXPLIN && (!(p.sigma_inf >= p.sigma0) || !(p.k0 >= p.H) || !std::isfinite(p.k0) ||
+                                        !std::isfinite(p.sigma_inf)))
+    return "exponential-linear hardening needs sigma_inf >= sigma0 and k0 >= H";
   out.kind = p.kind;
+  out.ds = out.dk = out.rate = 0.0;
+  if (p.kind == DMN_PHASE_J2_EXPLIN) {
+    if (p.sigma_inf > p.sigma0 && p.k0 > p.H) {
+      out.ds = p.sigma_inf - p.sigma0;
+      out.dk = p.k0 - p.H;
+      out.rate = out.dk / out.ds;
+    } else {
+      out.kind = DMN_PHASE_J2_LINEAR;   // no exponential term: the linear law
+    }
+  }
   out.K = p.E / (3.0 * (1.0 - 2.0 * p.nu));
   out.G = p.E / (2.0 * (1.0 + p.nu));
   out.s0 = p.sigma0;
@@ -944,7 +958,7 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     for (int f = 0; f < 2; ++f) {
       if (const char* m = make_phase(d.phase[f], t.ph[f]))
         return fail(nullptr, DMN_ERR_ARG, std::string("dmn_create: ") + m);
-      n_inel_phase += d.phase[f].kind == DMN_PHASE_J2_LINEAR;
+      n_inel_phase += d.phase[f].kind != DMN_PHASE_ELASTIC;
     }
     t.z_both = n_inel_phase == 2;
     t.nz = n_inel_phase * (t.L / 2);
@@ -1373,7 +1387,7 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   for (int f = 0; f < 2; ++f) {
     if (const char* m = make_phase(d.phase[f], td.ph[f]))
       return fail(nullptr, DMN_ERR_ARG, std::string("dmn_update_noalloc: ") + m);
-    n_inel += d.phase[f].kind == DMN_PHASE_J2_LINEAR;
+    n_inel += d.phase[f].kind != DMN_PHASE_ELASTIC;
   }
   td.z_both = n_inel == 2;
   td.nz = n_inel * (L / 2);

@@ -26,15 +26,19 @@ constexpr int NMAX = (1 << KMAX) - 1;
 constexpr double RS2 = 0.70710678118654752440;   // 1/sqrt(2)
 constexpr double SQ23 = 0.81649658092772603273;  // sqrt(2/3)
 
-// Isotropic phase: elastic (kind 0) or J2 with linear isotropic hardening
-// (kind 1).  Constants derived once on the host.
+// Isotropic phase: elastic (kind 0), J2 with linear isotropic hardening
+// (kind 1) or with exponential-linear hardening (kind 2, Sec. 4.1):
+//   sigma_Y(a) = s0 + H a + ds (1 - exp(-rate a)),  ds = sigma_inf - s0,
+//   rate = (k0 - H) / ds,  slope sigma_Y'(a) = H + (k0 - H) exp(-rate a).
+// Constants derived once on the host.
 struct PhaseDev {
   int kind;
   double K, G;       // bulk and shear modulus
-  double s0, H;      // yield stress and hardening modulus
+  double s0, H;      // yield stress and (linear part of the) hardening modulus
   double lam;        // K - 2G/3: sigma = lam tr(eps) 1 + 2G eps when elastic
-  double inv_den;    // 1 / (2G + 2H/3): plastic multiplier per unit overstress
-  double thb0;       // 1 / (1 + H / (3G))
+  double inv_den;    // 1 / (2G + 2H/3): plastic multiplier per unit overstress (kind 1)
+  double thb0;       // 1 / (1 + H / (3G)) (kind 1)
+  double ds, dk, rate;  // kind 2: sigma_inf - s0, k0 - H, (k0 - H) / (sigma_inf - s0)
 };
 
 // Per-laminate constants, heap order.
@@ -132,11 +136,30 @@ __device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], 
   for (int I = 0; I < 6; ++I) n2 += st[I] * st[I];
   const double ins = rsqrt(fmax(n2, 1e-300));
   const double ns = n2 * ins;
-  const double sy = ph.s0 + ph.H * z[0];
+  const bool explin = ph.kind == 2;
+  const double sy = ph.s0 + ph.H * z[0] + (explin ? ph.ds * (1.0 - exp(-ph.rate * z[0])) : 0.0);
   const double f = ns - SQ23 * sy;
   const bool plastic = f > 0.0;
   if (gap) *gap = fabs(f) / sy;
-  const double dg = plastic ? f * ph.inv_den : 0.0;
+  double dg = plastic ? f * ph.inv_den : 0.0;
+  double thb0 = ph.thb0;
+  if (explin && plastic) {
+    // scalar Newton on r(dg) = |s_tr| - 2G dg - sqrt(2/3) sigma_Y(a_n + sqrt(2/3) dg), from dg = 0;
+    // r is convex and decreasing, so the iterates rise monotonically to the root
+    dg = 0.0;
+    double slope = ph.H;
+    for (int it = 0; it < 40; ++it) {
+      const double a = z[0] + SQ23 * dg;
+      const double e = exp(-ph.rate * a);
+      slope = ph.H + ph.dk * e;
+      const double r = ns - twoG * dg - SQ23 * (ph.s0 + ph.H * a + ph.ds * (1.0 - e));
+      const double step = r / (twoG + (2.0 / 3.0) * slope);
+      dg += step;
+      if (fabs(step) <= 1e-15 * dg) break;
+    }
+    slope = ph.H + ph.dk * exp(-ph.rate * (z[0] + SQ23 * dg));   // hardening slope at the new a
+    thb0 = 1.0 / (1.0 + slope / (3.0 * ph.G));
+  }
   const double k2 = twoG * dg * ins;        // 2G dg / |s_tr| = 1 - th
   const double Kt = ph.K * tr;
 #pragma unroll
@@ -146,7 +169,7 @@ __device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], 
     const double mu = ph.G * (1.0 - k2);
     D->mu = (T)mu;
     D->lam = (T)(ph.K - (2.0 / 3.0) * mu);
-    D->c = (T)(plastic ? twoG * (ph.thb0 - k2) : 0.0);
+    D->c = (T)(plastic ? twoG * (thb0 - k2) : 0.0);
 #pragma unroll
     for (int I = 0; I < 6; ++I) D->m[I] = (T)(st[I] * ins);
   }
@@ -431,7 +454,7 @@ __device__ __forceinline__ void load_n<float>(const PointArrays& P, int node, do
 }
 
 __device__ __forceinline__ void load_z(const TreeDev& t, const PointArrays& P, int leaf, int phase, double z[6]) {
-  if (t.ph[phase].kind == 1) {
+  if (t.ph[phase].kind != 0) {
     const int slot = t.z_both ? leaf : (leaf >> 1);
     const double* b = P.z + (size_t)(6 * slot) * P.zs;
 #pragma unroll
@@ -586,7 +609,7 @@ __device__ inline void write_leaf_states(const TreeDev& t, const double Eloc[6],
     }
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
-      if (t.ph[side].kind != 1) continue;
+      if (t.ph[side].kind == 0) continue;
       const int leaf = 2 * m + side;
       double z[6], zn[6], sig[6];
       load_z(t, P, leaf, side, z);

@@ -20,6 +20,7 @@ EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_interp_orientatio
            "dmn_set_params", "dmn_grad", "dmn_profile_enable", "dmn_profile_read", "dmn_update_noalloc",
            "dmn_update_host", "dmn_last_error")
 
+PHASE_ELASTIC, PHASE_J2_LINEAR, PHASE_J2_EXPLIN = 0, 1, 2
 PREC_F64 = 0
 PREC_MIXED = 1
 STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE, STATUS_LINESEARCH, STATUS_BAD_TREE = 0, 1, 2, 3, 4
@@ -28,7 +29,8 @@ MAX_TREES = 8
 
 class Phase_(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("E", ctypes.c_double), ("nu", ctypes.c_double),
-                ("sigma0", ctypes.c_double), ("H", ctypes.c_double)]
+                ("sigma0", ctypes.c_double), ("H", ctypes.c_double), ("sigma_inf", ctypes.c_double),
+                ("k0", ctypes.c_double)]
 
 
 class TreeDesc_(ctypes.Structure):
@@ -140,7 +142,8 @@ class DMN:
             descs[k].K, descs[k].M = int(tr.K), int(tr.M)
             descs[k].p, descs[k].q, descs[k].w = p.ctypes.data_as(dp), q.ctypes.data_as(dp), w.ctypes.data_as(dp)
             for f, ph in enumerate(tr.phases):
-                descs[k].phase[f] = Phase_(int(ph.kind), float(ph.E), float(ph.nu), float(ph.sigma0), float(ph.H))
+                descs[k].phase[f] = Phase_(int(ph.kind), float(ph.E), float(ph.nu), float(ph.sigma0), float(ph.H),
+                                           float(getattr(ph, "sigma_inf", 0.0)), float(getattr(ph, "k0", 0.0)))
         if precision not in ("f64", "mixed"):
             raise ValueError("precision must be 'f64' or 'mixed'")
         opt = Options_(float(tol), int(max_iter), PREC_MIXED if precision == "mixed" else PREC_F64, int(block),

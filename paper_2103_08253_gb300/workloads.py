@@ -253,3 +253,109 @@ def mixed_depth_batch(n: int, seed: int, depths=(5, 6, 7, 8)):
     elastic = np.zeros(n, dtype=bool)
     elastic[rng.permutation(n)[: n // 2]] = True
     return tid.astype(np.int32), elastic
+
+
+# ---------------------------------------------------------------------------------------------
+# FE-coupled workload: a plate with a central hole in tension (stands in for the structural
+# models of Sec. 5, whose geometry and orientation fields are not available).
+
+
+@dataclass
+class PlateMesh:
+    xyz: np.ndarray        # [n_nodes, 3]
+    conn: np.ndarray       # [n_elem, 8] int32, hexahedron node order (-,-,-), (+,-,-), (+,+,-), (-,+,-), top
+    fixed: np.ndarray      # [3 n_nodes] bool: prescribed degrees of freedom
+    pull: np.ndarray       # [3 n_nodes] float: 1 on the x dofs of the loaded face (u = delta * pull there)
+    affine: np.ndarray     # [3 n_nodes] float: u_x = (x + H) / (2H), the uniform-strain field of unit delta
+    centroid: np.ndarray   # [n_elem, 3] mean of each element's nodes
+    H: float
+    R: float
+    T: float
+
+
+def plate_with_hole_mesh(n_t: int, n_r: int, n_z: int, R: float = 5.0, H: float = 25.0, T: float = 4.0,
+                         grade: float = 1.5) -> PlateMesh:
+    """O-grid hexahedral mesh of the square plate [-H, H]^2 with a central hole of radius R,
+    upper half of the thickness T (z in [0, T/2], the mid-plane z = 0 a symmetry plane).
+
+    4 n_t node columns around the hole (n_t even), n_r elements from the hole to the outer
+    square (spacing graded towards the hole by the exponent `grade`), n_z through the half
+    thickness: 4 n_t n_r n_z elements.  A node at angle theta sits between the hole point
+    R (cos, sin) and the square point H (cos, sin) / max(|cos|, |sin|).
+
+    Boundary conditions (tension along x): u_z = 0 on z = 0; u_x = 0 on the face x = -H;
+    u_x = delta on x = +H; u_y = 0 on the lines y = 0 of both loaded faces."""
+    if n_t % 2:
+        raise ValueError("n_t must be even")
+    nk = 4 * n_t
+    k = np.arange(nk)
+    theta = 2.0 * np.pi * k / nk - np.pi / 4.0
+    c, s = np.cos(theta), np.sin(theta)
+    sq = np.maximum(np.abs(c), np.abs(s))
+    inner = np.stack([R * c, R * s], axis=1)
+    outer = np.stack([H * c / sq, H * s / sq], axis=1)
+    rho = (np.arange(n_r + 1) / n_r) ** grade
+    z = 0.5 * T * np.arange(n_z + 1) / n_z
+    # node id = (j * (n_r + 1) + i) * nk + k
+    xy = inner[None, :, :] + rho[:, None, None] * (outer - inner)[None, :, :]      # [n_r+1, nk, 2]
+    xyz = np.zeros((n_z + 1, n_r + 1, nk, 3))
+    xyz[..., :2] = xy[None]
+    xyz[..., 2] = z[:, None, None]
+    xyz = xyz.reshape(-1, 3)
+
+    def nid(j, i, kk):
+        return (j * (n_r + 1) + i) * nk + kk % nk
+
+    J, I, Kk = np.meshgrid(np.arange(n_z), np.arange(n_r), np.arange(nk), indexing="ij")
+    J, I, Kk = J.ravel(), I.ravel(), Kk.ravel()
+    # local xi = radial (i), eta = angular (k), zeta = z: right-handed
+    conn = np.stack([nid(J, I, Kk), nid(J, I + 1, Kk), nid(J, I + 1, Kk + 1), nid(J, I, Kk + 1),
+                     nid(J + 1, I, Kk), nid(J + 1, I + 1, Kk), nid(J + 1, I + 1, Kk + 1), nid(J + 1, I, Kk + 1)],
+                    axis=1).astype(np.int32)
+    n_nodes = xyz.shape[0]
+    fixed = np.zeros((n_nodes, 3), dtype=bool)
+    pull = np.zeros((n_nodes, 3))
+    eps = 1e-9 * H
+    x, y = xyz[:, 0], xyz[:, 1]
+    fixed[np.abs(xyz[:, 2]) < eps, 2] = True
+    left = np.abs(x + H) < eps
+    right = np.abs(x - H) < eps
+    fixed[left, 0] = True
+    fixed[right, 0] = True
+    pull[right, 0] = 1.0
+    fixed[(left | right) & (np.abs(y) < eps), 1] = True
+    centroid = xyz[conn].mean(axis=1)
+    affine = np.zeros((n_nodes, 3))
+    affine[:, 0] = (x + H) / (2.0 * H)
+    return PlateMesh(xyz=xyz, conn=conn, fixed=fixed.reshape(-1), pull=pull.reshape(-1), affine=affine.reshape(-1),
+                     centroid=centroid, H=H, R=R, T=T)
+
+
+def plate_orientation_field(centroid: np.ndarray, R: float, H: float, T: float, seed: int) -> np.ndarray:
+    """Smooth fiber-orientation field A2 [n, 6] (plain components) at the given points.
+
+    Flow direction d: the potential flow of a uniform stream along x past the hole, its angle
+    perturbed by three seeded smooth modes (amplitude ~0.1 rad).  Through the thickness the
+    field goes from a nearly planar-isotropic core (mid-plane) to a flow-aligned skin (faces):
+    A2 = s A_flow + (1 - s) A_plane with s = 0.1 + 0.8 (2 z / T)^2,
+    A_flow = 0.92 d(x)d + 0.05 t(x)t + 0.03 e3(x)e3, A_plane = 0.485 (d(x)d + t(x)t) + 0.03 e3(x)e3,
+    t the in-plane normal of d (so lam3 = 0.03 >= 0.01 everywhere and lam1 > lam2)."""
+    rng = np.random.default_rng(seed)
+    x, y, z = centroid[:, 0], centroid[:, 1], centroid[:, 2]
+    r2 = np.maximum(x * x + y * y, (1e-6 * R) ** 2)
+    ux = 1.0 - R * R * (x * x - y * y) / (r2 * r2)
+    uy = -2.0 * R * R * x * y / (r2 * r2)
+    phi = np.arctan2(uy, ux)
+    for _ in range(3):
+        kx, ky = rng.uniform(0.5, 2.0, size=2) * np.pi / H
+        phi = phi + 0.1 * rng.standard_normal() * np.sin(kx * x + ky * y + rng.uniform(0, 2 * np.pi))
+    d = np.stack([np.cos(phi), np.sin(phi), np.zeros_like(phi)], axis=1)
+    t = np.stack([-np.sin(phi), np.cos(phi), np.zeros_like(phi)], axis=1)
+    e3 = np.array([0.0, 0.0, 1.0])
+    s = 0.1 + 0.8 * (2.0 * z / T) ** 2
+    l1 = s * 0.92 + (1 - s) * 0.485
+    l2 = s * 0.05 + (1 - s) * 0.485
+    A = (l1[:, None, None] * np.einsum("ni,nj->nij", d, d) + l2[:, None, None] * np.einsum("ni,nj->nij", t, t)
+         + 0.03 * np.outer(e3, e3)[None])
+    return np.ascontiguousarray(np.stack([A[:, 0, 0], A[:, 1, 1], A[:, 2, 2], A[:, 1, 2], A[:, 0, 2], A[:, 0, 1]],
+                                         axis=1))

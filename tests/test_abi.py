@@ -8,15 +8,15 @@ import re
 import numpy as np
 import pytest
 
-from paper_2103_08253_gb300 import dmn, workloads as W
+from paper_2103_08253_gb300 import dmn, fe, workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "dmn.h")).read()
+def declared_symbols(header="dmn.h", prefix="dmn_"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(dmn_[a-z_0-9]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(%s[a-z_0-9]+)\s*\(" % prefix, src)))
 
 
 def test_library_exports_every_declared_symbol():
@@ -26,6 +26,26 @@ def test_library_exports_every_declared_symbol():
     for s in syms:
         assert hasattr(lib, s), s
     assert set(dmn.EXPORTS) == set(syms)
+    fsyms = declared_symbols("fe.h", "fe_")
+    assert "fe_pcg" in fsyms
+    for s in fsyms:
+        assert hasattr(lib, s), s
+    assert set(fe.FE_EXPORTS) == set(fsyms)
+
+
+def test_fe_mesh_create_rejects_bad_meshes_without_touching_the_gpu():
+    lib = fe.load_library()
+    m = W.plate_with_hole_mesh(4, 2, 1)
+    h = ctypes.c_void_p(5)
+    bad = m.conn.copy()
+    bad[3, 2] = len(m.xyz)
+    rc = lib.fe_mesh_create(len(m.xyz), len(bad), m.xyz.ctypes.data_as(ctypes.c_void_p),
+                            bad.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+    assert rc == -1 and h.value is None and "out of range" in lib.fe_last_error(None).decode()
+    inv = np.ascontiguousarray(m.conn[:, [1, 0, 3, 2, 5, 4, 7, 6]])       # mirrored: det(J) < 0
+    rc = lib.fe_mesh_create(len(m.xyz), len(inv), m.xyz.ctypes.data_as(ctypes.c_void_p),
+                            inv.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+    assert rc == -1 and "det(J)" in lib.fe_last_error(None).decode()
 
 
 def _desc(K=3, M=3, w=None, kind=1):
@@ -44,7 +64,7 @@ def _desc(K=3, M=3, w=None, kind=1):
 @pytest.mark.parametrize("case,msg", [
     (dict(K=9), "K must be"), (dict(K=0), "K must be"), (dict(M=5), "M must be"),
     (dict(w=np.r_[np.ones(7), 0.0]), "weights"), (dict(w=np.r_[np.ones(7), np.nan]), "weights"),
-    (dict(kind=7), "phase kind")])
+    (dict(kind=7), "phase kind"), (dict(kind=2), "exponential-linear")])
 def test_create_rejects_bad_arguments_without_touching_the_gpu(case, msg):
     lib = dmn.load_library()
     d, keep = _desc(**case)

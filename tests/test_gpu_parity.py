@@ -154,6 +154,27 @@ def test_phase_combinations(phases):
         assert worst["stress"] <= TOL[prec] and worst["tangent"] <= TOL[prec], (prec, worst)
 
 
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_exponential_linear_matrix_depth8(prec):
+    """The paper's material set: glass fiber and the polyamide matrix with
+    exponential-linear hardening (Sec. 4.1, material table); K = 8, 48 points,
+    the first 10 of 30 increments to 3 % equivalent strain, plus both phases
+    inelastic at K = 4."""
+    K, n = 8, 48
+    tree = W.tree_d10_fit(K, seed=90, phases=(W.FIBER, W.MATRIX_EXPLIN))
+    A2, lam, Q = W.orientation_field(n, seed=91)
+    Ef = W.random6_path_final(n, 0.03, seed=92)
+    worst, out, st_o = run_path(tree, lam, Q, Ef, 30, prec, upto=10)
+    print(prec, worst)
+    assert worst["stress"] <= TOL[prec] and worst["tangent"] <= TOL[prec]
+    assert np.abs(st_o[0]).max() > 1e-3          # the matrix leaves did yield
+    tree = W.tree_d10_fit(4, seed=93, phases=(W.MATRIX_EXPLIN, W.MATRIX_EXPLIN))
+    A2, lam, Q = W.orientation_field(64, seed=94)
+    Ef = W.random6_path_final(64, 0.03, seed=95)
+    worst, _, _ = run_path(tree, lam, Q, Ef, 8, prec)
+    assert worst["stress"] <= TOL[prec] and worst["tangent"] <= TOL[prec], worst
+
+
 def test_status_codes_and_degenerate_inputs():
     K, n = 4, 64
     tree = W.tree_d10_fit(K, seed=80)
