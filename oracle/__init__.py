@@ -57,6 +57,7 @@ def _load():
         lib.oracle_rotate.argtypes = [_D, _D, _D, _D, _D]
         lib.oracle_interp_orientation.argtypes = [ctypes.c_long, _D, _D, _D]
         lib.oracle_state_size.argtypes = [ctypes.c_int, _D]
+        lib.oracle_state_size_w.argtypes = [ctypes.c_int, _D, _D]
         _lib = lib
     return _lib
 
@@ -81,9 +82,13 @@ def _phase_row(ph):
     return [ph.kind, ph.E, ph.nu, ph.sigma0, ph.H, getattr(ph, "sigma_inf", 0.0), getattr(ph, "k0", 0.0)]
 
 
-def state_size(K: int, phases) -> int:
+def state_size(K: int, phases, w=None) -> int:
+    """Doubles of state per point; with leaf weights w, of the compressed tree (weightless
+    leaves and the laminates without weight on both sides carry no state)."""
     m = phases_array(phases)
-    return int(_load().oracle_state_size(K, _p(m)))
+    if w is None:
+        return int(_load().oracle_state_size(K, _p(m)))
+    return int(_load().oracle_state_size_w(K, _p(m), _p(_f64(w))))
 
 
 def update(tree, lam, Q, E_n, dE, state_in, tol=1e-12, max_iter=50, line_search=False, nthreads=None):
@@ -94,7 +99,7 @@ def update(tree, lam, Q, E_n, dE, state_in, tol=1e-12, max_iter=50, line_search=
     lib = _load()
     lam = _f64(lam); Q = _f64(Q); E_n = _f64(E_n); dE = _f64(dE); state_in = _f64(state_in)
     n = lam.shape[0]
-    S = state_size(tree.K, tree.phases)
+    S = state_size(tree.K, tree.phases, tree.w)
     assert state_in.shape == (S, n), (state_in.shape, S, n)
     p = _f64(tree.p); q = _f64(tree.q); w = _f64(tree.w); m = phases_array(tree.phases)
     state_out = np.empty_like(state_in)

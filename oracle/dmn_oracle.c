@@ -76,11 +76,23 @@ typedef struct {
   double c1[OR_NMAX], c2[OR_NMAX];
   or_phase ph[2];
   double tol; int max_iter; int line_search;
-  /* ancestors of every leaf: for leaf l (0-based) and level k (1..K) the
-   * laminate index and the coefficient (-c2 or +c1) of its A block */
+  /* Tree compression (Sec. 3.1, removing laminates with a weightless
+   * subtree): a laminate is active when both of its subtrees carry weight;
+   * a laminate with one weightless subtree passes the other through (its
+   * jump does not reach a weighted leaf), one with two is dead.  Only the
+   * active laminates carry unknown jumps; they are numbered in the paper's
+   * order (cidx), and a leaf of zero weight has no strain, no state.  With
+   * all weights positive every laminate is active. */
+  int nact;
+  int act[OR_NMAX];           /* paper index of the c-th active laminate */
+  int cidx[OR_NMAX];          /* compressed index of laminate j, or -1 */
+  /* active ancestors of every leaf (0-based; none for a weightless leaf): the
+   * laminate's paper index and the coefficient (-c2 or +c1) of its A block */
+  int nanc[OR_LMAX];
   int anc_node[OR_LMAX][OR_KMAX];
   double anc_coef[OR_LMAX][OR_KMAX];
-  /* descendants / ancestors of every laminate (for the Cholesky pattern) */
+  /* active descendants / ancestors of every active laminate, as compressed
+   * indices (the Cholesky pattern) */
   int n_desc[OR_NMAX]; int* desc[OR_NMAX];
   int n_anc[OR_NMAX]; int anc[OR_NMAX][OR_KMAX];
   int nz;  /* number of inelastic leaves */
@@ -88,7 +100,7 @@ typedef struct {
 } or_tree;
 
 static void tree_free(or_tree* t) {
-  for (int j = 0; j < t->N; ++j) free(t->desc[j]);
+  for (int c = 0; c < t->nact; ++c) free(t->desc[c]);
 }
 
 /* weights: Sec. 2.1, w^i_k = w^{2i-1}_{k+1} + w^{2i}_{k+1}; c1 = w_left / (w_left + w_right). */
@@ -105,7 +117,8 @@ static int tree_init(or_tree* t, int K, int M, const double* p, const double* q,
     if (t->ph[f].kind < 0 || t->ph[f].kind > 2) return -1;
   }
   double sw = 0.0;
-  for (int l = 0; l < t->L; ++l) { if (!(w[l] > 0.0)) return -2; sw += w[l]; }
+  for (int l = 0; l < t->L; ++l) { if (!(w[l] >= 0.0) || !isfinite(w[l])) return -2; sw += w[l]; }
+  if (!(sw > 0.0)) return -2;
   for (int l = 0; l < t->L; ++l) t->w[l] = w[l] / sw;
   /* subtree weights level by level, leaves -> root */
   double Wlev[OR_KMAX + 2][OR_LMAX];
@@ -115,38 +128,51 @@ static int tree_init(or_tree* t, int K, int M, const double* p, const double* q,
       double wl = Wlev[k + 1][2 * i - 2], wr = Wlev[k + 1][2 * i - 1];
       Wlev[k][i - 1] = wl + wr;
       int j = node_index(K, k, i);
-      t->c1[j] = wl / (wl + wr);
+      t->c1[j] = (wl + wr > 0.0) ? wl / (wl + wr) : 0.5;   /* dead laminate: any split, never used */
       t->c2[j] = 1.0 - t->c1[j];
+      t->cidx[j] = (wl > 0.0 && wr > 0.0) ? 0 : -1;
     }
-  for (int l = 1; l <= t->L; ++l)
+  t->nact = 0;
+  for (int j = 0; j < t->N; ++j)
+    if (t->cidx[j] >= 0) { t->cidx[j] = t->nact; t->act[t->nact++] = j; }
+  for (int l = 1; l <= t->L; ++l) {
+    t->nanc[l - 1] = 0;
+    if (!(t->w[l - 1] > 0.0)) continue;
     for (int k = 1; k <= K; ++k) {
       int i = (l - 1) / (1 << (K - k + 1)) + 1;
       int j = node_index(K, k, i);
+      if (t->cidx[j] < 0) continue;
       int s = leaf_side(K, k, i, l);
-      t->anc_node[l - 1][k - 1] = j;
-      t->anc_coef[l - 1][k - 1] = (s < 0) ? -t->c2[j] : t->c1[j];
+      t->anc_node[l - 1][t->nanc[l - 1]] = j;
+      t->anc_coef[l - 1][t->nanc[l - 1]++] = (s < 0) ? -t->c2[j] : t->c1[j];
     }
-  for (int j = 0; j < t->N; ++j) {
-    int k, i; node_level_pos(K, j, &k, &i);
-    t->n_anc[j] = 0;
+  }
+  for (int c = 0; c < t->nact; ++c) {
+    int j = t->act[c], k, i;
+    node_level_pos(K, j, &k, &i);
+    t->n_anc[c] = 0;
     for (int kk = k - 1; kk >= 1; --kk) {
       int ii = (i - 1) / (1 << (k - kk)) + 1;
-      t->anc[j][t->n_anc[j]++] = node_index(K, kk, ii);
+      int a = t->cidx[node_index(K, kk, ii)];
+      if (a >= 0) t->anc[c][t->n_anc[c]++] = a;
     }
     int cnt = 0;
     for (int kk = k + 1; kk <= K; ++kk) cnt += 1 << (kk - k);
-    t->n_desc[j] = cnt;
-    t->desc[j] = (int*)malloc(sizeof(int) * (cnt > 0 ? cnt : 1));
-    int c = 0;
+    t->desc[c] = (int*)malloc(sizeof(int) * (cnt > 0 ? cnt : 1));
+    int d = 0;
     for (int kk = K; kk > k; --kk) {                /* in index order (deepest first) */
       int span = 1 << (kk - k);
-      for (int ii = (i - 1) * span + 1; ii <= i * span; ++ii) t->desc[j][c++] = node_index(K, kk, ii);
+      for (int ii = (i - 1) * span + 1; ii <= i * span; ++ii) {
+        int a = t->cidx[node_index(K, kk, ii)];
+        if (a >= 0) t->desc[c][d++] = a;
+      }
     }
+    t->n_desc[c] = d;
   }
   t->nz = 0;
   for (int l = 0; l < t->L; ++l) {
     int f = l % 2;   /* leaf l+1 odd -> phase 1, even -> phase 2 */
-    t->z_slot[l] = (t->ph[f].kind != 0) ? t->nz++ : -1;
+    t->z_slot[l] = (t->ph[f].kind != 0 && t->w[l] > 0.0) ? t->nz++ : -1;
   }
   return 0;
 }
@@ -331,11 +357,11 @@ typedef struct {
 static void leaf_strains(const or_tree* t, or_work* ws, const double E[6], const double* a) {
   for (int l = 0; l < t->L; ++l) {
     for (int I = 0; I < 6; ++I) ws->eps[l][I] = E[I];
-    for (int k = 0; k < t->K; ++k) {
-      int j = t->anc_node[l][k];
+    for (int k = 0; k < t->nanc[l]; ++k) {
+      int j = t->anc_node[l][k], cj = t->cidx[j];
       double c = t->anc_coef[l][k];
       for (int I = 0; I < 6; ++I)
-        for (int m = 0; m < 3; ++m) ws->eps[l][I] += c * ws->Nm[j][I][m] * a[3 * j + m];
+        for (int m = 0; m < 3; ++m) ws->eps[l][I] += c * ws->Nm[j][I][m] * a[3 * cj + m];
     }
   }
 }
@@ -347,31 +373,31 @@ static double evaluate(const or_tree* t, or_work* ws, const double E[6], const d
   for (int l = 0; l < t->L; ++l) {
     double g;
     phase_law(&t->ph[l % 2], ws->eps[l], ws->z_n[l], ws->sig[l], ws->D[l], ws->z_new[l], &g);
-    if (g < ws->gap) ws->gap = g;
+    if (g < ws->gap && t->w[l] > 0.0) ws->gap = g;
   }
   for (int I = 0; I < 6; ++I) ws->sbar[I] = 0.0;
   for (int l = 0; l < t->L; ++l)
     for (int I = 0; I < 6; ++I) ws->sbar[I] += t->w[l] * ws->sig[l][I];
-  for (int r = 0; r < 3 * t->N; ++r) ws->R[r] = 0.0;
+  for (int r = 0; r < 3 * t->nact; ++r) ws->R[r] = 0.0;
   for (int l = 0; l < t->L; ++l)
-    for (int k = 0; k < t->K; ++k) {
-      int j = t->anc_node[l][k];
+    for (int k = 0; k < t->nanc[l]; ++k) {
+      int j = t->anc_node[l][k], cj = t->cidx[j];
       double c = t->anc_coef[l][k] * t->w[l];
       for (int m = 0; m < 3; ++m)
-        for (int I = 0; I < 6; ++I) ws->R[3 * j + m] += c * ws->Nm[j][I][m] * ws->sig[l][I];
+        for (int I = 0; I < 6; ++I) ws->R[3 * cj + m] += c * ws->Nm[j][I][m] * ws->sig[l][I];
     }
   double s = 0.0;
-  for (int r = 0; r < 3 * t->N; ++r) s += ws->R[r] * ws->R[r];
+  for (int r = 0; r < 3 * t->nact; ++r) s += ws->R[r] * ws->R[r];
   return sqrt(s);
 }
 
 /* J = A^T W D A, assembled leaf by leaf over pairs of the leaf's ancestors. */
 static void assemble_J(const or_tree* t, or_work* ws) {
-  int n = 3 * t->N;
+  int n = 3 * t->nact;
   memset(ws->J, 0, sizeof(double) * (size_t)n * n);
   for (int l = 0; l < t->L; ++l) {
     double DN[OR_KMAX][6][3];
-    for (int k = 0; k < t->K; ++k) {
+    for (int k = 0; k < t->nanc[l]; ++k) {
       int j = t->anc_node[l][k];
       for (int I = 0; I < 6; ++I)
         for (int m = 0; m < 3; ++m) {
@@ -380,15 +406,16 @@ static void assemble_J(const or_tree* t, or_work* ws) {
           DN[k][I][m] = s;
         }
     }
-    for (int k1 = 0; k1 < t->K; ++k1)
-      for (int k2 = 0; k2 < t->K; ++k2) {
+    for (int k1 = 0; k1 < t->nanc[l]; ++k1)
+      for (int k2 = 0; k2 < t->nanc[l]; ++k2) {
         int j1 = t->anc_node[l][k1], j2 = t->anc_node[l][k2];
+        int c1 = t->cidx[j1], c2 = t->cidx[j2];
         double c = t->w[l] * t->anc_coef[l][k1] * t->anc_coef[l][k2];
         for (int m1 = 0; m1 < 3; ++m1)
           for (int m2 = 0; m2 < 3; ++m2) {
             double s = 0.0;
             for (int I = 0; I < 6; ++I) s += ws->Nm[j1][I][m1] * DN[k2][I][m2];
-            ws->J[(size_t)(3 * j1 + m1) * n + 3 * j2 + m2] += c * s;
+            ws->J[(size_t)(3 * c1 + m1) * n + 3 * c2 + m2] += c * s;
           }
       }
   }
@@ -399,10 +426,10 @@ static void assemble_J(const or_tree* t, or_work* ws) {
  * of row r is the laminate of column c or one of its ancestors; the sums run
  * over the descendants of the column's laminate. */
 static int cholesky(const or_tree* t, or_work* ws) {
-  int n = 3 * t->N;
+  int n = 3 * t->nact;
   double* L = ws->J;
 #define LL(r, c) L[(size_t)(r) * n + (c)]
-  for (int cn = 0; cn < t->N; ++cn)
+  for (int cn = 0; cn < t->nact; ++cn)
     for (int a = 0; a < 3; ++a) {
       int c = 3 * cn + a;
       double s = LL(c, c);
@@ -431,9 +458,9 @@ static int cholesky(const or_tree* t, or_work* ws) {
 
 /* solve L L^T x = b in place */
 static void chol_solve(const or_tree* t, or_work* ws, double* x) {
-  int n = 3 * t->N;
+  int n = 3 * t->nact;
   double* L = ws->J;
-  for (int rn = 0; rn < t->N; ++rn)
+  for (int rn = 0; rn < t->nact; ++rn)
     for (int a = 0; a < 3; ++a) {
       int r = 3 * rn + a;
       double s = x[r];
@@ -442,7 +469,7 @@ static void chol_solve(const or_tree* t, or_work* ws, double* x) {
       for (int b = 0; b < a; ++b) s -= LL(r, 3 * rn + b) * x[3 * rn + b];
       x[r] = s / LL(r, r);
     }
-  for (int cn = t->N - 1; cn >= 0; --cn)
+  for (int cn = t->nact - 1; cn >= 0; --cn)
     for (int a = 2; a >= 0; --a) {
       int c = 3 * cn + a;
       double s = x[c];
@@ -462,20 +489,20 @@ static double mandel_norm(const double v[6]) {
 
 /* C_algo = [I..I]^T W [D + D A dadE], with dadE from the six-RHS system. */
 static void algorithmic_tangent(const or_tree* t, or_work* ws, double C[6][6]) {
-  int n = 3 * t->N;
+  int n = 3 * t->nact;
   double* X = (double*)malloc(sizeof(double) * (size_t)n * 6);
   for (int col = 0; col < 6; ++col) {
     double* x = X + (size_t)col * n;
     for (int r = 0; r < n; ++r) x[r] = 0.0;
     /* rhs = -A^T W D e_col */
     for (int l = 0; l < t->L; ++l)
-      for (int k = 0; k < t->K; ++k) {
+      for (int k = 0; k < t->nanc[l]; ++k) {
         int j = t->anc_node[l][k];
         double c = t->anc_coef[l][k] * t->w[l];
         for (int m = 0; m < 3; ++m) {
           double s = 0.0;
           for (int I = 0; I < 6; ++I) s += ws->Nm[j][I][m] * ws->D[l][I][col];
-          x[3 * j + m] -= c * s;
+          x[3 * t->cidx[j] + m] -= c * s;
         }
       }
     chol_solve(t, ws, x);
@@ -484,12 +511,12 @@ static void algorithmic_tangent(const or_tree* t, or_work* ws, double C[6][6]) {
   for (int l = 0; l < t->L; ++l) {
     double G[6][6];  /* I + (A dadE)_l */
     for (int I = 0; I < 6; ++I) for (int J = 0; J < 6; ++J) G[I][J] = (I == J) ? 1.0 : 0.0;
-    for (int k = 0; k < t->K; ++k) {
+    for (int k = 0; k < t->nanc[l]; ++k) {
       int j = t->anc_node[l][k];
       double c = t->anc_coef[l][k];
       for (int I = 0; I < 6; ++I)
         for (int col = 0; col < 6; ++col)
-          for (int m = 0; m < 3; ++m) G[I][col] += c * ws->Nm[j][I][m] * X[(size_t)col * n + 3 * j + m];
+          for (int m = 0; m < 3; ++m) G[I][col] += c * ws->Nm[j][I][m] * X[(size_t)col * n + 3 * t->cidx[j] + m];
     }
     for (int I = 0; I < 6; ++I)
       for (int J = 0; J < 6; ++J) {
@@ -548,13 +575,13 @@ static int all_finite(const double* v, int n) {
 static void update_point(const or_tree* t, or_work* ws, long n, long pt, const double* lam, const double* Q,
                          const double* E_n, const double* dE, const double* state_in, double* state_out,
                          double* stress, double* tangent, int* iters, int* status, double* yield_gap) {
-  int N = t->N, nzf = 6 * t->nz;
+  int N = t->nact, nzf = 6 * t->nz;
   const double* Qp = Q + 9 * pt;
   double Eg[6], E[6];
   for (int I = 0; I < 6; ++I) Eg[I] = E_n[6 * pt + I] + dE[6 * pt + I];
   rotate_sym(Qp, Eg, E, 1);
   normals(t, lam[2 * pt], lam[2 * pt + 1], ws->nrm);
-  for (int j = 0; j < N; ++j) sym_operator(ws->nrm[j], ws->Nm[j]);
+  for (int j = 0; j < t->N; ++j) sym_operator(ws->nrm[j], ws->Nm[j]);
   /* z^n of every leaf (elastic leaves: zeros, unused) */
   for (int l = 0; l < t->L; ++l) {
     for (int c = 0; c < 7; ++c) ws->z_n[l][c] = 0.0;
@@ -632,7 +659,7 @@ static void update_point(const or_tree* t, or_work* ws, long n, long pt, const d
 
 static or_work* work_alloc(const or_tree* t) {
   or_work* ws = (or_work*)calloc(1, sizeof(or_work));
-  size_t n = 3 * (size_t)t->N;
+  size_t n = 3 * (size_t)(t->nact > 0 ? t->nact : 1);
   ws->J = (double*)calloc(n * n, sizeof(double));
   return ws;
 }
@@ -649,7 +676,18 @@ int oracle_state_size(int K, const double* mat) {
   for (int l = 0; l < (1 << K); ++l) w[l] = 1.0;
   double pq[OR_NMAX * 3] = {0};
   if (tree_init(&t, K, 3, pq, pq, w, mat, 1e-12, 1, 0) != 0) return -1;
-  int s = 6 * t.nz + 3 * t.N;
+  int s = 6 * t.nz + 3 * t.nact;
+  tree_free(&t);
+  return s;
+}
+
+/* doubles of state per point for the given weights (compressed tree) */
+int oracle_state_size_w(int K, const double* mat, const double* w) {
+  or_tree t;
+  if (K < 1 || K > OR_KMAX) return -1;
+  double pq[OR_NMAX * 6] = {0};
+  if (tree_init(&t, K, 3, pq, pq, w, mat, 1e-12, 1, 0) != 0) return -1;
+  int s = 6 * t.nz + 3 * t.nact;
   tree_free(&t);
   return s;
 }
@@ -703,7 +741,7 @@ int oracle_gradient_operator(int K, int M, const double* p, const double* q, con
   int nc = 3 * t.N;
   memset(A, 0, sizeof(double) * 6 * t.L * nc);
   for (int l = 0; l < t.L; ++l)
-    for (int k = 0; k < t.K; ++k) {
+    for (int k = 0; k < t.nanc[l]; ++k) {
       int j = t.anc_node[l][k];
       for (int I = 0; I < 6; ++I)
         for (int m = 0; m < 3; ++m) A[(size_t)(6 * l + I) * nc + 3 * j + m] = t.anc_coef[l][k] * ws->Nm[j][I][m];
@@ -726,7 +764,7 @@ int oracle_newton_system(int K, int M, const double* p, const double* q, const d
   for (int j = 0; j < t.N; ++j) sym_operator(ws->nrm[j], ws->Nm[j]);
   for (int l = 0; l < t.L; ++l) for (int c = 0; c < 7; ++c) ws->z_n[l][c] = z_n[7 * l + c];
   evaluate(&t, ws, E, a);
-  int n = 3 * t.N;
+  int n = 3 * t.nact;
   assemble_J(&t, ws);
   memcpy(J, ws->J, sizeof(double) * (size_t)n * n);
   int rc = cholesky(&t, ws);

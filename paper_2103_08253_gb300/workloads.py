@@ -359,3 +359,22 @@ def plate_orientation_field(centroid: np.ndarray, R: float, H: float, T: float, 
          + 0.03 * np.outer(e3, e3)[None])
     return np.ascontiguousarray(np.stack([A[:, 0, 0], A[:, 1, 1], A[:, 2, 2], A[:, 1, 2], A[:, 0, 2], A[:, 0, 1]],
                                          axis=1))
+
+
+def tree_with_zero_weights(K: int, seed: int, zero_fraction: float = 0.3, phases=(FIBER, MATRIX)) -> TreeParams:
+    """A D10-fitted tree whose leaf weights are partly zero, as after the offline training
+    (Sec. 3.1: weights that reach zero stay there and the tree is compressed).  One whole
+    subtree of the root's right child at depth 2 (a quarter of the leaves, when K >= 3) and a
+    random further share of single leaves get weight zero, so the compressed tree has
+    pass-through laminates, removed subtrees and leaves whose sibling is a laminate."""
+    t = tree_d10_fit(K, seed=seed, phases=phases)
+    rng = np.random.default_rng(seed + 7919)
+    L = 1 << K
+    w = t.w.copy()
+    if K >= 3:
+        w[L // 2: L // 2 + L // 4] = 0.0
+    alive = np.nonzero(w > 0)[0]
+    k = int(round(zero_fraction * L)) - (L - alive.size)
+    if k > 0:
+        w[rng.choice(alive, size=min(k, alive.size - 1), replace=False)] = 0.0
+    return TreeParams(K=K, M=t.M, p=t.p, q=t.q, w=w, phases=t.phases)
