@@ -42,6 +42,8 @@ N_INCREMENTS = 50
 EPS_EQ = 0.03
 SEED_TREE, SEED_ORI, SEED_PATH = 2103, 8253, 1208
 WORKLOAD = "K=8 D10-interpolated DMN, 2^20 points/GPU, random 6-comp paths, 50 increments to 3% eq. strain"
+WORKLOAD_CMP = ("K=8 D10-interpolated DMN compressed to 70% of its leaves (weights of zero, 178 of 255 laminates "
+                "left), 2^20 points/GPU, random 6-comp paths, 50 increments to 3% eq. strain")
 
 # FP64 peak: 152 SMs x 4 sub-partitions x 0.5 DFMA/clk x 2 flop x 2.07 GHz
 PEAK_F64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.07
@@ -66,38 +68,81 @@ F_STATE_NODE = 39       # state pass: per laminate (strains from the jumps)
 F_STATE_J2 = 68         # state pass: per J2 leaf (return mapping and new state)
 
 
-def pass_flops(K):
-    """(FP64 flops, T flops) of one Newton pass without the jump correction."""
-    N, L = (1 << K) - 1, 1 << K
-    nbot = L // 2
-    f64 = N * (F_NODE_F64 + F_RES) + nbot * (F_LEAF_EL + F_LEAF_J2) + F_TEST
-    ft = (N - nbot) * (F_COND + F_DEPS) + nbot * F_COND_BOTTOM
+F_LEAF_SUB = 84         # a leaf whose sibling is a laminate: its 21 tangent entries as a subtree (T)
+
+
+def tree_counts(w):
+    """Laminates and leaves of the tree with leaf weights w after compression (leaves of weight
+    zero removed, laminates with one weightless side passed through): dict(N = laminates,
+    pairs = laminates whose children are two leaves, inner = the other laminates, single =
+    leaves whose sibling is a laminate, el / j2 = remaining fiber (odd) / matrix (even) leaves)."""
+    w = np.asarray(w, dtype=np.float64)
+    L = w.size
+    Wh = np.zeros(2 * L)
+    Wh[L:] = w
+    for h in range(L - 1, 0, -1):
+        Wh[h] = Wh[2 * h] + Wh[2 * h + 1]
+
+    def kind(h):        # 'leaf', 'lam' or None after compression
+        if Wh[h] <= 0:
+            return None
+        if h >= L:
+            return "leaf"
+        if Wh[2 * h] > 0 and Wh[2 * h + 1] > 0:
+            return "lam"
+        return kind(2 * h if Wh[2 * h] > 0 else 2 * h + 1)
+
+    def child(h):       # the compressed node standing for heap node h
+        while h < L and not (Wh[2 * h] > 0 and Wh[2 * h + 1] > 0):
+            h = 2 * h if Wh[2 * h] > 0 else 2 * h + 1
+        return h
+
+    c = dict(N=0, pairs=0, inner=0, single=0, el=int((w[0::2] > 0).sum()), j2=int((w[1::2] > 0).sum()))
+    for h in range(1, L):
+        if not (Wh[2 * h] > 0 and Wh[2 * h + 1] > 0):
+            continue
+        c["N"] += 1
+        kl, kr = kind(child(2 * h)), kind(child(2 * h + 1))
+        if kl == "leaf" and kr == "leaf":
+            c["pairs"] += 1
+        else:
+            c["inner"] += 1
+            c["single"] += (kl == "leaf") + (kr == "leaf")
+    return c
+
+
+def pass_flops(K, w=None):
+    """(FP64 flops, T flops) of one Newton pass without the jump correction (w: leaf weights of
+    a compressed tree; None: the full tree)."""
+    c = tree_counts(np.ones(1 << K) if w is None else w)
+    f64 = c["N"] * (F_NODE_F64 + F_RES) + c["el"] * F_LEAF_EL + c["j2"] * F_LEAF_J2 + F_TEST
+    ft = c["inner"] * (F_COND + F_DEPS) + c["pairs"] * F_COND_BOTTOM + c["single"] * F_LEAF_SUB
     return f64, ft
 
 
-def corr_flops(K):
+def corr_flops(K, w=None):
     """(FP64 flops, T flops) of one jump correction of all laminates."""
-    N = (1 << K) - 1
+    N = tree_counts(np.ones(1 << K) if w is None else w)["N"]
     return N * F_A, N * F_DA
 
 
-def newton_flops(K, iters_sum, npts, mixed):
+def newton_flops(K, iters_sum, npts, mixed, w=None):
     """(FP64, FP32) flops of the Newton kernel over npts points with iters_sum corrections:
     one pass per point evaluates the starting jumps, one more per correction."""
-    f64, ft = pass_flops(K)
-    c64, ct = corr_flops(K)
+    f64, ft = pass_flops(K, w)
+    c64, ct = corr_flops(K, w)
     passes = iters_sum + npts
     F64 = passes * f64 + iters_sum * c64
     FT = passes * ft + iters_sum * ct
     return (F64, FT) if mixed else (F64 + FT, 0.0)
 
 
-def final_flops(K, npts, mixed):
+def final_flops(K, npts, mixed, w=None):
     """FP64 flops of the final kernel (state pass and rotation; mixed form: plus one FP64 pass)."""
-    N, L = (1 << K) - 1, 1 << K
-    f = npts * (F_ROTATE + N * F_STATE_NODE + (L // 2) * F_STATE_J2)
+    c = tree_counts(np.ones(1 << K) if w is None else w)
+    f = npts * (F_ROTATE + c["N"] * F_STATE_NODE + c["j2"] * F_STATE_J2)
     if mixed:
-        f64, ft = pass_flops(K)
+        f64, ft = pass_flops(K, w)
         f += npts * (f64 + ft)
     return f
 
@@ -165,8 +210,9 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
-def make_workload(n, rank):
-    tree = W.tree_d10_fit(K_DEPTH, seed=SEED_TREE)
+def make_workload(n, rank, compressed=False):
+    tree = (W.tree_with_zero_weights(K_DEPTH, seed=SEED_TREE) if compressed
+            else W.tree_d10_fit(K_DEPTH, seed=SEED_TREE))
     A2, lam, Q = W.orientation_field(n, seed=SEED_ORI + 1000 * rank)
     Ef = W.random6_path_final(n, EPS_EQ, seed=SEED_PATH + 1000 * rank)
     return tree, A2, lam, Q, Ef
@@ -177,7 +223,7 @@ def oracle_baseline(tree, A2, Ef, idx, warmup, steps, threads):
     import oracle
     A2s = A2[idx]
     lam, Q = oracle.interp_orientation(A2s)
-    S = W.state_size(K_DEPTH)
+    S = oracle.state_size(tree.K, tree.phases, tree.w)
     st = np.zeros((S, len(idx)))
     for s in range(1, warmup + 1):
         En, dE = W.proportional_increment(Ef[idx], s, N_INCREMENTS)
@@ -194,7 +240,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    tree, A2, lam, Q, Ef = make_workload(args.points, 0)
+    tree, A2, lam, Q, Ef = make_workload(args.points, 0, args.workload == "k8-compressed")
     cores = os.cpu_count() or 1
     m = args.ref_points
     idx = np.arange(m)
@@ -203,7 +249,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "K": K_DEPTH, "points_per_step": m,
+            "config": {"workload": WORKLOAD_CMP if args.workload == "k8-compressed" else WORKLOAD, "K": K_DEPTH,
+                       "points_per_step": m,
                        "increments": [args.warmup + 1, args.warmup + args.steps]},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "first %d points of the workload, increments %d..%d (after %d untimed)"
@@ -307,7 +354,7 @@ def parity_sample(form, r, ctx, args, pidx):
     import oracle
     tree, A2, Ef = ctx["tree"], ctx["A2_np"], ctx["Ef_np"]
     lam, Q = oracle.interp_orientation(A2[pidx])
-    S = W.state_size(K_DEPTH)
+    S = oracle.state_size(tree.K, tree.phases, tree.w)
     st = np.zeros((S, len(pidx)))
     for s in range(1, args.warmup + args.steps + 1):
         En, dE = W.proportional_increment(Ef[pidx], s, N_INCREMENTS)
@@ -361,28 +408,29 @@ def run_e2e(r, ctx, args, dist):
             "status_ok": int((out_h["status"] == 0).sum().item())}
 
 
-def roofline_f64(r, n, steps):
-    F, _ = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=False)
+def roofline_f64(r, n, steps, w=None):
+    F, _ = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=False, w=w)
     t = r["kms"]["newton"] * 1e-3
     ach = F / t / 1e9
-    tr = ncu_traffic("k_newton_f64", n)
+    tr = ncu_traffic("k_newton_f64" + ("_compressed" if w is not None and (np.asarray(w) == 0).any() else ""), n)
     return {"bound": "alu", "kernel": "k_newton<double>", "achieved": ach, "peak": PEAK_F64_GFLOPS,
             "unit": "GFLOP/s (FP64)", "frac": ach / PEAK_F64_GFLOPS, "traffic": tr,
             "flops_per_launch": F / steps, "launch_ms": r["kms"]["newton"] / steps,
             "peak_note": "derived: 152 SM x 4 SMSP x 0.5 DFMA/clk x 2 flop x 2.07 GHz"}
 
 
-def roofline_mixed(r, n, steps):
-    F64, F32 = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=True)
+def roofline_mixed(r, n, steps, w=None):
+    F64, F32 = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=True, w=w)
     t = r["kms"]["newton"] * 1e-3
     tb = F64 / (PEAK_F64_GFLOPS * 1e9) + F32 / (PEAK_F32_GFLOPS * 1e9)
-    Ff = final_flops(K_DEPTH, n * steps, mixed=True)
+    Ff = final_flops(K_DEPTH, n * steps, mixed=True, w=w)
     tf = r["kms"]["final"] * 1e-3
     fin = {"kernel": "k_final<sweep>", "achieved": Ff / tf / 1e9, "peak": PEAK_F64_GFLOPS, "unit": "GFLOP/s (FP64)",
            "frac": Ff / tf / 1e9 / PEAK_F64_GFLOPS, "launch_ms": r["kms"]["final"] / steps}
     return {"bound": "alu", "kernel": "k_newton<float>", "achieved": tb / t * PEAK_F64_GFLOPS,
             "peak": PEAK_F64_GFLOPS, "unit": "GFLOP/s (FP64-equivalent: F64/P64 + F32/P32)", "frac": tb / t,
-            "traffic": ncu_traffic("k_newton_mixed", n), "flops_f64_per_launch": F64 / steps,
+            "traffic": ncu_traffic("k_newton_mixed" + ("_compressed" if w is not None and (np.asarray(w) == 0).any()
+                                                       else ""), n), "flops_f64_per_launch": F64 / steps,
             "flops_f32_per_launch": F32 / steps, "launch_ms": r["kms"]["newton"] / steps, "final_kernel": fin}
 
 
@@ -570,6 +618,45 @@ def run_plate(args):
     return 0
 
 
+# ---------------------------------------------------------------------------------------------
+# Offline training (differentiation workload): a depth-8 DMN with trainable angle coefficients
+# and leaf weights fitted to a seeded target DMN on 4096 elastic stiffness samples (relative
+# error in the Sec. 3.1 loss, p = 1, q = 10, penalty 1e3) plus 4096 stresses of one
+# elastoplastic increment from the virgin state (1-3 % equivalent strain); AMSGrad with the
+# schedule of Sec. 4.4.  Forward: dmn_update (6 unit strains per stiffness sample), backward:
+# dmn_grad.  A secondary measurement (not the headline line).
+TRAIN_SAMPLES = 4096
+
+
+def run_train(args):
+    import torch
+    from paper_2103_08253_gb300 import training
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    target = W.tree_d10_fit(K_DEPTH, seed=SEED_TREE + 31)
+    tr = training.Trainer(K_DEPTH, target, TRAIN_SAMPLES, seed=SEED_TREE + 32, elastic_matrix=W.Phase(0, 3000.0, 0.35),
+                          plastic=W.MATRIX, n_plastic=TRAIN_SAMPLES)
+    tr.train(args.warmup)
+    clocks = ClockSampler("0")
+    t = tr.train(args.steps)
+    clk = clocks.stop()
+    hist = tr.history
+    n_upd = TRAIN_SAMPLES * 6 + TRAIN_SAMPLES          # updates per epoch (forward), each with its adjoint
+    line = {"metric": "DMN offline training: samples/s (forward + adjoint) at depth 8", "unit": "samples/s",
+            "value": 2 * TRAIN_SAMPLES * args.steps / t, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "K=8, %d stiffness samples (elastic phases) + %d stress samples (one J2 increment),"
+                                   " target = seeded DMN, AMSGrad + cosine schedule (Sec. 4.4); step = epoch"
+                                   % (TRAIN_SAMPLES, TRAIN_SAMPLES),
+                       "dmn_updates_per_epoch": n_upd},
+            "gp_updates_per_s": n_upd * args.steps / t,
+            "loss": [round(h[0], 6) for h in hist], "mean_stiffness_error": [round(h[2], 6) for h in hist],
+            "clocks": clk}
+    tr.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -587,12 +674,14 @@ def main():
     ap.add_argument("--parity-points", type=int, default=16)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the library's default launch shape instead of autotuning it")
-    ap.add_argument("--workload", default="k8", choices=["k8", "mixed-depth", "plate"],
+    ap.add_argument("--workload", default="k8", choices=["k8", "k8-compressed", "mixed-depth", "plate", "train"],
                     help="k8: the headline depth-8 batch; mixed-depth: 4M points of depths 5-8; plate: the "
                          "FE-coupled plate with a hole (both secondary)")
     args = ap.parse_args()
     if args.workload == "plate":
         return run_plate(args)
+    if args.workload == "train":
+        return run_train(args)
     if args.workload == "mixed-depth":
         if args.points == 1 << 20:
             args.points = 1 << 22
@@ -621,7 +710,8 @@ def run_gpu(args):
     from paper_2103_08253_gb300 import dmn
     dmn.load_library()
     n = args.points
-    tree, A2, lam_np, Q_np, Ef = make_workload(n, rank)
+    cmp = args.workload == "k8-compressed"
+    tree, A2, lam_np, Q_np, Ef = make_workload(n, rank, cmp)
     try:
         smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
@@ -656,7 +746,8 @@ def run_gpu(args):
         forms_out[form] = {"value": v, "unit": UNIT, "ms_per_step": r["t_ms"] / steps,
                            "kernel_ms_per_step": {k: x / steps for k, x in r["kms"].items()},
                            "newton_iters_per_update": r["iters_sum"] / (n * steps), "iters_hist": r["iters_hist"],
-                           "roofline": roofline_f64(r, n, steps) if form == "f64" else roofline_mixed(r, n, steps),
+                           "roofline": (roofline_f64(r, n, steps, tree.w) if form == "f64"
+                                        else roofline_mixed(r, n, steps, tree.w)),
                            "launch": r["launch"],
                            "parity_vs_oracle": r.get("parity"), "clocks": r["clocks"]}
     main_form = "f64" if "f64" in results else forms[0]
@@ -673,9 +764,11 @@ def run_gpu(args):
             "steps": steps, "warmup": args.warmup, "ms_per_step": mr["t_ms"] / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_form == "f64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "K": K_DEPTH, "points_per_gpu": n, "increments": N_INCREMENTS,
+            "config": {"workload": WORKLOAD_CMP if cmp else WORKLOAD, "K": K_DEPTH, "points_per_gpu": n,
+                       "increments": N_INCREMENTS,
                        "timed_increments": [args.warmup + 1, args.warmup + steps],
-                       "l2": "no flush: per-step inputs (state %.1f GB) exceed L2" % (W.state_size(K_DEPTH) * n * 8e-9),
+                       "l2": "no flush: per-step inputs (state %.1f GB) exceed L2"
+                             % ((6 * tree_counts(tree.w)["j2"] + 3 * tree_counts(tree.w)["N"]) * n * 8e-9),
                        "parallelism": "independent point shards per GPU, no collective"},
             "roofline": forms_out[main_form]["roofline"], "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 4 * steps, "clocks": mr["clocks"], "forms": forms_out}

@@ -41,6 +41,10 @@ struct Tree {
   float* d_cf = nullptr;   // c1f [N], c2f [N], c12f [N]
   double wsum = 1.0;       // sum of the leaf weights as given
   PhaseDev ph[2];
+  // compressed trees (some leaf weight zero): N laminates left, Lc leaves left,
+  // traversal tables lf [Lc] (int4), pre [N], post [N] in one allocation
+  int cmp = 0, Lc = 0;
+  int* d_tab = nullptr;
 };
 
 }  // namespace
@@ -74,6 +78,7 @@ struct dmn_handle {
   dmn_options opt;
   int device = 0, n_sm = 0;
   int64_t nslots = 0;
+  bool cmp = false;             // trees walked by tables (some tree has weightless leaves)
   WorkSet ws[2];                // [0]: dmn_update; [1]: second stage of dmn_update_host
   HostPipe hp;
   double* gwork = nullptr;      // dmn_grad per-point work, one chunk
@@ -103,6 +108,10 @@ TreeDev tree_dev(const Tree& t) {
   d.c1f = t.d_cf; d.c2f = t.d_cf + t.N; d.c12f = t.d_cf + 2 * t.N;
   d.wl = t.d_c + 3 * t.N; d.wsum = t.wsum;
   d.ph[0] = t.ph[0]; d.ph[1] = t.ph[1];
+  d.Lc = t.Lc;
+  d.lf = reinterpret_cast<const int4*>(t.d_tab);
+  d.pre = t.d_tab ? t.d_tab + 4 * t.Lc : nullptr;
+  d.post = t.d_tab ? t.d_tab + 4 * t.Lc + t.N : nullptr;
   return d;
 }
 
@@ -407,7 +416,9 @@ struct NewtonParams {
 // most 8 times.  Jumps and g, H are then kept in two buffers per lane: a pass
 // reads the accepted ones and writes the trial's, so a rejected trial leaves
 // the accepted iterate intact.
-template <typename T, int MINB, bool LS>
+// CMP: trees walked by their compressed-traversal tables (tree_pass_c), jumps
+// numbered as in the state; otherwise heap arithmetic (tree_pass).
+template <typename T, int MINB, bool LS, bool CMP>
 __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -464,7 +475,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
               const int node = f / 3, c = f - 3 * node;
               // heap node -> paper index of its jumps
               const int lvl = 32 - __clz(node + 1);
-              const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+              const int j = CMP ? node : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
               abuf[0][(size_t)f * ns] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
               const double nv = P.nbuf[(size_t)f * P.n + pt];
               my_nrm[(size_t)f * ns] = nv;
@@ -491,7 +502,8 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
     GH<T> gh{gbuf[cur], ns, gbuf[LS ? 1 - cur : cur]};
     Sub<T> root;
     double r2;
-    tree_pass<T, true>(t, Eloc, A, gh, !first, step, root, r2, nullptr);
+    if (CMP) tree_pass_c<T, true>(t, Eloc, A, gh, !first, step, root, r2, nullptr);
+    else tree_pass<T, true>(t, Eloc, A, gh, !first, step, root, r2, nullptr);
     const double rn = sqrt(r2);
     double sn2 = 0.0;
 #pragma unroll
@@ -533,7 +545,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
     for (int f = 0; f < 3 * t.N; ++f) {
       const int node = f / 3, c = f - 3 * node;
       const int lvl = 32 - __clz(node + 1);
-      const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+      const int j = CMP ? node : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
       P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt] = st == DMN_STATUS_NONFINITE ? qnan : afin[(size_t)f * ns];
     }
     P.iters[pt] = it;
@@ -560,7 +572,7 @@ struct FinalParams {
   const double* nbuf;
 };
 
-template <bool SWEEP>
+template <bool SWEEP, bool CMP>
 __global__ void __launch_bounds__(128) k_final(FinalParams P) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= P.n) return;
@@ -588,7 +600,8 @@ __global__ void __launch_bounds__(128) k_final(FinalParams P) {
     Sub<double> root;
     double r2;
     GH<double> gh{nullptr, 0, nullptr};
-    tree_pass<double, false>(t, Eloc, A, gh, false, 1.0, root, r2, nullptr);
+    if (CMP) tree_pass_c<double, false>(t, Eloc, A, gh, false, 1.0, root, r2, nullptr);
+    else tree_pass<double, false>(t, Eloc, A, gh, false, 1.0, root, r2, nullptr);
     write_stress_tangent<double>(P.Q + 9 * pt, root.sb, root.C, P.stress + 6 * pt, P.tangent + 36 * pt);
   } else {
     double sb[6], C[21];
@@ -598,7 +611,8 @@ __global__ void __launch_bounds__(128) k_final(FinalParams P) {
     for (int k = 0; k < 21; ++k) C[k] = P.tangent[36 * pt + k];
     write_stress_tangent<double>(P.Q + 9 * pt, sb, C, P.stress + 6 * pt, P.tangent + 36 * pt);
   }
-  write_leaf_states(t, Eloc, A, P.state_out + pt, (size_t)P.n, st == DMN_STATUS_NONFINITE);
+  if (CMP) write_leaf_states_c(t, Eloc, A, P.state_out + pt, (size_t)P.n, st == DMN_STATUS_NONFINITE);
+  else write_leaf_states(t, Eloc, A, P.state_out + pt, (size_t)P.n, st == DMN_STATUS_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------
@@ -748,16 +762,108 @@ void heap_params(const dmn_tree_desc& d, double* ph, double* qh) {
     }
 }
 
-const char* check_tree(const dmn_tree_desc& d) {
+const char* check_tree(const dmn_tree_desc& d, bool allow_zero = false) {
   if (d.K < 1 || d.K > KMAX) return "K must be in 1..8";
   if (d.M != 3 && d.M != 4 && d.M != 6) return "M must be 3, 4 or 6";
   if (!d.p || !d.q || !d.w) return "p, q, w must be non-NULL";
   const int N = (1 << d.K) - 1, L = 1 << d.K;
-  for (int l = 0; l < L; ++l)
-    if (!(d.w[l] > 0.0) || !std::isfinite(d.w[l])) return "leaf weights must be finite and > 0";
+  double wsum = 0.0;
+  for (int l = 0; l < L; ++l) {
+    if (!std::isfinite(d.w[l]) || !(allow_zero ? d.w[l] >= 0.0 : d.w[l] > 0.0))
+      return allow_zero ? "leaf weights must be finite and >= 0" : "leaf weights must be finite and > 0";
+    wsum += d.w[l];
+  }
+  if (!(wsum > 0.0)) return "leaf weights must not all be zero";
   for (int j = 0; j < N * d.M; ++j)
     if (!std::isfinite(d.p[j]) || !std::isfinite(d.q[j])) return "p, q must be finite";
   return nullptr;
+}
+
+// Tree compression (Sec. 3.1): leaves of weight zero are removed, a laminate
+// with one weightless subtree is replaced by the other subtree, one with two is
+// removed.  The remaining laminates are numbered in the paper's order (level K
+// first, root last) -- the numbering of their jumps in the state -- and the
+// compressed tree is described by traversal tables (see TreeDev).  With all
+// weights positive the result is the full tree in table form.
+struct CmpTree {
+  int N = 0, Lc = 0, nz = 0;
+  std::vector<double> p, q, c;   // p, q [N][M]; c = c1 [N], c2 [N], sc [N], leaf weights [L]
+  std::vector<float> cf;         // c1f [N], c2f [N], c12f [N]
+  std::vector<int> tab;          // lf [Lc] (4 ints each), pre [N], post [N]
+};
+
+void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& B) {
+  const int K = d.K, M = d.M, N = (1 << K) - 1, L = 1 << K;
+  double ws = 0.0;
+  for (int l = 0; l < L; ++l) ws += d.w[l];
+  // heap numbering 1..N for laminates, N+1..N+L for leaves; children of h: 2h, 2h+1
+  std::vector<double> W(2 * N + 2, 0.0);
+  for (int l = 0; l < L; ++l) W[N + 1 + l] = d.w[l] / ws;
+  for (int h = N; h >= 1; --h) W[h] = W[2 * h] + W[2 * h + 1];
+  std::vector<int> cid(N + 1, -1);
+  std::vector<int> paper_of;    // paper index of each kept laminate
+  for (int k = K; k >= 1; --k)
+    for (int i = 1; i <= (1 << (k - 1)); ++i) {
+      const int h = (1 << (k - 1)) + i - 1;
+      if (W[2 * h] > 0.0 && W[2 * h + 1] > 0.0) {
+        cid[h] = (int)paper_of.size();
+        paper_of.push_back((1 << K) - (1 << k) + (i - 1));
+      }
+    }
+  const int Nc = (int)paper_of.size();
+  B.N = Nc;
+  B.p.resize((size_t)Nc * M); B.q.resize((size_t)Nc * M);
+  B.c.assign(3 * (size_t)Nc + L, 0.0); B.cf.assign(3 * (size_t)Nc, 0.0f);
+  for (int c = 0; c < Nc; ++c)
+    for (int m = 0; m < M; ++m) { B.p[c * M + m] = d.p[paper_of[c] * M + m]; B.q[c * M + m] = d.q[paper_of[c] * M + m]; }
+  for (int h = 1; h <= N; ++h) {
+    const int c = cid[h];
+    if (c < 0) continue;
+    const double c1 = W[2 * h] / W[h], c2 = 1.0 - c1;
+    B.c[c] = c1; B.c[Nc + c] = c2; B.c[2 * Nc + c] = W[h] * c1 * c2;
+    B.cf[c] = (float)c1; B.cf[Nc + c] = (float)c2; B.cf[2 * Nc + c] = (float)(c1 * c2);
+  }
+  for (int l = 0; l < L; ++l) B.c[3 * Nc + l] = W[N + 1 + l];
+  std::vector<int> lf, pre, post;
+  B.nz = 0;
+  // depth-first walk of the compressed tree: `top` is the depth where the
+  // current descent started, `depth` the depth in the compressed tree
+  struct Walk {
+    const std::vector<double>& W; const std::vector<int>& cid; const bool* inel; int N;
+    std::vector<int>& lf; std::vector<int>& pre; std::vector<int>& post; int& nz;
+    void go(int h, int depth, int top) {
+      if (!(W[h] > 0.0)) return;
+      if (h > N) {                                     // a leaf
+        const int l = h - N - 1, ph = l & 1;
+        const int slot = inel[ph] ? nz++ : -1;
+        lf.insert(lf.end(), {top, depth - top, 0, ((slot + 1) << 2) | (ph << 1)});
+        return;
+      }
+      if (cid[h] < 0) {                                // one weightless side: pass the other through
+        go(W[2 * h] > 0.0 ? 2 * h : 2 * h + 1, depth, top);
+        return;
+      }
+      pre.push_back(cid[h]);
+      go(2 * h, depth + 1, top);
+      go(2 * h + 1, depth + 1, depth + 1);
+      post.push_back(cid[h]);
+      lf[lf.size() - 2] += 1;                          // completed right after the last leaf
+    }
+  } walk{W, cid, inelastic, N, lf, pre, post, B.nz};
+  walk.go(1, 0, 0);
+  const int Lc = (int)lf.size() / 4;
+  for (int l = 0; l + 1 < Lc; ++l)   // two sibling leaves: the left completes nothing, the right descends nothing
+    if (lf[4 * l + 2] == 0 && lf[4 * (l + 1) + 1] == 0) lf[4 * l + 3] |= 1;
+  B.Lc = Lc;
+  B.tab = lf;
+  B.tab.insert(B.tab.end(), pre.begin(), pre.end());
+  B.tab.insert(B.tab.end(), post.begin(), post.end());
+}
+
+bool has_zero_weight(const dmn_tree_desc& d) {
+  for (int l = 0; l < (1 << d.K); ++l)
+    if (d.w[l] == 0.0) return true;
+  return false;
 }
 
 }  // namespace
@@ -794,6 +900,15 @@ void free_pipe(HostPipe& p) {
   if (p.down) cudaStreamDestroy(p.down);
   if (p.start) cudaEventDestroy(p.start);
   p = HostPipe();
+}
+
+// Newton kernel variant for the launch shape: register cap by resident CTAs, line search.
+template <typename T, bool CMP>
+void launch_newton(const NewtonParams<T>& P, bool ls, int minb, unsigned grid, int block, cudaStream_t s) {
+  if (ls) k_newton<T, 2, true, CMP><<<grid, block, 0, s>>>(P);
+  else if (minb == 2) k_newton<T, 2, false, CMP><<<grid, block, 0, s>>>(P);
+  else if (minb == 3) k_newton<T, 3, false, CMP><<<grid, block, 0, s>>>(P);
+  else k_newton<T, 4, false, CMP><<<grid, block, 0, s>>>(P);
 }
 
 // One update on work set w and stream s (the body of dmn_update; arguments checked by the caller).
@@ -848,25 +963,27 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, cons
   const int threads_per_sm = h->opt.block * h->opt.ctas_per_sm;
   const int minb = threads_per_sm > 384 ? 4 : threads_per_sm > 256 ? 3 : 2;
   const bool ls = h->opt.line_search != 0;
+  const int block = h->opt.block;
   if (!mixed) {
     NewtonParams<double> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                            w.nbuf, w.scr_d, (double*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 1};
-    if (ls) k_newton<double, 2, true><<<grid, h->opt.block, 0, s>>>(P);
-    else if (minb == 2) k_newton<double, 2, false><<<grid, h->opt.block, 0, s>>>(P);
-    else if (minb == 3) k_newton<double, 3, false><<<grid, h->opt.block, 0, s>>>(P);
-    else k_newton<double, 4, false><<<grid, h->opt.block, 0, s>>>(P);
+    if (h->cmp) launch_newton<double, true>(P, ls, minb, grid, block, s);
+    else launch_newton<double, false>(P, ls, minb, grid, block, s);
   } else {
     NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                           w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 0};
-    if (ls) k_newton<float, 2, true><<<grid, h->opt.block, 0, s>>>(P);
-    else if (minb == 2) k_newton<float, 2, false><<<grid, h->opt.block, 0, s>>>(P);
-    else if (minb == 3) k_newton<float, 3, false><<<grid, h->opt.block, 0, s>>>(P);
-    else k_newton<float, 4, false><<<grid, h->opt.block, 0, s>>>(P);
+    if (h->cmp) launch_newton<float, true>(P, ls, minb, grid, block, s);
+    else launch_newton<float, false>(P, ls, minb, grid, block, s);
   }
   if (ev) cudaEventRecord(ev[2], s);
   FinalParams FP{F, n, NM, tree_id, perm, Q, state_in, state_out, stress, tangent, status, w.nbuf};
-  if (mixed) k_final<true><<<g1, 128, 0, s>>>(FP);
-  else k_final<false><<<g1, 128, 0, s>>>(FP);
+  if (mixed) {
+    if (h->cmp) k_final<true, true><<<g1, 128, 0, s>>>(FP);
+    else k_final<true, false><<<g1, 128, 0, s>>>(FP);
+  } else {
+    if (h->cmp) k_final<false, true><<<g1, 128, 0, s>>>(FP);
+    else k_final<false, false><<<g1, 128, 0, s>>>(FP);
+  }
   if (ev) cudaEventRecord(ev[3], s);
   e = cudaGetLastError();
   return e == cudaSuccess ? DMN_OK : cuda_fail(h, e, "dmn_update: launch");
@@ -947,11 +1064,16 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   if (!trees || n_trees < 1 || n_trees > DMN_MAX_TREES)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: n_trees must be in 1..8 and trees non-NULL");
   std::vector<Tree> tv(n_trees);
+  std::vector<CmpTree> cv(n_trees);
   int N_max = 0;
   int64_t S_max = 0;
+  bool cmp = false;
+  for (int k = 0; k < n_trees; ++k) {
+    if (const char* m = check_tree(trees[k], true)) return fail(nullptr, DMN_ERR_ARG, std::string("dmn_create: ") + m);
+    cmp = cmp || has_zero_weight(trees[k]);
+  }
   for (int k = 0; k < n_trees; ++k) {
     const dmn_tree_desc& d = trees[k];
-    if (const char* m = check_tree(d)) return fail(nullptr, DMN_ERR_ARG, std::string("dmn_create: ") + m);
     Tree& t = tv[k];
     t.K = d.K; t.M = d.M; t.N = (1 << d.K) - 1; t.L = 1 << d.K;
     int n_inel_phase = 0;
@@ -962,6 +1084,14 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     }
     t.z_both = n_inel_phase == 2;
     t.nz = n_inel_phase * (t.L / 2);
+    if (cmp) {   // every tree of the handle is walked by tables
+      const bool inel[2] = {d.phase[0].kind != DMN_PHASE_ELASTIC, d.phase[1].kind != DMN_PHASE_ELASTIC};
+      build_compressed(d, inel, cv[k]);
+      t.cmp = 1;
+      t.N = cv[k].N;
+      t.Lc = cv[k].Lc;
+      t.nz = cv[k].nz;
+    }
     t.S = 6 * t.nz + 3 * t.N;
     N_max = std::max(N_max, t.N);
     S_max = std::max<int64_t>(S_max, t.S);
@@ -993,7 +1123,8 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
 
   dmn_handle* h = new dmn_handle();
   h->trees = tv;
-  h->N_max = N_max;
+  h->cmp = cmp;
+  h->N_max = std::max(N_max, 1);
   h->S_max = S_max;
   h->opt = o;
   cudaError_t e = cudaGetDevice(&h->device);
@@ -1006,10 +1137,28 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     const dmn_tree_desc& d = trees[k];
     Tree& T = h->trees[k];
     const int N = T.N, M = T.M, L = T.L;
-    std::vector<double> ph(N * M), qh(N * M);
-    heap_params(d, ph.data(), qh.data());
     T.wsum = 0.0;
     for (int l = 0; l < L; ++l) T.wsum += d.w[l];
+    if (T.cmp) {   // host-built parameters in the compressed numbering, and the tables
+      const CmpTree& B = cv[k];
+      const size_t np = std::max<size_t>(B.p.size(), 1), nc = B.c.size(), nf = std::max<size_t>(B.cf.size(), 1);
+      e = cudaMalloc(&T.d_p, sizeof(double) * np);
+      if (e == cudaSuccess) e = cudaMalloc(&T.d_q, sizeof(double) * np);
+      if (e == cudaSuccess) e = cudaMalloc(&T.d_c, sizeof(double) * nc);
+      if (e == cudaSuccess) e = cudaMalloc(&T.d_cf, sizeof(float) * nf);
+      if (e == cudaSuccess) e = cudaMalloc(&T.d_tab, sizeof(int) * B.tab.size());
+      if (e == cudaSuccess && !B.p.empty())
+        e = cudaMemcpy(T.d_p, B.p.data(), sizeof(double) * B.p.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && !B.q.empty())
+        e = cudaMemcpy(T.d_q, B.q.data(), sizeof(double) * B.q.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(T.d_c, B.c.data(), sizeof(double) * nc, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && !B.cf.empty())
+        e = cudaMemcpy(T.d_cf, B.cf.data(), sizeof(float) * B.cf.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(T.d_tab, B.tab.data(), sizeof(int) * B.tab.size(), cudaMemcpyHostToDevice);
+      continue;
+    }
+    std::vector<double> ph(N * M), qh(N * M);
+    heap_params(d, ph.data(), qh.data());
     e = cudaMalloc(&T.d_p, sizeof(double) * N * M);
     if (e == cudaSuccess) e = cudaMalloc(&T.d_q, sizeof(double) * N * M);
     if (e == cudaSuccess) e = cudaMalloc(&T.d_c, sizeof(double) * (3 * N + L));
@@ -1039,7 +1188,7 @@ void dmn_destroy(dmn_handle* h) {
   cudaDeviceSynchronize();
   for (auto& a : h->events)
     for (auto& x : a) cudaEventDestroy(x);
-  for (auto& t : h->trees) { cudaFree(t.d_p); cudaFree(t.d_q); cudaFree(t.d_c); cudaFree(t.d_cf); }
+  for (auto& t : h->trees) { cudaFree(t.d_p); cudaFree(t.d_q); cudaFree(t.d_c); cudaFree(t.d_cf); cudaFree(t.d_tab); }
   for (auto& w : h->ws) free_ws(w);
   free_pipe(h->hp);
   cudaFree(h->gwork);
@@ -1185,6 +1334,8 @@ int dmn_set_params(dmn_handle* h, int32_t tree_id, const double* p, const double
   if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_set_params: NULL handle");
   if (tree_id < 0 || tree_id >= (int)h->trees.size()) return fail(h, DMN_ERR_ARG, "dmn_set_params: bad tree_id");
   Tree& T = h->trees[tree_id];
+  if (h->cmp)
+    return fail(h, DMN_ERR_ARG, "dmn_set_params: the handle holds compressed trees (weights of zero); create a new handle");
   dmn_tree_desc d;
   d.K = T.K; d.M = T.M; d.p = p; d.q = q; d.w = w;
   if (const char* m = check_tree(d)) return fail(h, DMN_ERR_ARG, std::string("dmn_set_params: ") + m);
@@ -1214,6 +1365,7 @@ int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam
   if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_grad: NULL handle");
   if (n < 0) return fail(h, DMN_ERR_ARG, "dmn_grad: n < 0");
   if (tree_id || h->trees.size() != 1) return fail(h, DMN_ERR_ARG, "dmn_grad: one tree only (tree_id must be NULL)");
+  if (h->cmp) return fail(h, DMN_ERR_ARG, "dmn_grad: compressed trees (weights of zero) are not supported");
   if (n == 0) return DMN_OK;
   if (!lam || !Q || !E_n || !dE || !state_in || !state_out || !g_stress || !g_p || !g_q || !g_w)
     return fail(h, DMN_ERR_ARG, "dmn_grad: NULL array");

@@ -57,6 +57,17 @@ struct TreeDev {
   const double* wl;  // [L] normalised leaf weights
   double wsum;       // sum of the leaf weights as given
   PhaseDev ph[2];
+  // Compressed traversal (tree compression, Sec. 3.1: leaves of weight zero
+  // removed, a laminate with one weightless subtree replaced by the other
+  // subtree).  The laminates are then numbered in the paper's order among the
+  // remaining ones (p, q, c1, ... follow that numbering, N counts them) and the
+  // tree is walked by tables instead of heap arithmetic.
+  int Lc;            // leaves with weight > 0, in leaf order
+  const int4* lf;    // per such leaf: x = depth where its descent starts, y = laminates descended to reach it,
+                     // z = laminates completed right after it, w = (state slot + 1) << 2 | phase << 1 | pair,
+                     // pair = 1 when this leaf and the next are the two children of one laminate
+  const int* pre;    // [N] laminates in descent (pre-) order
+  const int* post;   // [N] laminates in completion (post-) order
 };
 
 template <typename T>
@@ -575,6 +586,188 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
       condense<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node), node_c<T>(t, node),
                          pend[lvl + 1], B, res, gp, gh.s, r2);
     }
+  }
+}
+
+// Tangent and stress of one leaf as a subtree result (no inner jumps).
+template <typename T>
+__device__ __forceinline__ void leaf_sub(const LeafTan<T>& D, const double sig[6], Sub<T>& s) {
+#pragma unroll
+  for (int I = 0; I < 6; ++I) { s.sb[I] = sig[I]; s.ds[I] = (T)0; }
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = I; J < 6; ++J) {
+      T v = -D.c * D.m[I] * D.m[J];
+      if (I < 3 && J < 3) v += D.lam;
+      if (I == J) v += (T)2 * D.mu;
+      s.C[sidx(I, J)] = v;
+    }
+}
+
+__device__ __forceinline__ void load_z_slot(const PointArrays& P, int slot, double z[6]) {
+  if (slot >= 0) {
+    const double* b = P.z + (size_t)(6 * slot) * P.zs;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) z[c] = b[c * P.zs];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) z[c] = 0.0;
+  }
+}
+
+// The pass of tree_pass over a compressed tree, driven by the tables of
+// TreeDev (laminates by their compressed number; jumps at that number in both
+// the scratch and the state).  Same arithmetic per laminate and leaf; a leaf
+// whose sibling is a laminate enters the condensation as a subtree with the
+// leaf's tangent, two sibling leaves use the structured bottom condensation.
+template <typename T, bool STORE>
+__device__ void tree_pass_c(const TreeDev& t, const double Eloc[6], const PointArrays& P, GH<T> gh, bool apply,
+                            T step, Sub<T>& root, double& r2, double* gap_min) {
+  double epsR[KMAX + 1][6];
+  T depsR[KMAX + 1][6];
+  Sub<T> pend[KMAX + 1];
+  r2 = 0.0;
+  int ipre = 0, ipost = 0;
+  for (int l = 0; l < t.Lc;) {
+    const int4 f = __ldg(t.lf + l);
+    const bool pair = f.w & 1;
+    int d = f.x;
+    double e[6];
+    T de[6];
+    if (l == 0) {
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { e[I] = Eloc[I]; de[I] = (T)0; }
+    } else {
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { e[I] = epsR[d][I]; de[I] = depsR[d][I]; }
+    }
+    for (int s = 0; s < f.y; ++s, ++d) {
+      const int node = __ldg(t.pre + ipre++);
+      double nd[3];
+      T nt[3];
+      load_n<T>(P, node, nd, nt);
+      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      const double* ap = P.a + (size_t)(3 * node) * P.as;
+      double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
+      T da[3] = {(T)0, (T)0, (T)0};
+      if (STORE) {
+        const T* gp = gh.p + (size_t)(21 * node) * gh.s;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T v = step * gp[c * gh.s];
+#pragma unroll
+          for (int I = 0; I < 6; ++I) v += gp[(3 + 6 * c + I) * gh.s] * de[I];
+          da[c] = apply ? v : (T)0;
+        }
+        double* aw = P.a_out + (size_t)(3 * node) * P.as;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { a[c] += (double)da[c]; aw[c * P.as] = a[c]; }
+      }
+      const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+      double Na[6];
+      N_apply<double>(nd, ndr, a, Na);
+      T dR[6];
+      if (STORE && !(pair && s == f.y - 1)) {   // children that are laminates need strain corrections
+        const NodeC<T> cc = node_c<T>(t, node);
+        const T ntr[3] = {nt[0] * (T)RS2, nt[1] * (T)RS2, nt[2] * (T)RS2};
+        T Nda[6];
+        N_apply<T>(nt, ntr, da, Nda);
+#pragma unroll
+        for (int I = 0; I < 6; ++I) { dR[I] = de[I] + cc.c1 * Nda[I]; de[I] = de[I] - cc.c2 * Nda[I]; }
+      } else {
+#pragma unroll
+        for (int I = 0; I < 6; ++I) dR[I] = (T)0;
+      }
+#pragma unroll
+      for (int I = 0; I < 6; ++I) {
+        epsR[d + 1][I] = e[I] + c1 * Na[I];
+        depsR[d + 1][I] = dR[I];
+        e[I] = e[I] - c2 * Na[I];
+      }
+    }
+    Sub<T> res;
+    int nup;
+    const int ph0 = (f.w >> 1) & 1;
+    double z[6], g;
+    if (pair) {
+      const int4 f2 = __ldg(t.lf + l + 1);
+      const int ph1 = (f2.w >> 1) & 1;
+      double sL[6], sR[6];
+      LeafTan<T> DL, DR;
+      load_z_slot(P, (f.w >> 2) - 1, z);
+      leaf_iso<T>(t.ph[ph0], e, z, sL, &DL, nullptr, gap_min ? &g : nullptr);
+      if (gap_min) *gap_min = fmin(*gap_min, g);
+      load_z_slot(P, (f2.w >> 2) - 1, z);
+      leaf_iso<T>(t.ph[ph1], epsR[d], z, sR, &DR, nullptr, gap_min ? &g : nullptr);
+      if (gap_min) *gap_min = fmin(*gap_min, g);
+      const int node = __ldg(t.post + ipost++);
+      double nd[3];
+      T nt[3];
+      load_n<T>(P, node, nd, nt);
+      T* gp = STORE ? gh.q + (size_t)(21 * node) * gh.s : nullptr;
+      condense_bottom<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node),
+                                node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2);
+      --d;
+      nup = f2.z - 1;
+      l += 2;
+    } else {
+      double sg[6];
+      LeafTan<T> D;
+      load_z_slot(P, (f.w >> 2) - 1, z);
+      leaf_iso<T>(t.ph[ph0], e, z, sg, &D, nullptr, gap_min ? &g : nullptr);
+      if (gap_min) *gap_min = fmin(*gap_min, g);
+      leaf_sub<T>(D, sg, res);
+      nup = f.z;
+      l += 1;
+    }
+    for (int u = 0; u < nup; ++u) {
+      const int node = __ldg(t.post + ipost++);
+      double nd[3];
+      T nt[3];
+      load_n<T>(P, node, nd, nt);
+      T* gp = STORE ? gh.q + (size_t)(21 * node) * gh.s : nullptr;
+      const Sub<T> B = res;
+      condense<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node), node_c<T>(t, node),
+                         pend[d], B, res, gp, gh.s, r2);
+      --d;
+    }
+    if (d == 0) root = res;
+    else pend[d] = res;
+  }
+}
+
+// write_leaf_states for a compressed tree (tables of TreeDev).
+__device__ inline void write_leaf_states_c(const TreeDev& t, const double Eloc[6], const PointArrays& P, double* zout,
+                                           size_t zos, bool nan_out) {
+  double epsR[KMAX + 1][6];
+  int ipre = 0;
+  for (int l = 0; l < t.Lc; ++l) {
+    const int4 f = __ldg(t.lf + l);
+    int d = f.x;
+    double e[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) e[I] = (l == 0) ? Eloc[I] : epsR[d][I];
+    for (int s = 0; s < f.y; ++s, ++d) {
+      const int node = __ldg(t.pre + ipre++);
+      const double nd[3] = {P.nrm[(3 * node) * P.ns], P.nrm[(3 * node + 1) * P.ns], P.nrm[(3 * node + 2) * P.ns]};
+      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      const double* ap = P.a + (size_t)(3 * node) * P.as;
+      const double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
+      const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+      double Na[6];
+      N_apply<double>(nd, ndr, a, Na);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { epsR[d + 1][I] = e[I] + c1 * Na[I]; e[I] -= c2 * Na[I]; }
+    }
+    const int slot = (f.w >> 2) - 1;
+    if (slot < 0) continue;
+    double z[6], zn[6], sig[6];
+    load_z_slot(P, slot, z);
+    leaf_iso<double>(t.ph[(f.w >> 1) & 1], e, z, sig, nullptr, zn, nullptr);
+    double* b = zout + (size_t)(6 * slot) * zos;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) b[c * zos] = nan_out ? __longlong_as_double(0x7ff8000000000000LL) : zn[c];
   }
 }
 

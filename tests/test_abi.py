@@ -63,7 +63,8 @@ def _desc(K=3, M=3, w=None, kind=1):
 
 @pytest.mark.parametrize("case,msg", [
     (dict(K=9), "K must be"), (dict(K=0), "K must be"), (dict(M=5), "M must be"),
-    (dict(w=np.r_[np.ones(7), 0.0]), "weights"), (dict(w=np.r_[np.ones(7), np.nan]), "weights"),
+    (dict(w=np.r_[np.ones(7), -1.0]), "weights"), (dict(w=np.r_[np.ones(7), np.nan]), "weights"),
+    (dict(w=np.zeros(8)), "all be zero"),
     (dict(kind=7), "phase kind"), (dict(kind=2), "exponential-linear")])
 def test_create_rejects_bad_arguments_without_touching_the_gpu(case, msg):
     lib = dmn.load_library()

@@ -1,0 +1,145 @@
+"""Compressed trees (leaf weights of zero, Sec. 3.1) on the GPU.
+
+Parity with the oracle's compression; agreement to rounding between the
+table-driven traversal and the heap traversal on equivalent trees (a full
+tree walked both ways; a tree whose right half is weightless against the
+depth-(K-1) tree of its left half).  The two traversals are separately
+compiled code, so the compiler's choice of fused multiply-adds may differ
+between them: the comparison allows 1e-12 relative instead of bit equality."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2103_08253_gb300 import dmn, workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+TOL = {"f64": 1e-10, "mixed": 1e-6}
+
+
+def d(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def rel(a, b):
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
+
+
+def close(x, y):
+    """Equal to rounding: same iterations and status, values within 1e-12 of the array's scale."""
+    if x.dtype.kind == "i":
+        np.testing.assert_array_equal(x, y)
+    else:
+        assert np.abs(x - y).max() <= 1e-12 * (np.abs(y).max() + 1e-300)
+
+
+def gpu_path(m, lam, Q, Ef, steps, n_steps, tree_id=None, S=None):
+    n = lam.shape[0]
+    st = torch.zeros((S or m.state_size, n), dtype=torch.float64, device=DEV)
+    outs = []
+    for s in range(1, steps + 1):
+        En, dE = W.proportional_increment(Ef, s, n_steps)
+        o = m.update(d(lam), d(Q), d(En), d(dE), st, tree_id=tree_id)
+        st = o["state_out"]
+        outs.append({k: v.cpu().numpy() for k, v in o.items()})
+    return outs
+
+
+@pytest.mark.parametrize("K,prec", [(5, "f64"), (8, "f64"), (8, "mixed")])
+def test_compressed_tree_matches_the_oracle(K, prec):
+    tree = W.tree_with_zero_weights(K, seed=20 + K)
+    n, steps, n_steps = 40, 8, 20
+    A2, lam, Q = W.orientation_field(n, seed=21)
+    Ef = W.random6_path_final(n, 0.03, seed=22)
+    m = dmn.DMN(tree, precision=prec)
+    S = oracle.state_size(K, tree.phases, tree.w)
+    assert m.state_size == S < W.state_size(K)
+    outs = gpu_path(m, lam, Q, Ef, steps, n_steps)
+    st = np.zeros((S, n))
+    for s in range(1, steps + 1):
+        En, dE = W.proportional_increment(Ef, s, n_steps)
+        st, sig, C, it, stat, gap = oracle.update(tree, lam, Q, En, dE, st)
+        o = outs[s - 1]
+        np.testing.assert_array_equal(o["status"], stat)
+        ok = stat == 0
+        assert rel(o["stress"][ok], sig[ok]).max() <= TOL[prec]
+        tie = gap < 1e-9
+        assert rel(o["tangent"][ok & ~tie], C[ok & ~tie]).max() <= TOL[prec]
+        if prec == "f64":
+            assert np.abs(o["iters"] - it).max() <= 1
+            # leaf variables and jumps, each against the largest entry of its block (a leaf that
+            # barely yields at one point may flip with the rounding order there)
+            nz6 = 6 * int(sum(1 for l in range(1 << K) if tree.w[l] > 0 and tree.phases[l % 2].kind != 0))
+            for blk in (slice(0, nz6), slice(nz6, S)):
+                ref = st[blk]
+                assert np.abs(o["state_out"][blk] - ref).max() <= 1e-9 * (np.abs(ref).max() + 1e-300)
+    m.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_table_traversal_equals_the_heap_traversal(prec):
+    """A handle that holds a compressed tree walks every tree by tables; the full tree
+    in it must give exactly what a handle of the full tree alone (heap arithmetic) gives."""
+    K, n = 6, 200
+    full = W.tree_d10_fit(K, seed=30)
+    other = W.tree_with_zero_weights(4, seed=31)
+    A2, lam, Q = W.orientation_field(n, seed=32)
+    Ef = W.random6_path_final(n, 0.03, seed=33)
+    heap = dmn.DMN(full, precision=prec)
+    table = dmn.DMN([full, other], precision=prec)
+    assert table.tree_state_sizes[0] == heap.state_size
+    a = gpu_path(heap, lam, Q, Ef, 4, 10)
+    b = gpu_path(table, lam, Q, Ef, 4, 10, tree_id=d(np.zeros(n, dtype=np.int32)))
+    for x, y in zip(a, b):
+        for k in ("stress", "tangent", "iters", "status"):
+            close(x[k], y[k])
+        close(x["state_out"], y["state_out"][: heap.state_size])
+    heap.close()
+    table.close()
+
+
+def test_weightless_half_equals_the_smaller_tree():
+    K = 5
+    big = W.tree_d10_fit(K, seed=40)
+    w = big.w.copy()
+    w[16:] = 0.0
+    big = W.TreeParams(K, big.M, big.p, big.q, w, big.phases)
+    rows = [(1 << K) - (1 << k) + i - 1 for k in range(K, 1, -1) for i in range(1, (1 << (k - 2)) + 1)]
+    small = W.TreeParams(K - 1, big.M, big.p[rows], big.q[rows], w[:16], big.phases)
+    n = 100
+    A2, lam, Q = W.orientation_field(n, seed=41)
+    Ef = W.random6_path_final(n, 0.03, seed=42)
+    mb, ms = dmn.DMN(big), dmn.DMN(small)
+    assert mb.state_size == ms.state_size
+    for x, y in zip(gpu_path(mb, lam, Q, Ef, 4, 10), gpu_path(ms, lam, Q, Ef, 4, 10)):
+        for k in x:
+            close(x[k], y[k])
+
+
+def test_single_leaf_and_unsupported_calls():
+    K = 3
+    t = W.tree_d10_fit(K, seed=50)
+    w = np.zeros(1 << K)
+    w[3] = 1.0
+    t = W.TreeParams(K, t.M, t.p, t.q, w, t.phases)
+    m = dmn.DMN(t)
+    assert m.state_size == 6
+    lam, Q = W.identity_orientation(5)
+    Ef = W.random6_path_final(5, 0.03, seed=51)
+    o = gpu_path(m, lam, Q, Ef, 3, 3)[-1]
+    st = np.zeros((6, 5))
+    for s in range(1, 4):
+        En, dE = W.proportional_increment(Ef, s, 3)
+        st, sig, C, it, stat, gap = oracle.update(t, lam, Q, En, dE, st)
+    assert (o["status"] == 0).all() and (o["iters"] == 0).all()
+    assert rel(o["stress"], sig).max() <= 1e-12 and rel(o["tangent"], C).max() <= 1e-12
+    with pytest.raises(RuntimeError):
+        m.set_params(t.p, t.q, t.w)
+    n = 5
+    z = d(np.zeros((n, 6)))
+    with pytest.raises(RuntimeError):
+        m.grad(d(lam), d(Q), z, z, d(np.zeros((6, n))), d(np.zeros((6, n))), z)
+    m.close()

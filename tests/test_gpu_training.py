@@ -1,0 +1,51 @@
+"""Offline training through the GPU adjoint (Sec. 3.1 loss, AMSGrad with the
+schedule of Sec. 4.4) against a seeded target DMN."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2103_08253_gb300 import dmn, training as T, workloads as W
+
+pytestmark = pytest.mark.gpu
+EL_MATRIX = W.Phase(0, 3000.0, 0.35)
+
+
+def test_schedule_follows_the_formula():
+    assert abs(T.lr_schedule(0) - 1.5e-2) < 1e-15
+    assert abs(T.lr_schedule(50) - 0.999 ** 50 * 1.5e-3) < 1e-15
+    assert abs(T.lr_schedule(100) - 0.999 ** 100 * 1.5e-2) < 1e-15
+
+
+def test_stiffness_loss_matches_its_definition():
+    rng = np.random.default_rng(1)
+    C = torch.from_numpy(rng.standard_normal((5, 6, 6)))
+    Ct = torch.from_numpy(rng.standard_normal((5, 6, 6)))
+    w = np.array([1, 1, 1, np.sqrt(2), np.sqrt(2), np.sqrt(2)])
+    s = 1.0 / np.outer(w, w)
+    e = np.abs((C.numpy() - Ct.numpy()) * s).reshape(5, -1).sum(1) / np.abs(Ct.numpy() * s).reshape(5, -1).sum(1)
+    ref = (e ** 10).sum() ** 0.1 / 5
+    assert abs(float(T.stiffness_loss(C, Ct)) - ref) < 1e-14 * ref
+
+
+@pytest.mark.parametrize("n_plastic", [0, 64])
+def test_training_lowers_the_loss(n_plastic):
+    K = 4
+    target = W.tree_d10_fit(K, seed=2)
+    tr = T.Trainer(K, target, 128, seed=3, elastic_matrix=EL_MATRIX, plastic=W.MATRIX, n_plastic=n_plastic)
+    first = tr.step()
+    tr.train(80)
+    last = tr.history[-1]
+    assert last[0] < 0.75 * first[0], (first, last)
+    assert last[2] < 0.6 * first[2], (first, last)
+    # the trained (and compressed) tree runs online
+    t = tr.compress()
+    m = dmn.DMN(t)
+    n = 16
+    A2, lam, Q = W.orientation_field(n, seed=4)
+    dev = torch.device("cuda:0")
+    st = torch.zeros((m.state_size, n), dtype=torch.float64, device=dev)
+    E = torch.from_numpy(W.random6_path_final(n, 0.01, seed=5)).to(dev)
+    o = m.update(torch.from_numpy(lam).to(dev), torch.from_numpy(Q).to(dev), torch.zeros_like(E), E, st)
+    assert (o["status"] == 0).all()
+    m.close()
+    tr.close()
