@@ -87,6 +87,17 @@ int fe_tangent_diagonal(fe_mesh* m, const double* C, double* diag, void* stream)
 int fe_pcg(fe_mesh* m, const double* C, const double* free, const double* diag, const double* b, double* x,
            double rtol, int32_t max_iter, int32_t* iters, double* rel_res, void* stream);
 
+/* fe_pcg with the products K p formed in FP32: C is rounded to FP32 on each
+ * call (a field-major copy), the shape-function gradients on the first call;
+ * element sums are FP32, node sums and the CG vectors and scalars FP64.  The
+ * operator's rounding (about 1e-7 relative) bounds the attainable residual, so
+ * rtol should be 1e-6 or larger; an inexact Newton method on the macroscopic
+ * equilibrium needs no more.  GB300's FP32 rate is 64 times its FP64 rate, which
+ * is why this form exists.  Allocates about n_gp x 244 bytes on first use.
+ * Same arguments, results and errors as fe_pcg. */
+int fe_pcg_f32(fe_mesh* m, const double* C, const double* free, const double* diag, const double* b, double* x,
+               double rtol, int32_t max_iter, int32_t* iters, double* rel_res, void* stream);
+
 /* Blocking reductions for the Newton loop (host results):
  * *out = sum over dofs of free[dof] * a[dof] * b[dof] (free may be NULL: all dofs). */
 int fe_dot(fe_mesh* m, const double* a, const double* b, const double* free, double* out, void* stream);

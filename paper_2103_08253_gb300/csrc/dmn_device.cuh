@@ -259,7 +259,7 @@ __device__ __forceinline__ void residual_share(const double nd[3], double c1, do
   Nt_apply<double>(nd, ndr, d, t);
   r2 += sc * sc * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
 #pragma unroll
-  for (int I = 0; I < 6; ++I) sb[I] = c1 * sL[I] + c2 * sR[I];
+  for (int I = 0; I < 6; ++I) sb[I] = sL[I] + c2 * d[I];   // c1 sL + c2 sR with c1 = 1 - c2
 }
 
 // ---------------------------------------------------------------------------
@@ -289,9 +289,11 @@ __device__ __forceinline__ void condense(const double nd[3], const T n[3], doubl
   }
   const T c1 = cc.c1, c2 = cc.c2, c12 = cc.c12;
   const T nr[3] = {n[0] * (T)RS2, n[1] * (T)RS2, n[2] * (T)RS2};
+  // c2 C_L + c1 C_R = C_R - c2 dC and c1 X_L + c2 X_R = X_L + c2 dX with c1 = 1 - c2: one
+  // fused multiply-add per entry
   T Ch[21], dC[21];
 #pragma unroll
-  for (int k = 0; k < 21; ++k) { Ch[k] = c2 * L.C[k] + c1 * R.C[k]; dC[k] = R.C[k] - L.C[k]; }
+  for (int k = 0; k < 21; ++k) { dC[k] = R.C[k] - L.C[k]; Ch[k] = R.C[k] - c2 * dC[k]; }
   T ChN[6][3], B[6][3];
   SN_apply<T>(Ch, n, nr, ChN);
   SN_apply<T>(dC, n, nr, B);
@@ -321,13 +323,13 @@ __device__ __forceinline__ void condense(const double nd[3], const T n[3], doubl
   for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
 #pragma unroll
   for (int I = 0; I < 6; ++I)
-    out.ds[I] = c1 * L.ds[I] + c2 * R.ds[I] + c12 * (B[I][0] * g[0] + B[I][1] * g[1] + B[I][2] * g[2]);
+    out.ds[I] = L.ds[I] + c2 * dds[I] + c12 * (B[I][0] * g[0] + B[I][1] * g[1] + B[I][2] * g[2]);
 #pragma unroll
   for (int I = 0; I < 6; ++I)
 #pragma unroll
     for (int J = I; J < 6; ++J) {
       const int s = sidx(I, J);
-      out.C[s] = c1 * L.C[s] + c2 * R.C[s] + c12 * (B[I][0] * H[0][J] + B[I][1] * H[1][J] + B[I][2] * H[2][J]);
+      out.C[s] = L.C[s] + c2 * dC[s] + c12 * (B[I][0] * H[0][J] + B[I][1] * H[1][J] + B[I][2] * H[2][J]);
     }
   if (STORE) {
 #pragma unroll

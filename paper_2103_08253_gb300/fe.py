@@ -19,8 +19,8 @@ import time
 from . import dmn as _dmn
 
 FE_EXPORTS = ("fe_mesh_create", "fe_mesh_destroy", "fe_num_gauss_points", "fe_num_dofs", "fe_volume",
-              "fe_strain", "fe_internal_force", "fe_apply_tangent", "fe_tangent_diagonal", "fe_pcg", "fe_dot",
-              "fe_axpy", "fe_last_error")
+              "fe_strain", "fe_internal_force", "fe_apply_tangent", "fe_tangent_diagonal", "fe_pcg", "fe_pcg_f32",
+              "fe_dot", "fe_axpy", "fe_last_error")
 
 _ready = False
 
@@ -45,8 +45,9 @@ def load_library():
             getattr(lib, name).restype = ctypes.c_int
         lib.fe_apply_tangent.argtypes = [vp, vp, vp, vp, vp]
         lib.fe_apply_tangent.restype = ctypes.c_int
-        lib.fe_pcg.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
-        lib.fe_pcg.restype = ctypes.c_int
+        for name in ("fe_pcg", "fe_pcg_f32"):
+            getattr(lib, name).argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
+            getattr(lib, name).restype = ctypes.c_int
         lib.fe_dot.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl), vp]
         lib.fe_dot.restype = ctypes.c_int
         lib.fe_axpy.argtypes = [vp, dbl, vp, vp, vp, vp]
@@ -113,12 +114,14 @@ class Hex8Mesh:
         self._check("fe_tangent_diagonal", self._lib.fe_tangent_diagonal(self._h, _p(C), _p(out), _stream()))
         return out
 
-    def pcg(self, C, free, diag, b, x, rtol=1e-8, max_iter=20000):
-        """Jacobi-PCG on the free dofs; returns (iterations, relative residual)."""
+    def pcg(self, C, free, diag, b, x, rtol=1e-8, max_iter=20000, f32=False):
+        """Jacobi-PCG on the free dofs (f32: products K p in FP32, fe_pcg_f32); returns
+        (iterations, relative residual)."""
         it = ctypes.c_int32()
         rr = ctypes.c_double()
-        self._check("fe_pcg", self._lib.fe_pcg(self._h, _p(C), _p(free), _p(diag), _p(b), _p(x), float(rtol),
-                                               int(max_iter), ctypes.byref(it), ctypes.byref(rr), _stream()))
+        name = "fe_pcg_f32" if f32 else "fe_pcg"
+        self._check(name, getattr(self._lib, name)(self._h, _p(C), _p(free), _p(diag), _p(b), _p(x), float(rtol),
+                                                   int(max_iter), ctypes.byref(it), ctypes.byref(rr), _stream()))
         return it.value, rr.value
 
     def dot(self, a, b, free=None):
@@ -152,7 +155,7 @@ class FEDMN:
     orientation per element (all 8 Gauss points share it); tree: DMN parameters."""
 
     def __init__(self, mesh, tree, A2, precision="f64", newton_rtol=1e-6, max_newton=20, cg_rtol=1e-8,
-                 cg_max_iter=50000, line_search=True, block=0, ctas_per_sm=0):
+                 cg_max_iter=50000, line_search=True, block=0, ctas_per_sm=0, cg_f32=False):
         import numpy as np
         import torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
@@ -179,7 +182,7 @@ class FEDMN:
         self.du = torch.empty(nd, dtype=torch.float64, device=dev)
         self.diag = torch.empty(nd, dtype=torch.float64, device=dev)
         self.newton_rtol, self.max_newton = newton_rtol, max_newton
-        self.cg_rtol, self.cg_max_iter = cg_rtol, cg_max_iter
+        self.cg_rtol, self.cg_max_iter, self.cg_f32 = cg_rtol, cg_max_iter, cg_f32
         self.timing = dict(dmn_s=0.0, fe_s=0.0, dmn_calls=0, cg_iters=0)
 
     def increment(self, delta):
@@ -216,7 +219,7 @@ class FEDMN:
                 break
             self.mesh.tangent_diagonal(self.out["tangent"], self.diag)
             k, _ = self.mesh.pcg(self.out["tangent"], self.free, self.diag, self.f, self.du, self.cg_rtol,
-                                 self.cg_max_iter)
+                                 self.cg_max_iter, f32=self.cg_f32)
             cg_total += k
             self.mesh.axpy(-1.0, self.du, self.u, self.free)
             torch.cuda.synchronize()

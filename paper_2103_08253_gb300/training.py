@@ -18,6 +18,13 @@ increment from the virgin state (relative Frobenius error), as in the
 differentiation workload.  Every forward and backward pass runs through
 dmn_update and dmn_grad.
 
+Learning rates: the paper sets them by a learning-rate sweep and finds them
+almost equal for p, q and v.  The weights here start at 1/2^K each, so one
+AMSGrad step of the angle coefficients' size (about alpha) would move every
+weight by several times its value; the weights' rate is scaled by
+min(1, 8 / 2^K) (`lr_scale_v`), which bounds a step at about a tenth of a
+weight.
+
 A weight that reaches zero stays there (the Macaulay bracket has no gradient
 below zero).  The update path needs positive weights for the adjoint, so w is
 floored at `w_floor` (1e-9 of the sum) during training; `compress` sets the
@@ -76,7 +83,7 @@ class Trainer:
     stiffness samples; `plastic` (a J2 phase) adds stress samples of one increment."""
 
     def __init__(self, K, target, n_stiff, seed, elastic_matrix, plastic=None, n_plastic=0, lam_pen=1e3,
-                 w_floor=1e-9, alpha_max=1.5e-2, alpha_min=1.5e-3):
+                 w_floor=1e-9, alpha_max=1.5e-2, alpha_min=1.5e-3, lr_scale_v=None):
         import torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
         rng = np.random.default_rng(seed)
@@ -89,7 +96,8 @@ class Trainer:
         self.q = d(rng.uniform(0.0, 2 * np.pi, (N, M))).requires_grad_()
         v0 = rng.uniform(0.0, 1.0, L)
         self.v = d(v0 / v0.sum()).requires_grad_()
-        self.opt = torch.optim.Adam([self.p, self.q, self.v], lr=alpha_max, amsgrad=True)
+        self.lr_scale = [1.0, min(1.0, 8.0 / L) if lr_scale_v is None else lr_scale_v]
+        self.opt = torch.optim.Adam([{"params": [self.p, self.q]}, {"params": [self.v]}], lr=alpha_max, amsgrad=True)
         el_phases = (W.FIBER, elastic_matrix)
         start = W.TreeParams(K, M, self.p.detach().cpu().numpy(), self.q.detach().cpu().numpy(), v0 / v0.sum(),
                              el_phases)
@@ -139,8 +147,8 @@ class Trainer:
     def step(self):
         """One epoch (the whole sample set as one batch): returns (loss, max sample error, mean)."""
         import torch
-        for g in self.opt.param_groups:
-            g["lr"] = lr_schedule(self.epoch, *self.alpha)
+        for g, f in zip(self.opt.param_groups, self.lr_scale):
+            g["lr"] = f * lr_schedule(self.epoch, *self.alpha)
         self.opt.zero_grad()
         L, C = self.loss()
         L.backward()

@@ -28,12 +28,12 @@ def rel(a, b):
     return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
 
 
-def close(x, y):
-    """Equal to rounding: same iterations and status, values within 1e-12 of the array's scale."""
+def close(x, y, tol=1e-12):
+    """Equal to rounding: same iterations and status, values within tol of the array's scale."""
     if x.dtype.kind == "i":
         np.testing.assert_array_equal(x, y)
     else:
-        assert np.abs(x - y).max() <= 1e-12 * (np.abs(y).max() + 1e-300)
+        assert np.abs(x - y).max() <= tol * (np.abs(y).max() + 1e-300)
 
 
 def gpu_path(m, lam, Q, Ef, steps, n_steps, tree_id=None, S=None):
@@ -94,9 +94,12 @@ def test_table_traversal_equals_the_heap_traversal(prec):
     a = gpu_path(heap, lam, Q, Ef, 4, 10)
     b = gpu_path(table, lam, Q, Ef, 4, 10, tree_id=d(np.zeros(n, dtype=np.int32)))
     for x, y in zip(a, b):
+        # the mixed form's FP32 condensation rounds differently in the two traversals: its iterates,
+        # and so the converged jumps, agree to the FP64 criterion, not to the last bit
+        tol = 1e-12 if prec == "f64" else 1e-9
         for k in ("stress", "tangent", "iters", "status"):
-            close(x[k], y[k])
-        close(x["state_out"], y["state_out"][: heap.state_size])
+            close(x[k], y[k], tol)
+        close(x["state_out"], y["state_out"][: heap.state_size], tol)
     heap.close()
     table.close()
 

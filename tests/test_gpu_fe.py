@@ -76,21 +76,25 @@ def test_pcg_matches_a_direct_solve():
     xg = x.cpu().numpy()
     assert np.abs(xg[m.fixed]).max() == 0.0
     assert np.linalg.norm(xg - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+    # FP32 products: the residual reachable is about 1e-6
+    it32, res32 = g.pcg(Cd, free, diag, d(b), x, rtol=1e-6, max_iter=5000, f32=True)
+    assert res32 <= 1e-6 and 0 < it32 < 5000
+    assert np.linalg.norm(x.cpu().numpy() - x_ref) <= 1e-4 * np.linalg.norm(x_ref)
     # zero right-hand side: zero solution, no iterations
     it, res = g.pcg(Cd, free, diag, torch.zeros_like(x), x, rtol=1e-8)
     assert it == 0 and float(x.abs().max()) == 0.0
     g.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-8), ("mixed", 1e-6)])
-def test_fe_dmn_plate_matches_the_oracle(prec, tol):
+@pytest.mark.parametrize("prec,tol,cg32", [("f64", 1e-8, False), ("mixed", 1e-6, False), ("f64", 1e-6, True)])
+def test_fe_dmn_plate_matches_the_oracle(prec, tol, cg32):
     m = W.plate_with_hole_mesh(4, 2, 1, R=2.0, H=6.0, T=2.0)
     A2 = W.plate_orientation_field(m.centroid, m.R, m.H, m.T, seed=11)
     tree = W.tree_d10_fit(3, seed=12)
     deltas = [0.015 * 2 * m.H * k / 3 for k in (1, 2, 3)]
     lam, Q = oracle.interp_orientation(np.repeat(A2, 8, axis=0))
     ref = FE.run_fe_dmn(FE.Mesh(m.xyz, m.conn), tree, lam, Q, m.fixed, m.pull, deltas, affine=m.affine, rtol=1e-10)
-    run = fe.FEDMN(m, tree, A2, precision=prec, newton_rtol=1e-10, cg_rtol=1e-13)
+    run = fe.FEDMN(m, tree, A2, precision=prec, newton_rtol=1e-10, cg_rtol=1e-6 if cg32 else 1e-13, cg_f32=cg32)
     for k, delta in enumerate(deltas):
         r = run.increment(delta)
         assert r["converged"] and r["dmn_status_bad"] == 0, r
