@@ -210,6 +210,21 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
+def max_over_ranks(t_ms, dist, device):
+    """The largest of the ranks' times (all ranks get it); t_ms itself without a process group."""
+    if not dist:
+        return t_ms
+    import torch
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, n, steps, t_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * n * steps / (t_ms * 1e-3)
+
+
 def make_workload(n, rank, compressed=False):
     tree = (W.tree_with_zero_weights(K_DEPTH, seed=SEED_TREE) if compressed
             else W.tree_d10_fit(K_DEPTH, seed=SEED_TREE))
@@ -330,11 +345,8 @@ def run_form(form, ctx, args, dist):
         cur = step(s, cur, iters_steps[j])
     e1.record()
     torch.cuda.synchronize()
-    t_ms = e0.elapsed_time(e1)
+    t_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     if dist:
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
         dist.barrier()
     clk = clocks.stop() if clocks else None
     kms, cnt = m.profile_read()
@@ -396,13 +408,9 @@ def run_e2e(r, ctx, args, dist):
     t0 = time.perf_counter()
     for j in range(steps):
         m.update_host(lam_h, Q_h, En_h[j], dE_h[j], st_h, out=out_h, chunk=args.e2e_chunk)
-    t_ms = 1e3 * (time.perf_counter() - t0)
-    if dist:
-        t = torch.tensor([t_ms], device=ctx["dev"])
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), dist, ctx["dev"])
     world = dist.get_world_size() if dist else 1
-    return {"value": world * n * steps / (t_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    return {"value": job_value(world, n, steps, t_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps, "form": "f64", "ms_per_step": t_ms / steps,
             "api": "dmn_update_host", "chunk": args.e2e_chunk or "default",
             "status_ok": int((out_h["status"] == 0).sum().item())}
@@ -743,7 +751,7 @@ def run_gpu(args):
     steps = args.steps
     forms_out = {}
     for form, r in results.items():
-        v = world * n * steps / (r["t_ms"] * 1e-3)
+        v = job_value(world, n, steps, r["t_ms"])
         forms_out[form] = {"value": v, "unit": UNIT, "ms_per_step": r["t_ms"] / steps,
                            "kernel_ms_per_step": {k: x / steps for k, x in r["kms"].items()},
                            "newton_iters_per_update": r["iters_sum"] / (n * steps), "iters_hist": r["iters_hist"],
