@@ -55,13 +55,13 @@ PEAK_F32_GFLOPS = 152 * 128 * 2 * 2.07
 # method, counted from the arithmetic of csrc/dmn_device.cuh.  T = FP64 in the FP64 form, FP32
 # in the mixed form.
 #   per laminate, every pass:  N a and the children's strains 39 (FP64); residual share and
-#                              plain stress average 44 (FP64); condensation 699 (T), or 605 (T)
+#                              plain stress average 44 (FP64); condensation 678 (T), or 605 (T)
 #                              for a bottom laminate (leaf tangents D = lam 1(x)1 + 2 mu I - c m(x)m)
 #   per inner laminate:        children's strain corrections 39 (T)
 #   per laminate, per Newton correction: da = g + H d_eps 39 (T), a += da 3 (FP64)
 #   per leaf:                  elastic stress 13; J2 stress 56 + tangent scalars 12 (FP64)
 #   per pass:                  convergence test 15 (FP64)
-F_NODE_F64, F_RES, F_COND, F_COND_BOTTOM, F_DEPS, F_DA, F_A = 39, 44, 699, 605, 39, 39, 3
+F_NODE_F64, F_RES, F_COND, F_COND_BOTTOM, F_DEPS, F_DA, F_A = 39, 44, 678, 605, 39, 39, 3
 F_LEAF_EL, F_LEAF_J2, F_TEST = 13, 56 + 12, 15
 F_ROTATE = 1150         # per point: stress and tangent back to the global frame (k_final)
 F_STATE_NODE = 39       # state pass: per laminate (strains from the jumps)

@@ -297,17 +297,15 @@ __device__ __forceinline__ void condense(const double nd[3], const T n[3], doubl
   T ChN[6][3], B[6][3];
   SN_apply<T>(Ch, n, nr, ChN);
   SN_apply<T>(dC, n, nr, B);
-  T k[3][3];
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    const T col[6] = {ChN[0][m], ChN[1][m], ChN[2][m], ChN[3][m], ChN[4][m], ChN[5][m]};
-    T r[3];
-    Nt_apply<T>(n, nr, col, r);
-    k[0][m] = r[0]; k[1][m] = r[1]; k[2][m] = r[2];
-  }
+  // Kn = N^T (C-hat N), symmetric: its six distinct entries, row i of N^T against column m
+  const T k00 = n[0] * ChN[0][0] + nr[2] * ChN[4][0] + nr[1] * ChN[5][0];
+  const T k10 = n[1] * ChN[1][0] + nr[2] * ChN[3][0] + nr[0] * ChN[5][0];
+  const T k20 = n[2] * ChN[2][0] + nr[1] * ChN[3][0] + nr[0] * ChN[4][0];
+  const T k11 = n[1] * ChN[1][1] + nr[2] * ChN[3][1] + nr[0] * ChN[5][1];
+  const T k21 = n[2] * ChN[2][1] + nr[1] * ChN[3][1] + nr[0] * ChN[4][1];
+  const T k22 = n[2] * ChN[2][2] + nr[1] * ChN[3][2] + nr[0] * ChN[4][2];
   T Ki[3][3];
-  inv3_sym<T>(k[0][0], (T)0.5 * (k[0][1] + k[1][0]), (T)0.5 * (k[0][2] + k[2][0]), k[1][1],
-              (T)0.5 * (k[1][2] + k[2][1]), k[2][2], Ki);
+  inv3_sym<T>(k00, k10, k20, k11, k21, k22, Ki);
   T H[3][6];
 #pragma unroll
   for (int m = 0; m < 3; ++m)
