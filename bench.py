@@ -42,6 +42,9 @@ N_INCREMENTS = 50
 EPS_EQ = 0.03
 SEED_TREE, SEED_ORI, SEED_PATH = 2103, 8253, 1208
 WORKLOAD = "K=8 D10-interpolated DMN, 2^20 points/GPU, random 6-comp paths, 50 increments to 3% eq. strain"
+MATRIX_NOTE = {"linear": "J2, linear hardening 40 + 300 a MPa (E 3 GPa, nu 0.35)",
+               "explin": "J2, exponential-linear hardening of the paper's polyamide (E 2.1 GPa, nu 0.3, s0 29, "
+                         "s_inf 61.7 MPa, k0 10.6 GPa, k_inf 139 MPa); flop counts exclude its scalar Newton"}
 WORKLOAD_CMP = ("K=8 D10-interpolated DMN compressed to 70% of its leaves (weights of zero, 178 of 255 laminates "
                 "left), 2^20 points/GPU, random 6-comp paths, 50 increments to 3% eq. strain")
 
@@ -225,9 +228,10 @@ def job_value(world, n, steps, t_ms):
     return world * n * steps / (t_ms * 1e-3)
 
 
-def make_workload(n, rank, compressed=False):
-    tree = (W.tree_with_zero_weights(K_DEPTH, seed=SEED_TREE) if compressed
-            else W.tree_d10_fit(K_DEPTH, seed=SEED_TREE))
+def make_workload(n, rank, compressed=False, matrix="linear"):
+    phases = (W.FIBER, W.MATRIX_EXPLIN if matrix == "explin" else W.MATRIX)
+    tree = (W.tree_with_zero_weights(K_DEPTH, seed=SEED_TREE, phases=phases) if compressed
+            else W.tree_d10_fit(K_DEPTH, seed=SEED_TREE, phases=phases))
     A2, lam, Q = W.orientation_field(n, seed=SEED_ORI + 1000 * rank)
     Ef = W.random6_path_final(n, EPS_EQ, seed=SEED_PATH + 1000 * rank)
     return tree, A2, lam, Q, Ef
@@ -255,7 +259,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    tree, A2, lam, Q, Ef = make_workload(args.points, 0, args.workload == "k8-compressed")
+    tree, A2, lam, Q, Ef = make_workload(args.points, 0, args.workload == "k8-compressed", args.matrix)
     cores = os.cpu_count() or 1
     m = args.ref_points
     idx = np.arange(m)
@@ -332,8 +336,9 @@ def run_form(form, ctx, args, dist):
     torch.cuda.synchronize()
     host_state = None
     if form == "f64" and args.e2e_steps != 0:
-        host_state = torch.empty((S, n), dtype=torch.float64, pin_memory=True)
-        host_state.copy_(st[cur])
+        # the host state an application would hold: written by the CPU, then pinned (a copy-engine
+        # write into freshly pinned pages gave a 4x slower host-to-device rate on the box)
+        host_state = st[cur].cpu().pin_memory()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -399,6 +404,18 @@ def run_e2e(r, ctx, args, dist):
     # untimed call (its own state_out): allocates the library's stage buffers and second work set
     m.update_host(lam_h, Q_h, En_h[0], dE_h[0], st_h, out=out_h, chunk=args.e2e_chunk)
     out_h["state_out"] = st_h
+    # copy bandwidth of this process's pinned state buffer (1 GiB each way), for the record; the
+    # device-to-host copy writes back the bytes the host-to-device copy just read
+    probe = torch.empty(1 << 27, dtype=torch.float64, device=ctx["dev"])
+    flat = st_h.view(-1)[: 1 << 27]
+    bw = {}
+    for name, dst, src in (("h2d_GBps", probe, flat), ("d2h_GBps", flat, probe)):
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        bw[name] = round(8 * (1 << 27) / (time.perf_counter() - c0) / 1e9, 1)
+    del probe
     h2d = lam_h.nbytes + Q_h.nbytes + En_h[0].nbytes + dE_h[0].nbytes + st_h.nbytes
     d2h = (out_h["stress"].nbytes + out_h["tangent"].nbytes + st_h.nbytes + out_h["iters"].nbytes
            + out_h["status"].nbytes)
@@ -412,7 +429,7 @@ def run_e2e(r, ctx, args, dist):
     world = dist.get_world_size() if dist else 1
     return {"value": job_value(world, n, steps, t_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps, "form": "f64", "ms_per_step": t_ms / steps,
-            "api": "dmn_update_host", "chunk": args.e2e_chunk or "default",
+            "api": "dmn_update_host", "chunk": args.e2e_chunk or "default", "pinned_copy": bw,
             "status_ok": int((out_h["status"] == 0).sum().item())}
 
 
@@ -681,6 +698,8 @@ def main():
     ap.add_argument("--ref-points", type=int, default=1024)
     ap.add_argument("--cpu-points", type=int, default=1024)
     ap.add_argument("--parity-points", type=int, default=16)
+    ap.add_argument("--matrix", default="linear", choices=["linear", "explin"],
+                    help="matrix law of the k8 workloads: linear hardening (default) or the paper's exp-linear")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the library's default launch shape instead of autotuning it")
     ap.add_argument("--workload", default="k8", choices=["k8", "k8-compressed", "mixed-depth", "plate", "train"],
@@ -720,7 +739,7 @@ def run_gpu(args):
     dmn.load_library()
     n = args.points
     cmp = args.workload == "k8-compressed"
-    tree, A2, lam_np, Q_np, Ef = make_workload(n, rank, cmp)
+    tree, A2, lam_np, Q_np, Ef = make_workload(n, rank, cmp, args.matrix)
     try:
         smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
@@ -774,7 +793,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_form == "f64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_CMP if cmp else WORKLOAD, "K": K_DEPTH, "points_per_gpu": n,
-                       "increments": N_INCREMENTS,
+                       "increments": N_INCREMENTS, "matrix": MATRIX_NOTE[args.matrix],
                        "timed_increments": [args.warmup + 1, args.warmup + steps],
                        "l2": "no flush: per-step inputs (state %.1f GB) exceed L2"
                              % ((6 * tree_counts(tree.w)["j2"] + 3 * tree_counts(tree.w)["N"]) * n * 8e-9),

@@ -23,6 +23,7 @@ EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_interp_orientatio
 PHASE_ELASTIC, PHASE_J2_LINEAR, PHASE_J2_EXPLIN = 0, 1, 2
 PREC_F64 = 0
 PREC_MIXED = 1
+PRECISIONS = {"f64": PREC_F64, "mixed": PREC_MIXED}
 STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE, STATUS_LINESEARCH, STATUS_BAD_TREE = 0, 1, 2, 3, 4
 MAX_TREES = 8
 
@@ -144,9 +145,9 @@ class DMN:
             for f, ph in enumerate(tr.phases):
                 descs[k].phase[f] = Phase_(int(ph.kind), float(ph.E), float(ph.nu), float(ph.sigma0), float(ph.H),
                                            float(getattr(ph, "sigma_inf", 0.0)), float(getattr(ph, "k0", 0.0)))
-        if precision not in ("f64", "mixed"):
-            raise ValueError("precision must be 'f64' or 'mixed'")
-        opt = Options_(float(tol), int(max_iter), PREC_MIXED if precision == "mixed" else PREC_F64, int(block),
+        if precision not in PRECISIONS:
+            raise ValueError("precision must be one of %s" % (tuple(PRECISIONS),))
+        opt = Options_(float(tol), int(max_iter), PRECISIONS[precision], int(block),
                        int(ctas_per_sm), int(bool(line_search)))
         self.precision = precision
         h = ctypes.c_void_p()
