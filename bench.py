@@ -676,6 +676,8 @@ def run_train(args):
                                    % (TRAIN_SAMPLES, TRAIN_SAMPLES),
                        "dmn_updates_per_epoch": n_upd},
             "gp_updates_per_s": n_upd * args.steps / t,
+            "compression": {"handle_rebuilds": tr.rebuilds, "leaves_left": int(tr.pattern.sum()),
+                            "leaves": 1 << K_DEPTH},
             "loss": [round(h[0], 6) for h in hist], "mean_stiffness_error": [round(h[2], 6) for h in hist],
             "clocks": clk}
     tr.close()

@@ -199,10 +199,14 @@ int dmn_update_host(dmn_handle* h, int64_t n, const int32_t* tree_id, const doub
                     double* tangent, int32_t* iters, int32_t* status, int64_t chunk, void* stream);
 
 /* Replace the parameters of tree tree_id (host arrays laid out as in
- * dmn_tree_desc: p, q [(2^K-1) * M] in the paper's ordering, w [2^K] > 0),
+ * dmn_tree_desc: p, q [(2^K-1) * M] in the paper's ordering, w [2^K] >= 0),
  * e.g. after an optimiser step of the offline training (Sec. 3.1).  Depth,
- * shape functions and phases stay.  Synchronises the device.  Errors:
- * DMN_ERR_ARG for a bad tree_id or parameters (as dmn_create). */
+ * shape functions and phases stay, and so does the set of leaves of weight
+ * zero: a handle without zero weights takes only positive ones, a handle of
+ * compressed trees only weights that are zero exactly where they were (a new
+ * compression needs a new handle).  Synchronises the device.  Errors:
+ * DMN_ERR_ARG for a bad tree_id, parameters that dmn_create rejects, or a
+ * changed set of zero weights. */
 int dmn_set_params(dmn_handle* h, int32_t tree_id, const double* p, const double* q, const double* w);
 
 /* Adjoint of the converged update (FP64): for a loss L with g_stress =
@@ -217,7 +221,10 @@ int dmn_set_params(dmn_handle* h, int32_t tree_id, const double* p, const double
  * dL/dtheta = g.d sigma_bar/d theta + mu.dR/d theta with mu = (da/dE) g, the
  * response of the condensed tree to a macro perturbation g (no extra solve);
  * the condensation at the converged jumps is recomputed, nothing from the
- * Newton iterations is stored.  Inputs are those of the dmn_update call that
+ * Newton iterations is stored.  For a compressed tree the gradient covers the
+ * remaining laminates and leaves; laminates passed through and leaves of
+ * weight zero get none (the weights' Macaulay bracket of Sec. 3.1 passes none
+ * below zero either).  Inputs are those of the dmn_update call that
  * produced state_out (its output, read only) from state_in; points whose
  * update did not converge should get g_stress = 0.  One tree per handle
  * (tree_id must be NULL).  The first call with a larger n than any earlier

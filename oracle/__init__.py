@@ -145,10 +145,11 @@ def gradient_operator(tree, lam1, lam2):
 
 def newton_system(tree, lam1, lam2, E_loc, a, z_n):
     """J (dense), R, da = -J^{-1} R (oracle's Cholesky), leaf eps, sigma and
-    sigma_bar at one iterate.  z_n: [2^K, 7] per leaf (alpha_bar, ep6)."""
+    sigma_bar at one iterate.  z_n: [2^K, 7] per leaf (alpha_bar, ep6); a: the jumps of
+    the (compressed) tree's laminates, as in the state."""
     L = 1 << tree.K
-    N = L - 1
-    J = np.empty((3 * N, 3 * N)); R = np.empty(3 * N); da = np.empty(3 * N)
+    n_a = np.asarray(a).size
+    J = np.empty((n_a, n_a)); R = np.empty(n_a); da = np.empty(n_a)
     eps = np.empty((L, 6)); sig = np.empty((L, 6)); sbar = np.empty(6)
     p = _f64(tree.p); q = _f64(tree.q); w = _f64(tree.w); m = phases_array(tree.phases)
     rc = _load().oracle_newton_system(tree.K, tree.M, _p(p), _p(q), _p(w), _p(m), float(lam1), float(lam2),
@@ -237,6 +238,7 @@ def gradient_ift(tree, lam, Q, E_glob, a_star, z_leaf, g_glob, directions=None, 
         return g_loc @ (sp - sm) / (2 * step) - lamv @ (Rp - Rm) / (2 * step)
 
     hw = h * w0.max()
+    alive = w0 > 0   # weights of zero stay out: a step would change the compressed tree
     if directions is not None:
         return [partial(dp, dq, dw, h) for dp, dq, dw in directions]
     gp = np.zeros_like(p0)
@@ -248,6 +250,8 @@ def gradient_ift(tree, lam, Q, E_glob, a_star, z_leaf, g_glob, directions=None, 
         gp[idx] = partial(e, 0 * q0, 0 * w0, h)
         gq[idx] = partial(0 * p0, e, 0 * w0, h)
     for l in range(w0.size):
+        if not alive[l]:
+            continue
         e = np.zeros_like(w0)
         e[l] = 1.0
         gw[l] = partial(0 * p0, 0 * q0, e, hw)
@@ -255,12 +259,13 @@ def gradient_ift(tree, lam, Q, E_glob, a_star, z_leaf, g_glob, directions=None, 
 
 
 def leaf_states(tree, state, i):
-    """z^n of every leaf of point i, [2^K, 7] (alpha_bar, ep6), from a field-major state."""
+    """z^n of every leaf of point i, [2^K, 7] (alpha_bar, ep6), from a field-major state
+    (leaves of weight zero carry no state: zeros)."""
     L = 1 << tree.K
     z = np.zeros((L, 7))
     slot = 0
     for l in range(L):
-        if tree.phases[l % 2].kind != 0:
+        if tree.phases[l % 2].kind != 0 and tree.w[l] > 0:
             b = state[6 * slot:6 * slot + 6, i]
             z[l] = [b[0], b[1], b[2], -(b[1] + b[2]), b[3], b[4], b[5]]
             slot += 1
@@ -270,5 +275,5 @@ def leaf_states(tree, state, i):
 def jumps(tree, state, i):
     """a of point i (paper ordering) from a field-major state."""
     L = 1 << tree.K
-    nz = sum(1 for l in range(L) if tree.phases[l % 2].kind != 0)
+    nz = sum(1 for l in range(L) if tree.phases[l % 2].kind != 0 and tree.w[l] > 0)
     return np.array(state[6 * nz:, i])

@@ -42,9 +42,10 @@ struct Tree {
   double wsum = 1.0;       // sum of the leaf weights as given
   PhaseDev ph[2];
   // compressed trees (some leaf weight zero): N laminates left, Lc leaves left,
-  // traversal tables lf [Lc] (int4), pre [N], post [N] in one allocation
+  // traversal tables lf [Lc] (int4), pre [N], post [N], paper index [N] in one allocation
   int cmp = 0, Lc = 0;
   int* d_tab = nullptr;
+  std::vector<char> alive;  // compressed trees: which leaf weights are positive
 };
 
 }  // namespace
@@ -101,7 +102,7 @@ int cuda_fail(dmn_handle* h, cudaError_t e, const char* what) {
 }
 
 TreeDev tree_dev(const Tree& t) {
-  TreeDev d;
+  TreeDev d{};
   d.K = t.K; d.M = t.M; d.N = t.N; d.L = t.L; d.nz = t.nz; d.z_both = t.z_both;
   d.p = t.d_p; d.q = t.d_q;
   d.c1 = t.d_c; d.c2 = t.d_c + t.N; d.sc = t.d_c + 2 * t.N;
@@ -112,6 +113,7 @@ TreeDev tree_dev(const Tree& t) {
   d.lf = reinterpret_cast<const int4*>(t.d_tab);
   d.pre = t.d_tab ? t.d_tab + 4 * t.Lc : nullptr;
   d.post = t.d_tab ? t.d_tab + 4 * t.Lc + t.N : nullptr;
+  d.pidx = t.d_tab ? t.d_tab + 4 * t.Lc + 2 * t.N : nullptr;
   return d;
 }
 
@@ -629,6 +631,8 @@ struct GradParams {
 // work fields per point
 __host__ __device__ inline size_t grad_fields(int N, int L) { return (size_t)33 * N + 2 * L + 6; }
 
+// CMP: the tree is walked by its compressed-traversal tables.
+template <bool CMP>
 __global__ void __launch_bounds__(128) k_grad(GradParams P) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= P.nc) return;
@@ -669,7 +673,7 @@ __global__ void __launch_bounds__(128) k_grad(GradParams P) {
   for (int f = 0; f < 3 * N; ++f) {
     const int node = f / 3, c = f - 3 * node;
     const int lvl = 32 - __clz(node + 1);
-    const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+    const int j = CMP ? node : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
     a[(size_t)f * ws] = P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt];
   }
   double Eloc[6];
@@ -682,7 +686,8 @@ __global__ void __launch_bounds__(128) k_grad(GradParams P) {
   Sub<double> root;
   double r2;
   GH<double> g{gh, ws, gh};
-  tree_pass<double, true>(t, Eloc, A, g, false, 1.0, root, r2, nullptr);
+  if (CMP) tree_pass_c<double, true>(t, Eloc, A, g, false, 1.0, root, r2, nullptr);
+  else tree_pass<double, true>(t, Eloc, A, g, false, 1.0, root, r2, nullptr);
   // loss gradient into the local frame: sigma_glob = R sigma_loc  =>  g_loc = R^T g_glob
   double R[6][6], gl[6];
   mandel_rotation(P.Q + 9 * pt, R);
@@ -693,8 +698,13 @@ __global__ void __launch_bounds__(128) k_grad(GradParams P) {
     for (int I = 0; I < 6; ++I) s += R[I][J] * P.g_stress[6 * pt + I];
     gl[J] = s;
   }
-  adjoint_pass(t, Eloc, gl, ph, A, Wk);
-  adjoint_weights(t, t.wl, t.wsum, Wk, gw, ws);
+  if (CMP) {
+    adjoint_pass_c(t, Eloc, gl, ph, A, Wk);
+    adjoint_weights_c(t, t.wl, t.wsum, Wk, gw, ws);
+  } else {
+    adjoint_pass(t, Eloc, gl, ph, A, Wk);
+    adjoint_weights(t, t.wl, t.wsum, Wk, gw, ws);
+  }
   if (P.g_E) {   // dL/dE = C^T g (C symmetric), rotated back
     double ge[6];
 #pragma unroll
@@ -730,7 +740,7 @@ __global__ void __launch_bounds__(256) k_grad_reduce(TreeDev t, int64_t nc, cons
     base = work + (size_t)(31 * N + which * N + node) * ws;
     fac = work + (size_t)(33 * N + 2 * L + m) * ws;
     const int lvl = 32 - __clz(node + 1);
-    const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+    const int j = t.pidx ? t.pidx[node] : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
     out = (which ? g_q : g_p) + j * M + m;
   } else {
     const int l = r - 2 * N * M;
@@ -789,7 +799,7 @@ struct CmpTree {
   int N = 0, Lc = 0, nz = 0;
   std::vector<double> p, q, c;   // p, q [N][M]; c = c1 [N], c2 [N], sc [N], leaf weights [L]
   std::vector<float> cf;         // c1f [N], c2f [N], c12f [N]
-  std::vector<int> tab;          // lf [Lc] (4 ints each), pre [N], post [N]
+  std::vector<int> tab;          // lf [Lc] (4 ints each), pre [N], post [N], paper index [N]
 };
 
 void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& B) {
@@ -836,7 +846,7 @@ void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& 
       if (h > N) {                                     // a leaf
         const int l = h - N - 1, ph = l & 1;
         const int slot = inel[ph] ? nz++ : -1;
-        lf.insert(lf.end(), {top, depth - top, 0, ((slot + 1) << 2) | (ph << 1)});
+        lf.insert(lf.end(), {top, depth - top, 0, (l << 12) | ((slot + 1) << 2) | (ph << 1)});
         return;
       }
       if (cid[h] < 0) {                                // one weightless side: pass the other through
@@ -858,6 +868,7 @@ void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& 
   B.tab = lf;
   B.tab.insert(B.tab.end(), pre.begin(), pre.end());
   B.tab.insert(B.tab.end(), post.begin(), post.end());
+  B.tab.insert(B.tab.end(), paper_of.begin(), paper_of.end());
 }
 
 bool has_zero_weight(const dmn_tree_desc& d) {
@@ -1088,6 +1099,8 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
       const bool inel[2] = {d.phase[0].kind != DMN_PHASE_ELASTIC, d.phase[1].kind != DMN_PHASE_ELASTIC};
       build_compressed(d, inel, cv[k]);
       t.cmp = 1;
+      t.alive.resize(t.L);
+      for (int l = 0; l < t.L; ++l) t.alive[l] = d.w[l] > 0.0;
       t.N = cv[k].N;
       t.Lc = cv[k].Lc;
       t.nz = cv[k].nz;
@@ -1334,11 +1347,30 @@ int dmn_set_params(dmn_handle* h, int32_t tree_id, const double* p, const double
   if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_set_params: NULL handle");
   if (tree_id < 0 || tree_id >= (int)h->trees.size()) return fail(h, DMN_ERR_ARG, "dmn_set_params: bad tree_id");
   Tree& T = h->trees[tree_id];
-  if (h->cmp)
-    return fail(h, DMN_ERR_ARG, "dmn_set_params: the handle holds compressed trees (weights of zero); create a new handle");
   dmn_tree_desc d;
   d.K = T.K; d.M = T.M; d.p = p; d.q = q; d.w = w;
-  if (const char* m = check_tree(d)) return fail(h, DMN_ERR_ARG, std::string("dmn_set_params: ") + m);
+  if (const char* m = check_tree(d, h->cmp)) return fail(h, DMN_ERR_ARG, std::string("dmn_set_params: ") + m);
+  if (h->cmp) {   // same compressed structure: new parameters in its numbering
+    for (int l = 0; l < T.L; ++l)
+      if ((w[l] > 0.0) != (T.alive.empty() ? true : T.alive[l] != 0))
+        return fail(h, DMN_ERR_ARG, "dmn_set_params: the set of zero leaf weights changed (another compressed "
+                                    "tree); create a new handle");
+    const bool inel[2] = {T.ph[0].kind != 0, T.ph[1].kind != 0};
+    CmpTree B;
+    build_compressed(d, inel, B);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && !B.p.empty())
+      e = cudaMemcpy(T.d_p, B.p.data(), sizeof(double) * B.p.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !B.q.empty())
+      e = cudaMemcpy(T.d_q, B.q.data(), sizeof(double) * B.q.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(T.d_c, B.c.data(), sizeof(double) * B.c.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !B.cf.empty())
+      e = cudaMemcpy(T.d_cf, B.cf.data(), sizeof(float) * B.cf.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_set_params");
+    T.wsum = 0.0;
+    for (int l = 0; l < T.L; ++l) T.wsum += w[l];
+    return DMN_OK;
+  }
   std::vector<double> ph(T.N * T.M), qh(T.N * T.M);
   heap_params(d, ph.data(), qh.data());
   cudaError_t e = cudaDeviceSynchronize();
@@ -1365,7 +1397,6 @@ int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam
   if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_grad: NULL handle");
   if (n < 0) return fail(h, DMN_ERR_ARG, "dmn_grad: n < 0");
   if (tree_id || h->trees.size() != 1) return fail(h, DMN_ERR_ARG, "dmn_grad: one tree only (tree_id must be NULL)");
-  if (h->cmp) return fail(h, DMN_ERR_ARG, "dmn_grad: compressed trees (weights of zero) are not supported");
   if (n == 0) return DMN_OK;
   if (!lam || !Q || !E_n || !dE || !state_in || !state_out || !g_stress || !g_p || !g_q || !g_w)
     return fail(h, DMN_ERR_ARG, "dmn_grad: NULL array");
@@ -1386,7 +1417,8 @@ int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam
   for (int64_t n0 = 0; n0 < n; n0 += chunk) {
     const int64_t nc = std::min(chunk, n - n0);
     GradParams P{td, n, n0, nc, lam, Q, E_n, dE, state_in, state_out, g_stress, g_E, h->gwork};
-    k_grad<<<(unsigned)div_up(nc, 128), 128, 0, s>>>(P);
+    if (h->cmp) k_grad<true><<<(unsigned)div_up(nc, 128), 128, 0, s>>>(P);
+    else k_grad<false><<<(unsigned)div_up(nc, 128), 128, 0, s>>>(P);
     k_grad_reduce<<<n_params, 256, 0, s>>>(td, nc, h->gwork, g_p, g_q, g_w);
   }
   e = cudaGetLastError();
@@ -1533,7 +1565,7 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
     if (opt->tol > 0.0) tol = opt->tol;
     if (opt->max_iter > 0) max_iter = opt->max_iter;
   }
-  TreeDev td;
+  TreeDev td{};
   td.K = K; td.M = M; td.N = N; td.L = L;
   int n_inel = 0;
   for (int f = 0; f < 2; ++f) {

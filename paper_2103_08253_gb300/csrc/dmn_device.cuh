@@ -64,11 +64,18 @@ struct TreeDev {
   // tree is walked by tables instead of heap arithmetic.
   int Lc;            // leaves with weight > 0, in leaf order
   const int4* lf;    // per such leaf: x = depth where its descent starts, y = laminates descended to reach it,
-                     // z = laminates completed right after it, w = (state slot + 1) << 2 | phase << 1 | pair,
+                     // z = laminates completed right after it,
+                     // w = leaf << 12 | (state slot + 1) << 2 | phase << 1 | pair,
                      // pair = 1 when this leaf and the next are the two children of one laminate
   const int* pre;    // [N] laminates in descent (pre-) order
   const int* post;   // [N] laminates in completion (post-) order
+  const int* pidx;   // [N] the paper's index of each laminate (in the uncompressed tree)
 };
+
+// fields of TreeDev::lf .w
+__device__ __forceinline__ int lf_slot(int w) { return ((w >> 2) & 1023) - 1; }
+__device__ __forceinline__ int lf_phase(int w) { return (w >> 1) & 1; }
+__device__ __forceinline__ int lf_leaf(int w) { return w >> 12; }
 
 template <typename T>
 struct NodeC {
@@ -688,17 +695,17 @@ __device__ void tree_pass_c(const TreeDev& t, const double Eloc[6], const PointA
     }
     Sub<T> res;
     int nup;
-    const int ph0 = (f.w >> 1) & 1;
+    const int ph0 = lf_phase(f.w);
     double z[6], g;
     if (pair) {
       const int4 f2 = __ldg(t.lf + l + 1);
-      const int ph1 = (f2.w >> 1) & 1;
+      const int ph1 = lf_phase(f2.w);
       double sL[6], sR[6];
       LeafTan<T> DL, DR;
-      load_z_slot(P, (f.w >> 2) - 1, z);
+      load_z_slot(P, lf_slot(f.w), z);
       leaf_iso<T>(t.ph[ph0], e, z, sL, &DL, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
-      load_z_slot(P, (f2.w >> 2) - 1, z);
+      load_z_slot(P, lf_slot(f2.w), z);
       leaf_iso<T>(t.ph[ph1], epsR[d], z, sR, &DR, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
       const int node = __ldg(t.post + ipost++);
@@ -714,7 +721,7 @@ __device__ void tree_pass_c(const TreeDev& t, const double Eloc[6], const PointA
     } else {
       double sg[6];
       LeafTan<T> D;
-      load_z_slot(P, (f.w >> 2) - 1, z);
+      load_z_slot(P, lf_slot(f.w), z);
       leaf_iso<T>(t.ph[ph0], e, z, sg, &D, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
       leaf_sub<T>(D, sg, res);
@@ -760,11 +767,11 @@ __device__ inline void write_leaf_states_c(const TreeDev& t, const double Eloc[6
 #pragma unroll
       for (int I = 0; I < 6; ++I) { epsR[d + 1][I] = e[I] + c1 * Na[I]; e[I] -= c2 * Na[I]; }
     }
-    const int slot = (f.w >> 2) - 1;
+    const int slot = lf_slot(f.w);
     if (slot < 0) continue;
     double z[6], zn[6], sig[6];
     load_z_slot(P, slot, z);
-    leaf_iso<double>(t.ph[(f.w >> 1) & 1], e, z, sig, nullptr, zn, nullptr);
+    leaf_iso<double>(t.ph[lf_phase(f.w)], e, z, sig, nullptr, zn, nullptr);
     double* b = zout + (size_t)(6 * slot) * zos;
 #pragma unroll
     for (int c = 0; c < 6; ++c) b[c * zos] = nan_out ? __longlong_as_double(0x7ff8000000000000LL) : zn[c];
@@ -1011,6 +1018,155 @@ __device__ void adjoint_weights(const TreeDev& t, const double* wl, double S, co
     sum_gw += G0 * __ldg(wl + 2 * m) + G1 * __ldg(wl + 2 * m + 1);
   }
   for (int l = 0; l < L; ++l) gw[(size_t)l * gws] = (gw[(size_t)l * gws] - sum_gw) / S;
+}
+
+// adjoint_pass over a compressed tree (tables of TreeDev): the same per-laminate and
+// per-leaf terms, leaves one at a time, laminates numbered as in the state.
+__device__ void adjoint_pass_c(const TreeDev& t, const double Eloc[6], const double gl[6], const double ph[6],
+                               const PointArrays& P, const AdjWork& Wk) {
+  double epsR[KMAX + 1][6], gR[KMAX + 1][6];
+  double pend_s[KMAX + 1][6], pend_t[KMAX + 1][6];
+  const size_t ws = Wk.ws;
+  int ipre = 0, ipost = 0;
+  for (int l = 0; l < t.Lc; ++l) {
+    const int4 f = __ldg(t.lf + l);
+    int d = f.x;
+    double e[6], ge[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) {
+      e[I] = (l == 0) ? Eloc[I] : epsR[d][I];
+      ge[I] = (l == 0) ? gl[I] : gR[d][I];
+    }
+    for (int s = 0; s < f.y; ++s, ++d) {
+      const int node = __ldg(t.pre + ipre++);
+      double nd[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) nd[c] = P.nrm[(3 * node + c) * P.ns];
+      const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      const double* ap = P.a + (size_t)(3 * node) * P.as;
+      const double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
+      const double* Hp = Wk.H + (size_t)(21 * node + 3) * Wk.hs;
+      double mu[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double v = 0.0;
+#pragma unroll
+        for (int I = 0; I < 6; ++I) v += Hp[(6 * c + I) * Wk.hs] * ge[I];
+        mu[c] = v;
+        Wk.mu[(size_t)(3 * node + c) * ws] = v;
+      }
+      double Na[6], Nm[6];
+      N_apply<double>(nd, ndr, a, Na);
+      N_apply<double>(nd, ndr, mu, Nm);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) {
+        epsR[d + 1][I] = e[I] + c1 * Na[I];
+        gR[d + 1][I] = ge[I] + c1 * Nm[I];
+        e[I] -= c2 * Na[I];
+        ge[I] -= c2 * Nm[I];
+      }
+    }
+    // the leaf: stress, D g_i, direct weight term
+    double sb[6], tb[6];
+    {
+      double z[6];
+      LeafTan<double> D;
+      load_z_slot(P, lf_slot(f.w), z);
+      leaf_iso<double>(t.ph[lf_phase(f.w)], e, z, sb, &D, nullptr, nullptr);
+      const double tr = ge[0] + ge[1] + ge[2];
+      double mg = 0.0, gs = 0.0;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { mg += D.m[I] * ge[I]; gs += ge[I] * sb[I]; }
+#pragma unroll
+      for (int I = 0; I < 6; ++I) tb[I] = 2.0 * D.mu * ge[I] - D.c * mg * D.m[I] + (I < 3 ? D.lam * tr : 0.0);
+      Wk.direct[(size_t)lf_leaf(f.w) * ws] = gs;
+    }
+    // laminates completed by this leaf: left sibling pending at the same depth
+    for (int u = 0; u < f.z; ++u) {
+      const int node = __ldg(t.post + ipost++);
+      double sbL[6], tbL[6];
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { sbL[I] = pend_s[d][I]; tbL[I] = pend_t[d][I]; }
+      double nd[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) nd[c] = P.nrm[(3 * node + c) * P.ns];
+      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      const double W = __ldg(t.sc + node) / (c1 * c2);
+      const double* ap = P.a + (size_t)(3 * node) * P.as;
+      const double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
+      double mu[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mu[c] = Wk.mu[(size_t)(3 * node + c) * ws];
+      const double ar[3] = {a[0] * RS2, a[1] * RS2, a[2] * RS2}, mr[3] = {mu[0] * RS2, mu[1] * RS2, mu[2] * RS2};
+      double ds[6], dt[6];
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { ds[I] = sb[I] - sbL[I]; dt[I] = tb[I] - tbL[I]; }
+      double u1[3], u2[3];
+      Nt_apply<double>(a, ar, dt, u1);    // N(a)^T (tau_R - tau_L)
+      Nt_apply<double>(mu, mr, ds, u2);   // N(mu)^T (sb_R - sb_L)
+      const double sc = W * c1 * c2;
+      const double gn[3] = {sc * (u1[0] + u2[0]), sc * (u1[1] + u2[1]), sc * (u1[2] + u2[2])};
+      double al, be, sa, ca, sbeta, cbeta;
+      node_angles(t, node, ph, al, be);
+      sincos(al, &sa, &ca);
+      sincos(be, &sbeta, &cbeta);
+      Wk.gab[(size_t)node * ws] = gn[0] * ca * cbeta + gn[1] * ca * sbeta - gn[2] * sa;
+      Wk.gab[(size_t)(t.N + node) * ws] = -gn[0] * sa * sbeta + gn[1] * sa * cbeta;
+      const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+      double Nm[6], Na[6];
+      N_apply<double>(nd, ndr, mu, Nm);
+      N_apply<double>(nd, ndr, a, Na);
+      double GL = 0.0, GR = 0.0;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) {
+        GL += Nm[I] * sbL[I] + Na[I] * tbL[I];
+        GR += Nm[I] * sb[I] + Na[I] * tb[I];
+      }
+      const double WL = c1 * W, WR = c2 * W;
+      Wk.xi[(size_t)node * ws] = (WR * GR + WL * GL) / (W * W);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { sb[I] = c1 * sbL[I] + c2 * sb[I]; tb[I] = c1 * tbL[I] + c2 * tb[I]; }
+      --d;
+    }
+    if (d > 0) {
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { pend_s[d][I] = sb[I]; pend_t[d][I] = tb[I]; }
+    }
+  }
+}
+
+// adjoint_weights over a compressed tree.  Leaves of weight zero get no gradient: the
+// compressed tree holds nothing of them, and the weights' Macaulay bracket (Sec. 3.1)
+// passes none below zero.
+__device__ void adjoint_weights_c(const TreeDev& t, const double* wl, double S, const AdjWork& Wk, double* gw,
+                                  size_t gws) {
+  const size_t ws = Wk.ws;
+  double accR[KMAX + 2];
+  double sum_gw = 0.0;
+  for (int l = 0; l < t.L; ++l) gw[(size_t)l * gws] = 0.0;
+  int ipre = 0;
+  for (int l = 0; l < t.Lc; ++l) {
+    const int4 f = __ldg(t.lf + l);
+    int d = f.x;
+    double acc = (l == 0) ? 0.0 : accR[d];
+    for (int s = 0; s < f.y; ++s, ++d) {
+      const int node = __ldg(t.pre + ipre++);
+      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      const double W = __ldg(t.sc + node) / (c1 * c2);
+      const double xi = Wk.xi[(size_t)node * ws];
+      accR[d + 1] = acc - c1 * W * xi;   // right subtree: - W_L Xi
+      acc += c2 * W * xi;                // left subtree: + W_R Xi
+    }
+    const int leaf = lf_leaf(f.w);
+    const double G = Wk.direct[(size_t)leaf * ws] + acc;
+    gw[(size_t)leaf * gws] = G;
+    sum_gw += G * __ldg(wl + leaf);
+  }
+  for (int l = 0; l < t.Lc; ++l) {
+    const int leaf = lf_leaf(__ldg(t.lf + l).w);
+    gw[(size_t)leaf * gws] = (gw[(size_t)leaf * gws] - sum_gw) / S;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -26,10 +26,11 @@ min(1, 8 / 2^K) (`lr_scale_v`), which bounds a step at about a tenth of a
 weight.
 
 A weight that reaches zero stays there (the Macaulay bracket has no gradient
-below zero).  The update path needs positive weights for the adjoint, so w is
-floored at `w_floor` (1e-9 of the sum) during training; `compress` sets the
-floored weights to zero afterwards, and the online update then runs on the
-compressed tree.
+below zero), and the tree is compressed (Sec. 3.1): with `compress` (default)
+the weights are w = <v>_+ exactly, and whenever the set of zero weights changes
+the DMN handles are rebuilt on the newly compressed tree, so that later epochs
+condense fewer laminates.  Without it, w is floored at `w_floor` and the tree
+stays whole.
 """
 from __future__ import annotations
 
@@ -83,12 +84,13 @@ class Trainer:
     stiffness samples; `plastic` (a J2 phase) adds stress samples of one increment."""
 
     def __init__(self, K, target, n_stiff, seed, elastic_matrix, plastic=None, n_plastic=0, lam_pen=1e3,
-                 w_floor=1e-9, alpha_max=1.5e-2, alpha_min=1.5e-3, lr_scale_v=None):
+                 w_floor=1e-9, alpha_max=1.5e-2, alpha_min=1.5e-3, lr_scale_v=None, compress=True):
         import torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
         rng = np.random.default_rng(seed)
         N, L, M = (1 << K) - 1, 1 << K, 3
-        self.K, self.lam_pen, self.w_floor = K, lam_pen, w_floor
+        self.K, self.lam_pen, self.w_floor, self.compress_on = K, lam_pen, w_floor, compress
+        self.rebuilds = 0
         self.alpha = (alpha_min, alpha_max)
         d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(self.dev)
         # initial parameters as in Sec. 4.4
@@ -99,9 +101,12 @@ class Trainer:
         self.lr_scale = [1.0, min(1.0, 8.0 / L) if lr_scale_v is None else lr_scale_v]
         self.opt = torch.optim.Adam([{"params": [self.p, self.q]}, {"params": [self.v]}], lr=alpha_max, amsgrad=True)
         el_phases = (W.FIBER, elastic_matrix)
+        self.el_phases = el_phases
+        self.pl_phases = None if plastic is None else (W.FIBER, plastic)
         start = W.TreeParams(K, M, self.p.detach().cpu().numpy(), self.q.detach().cpu().numpy(), v0 / v0.sum(),
                              el_phases)
         self.m_el = dmn.DMN(start)
+        self.pattern = v0 > 0
         tgt_el = dmn.DMN(W.TreeParams(K, M, target.p, target.q, target.w, el_phases))
         A2, lam, Q = W.orientation_field(n_stiff, seed=seed + 1)
         self.lam_e, self.Q_e = d(lam), d(Q)
@@ -127,13 +132,32 @@ class Trainer:
         self.history = []
 
     def weights(self):
-        """w = <v>_+, floored (the floor carries no gradient)."""
+        """w = <v>_+ (compressing), or floored at w_floor (the floor carries no gradient)."""
         import torch
-        return torch.clamp(self.v, min=self.w_floor)
+        return torch.clamp(self.v, min=0.0 if self.compress_on else self.w_floor)
+
+    def _recompress(self, w):
+        """New handles when the set of zero weights has changed (another compressed tree)."""
+        import torch
+        pattern = (w.detach() > 0).cpu().numpy()
+        if (pattern == self.pattern).all():
+            return
+        self.pattern = pattern
+        self.rebuilds += 1
+        p, q, wn = (x.detach().cpu().numpy() for x in (self.p, self.q, w))
+        self.m_el.close()
+        self.m_el = dmn.DMN(W.TreeParams(self.K, 3, p, q, wn, self.el_phases))
+        if self.m_pl is not None:
+            self.m_pl.close()
+            self.m_pl = dmn.DMN(W.TreeParams(self.K, 3, p, q, wn, self.pl_phases), line_search=True)
+            self.z_st = torch.zeros((self.m_pl.state_size, self.E_p.shape[0]), dtype=torch.float64,
+                                    device=self.dev)
 
     def loss(self):
         import torch
         w = self.weights()
+        if self.compress_on:
+            self._recompress(w)
         C = ag.dmn_stiffness(self.m_el, self.lam_e, self.Q_e, self.p, self.q, w)
         J = stiffness_loss(C, self.C_t)
         if self.m_pl is not None:

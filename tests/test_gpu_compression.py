@@ -122,7 +122,7 @@ def test_weightless_half_equals_the_smaller_tree():
             close(x[k], y[k])
 
 
-def test_single_leaf_and_unsupported_calls():
+def test_single_leaf_parameters_and_gradient():
     K = 3
     t = W.tree_d10_fit(K, seed=50)
     w = np.zeros(1 << K)
@@ -139,10 +139,15 @@ def test_single_leaf_and_unsupported_calls():
         st, sig, C, it, stat, gap = oracle.update(t, lam, Q, En, dE, st)
     assert (o["status"] == 0).all() and (o["iters"] == 0).all()
     assert rel(o["stress"], sig).max() <= 1e-12 and rel(o["tangent"], C).max() <= 1e-12
-    with pytest.raises(RuntimeError):
-        m.set_params(t.p, t.q, t.w)
-    n = 5
-    z = d(np.zeros((n, 6)))
-    with pytest.raises(RuntimeError):
-        m.grad(d(lam), d(Q), z, z, d(np.zeros((6, n))), d(np.zeros((6, n))), z)
+    m.set_params(t.p + 0.1, t.q, 2.0 * t.w)          # same zero pattern: accepted
+    w2 = t.w.copy()
+    w2[0] = 0.5
+    with pytest.raises(RuntimeError):                # another compressed tree: a new handle is needed
+        m.set_params(t.p, t.q, w2)
+    # one leaf left: the stress does not depend on p, q or w
+    st0 = torch.zeros((6, 5), dtype=torch.float64, device=DEV)
+    En, dE = W.proportional_increment(Ef, 3, 3)
+    o = m.update(d(lam), d(Q), d(En), d(dE), st0)
+    g_p, g_q, g_w, g_E = m.grad(d(lam), d(Q), d(En), d(dE), st0, o["state_out"], d(np.ones((5, 6))))
+    assert float(g_p.abs().max()) == 0.0 and float(g_q.abs().max()) == 0.0 and float(g_w.abs().max()) == 0.0
     m.close()

@@ -69,6 +69,39 @@ def test_adjoint_matches_oracle_ift_gradient(K, steps):
     np.testing.assert_allclose(g_E.cpu().numpy(), np.einsum("nji,nj->ni", C, g), rtol=1e-10, atol=1e-10)
 
 
+def test_adjoint_of_a_compressed_tree_matches_oracle_ift_gradient():
+    """Leaf weights of zero: the adjoint walks the compressed tree; laminates that are
+    passed through and weightless leaves get no gradient."""
+    n, K, steps = 3, 5, 6
+    tree = W.tree_with_zero_weights(K, seed=70)
+    A2, lam, Q = W.orientation_field(n, seed=71)
+    Ef = W.random6_path_final(n, 0.03, seed=72)
+    m = dmn.DMN(tree)
+    S = oracle.state_size(K, tree.phases, tree.w)
+    assert m.state_size == S
+    st = torch.zeros((S, n), dtype=torch.float64, device=DEV)
+    so = np.zeros((S, n))
+    for s in range(1, steps + 1):
+        En, dE = W.proportional_increment(Ef, s, 10)
+        prev, so_prev = st, so
+        st = m.update(d(lam), d(Q), d(En), d(dE), st)["state_out"]
+        so = oracle.update(tree, lam, Q, En, dE, so)[0]
+    g = np.random.default_rng(73).standard_normal((n, 6))
+    g_p, g_q, g_w, _ = m.grad(d(lam), d(Q), d(En), d(dE), prev, st, d(g))
+    tot = dict(p=0.0, q=0.0, w=0.0)
+    for i in range(n):
+        gi = oracle.gradient_ift(tree, lam[i], Q[i], (En + dE)[i], oracle.jumps(tree, so, i),
+                                 oracle.leaf_states(tree, so_prev, i), g[i])
+        for k in tot:
+            tot[k] = tot[k] + gi[k]
+    for k, gg in (("p", g_p), ("q", g_q), ("w", g_w)):
+        ref = tot[k]
+        err = np.abs(gg.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err < 1e-6, (k, err)
+    assert (g_w.cpu().numpy()[tree.w == 0] == 0).all()
+    m.close()
+
+
 def test_adjoint_matches_finite_differences_of_the_solve():
     K, n = 6, 16
     tree = W.tree_d10_fit(K, seed=70)

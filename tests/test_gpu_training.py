@@ -29,6 +29,7 @@ def test_stiffness_loss_matches_its_definition():
 
 @pytest.mark.parametrize("n_plastic", [0, 64])
 def test_training_lowers_the_loss(n_plastic):
+    """80 epochs lower the loss; weights that reach zero compress the tree (Sec. 3.1)."""
     K = 4
     target = W.tree_d10_fit(K, seed=2)
     tr = T.Trainer(K, target, 128, seed=3, elastic_matrix=EL_MATRIX, plastic=W.MATRIX, n_plastic=n_plastic)
@@ -37,6 +38,8 @@ def test_training_lowers_the_loss(n_plastic):
     last = tr.history[-1]
     assert last[0] < 0.75 * first[0], (first, last)
     assert last[2] < 0.9 * first[2], (first, last)
+    # weights driven to zero compress the tree: the handles follow the set of zero weights
+    assert (tr.weights() > 0).sum().item() == int(tr.pattern.sum())
     # the trained (and compressed) tree runs online
     t = tr.compress()
     m = dmn.DMN(t)
