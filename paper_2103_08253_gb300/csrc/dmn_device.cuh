@@ -155,27 +155,32 @@ __device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], 
   const double ins = rsqrt(fmax(n2, 1e-300));
   const double ns = n2 * ins;
   const bool explin = ph.kind == 2;
-  const double sy = ph.s0 + ph.H * z[0] + (explin ? ph.ds * (1.0 - exp(-ph.rate * z[0])) : 0.0);
+  const double e_n = explin ? exp(-ph.rate * z[0]) : 1.0;
+  const double sy = ph.s0 + ph.H * z[0] + (explin ? ph.ds * (1.0 - e_n) : 0.0);
   const double f = ns - SQ23 * sy;
   const bool plastic = f > 0.0;
   if (gap) *gap = fabs(f) / sy;
   double dg = plastic ? f * ph.inv_den : 0.0;
   double thb0 = ph.thb0;
   if (explin && plastic) {
-    // scalar Newton on r(dg) = |s_tr| - 2G dg - sqrt(2/3) sigma_Y(a_n + sqrt(2/3) dg), from dg = 0;
-    // r is convex and decreasing, so the iterates rise monotonically to the root
-    dg = 0.0;
-    double slope = ph.H;
+    // scalar Newton on r(dg) = |s_tr| - 2G dg - sqrt(2/3) sigma_Y(a_n + sqrt(2/3) dg).  r is convex and
+    // decreasing, so from dg = 0 the iterates rise monotonically to the root; the first iterate,
+    // f / (2G + 2/3 sigma_Y'(a_n)), needs no new exponential.  Convergence is quadratic, so once a
+    // step is below 1e-10 dg the next would be below the rounding of dg: stop there.
+    double slope = ph.H + ph.dk * e_n, e = e_n, step = 0.0;
+    dg = f / (twoG + (2.0 / 3.0) * slope);
     for (int it = 0; it < 40; ++it) {
       const double a = z[0] + SQ23 * dg;
-      const double e = exp(-ph.rate * a);
+      e = exp(-ph.rate * a);
       slope = ph.H + ph.dk * e;
       const double r = ns - twoG * dg - SQ23 * (ph.s0 + ph.H * a + ph.ds * (1.0 - e));
-      const double step = r / (twoG + (2.0 / 3.0) * slope);
+      step = r / (twoG + (2.0 / 3.0) * slope);
       dg += step;
-      if (fabs(step) <= 1e-15 * dg) break;
+      if (fabs(step) <= 1e-10 * dg) break;
     }
-    slope = ph.H + ph.dk * exp(-ph.rate * (z[0] + SQ23 * dg));   // hardening slope at the new a
+    // hardening slope at the new a: the last one was taken one step earlier; its first-order
+    // correction -rate dk e sqrt(2/3) step leaves an error of order (rate step)^2
+    slope -= ph.rate * ph.dk * e * SQ23 * step;
     thb0 = 1.0 / (1.0 + slope / (3.0 * ph.G));
   }
   const double k2 = twoG * dg * ins;        // 2G dg / |s_tr| = 1 - th
