@@ -1,6 +1,10 @@
 #!/usr/bin/env python
 """DMN Gauss-point updates/s at depth 8 on one GB300, FP64 and mixed forms.
 
+The JSON line's value is the FP64 form; "forms" adds the mixed form (FP32
+condensation, FP64 residual and final sweep) and the mixed form with an FP32
+tangent (no final sweep), each with its error against the oracle.
+
 Workload (one "step" = one increment of the load path over the whole batch:
 orientation set-up + material-point update, all through the C ABI):
   * K = 8 DMN (256 leaves, 255 laminates), linear angle interpolation fitted to
@@ -140,11 +144,11 @@ def newton_flops(K, iters_sum, npts, mixed, w=None):
     return (F64, FT) if mixed else (F64 + FT, 0.0)
 
 
-def final_flops(K, npts, mixed, w=None):
+def final_flops(K, npts, sweep, w=None):
     """FP64 flops of the final kernel (state pass and rotation; mixed form: plus one FP64 pass)."""
     c = tree_counts(np.ones(1 << K) if w is None else w)
     f = npts * (F_ROTATE + c["N"] * F_STATE_NODE + c["j2"] * F_STATE_J2)
-    if mixed:
+    if sweep:
         f64, ft = pass_flops(K, w)
         f += npts * (f64 + ft)
     return f
@@ -444,13 +448,15 @@ def roofline_f64(r, n, steps, w=None):
             "peak_note": "derived: 152 SM x 4 SMSP x 0.5 DFMA/clk x 2 flop x 2.07 GHz"}
 
 
-def roofline_mixed(r, n, steps, w=None):
+def roofline_mixed(r, n, steps, w=None, sweep=True):
+    """Mixed forms: the Newton kernel against F64/P64 + F32/P32; the final kernel (with the FP64 sweep,
+    or only the state pass and rotation in the form with an FP32 tangent) against the FP64 peak."""
     F64, F32 = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=True, w=w)
     t = r["kms"]["newton"] * 1e-3
     tb = F64 / (PEAK_F64_GFLOPS * 1e9) + F32 / (PEAK_F32_GFLOPS * 1e9)
-    Ff = final_flops(K_DEPTH, n * steps, mixed=True, w=w)
+    Ff = final_flops(K_DEPTH, n * steps, sweep=sweep, w=w)
     tf = r["kms"]["final"] * 1e-3
-    fin = {"kernel": "k_final<sweep>", "achieved": Ff / tf / 1e9, "peak": PEAK_F64_GFLOPS, "unit": "GFLOP/s (FP64)",
+    fin = {"kernel": "k_final<sweep>" if sweep else "k_final", "achieved": Ff / tf / 1e9, "peak": PEAK_F64_GFLOPS, "unit": "GFLOP/s (FP64)",
            "frac": Ff / tf / 1e9 / PEAK_F64_GFLOPS, "launch_ms": r["kms"]["final"] / steps}
     return {"bound": "alu", "kernel": "k_newton<float>", "achieved": tb / t * PEAK_F64_GFLOPS,
             "peak": PEAK_F64_GFLOPS, "unit": "GFLOP/s (FP64-equivalent: F64/P64 + F32/P32)", "frac": tb / t,
@@ -692,7 +698,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--points", type=int, default=1 << 20)
-    ap.add_argument("--forms", default="f64,mixed")
+    ap.add_argument("--forms", default="f64,mixed,mixed-f32-tangent")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="points per chunk of dmn_update_host (0: the library's default)")
     ap.add_argument("--e2e-steps", type=int, default=-1,
@@ -777,7 +783,7 @@ def run_gpu(args):
                            "kernel_ms_per_step": {k: x / steps for k, x in r["kms"].items()},
                            "newton_iters_per_update": r["iters_sum"] / (n * steps), "iters_hist": r["iters_hist"],
                            "roofline": (roofline_f64(r, n, steps, tree.w) if form == "f64"
-                                        else roofline_mixed(r, n, steps, tree.w)),
+                                        else roofline_mixed(r, n, steps, tree.w, sweep=form == "mixed")),
                            "launch": r["launch"],
                            "parity_vs_oracle": r.get("parity"), "clocks": r["clocks"]}
     main_form = "f64" if "f64" in results else forms[0]

@@ -67,8 +67,14 @@ enum { DMN_PHASE_ELASTIC = 0, DMN_PHASE_J2_LINEAR = 1, DMN_PHASE_J2_EXPLIN = 2 }
 /* DMN_PREC_F64: every step in FP64.
  * DMN_PREC_MIXED: leaf tangents, laminate condensation and jump corrections
  * in FP32; leaf stresses, strains, jumps, the Newton residual and the final
- * sweep that yields stress and tangent in FP64. */
-enum { DMN_PREC_F64 = 0, DMN_PREC_MIXED = 1 };
+ * sweep that yields stress and tangent in FP64.
+ * DMN_PREC_MIXED_F32_TANGENT: the Newton iteration of DMN_PREC_MIXED (same
+ * jumps, state and FP64 stress), without the FP64 final sweep: the tangent is
+ * the FP32 condensation of the last Newton pass, which ran at the converged
+ * jumps (relative error a few 1e-7 at depth 8).  For callers whose solver rounds the
+ * tangent to FP32 anyway, or that only need a Newton matrix (Sec. 3.2's
+ * algorithmic tangent drives the macroscopic Newton method, Sec. 4.6). */
+enum { DMN_PREC_F64 = 0, DMN_PREC_MIXED = 1, DMN_PREC_MIXED_F32_TANGENT = 2 };
 
 /* per-point status */
 enum {
@@ -103,10 +109,10 @@ typedef struct {
 typedef struct {
   double tol;          /* ||A^T W sigma|| / ((2^K - 1) ||sigma_bar||) <= tol (Sec. 4.6); <= 0 selects 1e-12 */
   int32_t max_iter;    /* Newton corrections before status MAXITER; <= 0 selects 50 */
-  int32_t precision;   /* DMN_PREC_F64 or DMN_PREC_MIXED */
+  int32_t precision;   /* DMN_PREC_F64, DMN_PREC_MIXED or DMN_PREC_MIXED_F32_TANGENT */
   int32_t block;       /* threads per CTA of the Newton kernel (multiple of 32); 0 selects 128 */
   int32_t ctas_per_sm; /* resident CTAs per SM of the persistent Newton kernel; 0 selects 384 threads
-                        * per SM for DMN_PREC_F64 and 512 for DMN_PREC_MIXED;
+                        * per SM for DMN_PREC_F64 and 512 for the mixed forms;
                         * block * ctas_per_sm <= 512 (registers are capped to fit) */
   int32_t line_search; /* 0: full Newton steps; 1: backtracking (Sec. 3.2 allows a step in (0, 1]):
                         * a trial step is accepted when it lowers ||A^T W sigma||, else halved, at

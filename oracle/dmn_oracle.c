@@ -24,7 +24,8 @@
  *   - convergence criterion ||A^T W sigma|| / ((2^K - 1) ||sigma_bar||) <= tol
  *     and a Cholesky solve: Sec. 4.6;
  *   - matrix law: J2 plasticity with isotropic hardening (Sec. 4.1, radial
- *     return of Simo-Hughes ch. 3), here with linear hardening.
+ *     return of Simo-Hughes ch. 3), with linear or exponential-linear
+ *     hardening.
  *
  * Conventions: Mandel 6-vectors (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12);
  * the state of a point is stored field-major ("SoA"): field f of point i is

@@ -12,7 +12,8 @@
 //   k_final    one thread per point: the return mapping at the converged jumps
 //              writes z^{n+1}, and stress and tangent are rotated back to the
 //              global frame; in the mixed form this kernel first runs the FP64
-//              sweep that yields them.
+//              sweep that yields them (the form with an FP32 tangent skips it
+//              and rotates what the last Newton pass condensed).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -408,7 +409,7 @@ struct NewtonParams {
   unsigned long long* counter;
   double tol;
   int max_iter;
-  int write_outputs;  // FP64 form: stress and tangent (local frame) come from the converged Newton pass
+  int write_outputs;  // no final sweep: stress and tangent (local frame) come from the converged Newton pass
 };
 
 // MINB: resident CTAs per SM the register allocation is sized for (255, 170 or
@@ -540,8 +541,8 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
         continue;
       }
     }
-    // finished point: jumps (paper ordering), counters, and in the FP64 form the
-    // local-frame stress and packed tangent for k_final to rotate
+    // finished point: jumps (paper ordering), counters, and without a final sweep
+    // the local-frame stress and packed tangent for k_final to rotate
     const double* afin = abuf[cur];
     const int nzf = 6 * t.nz;
     for (int f = 0; f < 3 * t.N; ++f) {
@@ -970,7 +971,8 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, cons
   k_prepare<<<g1, 128, 0, s>>>(F, n, tree_id, perm, lam, Q, E_n, dE, w.nbuf, NM);
   if (ev) cudaEventRecord(ev[1], s);
   const unsigned grid = (unsigned)(h->n_sm * h->opt.ctas_per_sm);
-  const bool mixed = h->opt.precision == DMN_PREC_MIXED;
+  const bool mixed = h->opt.precision != DMN_PREC_F64;
+  const bool sweep = h->opt.precision == DMN_PREC_MIXED;   // FP64 final sweep for stress and tangent
   const int threads_per_sm = h->opt.block * h->opt.ctas_per_sm;
   const int minb = threads_per_sm > 384 ? 4 : threads_per_sm > 256 ? 3 : 2;
   const bool ls = h->opt.line_search != 0;
@@ -982,13 +984,13 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, cons
     else launch_newton<double, false>(P, ls, minb, grid, block, s);
   } else {
     NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
-                          w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 0};
+                          w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, sweep ? 0 : 1};
     if (h->cmp) launch_newton<float, true>(P, ls, minb, grid, block, s);
     else launch_newton<float, false>(P, ls, minb, grid, block, s);
   }
   if (ev) cudaEventRecord(ev[2], s);
   FinalParams FP{F, n, NM, tree_id, perm, Q, state_in, state_out, stress, tangent, status, w.nbuf};
-  if (mixed) {
+  if (sweep) {
     if (h->cmp) k_final<true, true><<<g1, 128, 0, s>>>(FP);
     else k_final<true, false><<<g1, 128, 0, s>>>(FP);
   } else {
@@ -1123,13 +1125,13 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
   if (o.line_search != 0 && o.line_search != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: line_search must be 0 or 1");
   // the line-search kernel keeps two buffers per lane and is built for 256 threads per SM
   if (o.line_search && o.ctas_per_sm <= 0) o.ctas_per_sm = 256 / o.block;
-  if (o.precision != DMN_PREC_F64 && o.precision != DMN_PREC_MIXED)
+  if (o.precision != DMN_PREC_F64 && o.precision != DMN_PREC_MIXED && o.precision != DMN_PREC_MIXED_F32_TANGENT)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: unknown precision");
   if (o.block % 32 != 0 || o.block > 128)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: block must be a multiple of 32 and at most 128");
   // default occupancy: the FP64 form is bound by the FP64 pipe from 256 threads per SM on;
   // the FP32 form hides latency with 512
-  if (o.ctas_per_sm <= 0) o.ctas_per_sm = (o.precision == DMN_PREC_MIXED ? 512 : 384) / o.block;
+  if (o.ctas_per_sm <= 0) o.ctas_per_sm = (o.precision != DMN_PREC_F64 ? 512 : 384) / o.block;
   if (o.block * o.ctas_per_sm > (o.line_search ? 256 : 512))
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: block * ctas_per_sm must be at most 512 threads per SM "
                                       "(256 with the line search)");

@@ -23,7 +23,8 @@ EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_interp_orientatio
 PHASE_ELASTIC, PHASE_J2_LINEAR, PHASE_J2_EXPLIN = 0, 1, 2
 PREC_F64 = 0
 PREC_MIXED = 1
-PRECISIONS = {"f64": PREC_F64, "mixed": PREC_MIXED}
+PREC_MIXED_F32_TANGENT = 2
+PRECISIONS = {"f64": PREC_F64, "mixed": PREC_MIXED, "mixed-f32-tangent": PREC_MIXED_F32_TANGENT}
 STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE, STATUS_LINESEARCH, STATUS_BAD_TREE = 0, 1, 2, 3, 4
 MAX_TREES = 8
 

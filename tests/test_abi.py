@@ -76,6 +76,20 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(case, msg):
     assert msg in lib.dmn_last_error(None).decode()
 
 
+@pytest.mark.parametrize("opt,msg", [((1e-12, 50, 3, 0, 0, 0), "unknown precision"),
+                                     ((1e-12, 50, -1, 0, 0, 0), "unknown precision"),
+                                     ((1e-12, 50, dmn.PREC_MIXED_F32_TANGENT, 48, 0, 0), "multiple of 32"),
+                                     ((1e-12, 50, dmn.PREC_F64, 128, 3, 1), "256 with the line search")])
+def test_create_rejects_bad_options_without_touching_the_gpu(opt, msg):
+    lib = dmn.load_library()
+    d, keep = _desc()
+    o = dmn.Options_(*opt)
+    h = ctypes.c_void_p(123)
+    assert lib.dmn_create(ctypes.byref(d), 1, ctypes.byref(o), ctypes.byref(h)) == -1
+    assert h.value is None and msg in lib.dmn_last_error(None).decode()
+    assert set(dmn.PRECISIONS.values()) == {dmn.PREC_F64, dmn.PREC_MIXED, dmn.PREC_MIXED_F32_TANGENT}
+
+
 def test_calls_on_null_handle_are_argument_errors():
     lib = dmn.load_library()
     assert lib.dmn_update(None, 4, None, *([None] * 10), None) == -1

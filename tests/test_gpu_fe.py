@@ -86,7 +86,8 @@ def test_pcg_matches_a_direct_solve():
     g.close()
 
 
-@pytest.mark.parametrize("prec,tol,cg32", [("f64", 1e-8, False), ("mixed", 1e-6, False), ("f64", 1e-6, True)])
+@pytest.mark.parametrize("prec,tol,cg32", [("f64", 1e-8, False), ("mixed", 1e-6, False), ("f64", 1e-6, True),
+                                          ("mixed-f32-tangent", 1e-6, True)])
 def test_fe_dmn_plate_matches_the_oracle(prec, tol, cg32):
     m = W.plate_with_hole_mesh(4, 2, 1, R=2.0, H=6.0, T=2.0)
     A2 = W.plate_orientation_field(m.centroid, m.R, m.H, m.T, seed=11)
