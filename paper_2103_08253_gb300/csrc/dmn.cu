@@ -144,6 +144,8 @@ const char* make_phase(const dmn_phase& p, PhaseDev& out) {
   out.s0 = p.sigma0;
   out.H = p.H;
   out.lam = out.K - 2.0 * out.G / 3.0;
+  out.lamf = (float)out.lam;
+  out.Gf = (float)out.G;
   out.inv_den = 1.0 / (2.0 * out.G + 2.0 * p.H / 3.0);
   out.thb0 = 1.0 / (1.0 + p.H / (3.0 * out.G));
   return nullptr;
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
               abuf[0][(size_t)f * ns] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
               const double nv = P.nbuf[(size_t)f * P.n + pt];
               my_nrm[(size_t)f * ns] = nv;
-              if (sizeof(T) == 4) my_nrmf[(size_t)f * ns] = (float)nv;
+              if (sizeof(T) == 4) my_nrmf[(size_t)f * ns] = narrow_rn(nv);
             }
             A.z = P.state_in + pt;
             it = 0;
@@ -557,7 +559,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
 #pragma unroll
       for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = root.sb[I];
 #pragma unroll
-      for (int k = 0; k < 21; ++k) P.tangent[36 * pt + k] = (double)root.C[k];
+      for (int k = 0; k < 21; ++k) P.tangent[36 * pt + k] = widen(root.C[k]);
     }
     pt = -1;
   }

@@ -15,6 +15,7 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #ifndef DMN_HOST_EMULATION
 #include <cuda_runtime.h>
 #endif
@@ -36,6 +37,7 @@ struct PhaseDev {
   double K, G;       // bulk and shear modulus
   double s0, H;      // yield stress and (linear part of the) hardening modulus
   double lam;        // K - 2G/3: sigma = lam tr(eps) 1 + 2G eps when elastic
+  float lamf, Gf;    // FP32 copies of lam and G (elastic leaf tangents of the FP32 form)
   double inv_den;    // 1 / (2G + 2H/3): plastic multiplier per unit overstress (kind 1)
   double thb0;       // 1 / (1 + H / (3G)) (kind 1)
   double ds, dk, rate;  // kind 2: sigma_inf - s0, k0 - H, (k0 - H) / (sigma_inf - s0)
@@ -93,6 +95,94 @@ __device__ __forceinline__ NodeC<float> node_c<float>(const TreeDev& t, int node
   return {__ldg(t.c1f + node), __ldg(t.c2f + node), __ldg(t.c12f + node)};
 }
 
+// ---------------------------------------------------------------------------
+// Conversions between FP64 and the working precision T.  For T = float they
+// work on the IEEE 754 binary64 / binary32 bit patterns with integer
+// instructions: GB300 executes a hardware FP64 <-> FP32 conversion on its FP64
+// pipe, at 1/64 of the rate of the FP32 and integer pipes, and the FP32 form
+// converts some 3000 values per tree pass.
+//   narrow_rn: round to nearest, ties to even; results below the smallest
+//              normal FP32 number (2^-126) become a signed zero; overflow
+//              gives infinity, NaN stays NaN.
+//   widen:     exact; FP32 subnormals become a signed zero.
+// (host and device: the host build lets a CPU test compare them with the host's IEEE conversions)
+__host__ __device__ __forceinline__ unsigned long long bits_of(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long u;
+  memcpy(&u, &x, sizeof u);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ double double_of(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  memcpy(&x, &u, sizeof x);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned bits_of(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  unsigned u;
+  memcpy(&u, &x, sizeof u);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ float float_of(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float x;
+  memcpy(&x, &u, sizeof x);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ float narrow_rn(double x) {
+  const unsigned long long b = bits_of(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned e = (hi >> 20) & 0x7ffu;                      // biased exponent (bias 1023)
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);   // the 23 leading fraction bits
+  const unsigned rest = lo & 0x1fffffffu;                      // the 29 fraction bits rounded away
+  unsigned r = ((e - 896u) << 23) + mant;                      // bias 127; a rounding carry may reach the exponent
+  r += (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+  if (e <= 896u) r = 0u;
+  if (e >= 1151u) r = (e == 2047u && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+  return float_of(sign | r);
+}
+__host__ __device__ __forceinline__ double widen(float x) {
+  const unsigned u = bits_of(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20));
+  unsigned lo = u << 29;
+  if (e == 0u) {
+    hi = u & 0x80000000u;
+    lo = 0u;
+  } else if (e == 255u) {
+    hi = (u & 0x80000000u) | 0x7ff00000u | ((u & 0x7fffffu) >> 3);
+  }
+  return double_of((unsigned long long)hi << 32 | lo);
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+template <typename T>
+__device__ __forceinline__ T narrow(double x);
+template <>
+__device__ __forceinline__ double narrow<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float narrow<float>(double x) { return narrow_rn(x); }
+// a constant held in both precisions
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f);
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
 // packed symmetric 6x6: upper triangle row by row
 __host__ __device__ constexpr int sidx(int i, int j) {
   return i <= j ? i * 6 - (i * (i - 1)) / 2 + (j - i) : j * 6 - (j * (j - 1)) / 2 + (i - j);
@@ -138,7 +228,7 @@ __device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], 
     for (int I = 0; I < 6; ++I) sig[I] = twoG * e[I];
     sig[0] += lt; sig[1] += lt; sig[2] += lt;
     if (D) {
-      D->lam = (T)ph.lam; D->mu = (T)ph.G; D->c = (T)0;
+      D->lam = pick<T>(ph.lam, ph.lamf); D->mu = pick<T>(ph.G, ph.Gf); D->c = (T)0;
 #pragma unroll
       for (int I = 0; I < 6; ++I) D->m[I] = (T)0;
     }
@@ -190,11 +280,17 @@ __device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], 
   sig[0] += Kt; sig[1] += Kt; sig[2] += Kt;
   if (D) {
     const double mu = ph.G * (1.0 - k2);
-    D->mu = (T)mu;
-    D->lam = (T)(ph.K - (2.0 / 3.0) * mu);
-    D->c = (T)(plastic ? twoG * (thb0 - k2) : 0.0);
+    D->mu = narrow<T>(mu);
+    D->lam = narrow<T>(ph.K - (2.0 / 3.0) * mu);
+    D->c = narrow<T>(plastic ? twoG * (thb0 - k2) : 0.0);
+    if (sizeof(T) == 8) {
 #pragma unroll
-    for (int I = 0; I < 6; ++I) D->m[I] = (T)(st[I] * ins);
+      for (int I = 0; I < 6; ++I) D->m[I] = narrow<T>(st[I] * ins);
+    } else {   // the FP32 tangent's flow direction, normalised in FP32
+      const T it = narrow<T>(ins);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) D->m[I] = narrow<T>(st[I]) * it;
+    }
   }
   if (znew) {
     const double di = dg * ins;
@@ -297,7 +393,7 @@ __device__ __forceinline__ void condense(const double nd[3], const T n[3], doubl
   {
     double t[3];
     residual_share(nd, c1d, c2d, sc, L.sb, R.sb, out.sb, t, r2);
-    u[0] = (T)t[0]; u[1] = (T)t[1]; u[2] = (T)t[2];
+    u[0] = narrow<T>(t[0]); u[1] = narrow<T>(t[1]); u[2] = narrow<T>(t[2]);
   }
   const T c1 = cc.c1, c2 = cc.c2, c12 = cc.c12;
   const T nr[3] = {n[0] * (T)RS2, n[1] * (T)RS2, n[2] * (T)RS2};
@@ -369,7 +465,7 @@ __device__ __forceinline__ void condense_bottom(const double nd[3], const T n[3]
   {
     double t[3];
     residual_share(nd, c1d, c2d, sc, sL, sR, out.sb, t, r2);
-    u[0] = (T)t[0]; u[1] = (T)t[1]; u[2] = (T)t[2];
+    u[0] = narrow<T>(t[0]); u[1] = narrow<T>(t[1]); u[2] = narrow<T>(t[2]);
   }
   const T c1 = cc.c1, c2 = cc.c2, c12 = cc.c12;
   const T nr[3] = {n[0] * (T)RS2, n[1] * (T)RS2, n[2] * (T)RS2};
@@ -539,7 +635,7 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
         }
         double* aw = P.a_out + aoff;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) { a[c] += (double)da[c]; aw[c * P.as] = a[c]; }
+        for (int c = 0; c < 3; ++c) { a[c] += widen(da[c]); aw[c * P.as] = a[c]; }
       }
       const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
       double Na[6];
@@ -674,7 +770,7 @@ __device__ void tree_pass_c(const TreeDev& t, const double Eloc[6], const PointA
         }
         double* aw = P.a_out + (size_t)(3 * node) * P.as;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) { a[c] += (double)da[c]; aw[c * P.as] = a[c]; }
+        for (int c = 0; c < 3; ++c) { a[c] += widen(da[c]); aw[c * P.as] = a[c]; }
       }
       const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
       double Na[6];
