@@ -46,6 +46,8 @@ N_INCREMENTS = 50
 EPS_EQ = 0.03
 SEED_TREE, SEED_ORI, SEED_PATH = 2103, 8253, 1208
 WORKLOAD = "K=8 D10-interpolated DMN, 2^20 points/GPU, random 6-comp paths, 50 increments to 3% eq. strain"
+SHAPE_NOTE = {3: "linear (M = 3), coefficients fitted at the D10 points", 4: "tri-linear (M = 4), seeded nodal angles",
+              6: "quadratic (M = 6), seeded nodal angles"}
 MATRIX_NOTE = {"linear": "J2, linear hardening 40 + 300 a MPa (E 3 GPa, nu 0.35)",
                "explin": "J2, exponential-linear hardening of the paper's polyamide (E 2.1 GPa, nu 0.3, s0 29, "
                          "s_inf 61.7 MPa, k0 10.6 GPa, k_inf 139 MPa); flop counts exclude its scalar Newton"}
@@ -232,10 +234,14 @@ def job_value(world, n, steps, t_ms):
     return world * n * steps / (t_ms * 1e-3)
 
 
-def make_workload(n, rank, compressed=False, matrix="linear"):
+def make_workload(n, rank, compressed=False, matrix="linear", shape=3):
     phases = (W.FIBER, W.MATRIX_EXPLIN if matrix == "explin" else W.MATRIX)
-    tree = (W.tree_with_zero_weights(K_DEPTH, seed=SEED_TREE, phases=phases) if compressed
-            else W.tree_d10_fit(K_DEPTH, seed=SEED_TREE, phases=phases))
+    if compressed:
+        tree = W.tree_with_zero_weights(K_DEPTH, seed=SEED_TREE, phases=phases)
+    elif shape != 3:
+        tree = W.tree_nodal_angles(K_DEPTH, shape, seed=SEED_TREE, phases=phases)
+    else:
+        tree = W.tree_d10_fit(K_DEPTH, seed=SEED_TREE, phases=phases)
     A2, lam, Q = W.orientation_field(n, seed=SEED_ORI + 1000 * rank)
     Ef = W.random6_path_final(n, EPS_EQ, seed=SEED_PATH + 1000 * rank)
     return tree, A2, lam, Q, Ef
@@ -263,7 +269,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    tree, A2, lam, Q, Ef = make_workload(args.points, 0, args.workload == "k8-compressed", args.matrix)
+    tree, A2, lam, Q, Ef = make_workload(args.points, 0, args.workload == "k8-compressed", args.matrix, args.shape)
     cores = os.cpu_count() or 1
     m = args.ref_points
     idx = np.arange(m)
@@ -708,6 +714,9 @@ def main():
     ap.add_argument("--parity-points", type=int, default=16)
     ap.add_argument("--matrix", default="linear", choices=["linear", "explin"],
                     help="matrix law of the k8 workloads: linear hardening (default) or the paper's exp-linear")
+    ap.add_argument("--shape", type=int, default=3, choices=[3, 4, 6],
+                    help="shape functions of the angle interpolation: 3 linear (default, D10 fit), 4 tri-linear, "
+                         "6 quadratic (seeded nodal angles)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the library's default launch shape instead of autotuning it")
     ap.add_argument("--workload", default="k8", choices=["k8", "k8-compressed", "mixed-depth", "plate", "train"],
@@ -747,7 +756,7 @@ def run_gpu(args):
     dmn.load_library()
     n = args.points
     cmp = args.workload == "k8-compressed"
-    tree, A2, lam_np, Q_np, Ef = make_workload(n, rank, cmp, args.matrix)
+    tree, A2, lam_np, Q_np, Ef = make_workload(n, rank, cmp, args.matrix, args.shape)
     try:
         smi_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
@@ -802,6 +811,7 @@ def run_gpu(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_CMP if cmp else WORKLOAD, "K": K_DEPTH, "points_per_gpu": n,
                        "increments": N_INCREMENTS, "matrix": MATRIX_NOTE[args.matrix],
+                       "shape_functions": SHAPE_NOTE[args.shape],
                        "timed_increments": [args.warmup + 1, args.warmup + steps],
                        "l2": "no flush: per-step inputs (state %.1f GB) exceed L2"
                              % ((6 * tree_counts(tree.w)["j2"] + 3 * tree_counts(tree.w)["N"]) * n * 8e-9),

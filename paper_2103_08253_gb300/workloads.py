@@ -133,6 +133,22 @@ def tree_d10_fit(K: int, seed: int, spread: float = 0.35, phases=(FIBER, MATRIX)
     return TreeParams(K=K, M=3, p=p, q=q, w=w, phases=tuple(phases))
 
 
+def tree_nodal_angles(K: int, M: int, seed: int, spread: float = 0.35, phases=(FIBER, MATRIX)) -> TreeParams:
+    """Angle coefficients for the tri-linear (M = 4) or quadratic (M = 6) shape
+    functions: per laminate a base direction uniform on the sphere, and at each
+    of the M interpolation nodes its angles perturbed by N(0, spread^2).  The
+    shape functions sum to one, so the coefficients are the nodal angles and the
+    normals vary over the triangle about the base direction as in tree_d10_fit.
+    Leaf weights are Dirichlet(1, ..., 1)."""
+    rng = np.random.default_rng(seed)
+    N = n_nodes(K)
+    alpha0, beta0 = _uniform_sphere_angles(rng, N)
+    p = alpha0[:, None] + spread * rng.standard_normal((N, M))
+    q = beta0[:, None] + spread * rng.standard_normal((N, M))
+    w = rng.dirichlet(np.ones(n_leaves(K)))
+    return TreeParams(K=K, M=M, p=p, q=q, w=w, phases=tuple(phases))
+
+
 def haar_rotations(rng, n: int) -> np.ndarray:
     """n Haar-distributed rotation matrices [n, 3, 3] (QR of Gaussian matrices
     with the sign of R's diagonal fixed, then det forced to +1)."""

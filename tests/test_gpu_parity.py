@@ -145,6 +145,19 @@ def test_higher_order_shape_functions(M):
     assert worst["stress"] <= 1e-10 and worst["tangent"] <= 1e-10
 
 
+@pytest.mark.parametrize("M", [4, 6])
+def test_higher_order_shape_functions_depth8(M):
+    """The timed shape-function variants of the bench: K = 8 with seeded nodal
+    angles for the tri-linear and quadratic shape functions, 40 points, both
+    forms, the first 4 of 50 increments to 3 % equivalent strain."""
+    tree = W.tree_nodal_angles(8, M, seed=120 + M)
+    A2, lam, Q = W.orientation_field(40, seed=121 + M)
+    Ef = W.random6_path_final(40, 0.03, seed=122 + M)
+    for prec in ("f64", "mixed"):
+        worst, _, _ = run_path(tree, lam, Q, Ef, 50, prec, upto=4)
+        assert worst["stress"] <= TOL[prec] and worst["tangent"] <= TOL_TANGENT[prec], (prec, worst)
+
+
 @pytest.mark.parametrize("phases", [(W.MATRIX, W.MATRIX), (W.FIBER, W.Phase(0, 3000.0, 0.35)),
                                     (W.Phase(1, 3000.0, 0.35, 40.0, 300.0), W.FIBER)])
 def test_phase_combinations(phases):
