@@ -123,7 +123,10 @@ class DMN:
 
     tree: an object with K, M, p [N, M], q [N, M], w [2^K] (numpy, paper
     ordering) and phases (two objects with kind, E, nu, sigma0, H), or a list
-    of such objects (tree i is selected by tree_id == i in update())."""
+    of such objects (tree i is selected by tree_id == i in update()).
+    precision: "f64"; "mixed" (FP32 condensation, FP64 residual and final
+    sweep); "mixed-f32-tangent" (the mixed iteration, tangent from its last
+    FP32 condensation).  The other options are those of dmn_options."""
 
     def __init__(self, tree, precision: str = "f64", tol: float = 1e-12, max_iter: int = 50, block: int = 0,
                  ctas_per_sm: int = 0, line_search: bool = False):
