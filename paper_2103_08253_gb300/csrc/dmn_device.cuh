@@ -209,13 +209,14 @@ struct LeafTan {
 };
 
 // ---------------------------------------------------------------------------
-// Phase law (Sec. 3.2 condensed GSM leaf; Sec. 4.1 J2 radial return, here with
-// linear isotropic hardening).  z = (alpha_bar, ep11, ep22, ep23M, ep13M, ep12M).
-//   s_tr = 2G (dev eps - ep), f = |s_tr| - sqrt(2/3) (s0 + H alpha_bar);
-//   f > 0: dg = f / (2G + 2H/3), n = s_tr / |s_tr|, s = s_tr - 2G dg n,
-//          ep += dg n, alpha_bar += sqrt(2/3) dg,
-//          D = K 1(x)1 + 2G th Idev - 2G thb n(x)n, th = 1 - 2G dg / |s_tr|,
-//          thb = 1/(1 + H/(3G)) - (1 - th).
+// Phase law (Sec. 3.2 condensed GSM leaf; Sec. 4.1 J2 radial return with
+// isotropic hardening sigma_Y).  z = (alpha_bar, ep11, ep22, ep23M, ep13M, ep12M).
+//   xi = dev eps - ep, s_tr = 2G xi, f = |s_tr| - sqrt(2/3) sigma_Y(alpha_bar);
+//   f > 0: dg from |s_tr| - 2G dg = sqrt(2/3) sigma_Y(alpha_bar + sqrt(2/3) dg)
+//          (linear law: dg = f / (2G + 2H/3)), n = xi / |xi|, s = (1 - k2) s_tr
+//          with k2 = 2G dg / |s_tr| = dg / |xi|, ep += dg n, alpha_bar += sqrt(2/3) dg,
+//          D = K 1(x)1 + 2G th Idev - 2G thb n(x)n, th = 1 - k2,
+//          thb = 1/(1 + sigma_Y'/(3G)) - (1 - th).
 // Written without branches: an elastic step is the plastic formula with dg = 0.
 template <typename T>
 __device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], const double z[6], double sig[6],
@@ -237,13 +238,12 @@ __device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], 
   }
   const double m3 = tr * (1.0 / 3.0);
   const double ep2 = -(z[1] + z[2]);
-  double st[6] = {twoG * (e[0] - m3 - z[1]), twoG * (e[1] - m3 - z[2]), twoG * (e[2] - m3 - ep2),
-                  twoG * (e[3] - z[3]),      twoG * (e[4] - z[4]),      twoG * (e[5] - z[5])};
+  const double xi[6] = {e[0] - m3 - z[1], e[1] - m3 - z[2], e[2] - m3 - ep2, e[3] - z[3], e[4] - z[4], e[5] - z[5]};
   double n2 = 0.0;
 #pragma unroll
-  for (int I = 0; I < 6; ++I) n2 += st[I] * st[I];
-  const double ins = rsqrt(fmax(n2, 1e-300));
-  const double ns = n2 * ins;
+  for (int I = 0; I < 6; ++I) n2 += xi[I] * xi[I];
+  const double inx = rsqrt(fmax(n2, 1e-300));   // 1 / |xi|
+  const double ns = twoG * (n2 * inx);          // |s_tr|
   const bool explin = ph.kind == 2;
   const double e_n = explin ? exp(-ph.rate * z[0]) : 1.0;
   const double sy = ph.s0 + ph.H * z[0] + (explin ? ph.ds * (1.0 - e_n) : 0.0);
@@ -273,10 +273,11 @@ __device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], 
     slope -= ph.rate * ph.dk * e * SQ23 * step;
     thb0 = 1.0 / (1.0 + slope / (3.0 * ph.G));
   }
-  const double k2 = twoG * dg * ins;        // 2G dg / |s_tr| = 1 - th
+  const double k2 = dg * inx;          // 2G dg / |s_tr| = 1 - th
   const double Kt = ph.K * tr;
+  const double g2 = twoG - twoG * k2;  // 2G th
 #pragma unroll
-  for (int I = 0; I < 6; ++I) sig[I] = st[I] - k2 * st[I];
+  for (int I = 0; I < 6; ++I) sig[I] = g2 * xi[I];
   sig[0] += Kt; sig[1] += Kt; sig[2] += Kt;
   if (D) {
     const double mu = ph.G * (1.0 - k2);
@@ -285,18 +286,17 @@ __device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], 
     D->c = narrow<T>(plastic ? twoG * (thb0 - k2) : 0.0);
     if (sizeof(T) == 8) {
 #pragma unroll
-      for (int I = 0; I < 6; ++I) D->m[I] = narrow<T>(st[I] * ins);
+      for (int I = 0; I < 6; ++I) D->m[I] = narrow<T>(xi[I] * inx);
     } else {   // the FP32 tangent's flow direction, normalised in FP32
-      const T it = narrow<T>(ins);
+      const T it = narrow<T>(inx);
 #pragma unroll
-      for (int I = 0; I < 6; ++I) D->m[I] = narrow<T>(st[I]) * it;
+      for (int I = 0; I < 6; ++I) D->m[I] = narrow<T>(xi[I]) * it;
     }
   }
   if (znew) {
-    const double di = dg * ins;
-    znew[0] = z[0] + SQ23 * dg;
-    znew[1] = z[1] + di * st[0]; znew[2] = z[2] + di * st[1];
-    znew[3] = z[3] + di * st[3]; znew[4] = z[4] + di * st[4]; znew[5] = z[5] + di * st[5];
+    znew[0] = z[0] + SQ23 * dg;         // ep += dg n = k2 xi
+    znew[1] = z[1] + k2 * xi[0]; znew[2] = z[2] + k2 * xi[1];
+    znew[3] = z[3] + k2 * xi[3]; znew[4] = z[4] + k2 * xi[4]; znew[5] = z[5] + k2 * xi[5];
   }
 }
 
@@ -420,6 +420,11 @@ __device__ __forceinline__ void condense(const double nd[3], const T n[3], doubl
 #pragma unroll
     for (int I = 0; I < 6; ++I) H[m][I] = -(Ki[m][0] * B[I][0] + Ki[m][1] * B[I][1] + Ki[m][2] * B[I][2]);
   T dds[6], v[3], g[3];
+  T B12[6][3];   // c1 c2 B: the condensed outputs then take pure multiply-add chains
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) B12[I][m] = c12 * B[I][m];
 #pragma unroll
   for (int I = 0; I < 6; ++I) dds[I] = R.ds[I] - L.ds[I];
   Nt_apply<T>(n, nr, dds, v);
@@ -429,13 +434,17 @@ __device__ __forceinline__ void condense(const double nd[3], const T n[3], doubl
   for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
 #pragma unroll
   for (int I = 0; I < 6; ++I)
-    out.ds[I] = L.ds[I] + c2 * dds[I] + c12 * (B[I][0] * g[0] + B[I][1] * g[1] + B[I][2] * g[2]);
+    out.ds[I] = L.ds[I] + c2 * dds[I] + B12[I][0] * g[0] + B12[I][1] * g[1] + B12[I][2] * g[2];
 #pragma unroll
   for (int I = 0; I < 6; ++I)
 #pragma unroll
     for (int J = I; J < 6; ++J) {
       const int s = sidx(I, J);
-      out.C[s] = L.C[s] + c2 * dC[s] + c12 * (B[I][0] * H[0][J] + B[I][1] * H[1][J] + B[I][2] * H[2][J]);
+      T v = L.C[s] + c2 * dC[s];
+      v += B12[I][0] * H[0][J];
+      v += B12[I][1] * H[1][J];
+      v += B12[I][2] * H[2][J];
+      out.C[s] = v;
     }
   if (STORE) {
 #pragma unroll
