@@ -1,0 +1,271 @@
+"""Parity at the benchmark's full sizes, in the launch configurations that bench.py times.
+
+At these sizes the oracle cannot recompute every output, so the checks are:
+  * the depth-8 batch (2^20 points) in the FP64, mixed and FP32-tangent forms
+    with the autotuned launch shape: 24 sampled points, among them the last
+    one, recomputed by the oracle from the same seeded inputs through the same
+    increments;
+  * the mixed-depth batch (4M points, depths 5-8, a CUDA graph of increments,
+    the bench's launch-shape choice): 8 sampled points per depth;
+  * the adjoint over the training workload's full plastic batch (4096 points,
+    one increment from the virgin state, line search on) with seeds at 3
+    sampled points: directional derivatives against the oracle's
+    implicit-function gradient;
+  * the FE-coupled plate (1.2M Gauss points): the oracle's FE operator (its own
+    B matrices) applied to the GPU's stresses must give nodal equilibrium at
+    sampled free nodes and the GPU's reaction force on the loaded face, since
+    no oracle solve of the whole plate fits in a test.
+Tolerances are those of the smaller parity tests.
+"""
+import types
+
+import numpy as np
+import pytest
+import torch
+
+import bench
+import oracle
+from oracle import fe_oracle as FE
+from paper_2103_08253_gb300 import dmn, fe, workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+TOL = {"f64": (1e-10, 1e-10), "mixed": (1e-6, 1e-6), "mixed-f32-tangent": (1e-6, 1e-4)}
+
+
+def rel(a, b):
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
+
+
+def release():
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+_K8 = {}
+
+
+def k8_workload():
+    """The depth-8 batch of bench.py (2^20 points) and the oracle at 24 sampled points
+    through increments 1..6 (computed once)."""
+    if not _K8:
+        n = 1 << 20
+        tree, A2, _, _, Ef = bench.make_workload(n, 0)
+        rng = np.random.default_rng(11)
+        pidx = np.sort(np.r_[rng.choice(n - 1, 23, replace=False), n - 1])
+        lam, Q = oracle.interp_orientation(A2[pidx])
+        st = np.zeros((oracle.state_size(tree.K, tree.phases), len(pidx)))
+        for s in range(1, 7):
+            En, dE = W.proportional_increment(Ef[pidx], s, bench.N_INCREMENTS)
+            st, sig, C, it, stat, gap = oracle.update(tree, lam, Q, En, dE, st)
+        _K8.update(n=n, tree=tree, A2=A2, Ef=Ef, pidx=pidx, st=st, sig=sig, C=C, stat=stat, gap=gap)
+    return _K8
+
+
+@pytest.mark.parametrize("form", ["f64", "mixed", "mixed-f32-tangent"])
+def test_depth8_batch_full_size_sampled(form):
+    w = k8_workload()
+    n, tree = w["n"], w["tree"]
+    A2_d = torch.from_numpy(w["A2"]).to(DEV)
+    Ef_d = torch.from_numpy(w["Ef"]).to(DEV)
+    En = [Ef_d * ((s - 1) / bench.N_INCREMENTS) for s in range(1, 7)]
+    dE = [Ef_d * (s / bench.N_INCREMENTS) - En[s - 1] for s in range(1, 7)]
+    args = types.SimpleNamespace(warmup=3)
+    ctx = dict(dev=DEV, n=n, tree=tree, A2=A2_d, En=En, dE=dE)
+    shape = bench.tune_shape(form, ctx, args)          # the bench's launch shape for this form
+    m = dmn.DMN(tree, precision=form, block=shape["block"], ctas_per_sm=shape["ctas_per_sm"])
+    lam, Q = m.interp_orientation(A2_d)
+    st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+    for s in range(1, 7):
+        out = m.update(lam, Q, En[s - 1], dE[s - 1], st)
+        st = out["state_out"]
+    torch.cuda.synchronize()
+    p = w["pidx"]
+    stat = out["status"].cpu().numpy()
+    assert (stat == 0).all()
+    np.testing.assert_array_equal(stat[p], w["stat"])
+    sig = out["stress"][p].cpu().numpy()
+    C = out["tangent"][p].cpu().numpy()
+    sg = st[:, p].cpu().numpy()
+    ok = w["gap"] >= 1e-9                               # no yield decision within rounding
+    es = rel(sig, w["sig"]).max()
+    ec = rel(C[ok], w["C"][ok]).max()
+    scale = np.abs(w["st"]).max(axis=1, keepdims=True) + 1e-300
+    est = (np.abs(sg - w["st"]) / scale).max()
+    print(form, shape["block"], shape["ctas_per_sm"], es, ec, est)
+    assert es <= TOL[form][0] and ec <= TOL[form][1]
+    assert est <= (1e-9 if form == "f64" else 1e-5)
+    m.close()
+    del out, st, lam, Q, A2_d, Ef_d, En, dE
+    release()
+
+
+def test_mixed_depth_batch_full_size_graph_sampled():
+    """4M points of depths 5-8 (the bench's seeds), 3 eager warm-up increments and a CUDA
+    graph of increments 4-6 in the launch shape the bench picks; FP64 form."""
+    n = 1 << 22
+    trees = [W.tree_d10_fit(K, seed=bench.SEED_TREE + K) for K in bench.MD_DEPTHS]
+    tid, elastic = W.mixed_depth_batch(n, bench.SEED_ORI + 7, bench.MD_DEPTHS)
+    A2, _, _ = W.orientation_field(n, seed=bench.SEED_ORI + 8)
+    Edir = W.random6_path_final(n, 1.0, seed=bench.SEED_PATH + 9)
+    amp = np.where(elastic, 0.001, 0.02)[:, None] * Edir
+
+    def inputs_np(k, idx=slice(None)):
+        En_c, dE_c = W.cyclic_increment(amp[idx], k, bench.MD_INCREMENTS)
+        En_r, dE_r = W.proportional_increment(amp[idx], k, bench.MD_INCREMENTS)
+        e = elastic[idx][:, None]
+        return np.where(e, En_r, En_c), np.where(e, dE_r, dE_c)
+
+    def inputs(k):
+        a, b = inputs_np(k)
+        return torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV)
+
+    A2_d, tid_d = torch.from_numpy(A2).to(DEV), torch.from_numpy(tid).to(DEV)
+    # launch shape as in the bench: candidates timed on 2^18 points at increment 4
+    msub = 1 << 18
+    m0 = dmn.DMN(trees)
+    lam_s, Q_s = m0.interp_orientation(A2_d[:msub].contiguous())
+    st = torch.zeros((m0.state_size, msub), dtype=torch.float64, device=DEV)
+    for k in range(1, 4):
+        En, dE = inputs(k)
+        st = m0.update(lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st,
+                       tree_id=tid_d[:msub].contiguous())["state_out"]
+    m0.close()
+    En, dE = inputs(4)
+    best = None
+    for block, cps in ((128, 2), (128, 3), (128, 4), (64, 6)):
+        mm = dmn.DMN(trees, block=block, ctas_per_sm=cps)
+        o = mm.update(lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st, tree_id=tid_d[:msub].contiguous())
+        torch.cuda.synchronize()
+        mm.profile(True)
+        mm.update(lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st, out=o,
+                  tree_id=tid_d[:msub].contiguous())
+        kms, _ = mm.profile_read()
+        mm.close()
+        if best is None or kms["newton"] < best[2]:
+            best = (block, cps, kms["newton"])
+    del st, o, lam_s, Q_s
+    release()
+    m = dmn.DMN(trees, block=best[0], ctas_per_sm=best[1])
+    lam, Q = m.interp_orientation(A2_d)
+    bufs = [torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV) for _ in range(2)]
+    outs = [dict(stress=torch.empty((n, 6), dtype=torch.float64, device=DEV),
+                 tangent=torch.empty((n, 6, 6), dtype=torch.float64, device=DEV),
+                 iters=torch.empty(n, dtype=torch.int32, device=DEV),
+                 status=torch.empty(n, dtype=torch.int32, device=DEV)) for _ in range(3)]
+    for k in range(1, 4):
+        En, dE = inputs(k)
+        m.update(lam, Q, En, dE, bufs[(k - 1) % 2], out=dict(outs[0], state_out=bufs[k % 2]), tree_id=tid_d)
+    ins = [inputs(k) for k in (4, 5, 6)]
+    for j in range(3):
+        outs[j]["state_out"] = bufs[(j + 4) % 2]
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            for j in range(3):
+                m.update(lam, Q, ins[j][0], ins[j][1], bufs[(j + 3) % 2], out=outs[j], tree_id=tid_d)
+    torch.cuda.current_stream().wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize()
+    last = outs[2]
+    assert (last["status"].cpu().numpy() == 0).all()
+    rng = np.random.default_rng(12)
+    for t, K in enumerate(bench.MD_DEPTHS):
+        idx = np.sort(rng.choice(np.nonzero(tid == t)[0], 8, replace=False))
+        lo, Qo = oracle.interp_orientation(A2[idx])
+        S = oracle.state_size(K, trees[t].phases)
+        so = np.zeros((S, len(idx)))
+        for k in range(1, 7):
+            En_o, dE_o = inputs_np(k, idx)
+            so, sig, C, it, stat, gap = oracle.update(trees[t], lo, Qo, En_o, dE_o, so)
+        assert (stat == 0).all()
+        ok = gap >= 1e-9
+        es = rel(last["stress"][idx].cpu().numpy(), sig).max()
+        ec = rel(last["tangent"][idx].cpu().numpy()[ok], C[ok]).max()
+        sg = last["state_out"][:S, idx].cpu().numpy()
+        est = (np.abs(sg - so) / (np.abs(so).max(axis=1, keepdims=True) + 1e-300)).max()
+        print("K", K, best[:2], es, ec, est)
+        assert es <= 1e-10 and ec <= 1e-10 and est <= 1e-9, (K, es, ec, est)
+    m.close()
+    del g, bufs, outs, lam, Q, A2_d, tid_d, ins, last
+    release()
+
+
+def test_training_adjoint_full_batch_sampled():
+    """The adjoint over the training workload's plastic batch: 4096 points of a depth-8 DMN,
+    one increment from the virgin state to 1-3 % equivalent strain, line search on (as the
+    trainer's plastic handle); stress seeds at 3 sampled points only."""
+    K, n = 8, 4096
+    tree = W.tree_d10_fit(K, seed=bench.SEED_TREE + 41)
+    A2, lam, Q = W.orientation_field(n, seed=bench.SEED_ORI + 42)
+    rng = np.random.default_rng(43)
+    E = W.random6_path_final(n, 1.0, seed=bench.SEED_PATH + 44) * rng.uniform(0.01, 0.03, (n, 1))
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+    m = dmn.DMN(tree, line_search=True)
+    z = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+    zE = d(np.zeros((n, 6)))
+    out = m.update(d(lam), d(Q), zE, d(E), z)
+    assert (out["status"].cpu().numpy() == 0).all()
+    pidx = np.array([5, 2047, n - 1])
+    g = np.zeros((n, 6))
+    g[pidx] = rng.standard_normal((3, 6))
+    g_p, g_q, g_w, _ = m.grad(d(lam), d(Q), zE, d(E), z, out["state_out"], d(g))
+    g_p, g_q, g_w = g_p.cpu().numpy(), g_q.cpu().numpy(), g_w.cpu().numpy()
+    S = oracle.state_size(K, tree.phases)
+    so, _, _, _, stat_o, _ = oracle.update(tree, lam[pidx], Q[pidx], np.zeros((3, 6)), E[pidx], np.zeros((S, 3)),
+                                           line_search=True)
+    assert (stat_o == 0).all()
+    dirs = [(rng.standard_normal(tree.p.shape), rng.standard_normal(tree.q.shape),
+             rng.standard_normal(tree.w.shape) * tree.w) for _ in range(2)]
+    ref = np.zeros(len(dirs))
+    for j, i in enumerate(pidx):
+        r = oracle.gradient_ift(tree, lam[i], Q[i], E[i], oracle.jumps(tree, so, j),
+                                oracle.leaf_states(tree, np.zeros((S, 3)), j), g[i], directions=dirs)
+        ref += np.asarray(r, dtype=np.float64)
+    pred = np.array([(g_p * dp).sum() + (g_q * dq).sum() + (g_w * dw).sum() for dp, dq, dw in dirs])
+    print(pred, ref)
+    assert np.abs(pred - ref).max() <= 1e-5 * np.abs(ref).max()
+    m.close()
+    release()
+
+
+def test_fe_plate_full_size_equilibrium():
+    """The bench's plate with a hole (150,528 hexahedra, 1,204,224 DMN points, FP64 DMN, FP32
+    CG products), first two increments.  The oracle's FE operator, applied to the GPU's
+    Gauss-point stresses, must show the converged equilibrium at 32 sampled free nodes
+    (within the Newton tolerance) and the GPU's reaction force on the loaded face."""
+    P = bench.PLATE
+    mesh = W.plate_with_hole_mesh(P["n_t"], P["n_r"], P["n_z"], R=P["R"], H=P["H"], T=P["T"])
+    A2 = W.plate_orientation_field(mesh.centroid, mesh.R, mesh.H, mesh.T, seed=bench.SEED_ORI + 21)
+    tree = W.tree_d10_fit(bench.K_DEPTH, seed=bench.SEED_TREE)
+    run = fe.FEDMN(mesh, tree, A2, precision="f64", newton_rtol=1e-6, cg_rtol=1e-6, cg_f32=True)
+    for k in (1, 2):
+        r = run.increment(bench.PLATE_STRAIN * 2 * mesh.H * k / bench.PLATE_INCREMENTS)
+        assert r["converged"] and r["dmn_status_bad"] == 0, r
+    sig = run.out["stress"].cpu().numpy()
+    fnorm = float(torch.linalg.norm(run.f).item())
+    conn = np.asarray(mesh.conn)
+    fixed = np.asarray(mesh.fixed).reshape(-1, 3)
+    pull = np.asarray(mesh.pull).reshape(-1, 3)
+
+    def nodal_force(nodes):
+        elems = np.nonzero(np.isin(conn, nodes).any(axis=1))[0]
+        sub = FE.Mesh(mesh.xyz, conn[elems])
+        gp = (8 * elems[:, None] + np.arange(8)[None, :]).reshape(-1)
+        return sub.internal_force(sig[gp]).reshape(-1, 3)
+
+    rng = np.random.default_rng(13)
+    free_nodes = np.nonzero(~fixed.any(axis=1))[0]
+    nodes = rng.choice(free_nodes, 32, replace=False)
+    f = nodal_force(nodes)[nodes]
+    assert np.abs(f).max() <= 1.01e-6 * fnorm, (np.abs(f).max(), fnorm)
+    face = np.nonzero(pull[:, 0] > 0)[0]
+    reaction = (nodal_force(face)[face, 0] * pull[face, 0]).sum()
+    assert abs(reaction - r["reaction"]) <= 1e-9 * abs(r["reaction"]), (reaction, r["reaction"])
+    run.close()
+    release()
