@@ -295,11 +295,24 @@ def rel_rows(a, b):
     return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
 
 
+def form_opts(form):
+    """(precision, extrapolated start) of a form name such as "f64" or "mixed-f32-tangent/extrap"."""
+    prec, _, start = form.partition("/")
+    if start not in ("", "extrap"):
+        raise ValueError("unknown start in form %r" % form)
+    return prec, start == "extrap"
+
+
 def tune_shape(form, ctx, args):
     """Launch shape of the Newton kernel from the autotuner, tuned on the first 2^18 points at the
-    first timed increment (after the warm-up increments)."""
+    first timed increment (after the warm-up increments).  Forms that differ only in the start
+    share the kernel and its shape."""
     import torch
     from paper_2103_08253_gb300 import autotune, dmn
+    form, _ = form_opts(form)
+    cache = ctx.setdefault("shapes", {})
+    if form in cache:
+        return cache[form]
     dev = ctx["dev"]
     m = min(ctx["n"], 1 << 18)
     A2 = ctx["A2"][:m].contiguous()
@@ -314,6 +327,7 @@ def tune_shape(form, ctx, args):
                         ctx["dE"][s - 1][:m].contiguous(), st, reps=1)
     del st
     torch.cuda.empty_cache()
+    cache[form] = res
     return res
 
 
@@ -323,8 +337,9 @@ def run_form(form, ctx, args, dist):
     from paper_2103_08253_gb300 import dmn
     dev, n = ctx["dev"], ctx["n"]
     shape = tune_shape(form, ctx, args) if args.autotune else None
-    m = dmn.DMN(ctx["tree"], precision=form, block=shape["block"] if shape else 0,
-                ctas_per_sm=shape["ctas_per_sm"] if shape else 0)
+    prec, pred = form_opts(form)
+    m = dmn.DMN(ctx["tree"], precision=prec, block=shape["block"] if shape else 0,
+                ctas_per_sm=shape["ctas_per_sm"] if shape else 0, predictor=pred)
     S = m.state_size
     st = [torch.zeros((S, n), dtype=torch.float64, device=dev), torch.zeros((S, n), dtype=torch.float64, device=dev)]
     lam = torch.empty((n, 2), dtype=torch.float64, device=dev)
@@ -380,12 +395,13 @@ def parity_sample(form, r, ctx, args, pidx):
     """Oracle on the sampled points through increments 1..warmup+steps, compared with the GPU."""
     import oracle
     tree, A2, Ef = ctx["tree"], ctx["A2_np"], ctx["Ef_np"]
+    _, pred = form_opts(form)
     lam, Q = oracle.interp_orientation(A2[pidx])
-    S = oracle.state_size(tree.K, tree.phases, tree.w)
-    st = np.zeros((S, len(pidx)))
+    S0, J = oracle.jump_fields(tree)
+    st = np.zeros((S0 + J + 6 if pred else S0, len(pidx)))
     for s in range(1, args.warmup + args.steps + 1):
         En, dE = W.proportional_increment(Ef[pidx], s, N_INCREMENTS)
-        st, sig, C, it, stat, gap = oracle.update(tree, lam, Q, En, dE, st)
+        st, sig, C, it, stat, gap = oracle.update(tree, lam, Q, En, dE, st, predictor=pred)
     sig_g = r["stress"][pidx].cpu().numpy()
     C_g = r["tangent"][pidx].cpu().numpy()
     st_g = r["state"][:, pidx].cpu().numpy()
@@ -510,7 +526,8 @@ def run_mixed_depth(args):
             "forms": {}}
     for form in [f for f in args.forms.split(",") if f]:
         # autotuned shape on 2^18 points of the batch at the first timed increment
-        m0 = dmn.DMN(trees, precision=form)
+        prec, pred = form_opts(form)
+        m0 = dmn.DMN(trees, precision=prec)
         msub = min(n, 1 << 18)
         lam_s, Q_s = m0.interp_orientation(A2_d[:msub].contiguous())
         st = torch.zeros((m0.state_size, msub), dtype=torch.float64, device=dev)
@@ -523,7 +540,7 @@ def run_mixed_depth(args):
         best = None
         En, dE = inputs(first)
         for block, cps in ((128, 2), (128, 3), (128, 4), (64, 6)):
-            mm = dmn.DMN(trees, precision=form, block=block, ctas_per_sm=cps)
+            mm = dmn.DMN(trees, precision=prec, block=block, ctas_per_sm=cps)
             o = mm.update(lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st, tree_id=tid_d[:msub].contiguous())
             torch.cuda.synchronize()
             mm.profile(True)
@@ -535,7 +552,7 @@ def run_mixed_depth(args):
                 best = (block, cps, kms["newton"])
         del st
         torch.cuda.empty_cache()
-        m = dmn.DMN(trees, precision=form, block=best[0], ctas_per_sm=best[1])
+        m = dmn.DMN(trees, precision=prec, block=best[0], ctas_per_sm=best[1], predictor=pred)
         lam, Q = m.interp_orientation(A2_d)
         S = m.state_size
         bufs = [torch.zeros((S, n), dtype=torch.float64, device=dev) for _ in range(2)]
@@ -587,7 +604,7 @@ def run_mixed_depth(args):
         torch.cuda.empty_cache()
     main_form = "f64" if "f64" in line["forms"] else next(iter(line["forms"]))
     line["value"] = line["forms"][main_form]["value"]
-    line["dtype"] = "f64" if main_form == "f64" else "f32+f64"
+    line["dtype"] = "f64" if form_opts(main_form)[0] == "f64" else "f32+f64"
     print(json.dumps(line), flush=True)
     return 0
 
@@ -623,7 +640,8 @@ def run_plate(args):
                        "dmn_line_search": True, "predictor": "uniform strain, then extrapolated increments"},
             "forms": {}}
     for form in [f for f in args.forms.split(",") if f]:
-        run = fe.FEDMN(mesh, tree, A2, precision=form, newton_rtol=1e-6, cg_rtol=1e-6, cg_f32=True)
+        prec, pred = form_opts(form)
+        run = fe.FEDMN(mesh, tree, A2, precision=prec, newton_rtol=1e-6, cg_rtol=1e-6, cg_f32=True, predictor=pred)
         clocks = ClockSampler("0")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -651,7 +669,7 @@ def run_plate(args):
     main_form = "f64" if "f64" in line["forms"] else next(iter(line["forms"]))
     line["value"] = line["forms"][main_form]["value"]
     line["ms_per_step"] = line["forms"][main_form]["ms_per_increment"]
-    line["dtype"] = "f64" if main_form == "f64" else "f32+f64"
+    line["dtype"] = "f64" if form_opts(main_form)[0] == "f64" else "f32+f64"
     print(json.dumps(line), flush=True)
     return 0
 
@@ -704,7 +722,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--points", type=int, default=1 << 20)
-    ap.add_argument("--forms", default="f64,mixed,mixed-f32-tangent")
+    ap.add_argument("--forms", default="f64,mixed,mixed-f32-tangent,f64/extrap,mixed-f32-tangent/extrap",
+                    help="precisions, each optionally with /extrap: the Newton iteration starts from the last "
+                         "update's jumps extrapolated along the strain increment instead of the paper's a^n")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="points per chunk of dmn_update_host (0: the library's default)")
     ap.add_argument("--e2e-steps", type=int, default=-1,
@@ -791,8 +811,9 @@ def run_gpu(args):
         forms_out[form] = {"value": v, "unit": UNIT, "ms_per_step": r["t_ms"] / steps,
                            "kernel_ms_per_step": {k: x / steps for k, x in r["kms"].items()},
                            "newton_iters_per_update": r["iters_sum"] / (n * steps), "iters_hist": r["iters_hist"],
-                           "roofline": (roofline_f64(r, n, steps, tree.w) if form == "f64"
-                                        else roofline_mixed(r, n, steps, tree.w, sweep=form == "mixed")),
+                           "roofline": (roofline_f64(r, n, steps, tree.w) if form_opts(form)[0] == "f64"
+                                        else roofline_mixed(r, n, steps, tree.w,
+                                                            sweep=form_opts(form)[0] == "mixed")),
                            "launch": r["launch"],
                            "parity_vs_oracle": r.get("parity"), "clocks": r["clocks"]}
     main_form = "f64" if "f64" in results else forms[0]
@@ -807,7 +828,7 @@ def run_gpu(args):
                          % (len(idx), args.warmup + 1, args.warmup + min(3, steps), args.warmup)}
     line = {"metric": METRIC, "value": forms_out[main_form]["value"], "unit": UNIT, "n_gpus": world,
             "steps": steps, "warmup": args.warmup, "ms_per_step": mr["t_ms"] / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_form == "f64" else "f32+f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if form_opts(main_form)[0] == "f64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_CMP if cmp else WORKLOAD, "K": K_DEPTH, "points_per_gpu": n,
                        "increments": N_INCREMENTS, "matrix": MATRIX_NOTE[args.matrix],

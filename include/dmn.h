@@ -27,7 +27,10 @@
  *     equivalent plastic strain and the deviatoric plastic strain
  *     (ep33 = -ep11 - ep22); then three jump components per laminate in the
  *     paper's ordering (level K first, root last; Sec. 3.2, Eq. of the normal
- *     ordering).  A zero state is the virgin state.
+ *     ordering).  With the extrapolated start (dmn_options.predictor = 1) more
+ *     fields follow: the jump change a^{n+1} - a^n of the last update (same
+ *     ordering, three per laminate), then that update's strain increment dE
+ *     (six, Mandel, global frame).  A zero state is the virgin state.
  *   - Pointers named "dev" are CUDA device pointers; "host" are host
  *     pointers.  The caller owns every array passed in; the handle owns its
  *     parameters and work space.  Device calls are asynchronous on the given
@@ -118,6 +121,18 @@ typedef struct {
                         * a trial step is accepted when it lowers ||A^T W sigma||, else halved, at
                         * most 8 times (then status LINESEARCH and the last accepted iterate).
                         * Needs 2x the per-lane scratch and at most 256 threads per SM. */
+  int32_t predictor;   /* 0: each update's Newton iteration starts from the stored jumps a^n, as in
+                        * Sec. 4.7.  1: it starts from a^n + rho (a^n - a^{n-1}), with
+                        * rho = (dE . dE_prev) / (dE_prev . dE_prev) clamped to [0, 1] (0 when
+                        * dE_prev = 0 or the ratio is not finite): the jumps of the last update
+                        * extrapolated along the new strain increment while the load keeps its
+                        * sense.  A point with rho > 0 that has not met the criterion after 6
+                        * corrections (or whose iterates are not finite, or whose line search
+                        * fails) restarts from a^n with max_iter corrections; iters counts both
+                        * attempts.  The paper has no such start; it reaches the same solution
+                        * (up to the stopping criterion) in fewer Newton steps on smooth load
+                        * paths.  The state then carries 3 fields per laminate and 6 more (see
+                        * the state layout above). */
 } dmn_options;
 
 /* Create a handle for n_trees DMNs (1 <= n_trees <= DMN_MAX_TREES; trees may
@@ -136,7 +151,8 @@ void dmn_destroy(dmn_handle* h);
 
 /* Doubles of state per point for tree tree_id: 6 per inelastic leaf plus
  * 3 per laminate (1533 for K = 8 with one inelastic phase; the paper counts
- * the same 128 x (1 + 5) + 255 x 3 scalars, Sec. 4.7).  tree_id = -1 gives
+ * the same 128 x (1 + 5) + 255 x 3 scalars, Sec. 4.7), plus 3 per laminate
+ * and 6 with the extrapolated start (2304 for K = 8).  tree_id = -1 gives
  * the maximum over the handle's trees: the number of fields S of the state
  * arrays passed to dmn_update (a point of tree t uses the first
  * dmn_state_size(h, t) of them).  -1 on a bad argument. */
@@ -169,7 +185,8 @@ int dmn_interp_orientation(dmn_handle* h, int64_t n, const double* A2, double* l
  *                          state_out is left untouched
  * With several trees the points are first sorted by tree on the device so
  * that the lanes of a warp walk the same tree.  The Newton iteration starts
- * from a^n (Sec. 4.7) and stops when the criterion of Sec. 4.6 holds.  The
+ * from a^n (Sec. 4.7), or from the extrapolated jumps of dmn_options.predictor,
+ * and stops when the criterion of Sec. 4.6 holds.  The
  * first call with a larger n than any earlier call allocates per-point work
  * space (cudaMalloc, synchronous); calls with at most that n allocate nothing
  * and may be captured in a CUDA graph.  Errors: DMN_ERR_ARG for n < 0, NULL
@@ -272,7 +289,7 @@ int dmn_profile_read(dmn_handle* h, double ms[3], int64_t* updates);
  *
  * Arguments are those of dmn_create (tree, opt) and dmn_update (n and the
  * arrays, same layouts and ownership).  Only the FP64 form is offered
- * (opt->precision must be DMN_PREC_F64; opt may be NULL); opt->block and
+ * (opt->precision must be DMN_PREC_F64 and opt->predictor 0; opt may be NULL); opt->block and
  * opt->ctas_per_sm are ignored.  The static work space limits parallelism:
  * 1152 lanes at K = 8 (more for shallower trees), so it is slower than
  * dmn_update.  Errors: DMN_ERR_ARG for the argument errors of dmn_create and

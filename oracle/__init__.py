@@ -91,11 +91,77 @@ def state_size(K: int, phases, w=None) -> int:
     return int(_load().oracle_state_size_w(K, _p(m), _p(_f64(w))))
 
 
-def update(tree, lam, Q, E_n, dE, state_in, tol=1e-12, max_iter=50, line_search=False, nthreads=None):
+PRED_TRIES = 6   # corrections from the extrapolated start before a restart from a^n
+
+
+def jump_fields(tree):
+    """(S0, J): state fields of the tree (its compressed form when weights are zero) and
+    how many of them, the last ones, are laminate jumps (3 per remaining laminate).  The
+    others are 6 per remaining inelastic leaf."""
+    S0 = state_size(tree.K, tree.phases, tree.w)
+    w = np.asarray(tree.w, dtype=np.float64)
+    inel = [int(ph.kind) != 0 for ph in tree.phases]
+    nz = sum(1 for leaf in range(w.size) if w[leaf] > 0 and inel[leaf % 2])
+    return S0, S0 - 6 * nz
+
+
+def update(tree, lam, Q, E_n, dE, state_in, tol=1e-12, max_iter=50, line_search=False, nthreads=None,
+           predictor=False):
     """One material-point update of n points (Sec. 3.2): returns
     (state_out, stress [n,6], tangent [n,6,6], iters [n], status [n], yield_gap [n]).
 
-    state_in is field-major [S, n]; stress/tangent are in the global frame."""
+    state_in is field-major [S, n]; stress/tangent are in the global frame.  The Newton
+    iteration starts from the jumps held in state_in (Sec. 4.7: the last converged ones).
+
+    predictor: the extrapolated start of this library (the paper has none).  state_in then
+    carries J more fields (the last update's jump change) and 6 (its strain increment
+    dE_prev) after the S0 of the tree, J and S0 as given by jump_fields.  The iteration
+    starts from a^n + rho (jump change), rho = (dE . dE_prev) / (dE_prev . dE_prev)
+    clipped to [0, 1], or 0 when dE_prev = 0 or the ratio is not finite.  A point with
+    rho > 0 gets PRED_TRIES corrections; if it has not converged by then (any status but
+    0), it starts again from a^n with max_iter corrections, and its iteration count is the
+    sum of both attempts.  state_out carries this update's jump change and dE in the same
+    places."""
+    if predictor:
+        S0, J = jump_fields(tree)
+        state_in = _f64(state_in)
+        assert state_in.shape[0] == S0 + J + 6, (state_in.shape, S0, J)
+        a_n = state_in[S0 - J:S0]
+        change = state_in[S0:S0 + J]
+        dE_prev = state_in[S0 + J:]
+        dE = _f64(dE)
+        num = np.einsum("ni,in->n", dE, dE_prev)
+        den = (dE_prev * dE_prev).sum(axis=0)
+        with np.errstate(all="ignore"):
+            r = num / den
+            rho = np.where((den > 0) & np.isfinite(r), np.clip(r, 0.0, 1.0), 0.0)
+        paper = np.array(state_in[:S0])
+        start = paper.copy()
+        start[S0 - J:] = a_n + rho[None, :] * change
+        ext = rho > 0
+        lam = _f64(lam); Q = _f64(Q); E_n = _f64(E_n)
+        res = list(update(tree, lam, Q, E_n, dE, paper, tol, max_iter, line_search, nthreads))
+        if ext.any():   # the extrapolated attempts, and restarts of those that failed
+            x = np.nonzero(ext)[0]
+            r1 = update(tree, lam[x], Q[x], E_n[x], dE[x], start[:, x], tol, PRED_TRIES, line_search, nthreads)
+            fail = x[r1[4] != 0]
+            keep = r1[4] == 0
+            for k, v in enumerate(r1):
+                if v.ndim == 2 and v.shape[0] != len(x):      # field-major state
+                    res[k][:, x[keep]] = v[:, keep]
+                else:
+                    res[k][x[keep]] = v[keep]
+            if fail.size:
+                r2 = update(tree, lam[fail], Q[fail], E_n[fail], dE[fail], paper[:, fail], tol, max_iter,
+                            line_search, nthreads)
+                for k, v in enumerate(r2):
+                    if v.ndim == 2 and v.shape[0] != len(fail):
+                        res[k][:, fail] = v
+                    else:
+                        res[k][fail] = v
+                res[3][fail] += r1[3][r1[4] != 0]
+        st = res[0]
+        return (np.vstack([st, st[S0 - J:] - a_n, dE.T]),) + tuple(res[1:])
     lib = _load()
     lam = _f64(lam); Q = _f64(Q); E_n = _f64(E_n); dE = _f64(dE); state_in = _f64(state_in)
     n = lam.shape[0]

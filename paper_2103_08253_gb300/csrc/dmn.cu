@@ -412,6 +412,8 @@ struct NewtonParams {
   double tol;
   int max_iter;
   int write_outputs;  // no final sweep: stress and tangent (local frame) come from the converged Newton pass
+  int predictor;      // extrapolated start; the state carries the last jump change and strain increment
+  const double* dE;   // [n][6] strain increments (global frame), read with the extrapolated start
 };
 
 // MINB: resident CTAs per SM the register allocation is sized for (255, 170 or
@@ -423,7 +425,11 @@ struct NewtonParams {
 // the accepted iterate intact.
 // CMP: trees walked by their compressed-traversal tables (tree_pass_c), jumps
 // numbered as in the state; otherwise heap arithmetic (tree_pass).
-template <typename T, int MINB, bool LS, bool CMP>
+// Extrapolated start: corrections allowed before a point restarts from a^n.
+constexpr int PRED_TRIES = 6;
+
+// PRED: extrapolated start (a separate instantiation, so that the paper's start pays nothing for it).
+template <typename T, int MINB, bool LS, bool CMP, bool PRED>
 __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -447,9 +453,26 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   bool first = true; // the next pass evaluates the starting jumps
   T step = (T)1;     // line search: scale of the trial step
   int halvings = 0;
+  bool retry = false; // extrapolated start: restart from a^n if it has not converged by lim
+  int lim = 0;        // corrections after which the current attempt ends with MAXITER
   double rn_acc = 0.0;
   Sub<T> root_acc;   // line search: results at the accepted iterate
   double Eloc[6];
+  // the extrapolated start failed: continue from the stored jumps a^n, as a new point would
+  auto restart = [&](const TreeDev& t) {
+    const int nzf = 6 * t.nz;
+    for (int f = 0; f < 3 * t.N; ++f) {
+      const int node = f / 3, c = f - 3 * node;
+      const int lvl = 32 - __clz(node + 1);
+      const int j = CMP ? node : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+      abuf[cur][(size_t)f * ns] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
+    }
+    retry = false;
+    lim = it + P.max_iter;
+    first = true;
+    step = (T)1;
+    halvings = 0;
+  };
   for (;;) {
     const bool need = pt < 0;
     const unsigned mask = __ballot_sync(0xffffffffu, need);
@@ -476,12 +499,32 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
             cur = 0;
 #pragma unroll
             for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * NM + I) * P.n + pt];
+            // extrapolated start: rho = (dE . dE_prev) / (dE_prev . dE_prev), clamped to [-2, 2]
+            const int pf0 = nzf + 3 * t.N;   // first field of the last jump change
+            double rho = 0.0;
+            if (PRED) {
+              double num = 0.0, den = 0.0;
+#pragma unroll
+              for (int c = 0; c < 6; ++c) {
+                const double q = P.state_in[(size_t)(pf0 + 3 * t.N + c) * P.n + pt];
+                num += P.dE[6 * pt + c] * q;
+                den += q * q;
+              }
+              const double r = num / den;
+              rho = (den > 0.0 && isfinite(r)) ? fmin(fmax(r, 0.0), 1.0) : 0.0;
+            }
+            if (PRED) {
+              retry = rho > 0.0;
+              lim = retry ? PRED_TRIES : P.max_iter;
+            }
             for (int f = 0; f < 3 * t.N; ++f) {
               const int node = f / 3, c = f - 3 * node;
               // heap node -> paper index of its jumps
               const int lvl = 32 - __clz(node + 1);
               const int j = CMP ? node : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
-              abuf[0][(size_t)f * ns] = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
+              double a0 = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
+              if (PRED) a0 += rho * P.state_in[(size_t)(pf0 + 3 * j + c) * P.n + pt];
+              abuf[0][(size_t)f * ns] = a0;
               const double nv = P.nbuf[(size_t)f * P.n + pt];
               my_nrm[(size_t)f * ns] = nv;
               if (sizeof(T) == 4) my_nrmf[(size_t)f * ns] = narrow_rn(nv);
@@ -519,7 +562,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
       first = false;
       if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
       else if (rn <= P.tol * (double)t.N * sn) st = DMN_STATUS_OK;
-      else if (it >= P.max_iter) st = DMN_STATUS_MAXITER;
+      else if (it >= (PRED ? lim : P.max_iter)) st = DMN_STATUS_MAXITER;
       if (st < 0) { ++it; continue; }
     } else {
       bool accepted = first || rn < rn_acc;
@@ -532,7 +575,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
         halvings = 0;
         if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
         else if (rn <= P.tol * (double)t.N * sn) st = DMN_STATUS_OK;
-        else if (it >= P.max_iter) st = DMN_STATUS_MAXITER;
+        else if (it >= (PRED ? lim : P.max_iter)) st = DMN_STATUS_MAXITER;
         if (st < 0) { ++it; continue; }
       } else if (++halvings > 8) {
         st = DMN_STATUS_LINESEARCH;   // no halving lowered the residual: keep the accepted iterate
@@ -543,6 +586,10 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
         continue;
       }
     }
+    if (PRED && st > 0 && retry) {   // the extrapolated start failed: the stored jumps a^n, as a new point
+      restart(t);
+      continue;
+    }
     // finished point: jumps (paper ordering), counters, and without a final sweep
     // the local-frame stress and packed tangent for k_final to rotate
     const double* afin = abuf[cur];
@@ -551,7 +598,14 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
       const int node = f / 3, c = f - 3 * node;
       const int lvl = 32 - __clz(node + 1);
       const int j = CMP ? node : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
-      P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt] = st == DMN_STATUS_NONFINITE ? qnan : afin[(size_t)f * ns];
+      const double af = st == DMN_STATUS_NONFINITE ? qnan : afin[(size_t)f * ns];
+      P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt] = af;
+      if (PRED)   // this update's jump change, for the next update's start
+        P.state_out[(size_t)(nzf + 3 * t.N + 3 * j + c) * P.n + pt] = af - P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
+    }
+    if (PRED) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) P.state_out[(size_t)(nzf + 6 * t.N + c) * P.n + pt] = P.dE[6 * pt + c];
     }
     P.iters[pt] = it;
     P.status[pt] = st;
@@ -917,12 +971,17 @@ void free_pipe(HostPipe& p) {
 }
 
 // Newton kernel variant for the launch shape: register cap by resident CTAs, line search.
+template <typename T, bool CMP, bool PRED>
+void launch_newton_p(const NewtonParams<T>& P, bool ls, int minb, unsigned grid, int block, cudaStream_t s) {
+  if (ls) k_newton<T, 2, true, CMP, PRED><<<grid, block, 0, s>>>(P);
+  else if (minb == 2) k_newton<T, 2, false, CMP, PRED><<<grid, block, 0, s>>>(P);
+  else if (minb == 3) k_newton<T, 3, false, CMP, PRED><<<grid, block, 0, s>>>(P);
+  else k_newton<T, 4, false, CMP, PRED><<<grid, block, 0, s>>>(P);
+}
 template <typename T, bool CMP>
 void launch_newton(const NewtonParams<T>& P, bool ls, int minb, unsigned grid, int block, cudaStream_t s) {
-  if (ls) k_newton<T, 2, true, CMP><<<grid, block, 0, s>>>(P);
-  else if (minb == 2) k_newton<T, 2, false, CMP><<<grid, block, 0, s>>>(P);
-  else if (minb == 3) k_newton<T, 3, false, CMP><<<grid, block, 0, s>>>(P);
-  else k_newton<T, 4, false, CMP><<<grid, block, 0, s>>>(P);
+  if (P.predictor) launch_newton_p<T, CMP, true>(P, ls, minb, grid, block, s);
+  else launch_newton_p<T, CMP, false>(P, ls, minb, grid, block, s);
 }
 
 // One update on work set w and stream s (the body of dmn_update; arguments checked by the caller).
@@ -981,12 +1040,14 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, cons
   const int block = h->opt.block;
   if (!mixed) {
     NewtonParams<double> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
-                           w.nbuf, w.scr_d, (double*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 1};
+                           w.nbuf, w.scr_d, (double*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 1,
+                           h->opt.predictor, dE};
     if (h->cmp) launch_newton<double, true>(P, ls, minb, grid, block, s);
     else launch_newton<double, false>(P, ls, minb, grid, block, s);
   } else {
     NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
-                          w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, sweep ? 0 : 1};
+                          w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, sweep ? 0 : 1,
+                          h->opt.predictor, dE};
     if (h->cmp) launch_newton<float, true>(P, ls, minb, grid, block, s);
     else launch_newton<float, false>(P, ls, minb, grid, block, s);
   }
@@ -1116,6 +1177,7 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
 
   dmn_options o;
   o.tol = 1e-12; o.max_iter = 50; o.precision = DMN_PREC_F64; o.block = 128; o.ctas_per_sm = 0; o.line_search = 0;
+  o.predictor = 0;
   if (opt) {
     if (opt->tol > 0.0) o.tol = opt->tol;
     if (opt->max_iter > 0) o.max_iter = opt->max_iter;
@@ -1123,8 +1185,17 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     if (opt->block > 0) o.block = opt->block;
     if (opt->ctas_per_sm > 0) o.ctas_per_sm = opt->ctas_per_sm;
     o.line_search = opt->line_search;
+    o.predictor = opt->predictor;
   }
   if (o.line_search != 0 && o.line_search != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: line_search must be 0 or 1");
+  if (o.predictor != 0 && o.predictor != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: predictor must be 0 or 1");
+  if (o.predictor) {   // the last update's jump change and strain increment follow the jumps
+    S_max = 0;
+    for (Tree& t : tv) {
+      t.S += 3 * t.N + 6;
+      S_max = std::max<int64_t>(S_max, t.S);
+    }
+  }
   // the line-search kernel keeps two buffers per lane and is built for 256 threads per SM
   if (o.line_search && o.ctas_per_sm <= 0) o.ctas_per_sm = 256 / o.block;
   if (o.precision != DMN_PREC_F64 && o.precision != DMN_PREC_MIXED && o.precision != DMN_PREC_MIXED_F32_TANGENT)
@@ -1566,6 +1637,8 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   if (opt) {
     if (opt->precision != DMN_PREC_F64)
       return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: only the FP64 form is available without allocation");
+    if (opt->predictor != 0)
+      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: the extrapolated start is not available without allocation");
     if (opt->tol > 0.0) tol = opt->tol;
     if (opt->max_iter > 0) max_iter = opt->max_iter;
   }

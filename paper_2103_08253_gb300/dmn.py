@@ -43,7 +43,8 @@ class TreeDesc_(ctypes.Structure):
 
 class Options_(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("line_search", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("line_search", ctypes.c_int32),
+                ("predictor", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -126,10 +127,12 @@ class DMN:
     of such objects (tree i is selected by tree_id == i in update()).
     precision: "f64"; "mixed" (FP32 condensation, FP64 residual and final
     sweep); "mixed-f32-tangent" (the mixed iteration, tangent from its last
-    FP32 condensation).  The other options are those of dmn_options."""
+    FP32 condensation).  predictor: start each Newton iteration from the last update's jumps
+    extrapolated along the new strain increment (the state then holds the last jump change
+    and strain increment too).  The other options are those of dmn_options."""
 
     def __init__(self, tree, precision: str = "f64", tol: float = 1e-12, max_iter: int = 50, block: int = 0,
-                 ctas_per_sm: int = 0, line_search: bool = False):
+                 ctas_per_sm: int = 0, line_search: bool = False, predictor: bool = False):
         import numpy as np
         self._lib = load_library()
         trees = list(tree) if isinstance(tree, (list, tuple)) else [tree]
@@ -152,8 +155,9 @@ class DMN:
         if precision not in PRECISIONS:
             raise ValueError("precision must be one of %s" % (tuple(PRECISIONS),))
         opt = Options_(float(tol), int(max_iter), PRECISIONS[precision], int(block),
-                       int(ctas_per_sm), int(bool(line_search)))
+                       int(ctas_per_sm), int(bool(line_search)), int(bool(predictor)))
         self.precision = precision
+        self.predictor = bool(predictor)
         h = ctypes.c_void_p()
         rc = self._lib.dmn_create(descs, len(trees), ctypes.byref(opt), ctypes.byref(h))
         if rc != 0:

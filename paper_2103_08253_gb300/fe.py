@@ -152,15 +152,18 @@ class FEDMN:
 
     mesh: object with xyz [n_nodes, 3], conn [n_elem, 8], fixed [n_dofs] bool, pull [n_dofs]
     (the prescribed displacement of a fixed dof is delta * pull); A2 [n_elem, 6] fiber
-    orientation per element (all 8 Gauss points share it); tree: DMN parameters."""
+    orientation per element (all 8 Gauss points share it); tree: DMN parameters.
+    predictor: the DMN's extrapolated start (every macro Newton iteration of an increment
+    extrapolates from the last committed increment)."""
 
     def __init__(self, mesh, tree, A2, precision="f64", newton_rtol=1e-6, max_newton=20, cg_rtol=1e-8,
-                 cg_max_iter=50000, line_search=True, block=0, ctas_per_sm=0, cg_f32=False):
+                 cg_max_iter=50000, line_search=True, block=0, ctas_per_sm=0, cg_f32=False, predictor=False):
         import numpy as np
         import torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.mesh = Hex8Mesh(mesh.xyz, mesh.conn)
-        self.m = _dmn.DMN(tree, precision=precision, block=block, ctas_per_sm=ctas_per_sm, line_search=line_search)
+        self.m = _dmn.DMN(tree, precision=precision, block=block, ctas_per_sm=ctas_per_sm, line_search=line_search,
+                          predictor=predictor)
         n, dev = self.mesh.n_gp, self.dev
         A2g = torch.from_numpy(np.ascontiguousarray(np.repeat(np.asarray(A2, dtype=np.float64), 8, axis=0))).to(dev)
         self.lam, self.Q = self.m.interp_orientation(A2g)

@@ -90,6 +90,19 @@ def test_create_rejects_bad_options_without_touching_the_gpu(opt, msg):
     assert set(dmn.PRECISIONS.values()) == {dmn.PREC_F64, dmn.PREC_MIXED, dmn.PREC_MIXED_F32_TANGENT}
 
 
+def test_predictor_option_is_checked_without_touching_the_gpu():
+    lib = dmn.load_library()
+    d, keep = _desc()
+    h = ctypes.c_void_p(123)
+    o = dmn.Options_(1e-12, 50, dmn.PREC_F64, 0, 0, 0, 2)
+    assert lib.dmn_create(ctypes.byref(d), 1, ctypes.byref(o), ctypes.byref(h)) == -1
+    assert h.value is None and "predictor must be 0 or 1" in lib.dmn_last_error(None).decode()
+    # the allocation-free update has no extrapolated start
+    o = dmn.Options_(1e-12, 50, dmn.PREC_F64, 0, 0, 0, 1)
+    rc = lib.dmn_update_noalloc(ctypes.byref(d), ctypes.byref(o), 8, *([None] * 10), None)
+    assert rc == -1 and "extrapolated start" in lib.dmn_last_error(None).decode()
+
+
 def test_calls_on_null_handle_are_argument_errors():
     lib = dmn.load_library()
     assert lib.dmn_update(None, 4, None, *([None] * 10), None) == -1
