@@ -396,19 +396,25 @@ def parity_sample(form, r, ctx, args, pidx):
     import oracle
     tree, A2, Ef = ctx["tree"], ctx["A2_np"], ctx["Ef_np"]
     _, pred = form_opts(form)
-    lam, Q = oracle.interp_orientation(A2[pidx])
-    S0, J = oracle.jump_fields(tree)
-    st = np.zeros((S0 + J + 6 if pred else S0, len(pidx)))
-    for s in range(1, args.warmup + args.steps + 1):
-        En, dE = W.proportional_increment(Ef[pidx], s, N_INCREMENTS)
-        st, sig, C, it, stat, gap = oracle.update(tree, lam, Q, En, dE, st, predictor=pred)
+    cache = ctx.setdefault("oracle_runs", {})   # the oracle's results depend only on the start
+    if pred not in cache:
+        lam, Q = oracle.interp_orientation(A2[pidx])
+        S0, J = oracle.jump_fields(tree)
+        st = np.zeros((S0 + J + 6 if pred else S0, len(pidx)))
+        for s in range(1, args.warmup + args.steps + 1):
+            En, dE = W.proportional_increment(Ef[pidx], s, N_INCREMENTS)
+            st, sig, C, it, stat, gap = oracle.update(tree, lam, Q, En, dE, st, predictor=pred)
+        cache[pred] = (st, sig, C, stat, gap)
+    st, sig, C, stat, gap = cache[pred]
     sig_g = r["stress"][pidx].cpu().numpy()
     C_g = r["tangent"][pidx].cpu().numpy()
     st_g = r["state"][:, pidx].cpu().numpy()
     ok = (stat == 0) & (r["status"][pidx].cpu().numpy() == 0)
+    tie = ok & (gap < 1e-9)    # yield decision within rounding: the tangent may take either branch
     scale = np.abs(st).max(axis=1, keepdims=True) + 1e-300
     return {"points": int(len(pidx)), "max_rel_stress": float(rel_rows(sig_g[ok], sig[ok]).max(initial=0)),
-            "max_rel_tangent": float(rel_rows(C_g[ok], C[ok]).max(initial=0)),
+            "max_rel_tangent": float(rel_rows(C_g[ok & ~tie], C[ok & ~tie]).max(initial=0)),
+            "tangent_ties_excluded": int(tie.sum()),
             "max_rel_state": float((np.abs(st_g - st) / scale).max()), "status_ok": int(ok.sum())}
 
 
@@ -731,7 +737,8 @@ def main():
                     help="increments timed through dmn_update_host (-1: the same increments as the device timing)")
     ap.add_argument("--ref-points", type=int, default=1024)
     ap.add_argument("--cpu-points", type=int, default=1024)
-    ap.add_argument("--parity-points", type=int, default=16)
+    ap.add_argument("--parity-points", type=int, default=256,
+                    help="points of the timed batch recomputed by the oracle for the error statement")
     ap.add_argument("--matrix", default="linear", choices=["linear", "explin"],
                     help="matrix law of the k8 workloads: linear hardening (default) or the paper's exp-linear")
     ap.add_argument("--shape", type=int, default=3, choices=[3, 4, 6],
