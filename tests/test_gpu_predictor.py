@@ -120,3 +120,27 @@ def test_several_depths_and_host_buffers():
             assert rel(out["stress"].cpu().numpy()[idx], sig).max() <= 1e-10
         st = out["state_out"]
     m.close()
+
+
+def test_adjoint_on_a_handle_with_the_extrapolated_start():
+    """dmn_grad reads the jumps and leaf states of the longer state: its gradients match those of
+    a handle with the paper's start at the same path (the two converged states agree to the
+    stopping criterion, so the gradients to 1e-6)."""
+    tree = W.tree_d10_fit(5, seed=160)
+    n = 16
+    A2, lam, Q = W.orientation_field(n, seed=161)
+    Ef = W.random6_path_final(n, 0.03, seed=162)
+    g = np.random.default_rng(163).standard_normal((n, 6))
+    grads = []
+    for pred in (False, True):
+        m = dmn.DMN(tree, predictor=pred)
+        st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+        for s in range(1, 7):
+            En, dE = W.proportional_increment(Ef, s, 20)
+            prev = st
+            st = m.update(d(lam), d(Q), d(En), d(dE), prev)["state_out"]
+        gp, gq, gw, gE = m.grad(d(lam), d(Q), d(En), d(dE), prev, st, d(g))
+        grads.append([x.cpu().numpy() for x in (gp, gq, gw, gE)])
+        m.close()
+    for a, b in zip(*grads):
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max(), np.abs(a - b).max() / np.abs(a).max()
