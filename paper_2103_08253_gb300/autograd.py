@@ -21,7 +21,8 @@ from __future__ import annotations
 import torch
 
 
-def _sync_params(m, p, q, w):
+def sync_params(m, p, q, w):
+    """Upload p, q, w to the handle if they differ from the ones it holds (synchronises the device)."""
     key = tuple(x.detach().double().cpu().numpy().tobytes() for x in (p, q, w))
     if getattr(m, "_param_key", None) != key:
         m.set_params(p.detach().double().cpu().numpy(), q.detach().double().cpu().numpy(),
@@ -32,7 +33,7 @@ def _sync_params(m, p, q, w):
 class _Stress(torch.autograd.Function):
     @staticmethod
     def forward(ctx, m, lam, Q, E_n, dE, state_in, p, q, w):
-        _sync_params(m, p, q, w)
+        sync_params(m, p, q, w)
         out = m.update(lam, Q, E_n.detach(), dE.detach(), state_in)
         ctx.m = m
         ctx.save_for_backward(lam, Q, E_n.detach(), dE.detach(), state_in, out["state_out"], out["status"])
@@ -57,7 +58,7 @@ def dmn_stress(m, lam, Q, E_n, dE, state_in, p, q, w):
 class _Stiffness(torch.autograd.Function):
     @staticmethod
     def forward(ctx, m, lam, Q, p, q, w):
-        _sync_params(m, p, q, w)
+        sync_params(m, p, q, w)
         n = lam.shape[0]
         dev = lam.device
         S = m.state_size

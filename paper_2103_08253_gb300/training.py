@@ -91,6 +91,7 @@ class Trainer:
         N, L, M = (1 << K) - 1, 1 << K, 3
         self.K, self.lam_pen, self.w_floor, self.compress_on = K, lam_pen, w_floor, compress
         self.rebuilds = 0
+        self.side = torch.cuda.Stream()   # the plastic samples' stream (see loss)
         self.alpha = (alpha_min, alpha_max)
         d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(self.dev)
         # initial parameters as in Sec. 4.4
@@ -158,13 +159,27 @@ class Trainer:
         w = self.weights()
         if self.compress_on:
             self._recompress(w)
+        # The plastic samples (few points, many Newton steps, latency-bound) run on a stream of their
+        # own, beside the stiffness samples; autograd runs each backward on its forward's stream, so
+        # the two adjoints overlap too.  Parameter uploads synchronise the device: both come first.
+        ag.sync_params(self.m_el, self.p, self.q, w)
+        if self.m_pl is not None:
+            ag.sync_params(self.m_pl, self.p, self.q, w)
+            main = torch.cuda.current_stream()
+            self.side.wait_stream(main)
+            with torch.cuda.stream(self.side):
+                s, _, stat = ag.dmn_stress(self.m_pl, self.lam_p, self.Q_p, self.zE, self.E_p, self.z_st, self.p,
+                                           self.q, w)
+                # unconverged samples contribute 0 (a mask by indexing would stop the host until the
+                # solve ends, and the stiffness samples could not be queued beside it)
+                e = torch.linalg.norm(s - self.s_t, dim=1) / torch.linalg.norm(self.s_t, dim=1)
+                e = torch.where(stat == 0, e, torch.zeros_like(e))
+                J_pl = torch.linalg.vector_norm(e, ord=10) / s.shape[0]
         C = ag.dmn_stiffness(self.m_el, self.lam_e, self.Q_e, self.p, self.q, w)
         J = stiffness_loss(C, self.C_t)
         if self.m_pl is not None:
-            s, _, stat = ag.dmn_stress(self.m_pl, self.lam_p, self.Q_p, self.zE, self.E_p, self.z_st, self.p, self.q, w)
-            ok = stat == 0
-            e = torch.linalg.norm((s - self.s_t)[ok], dim=1) / torch.linalg.norm(self.s_t[ok], dim=1)
-            J = J + torch.linalg.vector_norm(e, ord=10) / s.shape[0]
+            torch.cuda.current_stream().wait_stream(self.side)
+            J = J + J_pl
         pen = self.lam_pen * (torch.clamp(self.v, min=0.0).sum() - 1.0) ** 2
         return J + pen, C
 
