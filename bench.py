@@ -697,7 +697,7 @@ def run_train(args):
     torch.cuda.set_device(dev)
     target = W.tree_d10_fit(K_DEPTH, seed=SEED_TREE + 31)
     tr = training.Trainer(K_DEPTH, target, TRAIN_SAMPLES, seed=SEED_TREE + 32, elastic_matrix=W.Phase(0, 3000.0, 0.35),
-                          plastic=W.MATRIX, n_plastic=TRAIN_SAMPLES)
+                          plastic=W.MATRIX, n_plastic=TRAIN_SAMPLES, plastic_precision=args.train_plastic)
     tr.train(args.warmup)
     clocks = ClockSampler("0")
     t = tr.train(args.steps)
@@ -710,7 +710,8 @@ def run_train(args):
             "config": {"workload": "K=8, %d stiffness samples (elastic phases) + %d stress samples (one J2 increment),"
                                    " target = seeded DMN, AMSGrad + cosine schedule (Sec. 4.4); step = epoch"
                                    % (TRAIN_SAMPLES, TRAIN_SAMPLES),
-                       "dmn_updates_per_epoch": n_upd},
+                       "dmn_updates_per_epoch": n_upd,
+                       "plastic_samples_precision": args.train_plastic},
             "gp_updates_per_s": n_upd * args.steps / t,
             "compression": {"handle_rebuilds": tr.rebuilds, "leaves_left": int(tr.pattern.sum()),
                             "leaves": 1 << K_DEPTH},
@@ -741,6 +742,8 @@ def main():
                     help="points of the timed batch recomputed by the oracle for the error statement")
     ap.add_argument("--matrix", default="linear", choices=["linear", "explin"],
                     help="matrix law of the k8 workloads: linear hardening (default) or the paper's exp-linear")
+    ap.add_argument("--train-plastic", default="mixed-f32-tangent", choices=["f64", "mixed", "mixed-f32-tangent"],
+                    help="precision of the training workload's plastic forward solves (the adjoint is FP64)")
     ap.add_argument("--shape", type=int, default=3, choices=[3, 4, 6],
                     help="shape functions of the angle interpolation: 3 linear (default, D10 fit), 4 tri-linear, "
                          "6 quadratic (seeded nodal angles)")
