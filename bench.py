@@ -706,7 +706,7 @@ def run_train(args):
     n_upd = TRAIN_SAMPLES * 6 + TRAIN_SAMPLES          # updates per epoch (forward), each with its adjoint
     line = {"metric": "DMN offline training: samples/s (forward + adjoint) at depth 8", "unit": "samples/s",
             "value": 2 * TRAIN_SAMPLES * args.steps / t, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "dtype": "f64" if args.train_plastic == "f64" else "f32+f64", "data": "synthetic",
             "config": {"workload": "K=8, %d stiffness samples (elastic phases) + %d stress samples (one J2 increment),"
                                    " target = seeded DMN, AMSGrad + cosine schedule (Sec. 4.4); step = epoch"
                                    % (TRAIN_SAMPLES, TRAIN_SAMPLES),
