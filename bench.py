@@ -697,7 +697,8 @@ def run_train(args):
     torch.cuda.set_device(dev)
     target = W.tree_d10_fit(K_DEPTH, seed=SEED_TREE + 31)
     tr = training.Trainer(K_DEPTH, target, TRAIN_SAMPLES, seed=SEED_TREE + 32, elastic_matrix=W.Phase(0, 3000.0, 0.35),
-                          plastic=W.MATRIX, n_plastic=TRAIN_SAMPLES, plastic_precision=args.train_plastic)
+                          plastic=W.MATRIX, n_plastic=TRAIN_SAMPLES, plastic_precision=args.train_plastic,
+                          elastic_precision=args.train_elastic)
     tr.train(args.warmup)
     clocks = ClockSampler("0")
     t = tr.train(args.steps)
@@ -706,12 +707,13 @@ def run_train(args):
     n_upd = TRAIN_SAMPLES * 6 + TRAIN_SAMPLES          # updates per epoch (forward), each with its adjoint
     line = {"metric": "DMN offline training: samples/s (forward + adjoint) at depth 8", "unit": "samples/s",
             "value": 2 * TRAIN_SAMPLES * args.steps / t, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "dtype": "f64" if args.train_plastic == "f64" else "f32+f64", "data": "synthetic",
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "dtype": "f64" if args.train_plastic == args.train_elastic == "f64" else "f32+f64", "data": "synthetic",
             "config": {"workload": "K=8, %d stiffness samples (elastic phases) + %d stress samples (one J2 increment),"
                                    " target = seeded DMN, AMSGrad + cosine schedule (Sec. 4.4); step = epoch"
                                    % (TRAIN_SAMPLES, TRAIN_SAMPLES),
                        "dmn_updates_per_epoch": n_upd,
-                       "plastic_samples_precision": args.train_plastic},
+                       "plastic_samples_precision": args.train_plastic,
+                       "stiffness_samples_precision": args.train_elastic},
             "gp_updates_per_s": n_upd * args.steps / t,
             "compression": {"handle_rebuilds": tr.rebuilds, "leaves_left": int(tr.pattern.sum()),
                             "leaves": 1 << K_DEPTH},
@@ -744,6 +746,8 @@ def main():
                     help="matrix law of the k8 workloads: linear hardening (default) or the paper's exp-linear")
     ap.add_argument("--train-plastic", default="mixed-f32-tangent", choices=["f64", "mixed", "mixed-f32-tangent"],
                     help="precision of the training workload's plastic forward solves (the adjoint is FP64)")
+    ap.add_argument("--train-elastic", default="mixed-f32-tangent", choices=["f64", "mixed", "mixed-f32-tangent"],
+                    help="precision of the training workload's stiffness-sample forward solves")
     ap.add_argument("--shape", type=int, default=3, choices=[3, 4, 6],
                     help="shape functions of the angle interpolation: 3 linear (default, D10 fit), 4 tri-linear, "
                          "6 quadratic (seeded nodal angles)")

@@ -25,13 +25,13 @@ weight by several times its value; the weights' rate is scaled by
 min(1, 8 / 2^K) (`lr_scale_v`), which bounds a step at about a tenth of a
 weight.
 
-The plastic samples' forward solves use, by default, the mixed form with an FP32
-tangent (`plastic_precision`): the Newton iteration stops on the same FP64 residual
-criterion, so the stresses the loss reads are the FP64 solution's (to about 1e-11),
-and the adjoint recomputes in FP64 at the converged jumps.  Those solves are
-latency-bound (few points, many line-search steps), and the FP32 condensation has
-shorter dependency chains: at K = 8 the epoch of 4096 + 4096 samples took 55 ms
-instead of 104 ms with FP64 solves, with the same losses to six digits.
+The forward solves use, by default, the mixed form with an FP32 tangent
+(`plastic_precision`, `elastic_precision`): the Newton iteration stops on the same
+FP64 residual criterion, so the stresses the loss reads are the FP64 solution's (to
+about 1e-11), and the adjoint recomputes in FP64 at the converged jumps.  The plastic
+solves are latency-bound (few points, many line-search steps), and the FP32
+condensation has shorter dependency chains.  At K = 8 an epoch of 4096 + 4096 samples
+takes 49 ms, against 104 ms with FP64 solves, with the same losses to six digits.
 
 A weight that reaches zero stays there (the Macaulay bracket has no gradient
 below zero), and the tree is compressed (Sec. 3.1): with `compress` (default)
@@ -93,7 +93,7 @@ class Trainer:
 
     def __init__(self, K, target, n_stiff, seed, elastic_matrix, plastic=None, n_plastic=0, lam_pen=1e3,
                  w_floor=1e-9, alpha_max=1.5e-2, alpha_min=1.5e-3, lr_scale_v=None, compress=True,
-                 plastic_precision="mixed-f32-tangent"):
+                 plastic_precision="mixed-f32-tangent", elastic_precision="mixed-f32-tangent"):
         import torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
         rng = np.random.default_rng(seed)
@@ -101,6 +101,7 @@ class Trainer:
         self.K, self.lam_pen, self.w_floor, self.compress_on = K, lam_pen, w_floor, compress
         self.rebuilds = 0
         self.pl_prec = plastic_precision
+        self.el_prec = elastic_precision
         self.side = torch.cuda.Stream()   # the plastic samples' stream (see loss)
         self.alpha = (alpha_min, alpha_max)
         d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(self.dev)
@@ -116,7 +117,7 @@ class Trainer:
         self.pl_phases = None if plastic is None else (W.FIBER, plastic)
         start = W.TreeParams(K, M, self.p.detach().cpu().numpy(), self.q.detach().cpu().numpy(), v0 / v0.sum(),
                              el_phases)
-        self.m_el = dmn.DMN(start)
+        self.m_el = dmn.DMN(start, precision=elastic_precision)
         self.pattern = v0 > 0
         tgt_el = dmn.DMN(W.TreeParams(K, M, target.p, target.q, target.w, el_phases))
         A2, lam, Q = W.orientation_field(n_stiff, seed=seed + 1)
@@ -158,7 +159,7 @@ class Trainer:
         self.rebuilds += 1
         p, q, wn = (x.detach().cpu().numpy() for x in (self.p, self.q, w))
         self.m_el.close()
-        self.m_el = dmn.DMN(W.TreeParams(self.K, 3, p, q, wn, self.el_phases))
+        self.m_el = dmn.DMN(W.TreeParams(self.K, 3, p, q, wn, self.el_phases), precision=self.el_prec)
         if self.m_pl is not None:
             self.m_pl.close()
             self.m_pl = dmn.DMN(W.TreeParams(self.K, 3, p, q, wn, self.pl_phases), line_search=True,
