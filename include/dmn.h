@@ -251,7 +251,7 @@ int dmn_set_params(dmn_handle* h, int32_t tree_id, const double* p, const double
  * produced state_out (its output, read only) from state_in; points whose
  * update did not converge should get g_stress = 0.  One tree per handle
  * (tree_id must be NULL).  The first call with a larger n than any earlier
- * call (up to 16384 points per chunk) allocates work space.  Errors:
+ * call (up to 65536 points per chunk, about 71 KB each at K = 8) allocates work space.  Errors:
  * DMN_ERR_ARG for NULL arrays, n < 0, a non-NULL tree_id or a handle with
  * several trees. */
 int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam, const double* Q, const double* E_n,

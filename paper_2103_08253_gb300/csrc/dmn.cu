@@ -1477,7 +1477,7 @@ int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam
     return fail(h, DMN_ERR_ARG, "dmn_grad: NULL array");
   const Tree& T = h->trees[0];
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t chunk = std::min<int64_t>(n, 16384);
+  const int64_t chunk = std::min<int64_t>(n, 65536);   // few points per chunk leave the adjoint latency-bound
   const size_t fields = grad_fields(T.N, T.L);
   cudaError_t e;
   if (chunk > h->gwork_cap) {
