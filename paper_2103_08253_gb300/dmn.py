@@ -85,6 +85,9 @@ def load_library(build_if_missing: bool = True):
     lib.dmn_profile_enable.restype = ctypes.c_int
     lib.dmn_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.dmn_profile_read.restype = ctypes.c_int
+    lib.dmn_update_noalloc.argtypes = [ctypes.POINTER(TreeDesc_), ctypes.POINTER(Options_), i64,
+                                       vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.dmn_update_noalloc.restype = ctypes.c_int
     lib.dmn_last_error.argtypes = [vp]
     lib.dmn_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -95,16 +98,21 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def _check_dev(name, t, dtype, shape):
+def _check_dev(name, t, dtype, shape, device=None):
+    """Raise unless t is a contiguous CUDA tensor of dtype, of shape `shape` (a tuple, or a list of
+    accepted tuples), on `device` if given (the device whose memory the library's kernels read)."""
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError("%s must be a CUDA tensor" % name)
+    if device is not None and t.device != device:
+        raise ValueError("%s is on %s, the handle on %s" % (name, t.device, device))
     if t.dtype != dtype:
         raise TypeError("%s must be %s" % (name, dtype))
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
-    if tuple(t.shape) != tuple(shape):
-        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    shapes = shape if isinstance(shape, list) else [shape]
+    if tuple(t.shape) not in [tuple(x) for x in shapes]:
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), " or ".join(str(tuple(x)) for x in shapes)))
 
 
 def _check_host(name, t, dtype, shape):
@@ -117,6 +125,61 @@ def _check_host(name, t, dtype, shape):
         raise ValueError("%s must be contiguous" % name)
     if tuple(t.shape) != tuple(shape):
         raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+
+
+def _fill_desc(d, tr):
+    """Fill the dmn_tree_desc d from a tree object; returns the arrays d points into (keep them alive)."""
+    import numpy as np
+    dp = ctypes.POINTER(ctypes.c_double)
+    keep = [np.ascontiguousarray(x, dtype=np.float64).reshape(-1) for x in (tr.p, tr.q, tr.w)]
+    d.K, d.M = int(tr.K), int(tr.M)
+    d.p, d.q, d.w = (a.ctypes.data_as(dp) for a in keep)
+    for f, ph in enumerate(tr.phases):
+        d.phase[f] = Phase_(int(ph.kind), float(ph.E), float(ph.nu), float(ph.sigma0), float(ph.H),
+                            float(getattr(ph, "sigma_inf", 0.0)), float(getattr(ph, "k0", 0.0)))
+    return keep
+
+
+def update_noalloc(tree, lam, Q, E_n, dE, state_in, out=None, tol=1e-12, max_iter=50):
+    """dmn_update_noalloc: the FP64 update of one uncompressed tree with no handle, the library allocating
+    no device memory (its work space is a static 64 MiB array; calls that overlap on the GPU race).
+    Arrays as in DMN.update, on lam's device, state [6 (inelastic leaves) + 3 (2^K - 1)][n]; `out`
+    (a dict like DMN.alloc_outputs) is allocated by torch if None.  Returns out."""
+    import torch
+    lib = load_library()
+    n = lam.shape[0]
+    dev = lam.device
+    K = int(tree.K)
+    n_inel = sum(int(ph.kind) != PHASE_ELASTIC for ph in tree.phases)
+    S = 6 * n_inel * (1 << (K - 1)) + 3 * ((1 << K) - 1)
+    if out is None:
+        out = dict(state_out=torch.empty((S, n), dtype=torch.float64, device=dev),
+                   stress=torch.empty((n, 6), dtype=torch.float64, device=dev),
+                   tangent=torch.empty((n, 6, 6), dtype=torch.float64, device=dev),
+                   iters=torch.empty(n, dtype=torch.int32, device=dev),
+                   status=torch.empty(n, dtype=torch.int32, device=dev))
+    for name, t, dtype, shape in (("lam", lam, torch.float64, (n, 2)), ("Q", Q, torch.float64, (n, 9)),
+                                  ("E_n", E_n, torch.float64, (n, 6)), ("dE", dE, torch.float64, (n, 6)),
+                                  ("state_in", state_in, torch.float64, (S, n)),
+                                  ("state_out", out["state_out"], torch.float64, (S, n)),
+                                  ("stress", out["stress"], torch.float64, (n, 6)),
+                                  ("tangent", out["tangent"], torch.float64, (n, 6, 6)),
+                                  ("iters", out["iters"], torch.int32, (n,)),
+                                  ("status", out["status"], torch.int32, (n,))):
+        _check_dev(name, t, dtype, shape, dev)
+    d = TreeDesc_()
+    keep = _fill_desc(d, tree)
+    opt = Options_(float(tol), int(max_iter), PREC_F64, 0, 0, 0, 0)
+    with torch.cuda.device(dev):
+        s = torch.cuda.current_stream(dev).cuda_stream
+        rc = lib.dmn_update_noalloc(ctypes.byref(d), ctypes.byref(opt), n, _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE),
+                                    _ptr(state_in), _ptr(out["state_out"]), _ptr(out["stress"]),
+                                    _ptr(out["tangent"]), _ptr(out["iters"]), _ptr(out["status"]),
+                                    ctypes.c_void_p(s))
+    del keep   # the library copied the parameters during the call
+    if rc != 0:
+        raise RuntimeError("dmn_update_noalloc failed (%d): %s" % (rc, lib.dmn_last_error(None).decode()))
+    return out
 
 
 class DMN:
@@ -133,25 +196,22 @@ class DMN:
 
     def __init__(self, tree, precision: str = "f64", tol: float = 1e-12, max_iter: int = 50, block: int = 0,
                  ctas_per_sm: int = 0, line_search: bool = False, predictor: bool = False):
-        import numpy as np
+        import torch
         self._lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("dmn.DMN needs a CUDA device; the library has no CPU path")
+        # the handle's parameters and scratch live on this device; every call runs there
+        self.device = torch.device("cuda", torch.cuda.current_device())
         trees = list(tree) if isinstance(tree, (list, tuple)) else [tree]
         self.n_trees = len(trees)
         self.K, self.M = int(trees[0].K), int(trees[0].M)
+        self._Ks = [int(tr.K) for tr in trees]
+        self._Ms = [int(tr.M) for tr in trees]
         self.phases = tuple(trees[0].phases)
-        dp = ctypes.POINTER(ctypes.c_double)
         descs = (TreeDesc_ * len(trees))()
         self._keep = []
         for k, tr in enumerate(trees):
-            p = np.ascontiguousarray(tr.p, dtype=np.float64).reshape(-1)
-            q = np.ascontiguousarray(tr.q, dtype=np.float64).reshape(-1)
-            w = np.ascontiguousarray(tr.w, dtype=np.float64).reshape(-1)
-            self._keep += [p, q, w]
-            descs[k].K, descs[k].M = int(tr.K), int(tr.M)
-            descs[k].p, descs[k].q, descs[k].w = p.ctypes.data_as(dp), q.ctypes.data_as(dp), w.ctypes.data_as(dp)
-            for f, ph in enumerate(tr.phases):
-                descs[k].phase[f] = Phase_(int(ph.kind), float(ph.E), float(ph.nu), float(ph.sigma0), float(ph.H),
-                                           float(getattr(ph, "sigma_inf", 0.0)), float(getattr(ph, "k0", 0.0)))
+            self._keep += _fill_desc(descs[k], tr)
         if precision not in PRECISIONS:
             raise ValueError("precision must be one of %s" % (tuple(PRECISIONS),))
         opt = Options_(float(tol), int(max_iter), PRECISIONS[precision], int(block),
@@ -169,8 +229,16 @@ class DMN:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.dmn_destroy(self._h)
+            with self._on_device():
+                self._lib.dmn_destroy(self._h)
             self._h = None
+
+    def _on_device(self):
+        import torch
+        return torch.cuda.device(self.device)
+
+    def _check(self, name, t, dtype, shape):
+        _check_dev(name, t, dtype, shape, self.device)
 
     def __del__(self):
         # at interpreter exit the CUDA runtime may already be torn down; the
@@ -190,13 +258,14 @@ class DMN:
         """A2 [n, 6] float64 CUDA -> (lam [n, 2], Q [n, 9])."""
         import torch
         n = A2.shape[0]
-        _check_dev("A2", A2, torch.float64, (n, 6))
+        self._check("A2", A2, torch.float64, (n, 6))
         lam = torch.empty((n, 2), dtype=torch.float64, device=A2.device) if lam is None else lam
         Q = torch.empty((n, 9), dtype=torch.float64, device=A2.device) if Q is None else Q
-        _check_dev("lam", lam, torch.float64, (n, 2))
-        _check_dev("Q", Q, torch.float64, (n, 9))
-        s = torch.cuda.current_stream(A2.device).cuda_stream
-        rc = self._lib.dmn_interp_orientation(self._h, n, _ptr(A2), _ptr(lam), _ptr(Q), ctypes.c_void_p(s))
+        self._check("lam", lam, torch.float64, (n, 2))
+        self._check("Q", Q, torch.float64, (n, 9))
+        with self._on_device():
+            s = torch.cuda.current_stream(self.device).cuda_stream
+            rc = self._lib.dmn_interp_orientation(self._h, n, _ptr(A2), _ptr(lam), _ptr(Q), ctypes.c_void_p(s))
         if rc != 0:
             self._err("dmn_interp_orientation", rc)
         return lam, Q
@@ -206,7 +275,16 @@ class DMN:
         import numpy as np
         arrs = [np.ascontiguousarray(np.asarray(x, dtype=np.float64)).reshape(-1) for x in (p, q, w)]
         dp = ctypes.POINTER(ctypes.c_double)
-        rc = self._lib.dmn_set_params(self._h, int(tree_id), *(a.ctypes.data_as(dp) for a in arrs))
+        tr = int(tree_id)
+        if not 0 <= tr < self.n_trees:
+            raise ValueError("tree_id must be in 0..%d" % (self.n_trees - 1))
+        K = self._Ks[tr]
+        N = (1 << K) - 1
+        for name, a, size in (("p", arrs[0], N * self._Ms[tr]), ("q", arrs[1], N * self._Ms[tr]), ("w", arrs[2], 1 << K)):
+            if a.size != size:
+                raise ValueError("%s has %d entries, expected %d" % (name, a.size, size))
+        with self._on_device():
+            rc = self._lib.dmn_set_params(self._h, tr, *(a.ctypes.data_as(dp) for a in arrs))
         if rc != 0:
             self._err("dmn_set_params", rc)
 
@@ -220,23 +298,29 @@ class DMN:
         for name, t, shape in (("lam", lam, (n, 2)), ("Q", Q, (n, 9)), ("E_n", E_n, (n, 6)), ("dE", dE, (n, 6)),
                                ("state_in", state_in, (self.state_size, n)),
                                ("state_out", state_out, (self.state_size, n)), ("g_stress", g_stress, (n, 6))):
-            _check_dev(name, t, torch.float64, shape)
+            self._check(name, t, torch.float64, shape)
         z = lambda *sh: torch.zeros(sh, dtype=torch.float64, device=dev)
         g_p = z(N, self.M) if g_p is None else g_p
         g_q = z(N, self.M) if g_q is None else g_q
         g_w = z(1 << self.K) if g_w is None else g_w
+        # the library adds into these: their size bounds its writes
+        self._check("g_p", g_p, torch.float64, (N, self.M))
+        self._check("g_q", g_q, torch.float64, (N, self.M))
+        self._check("g_w", g_w, torch.float64, (1 << self.K,))
         g_E = torch.empty((n, 6), dtype=torch.float64, device=dev) if want_E else None
-        s = torch.cuda.current_stream(dev).cuda_stream
-        rc = self._lib.dmn_grad(self._h, n, None, _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE), _ptr(state_in),
-                                _ptr(state_out), _ptr(g_stress), _ptr(g_p), _ptr(g_q), _ptr(g_w), _ptr(g_E),
-                                ctypes.c_void_p(s))
+        with self._on_device():
+            s = torch.cuda.current_stream(self.device).cuda_stream
+            rc = self._lib.dmn_grad(self._h, n, None, _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE), _ptr(state_in),
+                                    _ptr(state_out), _ptr(g_stress), _ptr(g_p), _ptr(g_q), _ptr(g_w), _ptr(g_E),
+                                    ctypes.c_void_p(s))
         if rc != 0:
             self._err("dmn_grad", rc)
         return g_p, g_q, g_w, g_E
 
     def profile(self, enable: bool):
         """Start (clearing the totals) or stop per-kernel event timing of update()."""
-        rc = self._lib.dmn_profile_enable(self._h, 1 if enable else 0)
+        with self._on_device():
+            rc = self._lib.dmn_profile_enable(self._h, 1 if enable else 0)
         if rc != 0:
             self._err("dmn_profile_enable", rc)
 
@@ -244,7 +328,8 @@ class DMN:
         """(ms of the normals, Newton and final kernels summed over the timed updates, number of updates)."""
         ms = (ctypes.c_double * 3)()
         cnt = ctypes.c_int64()
-        rc = self._lib.dmn_profile_read(self._h, ms, ctypes.byref(cnt))
+        with self._on_device():
+            rc = self._lib.dmn_profile_read(self._h, ms, ctypes.byref(cnt))
         if rc != 0:
             self._err("dmn_profile_read", rc)
         return dict(normals=ms[0], newton=ms[1], final=ms[2]), int(cnt.value)
@@ -264,22 +349,24 @@ class DMN:
         n = lam.shape[0]
         dev = lam.device
         if tree_id is not None:
-            _check_dev("tree_id", tree_id, torch.int32, (n,))
-        _check_dev("lam", lam, torch.float64, (n, 2))
-        _check_dev("Q", Q, torch.float64, (n, 9))
-        _check_dev("E_n", E_n, torch.float64, (n, 6))
-        _check_dev("dE", dE, torch.float64, (n, 6))
-        _check_dev("state_in", state_in, torch.float64, (self.state_size, n))
+            self._check("tree_id", tree_id, torch.int32, (n,))
+        self._check("lam", lam, torch.float64, (n, 2))
+        self._check("Q", Q, torch.float64, (n, 9))
+        self._check("E_n", E_n, torch.float64, (n, 6))
+        self._check("dE", dE, torch.float64, (n, 6))
+        self._check("state_in", state_in, torch.float64, (self.state_size, n))
         out = self.alloc_outputs(n, dev) if out is None else out
-        _check_dev("state_out", out["state_out"], torch.float64, (self.state_size, n))
-        _check_dev("stress", out["stress"], torch.float64, (n, 6))
-        _check_dev("tangent", out["tangent"], torch.float64, (n, 6, 6))
-        _check_dev("iters", out["iters"], torch.int32, (n,))
-        _check_dev("status", out["status"], torch.int32, (n,))
-        s = torch.cuda.current_stream(dev).cuda_stream
-        rc = self._lib.dmn_update(self._h, n, _ptr(tree_id), _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE), _ptr(state_in),
-                                  _ptr(out["state_out"]), _ptr(out["stress"]), _ptr(out["tangent"]),
-                                  _ptr(out["iters"]), _ptr(out["status"]), ctypes.c_void_p(s))
+        self._check("state_out", out["state_out"], torch.float64, (self.state_size, n))
+        self._check("stress", out["stress"], torch.float64, (n, 6))
+        self._check("tangent", out["tangent"], torch.float64, (n, 6, 6))
+        self._check("iters", out["iters"], torch.int32, (n,))
+        self._check("status", out["status"], torch.int32, (n,))
+        with self._on_device():
+            s = torch.cuda.current_stream(self.device).cuda_stream
+            rc = self._lib.dmn_update(self._h, n, _ptr(tree_id), _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE),
+                                      _ptr(state_in), _ptr(out["state_out"]), _ptr(out["stress"]),
+                                      _ptr(out["tangent"]), _ptr(out["iters"]), _ptr(out["status"]),
+                                      ctypes.c_void_p(s))
         if rc != 0:
             self._err("dmn_update", rc)
         return out
@@ -312,11 +399,12 @@ class DMN:
         _check_host("tangent", out["tangent"], torch.float64, (n, 6, 6))
         _check_host("iters", out["iters"], torch.int32, (n,))
         _check_host("status", out["status"], torch.int32, (n,))
-        s = torch.cuda.current_stream().cuda_stream
-        rc = self._lib.dmn_update_host(self._h, n, _ptr(tree_id), _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE),
-                                       _ptr(state_in), _ptr(out["state_out"]), _ptr(out["stress"]),
-                                       _ptr(out["tangent"]), _ptr(out["iters"]), _ptr(out["status"]),
-                                       int(chunk), ctypes.c_void_p(s))
+        with self._on_device():
+            s = torch.cuda.current_stream(self.device).cuda_stream
+            rc = self._lib.dmn_update_host(self._h, n, _ptr(tree_id), _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE),
+                                           _ptr(state_in), _ptr(out["state_out"]), _ptr(out["stress"]),
+                                           _ptr(out["tangent"]), _ptr(out["iters"]), _ptr(out["status"]),
+                                           int(chunk), ctypes.c_void_p(s))
         if rc != 0:
             self._err("dmn_update_host", rc)
         return out

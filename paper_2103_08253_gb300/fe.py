@@ -62,9 +62,9 @@ def _p(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def _stream():
+def _stream(device):
     import torch
-    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
 class Hex8Mesh:
@@ -72,12 +72,19 @@ class Hex8Mesh:
 
     def __init__(self, xyz, conn):
         import numpy as np
+        import torch
         self._lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("fe.Hex8Mesh needs a CUDA device; the library has no CPU path")
+        self.device = torch.device("cuda", torch.cuda.current_device())
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         conn = np.ascontiguousarray(conn, dtype=np.int32)
+        if xyz.ndim != 2 or xyz.shape[1] != 3 or conn.ndim != 2 or conn.shape[1] != 8:
+            raise ValueError("xyz must be [n_nodes, 3] and conn [n_elem, 8]")
         h = ctypes.c_void_p()
-        rc = self._lib.fe_mesh_create(xyz.shape[0], conn.shape[0], xyz.ctypes.data_as(ctypes.c_void_p),
-                                      conn.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+        with torch.cuda.device(self.device):
+            rc = self._lib.fe_mesh_create(xyz.shape[0], conn.shape[0], xyz.ctypes.data_as(ctypes.c_void_p),
+                                          conn.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
         if rc != 0:
             raise ValueError("fe_mesh_create failed (%d): %s" % (rc, self._lib.fe_last_error(None).decode()))
         self._h = h
@@ -89,52 +96,75 @@ class Hex8Mesh:
         if rc != 0:
             raise RuntimeError("%s failed (%d): %s" % (name, rc, self._lib.fe_last_error(self._h).decode()))
 
-    def _vec(self, dev, n=None):
+    def _args(self, **arrays):
+        """Check the arrays of one call against the layouts of fe.h (FP64, contiguous, on the mesh's
+        device): u-like names are [n_dofs], E/sigma [n_gp, 6], C [n_gp, 6, 6] or [n_gp, 36]; None
+        (an optional `free`) is passed through."""
         import torch
-        return torch.empty(n or self.n_dofs, dtype=torch.float64, device=dev)
+        shapes = {"vec": (self.n_dofs,), "gp6": (self.n_gp, 6), "C": [(self.n_gp, 6, 6), (self.n_gp, 36)]}
+        for name, (t, kind) in arrays.items():
+            if t is not None:
+                _dmn._check_dev(name, t, torch.float64, shapes[kind], self.device)
+
+    def _call(self, name, *args):
+        import torch
+        with torch.cuda.device(self.device):
+            self._check(name, getattr(self._lib, name)(self._h, *args, _stream(self.device)))
+
+    def _vec(self):
+        import torch
+        return torch.empty(self.n_dofs, dtype=torch.float64, device=self.device)
 
     def strain(self, u, out=None):
         import torch
-        out = torch.empty((self.n_gp, 6), dtype=torch.float64, device=u.device) if out is None else out
-        self._check("fe_strain", self._lib.fe_strain(self._h, _p(u), _p(out), _stream()))
+        out = torch.empty((self.n_gp, 6), dtype=torch.float64, device=self.device) if out is None else out
+        self._args(u=(u, "vec"), E=(out, "gp6"))
+        self._call("fe_strain", _p(u), _p(out))
         return out
 
     def internal_force(self, sigma, out=None):
-        out = self._vec(sigma.device) if out is None else out
-        self._check("fe_internal_force", self._lib.fe_internal_force(self._h, _p(sigma), _p(out), _stream()))
+        out = self._vec() if out is None else out
+        self._args(sigma=(sigma, "gp6"), f=(out, "vec"))
+        self._call("fe_internal_force", _p(sigma), _p(out))
         return out
 
     def apply_tangent(self, C, v, out=None):
-        out = self._vec(v.device) if out is None else out
-        self._check("fe_apply_tangent", self._lib.fe_apply_tangent(self._h, _p(C), _p(v), _p(out), _stream()))
+        out = self._vec() if out is None else out
+        self._args(C=(C, "C"), v=(v, "vec"), Kv=(out, "vec"))
+        self._call("fe_apply_tangent", _p(C), _p(v), _p(out))
         return out
 
     def tangent_diagonal(self, C, out=None):
-        out = self._vec(C.device) if out is None else out
-        self._check("fe_tangent_diagonal", self._lib.fe_tangent_diagonal(self._h, _p(C), _p(out), _stream()))
+        out = self._vec() if out is None else out
+        self._args(C=(C, "C"), diag=(out, "vec"))
+        self._call("fe_tangent_diagonal", _p(C), _p(out))
         return out
 
     def pcg(self, C, free, diag, b, x, rtol=1e-8, max_iter=20000, f32=False):
         """Jacobi-PCG on the free dofs (f32: products K p in FP32, fe_pcg_f32); returns
         (iterations, relative residual)."""
+        self._args(C=(C, "C"), free=(free, "vec"), diag=(diag, "vec"), b=(b, "vec"), x=(x, "vec"))
         it = ctypes.c_int32()
         rr = ctypes.c_double()
-        name = "fe_pcg_f32" if f32 else "fe_pcg"
-        self._check(name, getattr(self._lib, name)(self._h, _p(C), _p(free), _p(diag), _p(b), _p(x), float(rtol),
-                                                   int(max_iter), ctypes.byref(it), ctypes.byref(rr), _stream()))
+        self._call("fe_pcg_f32" if f32 else "fe_pcg", _p(C), _p(free), _p(diag), _p(b), _p(x), float(rtol),
+                   int(max_iter), ctypes.byref(it), ctypes.byref(rr))
         return it.value, rr.value
 
     def dot(self, a, b, free=None):
+        self._args(a=(a, "vec"), b=(b, "vec"), free=(free, "vec"))
         out = ctypes.c_double()
-        self._check("fe_dot", self._lib.fe_dot(self._h, _p(a), _p(b), _p(free), ctypes.byref(out), _stream()))
+        self._call("fe_dot", _p(a), _p(b), _p(free), ctypes.byref(out))
         return out.value
 
     def axpy(self, alpha, x, y, free=None):
-        self._check("fe_axpy", self._lib.fe_axpy(self._h, float(alpha), _p(x), _p(free), _p(y), _stream()))
+        self._args(x=(x, "vec"), y=(y, "vec"), free=(free, "vec"))
+        self._call("fe_axpy", float(alpha), _p(x), _p(free), _p(y))
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.fe_mesh_destroy(self._h)
+            import torch
+            with torch.cuda.device(self.device):
+                self._lib.fe_mesh_destroy(self._h)
             self._h = None
 
     def __del__(self):

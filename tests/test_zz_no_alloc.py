@@ -97,3 +97,28 @@ def test_noalloc_rejects_what_it_cannot_do():
     d.K = 9
     rc = lib.dmn_update_noalloc(ctypes.byref(d), None, 8, *([None] * 10), None)
     assert rc == -1 and "K must be" in lib.dmn_last_error(None).decode()
+
+
+def test_python_binding_matches_dmn_update():
+    """dmn.update_noalloc (the binding of the same entry point) on a depth-5 tree, along a plastic
+    path: statuses and iteration counts equal, stress and tangent within 1e-10 of dmn_update."""
+    K, n = 5, 777
+    tree = W.tree_d10_fit(K, seed=126)
+    A2, lam, Q = W.orientation_field(n, seed=127)
+    Ef = W.random6_path_final(n, 0.03, seed=128)
+    m = dmn.DMN(tree, precision="f64")
+    lam_d, Q_d = torch.from_numpy(lam).to(DEV), torch.from_numpy(Q).to(DEV)
+    st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+    for step in range(1, 6):
+        En, dE = W.proportional_increment(Ef, step, 8)
+        args = (lam_d, Q_d, torch.from_numpy(En).to(DEV), torch.from_numpy(dE).to(DEV), st)
+        ref = m.update(*args)
+        out = dmn.update_noalloc(tree, *args)
+        torch.cuda.synchronize()
+        assert torch.equal(out["status"], ref["status"]) and torch.equal(out["iters"], ref["iters"])
+        ok = (ref["status"] == 0).cpu().numpy()
+        assert ok.mean() > 0.99
+        assert _rel(out["stress"].cpu().numpy()[ok], ref["stress"].cpu().numpy()[ok]) <= 1e-10
+        assert _rel(out["tangent"].cpu().numpy()[ok], ref["tangent"].cpu().numpy()[ok]) <= 1e-10
+        st = ref["state_out"]
+    m.close()
