@@ -277,6 +277,38 @@ def test_interp_orientation_against_oracle():
     m.close()
 
 
+def test_interp_orientation_at_the_triangle_corners():
+    """Orientation tensors with repeated eigenvalues: the corners UD (1, 0, 0), ISO (1/3, 1/3, 1/3) and
+    PI (1/2, 1/2, 0) of the triangle and points 1e-9 and 1e-12 away, unrotated and in random frames.
+    The eigenvalues are unique and must match the oracle's; the eigenframe within a repeated
+    eigenvalue is not, so Q must be a right-handed orthonormal frame that reproduces A2.  The update
+    on the GPU's (lam, Q) must then match the oracle's on the same (lam, Q)."""
+    rng = np.random.default_rng(92)
+    spectra = [(1.0, 0.0, 0.0), (1 / 3, 1 / 3, 1 / 3), (0.5, 0.5, 0.0), (1 - 2e-9, 1e-9, 1e-9),
+               (0.5 + 1e-12, 0.5 - 1e-12, 0.0)]
+    R = np.concatenate([np.eye(3)[None], W.haar_rotations(rng, 24)])
+    A = np.einsum("rik,sk,rjk->srij", R, np.array(spectra), R).reshape(-1, 3, 3)
+    A2 = np.ascontiguousarray(A[:, [0, 1, 2, 1, 0, 0], [0, 1, 2, 2, 2, 1]])
+    n = A2.shape[0]
+    m = dmn.DMN(W.tree_d10_fit(2, seed=1))
+    lam_g, Q_g = m.interp_orientation(d(A2))
+    m.close()
+    lam, Q = lam_g.cpu().numpy(), Q_g.cpu().numpy()
+    assert np.isfinite(lam).all() and np.isfinite(Q).all()
+    lo, _ = oracle.interp_orientation(A2)
+    np.testing.assert_allclose(lam, lo, atol=1e-13)
+    Qm = Q.reshape(n, 3, 3)
+    np.testing.assert_allclose(np.einsum("nki,nkj->nij", Qm, Qm), np.broadcast_to(np.eye(3), (n, 3, 3)), atol=1e-13)
+    np.testing.assert_allclose(np.linalg.det(Qm), 1.0, atol=1e-13)
+    l3 = np.stack([lam[:, 0], lam[:, 1], A2[:, :3].sum(1) - lam.sum(1)], 1)
+    np.testing.assert_allclose(np.einsum("nij,nj,nkj->nik", Qm, l3, Qm), A, atol=1e-13)
+    tree = W.tree_d10_fit(4, seed=93)
+    Ef = W.random6_path_final(n, 0.025, seed=94)
+    worst, _, _ = run_path(tree, lam, Q, Ef, 4, "f64")
+    assert worst["stress"] <= 1e-10 and worst["tangent"] <= 1e-10, worst
+    assert worst["iters_mismatch"] <= 0.005 * n * 4, worst
+
+
 def test_repeatable_bitwise():
     K, n = 6, 500
     tree = W.tree_d10_fit(K, seed=95)
