@@ -309,6 +309,35 @@ def test_interp_orientation_at_the_triangle_corners():
     assert worst["iters_mismatch"] <= 0.005 * n * 4, worst
 
 
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_points_are_independent_of_the_batch(prec):
+    """Every point's update depends on that point alone: 65,537 points at depth 6 (more than one
+    point per lane of the persistent kernel) give bit for bit the results of the same points
+    updated as two uneven parts in the reverse order."""
+    K, n, cut = 6, 65537, 40001
+    tree = W.tree_d10_fit(K, seed=97)
+    A2, lam, Q = W.orientation_field(n, seed=98)
+    Ef = W.random6_path_final(n, 0.03, seed=99)
+    m = dmn.DMN(tree, precision=prec)
+    lam_d, Q_d = d(lam), d(Q)
+    st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+    for s in range(1, 4):
+        En, dE = W.proportional_increment(Ef, s, 20)
+        En_d, dE_d = d(En), d(dE)
+        whole = m.update(lam_d, Q_d, En_d, dE_d, st)
+        parts = {}
+        for a, b in ((cut, n), (0, cut)):
+            o = m.update(lam_d[a:b], Q_d[a:b], En_d[a:b], dE_d[a:b], st[:, a:b].contiguous())
+            for k, v in o.items():
+                parts.setdefault(k, [None, None])[0 if a == 0 else 1] = v
+        for k, (lo, hi) in parts.items():
+            joined = torch.cat([lo, hi], dim=1 if k == "state_out" else 0)
+            assert torch.equal(joined, whole[k]), (prec, s, k)
+        assert (whole["status"] == 0).all()
+        st = whole["state_out"]
+    m.close()
+
+
 def test_repeatable_bitwise():
     K, n = 6, 500
     tree = W.tree_d10_fit(K, seed=95)
