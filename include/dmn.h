@@ -39,8 +39,11 @@
  *     launched; DMN_ERR_CUDA (-2) a CUDA call failed (dmn_last_error has the
  *     message).  Kernels never trap: per-point failures are reported in the
  *     status array.
- *   - One handle may have one update in flight at a time: concurrent calls
- *     on the same handle share its work space and race.
+ *   - One handle may have one call in flight at a time (dmn_update,
+ *     dmn_update_host, dmn_grad or dmn_set_params): calls on the same handle
+ *     share its work space, and a call that grows a buffer waits only for its
+ *     own stream before freeing the old one.  Calls on different streams must
+ *     be ordered by the caller (events); different handles are independent.
  */
 #ifndef DMN_H
 #define DMN_H
