@@ -44,6 +44,10 @@
  *     share its work space, and a call that grows a buffer waits only for its
  *     own stream before freeing the old one.  Calls on different streams must
  *     be ordered by the caller (events); different handles are independent.
+ *   - A handle belongs to the CUDA device that was current when dmn_create
+ *     ran: its parameters and work space live there.  Make that device
+ *     current for every later call, and pass arrays in its memory (or, for
+ *     dmn_update_host, in host memory).
  */
 #ifndef DMN_H
 #define DMN_H

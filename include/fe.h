@@ -29,6 +29,10 @@
  *     stream unless stated otherwise.
  *   - Return codes: 0 success, -1 invalid argument (nothing launched),
  *     -2 a CUDA call failed; fe_last_error gives the message.
+ *   - A mesh belongs to the CUDA device that was current when fe_mesh_create
+ *     ran; make that device current for every later call on it.  One call
+ *     per mesh may be in flight at a time: its element vectors, partial sums
+ *     and CG vectors are work space shared by all calls.
  */
 #ifndef FE_H
 #define FE_H
