@@ -1,0 +1,53 @@
+"""Host-side arithmetic of the benchmark: the algorithmic flop counts behind the
+roofline fraction.
+
+The per-laminate and per-leaf counts are constants counted from the kernels'
+arithmetic.  These tests pin what follows from them and from the tree's
+structure: the per-pass totals of the full depth-8 tree (31,548 FP64 and
+168,499 condensation flops) and of the benchmark's compressed tree (178
+laminates), and the structure of compressed trees against the oracle's own
+compression, whose state holds 6 values per inelastic leaf and 3 per laminate.
+"""
+import numpy as np
+
+import bench
+import oracle
+from paper_2103_08253_gb300 import workloads as W
+
+
+def test_full_tree_counts_and_flops_per_pass():
+    for K in range(1, 9):
+        L = 1 << K
+        assert bench.tree_counts(np.ones(L)) == dict(N=L - 1, pairs=L // 2, inner=L // 2 - 1, single=0,
+                                                     el=L // 2, j2=L // 2)
+    # 255 x (39 + 44) + 128 x 13 + 128 x 68 + 15; 127 x (678 + 39) + 128 x 605
+    assert bench.pass_flops(8) == (31548, 168499)
+    assert bench.corr_flops(8) == (255 * 3, 255 * 39)
+
+
+def test_compressed_tree_structure_against_the_oracle():
+    rng = np.random.default_rng(7)
+    phases = (W.FIBER, W.MATRIX)
+    for _ in range(300):
+        K = int(rng.integers(1, 9))
+        L = 1 << K
+        w = rng.dirichlet(np.ones(L))
+        w[rng.random(L) < rng.uniform(0.0, 0.9)] = 0.0
+        if not (w > 0).any():
+            w[rng.integers(L)] = 1.0
+        c = bench.tree_counts(w)
+        leaves = int((w > 0).sum())
+        assert c["el"] + c["j2"] == leaves
+        assert c["N"] == leaves - 1                      # a full binary tree over the remaining leaves
+        assert c["pairs"] + c["inner"] == c["N"]
+        if c["N"] > 0:                                   # each leaf hangs below one laminate
+            assert 2 * c["pairs"] + c["single"] == leaves
+        assert oracle.state_size(K, phases, w) == 6 * c["j2"] + 3 * c["N"], (K, w)
+
+
+def test_benchmark_compressed_tree():
+    tree = W.tree_with_zero_weights(bench.K_DEPTH, seed=bench.SEED_TREE)
+    c = bench.tree_counts(tree.w)
+    assert c["N"] == 178
+    f64, ft = bench.pass_flops(bench.K_DEPTH, tree.w)
+    assert round(f64 / 100) == 218 and round(ft / 100) == 1191     # 21.8 k + 119.1 k per pass
