@@ -125,3 +125,46 @@ def test_update_is_capturable_in_a_cuda_graph():
                 assert torch.equal(outs[s][k], eager[s][k]) or torch.allclose(outs[s][k], eager[s][k], equal_nan=True), (s, k)
         assert torch.equal(bufs[n_steps % 2], eager[-1]["state_out"])
     m.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_eight_trees_in_one_handle(prec):
+    """The largest handle: 8 trees, depths 1-8, the exponential-linear matrix on every other
+    tree, points of all trees interleaved at random; each point against the oracle on its tree."""
+    rng = np.random.default_rng(600)
+    trees = [W.tree_d10_fit(K, seed=600 + K, phases=(W.FIBER, W.MATRIX_EXPLIN if K % 2 else W.MATRIX))
+             for K in range(1, 9)]
+    n = 8 * 61 + 3
+    tid = rng.permutation(np.arange(n) % 8).astype(np.int32)
+    A2, lam, Q = W.orientation_field(n, seed=601)
+    Ef = W.random6_path_final(n, 0.025, seed=602)
+    m = dmn.DMN(trees, precision=prec)
+    assert m.n_trees == dmn.MAX_TREES
+    assert m.tree_state_sizes == [W.state_size(t.K, t.phases) for t in trees]
+    st_g = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+    st_o = [np.zeros((m.tree_state_sizes[k], int((tid == k).sum()))) for k in range(8)]
+    worst = [0.0, 0.0]
+    alive = np.ones(n, dtype=bool)     # converged on both sides in every increment so far
+    for s in range(1, 5):
+        En, dE = W.proportional_increment(Ef, s, 10)
+        out = m.update(d(lam), d(Q), d(En), d(dE), st_g, tree_id=d(tid))
+        st_g = out["state_out"]
+        sig, C, stat = out["stress"].cpu().numpy(), out["tangent"].cpu().numpy(), out["status"].cpu().numpy()
+        it = out["iters"].cpu().numpy()
+        for k in range(8):
+            idx = np.nonzero(tid == k)[0]
+            st_o[k], so, Co, io, sto, gap = oracle.update(trees[k], lam[idx], Q[idx], En[idx], dE[idx], st_o[k])
+            # a point at max_iter keeps a rounding-dependent state: it leaves the comparison for good
+            alive[idx] &= (sto == 0) & (stat[idx] == 0)
+            a = alive[idx]
+            worst[0] = max(worst[0], rel(sig[idx][a], so[a]).max(initial=0.0))
+            ok = a & (gap > 1e-9)
+            worst[1] = max(worst[1], rel(C[idx][ok], Co[ok]).max(initial=0.0))
+            if prec == "f64":
+                assert np.abs(it[idx][a] - io[a]).max(initial=0) <= 1
+            sg = st_g[: m.tree_state_sizes[k]][:, idx[a]].cpu().numpy()
+            ref = st_o[k][:, a]
+            assert np.abs(sg - ref).max(initial=0.0) <= 1e-7 * (np.abs(ref).max(initial=0.0) + 1e-30), (k, s)
+    assert worst[0] <= TOL[prec] and worst[1] <= TOL[prec], worst
+    assert alive.mean() > 0.97
+    m.close()
