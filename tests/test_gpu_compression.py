@@ -151,3 +151,43 @@ def test_single_leaf_parameters_and_gradient():
     g_p, g_q, g_w, g_E = m.grad(d(lam), d(Q), d(En), d(dE), st0, o["state_out"], d(np.ones((5, 6))))
     assert float(g_p.abs().max()) == 0.0 and float(g_q.abs().max()) == 0.0 and float(g_w.abs().max()) == 0.0
     m.close()
+
+
+@pytest.mark.parametrize("prec,ls", [("f64", True), ("mixed-f32-tangent", False), ("mixed-f32-tangent", True)])
+def test_compressed_tree_with_line_search_and_fp32_tangent(prec, ls):
+    """The table-driven traversal in its other instantiations: the line search (large cyclic
+    steps, where it halves) and the mixed form with an FP32 tangent, against the oracle with the
+    same options on a depth-7 tree compressed to 90 leaves."""
+    K, n, n_steps = 7, 200, 8
+    tree = W.tree_with_zero_weights(K, seed=540)
+    A2, lam, Q = W.orientation_field(n, seed=541)
+    amp = W.random6_path_final(n, 0.025, seed=542)
+    m = dmn.DMN(tree, precision=prec, line_search=ls)
+    S = oracle.state_size(K, tree.phases, tree.w)
+    assert m.state_size == S
+    st_g = torch.zeros((S, n), dtype=torch.float64, device=DEV)
+    st_o = np.zeros((S, n))
+    tol_s, tol_c = (1e-10, 1e-10) if prec == "f64" else (1e-6, 1e-4)
+    worst = [0.0, 0.0, 0.0]
+    alive = np.ones(n, dtype=bool)
+    for s in range(1, n_steps + 1):
+        En, dE = W.cyclic_increment(amp, s, n_steps) if ls else W.proportional_increment(amp, s, 20)
+        out = m.update(d(lam), d(Q), d(En), d(dE), st_g)
+        st_g = out["state_out"]
+        st_o, so, Co, io, sto, gap = oracle.update(tree, lam, Q, En, dE, st_o, line_search=ls)
+        stat = out["status"].cpu().numpy()
+        alive &= (sto == 0) & (stat == 0)
+        sig, C, it = out["stress"].cpu().numpy(), out["tangent"].cpu().numpy(), out["iters"].cpu().numpy()
+        worst[0] = max(worst[0], rel(sig[alive], so[alive]).max(initial=0.0))
+        ok = alive & (gap > 1e-9)
+        worst[1] = max(worst[1], rel(C[ok], Co[ok]).max(initial=0.0))
+        sg = st_g.cpu().numpy()
+        scale = np.abs(st_o[:, alive]).max(axis=1, keepdims=True) + 1e-300
+        worst[2] = max(worst[2], (np.abs(sg[:, alive] - st_o[:, alive]) / scale).max(initial=0.0))
+        if prec == "f64":
+            assert np.abs(it[alive] - io[alive]).max(initial=0) <= 1
+    print(prec, ls, "worst", worst, "alive", alive.mean())
+    assert worst[0] <= tol_s and worst[1] <= tol_c, worst
+    assert worst[2] <= (1e-9 if prec == "f64" else 1e-5), worst
+    assert alive.mean() > 0.97
+    m.close()
