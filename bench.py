@@ -20,6 +20,11 @@ flush is needed between steps.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
 bounded sample of the same workload instead.
+
+The oracle runs only in the CPU-baseline leg (N = 1): timed on a bounded sample
+(``cpu_baseline``) and, untimed, on --parity-points sampled points of the timed
+batch, whose results it compares with the GPU's (each form's
+``parity_vs_oracle``).  No result of the GPU path comes from it.
 """
 from __future__ import annotations
 
@@ -392,7 +397,8 @@ def run_form(form, ctx, args, dist):
 
 
 def parity_sample(form, r, ctx, args, pidx):
-    """Oracle on the sampled points through increments 1..warmup+steps, compared with the GPU."""
+    """CPU-baseline leg, untimed part: the oracle on the sampled points through increments
+    1..warmup+steps, compared with the GPU's results there (the form's error statement)."""
     import oracle
     tree, A2, Ef = ctx["tree"], ctx["A2_np"], ctx["Ef_np"]
     _, pred = form_opts(form)
@@ -807,7 +813,7 @@ def run_gpu(args):
     results, e2e = {}, None
     for form in forms:
         r = run_form(form, ctx, args, dist)
-        if rank == 0 and args.parity_points > 0:
+        if world == 1 and args.parity_points > 0:     # the CPU-baseline leg: N = 1 only
             r["parity"] = parity_sample(form, r, ctx, args, pidx)
         if form == "f64" and args.e2e_steps != 0:
             e2e = run_e2e(r, ctx, args, dist)
