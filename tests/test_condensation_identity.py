@@ -126,3 +126,42 @@ def test_condensation_is_the_newton_step(K, M, history):
         np.testing.assert_allclose(s_root, s_lin, rtol=0, atol=1e-9 * np.abs(s_lin).max())
         # and the plain average of the leaf stresses is the oracle's sigma_bar
         np.testing.assert_allclose(w @ ns["sig"], ns["sbar"], rtol=0, atol=1e-12 * np.abs(ns["sbar"]).max())
+
+
+def test_identities_of_the_bottom_laminate():
+    """For a unit normal n: N^T 1 = n and N^T N = (I + n (x) n) / 2, the identities that shorten the
+    condensation of two leaves whose tangents have the form lam 1(x)1 + 2 mu I - c m(x)m."""
+    rng = np.random.default_rng(5)
+    one = np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
+    for _ in range(20):
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        N = sym_operator(n)
+        np.testing.assert_allclose(N.T @ one, n, atol=1e-15)
+        np.testing.assert_allclose(N.T @ N, 0.5 * (np.eye(3) + np.outer(n, n)), atol=1e-15)
+
+
+def test_leaf_tangent_has_the_isotropic_rank_one_form():
+    """The leaf tangent is lam 1(x)1 + 2 mu I - c m(x)m with m the unit flow direction (Mandel, deviatoric):
+    for J2 leaves lam + 2 mu / 3 = K, mu < G and c > 0 once they yield; elastic leaves have mu = G, c = 0.
+    With m deviatoric and of unit length, m^T D m = 2 mu - c and 1^T D 1 = 9 lam + 6 mu."""
+    rng = np.random.default_rng(6)
+    one = np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
+    for ph in (W.MATRIX, W.MATRIX_EXPLIN, W.FIBER):
+        Kb, G = ph.E / (3 * (1 - 2 * ph.nu)), ph.E / (2 * (1 + ph.nu))
+        for _ in range(10):
+            eps = rng.standard_normal(6) * 0.02
+            sig, D, z = oracle.phase_law(ph, eps)
+            dev = eps - np.r_[np.full(3, eps[:3].sum() / 3), np.zeros(3)]
+            m = dev / np.linalg.norm(dev)                # the flow direction from the virgin state
+            e = np.linalg.svd(np.vstack([one, m]))[2][2]  # a unit direction orthogonal to 1 and m
+            mu = 0.5 * (e @ D @ e)
+            c = 2 * mu - m @ D @ m
+            lam = (one @ D @ one - 6 * mu) / 9.0
+            rebuilt = lam * np.outer(one, one) + 2 * mu * np.eye(6) - c * np.outer(m, m)
+            np.testing.assert_allclose(D, rebuilt, atol=1e-9 * np.abs(D).max())
+            assert abs(lam + 2 * mu / 3 - Kb) <= 1e-9 * Kb
+            if ph.kind == 0:
+                assert abs(mu - G) <= 1e-9 * G and abs(c) <= 1e-9 * G
+            else:
+                assert z[0] > 0 and c > 0 and mu < G     # yielded
