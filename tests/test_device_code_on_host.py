@@ -1,0 +1,270 @@
+"""The kernels' per-thread arithmetic, compiled for the host, against the oracle.
+
+csrc/dmn_device.cuh holds everything one GPU thread does for one Gauss point:
+the depth-first tree pass (jump correction, leaf laws, condensation, residual)
+and the leaf-state update.  This test compiles that header with g++, defining
+the handful of CUDA names it uses from their documented meaning (__ldg as a
+plain load, rsqrt as 1/sqrt, the bit casts as memcpy), and drives it with a
+small harness: the tree constants, the point's normals and local strain, the
+Newton loop of the persistent kernel and the rotation back, each restated from
+csrc/dmn.cu.  The result must match the oracle to the GPU parity tolerances on
+every increment of a plastic path, in the FP64 form and in the mixed form with
+an FP32 tangent.
+
+It checks the device arithmetic without a GPU, so a change to it can be tried
+against the oracle on the CPU first.  It is a test only: nothing in the
+package runs device code on the host.
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_08253_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+HARNESS = r'''
+#define DMN_HOST_EMULATION 1
+#define __device__
+#define __host__
+#define __global__
+#define __forceinline__ inline
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+using std::isfinite;
+struct int4 { int x, y, z, w; };
+template <class T> inline T __ldg(const T* p) { return *p; }
+inline int __ffs(int x) { return __builtin_ffs(x); }
+inline double __longlong_as_double(long long v) { double d; std::memcpy(&d, &v, 8); return d; }
+inline long long __double_as_longlong(double d) { long long v; std::memcpy(&v, &d, 8); return v; }
+inline float __uint_as_float(unsigned u) { float f; std::memcpy(&f, &u, 4); return f; }
+inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f, 4); return u; }
+inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
+#include "dmn_device.cuh"
+using namespace dmn;
+
+static void rd(void* dst, size_t count, FILE* in) {   // read count doubles or fail
+  if (fread(dst, 8, count, in) != count) { fprintf(stderr, "short input\n"); std::exit(2); }
+}
+
+// phase constants (restated from the library's set-up)
+static PhaseDev make_phase(const double* r) {
+  PhaseDev o{};
+  o.kind = (int)r[0];
+  const double E = r[1], nu = r[2], s0 = r[3], H = r[4], sinf = r[5], k0 = r[6];
+  if (o.kind == 2) {
+    if (sinf > s0 && k0 > H) { o.ds = sinf - s0; o.dk = k0 - H; o.rate = o.dk / o.ds; }
+    else o.kind = 1;
+  }
+  o.K = E / (3.0 * (1.0 - 2.0 * nu));
+  o.G = E / (2.0 * (1.0 + nu));
+  o.s0 = s0; o.H = H;
+  o.lam = o.K - 2.0 * o.G / 3.0;
+  o.lamf = (float)o.lam; o.Gf = (float)o.G;
+  o.inv_den = 1.0 / (2.0 * o.G + 2.0 * H / 3.0);
+  o.thb0 = 1.0 / (1.0 + H / (3.0 * o.G));
+  return o;
+}
+
+template <typename T>
+static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double tol) {
+  const int L = 1 << K, N = L - 1;
+  std::vector<double> p(N * M), q(N * M), w(L), ph(14);
+  rd(p.data(), N * M, in); rd(q.data(), N * M, in); rd(w.data(), L, in); rd(ph.data(), 14, in);
+  TreeDev t{};
+  t.K = K; t.M = M; t.N = N; t.L = L;
+  t.ph[0] = make_phase(ph.data()); t.ph[1] = make_phase(ph.data() + 7);
+  const int inel = (t.ph[0].kind != 0) + (t.ph[1].kind != 0);
+  t.z_both = inel == 2; t.nz = inel * (L / 2);
+  // laminate parameters in heap order (array index h - 1), paper order at the interface
+  std::vector<double> hp(N * M), hq(N * M);
+  for (int k = 1; k <= K; ++k)
+    for (int i = 1; i <= (1 << (k - 1)); ++i) {
+      const int j = L - (1 << k) + (i - 1), hn = (1 << (k - 1)) + i - 2;
+      for (int m = 0; m < M; ++m) { hp[hn * M + m] = p[j * M + m]; hq[hn * M + m] = q[j * M + m]; }
+    }
+  // volume fractions, residual scales, normalised leaf weights
+  std::vector<double> c(3 * N + L), Wsub(N);
+  std::vector<float> cf(3 * N);
+  double s = 0.0;
+  for (int l = 0; l < L; ++l) s += w[l];
+  for (int h = N; h >= 1; --h) {
+    double wl, wr;
+    if (h >= (1 << (K - 1))) { const int m = h - (1 << (K - 1)); wl = w[2 * m] / s; wr = w[2 * m + 1] / s; }
+    else { wl = Wsub[2 * h - 1]; wr = Wsub[2 * h]; }
+    Wsub[h - 1] = wl + wr;
+    const double c1 = wl / (wl + wr), c2 = 1.0 - c1;
+    c[h - 1] = c1; c[N + h - 1] = c2; c[2 * N + h - 1] = Wsub[h - 1] * c1 * c2;
+    cf[h - 1] = (float)c1; cf[N + h - 1] = (float)c2; cf[2 * N + h - 1] = (float)(c1 * c2);
+  }
+  for (int l = 0; l < L; ++l) c[3 * N + l] = w[l] / s;
+  t.p = hp.data(); t.q = hq.data();
+  t.c1 = c.data(); t.c2 = c.data() + N; t.sc = c.data() + 2 * N; t.wl = c.data() + 3 * N;
+  t.c1f = cf.data(); t.c2f = cf.data() + N; t.c12f = cf.data() + 2 * N;
+  t.wsum = s;
+  const long S = 6L * t.nz + 3L * N;
+  std::vector<double> lam(2 * n), Q(9 * n), En(6 * n), dE(6 * n), st(S * n), so(S * n);
+  rd(lam.data(), 2 * n, in); rd(Q.data(), 9 * n, in); rd(En.data(), 6 * n, in);
+  rd(dE.data(), 6 * n, in); rd(st.data(), S * n, in);
+  std::vector<double> stress(6 * n), tangent(36 * n), iters(n), status(n);
+  std::vector<double> nrm(3 * N), a(3 * N);
+  std::vector<float> nrmf(3 * N);
+  std::vector<T> gbuf(21 * N);
+  for (long pt = 0; pt < n; ++pt) {
+    // normals of every laminate (Sec. 2.3): barycentric coordinates, shape functions, spherical angles
+    const double l1 = lam[2 * pt], l2 = lam[2 * pt + 1];
+    const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
+    double f[6];
+    if (M == 3) { f[0] = v[0]; f[1] = v[1]; f[2] = v[2]; }
+    else if (M == 4) { const double b = v[0] * v[1] * v[2]; f[0] = v[0] - 9 * b; f[1] = v[1] - 9 * b; f[2] = v[2] - 9 * b; f[3] = 27 * b; }
+    else { f[0] = v[0] * (2 * v[0] - 1); f[1] = v[1] * (2 * v[1] - 1); f[2] = v[2] * (2 * v[2] - 1);
+           f[3] = 4 * v[0] * v[1]; f[4] = 4 * v[0] * v[2]; f[5] = 4 * v[1] * v[2]; }
+    for (int j = 0; j < N; ++j) {
+      double al = 0.0, be = 0.0;
+      for (int m = 0; m < M; ++m) { al += hp[j * M + m] * f[m]; be += hq[j * M + m] * f[m]; }
+      nrm[3 * j] = std::sin(al) * std::cos(be); nrm[3 * j + 1] = std::sin(al) * std::sin(be); nrm[3 * j + 2] = std::cos(al);
+    }
+    for (int k = 0; k < 3 * N; ++k) nrmf[k] = narrow_rn(nrm[k]);
+    // macro strain in the principal frame: E_loc = R^T (E_n + dE)
+    double R[6][6], Eloc[6];
+    mandel_rotation(&Q[9 * pt], R);
+    for (int J = 0; J < 6; ++J) {
+      double acc = 0.0;
+      for (int I = 0; I < 6; ++I) acc += R[I][J] * (En[6 * pt + I] + dE[6 * pt + I]);
+      Eloc[J] = acc;
+    }
+    for (int k = 0; k < 3 * N; ++k) a[k] = st[(6L * t.nz + k) * n + pt];
+    PointArrays A;
+    A.nrm = nrm.data(); A.ns = 1; A.nrmf = nrmf.data();
+    A.a = a.data(); A.as = 1; A.a_out = a.data(); A.paper = true;
+    A.z = st.data() + pt; A.zs = (size_t)n;
+    GH<T> gh{gbuf.data(), 1, gbuf.data()};
+    // the persistent kernel's Newton loop for one point (no line search)
+    int it = 0, stt = -1;
+    bool first = true;
+    Sub<T> root;
+    for (;;) {
+      double r2;
+      tree_pass<T, true>(t, Eloc, A, gh, !first, (T)1, root, r2, nullptr);
+      first = false;
+      double sn2 = 0.0;
+      for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
+      const double rn = std::sqrt(r2), sn = std::sqrt(sn2);
+      if (!std::isfinite(rn) || !std::isfinite(sn)) stt = 2;
+      else if (rn <= tol * (double)N * sn) stt = 0;
+      else if (it >= max_iter) stt = 1;
+      if (stt < 0) { ++it; continue; }
+      break;
+    }
+    iters[pt] = it; status[pt] = stt;
+    // stress and tangent back to the global frame: sigma = R sigma_loc, C = R C_loc R^T
+    double Cl[6][6];
+    for (int I = 0; I < 6; ++I) for (int J = 0; J < 6; ++J) Cl[I][J] = widen(root.C[sidx(I, J)]);
+    for (int I = 0; I < 6; ++I) {
+      double acc = 0.0;
+      for (int J = 0; J < 6; ++J) acc += R[I][J] * root.sb[J];
+      stress[6 * pt + I] = acc;
+      for (int J = 0; J < 6; ++J) {
+        double cc = 0.0;
+        for (int P2 = 0; P2 < 6; ++P2) for (int Q2 = 0; Q2 < 6; ++Q2) cc += R[I][P2] * Cl[P2][Q2] * R[J][Q2];
+        tangent[36 * pt + 6 * I + J] = cc;
+      }
+    }
+    for (int k = 0; k < 3 * N; ++k) so[(6L * t.nz + k) * n + pt] = a[k];
+    write_leaf_states(t, Eloc, A, so.data() + pt, (size_t)n, stt == 2);
+  }
+  fwrite(so.data(), 8, S * n, out); fwrite(stress.data(), 8, 6 * n, out); fwrite(tangent.data(), 8, 36 * n, out);
+  fwrite(iters.data(), 8, n, out); fwrite(status.data(), 8, n, out);
+  return 0;
+}
+
+int main(int argc, char** argv) {
+  FILE* in = argc == 3 ? fopen(argv[1], "rb") : nullptr;
+  FILE* out = argc == 3 ? fopen(argv[2], "wb") : nullptr;
+  double hdr[6];
+  if (argc != 3 || !in || !out) return 2;
+  rd(hdr, 6, in);
+  const int K = (int)hdr[0], M = (int)hdr[1], prec = (int)hdr[3], max_iter = (int)hdr[4];
+  const long n = (long)hdr[2];
+  const int rc = prec == 0 ? run<double>(in, out, K, M, n, max_iter, hdr[5]) : run<float>(in, out, K, M, n, max_iter, hdr[5]);
+  fclose(in); fclose(out);
+  return rc;
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("host_device_code")
+    src = d / "harness.cpp"
+    src.write_text(HARNESS)
+    exe = d / "harness"
+    subprocess.check_call([gxx, "-O2", "-std=c++17", "-Wall", "-Werror", "-Wno-unknown-pragmas", "-Wno-unused-variable", "-I",
+                           os.path.join(ROOT, "paper_2103_08253_gb300", "csrc"), "-o", str(exe), str(src)])
+    return str(exe), d
+
+
+def run_harness(harness, tree, lam, Q, En, dE, state, prec, max_iter=50):
+    exe, d = harness
+    n = lam.shape[0]
+    rows = [oracle.phases_array(tree.phases).ravel()]
+    hdr = np.array([tree.K, tree.M, n, prec, max_iter, 1e-12], dtype=np.float64)
+    blob = np.concatenate([hdr, np.ravel(tree.p), np.ravel(tree.q), np.ravel(tree.w), rows[0],
+                           lam.ravel(), Q.ravel(), En.ravel(), dE.ravel(), state.ravel()]).astype(np.float64)
+    fin, fout = d / "in.bin", d / "out.bin"
+    blob.tofile(fin)
+    subprocess.check_call([exe, str(fin), str(fout)])
+    r = np.fromfile(fout, dtype=np.float64)
+    S = state.shape[0]
+    o = 0
+    st = r[o:o + S * n].reshape(S, n); o += S * n
+    sig = r[o:o + 6 * n].reshape(n, 6); o += 6 * n
+    C = r[o:o + 36 * n].reshape(n, 6, 6); o += 36 * n
+    it = r[o:o + n].astype(int); o += n
+    stat = r[o:o + n].astype(int)
+    return st, sig, C, it, stat
+
+
+def rel(a, b):
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
+
+
+@pytest.mark.parametrize("K,M,matrix,prec", [(4, 3, "linear", 0), (6, 3, "explin", 0), (5, 6, "linear", 0),
+                                             (6, 3, "linear", 1)])
+def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
+    mat = W.MATRIX if matrix == "linear" else W.MATRIX_EXPLIN
+    tree = (W.tree_d10_fit(K, seed=30 + K, phases=(W.FIBER, mat)) if M == 3
+            else W.tree_nodal_angles(K, M, seed=30 + K, phases=(W.FIBER, mat)))
+    n = 24
+    A2, lam, Q = W.orientation_field(n, seed=40 + K)
+    Ef = W.random6_path_final(n, 0.03, seed=50 + K)
+    S = W.state_size(K, tree.phases)
+    sh, so = np.zeros((S, n)), np.zeros((S, n))
+    tol_s, tol_c = (1e-10, 1e-10) if prec == 0 else (1e-6, 1e-4)
+    alive = np.ones(n, dtype=bool)
+    for s in range(1, 9):
+        En, dE = W.proportional_increment(Ef, s, 20)
+        sh, sig_h, C_h, it_h, stat_h = run_harness(harness, tree, lam, Q, En, dE, sh, prec)
+        so, sig_o, C_o, it_o, stat_o, gap = oracle.update(tree, lam, Q, En, dE, so)
+        alive &= (stat_o == 0) & (stat_h == 0)
+        assert alive.mean() > 0.9
+        assert rel(sig_h[alive], sig_o[alive]).max() <= tol_s, s
+        ok = alive & (gap > 1e-9)
+        assert rel(C_h[ok], C_o[ok]).max() <= tol_c, s
+        scale = np.abs(so[:, alive]).max(axis=1, keepdims=True) + 1e-300
+        assert (np.abs(sh[:, alive] - so[:, alive]) / scale).max() <= (1e-9 if prec == 0 else 1e-5), s
+        if prec == 0:
+            assert np.abs(it_h[alive] - it_o[alive]).max() <= 1
