@@ -9,7 +9,7 @@ small harness: the tree constants, the point's normals and local strain, the
 Newton loop of the persistent kernel and the rotation back, each restated from
 csrc/dmn.cu.  The result must match the oracle to the GPU parity tolerances on
 every increment of a plastic path, in the FP64 form and in the mixed form with
-an FP32 tangent.
+an FP32 tangent or with its FP64 final sweep.
 
 It checks the device arithmetic without a GPU, so a change to it can be tried
 against the oracle on the CPU first.  It is a test only: nothing in the
@@ -74,8 +74,9 @@ static PhaseDev make_phase(const double* r) {
   return o;
 }
 
+// sweep: the mixed form's final FP64 pass at the converged jumps gives stress and tangent
 template <typename T>
-static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double tol) {
+static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double tol, bool sweep) {
   const int L = 1 << K, N = L - 1;
   std::vector<double> p(N * M), q(N * M), w(L), ph(14);
   rd(p.data(), N * M, in); rd(q.data(), N * M, in); rd(w.data(), L, in); rd(ph.data(), 14, in);
@@ -165,12 +166,20 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
       break;
     }
     iters[pt] = it; status[pt] = stt;
+    double Cl[6][6], sl[6];
+    if (sweep) {
+      Sub<double> fin;
+      double r2;
+      GH<double> none{nullptr, 0, nullptr};
+      tree_pass<double, false>(t, Eloc, A, none, false, 1.0, fin, r2, nullptr);
+      for (int I = 0; I < 6; ++I) { sl[I] = fin.sb[I]; for (int J = 0; J < 6; ++J) Cl[I][J] = fin.C[sidx(I, J)]; }
+    } else {
+      for (int I = 0; I < 6; ++I) { sl[I] = root.sb[I]; for (int J = 0; J < 6; ++J) Cl[I][J] = widen(root.C[sidx(I, J)]); }
+    }
     // stress and tangent back to the global frame: sigma = R sigma_loc, C = R C_loc R^T
-    double Cl[6][6];
-    for (int I = 0; I < 6; ++I) for (int J = 0; J < 6; ++J) Cl[I][J] = widen(root.C[sidx(I, J)]);
     for (int I = 0; I < 6; ++I) {
       double acc = 0.0;
-      for (int J = 0; J < 6; ++J) acc += R[I][J] * root.sb[J];
+      for (int J = 0; J < 6; ++J) acc += R[I][J] * sl[J];
       stress[6 * pt + I] = acc;
       for (int J = 0; J < 6; ++J) {
         double cc = 0.0;
@@ -194,7 +203,9 @@ int main(int argc, char** argv) {
   rd(hdr, 6, in);
   const int K = (int)hdr[0], M = (int)hdr[1], prec = (int)hdr[3], max_iter = (int)hdr[4];
   const long n = (long)hdr[2];
-  const int rc = prec == 0 ? run<double>(in, out, K, M, n, max_iter, hdr[5]) : run<float>(in, out, K, M, n, max_iter, hdr[5]);
+  // prec: 0 FP64, 1 mixed with the FP32 tangent, 2 mixed with the FP64 final sweep
+  const int rc = prec == 0 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false)
+                           : run<float>(in, out, K, M, n, max_iter, hdr[5], prec == 2);
   fclose(in); fclose(out);
   return rc;
 }
@@ -243,7 +254,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("K,M,matrix,prec", [(4, 3, "linear", 0), (6, 3, "explin", 0), (5, 6, "linear", 0),
-                                             (6, 3, "linear", 1)])
+                                             (6, 3, "linear", 1), (6, 3, "explin", 2)])
 def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
     mat = W.MATRIX if matrix == "linear" else W.MATRIX_EXPLIN
     tree = (W.tree_d10_fit(K, seed=30 + K, phases=(W.FIBER, mat)) if M == 3
@@ -253,7 +264,7 @@ def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
     Ef = W.random6_path_final(n, 0.03, seed=50 + K)
     S = W.state_size(K, tree.phases)
     sh, so = np.zeros((S, n)), np.zeros((S, n))
-    tol_s, tol_c = (1e-10, 1e-10) if prec == 0 else (1e-6, 1e-4)
+    tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6)}[prec]
     alive = np.ones(n, dtype=bool)
     for s in range(1, 9):
         En, dE = W.proportional_increment(Ef, s, 20)
