@@ -9,7 +9,9 @@ small harness: the tree constants, the point's normals and local strain, the
 Newton loop of the persistent kernel and the rotation back, each restated from
 csrc/dmn.cu.  The result must match the oracle to the GPU parity tolerances on
 every increment of a plastic path, in the FP64 form and in the mixed form with
-an FP32 tangent or with its FP64 final sweep.
+an FP32 tangent or with its FP64 final sweep.  The adjoint of the gradient
+kernel, driven the same way, must match the oracle's implicit-function
+gradient.
 
 It checks the device arithmetic without a GPU, so a change to it can be tried
 against the oracle on the CPU first.  It is a test only: nothing in the
@@ -74,56 +76,53 @@ static PhaseDev make_phase(const double* r) {
   return o;
 }
 
-// sweep: the mixed form's final FP64 pass at the converged jumps gives stress and tangent
-template <typename T>
-static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double tol, bool sweep) {
-  const int L = 1 << K, N = L - 1;
-  std::vector<double> p(N * M), q(N * M), w(L), ph(14);
-  rd(p.data(), N * M, in); rd(q.data(), N * M, in); rd(w.data(), L, in); rd(ph.data(), 14, in);
+// the tree's constants as the library sets them up: parameters in heap order (array index h - 1),
+// volume fractions, residual scales, normalised leaf weights
+struct Tree {
+  int K, M, N, L;
+  std::vector<double> hp, hq, c;
+  std::vector<float> cf;
   TreeDev t{};
-  t.K = K; t.M = M; t.N = N; t.L = L;
-  t.ph[0] = make_phase(ph.data()); t.ph[1] = make_phase(ph.data() + 7);
-  const int inel = (t.ph[0].kind != 0) + (t.ph[1].kind != 0);
-  t.z_both = inel == 2; t.nz = inel * (L / 2);
-  // laminate parameters in heap order (array index h - 1), paper order at the interface
-  std::vector<double> hp(N * M), hq(N * M);
-  for (int k = 1; k <= K; ++k)
-    for (int i = 1; i <= (1 << (k - 1)); ++i) {
-      const int j = L - (1 << k) + (i - 1), hn = (1 << (k - 1)) + i - 2;
-      for (int m = 0; m < M; ++m) { hp[hn * M + m] = p[j * M + m]; hq[hn * M + m] = q[j * M + m]; }
+  long S;
+  Tree(FILE* in, int K_, int M_) : K(K_), M(M_), N((1 << K_) - 1), L(1 << K_) {
+    std::vector<double> p(N * M), q(N * M), w(L), ph(14);
+    rd(p.data(), N * M, in); rd(q.data(), N * M, in); rd(w.data(), L, in); rd(ph.data(), 14, in);
+    t.K = K; t.M = M; t.N = N; t.L = L;
+    t.ph[0] = make_phase(ph.data()); t.ph[1] = make_phase(ph.data() + 7);
+    const int inel = (t.ph[0].kind != 0) + (t.ph[1].kind != 0);
+    t.z_both = inel == 2; t.nz = inel * (L / 2);
+    hp.resize(N * M); hq.resize(N * M);
+    for (int k = 1; k <= K; ++k)
+      for (int i = 1; i <= (1 << (k - 1)); ++i) {
+        const int j = L - (1 << k) + (i - 1), hn = (1 << (k - 1)) + i - 2;
+        for (int m = 0; m < M; ++m) { hp[hn * M + m] = p[j * M + m]; hq[hn * M + m] = q[j * M + m]; }
+      }
+    c.resize(3 * N + L); cf.resize(3 * N);
+    std::vector<double> Wsub(N);
+    double s = 0.0;
+    for (int l = 0; l < L; ++l) s += w[l];
+    for (int h = N; h >= 1; --h) {
+      double wl, wr;
+      if (h >= (1 << (K - 1))) { const int m = h - (1 << (K - 1)); wl = w[2 * m] / s; wr = w[2 * m + 1] / s; }
+      else { wl = Wsub[2 * h - 1]; wr = Wsub[2 * h]; }
+      Wsub[h - 1] = wl + wr;
+      const double c1 = wl / (wl + wr), c2 = 1.0 - c1;
+      c[h - 1] = c1; c[N + h - 1] = c2; c[2 * N + h - 1] = Wsub[h - 1] * c1 * c2;
+      cf[h - 1] = (float)c1; cf[N + h - 1] = (float)c2; cf[2 * N + h - 1] = (float)(c1 * c2);
     }
-  // volume fractions, residual scales, normalised leaf weights
-  std::vector<double> c(3 * N + L), Wsub(N);
-  std::vector<float> cf(3 * N);
-  double s = 0.0;
-  for (int l = 0; l < L; ++l) s += w[l];
-  for (int h = N; h >= 1; --h) {
-    double wl, wr;
-    if (h >= (1 << (K - 1))) { const int m = h - (1 << (K - 1)); wl = w[2 * m] / s; wr = w[2 * m + 1] / s; }
-    else { wl = Wsub[2 * h - 1]; wr = Wsub[2 * h]; }
-    Wsub[h - 1] = wl + wr;
-    const double c1 = wl / (wl + wr), c2 = 1.0 - c1;
-    c[h - 1] = c1; c[N + h - 1] = c2; c[2 * N + h - 1] = Wsub[h - 1] * c1 * c2;
-    cf[h - 1] = (float)c1; cf[N + h - 1] = (float)c2; cf[2 * N + h - 1] = (float)(c1 * c2);
+    for (int l = 0; l < L; ++l) c[3 * N + l] = w[l] / s;
+    t.p = hp.data(); t.q = hq.data();
+    t.c1 = c.data(); t.c2 = c.data() + N; t.sc = c.data() + 2 * N; t.wl = c.data() + 3 * N;
+    t.c1f = cf.data(); t.c2f = cf.data() + N; t.c12f = cf.data() + 2 * N;
+    t.wsum = s;
+    S = 6L * t.nz + 3L * N;
   }
-  for (int l = 0; l < L; ++l) c[3 * N + l] = w[l] / s;
-  t.p = hp.data(); t.q = hq.data();
-  t.c1 = c.data(); t.c2 = c.data() + N; t.sc = c.data() + 2 * N; t.wl = c.data() + 3 * N;
-  t.c1f = cf.data(); t.c2f = cf.data() + N; t.c12f = cf.data() + 2 * N;
-  t.wsum = s;
-  const long S = 6L * t.nz + 3L * N;
-  std::vector<double> lam(2 * n), Q(9 * n), En(6 * n), dE(6 * n), st(S * n), so(S * n);
-  rd(lam.data(), 2 * n, in); rd(Q.data(), 9 * n, in); rd(En.data(), 6 * n, in);
-  rd(dE.data(), 6 * n, in); rd(st.data(), S * n, in);
-  std::vector<double> stress(6 * n), tangent(36 * n), iters(n), status(n);
-  std::vector<double> nrm(3 * N), a(3 * N);
-  std::vector<float> nrmf(3 * N);
-  std::vector<T> gbuf(21 * N);
-  for (long pt = 0; pt < n; ++pt) {
-    // normals of every laminate (Sec. 2.3): barycentric coordinates, shape functions, spherical angles
-    const double l1 = lam[2 * pt], l2 = lam[2 * pt + 1];
+  // one point: shape-function values, normals of every laminate (Sec. 2.3), the Mandel rotation R of its
+  // frame and the macro strain in that frame, E_loc = R^T (E_n + dE)
+  void point(double l1, double l2, const double* Q, const double* En, const double* dE, double f[6],
+             double* nrm, float* nrmf, double R[6][6], double Eloc[6]) const {
     const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
-    double f[6];
+    for (int m = 0; m < 6; ++m) f[m] = 0.0;
     if (M == 3) { f[0] = v[0]; f[1] = v[1]; f[2] = v[2]; }
     else if (M == 4) { const double b = v[0] * v[1] * v[2]; f[0] = v[0] - 9 * b; f[1] = v[1] - 9 * b; f[2] = v[2] - 9 * b; f[3] = 27 * b; }
     else { f[0] = v[0] * (2 * v[0] - 1); f[1] = v[1] * (2 * v[1] - 1); f[2] = v[2] * (2 * v[2] - 1);
@@ -133,15 +132,33 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
       for (int m = 0; m < M; ++m) { al += hp[j * M + m] * f[m]; be += hq[j * M + m] * f[m]; }
       nrm[3 * j] = std::sin(al) * std::cos(be); nrm[3 * j + 1] = std::sin(al) * std::sin(be); nrm[3 * j + 2] = std::cos(al);
     }
-    for (int k = 0; k < 3 * N; ++k) nrmf[k] = narrow_rn(nrm[k]);
-    // macro strain in the principal frame: E_loc = R^T (E_n + dE)
-    double R[6][6], Eloc[6];
-    mandel_rotation(&Q[9 * pt], R);
+    if (nrmf) for (int k = 0; k < 3 * N; ++k) nrmf[k] = narrow_rn(nrm[k]);
+    mandel_rotation(Q, R);
     for (int J = 0; J < 6; ++J) {
       double acc = 0.0;
-      for (int I = 0; I < 6; ++I) acc += R[I][J] * (En[6 * pt + I] + dE[6 * pt + I]);
+      for (int I = 0; I < 6; ++I) acc += R[I][J] * (En[I] + dE[I]);
       Eloc[J] = acc;
     }
+  }
+};
+
+// sweep: the mixed form's final FP64 pass at the converged jumps gives stress and tangent
+template <typename T>
+static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double tol, bool sweep) {
+  const Tree tr(in, K, M);
+  const TreeDev& t = tr.t;
+  const int N = tr.N;
+  const long S = tr.S;
+  std::vector<double> lam(2 * n), Q(9 * n), En(6 * n), dE(6 * n), st(S * n), so(S * n);
+  rd(lam.data(), 2 * n, in); rd(Q.data(), 9 * n, in); rd(En.data(), 6 * n, in);
+  rd(dE.data(), 6 * n, in); rd(st.data(), S * n, in);
+  std::vector<double> stress(6 * n), tangent(36 * n), iters(n), status(n);
+  std::vector<double> nrm(3 * N), a(3 * N);
+  std::vector<float> nrmf(3 * N);
+  std::vector<T> gbuf(21 * N);
+  for (long pt = 0; pt < n; ++pt) {
+    double f[6], R[6][6], Eloc[6];
+    tr.point(lam[2 * pt], lam[2 * pt + 1], &Q[9 * pt], &En[6 * pt], &dE[6 * pt], f, nrm.data(), nrmf.data(), R, Eloc);
     for (int k = 0; k < 3 * N; ++k) a[k] = st[(6L * t.nz + k) * n + pt];
     PointArrays A;
     A.nrm = nrm.data(); A.ns = 1; A.nrmf = nrmf.data();
@@ -195,17 +212,77 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
   return 0;
 }
 
+// the adjoint of a converged update (the per-point work of the gradient kernel, then the sum over points):
+// inputs lam, Q, E_n, dE, the state before and after the update and the loss gradient g (global frame);
+// outputs dL/dp, dL/dq (paper ordering), dL/dw and dL/dE
+static int run_grad(FILE* in, FILE* out, int K, int M, long n) {
+  const Tree tr(in, K, M);
+  const TreeDev& t = tr.t;
+  const int N = tr.N, L = tr.L;
+  const long S = tr.S;
+  std::vector<double> lam(2 * n), Q(9 * n), En(6 * n), dE(6 * n), st_in(S * n), st_out(S * n), g(6 * n);
+  rd(lam.data(), 2 * n, in); rd(Q.data(), 9 * n, in); rd(En.data(), 6 * n, in); rd(dE.data(), 6 * n, in);
+  rd(st_in.data(), S * n, in); rd(st_out.data(), S * n, in); rd(g.data(), 6 * n, in);
+  std::vector<double> gp(N * M, 0.0), gq(N * M, 0.0), gwt(L, 0.0), gE(6 * n);
+  std::vector<double> nrm(3 * N), a(3 * N), gh(21 * N), mu(3 * N), xi(N), gab(2 * N), direct(L), gw(L);
+  for (long pt = 0; pt < n; ++pt) {
+    double f[6], R[6][6], Eloc[6];
+    tr.point(lam[2 * pt], lam[2 * pt + 1], &Q[9 * pt], &En[6 * pt], &dE[6 * pt], f, nrm.data(), nullptr, R, Eloc);
+    for (int k = 0; k < 3 * N; ++k) a[k] = st_out[(6L * t.nz + k) * n + pt];
+    PointArrays A;
+    A.nrm = nrm.data(); A.ns = 1; A.nrmf = nullptr;
+    A.a = a.data(); A.as = 1; A.a_out = a.data(); A.paper = true;
+    A.z = st_in.data() + pt; A.zs = (size_t)n;
+    // condensation at the converged jumps: g, H of every laminate and the tangent
+    Sub<double> root;
+    double r2;
+    GH<double> ghv{gh.data(), 1, gh.data()};
+    tree_pass<double, true>(t, Eloc, A, ghv, false, 1.0, root, r2, nullptr);
+    double gl[6];
+    for (int J = 0; J < 6; ++J) {
+      double acc = 0.0;
+      for (int I = 0; I < 6; ++I) acc += R[I][J] * g[6 * pt + I];
+      gl[J] = acc;
+    }
+    AdjWork Wk;
+    Wk.H = gh.data(); Wk.hs = 1; Wk.mu = mu.data(); Wk.xi = xi.data(); Wk.gab = gab.data();
+    Wk.direct = direct.data(); Wk.ws = 1;
+    adjoint_pass(t, Eloc, gl, f, A, Wk);
+    adjoint_weights(t, t.wl, t.wsum, Wk, gw.data(), 1);
+    for (int node = 0; node < N; ++node) {
+      const int lvl = 32 - __builtin_clz(node + 1);
+      const int j = L - 3 * (1 << (lvl - 1)) + node + 1;      // the paper's index of heap laminate `node`
+      for (int m = 0; m < M; ++m) { gp[j * M + m] += gab[node] * f[m]; gq[j * M + m] += gab[N + node] * f[m]; }
+    }
+    for (int l = 0; l < L; ++l) gwt[l] += gw[l];
+    // dL/dE = R C_loc g_loc
+    for (int I = 0; I < 6; ++I) {
+      double acc = 0.0;
+      for (int J = 0; J < 6; ++J) {
+        double ge = 0.0;
+        for (int P2 = 0; P2 < 6; ++P2) ge += root.C[sidx(J, P2)] * gl[P2];
+        acc += R[I][J] * ge;
+      }
+      gE[6 * pt + I] = acc;
+    }
+  }
+  fwrite(gp.data(), 8, N * M, out); fwrite(gq.data(), 8, N * M, out); fwrite(gwt.data(), 8, L, out);
+  fwrite(gE.data(), 8, 6 * n, out);
+  return 0;
+}
+
 int main(int argc, char** argv) {
   FILE* in = argc == 3 ? fopen(argv[1], "rb") : nullptr;
   FILE* out = argc == 3 ? fopen(argv[2], "wb") : nullptr;
-  double hdr[6];
   if (argc != 3 || !in || !out) return 2;
+  double hdr[6];
   rd(hdr, 6, in);
-  const int K = (int)hdr[0], M = (int)hdr[1], prec = (int)hdr[3], max_iter = (int)hdr[4];
+  const int K = (int)hdr[0], M = (int)hdr[1], mode = (int)hdr[3], max_iter = (int)hdr[4];
   const long n = (long)hdr[2];
-  // prec: 0 FP64, 1 mixed with the FP32 tangent, 2 mixed with the FP64 final sweep
-  const int rc = prec == 0 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false)
-                           : run<float>(in, out, K, M, n, max_iter, hdr[5], prec == 2);
+  // mode: 0 FP64, 1 mixed with the FP32 tangent, 2 mixed with the FP64 final sweep, 3 adjoint (FP64)
+  const int rc = mode == 0 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false)
+               : mode == 3 ? run_grad(in, out, K, M, n)
+                           : run<float>(in, out, K, M, n, max_iter, hdr[5], mode == 2);
   fclose(in); fclose(out);
   return rc;
 }
@@ -279,3 +356,53 @@ def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
         assert (np.abs(sh[:, alive] - so[:, alive]) / scale).max() <= (1e-9 if prec == 0 else 1e-5), s
         if prec == 0:
             assert np.abs(it_h[alive] - it_o[alive]).max() <= 1
+
+
+def run_grad_harness(harness, tree, lam, Q, En, dE, state_in, state_out, g):
+    exe, d = harness
+    n = lam.shape[0]
+    hdr = np.array([tree.K, tree.M, n, 3, 0, 0.0], dtype=np.float64)
+    blob = np.concatenate([hdr, np.ravel(tree.p), np.ravel(tree.q), np.ravel(tree.w),
+                           oracle.phases_array(tree.phases).ravel(), lam.ravel(), Q.ravel(), En.ravel(), dE.ravel(),
+                           state_in.ravel(), state_out.ravel(), g.ravel()]).astype(np.float64)
+    fin, fout = d / "grad_in.bin", d / "grad_out.bin"
+    blob.tofile(fin)
+    subprocess.check_call([exe, str(fin), str(fout)])
+    r = np.fromfile(fout, dtype=np.float64)
+    N, M, L = (1 << tree.K) - 1, tree.M, 1 << tree.K
+    gp = r[:N * M].reshape(N, M)
+    gq = r[N * M:2 * N * M].reshape(N, M)
+    gw = r[2 * N * M:2 * N * M + L]
+    gE = r[2 * N * M + L:].reshape(n, 6)
+    return gp, gq, gw, gE
+
+
+@pytest.mark.parametrize("K,matrix,steps", [(3, "linear", 4), (4, "explin", 6)])
+def test_device_adjoint_matches_the_oracle_gradient(harness, K, matrix, steps):
+    """The adjoint of the device code (condensation at the converged jumps, adjoint pass, weight
+    gradient) against the oracle's implicit-function gradient, summed over the points, and dL/dE
+    against the oracle's tangent applied to g."""
+    mat = W.MATRIX if matrix == "linear" else W.MATRIX_EXPLIN
+    tree = W.tree_d10_fit(K, seed=70 + K, phases=(W.FIBER, mat))
+    n = 3
+    A2, lam, Q = W.orientation_field(n, seed=71 + K)
+    Ef = W.random6_path_final(n, 0.03, seed=72 + K)
+    S = W.state_size(K, tree.phases)
+    st = np.zeros((S, n))
+    for s in range(1, steps + 1):
+        En, dE = W.proportional_increment(Ef, s, 10)
+        prev = st
+        st, sig, C, it, stat, gap = oracle.update(tree, lam, Q, En, dE, prev)
+    assert (stat == 0).all()
+    g = np.random.default_rng(K).standard_normal((n, 6))
+    gp, gq, gw, gE = run_grad_harness(harness, tree, lam, Q, En, dE, prev, st, g)
+    ref = dict(p=0.0, q=0.0, w=0.0)
+    for i in range(n):
+        gi = oracle.gradient_ift(tree, lam[i], Q[i], (En + dE)[i], oracle.jumps(tree, st, i),
+                                 oracle.leaf_states(tree, prev, i), g[i])
+        for k in ref:
+            ref[k] = ref[k] + gi[k]
+    for k, got in (("p", gp), ("q", gq), ("w", gw)):
+        err = np.abs(got - ref[k]).max() / np.abs(ref[k]).max()
+        assert err < 1e-6, (k, err)
+    np.testing.assert_allclose(gE, np.einsum("nij,nj->ni", C, g), rtol=1e-9, atol=1e-9 * np.abs(gE).max())
