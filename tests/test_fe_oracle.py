@@ -5,7 +5,6 @@ consistency of internal force and tangent for a linear material."""
 import math
 
 import numpy as np
-import pytest
 
 import oracle
 from oracle import fe_oracle as FE
