@@ -9,9 +9,9 @@ small harness: the tree constants, the point's normals and local strain, the
 Newton loop of the persistent kernel and the rotation back, each restated from
 csrc/dmn.cu.  The result must match the oracle to the GPU parity tolerances on
 every increment of a plastic path, in the FP64 form and in the mixed form with
-an FP32 tangent or with its FP64 final sweep.  The adjoint of the gradient
-kernel, driven the same way, must match the oracle's implicit-function
-gradient.
+an FP32 tangent or with its FP64 final sweep, and with the line search.  The
+adjoint of the gradient kernel, driven the same way, must match the oracle's
+implicit-function gradient.
 
 It checks the device arithmetic without a GPU, so a change to it can be tried
 against the oracle on the CPU first.  It is a test only: nothing in the
@@ -143,8 +143,9 @@ struct Tree {
 };
 
 // sweep: the mixed form's final FP64 pass at the converged jumps gives stress and tangent
+// ls: the backtracking line search with its two buffers of jumps and of g, H (accepted / trial)
 template <typename T>
-static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double tol, bool sweep) {
+static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double tol, bool sweep, bool ls) {
   const Tree tr(in, K, M);
   const TreeDev& t = tr.t;
   const int N = tr.N;
@@ -153,35 +154,49 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
   rd(lam.data(), 2 * n, in); rd(Q.data(), 9 * n, in); rd(En.data(), 6 * n, in);
   rd(dE.data(), 6 * n, in); rd(st.data(), S * n, in);
   std::vector<double> stress(6 * n), tangent(36 * n), iters(n), status(n);
-  std::vector<double> nrm(3 * N), a(3 * N);
+  std::vector<double> nrm(3 * N), abuf[2] = {std::vector<double>(3 * N), std::vector<double>(3 * N)};
   std::vector<float> nrmf(3 * N);
-  std::vector<T> gbuf(21 * N);
+  std::vector<T> gbuf[2] = {std::vector<T>(21 * N), std::vector<T>(21 * N)};
   for (long pt = 0; pt < n; ++pt) {
     double f[6], R[6][6], Eloc[6];
     tr.point(lam[2 * pt], lam[2 * pt + 1], &Q[9 * pt], &En[6 * pt], &dE[6 * pt], f, nrm.data(), nrmf.data(), R, Eloc);
-    for (int k = 0; k < 3 * N; ++k) a[k] = st[(6L * t.nz + k) * n + pt];
+    int cur = 0;
+    for (int k = 0; k < 3 * N; ++k) abuf[0][k] = st[(6L * t.nz + k) * n + pt];
     PointArrays A;
     A.nrm = nrm.data(); A.ns = 1; A.nrmf = nrmf.data();
-    A.a = a.data(); A.as = 1; A.a_out = a.data(); A.paper = true;
+    A.as = 1; A.paper = true;
     A.z = st.data() + pt; A.zs = (size_t)n;
-    GH<T> gh{gbuf.data(), 1, gbuf.data()};
-    // the persistent kernel's Newton loop for one point (no line search)
-    int it = 0, stt = -1;
+    // the persistent kernel's Newton loop for one point
+    int it = 0, stt = -1, halvings = 0;
     bool first = true;
-    Sub<T> root;
+    T step = (T)1;
+    double rn_acc = 0.0;
+    Sub<T> root, root_acc;
     for (;;) {
+      A.a = abuf[cur].data();
+      A.a_out = abuf[ls ? 1 - cur : cur].data();
+      GH<T> gh{gbuf[cur].data(), 1, gbuf[ls ? 1 - cur : cur].data()};
       double r2;
-      tree_pass<T, true>(t, Eloc, A, gh, !first, (T)1, root, r2, nullptr);
-      first = false;
+      tree_pass<T, true>(t, Eloc, A, gh, !first, step, root, r2, nullptr);
       double sn2 = 0.0;
       for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
       const double rn = std::sqrt(r2), sn = std::sqrt(sn2);
+      if (ls && !(first || rn < rn_acc)) {          // trial rejected: halve the step, at most 8 times
+        if (++halvings > 8) { stt = 3; ++it; root = root_acc; break; }
+        step *= (T)0.5;
+        continue;
+      }
+      if (ls) { cur = 1 - cur; rn_acc = rn; root_acc = root; step = (T)1; halvings = 0; }
+      first = false;
       if (!std::isfinite(rn) || !std::isfinite(sn)) stt = 2;
       else if (rn <= tol * (double)N * sn) stt = 0;
       else if (it >= max_iter) stt = 1;
       if (stt < 0) { ++it; continue; }
       break;
     }
+    A.a = abuf[cur].data();
+    A.a_out = A.a;
+    std::vector<double>& a = abuf[cur];
     iters[pt] = it; status[pt] = stt;
     double Cl[6][6], sl[6];
     if (sweep) {
@@ -279,10 +294,11 @@ int main(int argc, char** argv) {
   rd(hdr, 6, in);
   const int K = (int)hdr[0], M = (int)hdr[1], mode = (int)hdr[3], max_iter = (int)hdr[4];
   const long n = (long)hdr[2];
-  // mode: 0 FP64, 1 mixed with the FP32 tangent, 2 mixed with the FP64 final sweep, 3 adjoint (FP64)
-  const int rc = mode == 0 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false)
+  // mode: 0 FP64, 1 mixed with the FP32 tangent, 2 mixed with the FP64 final sweep, 3 adjoint (FP64),
+  //       4 FP64 with the line search
+  const int rc = mode == 0 || mode == 4 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false, mode == 4)
                : mode == 3 ? run_grad(in, out, K, M, n)
-                           : run<float>(in, out, K, M, n, max_iter, hdr[5], mode == 2);
+                           : run<float>(in, out, K, M, n, max_iter, hdr[5], mode == 2, false);
   fclose(in); fclose(out);
   return rc;
 }
@@ -406,3 +422,29 @@ def test_device_adjoint_matches_the_oracle_gradient(harness, K, matrix, steps):
         err = np.abs(got - ref[k]).max() / np.abs(ref[k]).max()
         assert err < 1e-6, (k, err)
     np.testing.assert_allclose(gE, np.einsum("nij,nj->ni", C, g), rtol=1e-9, atol=1e-9 * np.abs(gE).max())
+
+
+def test_device_line_search_matches_the_oracle(harness):
+    """The line search's two buffers (accepted and trial jumps, g and H) on large cyclic steps against
+    the oracle's line search; plain Newton takes other iterates there (the search halves steps)."""
+    K, n, n_steps = 6, 100, 8
+    tree = W.tree_d10_fit(K, seed=80)
+    A2, lam, Q = W.orientation_field(n, seed=81)
+    amp = W.random6_path_final(n, 0.025, seed=82)
+    S = W.state_size(K)
+    sh, so = np.zeros((S, n)), np.zeros((S, n))
+    alive = np.ones(n, dtype=bool)
+    differs = 0
+    for s in range(1, n_steps + 1):
+        En, dE = W.cyclic_increment(amp, s, n_steps)
+        _, _, _, it_plain, stat_plain, _ = oracle.update(tree, lam, Q, En, dE, so)
+        sh, sig_h, C_h, it_h, stat_h = run_harness(harness, tree, lam, Q, En, dE, sh, 4)
+        so, sig_o, C_o, it_o, stat_o, gap = oracle.update(tree, lam, Q, En, dE, so, line_search=True)
+        differs += int(((it_plain != it_o) | (stat_plain != stat_o)).sum())
+        alive &= (stat_o == 0) & (stat_h == 0)
+        assert alive.mean() > 0.97, (s, alive.mean())
+        assert rel(sig_h[alive], sig_o[alive]).max(initial=0.0) <= 1e-10, s
+        ok = alive & (gap > 1e-9)
+        assert rel(C_h[ok], C_o[ok]).max(initial=0.0) <= 1e-10, s
+        assert np.abs(it_h[alive] - it_o[alive]).max(initial=0) <= 1
+    assert differs > 0          # the search was active on this path
