@@ -9,9 +9,9 @@ small harness: the tree constants, the point's normals and local strain, the
 Newton loop of the persistent kernel and the rotation back, each restated from
 csrc/dmn.cu.  The result must match the oracle to the GPU parity tolerances on
 every increment of a plastic path, in the FP64 form and in the mixed form with
-an FP32 tangent or with its FP64 final sweep, and with the line search.  The
-adjoint of the gradient kernel, driven the same way, must match the oracle's
-implicit-function gradient.
+an FP32 tangent or with its FP64 final sweep, with the line search, and on
+compressed trees walked by their tables.  The adjoint of the gradient kernel,
+driven the same way, must match the oracle's implicit-function gradient.
 
 It checks the device arithmetic without a GPU, so a change to it can be tried
 against the oracle on the CPU first.  It is a test only: nothing in the
@@ -80,8 +80,10 @@ static PhaseDev make_phase(const double* r) {
 // volume fractions, residual scales, normalised leaf weights
 struct Tree {
   int K, M, N, L;
-  std::vector<double> hp, hq, c;
+  bool cmp = false;                // a leaf weight is zero: the compressed tree, walked by tables
+  std::vector<double> hp, hq, c;   // laminate parameters in the traversal's numbering
   std::vector<float> cf;
+  std::vector<int> tab;            // compressed tree: lf [Lc][4], pre [N], post [N], paper index [N]
   TreeDev t{};
   long S;
   Tree(FILE* in, int K_, int M_) : K(K_), M(M_), N((1 << K_) - 1), L(1 << K_) {
@@ -89,6 +91,8 @@ struct Tree {
     rd(p.data(), N * M, in); rd(q.data(), N * M, in); rd(w.data(), L, in); rd(ph.data(), 14, in);
     t.K = K; t.M = M; t.N = N; t.L = L;
     t.ph[0] = make_phase(ph.data()); t.ph[1] = make_phase(ph.data() + 7);
+    for (int l = 0; l < L; ++l) cmp = cmp || w[l] == 0.0;
+    if (cmp) { compressed(p, q, w); return; }
     const int inel = (t.ph[0].kind != 0) + (t.ph[1].kind != 0);
     t.z_both = inel == 2; t.nz = inel * (L / 2);
     hp.resize(N * M); hq.resize(N * M);
@@ -116,6 +120,75 @@ struct Tree {
     t.c1f = cf.data(); t.c2f = cf.data() + N; t.c12f = cf.data() + 2 * N;
     t.wsum = s;
     S = 6L * t.nz + 3L * N;
+  }
+  // Tree compression (Sec. 3.1) in the tables' documented format: leaves of weight zero removed, a laminate
+  // with one weightless side replaced by the other side, the remaining laminates numbered in the paper's
+  // order among themselves; per remaining leaf (leaf order) the depth where its descent starts, the
+  // laminates descended to reach it, the laminates completed right after it, and leaf, state slot + 1,
+  // phase and "the next leaf is its sibling"; the laminates in pre- and post-order; their paper indices.
+  void compressed(const std::vector<double>& p, const std::vector<double>& q, const std::vector<double>& w) {
+    const bool inel[2] = {t.ph[0].kind != 0, t.ph[1].kind != 0};
+    std::vector<double> Wh(2 * L, 0.0);          // heap: laminates 1..N, leaves N+1..N+L
+    double s = 0.0;
+    for (int l = 0; l < L; ++l) s += w[l];
+    for (int l = 0; l < L; ++l) Wh[N + 1 + l] = w[l] / s;
+    for (int h = N; h >= 1; --h) Wh[h] = Wh[2 * h] + Wh[2 * h + 1];
+    std::vector<int> cid(N + 1, -1), paper;
+    for (int k = K; k >= 1; --k)
+      for (int i = 1; i <= (1 << (k - 1)); ++i) {
+        const int h = (1 << (k - 1)) + i - 1;
+        if (Wh[2 * h] > 0.0 && Wh[2 * h + 1] > 0.0) { cid[h] = (int)paper.size(); paper.push_back(L - (1 << k) + i - 1); }
+      }
+    const int Nc = (int)paper.size();
+    hp.assign((size_t)std::max(Nc, 1) * M, 0.0); hq.assign((size_t)std::max(Nc, 1) * M, 0.0);
+    c.assign(3 * (size_t)Nc + L, 0.0); cf.assign(3 * (size_t)std::max(Nc, 1), 0.0f);
+    for (int k = 0; k < Nc; ++k)
+      for (int m = 0; m < M; ++m) { hp[k * M + m] = p[paper[k] * M + m]; hq[k * M + m] = q[paper[k] * M + m]; }
+    for (int h = 1; h <= N; ++h) {
+      const int k = cid[h];
+      if (k < 0) continue;
+      const double c1 = Wh[2 * h] / Wh[h], c2 = 1.0 - c1;
+      c[k] = c1; c[Nc + k] = c2; c[2 * Nc + k] = Wh[h] * c1 * c2;
+      cf[k] = (float)c1; cf[Nc + k] = (float)c2; cf[2 * Nc + k] = (float)(c1 * c2);
+    }
+    for (int l = 0; l < L; ++l) c[3 * Nc + l] = Wh[N + 1 + l];
+    std::vector<int> lf, pre, post;
+    int nz = 0;
+    struct Walk {
+      Tree& T; const std::vector<double>& Wh; const std::vector<int>& cid; const bool* inel;
+      std::vector<int>& lf; std::vector<int>& pre; std::vector<int>& post; int& nz;
+      void go(int h, int depth, int top) {
+        if (!(Wh[h] > 0.0)) return;
+        if (h > T.N) {
+          const int leaf = h - T.N - 1, ph = leaf & 1, slot = inel[ph] ? nz++ : -1;
+          lf.insert(lf.end(), {top, depth - top, 0, (leaf << 12) | ((slot + 1) << 2) | (ph << 1)});
+          return;
+        }
+        if (cid[h] < 0) { go(Wh[2 * h] > 0.0 ? 2 * h : 2 * h + 1, depth, top); return; }
+        pre.push_back(cid[h]);
+        go(2 * h, depth + 1, top);
+        go(2 * h + 1, depth + 1, depth + 1);
+        post.push_back(cid[h]);
+        lf[lf.size() - 2] += 1;
+      }
+    } walk{*this, Wh, cid, inel, lf, pre, post, nz};
+    walk.go(1, 0, 0);
+    const int Lc = (int)lf.size() / 4;
+    for (int l = 0; l + 1 < Lc; ++l)
+      if (lf[4 * l + 2] == 0 && lf[4 * (l + 1) + 1] == 0) lf[4 * l + 3] |= 1;
+    tab = lf;
+    tab.insert(tab.end(), pre.begin(), pre.end());
+    tab.insert(tab.end(), post.begin(), post.end());
+    tab.insert(tab.end(), paper.begin(), paper.end());
+    N = Nc;
+    t.N = Nc; t.Lc = Lc; t.nz = nz; t.z_both = 0;
+    t.lf = reinterpret_cast<const int4*>(tab.data());
+    t.pre = tab.data() + 4 * Lc; t.post = t.pre + Nc; t.pidx = t.post + Nc;
+    t.p = hp.data(); t.q = hq.data();
+    t.c1 = c.data(); t.c2 = c.data() + Nc; t.sc = c.data() + 2 * Nc; t.wl = c.data() + 3 * Nc;
+    t.c1f = cf.data(); t.c2f = cf.data() + Nc; t.c12f = cf.data() + 2 * Nc;
+    t.wsum = s;
+    S = 6L * nz + 3L * Nc;
   }
   // one point: shape-function values, normals of every laminate (Sec. 2.3), the Mandel rotation R of its
   // frame and the macro strain in that frame, E_loc = R^T (E_n + dE)
@@ -164,7 +237,7 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
     for (int k = 0; k < 3 * N; ++k) abuf[0][k] = st[(6L * t.nz + k) * n + pt];
     PointArrays A;
     A.nrm = nrm.data(); A.ns = 1; A.nrmf = nrmf.data();
-    A.as = 1; A.paper = true;
+    A.as = 1; A.paper = !tr.cmp;
     A.z = st.data() + pt; A.zs = (size_t)n;
     // the persistent kernel's Newton loop for one point
     int it = 0, stt = -1, halvings = 0;
@@ -177,7 +250,8 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
       A.a_out = abuf[ls ? 1 - cur : cur].data();
       GH<T> gh{gbuf[cur].data(), 1, gbuf[ls ? 1 - cur : cur].data()};
       double r2;
-      tree_pass<T, true>(t, Eloc, A, gh, !first, step, root, r2, nullptr);
+      if (tr.cmp) tree_pass_c<T, true>(t, Eloc, A, gh, !first, step, root, r2, nullptr);
+      else tree_pass<T, true>(t, Eloc, A, gh, !first, step, root, r2, nullptr);
       double sn2 = 0.0;
       for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
       const double rn = std::sqrt(r2), sn = std::sqrt(sn2);
@@ -203,7 +277,8 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
       Sub<double> fin;
       double r2;
       GH<double> none{nullptr, 0, nullptr};
-      tree_pass<double, false>(t, Eloc, A, none, false, 1.0, fin, r2, nullptr);
+      if (tr.cmp) tree_pass_c<double, false>(t, Eloc, A, none, false, 1.0, fin, r2, nullptr);
+      else tree_pass<double, false>(t, Eloc, A, none, false, 1.0, fin, r2, nullptr);
       for (int I = 0; I < 6; ++I) { sl[I] = fin.sb[I]; for (int J = 0; J < 6; ++J) Cl[I][J] = fin.C[sidx(I, J)]; }
     } else {
       for (int I = 0; I < 6; ++I) { sl[I] = root.sb[I]; for (int J = 0; J < 6; ++J) Cl[I][J] = widen(root.C[sidx(I, J)]); }
@@ -220,7 +295,8 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
       }
     }
     for (int k = 0; k < 3 * N; ++k) so[(6L * t.nz + k) * n + pt] = a[k];
-    write_leaf_states(t, Eloc, A, so.data() + pt, (size_t)n, stt == 2);
+    if (tr.cmp) write_leaf_states_c(t, Eloc, A, so.data() + pt, (size_t)n, stt == 2);
+    else write_leaf_states(t, Eloc, A, so.data() + pt, (size_t)n, stt == 2);
   }
   fwrite(so.data(), 8, S * n, out); fwrite(stress.data(), 8, 6 * n, out); fwrite(tangent.data(), 8, 36 * n, out);
   fwrite(iters.data(), 8, n, out); fwrite(status.data(), 8, n, out);
@@ -238,7 +314,8 @@ static int run_grad(FILE* in, FILE* out, int K, int M, long n) {
   std::vector<double> lam(2 * n), Q(9 * n), En(6 * n), dE(6 * n), st_in(S * n), st_out(S * n), g(6 * n);
   rd(lam.data(), 2 * n, in); rd(Q.data(), 9 * n, in); rd(En.data(), 6 * n, in); rd(dE.data(), 6 * n, in);
   rd(st_in.data(), S * n, in); rd(st_out.data(), S * n, in); rd(g.data(), 6 * n, in);
-  std::vector<double> gp(N * M, 0.0), gq(N * M, 0.0), gwt(L, 0.0), gE(6 * n);
+  const int Nfull = L - 1;   // parameter gradients in the paper's ordering of the whole tree
+  std::vector<double> gp(Nfull * M, 0.0), gq(Nfull * M, 0.0), gwt(L, 0.0), gE(6 * n);
   std::vector<double> nrm(3 * N), a(3 * N), gh(21 * N), mu(3 * N), xi(N), gab(2 * N), direct(L), gw(L);
   for (long pt = 0; pt < n; ++pt) {
     double f[6], R[6][6], Eloc[6];
@@ -246,13 +323,14 @@ static int run_grad(FILE* in, FILE* out, int K, int M, long n) {
     for (int k = 0; k < 3 * N; ++k) a[k] = st_out[(6L * t.nz + k) * n + pt];
     PointArrays A;
     A.nrm = nrm.data(); A.ns = 1; A.nrmf = nullptr;
-    A.a = a.data(); A.as = 1; A.a_out = a.data(); A.paper = true;
+    A.a = a.data(); A.as = 1; A.a_out = a.data(); A.paper = !tr.cmp;
     A.z = st_in.data() + pt; A.zs = (size_t)n;
     // condensation at the converged jumps: g, H of every laminate and the tangent
     Sub<double> root;
     double r2;
     GH<double> ghv{gh.data(), 1, gh.data()};
-    tree_pass<double, true>(t, Eloc, A, ghv, false, 1.0, root, r2, nullptr);
+    if (tr.cmp) tree_pass_c<double, true>(t, Eloc, A, ghv, false, 1.0, root, r2, nullptr);
+    else tree_pass<double, true>(t, Eloc, A, ghv, false, 1.0, root, r2, nullptr);
     double gl[6];
     for (int J = 0; J < 6; ++J) {
       double acc = 0.0;
@@ -262,11 +340,16 @@ static int run_grad(FILE* in, FILE* out, int K, int M, long n) {
     AdjWork Wk;
     Wk.H = gh.data(); Wk.hs = 1; Wk.mu = mu.data(); Wk.xi = xi.data(); Wk.gab = gab.data();
     Wk.direct = direct.data(); Wk.ws = 1;
-    adjoint_pass(t, Eloc, gl, f, A, Wk);
-    adjoint_weights(t, t.wl, t.wsum, Wk, gw.data(), 1);
+    if (tr.cmp) {
+      adjoint_pass_c(t, Eloc, gl, f, A, Wk);
+      adjoint_weights_c(t, t.wl, t.wsum, Wk, gw.data(), 1);
+    } else {
+      adjoint_pass(t, Eloc, gl, f, A, Wk);
+      adjoint_weights(t, t.wl, t.wsum, Wk, gw.data(), 1);
+    }
     for (int node = 0; node < N; ++node) {
       const int lvl = 32 - __builtin_clz(node + 1);
-      const int j = L - 3 * (1 << (lvl - 1)) + node + 1;      // the paper's index of heap laminate `node`
+      const int j = tr.cmp ? t.pidx[node] : L - 3 * (1 << (lvl - 1)) + node + 1;   // the laminate's paper index
       for (int m = 0; m < M; ++m) { gp[j * M + m] += gab[node] * f[m]; gq[j * M + m] += gab[N + node] * f[m]; }
     }
     for (int l = 0; l < L; ++l) gwt[l] += gw[l];
@@ -281,7 +364,7 @@ static int run_grad(FILE* in, FILE* out, int K, int M, long n) {
       gE[6 * pt + I] = acc;
     }
   }
-  fwrite(gp.data(), 8, N * M, out); fwrite(gq.data(), 8, N * M, out); fwrite(gwt.data(), 8, L, out);
+  fwrite(gp.data(), 8, Nfull * M, out); fwrite(gq.data(), 8, Nfull * M, out); fwrite(gwt.data(), 8, L, out);
   fwrite(gE.data(), 8, 6 * n, out);
   return 0;
 }
@@ -448,3 +531,57 @@ def test_device_line_search_matches_the_oracle(harness):
         assert rel(C_h[ok], C_o[ok]).max(initial=0.0) <= 1e-10, s
         assert np.abs(it_h[alive] - it_o[alive]).max(initial=0) <= 1
     assert differs > 0          # the search was active on this path
+
+
+@pytest.mark.parametrize("K,prec", [(5, 0), (7, 0), (7, 1), (7, 2)])
+def test_device_compressed_traversal_matches_the_oracle(harness, K, prec):
+    """Trees with weightless leaves, walked by the compression tables (restated in the harness from
+    their documented format), against the oracle's compression."""
+    tree = W.tree_with_zero_weights(K, seed=90 + K)
+    n = 24
+    A2, lam, Q = W.orientation_field(n, seed=91)
+    Ef = W.random6_path_final(n, 0.03, seed=92)
+    S = oracle.state_size(K, tree.phases, tree.w)
+    assert S < W.state_size(K)
+    sh, so = np.zeros((S, n)), np.zeros((S, n))
+    tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6)}[prec]
+    alive = np.ones(n, dtype=bool)
+    for s in range(1, 9):
+        En, dE = W.proportional_increment(Ef, s, 20)
+        sh, sig_h, C_h, it_h, stat_h = run_harness(harness, tree, lam, Q, En, dE, sh, prec)
+        so, sig_o, C_o, it_o, stat_o, gap = oracle.update(tree, lam, Q, En, dE, so)
+        alive &= (stat_o == 0) & (stat_h == 0)
+        assert alive.mean() > 0.9, (s, alive.mean())
+        assert rel(sig_h[alive], sig_o[alive]).max() <= tol_s, s
+        ok = alive & (gap > 1e-9)
+        assert rel(C_h[ok], C_o[ok]).max() <= tol_c, s
+        scale = np.abs(so[:, alive]).max(axis=1, keepdims=True) + 1e-300
+        assert (np.abs(sh[:, alive] - so[:, alive]) / scale).max() <= (1e-9 if prec == 0 else 1e-5), s
+        if prec == 0:
+            assert np.abs(it_h[alive] - it_o[alive]).max() <= 1
+
+
+def test_device_adjoint_of_a_compressed_tree(harness):
+    K, n, steps = 4, 3, 5
+    tree = W.tree_with_zero_weights(K, seed=95)
+    A2, lam, Q = W.orientation_field(n, seed=96)
+    Ef = W.random6_path_final(n, 0.03, seed=97)
+    st = np.zeros((oracle.state_size(K, tree.phases, tree.w), n))
+    for s in range(1, steps + 1):
+        En, dE = W.proportional_increment(Ef, s, 10)
+        prev = st
+        st, sig, C, it, stat, gap = oracle.update(tree, lam, Q, En, dE, prev)
+    assert (stat == 0).all()
+    g = np.random.default_rng(98).standard_normal((n, 6))
+    gp, gq, gw, gE = run_grad_harness(harness, tree, lam, Q, En, dE, prev, st, g)
+    ref = dict(p=0.0, q=0.0, w=0.0)
+    for i in range(n):
+        gi = oracle.gradient_ift(tree, lam[i], Q[i], (En + dE)[i], oracle.jumps(tree, st, i),
+                                 oracle.leaf_states(tree, prev, i), g[i])
+        for k in ref:
+            ref[k] = ref[k] + gi[k]
+    for k, got in (("p", gp), ("q", gq), ("w", gw)):
+        err = np.abs(got - ref[k]).max() / np.abs(ref[k]).max()
+        assert err < 1e-6, (k, err)
+    assert (gw[np.asarray(tree.w) == 0] == 0).all()
+    np.testing.assert_allclose(gE, np.einsum("nij,nj->ni", C, g), rtol=1e-9, atol=1e-9 * np.abs(gE).max())
