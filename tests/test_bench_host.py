@@ -5,8 +5,10 @@ The per-laminate and per-leaf counts are constants counted from the kernels'
 arithmetic.  These tests pin what follows from them and from the tree's
 structure: the per-pass totals of the full depth-8 tree (31,548 FP64 and
 168,499 condensation flops) and of the benchmark's compressed tree (178
-laminates), and the structure of compressed trees against the oracle's own
-compression, whose state holds 6 values per inelastic leaf and 3 per laminate.
+laminates), the structure of compressed trees against the oracle's own
+compression, whose state holds 6 values per inelastic leaf and 3 per laminate,
+and the roofline arithmetic of the JSON line (flops per launch, achieved rate,
+derived FP64 peak, the mixed forms' F64/P64 + F32/P32 bound).
 """
 import numpy as np
 
@@ -51,3 +53,27 @@ def test_benchmark_compressed_tree():
     assert c["N"] == 178
     f64, ft = bench.pass_flops(bench.K_DEPTH, tree.w)
     assert round(f64 / 100) == 218 and round(ft / 100) == 1191     # 21.8 k + 119.1 k per pass
+
+
+def test_roofline_arithmetic():
+    """The FP64 line's roofline from its parts: flops per launch = (corrections + points) x flops per
+    pass + corrections x flops per correction; achieved = flops / Newton time; the peak is
+    152 SMs x 4 SMSPs x 0.5 DFMA per clock x 2 flops x 2.07 GHz.  With the figures of a 2^20-point run
+    (3.6615 corrections per update, 1245.6 ms per launch) that is 1.0189e12 flops and 0.650 of the peak."""
+    n, steps = 1 << 20, 10
+    iters = 3.661489200592041 * n * steps
+    r = {"iters_sum": iters, "kms": {"newton": 1245.6054931640624 * steps, "final": 22.67 * steps}}
+    line = bench.roofline_f64(r, n, steps)
+    per_launch = ((iters / steps + n) * (31548 + 168499) + iters / steps * (255 * 3 + 255 * 39))
+    assert abs(line["flops_per_launch"] - per_launch) <= 1e-9 * per_launch
+    assert abs(line["flops_per_launch"] - 1.0189343e12) <= 1e-6 * 1.0189343e12
+    peak = 152 * 4 * 0.5 * 2 * 2.07
+    assert line["peak"] == peak and abs(line["frac"] - line["achieved"] / peak) <= 1e-12
+    assert abs(line["achieved"] - per_launch / 1.2456054931640624 / 1e9) <= 1e-9 * line["achieved"]
+    assert round(line["frac"], 3) == 0.650
+    # the mixed forms: the Newton kernel against F64/P64 + F32/P32
+    mx = bench.roofline_mixed(r, n, steps, sweep=True)
+    f64 = (iters / steps + n) * 31548 + iters / steps * 255 * 3
+    f32 = (iters / steps + n) * 168499 + iters / steps * 255 * 39
+    t_bound = f64 / (peak * 1e9) + f32 / (152 * 128 * 2 * 2.07 * 1e9)
+    assert abs(mx["frac"] - t_bound / 1.2456054931640624) <= 1e-9 * mx["frac"]
