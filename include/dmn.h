@@ -27,7 +27,8 @@
  *     equivalent plastic strain and the deviatoric plastic strain
  *     (ep33 = -ep11 - ep22); then three jump components per laminate in the
  *     paper's ordering (level K first, root last; Sec. 3.2, Eq. of the normal
- *     ordering).  With the extrapolated start (dmn_options.predictor = 1) more
+ *     ordering).  A compressed tree (leaf weights of zero, Sec. 3.1) keeps
+ *     only its remaining inelastic leaves and laminates, in the same orders.  With the extrapolated start (dmn_options.predictor = 1) more
  *     fields follow: the jump change a^{n+1} - a^n of the last update (same
  *     ordering, three per laminate), then that update's strain increment dE
  *     (six, Mandel, global frame).  A zero state is the virgin state.
@@ -112,7 +113,9 @@ typedef struct {
   int32_t M;         /* shape functions: 3 linear, 4 tri-linear, 6 quadratic (Tab. of shape functions) */
   const double* p;   /* host [(2^K-1) * M]: alpha_j = p_j . phi(lam1, lam2) (rad), paper ordering (Sec. 3.1) */
   const double* q;   /* host [(2^K-1) * M]: beta_j  = q_j . phi(lam1, lam2) (rad) */
-  const double* w;   /* host [2^K]: leaf weights, all > 0; normalised to sum 1 (Sec. 2.1) */
+  const double* w;   /* host [2^K]: leaf weights >= 0, not all zero; normalised to sum 1 (Sec. 2.1).
+                      * Leaves of weight zero are removed and the tree compressed (Sec. 3.1): a laminate
+                      * with one weightless side is replaced by the other side. */
   dmn_phase phase[2];/* phase 1 = odd leaves, phase 2 = even leaves (Sec. 2.1) */
 } dmn_tree_desc;
 
@@ -148,7 +151,8 @@ typedef struct {
  * weights to the laminate volume fractions (Sec. 2.1) and allocates the work
  * space of the persistent Newton kernel on the current CUDA device.  opt may
  * be NULL (defaults).  Errors: DMN_ERR_ARG for n_trees out of range, K outside
- * 1..8, M not in {3,4,6}, a weight <= 0 or non-finite, an unknown phase kind,
+ * 1..8, M not in {3,4,6}, a weight < 0 or non-finite, all weights zero, NULL
+ * or non-finite p, q, an unknown phase kind,
  * non-positive moduli or hardening parameters outside the ranges above; DMN_ERR_CUDA if an allocation fails.  On error *out
  * is NULL. */
 int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* opt, dmn_handle** out);
@@ -295,9 +299,10 @@ int dmn_profile_read(dmn_handle* h, double ms[3], int64_t* updates);
  * caller.  Each call re-uploads the tree and clears the counter.
  *
  * Arguments are those of dmn_create (tree, opt) and dmn_update (n and the
- * arrays, same layouts and ownership).  Only the FP64 form is offered
- * (opt->precision must be DMN_PREC_F64 and opt->predictor 0; opt may be NULL); opt->block and
- * opt->ctas_per_sm are ignored.  The static work space limits parallelism:
+ * arrays, same layouts and ownership), for one uncompressed tree: all leaf
+ * weights must be > 0.  Only the FP64 form with full Newton steps is offered
+ * (opt->precision must be DMN_PREC_F64 and opt->predictor 0; opt may be NULL);
+ * opt->line_search, opt->block and opt->ctas_per_sm are ignored.  The static work space limits parallelism:
  * 1152 lanes at K = 8 (more for shallower trees), so it is slower than
  * dmn_update.  Errors: DMN_ERR_ARG for the argument errors of dmn_create and
  * dmn_update and for a tree whose parameters or one CTA of scratch do not fit
