@@ -58,6 +58,10 @@ def _load():
         lib.oracle_interp_orientation.argtypes = [ctypes.c_long, _D, _D, _D]
         lib.oracle_state_size.argtypes = [ctypes.c_int, _D]
         lib.oracle_state_size_w.argtypes = [ctypes.c_int, _D, _D]
+        lib.oracle_eval_dual.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, ctypes.c_double,
+                                         ctypes.c_double, _D, _D, _D, _D, _D, ctypes.c_int, _D, _D, _D, _D, _D, _D]
+        lib.oracle_gradient.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_double,
+                                        ctypes.c_double, _D, _D, _D, _D, _D, _D, _D, _D, _D]
         _lib = lib
     return _lib
 
@@ -250,7 +254,7 @@ def interp_orientation(A2):
 
 
 __all__ = ["build", "update", "normals", "barycentric", "gradient_operator", "newton_system", "phase_law",
-           "rotate", "interp_orientation", "state_size", "phases_array"]
+           "rotate", "interp_orientation", "state_size", "phases_array", "eval_dual", "gradient_ift"]
 if "--build" in sys.argv[1:]:  # pragma: no cover
     print(build(force=True))
 
@@ -267,61 +271,76 @@ def _with_params(tree, p=None, q=None, w=None):
     return t
 
 
-def gradient_ift(tree, lam, Q, E_glob, a_star, z_leaf, g_glob, directions=None, h=1e-6):
-    """Gradient of g . sigma_bar at the converged jumps a_star of one point by the
-    implicit function theorem applied to R(a, theta) = A^T W sigma = 0 (Sec. 3.2):
-        dL/dtheta = g . d sigma_bar/d theta|_a - lambda . dR/d theta|_a,
-        J lambda = (d sigma_bar / d a)^T g,   J = A^T W D A (the oracle's dense matrix).
-    The partial derivatives at fixed jumps are central differences of the oracle's
-    own evaluation (step h), the solve is numpy's dense solve.  theta = (p, q, w) with w
-    the leaf weights before normalisation.
+def eval_dual(tree, lam1, lam2, E_loc, a, z_n, dp=None, dq=None, dw=None, dE=None, da=None, tangent=False):
+    """Exact directional derivatives at fixed z^n (local frame; forward-mode dual numbers of
+    dmn_oracle.c): R = A^T W sigma, sigma_bar and, with tangent=True, the algorithmic tangent C,
+    at (p, q, w, E_loc, a), each with its derivative along (dp, dq, dw, dE, da) (zeros where
+    None).  w is the weight vector as given (before normalisation); z_n [2^K, 7] per leaf."""
+    p = _f64(tree.p); q = _f64(tree.q); w = _f64(tree.w); m = phases_array(tree.phases)
+    a = _f64(a)
+    n_a = a.size
+    z = lambda x, like: _f64(np.zeros_like(like) if x is None else x)
+    dp, dq, dw = z(dp, p), z(dq, q), z(dw, w)
+    dE, da = z(dE, np.zeros(6)), z(da, a)
+    R = np.empty(max(n_a, 1)); dR = np.empty(max(n_a, 1)); sb = np.empty(6); dsb = np.empty(6)
+    C = np.empty(36); dC = np.empty(36)
+    rc = _load().oracle_eval_dual(tree.K, tree.M, _p(p), _p(q), _p(w), _p(m), _p(dp), _p(dq), _p(dw),
+                                  float(lam1), float(lam2), _p(_f64(E_loc)), _p(dE), _p(a), _p(da),
+                                  _p(_f64(z_n)), int(bool(tangent)), _p(R), _p(dR), _p(sb), _p(dsb), _p(C), _p(dC))
+    if rc != 0:
+        raise ValueError("oracle_eval_dual failed (rc=%d)" % rc)
+    out = dict(R=R[:n_a], dR=dR[:n_a], sbar=sb, dsbar=dsb)
+    if tangent:
+        out.update(C=C.reshape(6, 6), dC=dC.reshape(6, 6))
+    return out
 
-    directions: None for the full gradient (dict with 'p', 'q', 'w'), or a list of
-    (dp, dq, dw) triples for directional derivatives.  Also returns dL/dE = C g with C
-    from the oracle's update tangent (global frame) when the caller passes it in."""
+
+def gradient_ift(tree, lam, Q, E_glob, a_star, z_leaf, g_glob, directions=None, G_glob=None):
+    """Gradient of L = g . sigma_bar (+ G : C with a tangent seed G) at the converged jumps
+    a_star of one point, by the implicit function theorem applied to R(a, theta) = A^T W sigma = 0
+    (Sec. 3.2):
+        J lam = (d sigma_bar/d a)^T g + (dC/da)^T : G,   J = A^T W D A,
+        dL/dtheta = g . d sigma_bar/d theta|_a + G : dC/d theta|_a - lam . dR/d theta|_a.
+    Every partial derivative is exact (dual numbers, oracle_gradient in dmn_oracle.c) and the
+    solve uses the oracle's Cholesky factor of J.  theta = (p, q, w) with w the leaf weights
+    before normalisation, and the macro strain E.  g_glob [6] and G_glob [6, 6] (or None) are
+    in the global frame; returns dict(p, q, w, E) with E in the global frame.
+
+    directions: a list of (dp, dq, dw) triples; returns the directional derivatives by the
+    forward route instead (tangent-linear sensitivities: da = -J^-1 dR/dtheta, then the total
+    derivative of sigma_bar and C along (dtheta, da) from one more dual evaluation)."""
     lam = np.asarray(lam, dtype=np.float64)
     Qm = np.asarray(Q, dtype=np.float64).reshape(3, 3)
     _, E_loc = rotate(Qm.T, np.zeros((6, 6)), E_glob)
     _, g_loc = rotate(Qm.T, np.zeros((6, 6)), g_glob)
-    p0, q0, w0 = (np.array(x, dtype=np.float64) for x in (tree.p, tree.q, tree.w))
-
-    def ev(tr, a):
-        s = newton_system(tr, lam[0], lam[1], E_loc, a, z_leaf)
-        return s["sbar"], s["R"], s["J"]
-
-    s0, R0, J = ev(tree, a_star)
-    n_a = a_star.size
-    dsda = np.empty((6, n_a))
-    for k in range(n_a):
-        e = np.zeros(n_a)
-        e[k] = h
-        dsda[:, k] = (ev(tree, a_star + e)[0] - ev(tree, a_star - e)[0]) / (2 * h)
-    lamv = np.linalg.solve(J, dsda.T @ g_loc)
-
-    def partial(dp, dq, dw, step):
-        sp, Rp, _ = ev(_with_params(tree, p0 + step * dp, q0 + step * dq, w0 + step * dw), a_star)
-        sm, Rm, _ = ev(_with_params(tree, p0 - step * dp, q0 - step * dq, w0 - step * dw), a_star)
-        return g_loc @ (sp - sm) / (2 * step) - lamv @ (Rp - Rm) / (2 * step)
-
-    hw = h * w0.max()
-    alive = w0 > 0   # weights of zero stay out: a step would change the compressed tree
+    G_loc = None
+    if G_glob is not None:
+        G_loc, _ = rotate(Qm.T, np.asarray(G_glob, dtype=np.float64).reshape(6, 6), np.zeros(6))
+    a_star = _f64(a_star)
+    z_leaf = _f64(z_leaf)
     if directions is not None:
-        return [partial(dp, dq, dw, h) for dp, dq, dw in directions]
-    gp = np.zeros_like(p0)
-    gq = np.zeros_like(q0)
-    gw = np.zeros_like(w0)
-    for idx in np.ndindex(p0.shape):
-        e = np.zeros_like(p0)
-        e[idx] = 1.0
-        gp[idx] = partial(e, 0 * q0, 0 * w0, h)
-        gq[idx] = partial(0 * p0, e, 0 * w0, h)
-    for l in range(w0.size):
-        if not alive[l]:
-            continue
-        e = np.zeros_like(w0)
-        e[l] = 1.0
-        gw[l] = partial(0 * p0, 0 * q0, e, hw)
-    return dict(p=gp, q=gq, w=gw)
+        J = newton_system(tree, lam[0], lam[1], E_loc, a_star, z_leaf)["J"]
+        vals = []
+        for dp, dq, dw in directions:
+            r1 = eval_dual(tree, lam[0], lam[1], E_loc, a_star, z_leaf, dp, dq, dw)
+            da = -np.linalg.solve(J, r1["dR"])
+            r2 = eval_dual(tree, lam[0], lam[1], E_loc, a_star, z_leaf, dp, dq, dw, da=da,
+                           tangent=G_loc is not None)
+            v = g_loc @ r2["dsbar"]
+            if G_loc is not None:
+                v += (G_loc * r2["dC"]).sum()
+            vals.append(v)
+        return vals
+    p = _f64(tree.p); q = _f64(tree.q); w = _f64(tree.w); m = phases_array(tree.phases)
+    gp = np.empty_like(p); gq = np.empty_like(q); gw = np.empty_like(w); gE = np.empty(6)
+    Gp = _p(_f64(G_loc)) if G_loc is not None else None
+    rc = _load().oracle_gradient(tree.K, tree.M, _p(p), _p(q), _p(w), _p(m), float(lam[0]), float(lam[1]),
+                                 _p(_f64(E_loc)), _p(a_star), _p(z_leaf), _p(_f64(g_loc)), Gp, _p(gp), _p(gq),
+                                 _p(gw), _p(gE))
+    if rc != 0:
+        raise ValueError("oracle_gradient failed (rc=%d)" % rc)
+    _, gE_glob = rotate(Qm, np.zeros((6, 6)), gE)
+    return dict(p=gp, q=gq, w=gw, E=gE_glob)
 
 
 def leaf_states(tree, state, i):

@@ -801,6 +801,377 @@ int oracle_rotate(const double* Q, const double* Cl, const double* vl, double* C
   return 0;
 }
 
+/* ================================================================== */
+/* Exact derivatives by forward-mode dual numbers.
+ *
+ * A dual number x = v + d e (e^2 = 0) carries a value v and the derivative d
+ * of that value along one chosen direction of the inputs.  Every operation
+ * below applies the matching rule of differentiation, so each function written
+ * on duals returns the exact directional derivative of what its double
+ * counterpart above computes (no step size, no truncation error):
+ *   - the normals of Sec. 2.3 through the angle coefficients p, q;
+ *   - the normalised leaf weights and the volume fractions of Sec. 2.1
+ *     through the leaf weights w as given (before their normalisation);
+ *   - the leaf strains E + A a (Sec. 3.2) through E, a, the normals and the
+ *     fractions;
+ *   - the phase laws (Sec. 4.1; the exponential-linear law's scalar Newton
+ *     iteration carries its derivative along and ends at the implicit
+ *     derivative of the consistency condition);
+ *   - the residual R = A^T W sigma (Eq. euler_lagrange), the effective stress
+ *     sum w_i sigma_i and the algorithmic tangent of Eq. (lin_system_da_dE),
+ *     whose six right-hand sides are differentiated through the Cholesky
+ *     solve: d(J^-1 b) = J^-1 (db - dJ J^-1 b).
+ * oracle_gradient assembles from these partial derivatives the
+ * implicit-function gradient of the converged solve (Sec. 3.2). */
+typedef struct { double v, d; } dual;
+static dual dn(double v, double d) { dual r; r.v = v; r.d = d; return r; }
+static dual dc(double v) { return dn(v, 0.0); }
+static dual d_add(dual a, dual b) { return dn(a.v + b.v, a.d + b.d); }
+static dual d_sub(dual a, dual b) { return dn(a.v - b.v, a.d - b.d); }
+static dual d_mul(dual a, dual b) { return dn(a.v * b.v, a.d * b.v + a.v * b.d); }
+static dual d_div(dual a, dual b) { return dn(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+static dual d_scale(double s, dual a) { return dn(s * a.v, s * a.d); }
+static dual d_sqrt(dual a) { double r = sqrt(a.v); return dn(r, a.d / (2.0 * r)); }
+static dual d_sin(dual a) { return dn(sin(a.v), cos(a.v) * a.d); }
+static dual d_cos(dual a) { return dn(cos(a.v), -sin(a.v) * a.d); }
+static dual d_exp(dual a) { double e = exp(a.v); return dn(e, e * a.d); }
+/* a + b c */
+static dual d_fma(dual a, dual b, dual c) { return d_add(a, d_mul(b, c)); }
+
+/* sigma_Y and its slope at a dual alpha_bar (yield_stress on duals) */
+static dual yield_stress_dual(const or_phase* ph, dual ab, dual* slope) {
+  if (ph->kind == 2 && ph->sinf > ph->s0) {
+    double ds = ph->sinf - ph->s0, r = (ph->k0 - ph->H) / ds;
+    dual e = d_exp(d_scale(-r, ab));
+    if (slope) *slope = d_add(dc(ph->H), d_scale(ph->k0 - ph->H, e));
+    return d_add(d_add(dc(ph->s0), d_scale(ph->H, ab)), d_scale(ds, d_sub(dc(1.0), e)));
+  }
+  if (slope) *slope = dc(ph->H);
+  return d_add(dc(ph->s0), d_scale(ph->H, ab));
+}
+
+/* phase_law on a dual strain; z_n is fixed (the state of the last increment).
+ * The elastic/plastic branch is the one the value takes. */
+static void phase_law_dual(const or_phase* ph, const dual eps[6], const double z_n[7], dual sig[6], dual D[6][6]) {
+  double K = ph->E / (3.0 * (1.0 - 2.0 * ph->nu));
+  double G = ph->E / (2.0 * (1.0 + ph->nu));
+  dual tr = d_add(d_add(eps[0], eps[1]), eps[2]);
+  dual dev[6];
+  for (int I = 0; I < 6; ++I) dev[I] = I < 3 ? d_sub(eps[I], d_scale(1.0 / 3.0, tr)) : eps[I];
+  double Idev[6][6];
+  for (int I = 0; I < 6; ++I)
+    for (int J = 0; J < 6; ++J) Idev[I][J] = (I == J ? 1.0 : 0.0) - ((I < 3 && J < 3) ? 1.0 / 3.0 : 0.0);
+  int elastic = ph->kind == 0;
+  dual str[6], ns = dc(0.0), f = dc(-1.0);
+  if (!elastic) {
+    dual nrm2 = dc(0.0);
+    for (int I = 0; I < 6; ++I) { str[I] = d_scale(2.0 * G, d_sub(dev[I], dc(z_n[1 + I]))); nrm2 = d_fma(nrm2, str[I], str[I]); }
+    ns = d_sqrt(nrm2);
+    f = d_sub(ns, dc(sqrt(2.0 / 3.0) * yield_stress(ph, z_n[0], NULL)));
+  }
+  if (elastic || f.v <= 0.0) {
+    for (int I = 0; I < 6; ++I)
+      sig[I] = d_add(I < 3 ? d_scale(K, tr) : dc(0.0), elastic ? d_scale(2.0 * G, dev[I]) : str[I]);
+    if (D)
+      for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J) D[I][J] = dc(((I < 3 && J < 3) ? K : 0.0) + 2.0 * G * Idev[I][J]);
+    return;
+  }
+  dual dg, Hp;
+  if (ph->kind == 1) {
+    dg = d_scale(1.0 / (2.0 * G + 2.0 * ph->H / 3.0), f);
+    Hp = dc(ph->H);
+  } else {
+    dg = dc(0.0);
+    for (int it = 0; it < 100; ++it) {
+      dual slope;
+      dual sy = yield_stress_dual(ph, d_add(dc(z_n[0]), d_scale(sqrt(2.0 / 3.0), dg)), &slope);
+      dual r = d_sub(d_sub(ns, d_scale(2.0 * G, dg)), d_scale(sqrt(2.0 / 3.0), sy));
+      dual step = d_div(r, d_add(dc(2.0 * G), d_scale(2.0 / 3.0, slope)));
+      dg = d_add(dg, step);
+      if (fabs(step.v) <= 1e-15 * dg.v) break;
+    }
+    yield_stress_dual(ph, d_add(dc(z_n[0]), d_scale(sqrt(2.0 / 3.0), dg)), &Hp);
+  }
+  dual nh[6];
+  for (int I = 0; I < 6; ++I) nh[I] = d_div(str[I], ns);
+  dual th = d_sub(dc(1.0), d_div(d_scale(2.0 * G, dg), ns));
+  dual thb = d_sub(d_div(dc(1.0), d_add(dc(1.0), d_scale(1.0 / (3.0 * G), Hp))), d_sub(dc(1.0), th));
+  for (int I = 0; I < 6; ++I)
+    sig[I] = d_sub(d_add(I < 3 ? d_scale(K, tr) : dc(0.0), str[I]), d_scale(2.0 * G, d_mul(dg, nh[I])));
+  if (D)
+    for (int I = 0; I < 6; ++I)
+      for (int J = 0; J < 6; ++J)
+        D[I][J] = d_sub(d_add(dc((I < 3 && J < 3) ? K : 0.0), d_scale(2.0 * G * Idev[I][J], th)),
+                        d_scale(2.0 * G, d_mul(thb, d_mul(nh[I], nh[J]))));
+}
+
+/* Per-point dual work space. */
+typedef struct {
+  dual nrm[OR_NMAX][3];
+  double Nv[OR_NMAX][6][3], Nd[OR_NMAX][6][3];   /* N(n) and its derivative (N is linear in n) */
+  dual wn[OR_LMAX], c1[OR_NMAX], c2[OR_NMAX];
+  dual eps[OR_LMAX][6], sig[OR_LMAX][6], D[OR_LMAX][6][6];
+  dual R[3 * OR_NMAX], sbar[6], C[6][6];
+} or_dual;
+
+/* entry (I, m) of N_j on duals */
+static dual Nm_dual(const or_dual* u, int j, int I, int m) { return dn(u->Nv[j][I][m], u->Nd[j][I][m]); }
+/* coefficient of laminate j's block in leaf l's row of A: -c2 (left subtree) or +c1 (right) */
+static dual coef_dual(const or_tree* t, const or_dual* u, int l, int k) {
+  int j = t->anc_node[l][k];
+  return t->anc_coef[l][k] < 0.0 ? d_scale(-1.0, u->c2[j]) : u->c1[j];
+}
+
+/* One evaluation at (p + e dp, q + e dq, w + e dw, E + e dE, a + e da) with z^n
+ * fixed: R, sigma_bar and (when fac holds the Cholesky factor of J at the
+ * values) the algorithmic tangent, each with its derivative.  w_raw are the
+ * weights as given; t was initialised with them. */
+static void eval_dual(const or_tree* t, or_dual* u, const double* w_raw, const double* dp, const double* dq,
+                      const double* dw, double lam1, double lam2, const double* E, const double* dE,
+                      const double* a, const double* da, const double z_n[][7], or_work* fac) {
+  /* normals: alpha_j = p_j . phi, beta_j = q_j . phi (phi fixed by the orientation) */
+  double v[3], ph[6];
+  barycentric(lam1, lam2, v);
+  shape_functions(t->M, v, ph);
+  for (int j = 0; j < t->N; ++j) {
+    dual al = dc(0.0), be = dc(0.0);
+    for (int m = 0; m < t->M; ++m) {
+      al = d_add(al, dn(t->p[j * t->M + m] * ph[m], dp[j * t->M + m] * ph[m]));
+      be = d_add(be, dn(t->q[j * t->M + m] * ph[m], dq[j * t->M + m] * ph[m]));
+    }
+    u->nrm[j][0] = d_mul(d_sin(al), d_cos(be));
+    u->nrm[j][1] = d_mul(d_sin(al), d_sin(be));
+    u->nrm[j][2] = d_cos(al);
+    double nv[3] = {u->nrm[j][0].v, u->nrm[j][1].v, u->nrm[j][2].v};
+    double nd[3] = {u->nrm[j][0].d, u->nrm[j][1].d, u->nrm[j][2].d};
+    sym_operator(nv, u->Nv[j]);
+    sym_operator(nd, u->Nd[j]);
+  }
+  /* weights normalised to sum 1, subtree weights and fractions, leaves -> root */
+  dual sw = dc(0.0);
+  for (int l = 0; l < t->L; ++l) sw = d_add(sw, dn(w_raw[l], dw[l]));
+  dual Wlev[OR_LMAX];
+  for (int l = 0; l < t->L; ++l) { u->wn[l] = d_div(dn(w_raw[l], dw[l]), sw); Wlev[l] = u->wn[l]; }
+  for (int k = t->K; k >= 1; --k)
+    for (int i = 1; i <= (1 << (k - 1)); ++i) {
+      dual wl = Wlev[2 * i - 2], wr = Wlev[2 * i - 1], W = d_add(wl, wr);
+      int j = node_index(t->K, k, i);
+      u->c1[j] = W.v > 0.0 ? d_div(wl, W) : dc(0.5);
+      u->c2[j] = d_sub(dc(1.0), u->c1[j]);
+      Wlev[i - 1] = W;
+    }
+  /* leaf strains, laws, effective stress and residual */
+  for (int l = 0; l < t->L; ++l) {
+    for (int I = 0; I < 6; ++I) u->eps[l][I] = dn(E[I], dE[I]);
+    for (int k = 0; k < t->nanc[l]; ++k) {
+      int j = t->anc_node[l][k], cj = t->cidx[j];
+      dual c = coef_dual(t, u, l, k);
+      for (int I = 0; I < 6; ++I)
+        for (int m = 0; m < 3; ++m)
+          u->eps[l][I] = d_fma(u->eps[l][I], c, d_mul(Nm_dual(u, j, I, m), dn(a[3 * cj + m], da[3 * cj + m])));
+    }
+    phase_law_dual(&t->ph[l % 2], u->eps[l], z_n[l], u->sig[l], fac ? u->D[l] : NULL);
+  }
+  for (int I = 0; I < 6; ++I) u->sbar[I] = dc(0.0);
+  for (int l = 0; l < t->L; ++l)
+    for (int I = 0; I < 6; ++I) u->sbar[I] = d_fma(u->sbar[I], u->wn[l], u->sig[l][I]);
+  for (int r = 0; r < 3 * t->nact; ++r) u->R[r] = dc(0.0);
+  for (int l = 0; l < t->L; ++l)
+    for (int k = 0; k < t->nanc[l]; ++k) {
+      int j = t->anc_node[l][k], cj = t->cidx[j];
+      dual c = d_mul(coef_dual(t, u, l, k), u->wn[l]);
+      for (int m = 0; m < 3; ++m)
+        for (int I = 0; I < 6; ++I)
+          u->R[3 * cj + m] = d_fma(u->R[3 * cj + m], c, d_mul(Nm_dual(u, j, I, m), u->sig[l][I]));
+    }
+  if (!fac) return;
+  /* algorithmic tangent C = sum_l w_l D_l (I + A_l X), J X = -A^T W D [I..I]:
+   * X from the factor of J at the values; dX = J^-1 (dB - dJ X), with dJ the
+   * derivative of J = A^T W D A assembled on duals and dB that of the RHS. */
+  int n = 3 * t->nact;
+  double* dJ = (double*)calloc((size_t)n * n, sizeof(double));
+  double* X = (double*)malloc(sizeof(double) * (size_t)n * 6);
+  double* dX = (double*)malloc(sizeof(double) * (size_t)n * 6);
+  for (int i = 0; i < n * 6; ++i) { X[i] = 0.0; dX[i] = 0.0; }
+  for (int l = 0; l < t->L; ++l) {
+    dual DN[OR_KMAX][6][3];
+    for (int k = 0; k < t->nanc[l]; ++k) {
+      int j = t->anc_node[l][k];
+      for (int I = 0; I < 6; ++I)
+        for (int m = 0; m < 3; ++m) {
+          dual s = dc(0.0);
+          for (int P = 0; P < 6; ++P) s = d_fma(s, u->D[l][I][P], Nm_dual(u, j, P, m));
+          DN[k][I][m] = s;
+        }
+    }
+    for (int k1 = 0; k1 < t->nanc[l]; ++k1) {
+      int j1 = t->anc_node[l][k1], r1 = 3 * t->cidx[j1];
+      dual cw1 = d_mul(u->wn[l], coef_dual(t, u, l, k1));
+      for (int k2 = 0; k2 < t->nanc[l]; ++k2) {
+        int r2 = 3 * t->cidx[t->anc_node[l][k2]];
+        dual c = d_mul(cw1, coef_dual(t, u, l, k2));
+        for (int m1 = 0; m1 < 3; ++m1)
+          for (int m2 = 0; m2 < 3; ++m2) {
+            dual s = dc(0.0);
+            for (int I = 0; I < 6; ++I) s = d_fma(s, Nm_dual(u, j1, I, m1), DN[k2][I][m2]);
+            dJ[(size_t)(r1 + m1) * n + r2 + m2] += d_mul(c, s).d;
+          }
+      }
+      /* right-hand sides -A^T W D e_col and their derivatives */
+      for (int col = 0; col < 6; ++col)
+        for (int m = 0; m < 3; ++m) {
+          dual s = dc(0.0);
+          for (int I = 0; I < 6; ++I) s = d_fma(s, Nm_dual(u, j1, I, m), u->D[l][I][col]);
+          dual b = d_mul(cw1, s);
+          X[(size_t)col * n + r1 + m] -= b.v;
+          dX[(size_t)col * n + r1 + m] -= b.d;
+        }
+    }
+  }
+  for (int col = 0; col < 6; ++col) {
+    double* x = X + (size_t)col * n;
+    double* dx = dX + (size_t)col * n;
+    chol_solve(t, fac, x);
+    for (int r = 0; r < n; ++r) {
+      double s = 0.0;
+      for (int c = 0; c < n; ++c) s += dJ[(size_t)r * n + c] * x[c];
+      dx[r] -= s;
+    }
+    chol_solve(t, fac, dx);
+  }
+  for (int I = 0; I < 6; ++I) for (int J = 0; J < 6; ++J) u->C[I][J] = dc(0.0);
+  for (int l = 0; l < t->L; ++l) {
+    dual Gm[6][6];   /* I + (A X)_l */
+    for (int I = 0; I < 6; ++I) for (int J = 0; J < 6; ++J) Gm[I][J] = dc(I == J ? 1.0 : 0.0);
+    for (int k = 0; k < t->nanc[l]; ++k) {
+      int j = t->anc_node[l][k], r0 = 3 * t->cidx[j];
+      dual c = coef_dual(t, u, l, k);
+      for (int I = 0; I < 6; ++I)
+        for (int col = 0; col < 6; ++col)
+          for (int m = 0; m < 3; ++m)
+            Gm[I][col] = d_fma(Gm[I][col], c, d_mul(Nm_dual(u, j, I, m),
+                                                    dn(X[(size_t)col * n + r0 + m], dX[(size_t)col * n + r0 + m])));
+    }
+    for (int I = 0; I < 6; ++I)
+      for (int J = 0; J < 6; ++J) {
+        dual s = dc(0.0);
+        for (int P = 0; P < 6; ++P) s = d_fma(s, u->D[l][I][P], Gm[P][J]);
+        u->C[I][J] = d_fma(u->C[I][J], u->wn[l], s);
+      }
+  }
+  free(dJ); free(X); free(dX);
+}
+
+/* value pass at the given point: the Cholesky factor of J = A^T W D A in ws->J */
+static int factor_at(const or_tree* t, or_work* ws, double lam1, double lam2, const double* E, const double* a,
+                     const double z_n[][7]) {
+  normals(t, lam1, lam2, ws->nrm);
+  for (int j = 0; j < t->N; ++j) sym_operator(ws->nrm[j], ws->Nm[j]);
+  for (int l = 0; l < t->L; ++l) for (int c = 0; c < 7; ++c) ws->z_n[l][c] = z_n[l][c];
+  evaluate(t, ws, E, a);
+  assemble_J(t, ws);
+  return cholesky(t, ws);
+}
+
+/* derivative of g . sigma_bar + G : C along the direction of the last eval_dual */
+static double seed_value(const or_dual* u, const double* g, const double* Gt) {
+  double s = 0.0;
+  for (int I = 0; I < 6; ++I) s += g[I] * u->sbar[I].d;
+  if (Gt)
+    for (int I = 0; I < 6; ++I)
+      for (int J = 0; J < 6; ++J) s += Gt[6 * I + J] * u->C[I][J].d;
+  return s;
+}
+
+/* One directional derivative (local frame): R, sigma_bar and, if want_tangent,
+ * the algorithmic tangent C [6][6] at (p, q, w, E, a) with z^n fixed, and their
+ * derivatives along (dp, dq, dw, dE, da).  R, dR: [3 * active laminates];
+ * z_n: [2^K][7] per leaf.  Returns 0, -1 for invalid arguments, -2 if J is not
+ * positive definite. */
+int oracle_eval_dual(int K, int M, const double* p, const double* q, const double* w, const double* mat,
+                     const double* dp, const double* dq, const double* dw, double lam1, double lam2,
+                     const double* E, const double* dE, const double* a, const double* da, const double* z_n,
+                     int want_tangent, double* R, double* dR, double* sbar, double* dsbar, double* C, double* dC) {
+  or_tree t;
+  if (tree_init(&t, K, M, p, q, w, mat, 1e-12, 1, 0) != 0) return -1;
+  or_work* ws = work_alloc(&t);
+  or_dual* u = (or_dual*)calloc(1, sizeof(or_dual));
+  int rc = 0;
+  const double (*zl)[7] = (const double (*)[7])z_n;
+  if (want_tangent && factor_at(&t, ws, lam1, lam2, E, a, zl) != 0) rc = -2;
+  if (rc == 0) {
+    eval_dual(&t, u, w, dp, dq, dw, lam1, lam2, E, dE, a, da, zl, want_tangent ? ws : NULL);
+    for (int r = 0; r < 3 * t.nact; ++r) { R[r] = u->R[r].v; dR[r] = u->R[r].d; }
+    for (int I = 0; I < 6; ++I) { sbar[I] = u->sbar[I].v; dsbar[I] = u->sbar[I].d; }
+    if (want_tangent)
+      for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J) { C[6 * I + J] = u->C[I][J].v; dC[6 * I + J] = u->C[I][J].d; }
+  }
+  free(u);
+  work_free(ws);
+  tree_free(&t);
+  return rc;
+}
+
+/* Gradient of L = g . sigma_bar + G : C (local frame; G may be NULL) at the
+ * converged jumps a of one point, by the implicit function theorem applied to
+ * R(a, theta) = 0 (Sec. 3.2): with J = dR/da = A^T W D A,
+ *   J lam = (d sigma_bar/da)^T g + (dC/da)^T : G,
+ *   dL/dtheta = g . d sigma_bar/dtheta + G : dC/dtheta - lam . dR/dtheta,
+ * every partial derivative at fixed a from eval_dual (exact), the solve with
+ * the Cholesky factor of J in the paper's leaf-to-root order.  theta runs
+ * over p, q [N][M] (paper ordering), the leaf weights w [L] as given (leaves of
+ * weight zero get 0: the Macaulay bracket of Sec. 3.1 passes no change below
+ * zero) and the local macro strain E [6].  Returns 0, -1 for invalid
+ * arguments, -2 if J is not positive definite. */
+int oracle_gradient(int K, int M, const double* p, const double* q, const double* w, const double* mat,
+                    double lam1, double lam2, const double* E, const double* a, const double* z_n, const double* g,
+                    const double* Gt, double* gp, double* gq, double* gw, double* gE) {
+  or_tree t;
+  if (tree_init(&t, K, M, p, q, w, mat, 1e-12, 1, 0) != 0) return -1;
+  int L = t.L, NM = t.N * t.M, n = 3 * t.nact;
+  or_work* ws = work_alloc(&t);
+  or_dual* u = (or_dual*)calloc(1, sizeof(or_dual));
+  double* zp = (double*)calloc((size_t)NM, sizeof(double));
+  double* zq = (double*)calloc((size_t)NM, sizeof(double));
+  double* zw = (double*)calloc((size_t)L, sizeof(double));
+  double* za = (double*)calloc((size_t)n > 0 ? n : 1, sizeof(double));
+  double* lam = (double*)calloc((size_t)n > 0 ? n : 1, sizeof(double));
+  double zE[6] = {0, 0, 0, 0, 0, 0};
+  const double (*zl)[7] = (const double (*)[7])z_n;
+  int rc = factor_at(&t, ws, lam1, lam2, E, a, zl) != 0 ? -2 : 0;
+  or_work* fac = Gt ? ws : NULL;
+  if (rc == 0) {
+    for (int k = 0; k < n; ++k) {   /* right-hand side of the adjoint system, one jump at a time */
+      za[k] = 1.0;
+      eval_dual(&t, u, w, zp, zq, zw, lam1, lam2, E, zE, a, za, zl, fac);
+      lam[k] = seed_value(u, g, Gt);
+      za[k] = 0.0;
+    }
+    chol_solve(&t, ws, lam);
+    for (int x = 0; x < 2 * NM + L + 6; ++x) {
+      double* dp = zp; double* dq = zq; double* dw = zw; double dE[6] = {0, 0, 0, 0, 0, 0};
+      if (x < NM) dp[x] = 1.0;
+      else if (x < 2 * NM) dq[x - NM] = 1.0;
+      else if (x < 2 * NM + L) { if (!(w[x - 2 * NM] > 0.0)) { gw[x - 2 * NM] = 0.0; continue; } dw[x - 2 * NM] = 1.0; }
+      else dE[x - 2 * NM - L] = 1.0;
+      eval_dual(&t, u, w, dp, dq, dw, lam1, lam2, E, dE, a, za, zl, fac);
+      double v = seed_value(u, g, Gt);
+      for (int r = 0; r < n; ++r) v -= lam[r] * u->R[r].d;
+      if (x < NM) { gp[x] = v; dp[x] = 0.0; }
+      else if (x < 2 * NM) { gq[x - NM] = v; dq[x - NM] = 0.0; }
+      else if (x < 2 * NM + L) { gw[x - 2 * NM] = v; dw[x - 2 * NM] = 0.0; }
+      else gE[x - 2 * NM - L] = v;
+    }
+  }
+  free(zp); free(zq); free(zw); free(za); free(lam);
+  free(u);
+  work_free(ws);
+  tree_free(&t);
+  return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Eq. (eigen decomposition of A): cyclic Jacobi rotations on the symmetric
  * 3x3 matrix, eigenvalues sorted descending; each of the first two

@@ -503,7 +503,7 @@ def test_device_adjoint_matches_the_oracle_gradient(harness, K, matrix, steps):
             ref[k] = ref[k] + gi[k]
     for k, got in (("p", gp), ("q", gq), ("w", gw)):
         err = np.abs(got - ref[k]).max() / np.abs(ref[k]).max()
-        assert err < 1e-6, (k, err)
+        assert err < 1e-9, (k, err)
     np.testing.assert_allclose(gE, np.einsum("nij,nj->ni", C, g), rtol=1e-9, atol=1e-9 * np.abs(gE).max())
 
 
@@ -582,6 +582,6 @@ def test_device_adjoint_of_a_compressed_tree(harness):
             ref[k] = ref[k] + gi[k]
     for k, got in (("p", gp), ("q", gq), ("w", gw)):
         err = np.abs(got - ref[k]).max() / np.abs(ref[k]).max()
-        assert err < 1e-6, (k, err)
+        assert err < 1e-9, (k, err)
     assert (gw[np.asarray(tree.w) == 0] == 0).all()
     np.testing.assert_allclose(gE, np.einsum("nij,nj->ni", C, g), rtol=1e-9, atol=1e-9 * np.abs(gE).max())

@@ -229,7 +229,7 @@ def test_training_adjoint_full_batch_sampled():
         ref += np.asarray(r, dtype=np.float64)
     pred = np.array([(g_p * dp).sum() + (g_q * dq).sum() + (g_w * dw).sum() for dp, dq, dw in dirs])
     print(pred, ref)
-    assert np.abs(pred - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert np.abs(pred - ref).max() <= 1e-8 * np.abs(ref).max()
     m.close()
     release()
 

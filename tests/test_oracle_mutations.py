@@ -65,6 +65,24 @@ MUTATIONS = [
      "if (rn <= 1e4 * t->tol * (double)N * mandel_norm(ws->sbar)) break;", "stopping criterion (Sec. 4.6)"),
     ("compression_keeps_pass_through", "dmn_oracle.c", "t->cidx[j] = (wl > 0.0 && wr > 0.0) ? 0 : -1;",
      "t->cidx[j] = (wl > 0.0 || wr > 0.0) ? 0 : -1;", "compression removes laminates with a weightless side (Sec. 3.1)"),
+    ("dual_sine_rule", "dmn_oracle.c", "return dn(sin(a.v), cos(a.v) * a.d);", "return dn(sin(a.v), -cos(a.v) * a.d);",
+     "derivative of the spherical normal in the angles (Sec. 2.3)"),
+    ("dual_product_rule", "dmn_oracle.c", "return dn(a.v * b.v, a.d * b.v + a.v * b.d);", "return dn(a.v * b.v, a.d * b.v);",
+     "exact partial derivatives of R and sigma_bar (Sec. 3.2)"),
+    ("dual_quotient_rule", "dmn_oracle.c", "(a.d * b.v - a.v * b.d) / (b.v * b.v)", "a.d / b.v",
+     "exact partial derivatives of R and sigma_bar (Sec. 3.2)"),
+    ("dual_weight_normalisation", "dmn_oracle.c", "u->wn[l] = d_div(dn(w_raw[l], dw[l]), sw);",
+     "u->wn[l] = d_div(dn(w_raw[l], dw[l]), dc(sw.v));", "weights normalised to sum 1 (Sec. 2.1)"),
+    ("dual_fraction_complement", "dmn_oracle.c", "u->c2[j] = d_sub(dc(1.0), u->c1[j]);",
+     "u->c2[j] = dn(1.0 - u->c1[j].v, u->c1[j].d);", "c2 = 1 - c1 (Sec. 2.1)"),
+    ("dual_hardening_exponential", "dmn_oracle.c", "dual e = d_exp(d_scale(-r, ab));", "dual e = dc(exp(-r * ab.v));",
+     "exponential-linear hardening (Sec. 4.1)"),
+    ("dual_tangent_solve_term", "dmn_oracle.c", "      dx[r] -= s;\n", "      dx[r] -= 0.0 * s;\n",
+     "derivative of the six-right-hand-side solve of Eq. (lin_system_da_dE)"),
+    ("adjoint_solve_missing", "dmn_oracle.c", "    chol_solve(&t, ws, lam);\n", "",
+     "implicit-function gradient: J lam = (d sigma_bar/da)^T g (Sec. 3.2)"),
+    ("adjoint_sign", "dmn_oracle.c", "for (int r = 0; r < n; ++r) v -= lam[r] * u->R[r].d;",
+     "for (int r = 0; r < n; ++r) v += lam[r] * u->R[r].d;", "implicit-function gradient (Sec. 3.2)"),
     ("extrapolation_sign", "__init__.py", "start[S0 - J:] = a_n + rho[None, :] * change",
      "start[S0 - J:] = a_n - rho[None, :] * change", "extrapolated start a^n + rho (a^n - a^(n-1))"),
     ("extrapolation_clip", "__init__.py", "np.clip(r, 0.0, 1.0)", "np.clip(r, 0.0, 2.0)",
