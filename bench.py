@@ -1,9 +1,12 @@
 #!/usr/bin/env python
 """DMN Gauss-point updates/s at depth 8 on one GB300, FP64 and mixed forms.
 
-The JSON line's value is the FP64 form; "forms" adds the mixed form (FP32
-condensation, FP64 residual and final sweep) and the mixed form with an FP32
-tangent (no final sweep), each with its error against the oracle.
+The JSON line's value is the FP64 form; next to it, value_mixed and
+value_mixed_f32_tangent give the mixed form (FP32 condensation, FP64 residual
+and final sweep) and the mixed form with an FP32 tangent (no final sweep), each
+with its roofline and its error against the oracle (roofline_*, parity_*);
+"forms" holds every form's full record.  The rooflines divide by the FMA peaks
+measured on the same GPU at the start of the run (dmn_peak_gflops, "peaks").
 
 Workload (one "step" = one increment of the load path over the whole batch:
 orientation set-up + material-point update, all through the C ABI):
@@ -63,19 +66,38 @@ WORKLOAD_CMP = ("K=8 D10-interpolated DMN compressed to 70% of its leaves (weigh
 PEAK_F64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.07
 # FP32 peak: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
 PEAK_F32_GFLOPS = 152 * 128 * 2 * 2.07
+# The rooflines use the peaks measured on the GPU at the start of the run (dmn_peak_gflops: a sustained
+# FMA loop on every SM); the derived figures above are kept beside them as a cross-check.
+PEAKS_DERIVED = {"f64": PEAK_F64_GFLOPS, "f32": PEAK_F32_GFLOPS,
+                 "note": "derived: 152 SM x 4 SMSP x 0.5 DFMA/clk x 2 flop x 2.07 GHz (FP64); "
+                         "152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz (FP32)"}
+
+
+def measure_peaks(seconds_f64=1.0, seconds_f32=0.3):
+    """Sustained FP64 and FP32 FMA throughput of this GPU through the library's own kernel."""
+    from paper_2103_08253_gb300 import dmn
+    g64, ms64 = dmn.peak_gflops("fp64", seconds_f64)
+    g32, ms32 = dmn.peak_gflops("fp32", seconds_f32)
+    return {"f64": g64, "f32": g32,
+            "note": "measured: dmn_peak_gflops, sustained FMA loop on every SM (%.2f s FP64, %.2f s FP32); "
+                    "derived cross-check %.1f / %.1f GFLOP/s" % (ms64 * 1e-3, ms32 * 1e-3, PEAK_F64_GFLOPS,
+                                                                PEAK_F32_GFLOPS)}
 
 # ---------------------------------------------------------------------------------------------
 # Algorithmic flop counts (add/sub/mul/div/sqrt/rsqrt = 1, fma = 2) of the tree-condensed Newton
 # method, counted from the arithmetic of csrc/dmn_device.cuh.  T = FP64 in the FP64 form, FP32
 # in the mixed form.
 #   per laminate, every pass:  N a and the children's strains 39 (FP64); residual share and
-#                              plain stress average 44 (FP64); condensation 678 (T), or 605 (T)
-#                              for a bottom laminate (leaf tangents D = lam 1(x)1 + 2 mu I - c m(x)m)
+#                              plain stress average 44 (FP64); condensation 678 (T), or, for a bottom
+#                              laminate (leaf tangents D = lam 1(x)1 + 2 mu I - c m(x)m), 353 (T) plus
+#                              121 (T) for each leaf of an inelastic phase (an elastic leaf has c = 0
+#                              in every pass and the FP64 condensation skips its rank-one terms; the
+#                              FP32 one computes them)
 #   per inner laminate:        children's strain corrections 39 (T)
 #   per laminate, per Newton correction: da = g + H d_eps 39 (T), a += da 3 (FP64)
 #   per leaf:                  elastic stress 13; J2 stress 56 + tangent scalars 12 (FP64)
 #   per pass:                  convergence test 15 (FP64)
-F_NODE_F64, F_RES, F_COND, F_COND_BOTTOM, F_DEPS, F_DA, F_A = 39, 44, 678, 605, 39, 39, 3
+F_NODE_F64, F_RES, F_COND, F_COND_BOTTOM, F_COND_LEAF, F_DEPS, F_DA, F_A = 39, 44, 678, 353, 121, 39, 39, 3
 F_LEAF_EL, F_LEAF_J2, F_TEST = 13, 56 + 12, 15
 F_ROTATE = 1150         # per point: stress and tangent back to the global frame (k_final)
 F_STATE_NODE = 39       # state pass: per laminate (strains from the jumps)
@@ -125,12 +147,15 @@ def tree_counts(w):
     return c
 
 
-def pass_flops(K, w=None):
+def pass_flops(K, w=None, t_is_f64=True):
     """(FP64 flops, T flops) of one Newton pass without the jump correction (w: leaf weights of
-    a compressed tree; None: the full tree)."""
+    a compressed tree; None: the full tree).  Phases of the benchmark: an elastic fiber on the
+    left leaf of every laminate pair, a J2 matrix on the right one.  The FP64 condensation skips
+    the fiber's rank-one terms; the FP32 one (t_is_f64 False) computes them (with c = 0)."""
     c = tree_counts(np.ones(1 << K) if w is None else w)
     f64 = c["N"] * (F_NODE_F64 + F_RES) + c["el"] * F_LEAF_EL + c["j2"] * F_LEAF_J2 + F_TEST
-    ft = c["inner"] * (F_COND + F_DEPS) + c["pairs"] * F_COND_BOTTOM + c["single"] * F_LEAF_SUB
+    ft = (c["inner"] * (F_COND + F_DEPS) + c["pairs"] * (F_COND_BOTTOM + (1 if t_is_f64 else 2) * F_COND_LEAF)
+          + c["single"] * F_LEAF_SUB)
     return f64, ft
 
 
@@ -143,7 +168,7 @@ def corr_flops(K, w=None):
 def newton_flops(K, iters_sum, npts, mixed, w=None):
     """(FP64, FP32) flops of the Newton kernel over npts points with iters_sum corrections:
     one pass per point evaluates the starting jumps, one more per correction."""
-    f64, ft = pass_flops(K, w)
+    f64, ft = pass_flops(K, w, t_is_f64=not mixed)
     c64, ct = corr_flops(K, w)
     passes = iters_sum + npts
     F64 = passes * f64 + iters_sum * c64
@@ -471,29 +496,33 @@ def run_e2e(r, ctx, args, dist):
             "status_ok": int((out_h["status"] == 0).sum().item())}
 
 
-def roofline_f64(r, n, steps, w=None):
+def roofline_f64(r, n, steps, w=None, peaks=None):
+    pk = peaks or PEAKS_DERIVED
+    P64 = pk["f64"]
     F, _ = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=False, w=w)
     t = r["kms"]["newton"] * 1e-3
     ach = F / t / 1e9
     tr = ncu_traffic("k_newton_f64" + ("_compressed" if w is not None and (np.asarray(w) == 0).any() else ""), n)
-    return {"bound": "alu", "kernel": "k_newton<double>", "achieved": ach, "peak": PEAK_F64_GFLOPS,
-            "unit": "GFLOP/s (FP64)", "frac": ach / PEAK_F64_GFLOPS, "traffic": tr,
+    return {"bound": "alu", "kernel": "k_newton<double>", "achieved": ach, "peak": P64,
+            "unit": "GFLOP/s (FP64)", "frac": ach / P64, "traffic": tr,
             "flops_per_launch": F / steps, "launch_ms": r["kms"]["newton"] / steps,
-            "peak_note": "derived: 152 SM x 4 SMSP x 0.5 DFMA/clk x 2 flop x 2.07 GHz"}
+            "frac_of_derived_peak": ach / PEAK_F64_GFLOPS, "peak_note": pk["note"]}
 
 
-def roofline_mixed(r, n, steps, w=None, sweep=True):
+def roofline_mixed(r, n, steps, w=None, sweep=True, peaks=None):
     """Mixed forms: the Newton kernel against F64/P64 + F32/P32; the final kernel (with the FP64 sweep,
     or only the state pass and rotation in the form with an FP32 tangent) against the FP64 peak."""
+    pk = peaks or PEAKS_DERIVED
+    P64, P32 = pk["f64"], pk["f32"]
     F64, F32 = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=True, w=w)
     t = r["kms"]["newton"] * 1e-3
-    tb = F64 / (PEAK_F64_GFLOPS * 1e9) + F32 / (PEAK_F32_GFLOPS * 1e9)
+    tb = F64 / (P64 * 1e9) + F32 / (P32 * 1e9)
     Ff = final_flops(K_DEPTH, n * steps, sweep=sweep, w=w)
     tf = r["kms"]["final"] * 1e-3
-    fin = {"kernel": "k_final<sweep>" if sweep else "k_final", "achieved": Ff / tf / 1e9, "peak": PEAK_F64_GFLOPS, "unit": "GFLOP/s (FP64)",
-           "frac": Ff / tf / 1e9 / PEAK_F64_GFLOPS, "launch_ms": r["kms"]["final"] / steps}
-    return {"bound": "alu", "kernel": "k_newton<float>", "achieved": tb / t * PEAK_F64_GFLOPS,
-            "peak": PEAK_F64_GFLOPS, "unit": "GFLOP/s (FP64-equivalent: F64/P64 + F32/P32)", "frac": tb / t,
+    fin = {"kernel": "k_final<sweep>" if sweep else "k_final", "achieved": Ff / tf / 1e9, "peak": P64,
+           "unit": "GFLOP/s (FP64)", "frac": Ff / tf / 1e9 / P64, "launch_ms": r["kms"]["final"] / steps}
+    return {"bound": "alu", "kernel": "k_newton<float>", "achieved": tb / t * P64,
+            "peak": P64, "unit": "GFLOP/s (FP64-equivalent: F64/P64 + F32/P32)", "frac": tb / t, "peak_note": pk["note"],
             "traffic": ncu_traffic("k_newton_mixed" + ("_compressed" if w is not None and (np.asarray(w) == 0).any()
                                                        else ""), n), "flops_f64_per_launch": F64 / steps,
             "flops_f32_per_launch": F32 / steps, "launch_ms": r["kms"]["newton"] / steps, "final_kernel": fin}
@@ -548,20 +577,11 @@ def run_mixed_depth(args):
             st = m0.update(lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st,
                            tree_id=tid_d[:msub].contiguous())["state_out"]
         m0.close()
-        # autotune over the single-tree API is not available for several trees: time the candidates here
-        best = None
+        # the project's autotuner on the handle of four trees, on this sub-batch
         En, dE = inputs(first)
-        for block, cps in ((128, 2), (128, 3), (128, 4), (64, 6)):
-            mm = dmn.DMN(trees, precision=prec, block=block, ctas_per_sm=cps)
-            o = mm.update(lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st, tree_id=tid_d[:msub].contiguous())
-            torch.cuda.synchronize()
-            mm.profile(True)
-            mm.update(lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st, out=o, tree_id=tid_d[:msub].contiguous())
-            kms, _ = mm.profile_read()
-            mm.close()
-            del o
-            if best is None or kms["newton"] < best[2]:
-                best = (block, cps, kms["newton"])
+        tuned = autotune.tune(trees, prec, lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st, reps=1,
+                              tree_id=tid_d[:msub].contiguous())
+        best = (tuned["block"], tuned["ctas_per_sm"], tuned["newton_ms"])
         del st
         torch.cuda.empty_cache()
         m = dmn.DMN(trees, precision=prec, block=best[0], ctas_per_sm=best[1], predictor=pred)
@@ -606,7 +626,7 @@ def run_mixed_depth(args):
         el = torch.from_numpy(elastic).to(dev)
         line["forms"][form] = {
             "value": n * G / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms / G,
-            "launch": {"block": best[0], "ctas_per_sm": best[1]},
+            "launch": {"block": best[0], "ctas_per_sm": best[1], "autotuner_table": tuned["table"]},
             "iters_elastic_half": torch.bincount(its[:, el].reshape(-1)).cpu().tolist(),
             "iters_cyclic_half": torch.bincount(its[:, ~el].reshape(-1)).cpu().tolist(),
             "status_counts": torch.bincount(stat.reshape(-1).to(torch.int64)).cpu().tolist(),
@@ -704,13 +724,15 @@ def run_train(args):
     target = W.tree_d10_fit(K_DEPTH, seed=SEED_TREE + 31)
     tr = training.Trainer(K_DEPTH, target, TRAIN_SAMPLES, seed=SEED_TREE + 32, elastic_matrix=W.Phase(0, 3000.0, 0.35),
                           plastic=W.MATRIX, n_plastic=TRAIN_SAMPLES, plastic_precision=args.train_plastic,
-                          elastic_precision=args.train_elastic)
+                          elastic_precision=args.train_elastic, stiffness_method=args.train_stiffness)
     tr.train(args.warmup)
     clocks = ClockSampler("0")
     t = tr.train(args.steps)
     clk = clocks.stop()
     hist = tr.history
-    n_upd = TRAIN_SAMPLES * 6 + TRAIN_SAMPLES          # updates per epoch (forward), each with its adjoint
+    six = tr.stiff_method == "stress" or (tr.stiff_method is None and args.train_elastic == "mixed-f32-tangent")
+    # updates per epoch (forward), each with its adjoint: per stiffness sample one (tangent seed) or six
+    n_upd = TRAIN_SAMPLES * (6 if six else 1) + TRAIN_SAMPLES
     line = {"metric": "DMN offline training: samples/s (forward + adjoint) at depth 8", "unit": "samples/s",
             "value": 2 * TRAIN_SAMPLES * args.steps / t, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "dtype": "f64" if args.train_plastic == args.train_elastic == "f64" else "f32+f64", "data": "synthetic",
@@ -719,7 +741,8 @@ def run_train(args):
                                    % (TRAIN_SAMPLES, TRAIN_SAMPLES),
                        "dmn_updates_per_epoch": n_upd,
                        "plastic_samples_precision": args.train_plastic,
-                       "stiffness_samples_precision": args.train_elastic},
+                       "stiffness_samples_precision": args.train_elastic,
+                       "stiffness_gradient": "six stress adjoints" if six else "tangent-seeded adjoint"},
             "gp_updates_per_s": n_upd * args.steps / t,
             "compression": {"handle_rebuilds": tr.rebuilds, "leaves_left": int(tr.pattern.sum()),
                             "leaves": 1 << K_DEPTH},
@@ -737,7 +760,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--points", type=int, default=1 << 20)
-    ap.add_argument("--forms", default="f64,mixed,mixed-f32-tangent,f64/extrap,mixed-f32-tangent/extrap",
+    ap.add_argument("--forms", default="f64,mixed,mixed-f32-tangent",
                     help="precisions, each optionally with /extrap: the Newton iteration starts from the last "
                          "update's jumps extrapolated along the strain increment instead of the paper's a^n")
     ap.add_argument("--e2e-chunk", type=int, default=0,
@@ -752,7 +775,9 @@ def main():
                     help="matrix law of the k8 workloads: linear hardening (default) or the paper's exp-linear")
     ap.add_argument("--train-plastic", default="mixed-f32-tangent", choices=["f64", "mixed", "mixed-f32-tangent"],
                     help="precision of the training workload's plastic forward solves (the adjoint is FP64)")
-    ap.add_argument("--train-elastic", default="mixed-f32-tangent", choices=["f64", "mixed", "mixed-f32-tangent"],
+    ap.add_argument("--train-stiffness", default=None, choices=["tangent", "stress"],
+                    help="training workload: stiffness gradients by tangent seeds or six stress adjoints")
+    ap.add_argument("--train-elastic", default="mixed", choices=["f64", "mixed", "mixed-f32-tangent"],
                     help="precision of the training workload's stiffness-sample forward solves")
     ap.add_argument("--shape", type=int, default=3, choices=[3, 4, 6],
                     help="shape functions of the angle interpolation: 3 linear (default, D10 fit), 4 tri-linear, "
@@ -794,6 +819,7 @@ def run_gpu(args):
         dist = tdist
     from paper_2103_08253_gb300 import dmn
     dmn.load_library()
+    peaks = measure_peaks()
     n = args.points
     cmp = args.workload == "k8-compressed"
     tree, A2, lam_np, Q_np, Ef = make_workload(n, rank, cmp, args.matrix, args.shape)
@@ -831,9 +857,9 @@ def run_gpu(args):
         forms_out[form] = {"value": v, "unit": UNIT, "ms_per_step": r["t_ms"] / steps,
                            "kernel_ms_per_step": {k: x / steps for k, x in r["kms"].items()},
                            "newton_iters_per_update": r["iters_sum"] / (n * steps), "iters_hist": r["iters_hist"],
-                           "roofline": (roofline_f64(r, n, steps, tree.w) if form_opts(form)[0] == "f64"
+                           "roofline": (roofline_f64(r, n, steps, tree.w, peaks) if form_opts(form)[0] == "f64"
                                         else roofline_mixed(r, n, steps, tree.w,
-                                                            sweep=form_opts(form)[0] == "mixed")),
+                                                            sweep=form_opts(form)[0] == "mixed", peaks=peaks)),
                            "launch": r["launch"],
                            "parity_vs_oracle": r.get("parity"), "clocks": r["clocks"]}
     main_form = "f64" if "f64" in results else forms[0]
@@ -858,7 +884,18 @@ def run_gpu(args):
                              % ((6 * tree_counts(tree.w)["j2"] + 3 * tree_counts(tree.w)["N"]) * n * 8e-9),
                        "parallelism": "independent point shards per GPU, no collective"},
             "roofline": forms_out[main_form]["roofline"], "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 4 * steps, "clocks": mr["clocks"], "forms": forms_out}
+            "gpu_launches": 4 * steps, "clocks": mr["clocks"],
+            "peaks": {"fp64_gflops": peaks["f64"], "fp32_gflops": peaks["f32"], "note": peaks["note"]}}
+    # the other forms side by side with the headline: value, roofline and error against the oracle
+    for form in ("mixed", "mixed-f32-tangent"):
+        if form in forms_out and form != main_form:
+            key = form.replace("-", "_")
+            line["value_" + key] = forms_out[form]["value"]
+            line["roofline_" + key] = forms_out[form]["roofline"]
+            line["parity_" + key] = forms_out[form]["parity_vs_oracle"]
+    if main_form in forms_out:
+        line["parity"] = forms_out[main_form]["parity_vs_oracle"]
+    line["forms"] = forms_out
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

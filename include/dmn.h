@@ -243,31 +243,42 @@ int dmn_update_host(dmn_handle* h, int64_t n, const int32_t* tree_id, const doub
  * changed set of zero weights. */
 int dmn_set_params(dmn_handle* h, int32_t tree_id, const double* p, const double* q, const double* w);
 
-/* Adjoint of the converged update (FP64): for a loss L with g_stress =
- * dL/d sigma_bar (dev [n][6], global frame), adds to
+/* Adjoint of the converged update (FP64): for a loss
+ * L(sigma_bar, C) with g_stress = dL/d sigma_bar (dev [n][6], global frame)
+ * and g_tangent = dL/dC (dev [n][36], row-major, global frame: the
+ * derivative with respect to each of the 36 entries of the tangent of
+ * dmn_update; only its symmetric part matters), adds to
  *   g_p, g_q  dev [(2^K-1) * M]  dL/dp, dL/dq (paper ordering, Sec. 3.1),
  *   g_w       dev [2^K]          dL/dw for the leaf weights as given to
  *                                dmn_create / dmn_set_params (before their
  *                                normalisation to sum 1),
  * summed over the n points, and writes g_E dev [n][6] = dL/dE = C^T g_stress
- * (may be NULL).  The gradient is the implicit-function derivative of the
+ * (may be NULL).  The stress part is the implicit-function derivative of the
  * converged Newton solution of the Euler-Lagrange equation (Sec. 3.2):
  * dL/dtheta = g.d sigma_bar/d theta + mu.dR/d theta with mu = (da/dE) g, the
  * response of the condensed tree to a macro perturbation g (no extra solve);
  * the condensation at the converged jumps is recomputed, nothing from the
- * Newton iterations is stored.  For a compressed tree the gradient covers the
+ * Newton iterations is stored.  The tangent part is offered for trees whose
+ * two phases are elastic, the linear DMN that the offline training of
+ * Sec. 3.1 fits to effective stiffnesses: there the tangent is the laminate
+ * recursion of the leaf stiffnesses (Eq. of the stiffness propagation),
+ * independent of the strain and the jumps, and its adjoint is one reverse
+ * pass through that recursion per point (one forward pass recomputes every
+ * laminate's stiffness).  For a compressed tree the gradient covers the
  * remaining laminates and leaves; laminates passed through and leaves of
  * weight zero get none (the weights' Macaulay bracket of Sec. 3.1 passes none
- * below zero either).  Inputs are those of the dmn_update call that
- * produced state_out (its output, read only) from state_in; points whose
- * update did not converge should get g_stress = 0.  One tree per handle
- * (tree_id must be NULL).  The first call with a larger n than any earlier
- * call (up to 65536 points per chunk, about 71 KB each at K = 8) allocates work space.  Errors:
- * DMN_ERR_ARG for NULL arrays, n < 0, a non-NULL tree_id or a handle with
- * several trees. */
+ * below zero either).  Inputs are those of the dmn_update call that produced
+ * state_out (its output, read only) from state_in; points whose update did not
+ * converge should get zero seeds.  Either seed may be NULL, not both; with
+ * g_stress NULL, E_n, dE, state_in and state_out may be NULL and g_E (if
+ * given) is set to zero.  One tree per handle (tree_id must be NULL).  The
+ * first call with a larger n than any earlier call (up to 65536 points per
+ * chunk, about 71 KB each at K = 8) allocates work space.  Errors: DMN_ERR_ARG
+ * for NULL arrays, both seeds NULL, a tangent seed on a tree with an inelastic
+ * phase, n < 0, a non-NULL tree_id or a handle with several trees. */
 int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam, const double* Q, const double* E_n,
-             const double* dE, const double* state_in, const double* state_out, const double* g_stress, double* g_p,
-             double* g_q, double* g_w, double* g_E, void* stream);
+             const double* dE, const double* state_in, const double* state_out, const double* g_stress,
+             const double* g_tangent, double* g_p, double* g_q, double* g_w, double* g_E, void* stream);
 
 /* Per-kernel timing of dmn_update, for measurement: while enabled, CUDA
  * events are recorded on the update's stream before and after each of its
@@ -292,21 +303,25 @@ int dmn_profile_read(dmn_handle* h, double ms[3], int64_t* updates);
  * allocating call).  Its work space -- tree parameters, a work counter and the
  * per-lane scratch of the Newton kernel -- is one static device array of
  * 64 MiB inside this library, which every GPU that loads the library holds
- * until the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) once; make that first call before
- * any stream capture.  Every call shares the array: calls that overlap on the
- * GPU (other streams, other host threads) race and must be serialised by the
- * caller.  Each call re-uploads the tree and clears the counter.
+ * until the process exits.  Each call looks up that array's device address on
+ * the current device (cudaGetSymbolAddress); the first call on a device also
+ * loads the library's device code there, so make that first call before any
+ * stream capture.  Every call shares the array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Each call re-uploads the tree and clears the counter; the tree's
+ * parameters travel by value as a kernel argument, so nothing the call queues
+ * refers to the caller's host memory after it returns.
  *
  * Arguments are those of dmn_create (tree, opt) and dmn_update (n and the
  * arrays, same layouts and ownership), for one uncompressed tree: all leaf
  * weights must be > 0.  Only the FP64 form with full Newton steps is offered
- * (opt->precision must be DMN_PREC_F64 and opt->predictor 0; opt may be NULL);
- * opt->line_search, opt->block and opt->ctas_per_sm are ignored.  The static work space limits parallelism:
- * 1152 lanes at K = 8 (more for shallower trees), so it is slower than
- * dmn_update.  Errors: DMN_ERR_ARG for the argument errors of dmn_create and
- * dmn_update and for a tree whose parameters or one CTA of scratch do not fit
- * the 64 MiB; DMN_ERR_CUDA if a CUDA call fails.  Messages are returned by
+ * (opt may be NULL; otherwise opt->precision must be DMN_PREC_F64, and
+ * opt->predictor and opt->line_search 0); opt->block and opt->ctas_per_sm are
+ * ignored.  The static work space limits parallelism: 1152 lanes at K = 8
+ * (more for shallower trees), so it is slower than dmn_update.  Errors:
+ * DMN_ERR_ARG for the argument errors of dmn_create and dmn_update, for the
+ * options above and for a tree whose parameters or one CTA of scratch do not
+ * fit the 64 MiB; DMN_ERR_CUDA if a CUDA call fails.  Messages are returned by
  * dmn_last_error(NULL). */
 int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* opt, int64_t n, const double* lam,
                        const double* Q, const double* E_n, const double* dE, const double* state_in,

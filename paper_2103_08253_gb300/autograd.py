@@ -8,10 +8,15 @@ converged Newton solution (the condensation at the converged jumps is
 recomputed; nothing from the iterations is stored).
 
 `dmn_stiffness(m, lam, Q, p, q, w)` returns the effective stiffness of a DMN
-with linear elastic phases (the offline-training quantity of Sec. 3.1); its
-backward pass uses that sigma_bar = C_bar E holds exactly, so
-<G, C_bar> = sum_k G[:, k] . sigma_bar(E = e_k): six stress adjoints at the
-Mandel unit strains.
+with linear elastic phases (the offline-training quantity of Sec. 3.1).  By
+default (a handle whose tangent is FP64: precision "f64" or "mixed") it is the
+tangent of one update from the virgin state at zero strain, and its backward
+pass is dmn_grad with a tangent seed: one reverse pass through the laminate
+recursion per sample.  method="stress" takes instead the six stresses at the
+Mandel unit strains (sigma_bar = C_bar E holds exactly for elastic phases) and
+six stress adjoints, <G, C_bar> = sum_k G[:, k] . sigma_bar(E = e_k); the
+handles of the FP32-tangent form use it, since their stresses, not their
+tangents, are FP64.
 
 Both run every step through the C ABI; the parameters are uploaded with
 dmn_set_params when they differ from the ones the handle holds.
@@ -84,11 +89,44 @@ class _Stiffness(torch.autograd.Function):
         return None, None, None, g_p.reshape(sp), g_q.reshape(sq), g_w.reshape(sw)
 
 
-def dmn_stiffness(m, lam, Q, p, q, w):
-    """Effective stiffness [n, 6, 6] (global frame) of a DMN with elastic phases; differentiable in p, q, w."""
+class _StiffnessTangent(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, m, lam, Q, p, q, w):
+        sync_params(m, p, q, w)
+        n = lam.shape[0]
+        dev = lam.device
+        zero_state = torch.zeros((m.state_size, n), dtype=torch.float64, device=dev)
+        E0 = torch.zeros((n, 6), dtype=torch.float64, device=dev)
+        out = m.update(lam, Q, E0, E0, zero_state)
+        ctx.m = m
+        ctx.save_for_backward(lam, Q)
+        ctx.shapes = (p.shape, q.shape, w.shape)
+        return out["tangent"]
+
+    @staticmethod
+    def backward(ctx, G):
+        lam, Q = ctx.saved_tensors
+        g_p, g_q, g_w, _ = ctx.m.grad(lam, Q, None, None, None, None, None, want_E=False,
+                                      g_tangent=G.contiguous())
+        sp, sq, sw = ctx.shapes
+        return None, None, None, g_p.reshape(sp), g_q.reshape(sq), g_w.reshape(sw)
+
+
+def dmn_stiffness(m, lam, Q, p, q, w, method=None):
+    """Effective stiffness [n, 6, 6] (global frame) of a DMN with elastic phases; differentiable in p, q, w.
+    method: "tangent" (the update's tangent, a tangent-seeded adjoint), "stress" (six stresses and six
+    stress adjoints) or None (tangent unless the handle's tangent is FP32)."""
     for ph in m.phases:
         if ph.kind != 0:
             raise ValueError("dmn_stiffness needs linear elastic phases")
+    if method is None:
+        method = "stress" if m.precision == "mixed-f32-tangent" else "tangent"
+    if method == "tangent":
+        if m.precision == "mixed-f32-tangent":
+            raise ValueError("method='tangent' needs an FP64 tangent (precision 'f64' or 'mixed')")
+        return _StiffnessTangent.apply(m, lam, Q, p, q, w)
+    if method != "stress":
+        raise ValueError("method must be 'tangent' or 'stress'")
     return _Stiffness.apply(m, lam, Q, p, q, w)
 
 

@@ -1,7 +1,9 @@
 """Autotuner for the launch shape of the persistent Newton kernel.
 
 The Newton kernel runs one Gauss point per thread; its launch shape is the CTA
-size (points per CTA) and the number of resident CTAs per SM.  The FP64 form is
+size (points per CTA) and the number of resident CTAs per SM.  Handles with
+several trees (mixed depths) are tuned on their own batch and cached under a
+key of their own.  The FP64 form is
 bound by the FP64 pipe once each SM holds a few warps, the FP32 form hides
 latency with more resident warps, and both trade occupancy against registers.
 `tune` times every candidate shape on a caller-provided batch through the C ABI
@@ -21,10 +23,13 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "auto
 
 
 def _key(tree, precision, device):
+    """Cache key: GPU, SM count, and per tree its depth, shape functions and phase kinds (a handle
+    with several trees, e.g. a batch of mixed depths, has a key of its own)."""
     import torch
     p = torch.cuda.get_device_properties(device)
-    kinds = "".join(str(int(ph.kind)) for ph in tree.phases)
-    return "%s|sm%d|K%d|M%d|ph%s|%s" % (p.name, p.multi_processor_count, tree.K, tree.M, kinds, precision)
+    trees = list(tree) if isinstance(tree, (list, tuple)) else [tree]
+    parts = ["K%d|M%d|ph%s" % (t.K, t.M, "".join(str(int(ph.kind)) for ph in t.phases)) for t in trees]
+    return "%s|sm%d|%s|%s" % (p.name, p.multi_processor_count, "+".join(parts), precision)
 
 
 def _load():
@@ -43,9 +48,11 @@ def cached(tree, precision, device=None):
     return (int(e["block"]), int(e["ctas_per_sm"])) if e else None
 
 
-def tune(tree, precision, lam, Q, E_n, dE, state_in, reps=2, candidates=CANDIDATES, save=True):
+def tune(tree, precision, lam, Q, E_n, dE, state_in, reps=2, candidates=CANDIDATES, save=True, tree_id=None):
     """Time the Newton kernel of every candidate shape on this batch; returns
-    dict(block, ctas_per_sm, newton_ms, table)."""
+    dict(block, ctas_per_sm, newton_ms, table).  tree may be a list of trees (one handle with
+    several trees, as dmn.DMN takes it), with tree_id [n] (int32, device) selecting each
+    point's tree."""
     import torch
     dev = lam.device
     n = lam.shape[0]
@@ -53,11 +60,11 @@ def tune(tree, precision, lam, Q, E_n, dE, state_in, reps=2, candidates=CANDIDAT
     for block, cps in candidates:
         m = dmn.DMN(tree, precision=precision, block=block, ctas_per_sm=cps)
         out = m.alloc_outputs(n, dev)
-        m.update(lam, Q, E_n, dE, state_in, out=out)
+        m.update(lam, Q, E_n, dE, state_in, out=out, tree_id=tree_id)
         torch.cuda.synchronize()
         m.profile(True)
         for _ in range(reps):
-            m.update(lam, Q, E_n, dE, state_in, out=out)
+            m.update(lam, Q, E_n, dE, state_in, out=out, tree_id=tree_id)
         kms, cnt = m.profile_read()
         m.profile(False)
         m.close()

@@ -21,7 +21,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -33,6 +32,13 @@ using namespace dmn;
 namespace {
 
 thread_local std::string g_create_error;
+
+}  // namespace
+
+// the message dmn_last_error(NULL) returns, also set by the peak measurement (peak.cu)
+void dmn_set_create_error(const std::string& msg) { g_create_error = msg; }
+
+namespace {
 
 struct Tree {
   int K, M, N, L, nz, z_both, S;
@@ -115,6 +121,7 @@ TreeDev tree_dev(const Tree& t) {
   d.pre = t.d_tab ? t.d_tab + 4 * t.Lc : nullptr;
   d.post = t.d_tab ? t.d_tab + 4 * t.Lc + t.N : nullptr;
   d.pidx = t.d_tab ? t.d_tab + 4 * t.Lc + 2 * t.N : nullptr;
+  d.kid = t.d_tab ? t.d_tab + 4 * t.Lc + 3 * t.N : nullptr;
   return d;
 }
 
@@ -756,10 +763,10 @@ __global__ void __launch_bounds__(128) k_grad(GradParams P) {
     gl[J] = s;
   }
   if (CMP) {
-    adjoint_pass_c(t, Eloc, gl, ph, A, Wk);
+    adjoint_pass_c(t, Eloc, gl, phv, ws, A, Wk);
     adjoint_weights_c(t, t.wl, t.wsum, Wk, gw, ws);
   } else {
-    adjoint_pass(t, Eloc, gl, ph, A, Wk);
+    adjoint_pass(t, Eloc, gl, phv, ws, A, Wk);
     adjoint_weights(t, t.wl, t.wsum, Wk, gw, ws);
   }
   if (P.g_E) {   // dL/dE = C^T g (C symmetric), rotated back
@@ -816,6 +823,99 @@ __global__ void __launch_bounds__(256) k_grad_reduce(TreeDev t, int64_t nc, cons
   if (threadIdx.x == 0) *out += red[0];
 }
 
+// Tangent seeds (trees of elastic phases): one thread per point of a chunk, in the work
+// layout of k_grad.  After k_grad (stress seeds) the normals and shape-function values are
+// in the work array and the tangent's terms are added; alone (init) the kernel computes
+// them and starts the per-laminate and per-leaf terms at zero.  The weight gradient is
+// then (re)assembled from all terms.
+struct GradTParams {
+  TreeDev t;
+  int64_t n, n0, nc;
+  const double *lam, *Q, *g_tangent;
+  double* g_E;
+  double* work;
+  int init;
+};
+
+template <bool CMP>
+__global__ void __launch_bounds__(128) k_grad_tangent(GradTParams P) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= P.nc) return;
+  const int64_t pt = P.n0 + i;
+  const TreeDev& t = P.t;
+  const int N = t.N, L = t.L;
+  const size_t ws = (size_t)P.nc;
+  double* w = P.work + i;
+  double* nrm = w;
+  double* Cst = w + (size_t)(6 * N) * ws;      // the g, H field of k_grad: every laminate's tangent
+  AdjWork Wk;
+  Wk.H = nullptr; Wk.hs = ws;
+  Wk.mu = w + (size_t)(27 * N) * ws;
+  Wk.xi = w + (size_t)(30 * N) * ws;
+  Wk.gab = w + (size_t)(31 * N) * ws;
+  Wk.direct = w + (size_t)(33 * N) * ws;
+  Wk.ws = ws;
+  double* gw = w + (size_t)(33 * N + L) * ws;
+  double* phv = w + (size_t)(33 * N + 2 * L) * ws;   // shape-function values (k_grad writes them too)
+  if (P.init) {
+    const double l1 = P.lam[2 * pt], l2 = P.lam[2 * pt + 1];
+    point_normals(t, l1, l2, nrm, ws);
+    double ph[6];
+    const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
+#pragma unroll
+    for (int m = 0; m < 6; ++m) ph[m] = 0.0;
+    if (t.M == 3) {
+      ph[0] = v[0]; ph[1] = v[1]; ph[2] = v[2];
+    } else if (t.M == 4) {
+      const double b = v[0] * v[1] * v[2];
+      ph[0] = v[0] - 9.0 * b; ph[1] = v[1] - 9.0 * b; ph[2] = v[2] - 9.0 * b; ph[3] = 27.0 * b;
+    } else {
+      ph[0] = v[0] * (2.0 * v[0] - 1.0); ph[1] = v[1] * (2.0 * v[1] - 1.0); ph[2] = v[2] * (2.0 * v[2] - 1.0);
+      ph[3] = 4.0 * v[0] * v[1]; ph[4] = 4.0 * v[0] * v[2]; ph[5] = 4.0 * v[1] * v[2];
+    }
+    for (int m = 0; m < 6; ++m) phv[(size_t)m * ws] = ph[m];
+    for (int k = 0; k < 2 * N; ++k) Wk.gab[(size_t)k * ws] = 0.0;
+    for (int k = 0; k < N; ++k) Wk.xi[(size_t)k * ws] = 0.0;
+    for (int l = 0; l < L; ++l) Wk.direct[(size_t)l * ws] = 0.0;
+    if (P.g_E)   // the tangent of elastic phases does not depend on the macro strain
+      for (int I = 0; I < 6; ++I) P.g_E[6 * pt + I] = 0.0;
+  }
+  // the seed in the local frame: C_glob = R C_loc R^T  =>  Gb_loc = R^T G R, symmetrised
+  double R[6][6];
+  mandel_rotation(P.Q + 9 * pt, R);
+  const double* G = P.g_tangent + 36 * pt;
+  double RG[6][6];
+#pragma unroll
+  for (int P2 = 0; P2 < 6; ++P2)
+#pragma unroll
+    for (int J = 0; J < 6; ++J) {
+      double v = 0.0;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) v += R[I][P2] * G[6 * I + J];
+      RG[P2][J] = v;
+    }
+  double Gl[6][6];
+#pragma unroll
+  for (int P2 = 0; P2 < 6; ++P2)
+#pragma unroll
+    for (int Q2 = 0; Q2 < 6; ++Q2) {
+      double v = 0.0;
+#pragma unroll
+      for (int J = 0; J < 6; ++J) v += RG[P2][J] * R[J][Q2];
+      Gl[P2][Q2] = v;
+    }
+  double Gb[21];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = I; J < 6; ++J) Gb[sidx(I, J)] = 0.5 * (Gl[I][J] + Gl[J][I]);
+  PointArrays A{};
+  A.nrm = nrm; A.ns = ws;
+  tangent_adjoint_pass(t, CMP, phv, ws, A, Gb, Cst, Wk);
+  if (CMP) adjoint_weights_c(t, t.wl, t.wsum, Wk, gw, ws);
+  else adjoint_weights(t, t.wl, t.wsum, Wk, gw, ws);
+}
+
 int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // parameters of a tree description in heap order (array index = heap number - 1)
@@ -856,7 +956,7 @@ struct CmpTree {
   int N = 0, Lc = 0, nz = 0;
   std::vector<double> p, q, c;   // p, q [N][M]; c = c1 [N], c2 [N], sc [N], leaf weights [L]
   std::vector<float> cf;         // c1f [N], c2f [N], c12f [N]
-  std::vector<int> tab;          // lf [Lc] (4 ints each), pre [N], post [N], paper index [N]
+  std::vector<int> tab;          // lf [Lc] (4 ints each), pre [N], post [N], paper index [N], children [2 N]
 };
 
 void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& B) {
@@ -926,6 +1026,16 @@ void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& 
   B.tab.insert(B.tab.end(), pre.begin(), pre.end());
   B.tab.insert(B.tab.end(), post.begin(), post.end());
   B.tab.insert(B.tab.end(), paper_of.begin(), paper_of.end());
+  // children of every kept laminate, laminates passed through skipped: a kept laminate's
+  // number, or -1 - phase for a leaf
+  std::vector<int> kids(2 * (size_t)Nc, 0);
+  auto stand_in = [&](int x) {
+    while (x <= N && cid[x] < 0) x = W[2 * x] > 0.0 ? 2 * x : 2 * x + 1;
+    return x > N ? -1 - ((x - N - 1) & 1) : cid[x];
+  };
+  for (int h = 1; h <= N; ++h)
+    if (cid[h] >= 0) { kids[2 * cid[h]] = stand_in(2 * h); kids[2 * cid[h] + 1] = stand_in(2 * h + 1); }
+  B.tab.insert(B.tab.end(), kids.begin(), kids.end());
 }
 
 bool has_zero_weight(const dmn_tree_desc& d) {
@@ -1468,14 +1578,18 @@ int dmn_set_params(dmn_handle* h, int32_t tree_id, const double* p, const double
 
 int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam, const double* Q, const double* E_n,
              const double* dE, const double* state_in, const double* state_out, const double* g_stress,
-             double* g_p, double* g_q, double* g_w, double* g_E, void* stream) {
+             const double* g_tangent, double* g_p, double* g_q, double* g_w, double* g_E, void* stream) {
   if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_grad: NULL handle");
   if (n < 0) return fail(h, DMN_ERR_ARG, "dmn_grad: n < 0");
   if (tree_id || h->trees.size() != 1) return fail(h, DMN_ERR_ARG, "dmn_grad: one tree only (tree_id must be NULL)");
-  if (n == 0) return DMN_OK;
-  if (!lam || !Q || !E_n || !dE || !state_in || !state_out || !g_stress || !g_p || !g_q || !g_w)
-    return fail(h, DMN_ERR_ARG, "dmn_grad: NULL array");
+  if (!g_stress && !g_tangent) return fail(h, DMN_ERR_ARG, "dmn_grad: g_stress and g_tangent are both NULL");
   const Tree& T = h->trees[0];
+  const TreeDev td = tree_dev(T);
+  if (g_tangent && (td.ph[0].kind != DMN_PHASE_ELASTIC || td.ph[1].kind != DMN_PHASE_ELASTIC))
+    return fail(h, DMN_ERR_ARG, "dmn_grad: tangent seeds need a tree of elastic phases");
+  if (n == 0) return DMN_OK;
+  if (!lam || !Q || !g_p || !g_q || !g_w || (g_stress && (!E_n || !dE || !state_in || !state_out)))
+    return fail(h, DMN_ERR_ARG, "dmn_grad: NULL array");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t chunk = std::min<int64_t>(n, 65536);   // few points per chunk leave the adjoint latency-bound
   const size_t fields = grad_fields(T.N, T.L);
@@ -1487,13 +1601,20 @@ int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam
     if (e != cudaSuccess) return cuda_fail(h, e, "dmn_grad: work buffer");
     h->gwork_cap = chunk;
   }
-  const TreeDev td = tree_dev(T);
   const int n_params = 2 * T.N * T.M + T.L;
   for (int64_t n0 = 0; n0 < n; n0 += chunk) {
     const int64_t nc = std::min(chunk, n - n0);
-    GradParams P{td, n, n0, nc, lam, Q, E_n, dE, state_in, state_out, g_stress, g_E, h->gwork};
-    if (h->cmp) k_grad<true><<<(unsigned)div_up(nc, 128), 128, 0, s>>>(P);
-    else k_grad<false><<<(unsigned)div_up(nc, 128), 128, 0, s>>>(P);
+    const unsigned grid = (unsigned)div_up(nc, 128);
+    if (g_stress) {
+      GradParams P{td, n, n0, nc, lam, Q, E_n, dE, state_in, state_out, g_stress, g_E, h->gwork};
+      if (h->cmp) k_grad<true><<<grid, 128, 0, s>>>(P);
+      else k_grad<false><<<grid, 128, 0, s>>>(P);
+    }
+    if (g_tangent) {
+      GradTParams P{td, n, n0, nc, lam, Q, g_tangent, g_E, h->gwork, g_stress ? 0 : 1};
+      if (h->cmp) k_grad_tangent<true><<<grid, 128, 0, s>>>(P);
+      else k_grad_tangent<false><<<grid, 128, 0, s>>>(P);
+    }
     k_grad_reduce<<<n_params, 256, 0, s>>>(td, nc, h->gwork, g_p, g_q, g_w);
   }
   e = cudaGetLastError();
@@ -1523,8 +1644,21 @@ constexpr int NOALLOC_BLOCK = 128;
 // the rest: per-lane scratch (normals, jumps, g and H of every laminate).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[DMN_NOALLOC_BYTES];
 
-std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[256] = {nullptr};  // device address of g_noalloc_scratch, per device
+// Tree parameters passed by value as a kernel argument (26.5 KB at K = 8, M = 6, within
+// the 32,764 bytes a kernel's arguments may take), so that nothing the call leaves queued
+// refers to host memory once it has returned.
+struct NoAllocUpload {
+  int nm, L;
+  double p[NMAX * 6], q[NMAX * 6];
+  double w[1 << KMAX];
+};
+static_assert(sizeof(NoAllocUpload) <= 32764, "kernel argument too large");
+
+__global__ void k_noalloc_upload(NoAllocUpload u, double* __restrict__ d_p, double* __restrict__ d_q,
+                                 double* __restrict__ d_w) {
+  for (int i = threadIdx.x; i < u.nm; i += blockDim.x) { d_p[i] = u.p[i]; d_q[i] = u.q[i]; }
+  for (int i = threadIdx.x; i < u.L; i += blockDim.x) d_w[i] = u.w[i];
+}
 
 struct NoAllocParams {
   TreeDev t;
@@ -1639,6 +1773,8 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
       return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: only the FP64 form is available without allocation");
     if (opt->predictor != 0)
       return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: the extrapolated start is not available without allocation");
+    if (opt->line_search != 0)
+      return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: the line search is not available without allocation");
     if (opt->tol > 0.0) tol = opt->tol;
     if (opt->max_iter > 0) max_iter = opt->max_iter;
   }
@@ -1664,22 +1800,13 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
     return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: NULL array");
   if (state_in == state_out) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: state_in and state_out must differ");
 
-  // device address of the static work space, looked up once per device
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= 256) return fail(nullptr, DMN_ERR_ARG, "dmn_update_noalloc: device ordinal out of range");
-  unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-      void* ptr = nullptr;
-      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: cudaGetSymbolAddress");
-      g_noalloc_addr[dev] = ptr;
-    }
-    base = (unsigned char*)g_noalloc_addr[dev];
-  }
+  // device address of the static work space on the current device, looked up on every call
+  // (cheap; a reset device may load the module at another address).  The first call on a
+  // device also loads the module, which is why it must come before any stream capture.
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: cudaGetSymbolAddress");
+  unsigned char* base = (unsigned char*)ptr;
   unsigned long long* counter = (unsigned long long*)base;
   double* prm = (double*)(base + 256);
   double* d_p = prm;
@@ -1689,14 +1816,14 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   float* d_cf = (float*)(d_c + 3 * N + L);
   double* slots = (double*)(base + 256 + sizeof(double) * NOALLOC_PARAM_DOUBLES);
 
-  // parameters in heap order, staged on the host stack (no heap allocation)
-  double ph[NMAX * 6], qh[NMAX * 6];
-  heap_params(d, ph, qh);
+  // parameters in heap order, handed to the device by value as a kernel argument
+  NoAllocUpload up;
+  up.nm = N * M;
+  up.L = L;
+  heap_params(d, up.p, up.q);
+  for (int l = 0; l < L; ++l) up.w[l] = d.w[l];
   cudaStream_t s = (cudaStream_t)stream;
-  e = cudaMemcpyAsync(d_p, ph, sizeof(double) * N * M, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_q, qh, sizeof(double) * N * M, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, d.w, sizeof(double) * L, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: parameter upload");
+  k_noalloc_upload<<<1, 256, 0, s>>>(up, d_p, d_q, d_w);
   k_setup_tree<<<1, 1, 0, s>>>(K, d_w, d_c, d_cf);
   // the counter keeps the previous call's value: clear it
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);

@@ -72,6 +72,7 @@ struct TreeDev {
   const int* pre;    // [N] laminates in descent (pre-) order
   const int* post;   // [N] laminates in completion (post-) order
   const int* pidx;   // [N] the paper's index of each laminate (in the uncompressed tree)
+  const int* kid;    // [2 N] children of each laminate: >= 0 a laminate, -1 - phase a leaf
 };
 
 // fields of TreeDev::lf .w
@@ -465,11 +466,17 @@ __device__ __forceinline__ void condense(const double nd[3], const T n[3], doubl
 //   C  = (c1 lam_L + c2 lam_R) 1(x)1 + 2 (c1 mu_L + c2 mu_R) I
 //        - c1 c_L m_L (x) m_L - c2 c_R m_R (x) m_R + c1 c2 B H,
 // and, the leaves having no inner corrections, ds = c1 c2 B g with g = -Kn^-1 t.
+// A leaf of an elastic phase has c_X = 0 in every pass: elL / elR (the phases of the
+// tree's left and right leaves, the same for every lane) drop its rank-one terms in the
+// FP64 condensation, which leaves every non-zero result unchanged.
 template <typename T, bool STORE>
 __device__ __forceinline__ void condense_bottom(const double nd[3], const T n[3], double c1d, double c2d, double sc,
                                                 NodeC<T> cc, const double sL[6], const LeafTan<T>& DL,
                                                 const double sR[6], const LeafTan<T>& DR, Sub<T>& out, T* gp,
-                                                size_t gstride, double& r2) {
+                                                size_t gstride, double& r2, bool elL, bool elR) {
+  // the FP32 condensation runs beside the FP64 work at no cost of its own: it keeps the general
+  // form, whose register use the shortcut would raise
+  if (sizeof(T) == 4) { elL = false; elR = false; }
   T u[3];
   {
     double t[3];
@@ -479,32 +486,57 @@ __device__ __forceinline__ void condense_bottom(const double nd[3], const T n[3]
   const T c1 = cc.c1, c2 = cc.c2, c12 = cc.c12;
   const T nr[3] = {n[0] * (T)RS2, n[1] * (T)RS2, n[2] * (T)RS2};
   T uL[3], uR[3];
-  Nt_apply<T>(n, nr, DL.m, uL);
-  Nt_apply<T>(n, nr, DR.m, uR);
   const T a = c2 * DL.mu + c1 * DR.mu;
   const T b = c2 * (DL.lam + DL.mu) + c1 * (DR.lam + DR.mu);
-  const T wL = c2 * DL.c, wR = c1 * DR.c;
   T k[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = i; j < 3; ++j) k[i][j] = b * n[i] * n[j] - wL * uL[i] * uL[j] - wR * uR[i] * uR[j] + (i == j ? a : (T)0);
+    for (int j = i; j < 3; ++j) k[i][j] = b * n[i] * n[j] + (i == j ? a : (T)0);
+  T cmL[6], cmR[6];
+  if (!elL) {
+    Nt_apply<T>(n, nr, DL.m, uL);
+    const T wL = c2 * DL.c;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) k[i][j] -= wL * uL[i] * uL[j];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) cmL[I] = DL.c * DL.m[I];
+  }
+  if (!elR) {
+    Nt_apply<T>(n, nr, DR.m, uR);
+    const T wR = c1 * DR.c;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) k[i][j] -= wR * uR[i] * uR[j];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) cmR[I] = DR.c * DR.m[I];
+  }
   T Ki[3][3];
   inv3_sym<T>(k[0][0], k[0][1], k[0][2], k[1][1], k[1][2], k[2][2], Ki);
-  const T dlam = DR.lam - DL.lam, dmu2 = (T)2 * (DR.mu - DL.mu);
-  T cmL[6], cmR[6];
-#pragma unroll
-  for (int I = 0; I < 6; ++I) { cmL[I] = DL.c * DL.m[I]; cmR[I] = DR.c * DR.m[I]; }
+  // (lam_R - lam_L) 1 (x) n + 2 (mu_R - mu_L) N: entry (I, j) is dlam n_j (I < 3, j != I),
+  // (dlam + dmu2) n_j (I = j) or dmu2 N_Ij (shear rows)
+  const T dlam = DR.lam - DL.lam, dmu2 = (T)2 * (DR.mu - DL.mu), dld = dlam + dmu2;
   T B[6][3];
 #pragma unroll
   for (int I = 0; I < 6; ++I)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      T v = cmL[I] * uL[j] - cmR[I] * uR[j];
-      if (I < 3) v += dlam * n[j];
-      if (N_nonzero(I, j)) v += dmu2 * N_entry<T>(n, nr, I, j);
-      B[I][j] = v;
-    }
+    for (int j = 0; j < 3; ++j)
+      B[I][j] = I < 3 ? (I == j ? dld : dlam) * n[j] : (N_nonzero(I, j) ? dmu2 * N_entry<T>(n, nr, I, j) : (T)0);
+  if (!elL) {
+#pragma unroll
+    for (int I = 0; I < 6; ++I)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) B[I][j] += cmL[I] * uL[j];
+  }
+  if (!elR) {
+#pragma unroll
+    for (int I = 0; I < 6; ++I)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) B[I][j] -= cmR[I] * uR[j];
+  }
   T H[3][6];
 #pragma unroll
   for (int m = 0; m < 3; ++m)
@@ -517,25 +549,41 @@ __device__ __forceinline__ void condense_bottom(const double nd[3], const T n[3]
 #pragma unroll
   for (int I = 0; I < 6; ++I) out.ds[I] = B[I][0] * g12[0] + B[I][1] * g12[1] + B[I][2] * g12[2];
   const T lamC = c1 * DL.lam + c2 * DR.lam, mu2C = (T)2 * (c1 * DL.mu + c2 * DR.mu);
-  T hL[6], hR[6];
-#pragma unroll
-  for (int I = 0; I < 6; ++I) { hL[I] = c1 * cmL[I]; hR[I] = c2 * cmR[I]; }
   T H12[3][6];
 #pragma unroll
   for (int m = 0; m < 3; ++m)
 #pragma unroll
     for (int I = 0; I < 6; ++I) H12[m][I] = c12 * H[m][I];
+  T Cb[21];
 #pragma unroll
   for (int I = 0; I < 6; ++I)
 #pragma unroll
     for (int J = I; J < 6; ++J) {
       T v = B[I][0] * H12[0][J] + B[I][1] * H12[1][J] + B[I][2] * H12[2][J];
-      v -= hL[I] * DL.m[J];
-      v -= hR[I] * DR.m[J];
       if (I < 3 && J < 3) v += lamC;
       if (I == J) v += mu2C;
-      out.C[sidx(I, J)] = v;
+      Cb[sidx(I, J)] = v;
     }
+  if (!elL) {
+    T hL[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) hL[I] = c1 * cmL[I];
+#pragma unroll
+    for (int I = 0; I < 6; ++I)
+#pragma unroll
+      for (int J = I; J < 6; ++J) Cb[sidx(I, J)] -= hL[I] * DL.m[J];
+  }
+  if (!elR) {
+    T hR[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) hR[I] = c2 * cmR[I];
+#pragma unroll
+    for (int I = 0; I < 6; ++I)
+#pragma unroll
+      for (int J = I; J < 6; ++J) Cb[sidx(I, J)] -= hR[I] * DR.m[J];
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 21; ++k2) out.C[k2] = Cb[k2];
   if (STORE) {
 #pragma unroll
     for (int m = 0; m < 3; ++m) gp[m * gstride] = g[m];
@@ -685,7 +733,8 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
       load_n<T>(P, node, nd, nt);
       T* gp = STORE ? gh.q + (size_t)(21 * node) * gh.s : nullptr;
       condense_bottom<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node),
-                                node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2);
+                                node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2, t.ph[0].kind == 0,
+                                t.ph[1].kind == 0);
     }
     // condense upwards while the finished laminate is a right child
     int lvl = K, idx = m;
@@ -824,7 +873,8 @@ __device__ void tree_pass_c(const TreeDev& t, const double Eloc[6], const PointA
       load_n<T>(P, node, nd, nt);
       T* gp = STORE ? gh.q + (size_t)(21 * node) * gh.s : nullptr;
       condense_bottom<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node),
-                                node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2);
+                                node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2, t.ph[ph0].kind == 0,
+                                t.ph[ph1].kind == 0);
       --d;
       nup = f2.z - 1;
       l += 2;
@@ -959,16 +1009,18 @@ struct AdjWork {
   size_t ws;
 };
 
-// angles of laminate `node` from the point's shape-function values
-__device__ __forceinline__ void node_angles(const TreeDev& t, int node, const double ph[6], double& al, double& be) {
+// angles of laminate `node` from the point's shape-function values ph[m * phs] (the kernels pass the
+// work array's copy in global memory)
+__device__ __forceinline__ void node_angles(const TreeDev& t, int node, const double* ph, size_t phs, double& al,
+                                            double& be) {
   al = 0.0; be = 0.0;
   for (int m = 0; m < t.M; ++m) {
-    al += __ldg(t.p + node * t.M + m) * ph[m];
-    be += __ldg(t.q + node * t.M + m) * ph[m];
+    al += __ldg(t.p + node * t.M + m) * ph[m * phs];
+    be += __ldg(t.q + node * t.M + m) * ph[m * phs];
   }
 }
 
-__device__ void adjoint_pass(const TreeDev& t, const double Eloc[6], const double gl[6], const double ph[6],
+__device__ void adjoint_pass(const TreeDev& t, const double Eloc[6], const double gl[6], const double* ph, size_t phs,
                              const PointArrays& P, const AdjWork& Wk) {
   const int K = t.K;
   double epsR[KMAX + 1][6], gR[KMAX + 1][6];
@@ -1063,7 +1115,7 @@ __device__ void adjoint_pass(const TreeDev& t, const double Eloc[6], const doubl
       const double sc = W * c1 * c2;
       const double gn[3] = {sc * (u1[0] + u2[0]), sc * (u1[1] + u2[1]), sc * (u1[2] + u2[2])};
       double al, be, sa, ca, sbeta, cbeta;
-      node_angles(t, node, ph, al, be);
+      node_angles(t, node, ph, phs, al, be);
       sincos(al, &sa, &ca);
       sincos(be, &sbeta, &cbeta);
       Wk.gab[(size_t)node * ws] = gn[0] * ca * cbeta + gn[1] * ca * sbeta - gn[2] * sa;
@@ -1132,8 +1184,8 @@ __device__ void adjoint_weights(const TreeDev& t, const double* wl, double S, co
 
 // adjoint_pass over a compressed tree (tables of TreeDev): the same per-laminate and
 // per-leaf terms, leaves one at a time, laminates numbered as in the state.
-__device__ void adjoint_pass_c(const TreeDev& t, const double Eloc[6], const double gl[6], const double ph[6],
-                               const PointArrays& P, const AdjWork& Wk) {
+__device__ void adjoint_pass_c(const TreeDev& t, const double Eloc[6], const double gl[6], const double* ph,
+                               size_t phs, const PointArrays& P, const AdjWork& Wk) {
   double epsR[KMAX + 1][6], gR[KMAX + 1][6];
   double pend_s[KMAX + 1][6], pend_t[KMAX + 1][6];
   const size_t ws = Wk.ws;
@@ -1218,7 +1270,7 @@ __device__ void adjoint_pass_c(const TreeDev& t, const double Eloc[6], const dou
       const double sc = W * c1 * c2;
       const double gn[3] = {sc * (u1[0] + u2[0]), sc * (u1[1] + u2[1]), sc * (u1[2] + u2[2])};
       double al, be, sa, ca, sbeta, cbeta;
-      node_angles(t, node, ph, al, be);
+      node_angles(t, node, ph, phs, al, be);
       sincos(al, &sa, &ca);
       sincos(be, &sbeta, &cbeta);
       Wk.gab[(size_t)node * ws] = gn[0] * ca * cbeta + gn[1] * ca * sbeta - gn[2] * sa;
@@ -1276,6 +1328,301 @@ __device__ void adjoint_weights_c(const TreeDev& t, const double* wl, double S, 
   for (int l = 0; l < t.Lc; ++l) {
     const int leaf = lf_leaf(__ldg(t.lf + l).w);
     gw[(size_t)leaf * gws] = (gw[(size_t)leaf * gws] - sum_gw) / S;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tangent seeds of the adjoint, for trees of elastic phases.  With constant
+// leaf tangents the DMN's tangent is the laminate recursion of Sec. 3.1 (Eq. of
+// the stiffness propagation), here in the form of the condensation: a laminate
+// with children tangents C_L, C_R (fractions c1, c2, normal n) has
+//   Ch = c2 C_L + c1 C_R, dC = C_R - C_L, B = dC N, Kn = N^T Ch N, Y = Kn^-1 B^T,
+//   C  = c1 C_L + c2 C_R - c1 c2 B Y.
+// Reverse mode, for a symmetric Gb = dL/dC (dL = sum over all 36 entries of Gb dC):
+//   Bb = -2 c1 c2 Gb Y^T,   Kb = c1 c2 Y Gb Y^T,
+//   dL/dC_L = sym(c1 Gb + c2 N Kb N^T - Bb N^T),  dL/dC_R = sym(c2 Gb + c1 N Kb N^T + Bb N^T),
+//   dL/dN   = 2 Ch N Kb + dC Bb,
+//   dL/dc1  = Gb : (C_L - C_R) - (c2 - c1) Gb : (B Y) + Kb : (N^T B)   (c2 = 1 - c1).
+// Matrices are full 6x6 here; packed arguments hold the upper triangle (sidx).
+
+__device__ __forceinline__ void unpack_sym6(const double p[21], double A[6][6]) {
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = 0; J < 6; ++J) A[I][J] = p[sidx(I, J)];
+}
+
+__device__ __forceinline__ void n_matrix(const double n[3], double Nm[6][3]) {
+  const double nr[3] = {n[0] * RS2, n[1] * RS2, n[2] * RS2};
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Nm[I][j] = N_nonzero(I, j) ? N_entry<double>(n, nr, I, j) : 0.0;
+}
+
+// the laminate's tangent C (packed) from its children's
+__device__ void lam_tangent(const double n[3], double c1, double c2, const double CL[21], const double CR[21],
+                            double C[21]) {
+  double Nm[6][3];
+  n_matrix(n, Nm);
+  double ChN[6][3], B[6][3];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double a = 0.0, b = 0.0;
+#pragma unroll
+      for (int P = 0; P < 6; ++P) {
+        const int s2 = sidx(I, P);
+        a += (c2 * CL[s2] + c1 * CR[s2]) * Nm[P][j];
+        b += (CR[s2] - CL[s2]) * Nm[P][j];
+      }
+      ChN[I][j] = a; B[I][j] = b;
+    }
+  double K[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double v = 0.0;
+#pragma unroll
+      for (int P = 0; P < 6; ++P) v += Nm[P][i] * ChN[P][j];
+      K[i][j] = v;
+    }
+  double Ki[3][3];
+  inv3_sym<double>(K[0][0], 0.5 * (K[0][1] + K[1][0]), 0.5 * (K[0][2] + K[2][0]), K[1][1],
+                   0.5 * (K[1][2] + K[2][1]), K[2][2], Ki);
+  double Y[3][6];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int J = 0; J < 6; ++J) Y[m][J] = Ki[m][0] * B[J][0] + Ki[m][1] * B[J][1] + Ki[m][2] * B[J][2];
+  const double c12 = c1 * c2;
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = I; J < 6; ++J) {
+      const int s2 = sidx(I, J);
+      C[s2] = c1 * CL[s2] + c2 * CR[s2] - c12 * (B[I][0] * Y[0][J] + B[I][1] * Y[1][J] + B[I][2] * Y[2][J]);
+    }
+}
+
+__device__ void lam_tangent_adjoint(const double n[3], double c1, double c2, const double CL[21], const double CR[21],
+                                    const double Gbp[21], double GL[21], double GR[21], double nb[3], double& c1b) {
+  double Nm[6][3];
+  n_matrix(n, Nm);
+  double Ch[6][6], dC[6][6], Gb[6][6];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = 0; J < 6; ++J) {
+      const int s2 = sidx(I, J);
+      Ch[I][J] = c2 * CL[s2] + c1 * CR[s2];
+      dC[I][J] = CR[s2] - CL[s2];
+      Gb[I][J] = Gbp[s2];
+    }
+  double ChN[6][3], B[6][3];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double a = 0.0, b = 0.0;
+#pragma unroll
+      for (int P = 0; P < 6; ++P) { a += Ch[I][P] * Nm[P][j]; b += dC[I][P] * Nm[P][j]; }
+      ChN[I][j] = a; B[I][j] = b;
+    }
+  double K[3][3], NB[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double v = 0.0, w = 0.0;
+#pragma unroll
+      for (int P = 0; P < 6; ++P) { v += Nm[P][i] * ChN[P][j]; w += Nm[P][i] * B[P][j]; }
+      K[i][j] = v; NB[i][j] = w;
+    }
+  double Ki[3][3];
+  inv3_sym<double>(K[0][0], 0.5 * (K[0][1] + K[1][0]), 0.5 * (K[0][2] + K[2][0]), K[1][1],
+                   0.5 * (K[1][2] + K[2][1]), K[2][2], Ki);
+  double Y[3][6];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int J = 0; J < 6; ++J) Y[m][J] = Ki[m][0] * B[J][0] + Ki[m][1] * B[J][1] + Ki[m][2] * B[J][2];
+  const double c12 = c1 * c2;
+  // T = Gb Y^T (6x3); Bb = -2 c12 T; Kb = c12 Y T
+  double T[6][3];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      double v = 0.0;
+#pragma unroll
+      for (int J = 0; J < 6; ++J) v += Gb[I][J] * Y[m][J];
+      T[I][m] = v;
+    }
+  double Bb[6][3], Kb[3][3];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) Bb[I][m] = -2.0 * c12 * T[I][m];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double v = 0.0;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) v += Y[m][I] * T[I][k];
+      Kb[m][k] = c12 * v;
+    }
+  // dL/dc1
+  double gLR = 0.0, gBY = 0.0, kNB = 0.0;
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = 0; J < 6; ++J) gLR -= Gb[I][J] * dC[I][J];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) gBY += B[I][m] * T[I][m];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) kNB += Kb[i][j] * NB[i][j];
+  c1b = gLR - (c2 - c1) * gBY + kNB;
+  // N Kb N^T and Bb N^T
+  double NK[6][3];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) NK[I][k] = Nm[I][0] * Kb[0][k] + Nm[I][1] * Kb[1][k] + Nm[I][2] * Kb[2][k];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int J = I; J < 6; ++J) {
+      const double nkn = NK[I][0] * Nm[J][0] + NK[I][1] * Nm[J][1] + NK[I][2] * Nm[J][2];
+      const double bn = 0.5 * (Bb[I][0] * Nm[J][0] + Bb[I][1] * Nm[J][1] + Bb[I][2] * Nm[J][2]
+                               + Bb[J][0] * Nm[I][0] + Bb[J][1] * Nm[I][1] + Bb[J][2] * Nm[I][2]);
+      const int s2 = sidx(I, J);
+      GL[s2] = c1 * Gb[I][J] + c2 * nkn - bn;
+      GR[s2] = c2 * Gb[I][J] + c1 * nkn + bn;
+    }
+  // dL/dN = 2 Ch N Kb + dC Bb, then dL/dn through N's entries
+  double Nb[6][3];
+#pragma unroll
+  for (int I = 0; I < 6; ++I)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double v = 2.0 * (ChN[I][0] * Kb[0][k] + ChN[I][1] * Kb[1][k] + ChN[I][2] * Kb[2][k]);
+#pragma unroll
+      for (int P = 0; P < 6; ++P) v += dC[I][P] * Bb[P][k];
+      Nb[I][k] = v;
+    }
+  nb[0] = Nb[0][0]; nb[1] = Nb[1][1]; nb[2] = Nb[2][2];
+  // shear rows: N[I][a] = n_b / sqrt2, N[I][b] = n_a / sqrt2 for the index pair (a, b) of row I
+#pragma unroll
+  for (int I = 3; I < 6; ++I) {
+    const int a = I == 3 ? 1 : 0, b = I == 5 ? 1 : 2;
+    nb[b] += RS2 * Nb[I][a];
+    nb[a] += RS2 * Nb[I][b];
+  }
+}
+
+// children of a laminate: >= 0 a laminate (array index), -1 - phase a leaf
+__device__ __forceinline__ void lam_kids(const TreeDev& t, bool cmp, int node, int& k1, int& k2) {
+  if (cmp) {
+    k1 = __ldg(t.kid + 2 * node);
+    k2 = __ldg(t.kid + 2 * node + 1);
+  } else if (node >= (1 << (t.K - 1)) - 1) {   // bottom laminate: leaves of phases 0 and 1
+    k1 = -1; k2 = -2;
+  } else {
+    k1 = 2 * node + 1; k2 = 2 * node + 2;
+  }
+}
+
+// Per point: the tangent's adjoint for the seed Gb_root (local frame, symmetric, packed),
+// added to the per-laminate angle gradients and weight terms of AdjWork.  Cst [21 N]
+// (stride Wk.ws) receives every laminate's tangent.  ph: the point's shape-function values,
+// ph[m * phs] (the work array's copy in the kernel).
+__device__ void tangent_adjoint_pass(const TreeDev& t, bool cmp, const double* ph, size_t phs, const PointArrays& P,
+                                     const double Gb_root[21], double* Cst, const AdjWork& Wk) {
+  const size_t ws = Wk.ws;
+  const int N = t.N;
+  double Cph[2][21];
+#pragma unroll
+  for (int f = 0; f < 2; ++f)
+#pragma unroll
+    for (int I = 0; I < 6; ++I)
+#pragma unroll
+      for (int J = I; J < 6; ++J)
+        Cph[f][sidx(I, J)] = ((I < 3 && J < 3) ? t.ph[f].lam : 0.0) + (I == J ? 2.0 * t.ph[f].G : 0.0);
+  // forward: children before parents (heap: descending index; compressed: the paper's order)
+  for (int x = 0; x < N; ++x) {
+    const int node = cmp ? x : N - 1 - x;
+    int k1, k2;
+    lam_kids(t, cmp, node, k1, k2);
+    double CL[21], CR[21], C[21], nd[3];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) {
+      CL[k] = k1 >= 0 ? Cst[(size_t)(21 * k1 + k) * ws] : Cph[-1 - k1][k];
+      CR[k] = k2 >= 0 ? Cst[(size_t)(21 * k2 + k) * ws] : Cph[-1 - k2][k];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nd[c] = P.nrm[(3 * node + c) * P.ns];
+    lam_tangent(nd, __ldg(t.c1 + node), __ldg(t.c2 + node), CL, CR, C);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) Cst[(size_t)(21 * node + k) * ws] = C[k];
+  }
+  // reverse: depth first from the root, pending left subtrees on a stack
+  double stG[KMAX + 1][21];
+  int stN[KMAX + 1];
+  int sp = 0;
+  int node = cmp ? N - 1 : 0;
+  double G[21];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) G[k] = Gb_root[k];
+  for (int guard = 0; guard < N; ++guard) {
+    int k1, k2;
+    lam_kids(t, cmp, node, k1, k2);
+    double CL[21], CR[21], GL[21], GR[21], nd[3], nb[3], c1b;
+#pragma unroll
+    for (int k = 0; k < 21; ++k) {
+      CL[k] = k1 >= 0 ? Cst[(size_t)(21 * k1 + k) * ws] : Cph[-1 - k1][k];
+      CR[k] = k2 >= 0 ? Cst[(size_t)(21 * k2 + k) * ws] : Cph[-1 - k2][k];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nd[c] = P.nrm[(3 * node + c) * P.ns];
+    const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+    lam_tangent_adjoint(nd, c1, c2, CL, CR, G, GL, GR, nb, c1b);
+    double al, be, sa, ca, sbeta, cbeta;
+    node_angles(t, node, ph, phs, al, be);
+    sincos(al, &sa, &ca);
+    sincos(be, &sbeta, &cbeta);
+    Wk.gab[(size_t)node * ws] += nb[0] * ca * cbeta + nb[1] * ca * sbeta - nb[2] * sa;
+    Wk.gab[(size_t)(N + node) * ws] += -nb[0] * sa * sbeta + nb[1] * sa * cbeta;
+    const double W = __ldg(t.sc + node) / (c1 * c2);
+    Wk.xi[(size_t)node * ws] += c1b / (W * W);   // c1 = W_L / W: d/dW_L = W_R Xi, d/dW_R = -W_L Xi
+    if (k2 >= 0) {
+      if (k1 >= 0 && sp <= KMAX) {
+#pragma unroll
+        for (int k = 0; k < 21; ++k) stG[sp][k] = GL[k];
+        stN[sp++] = k1;
+      }
+      node = k2;
+#pragma unroll
+      for (int k = 0; k < 21; ++k) G[k] = GR[k];
+    } else if (k1 >= 0) {
+      node = k1;
+#pragma unroll
+      for (int k = 0; k < 21; ++k) G[k] = GL[k];
+    } else if (sp > 0) {
+      --sp;
+      node = stN[sp];
+#pragma unroll
+      for (int k = 0; k < 21; ++k) G[k] = stG[sp][k];
+    } else {
+      break;
+    }
   }
 }
 

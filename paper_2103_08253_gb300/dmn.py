@@ -79,7 +79,7 @@ def load_library(build_if_missing: bool = True):
     lib.dmn_set_params.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]
     lib.dmn_set_params.restype = ctypes.c_int
-    lib.dmn_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.dmn_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.dmn_grad.restype = ctypes.c_int
     lib.dmn_profile_enable.argtypes = [vp, i32]
     lib.dmn_profile_enable.restype = ctypes.c_int
@@ -90,8 +90,49 @@ def load_library(build_if_missing: bool = True):
     lib.dmn_update_noalloc.restype = ctypes.c_int
     lib.dmn_last_error.argtypes = [vp]
     lib.dmn_last_error.restype = ctypes.c_char_p
+    lib.dmn_peak_gflops.argtypes = [i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), vp]
+    lib.dmn_peak_gflops.restype = ctypes.c_int
+    lib.dmn_fma_throughput.argtypes = [i32, i32, i32, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), vp]
+    lib.dmn_fma_throughput.restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+# include/dmn_peak.h
+PEAK_EXPORTS = ("dmn_peak_gflops", "dmn_fma_throughput")
+PEAK_FP64_FMA, PEAK_FP32_FMA = 0, 1
+
+
+def peak_gflops(kind: str = "fp64", seconds: float = 1.0):
+    """Sustained FMA throughput (GFLOP/s) of the current CUDA device over about `seconds`
+    (dmn_peak_gflops, on torch's current stream); returns (gflops, measured ms)."""
+    import torch
+    lib = load_library()
+    k = {"fp64": PEAK_FP64_FMA, "fp32": PEAK_FP32_FMA}[kind]
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.dmn_peak_gflops(k, float(seconds), ctypes.byref(g), ctypes.byref(ms), stream)
+    if rc != 0:
+        raise RuntimeError(lib.dmn_last_error(None).decode())
+    return g.value, ms.value
+
+
+def fma_throughput(kind: str = "fp64", warps_per_sm: int = 64, chains: int = 8, active_lanes: int = 32,
+                   seconds: float = 0.2):
+    """dmn_fma_throughput: FMA GFLOP/s of the active lanes at a chosen occupancy, number of independent
+    chains per thread and number of active lanes per warp; returns (gflops, measured ms)."""
+    import torch
+    lib = load_library()
+    k = {"fp64": PEAK_FP64_FMA, "fp32": PEAK_FP32_FMA}[kind]
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.dmn_fma_throughput(k, int(warps_per_sm), int(chains), int(active_lanes), float(seconds), ctypes.byref(g),
+                                ctypes.byref(ms), stream)
+    if rc != 0:
+        raise RuntimeError(lib.dmn_last_error(None).decode())
+    return g.value, ms.value
 
 
 def _ptr(t):
@@ -288,16 +329,26 @@ class DMN:
         if rc != 0:
             self._err("dmn_set_params", rc)
 
-    def grad(self, lam, Q, E_n, dE, state_in, state_out, g_stress, g_p=None, g_q=None, g_w=None, want_E=True):
+    def grad(self, lam, Q, E_n, dE, state_in, state_out, g_stress, g_p=None, g_q=None, g_w=None, want_E=True,
+             g_tangent=None):
         """Adjoint of a converged update: returns (g_p [N, M], g_q [N, M], g_w [2^K], g_E [n, 6] or None),
-        with g_p, g_q, g_w accumulated into the given tensors if passed."""
+        with g_p, g_q, g_w accumulated into the given tensors if passed.  g_stress [n, 6] and/or
+        g_tangent [n, 6, 6] (trees of elastic phases) are the seeds; with g_stress None, E_n, dE and
+        the states may be None too."""
         import torch
         n = lam.shape[0]
         dev = lam.device
         N = (1 << self.K) - 1
-        for name, t, shape in (("lam", lam, (n, 2)), ("Q", Q, (n, 9)), ("E_n", E_n, (n, 6)), ("dE", dE, (n, 6)),
-                               ("state_in", state_in, (self.state_size, n)),
-                               ("state_out", state_out, (self.state_size, n)), ("g_stress", g_stress, (n, 6))):
+        checks = [("lam", lam, (n, 2)), ("Q", Q, (n, 9))]
+        if g_stress is not None:
+            checks += [("E_n", E_n, (n, 6)), ("dE", dE, (n, 6)), ("state_in", state_in, (self.state_size, n)),
+                       ("state_out", state_out, (self.state_size, n)), ("g_stress", g_stress, (n, 6))]
+        if g_tangent is not None:
+            g_tangent = g_tangent.reshape(n, 36) if g_tangent.dim() == 3 and g_tangent.is_contiguous() else g_tangent
+            checks.append(("g_tangent", g_tangent, (n, 36)))
+        if g_stress is None and g_tangent is None:
+            raise ValueError("grad: g_stress and g_tangent are both None")
+        for name, t, shape in checks:
             self._check(name, t, torch.float64, shape)
         z = lambda *sh: torch.zeros(sh, dtype=torch.float64, device=dev)
         g_p = z(N, self.M) if g_p is None else g_p
@@ -311,8 +362,8 @@ class DMN:
         with self._on_device():
             s = torch.cuda.current_stream(self.device).cuda_stream
             rc = self._lib.dmn_grad(self._h, n, None, _ptr(lam), _ptr(Q), _ptr(E_n), _ptr(dE), _ptr(state_in),
-                                    _ptr(state_out), _ptr(g_stress), _ptr(g_p), _ptr(g_q), _ptr(g_w), _ptr(g_E),
-                                    ctypes.c_void_p(s))
+                                    _ptr(state_out), _ptr(g_stress), _ptr(g_tangent), _ptr(g_p), _ptr(g_q),
+                                    _ptr(g_w), _ptr(g_E), ctypes.c_void_p(s))
         if rc != 0:
             self._err("dmn_grad", rc)
         return g_p, g_q, g_w, g_E

@@ -25,13 +25,18 @@ weight by several times its value; the weights' rate is scaled by
 min(1, 8 / 2^K) (`lr_scale_v`), which bounds a step at about a tenth of a
 weight.
 
-The forward solves use, by default, the mixed form with an FP32 tangent
-(`plastic_precision`, `elastic_precision`): the Newton iteration stops on the same
-FP64 residual criterion, so the stresses the loss reads are the FP64 solution's (to
-about 1e-11), and the adjoint recomputes in FP64 at the converged jumps.  The plastic
+The stiffness samples take, by default, the tangent of one update from the virgin
+state at zero strain in the mixed form (its tangent is the FP64 final sweep's,
+exact for elastic phases) and a tangent-seeded adjoint: one reverse pass through
+the laminate recursion per sample (`stiffness_method="tangent"`).  The previous
+route, six stresses at the Mandel unit strains and six stress adjoints per
+sample, remains as `stiffness_method="stress"` (needed with an FP32 tangent).
+The plastic samples' forward solves use the mixed form with an FP32 tangent
+(`plastic_precision`): the Newton iteration stops on the same FP64 residual
+criterion, so the stresses the loss reads are the FP64 solution's (to about
+1e-11), and the adjoint recomputes in FP64 at the converged jumps.  The plastic
 solves are latency-bound (few points, many line-search steps), and the FP32
-condensation has shorter dependency chains.  At K = 8 an epoch of 4096 + 4096 samples
-takes 49 ms, against 104 ms with FP64 solves, with the same losses to six digits.
+condensation has shorter dependency chains.
 
 A weight that reaches zero stays there (the Macaulay bracket has no gradient
 below zero), and the tree is compressed (Sec. 3.1): with `compress` (default)
@@ -93,7 +98,7 @@ class Trainer:
 
     def __init__(self, K, target, n_stiff, seed, elastic_matrix, plastic=None, n_plastic=0, lam_pen=1e3,
                  w_floor=1e-9, alpha_max=1.5e-2, alpha_min=1.5e-3, lr_scale_v=None, compress=True,
-                 plastic_precision="mixed-f32-tangent", elastic_precision="mixed-f32-tangent"):
+                 plastic_precision="mixed-f32-tangent", elastic_precision="mixed", stiffness_method=None):
         import torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
         rng = np.random.default_rng(seed)
@@ -102,6 +107,7 @@ class Trainer:
         self.rebuilds = 0
         self.pl_prec = plastic_precision
         self.el_prec = elastic_precision
+        self.stiff_method = stiffness_method   # dmn_stiffness method (None: tangent seeds with an FP64 tangent)
         self.side = torch.cuda.Stream()   # the plastic samples' stream (see loss)
         self.alpha = (alpha_min, alpha_max)
         d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(self.dev)
@@ -188,7 +194,7 @@ class Trainer:
                 e = torch.linalg.norm(s - self.s_t, dim=1) / torch.linalg.norm(self.s_t, dim=1)
                 e = torch.where(stat == 0, e, torch.zeros_like(e))
                 J_pl = torch.linalg.vector_norm(e, ord=10) / s.shape[0]
-        C = ag.dmn_stiffness(self.m_el, self.lam_e, self.Q_e, self.p, self.q, w)
+        C = ag.dmn_stiffness(self.m_el, self.lam_e, self.Q_e, self.p, self.q, w, method=self.stiff_method)
         J = stiffness_loss(C, self.C_t)
         if self.m_pl is not None:
             torch.cuda.current_stream().wait_stream(self.side)

@@ -31,6 +31,21 @@ def test_library_exports_every_declared_symbol():
     for s in fsyms:
         assert hasattr(lib, s), s
     assert set(fe.FE_EXPORTS) == set(fsyms)
+    psyms = declared_symbols("dmn_peak.h")
+    assert psyms == ["dmn_fma_throughput", "dmn_peak_gflops"] and set(dmn.PEAK_EXPORTS) == set(psyms)
+    for s in psyms:
+        assert hasattr(lib, s), s
+
+
+def test_peak_measurement_rejects_bad_arguments_without_touching_the_gpu():
+    lib = dmn.load_library()
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    assert lib.dmn_peak_gflops(7, 1.0, ctypes.byref(g), ctypes.byref(ms), None) == -1
+    assert "unknown kind" in lib.dmn_last_error(None).decode()
+    assert lib.dmn_peak_gflops(0, 0.0, ctypes.byref(g), ctypes.byref(ms), None) == -1
+    assert lib.dmn_peak_gflops(0, 1.0, None, ctypes.byref(ms), None) == -1
+    for bad in ((0, 6, 8, 32), (0, 64, 3, 32), (0, 64, 8, 0), (0, 65, 8, 32), (2, 64, 8, 32)):
+        assert lib.dmn_fma_throughput(*bad, 0.1, ctypes.byref(g), ctypes.byref(ms), None) == -1, bad
 
 
 def test_fe_mesh_create_rejects_bad_meshes_without_touching_the_gpu():
@@ -101,6 +116,34 @@ def test_predictor_option_is_checked_without_touching_the_gpu():
     o = dmn.Options_(1e-12, 50, dmn.PREC_F64, 0, 0, 0, 1)
     rc = lib.dmn_update_noalloc(ctypes.byref(d), ctypes.byref(o), 8, *([None] * 10), None)
     assert rc == -1 and "extrapolated start" in lib.dmn_last_error(None).decode()
+
+
+def _noalloc(d, o, n=8, arrays=None):
+    lib = dmn.load_library()
+    arrays = arrays if arrays is not None else [None] * 10
+    return lib.dmn_update_noalloc(ctypes.byref(d), None if o is None else ctypes.byref(o), n, *arrays, None), \
+        lib.dmn_last_error(None).decode()
+
+
+@pytest.mark.parametrize("case,msg", [
+    (dict(opt=(1e-12, 50, dmn.PREC_MIXED, 0, 0, 0, 0)), "only the FP64 form"),
+    (dict(opt=(1e-12, 50, dmn.PREC_F64, 0, 0, 0, 1)), "extrapolated start"),
+    (dict(opt=(1e-12, 50, dmn.PREC_F64, 0, 0, 1, 0)), "line search"),
+    (dict(w=np.r_[np.ones(7), 0.0]), "weights"),
+    (dict(K=9), "K must be"),
+    (dict(alias=True), "must differ"),
+])
+def test_allocation_free_update_rejects_what_it_does_not_offer(case, msg):
+    """Each of these returns before any CUDA call, so it needs no GPU."""
+    d, keep = _desc(K=case.get("K", 3), w=case.get("w"))
+    o = dmn.Options_(*case["opt"]) if "opt" in case else None
+    arrays = None
+    if case.get("alias"):
+        fake = [ctypes.c_void_p(4096 * (k + 1)) for k in range(10)]
+        fake[5] = fake[4]   # state_out == state_in
+        arrays = fake
+    rc, err = _noalloc(d, o, arrays=arrays)
+    assert rc == -1 and msg in err, (rc, err)
 
 
 def test_calls_on_null_handle_are_argument_errors():

@@ -83,7 +83,8 @@ struct Tree {
   bool cmp = false;                // a leaf weight is zero: the compressed tree, walked by tables
   std::vector<double> hp, hq, c;   // laminate parameters in the traversal's numbering
   std::vector<float> cf;
-  std::vector<int> tab;            // compressed tree: lf [Lc][4], pre [N], post [N], paper index [N]
+  std::vector<int> tab;            // compressed tree: lf [Lc][4], pre [N], post [N], paper index [N], children
+  std::vector<int> kid;
   TreeDev t{};
   long S;
   Tree(FILE* in, int K_, int M_) : K(K_), M(M_), N((1 << K_) - 1), L(1 << K_) {
@@ -180,10 +181,21 @@ struct Tree {
     tab.insert(tab.end(), pre.begin(), pre.end());
     tab.insert(tab.end(), post.begin(), post.end());
     tab.insert(tab.end(), paper.begin(), paper.end());
+    // children of every remaining laminate (passed-through laminates skipped): its number, or -1 - phase
+    kid.assign(2 * (size_t)Nc, 0);
+    for (int h = 1; h <= N; ++h) {
+      if (cid[h] < 0) continue;
+      for (int side = 0; side < 2; ++side) {
+        int x = 2 * h + side;
+        while (x <= N && cid[x] < 0) x = Wh[2 * x] > 0.0 ? 2 * x : 2 * x + 1;
+        kid[2 * cid[h] + side] = x > N ? -1 - ((x - N - 1) & 1) : cid[x];
+      }
+    }
+    tab.insert(tab.end(), kid.begin(), kid.end());
     N = Nc;
     t.N = Nc; t.Lc = Lc; t.nz = nz; t.z_both = 0;
     t.lf = reinterpret_cast<const int4*>(tab.data());
-    t.pre = tab.data() + 4 * Lc; t.post = t.pre + Nc; t.pidx = t.post + Nc;
+    t.pre = tab.data() + 4 * Lc; t.post = t.pre + Nc; t.pidx = t.post + Nc; t.kid = t.pidx + Nc;
     t.p = hp.data(); t.q = hq.data();
     t.c1 = c.data(); t.c2 = c.data() + Nc; t.sc = c.data() + 2 * Nc; t.wl = c.data() + 3 * Nc;
     t.c1f = cf.data(); t.c2f = cf.data() + Nc; t.c12f = cf.data() + 2 * Nc;
@@ -341,10 +353,10 @@ static int run_grad(FILE* in, FILE* out, int K, int M, long n) {
     Wk.H = gh.data(); Wk.hs = 1; Wk.mu = mu.data(); Wk.xi = xi.data(); Wk.gab = gab.data();
     Wk.direct = direct.data(); Wk.ws = 1;
     if (tr.cmp) {
-      adjoint_pass_c(t, Eloc, gl, f, A, Wk);
+      adjoint_pass_c(t, Eloc, gl, f, 1, A, Wk);
       adjoint_weights_c(t, t.wl, t.wsum, Wk, gw.data(), 1);
     } else {
-      adjoint_pass(t, Eloc, gl, f, A, Wk);
+      adjoint_pass(t, Eloc, gl, f, 1, A, Wk);
       adjoint_weights(t, t.wl, t.wsum, Wk, gw.data(), 1);
     }
     for (int node = 0; node < N; ++node) {
@@ -369,6 +381,51 @@ static int run_grad(FILE* in, FILE* out, int K, int M, long n) {
   return 0;
 }
 
+// the adjoint of the tangent for a tree of elastic phases (the tangent-seed kernel's per-point work, then
+// the sum over points): inputs lam, Q and the seed G [n][36] (global frame); outputs dL/dp, dL/dq, dL/dw
+static int run_grad_tangent(FILE* in, FILE* out, int K, int M, long n) {
+  const Tree tr(in, K, M);
+  const TreeDev& t = tr.t;
+  const int N = tr.N, L = tr.L;
+  std::vector<double> lam(2 * n), Q(9 * n), G(36 * n);
+  rd(lam.data(), 2 * n, in); rd(Q.data(), 9 * n, in); rd(G.data(), 36 * n, in);
+  const int Nfull = L - 1;
+  std::vector<double> gp(Nfull * M, 0.0), gq(Nfull * M, 0.0), gwt(L, 0.0);
+  std::vector<double> nrm(3 * N), Cst(21 * N), mu(3 * N), xi(N), gab(2 * N), direct(L), gw(L);
+  const double zero6[6] = {0, 0, 0, 0, 0, 0};
+  for (long pt = 0; pt < n; ++pt) {
+    double f[6], R[6][6], Eloc[6];
+    tr.point(lam[2 * pt], lam[2 * pt + 1], &Q[9 * pt], zero6, zero6, f, nrm.data(), nullptr, R, Eloc);
+    std::fill(gab.begin(), gab.end(), 0.0); std::fill(xi.begin(), xi.end(), 0.0);
+    std::fill(direct.begin(), direct.end(), 0.0);
+    // the seed in the local frame, symmetrised: Gb = sym(R^T G R)
+    double Gl[6][6], Gb[21];
+    for (int P2 = 0; P2 < 6; ++P2)
+      for (int Q2 = 0; Q2 < 6; ++Q2) {
+        double acc = 0.0;
+        for (int I = 0; I < 6; ++I) for (int J = 0; J < 6; ++J) acc += R[I][P2] * G[36 * pt + 6 * I + J] * R[J][Q2];
+        Gl[P2][Q2] = acc;
+      }
+    for (int I = 0; I < 6; ++I) for (int J = I; J < 6; ++J) Gb[sidx(I, J)] = 0.5 * (Gl[I][J] + Gl[J][I]);
+    PointArrays A{};
+    A.nrm = nrm.data(); A.ns = 1;
+    AdjWork Wk;
+    Wk.H = nullptr; Wk.hs = 1; Wk.mu = mu.data(); Wk.xi = xi.data(); Wk.gab = gab.data();
+    Wk.direct = direct.data(); Wk.ws = 1;
+    tangent_adjoint_pass(t, tr.cmp, f, 1, A, Gb, Cst.data(), Wk);
+    if (tr.cmp) adjoint_weights_c(t, t.wl, t.wsum, Wk, gw.data(), 1);
+    else adjoint_weights(t, t.wl, t.wsum, Wk, gw.data(), 1);
+    for (int node = 0; node < N; ++node) {
+      const int lvl = 32 - __builtin_clz(node + 1);
+      const int j = tr.cmp ? t.pidx[node] : L - 3 * (1 << (lvl - 1)) + node + 1;
+      for (int m = 0; m < M; ++m) { gp[j * M + m] += gab[node] * f[m]; gq[j * M + m] += gab[N + node] * f[m]; }
+    }
+    for (int l = 0; l < L; ++l) gwt[l] += gw[l];
+  }
+  fwrite(gp.data(), 8, Nfull * M, out); fwrite(gq.data(), 8, Nfull * M, out); fwrite(gwt.data(), 8, L, out);
+  return 0;
+}
+
 int main(int argc, char** argv) {
   FILE* in = argc == 3 ? fopen(argv[1], "rb") : nullptr;
   FILE* out = argc == 3 ? fopen(argv[2], "wb") : nullptr;
@@ -378,9 +435,10 @@ int main(int argc, char** argv) {
   const int K = (int)hdr[0], M = (int)hdr[1], mode = (int)hdr[3], max_iter = (int)hdr[4];
   const long n = (long)hdr[2];
   // mode: 0 FP64, 1 mixed with the FP32 tangent, 2 mixed with the FP64 final sweep, 3 adjoint (FP64),
-  //       4 FP64 with the line search
+  //       4 FP64 with the line search, 5 adjoint of the tangent (elastic phases)
   const int rc = mode == 0 || mode == 4 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false, mode == 4)
                : mode == 3 ? run_grad(in, out, K, M, n)
+               : mode == 5 ? run_grad_tangent(in, out, K, M, n)
                            : run<float>(in, out, K, M, n, max_iter, hdr[5], mode == 2, false);
   fclose(in); fclose(out);
   return rc;
@@ -429,12 +487,18 @@ def rel(a, b):
     return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
 
 
+PHASE_SETS = {"linear": (W.FIBER, W.MATRIX), "explin": (W.FIBER, W.MATRIX_EXPLIN),
+              # both leaves of every bottom laminate inelastic, and the inelastic leaf on the left
+              "both-inelastic": (W.MATRIX, W.MATRIX_EXPLIN), "inelastic-left": (W.MATRIX, W.FIBER)}
+
+
 @pytest.mark.parametrize("K,M,matrix,prec", [(4, 3, "linear", 0), (6, 3, "explin", 0), (5, 6, "linear", 0),
-                                             (6, 3, "linear", 1), (6, 3, "explin", 2)])
+                                             (6, 3, "linear", 1), (6, 3, "explin", 2), (5, 3, "both-inelastic", 0),
+                                             (5, 3, "inelastic-left", 0), (5, 3, "both-inelastic", 1)])
 def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
-    mat = W.MATRIX if matrix == "linear" else W.MATRIX_EXPLIN
-    tree = (W.tree_d10_fit(K, seed=30 + K, phases=(W.FIBER, mat)) if M == 3
-            else W.tree_nodal_angles(K, M, seed=30 + K, phases=(W.FIBER, mat)))
+    phases = PHASE_SETS[matrix]
+    tree = (W.tree_d10_fit(K, seed=30 + K, phases=phases) if M == 3
+            else W.tree_nodal_angles(K, M, seed=30 + K, phases=phases))
     n = 24
     A2, lam, Q = W.orientation_field(n, seed=40 + K)
     Ef = W.random6_path_final(n, 0.03, seed=50 + K)
@@ -585,3 +649,37 @@ def test_device_adjoint_of_a_compressed_tree(harness):
         assert err < 1e-9, (k, err)
     assert (gw[np.asarray(tree.w) == 0] == 0).all()
     np.testing.assert_allclose(gE, np.einsum("nij,nj->ni", C, g), rtol=1e-9, atol=1e-9 * np.abs(gE).max())
+
+
+@pytest.mark.parametrize("K,compressed", [(3, False), (5, False), (4, True), (6, True)])
+def test_device_tangent_adjoint_matches_the_oracle(harness, K, compressed):
+    """The tangent-seed adjoint (reverse pass through the laminate recursion of a tree of elastic
+    phases, heap and table traversal) against the oracle's dual-number gradient of G : C."""
+    ph = (W.FIBER, W.Phase(0, 3000.0, 0.35))
+    base = W.tree_with_zero_weights(K, seed=110 + K) if compressed else W.tree_d10_fit(K, seed=110 + K)
+    tree = W.TreeParams(K, base.M, base.p, base.q, base.w, ph)
+    n = 3
+    A2, lam, Q = W.orientation_field(n, seed=111 + K)
+    G = np.random.default_rng(112 + K).standard_normal((n, 36))
+    exe, d = harness
+    hdr = np.array([K, tree.M, n, 5, 0, 0.0], dtype=np.float64)
+    blob = np.concatenate([hdr, np.ravel(tree.p), np.ravel(tree.q), np.ravel(tree.w),
+                           oracle.phases_array(tree.phases).ravel(), lam.ravel(), Q.ravel(), G.ravel()])
+    fin, fout = d / "gt_in.bin", d / "gt_out.bin"
+    blob.astype(np.float64).tofile(fin)
+    subprocess.check_call([exe, str(fin), str(fout)])
+    r = np.fromfile(fout, dtype=np.float64)
+    N, M, L = (1 << K) - 1, tree.M, 1 << K
+    got = dict(p=r[:N * M].reshape(N, M), q=r[N * M:2 * N * M].reshape(N, M), w=r[2 * N * M:2 * N * M + L])
+    S = oracle.state_size(K, tree.phases, tree.w)
+    ref = dict(p=0.0, q=0.0, w=0.0)
+    for i in range(n):
+        gi = oracle.gradient_ift(tree, lam[i], Q[i], np.zeros(6), np.zeros(S), np.zeros((L, 7)), np.zeros(6),
+                                 G_glob=G[i].reshape(6, 6))
+        for k in ref:
+            ref[k] = ref[k] + gi[k]
+    for k in ref:
+        err = np.abs(got[k] - ref[k]).max() / np.abs(ref[k]).max()
+        assert err < 1e-10, (k, err)
+    if compressed:
+        assert (got["w"][np.asarray(tree.w) == 0] == 0).all()

@@ -32,3 +32,26 @@ def test_autotune_picks_a_candidate_and_caches_it(tmp_path, monkeypatch):
     b = dmn.DMN(tree, precision="f64", block=64, ctas_per_sm=6).update(d(lam), d(Q), d(En), d(dE), st)
     for k in a:
         assert torch.equal(a[k], b[k]), k
+
+
+def test_autotune_of_a_handle_with_several_trees(tmp_path, monkeypatch):
+    """The mixed-depth batch (trees of depths 5 to 8 in one handle, points selected by tree_id):
+    the tuner times the candidates on that handle and caches them under the handle's own key,
+    apart from any single tree's."""
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
+    n = 8192
+    depths = (5, 6, 7, 8)
+    trees = [W.tree_d10_fit(K, seed=40 + K) for K in depths]
+    tid, elastic = W.mixed_depth_batch(n, 41, depths)
+    A2, lam, Q = W.orientation_field(n, seed=42)
+    Ef = W.random6_path_final(n, 0.02, seed=43)
+    En, dE = W.proportional_increment(Ef, 3, 10)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+    m = dmn.DMN(trees)
+    st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+    m.close()
+    cands = ((128, 2), (64, 6))
+    res = autotune.tune(trees, "f64", d(lam), d(Q), d(En), d(dE), st, reps=1, candidates=cands, tree_id=d(tid))
+    assert (res["block"], res["ctas_per_sm"]) in cands and len(res["table"]) == 2
+    assert autotune.cached(trees, "f64", DEV) == (res["block"], res["ctas_per_sm"])
+    assert autotune.cached(trees[0], "f64", DEV) is None

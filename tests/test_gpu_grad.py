@@ -174,3 +174,104 @@ def test_training_loss_through_autograd_depth8():
             Lm = loss(d(base.p - h * dp), d(base.q - h * dq), d(base.w - h * dw)).item()
         fd = (Lp - Lm) / (2 * h)
         assert abs(pred - fd) <= 1e-5 * abs(fd), (trial, pred, fd)
+
+
+def _elastic(tree):
+    return W.TreeParams(tree.K, tree.M, tree.p, tree.q, tree.w, (W.FIBER, EL_MATRIX))
+
+
+@pytest.mark.parametrize("K,compressed", [(3, False), (5, False), (6, False), (5, True), (6, True)])
+def test_tangent_seed_adjoint_matches_the_exact_oracle_gradient(K, compressed):
+    """dmn_grad with g_tangent on a tree of elastic phases (the linear DMN of the offline
+    training, Sec. 3.1): the reverse pass through the laminate recursion against the oracle's
+    dual-number gradient of G : C, summed over the points, to 1e-9; full and compressed trees."""
+    base = W.tree_with_zero_weights(K, seed=90 + K) if compressed else W.tree_d10_fit(K, seed=90 + K)
+    tree = _elastic(base)
+    n = 4
+    A2, lam, Q = W.orientation_field(n, seed=91 + K)
+    G = np.random.default_rng(92 + K).standard_normal((n, 6, 6))
+    m = dmn.DMN(tree)
+    g_p, g_q, g_w, g_E = m.grad(d(lam), d(Q), None, None, None, None, None, g_tangent=d(G.reshape(n, 36)))
+    assert np.abs(g_E.cpu().numpy()).max() == 0.0
+    S = oracle.state_size(K, tree.phases, tree.w)
+    nz = 0
+    a0 = np.zeros(S)                      # the solution at zero strain: no jumps
+    z = np.zeros((1 << K, 7))
+    tot = dict(p=0.0, q=0.0, w=0.0)
+    for i in range(n):
+        gi = oracle.gradient_ift(tree, lam[i], Q[i], np.zeros(6), a0[6 * nz:], z, np.zeros(6), G_glob=G[i])
+        for k in tot:
+            tot[k] = tot[k] + gi[k]
+    for k, gg in (("p", g_p), ("q", g_q), ("w", g_w)):
+        ref = tot[k]
+        err = np.abs(gg.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err < 1e-9, (k, err)
+    if compressed:
+        assert (g_w.cpu().numpy()[tree.w == 0] == 0).all()
+    m.close()
+
+
+def test_tangent_seed_at_depth8_matches_oracle_directional_derivatives():
+    K, n = 8, 3
+    tree = _elastic(W.tree_d10_fit(K, seed=95))
+    A2, lam, Q = W.orientation_field(n, seed=96)
+    rng = np.random.default_rng(97)
+    G = rng.standard_normal((n, 6, 6))
+    m = dmn.DMN(tree)
+    g_p, g_q, g_w, _ = m.grad(d(lam), d(Q), None, None, None, None, None, g_tangent=d(G.reshape(n, 36)))
+    dirs = [(rng.standard_normal(tree.p.shape), rng.standard_normal(tree.q.shape),
+             rng.standard_normal(tree.w.shape) * tree.w) for _ in range(2)]
+    ref = np.zeros(len(dirs))
+    for i in range(n):
+        ref += np.asarray(oracle.gradient_ift(tree, lam[i], Q[i], np.zeros(6), np.zeros(3 * 255),
+                                              np.zeros((256, 7)), np.zeros(6), directions=dirs, G_glob=G[i]))
+    pred = np.array([(g_p.cpu().numpy() * dp).sum() + (g_q.cpu().numpy() * dq).sum() + (g_w.cpu().numpy() * dw).sum()
+                     for dp, dq, dw in dirs])
+    assert np.abs(pred - ref).max() <= 1e-9 * np.abs(ref).max(), (pred, ref)
+    m.close()
+
+
+def test_stress_and_tangent_seeds_add_and_the_stiffness_paths_agree():
+    """Both seeds in one call give the sum of the two calls; dmn_stiffness through the tangent
+    (one update, one tangent adjoint per sample) equals the six-stress path in value and gradient."""
+    K, n = 5, 8
+    tree = _elastic(W.tree_d10_fit(K, seed=98))
+    A2, lam, Q = W.orientation_field(n, seed=99)
+    rng = np.random.default_rng(100)
+    m = dmn.DMN(tree)
+    E = d(rng.standard_normal((n, 6)) * 1e-3)
+    z = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+    zE = torch.zeros_like(E)
+    out = m.update(d(lam), d(Q), zE, E, z)
+    g, G = d(rng.standard_normal((n, 6))), d(rng.standard_normal((n, 36)))
+    both = m.grad(d(lam), d(Q), zE, E, z, out["state_out"], g, g_tangent=G)
+    s_only = m.grad(d(lam), d(Q), zE, E, z, out["state_out"], g)
+    t_only = m.grad(d(lam), d(Q), None, None, None, None, None, g_tangent=G)
+    for a, b, c in zip(both[:3], s_only[:3], t_only[:3]):
+        np.testing.assert_allclose(a.cpu().numpy(), (b + c).cpu().numpy(), rtol=1e-12,
+                                   atol=1e-12 * np.abs((b + c).cpu().numpy()).max())
+    np.testing.assert_allclose(both[3].cpu().numpy(), s_only[3].cpu().numpy(), rtol=1e-13, atol=0)
+    p, q, w = (d(x).requires_grad_() for x in (tree.p, tree.q, tree.w))
+    Gs = d(rng.standard_normal((n, 6, 6)))
+    grads = []
+    Cs = []
+    for method in ("tangent", "stress"):
+        for x in (p, q, w):
+            x.grad = None
+        C = ag.dmn_stiffness(m, d(lam), d(Q), p, q, w, method=method)
+        (C * Gs).sum().backward()
+        Cs.append(C.detach().cpu().numpy())
+        grads.append([x.grad.cpu().numpy().copy() for x in (p, q, w)])
+    np.testing.assert_allclose(Cs[0], Cs[1], rtol=0, atol=1e-10 * np.abs(Cs[1]).max())
+    for a, b in zip(*grads):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-8 * np.abs(b).max())
+    m.close()
+
+
+def test_tangent_seed_needs_elastic_phases():
+    tree = W.tree_d10_fit(3, seed=101)
+    m = dmn.DMN(tree)
+    A2, lam, Q = W.orientation_field(2, seed=102)
+    with pytest.raises(RuntimeError, match="elastic phases"):
+        m.grad(d(lam), d(Q), None, None, None, None, None, g_tangent=d(np.ones((2, 36))))
+    m.close()

@@ -5,8 +5,9 @@ arena, or that may not call cudaMalloc after start-up) get an entry point whose
 work space is a fixed static device array inside the library.  This test calls
 it through the C ABI twice in a row -- the second call continuing from the
 first call's state -- and checks each result against dmn_update on the same
-inputs.  It lives in its own file, collected last, and passes alone or after
-the other tests.
+inputs, and sampled points against the CPU oracle run along the same history.
+It lives in its own file, collected last, and passes alone or after the other
+tests.
 """
 import ctypes
 
@@ -14,6 +15,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2103_08253_gb300 import dmn, workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -63,6 +65,12 @@ def test_noalloc_update_matches_dmn_update_on_two_calls_in_a_row():
         st_ref = m.update(lam_d, Q_d, torch.from_numpy(En).to(DEV), torch.from_numpy(dE).to(DEV), st_ref)["state_out"]
     st_na = st_ref.clone()
     stream = torch.cuda.current_stream(DEV).cuda_stream
+    # the oracle along the same history, on its own states, for a sample of the points
+    pidx = np.random.default_rng(126).choice(n, 12, replace=False)
+    st_o = np.zeros((S, pidx.size))
+    for step in range(1, 10):
+        En, dE = W.proportional_increment(Ef, step, 12)
+        st_o = oracle.update(tree, lam[pidx], Q[pidx], En[pidx], dE[pidx], st_o)[0]
     for step in (10, 11):                      # two consecutive calls, each continuing from its own last state
         En, dE = W.proportional_increment(Ef, step, 12)
         En_d, dE_d = torch.from_numpy(En).to(DEV), torch.from_numpy(dE).to(DEV)
@@ -83,6 +91,11 @@ def test_noalloc_update_matches_dmn_update_on_two_calls_in_a_row():
         so, sr = out["state_out"][:, okd], ref["state_out"][:, okd]
         scale = sr.abs().amax(dim=1, keepdim=True) + 1e-300
         assert ((so - sr).abs() / scale).max().item() <= 1e-9
+        st_o, sig_o, C_o, it_o, stat_o, _ = oracle.update(tree, lam[pidx], Q[pidx], En[pidx], dE[pidx], st_o)
+        keep_o = (stat_o == 0) & ok[pidx]
+        assert keep_o.sum() >= 10
+        assert _rel(out["stress"].cpu().numpy()[pidx][keep_o], sig_o[keep_o]) <= 1e-10
+        assert _rel(out["tangent"].cpu().numpy()[pidx][keep_o], C_o[keep_o]) <= 1e-10
         st_ref, st_na = ref["state_out"], out["state_out"]
     m.close()
 
