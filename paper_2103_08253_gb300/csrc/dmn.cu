@@ -122,6 +122,7 @@ TreeDev tree_dev(const Tree& t) {
   d.post = t.d_tab ? t.d_tab + 4 * t.Lc + t.N : nullptr;
   d.pidx = t.d_tab ? t.d_tab + 4 * t.Lc + 2 * t.N : nullptr;
   d.kid = t.d_tab ? t.d_tab + 4 * t.Lc + 3 * t.N : nullptr;
+  d.hcid = t.d_tab ? t.d_tab + 4 * t.Lc + 5 * t.N : nullptr;
   return d;
 }
 
@@ -257,7 +258,9 @@ __global__ void k_interp(int64_t n, const double* __restrict__ A2, double* __res
 // PI (1/2,1/2), i.e. phi = (lam1 - lam2, 3 lam3, 2 lam1 + 4 lam2 - 2); shape
 // functions of order M; alpha = p.phi, beta = q.phi;
 // n = (sin a cos b, sin a sin b, cos a).  Written to strided storage.
-__device__ void point_normals(const TreeDev& t, double l1, double l2, double* out, size_t stride) {
+// normals of the laminates first, first + step, ... (all of them by default)
+__device__ void point_normals(const TreeDev& t, double l1, double l2, double* out, size_t stride, int first = 0,
+                              int step = 1) {
   const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
   double ph[6];
   if (t.M == 3) {
@@ -269,7 +272,7 @@ __device__ void point_normals(const TreeDev& t, double l1, double l2, double* ou
     ph[0] = v[0] * (2.0 * v[0] - 1.0); ph[1] = v[1] * (2.0 * v[1] - 1.0); ph[2] = v[2] * (2.0 * v[2] - 1.0);
     ph[3] = 4.0 * v[0] * v[1]; ph[4] = 4.0 * v[0] * v[2]; ph[5] = 4.0 * v[1] * v[2];
   }
-  for (int j = 0; j < t.N; ++j) {
+  for (int j = first; j < t.N; j += step) {
     double al = 0.0, be = 0.0;
     for (int m = 0; m < t.M; ++m) {
       al += __ldg(t.p + j * t.M + m) * ph[m];
@@ -694,6 +697,8 @@ struct GradParams {
 
 // work fields per point
 __host__ __device__ inline size_t grad_fields(int N, int L) { return (size_t)33 * N + 2 * L + 6; }
+// with tangent seeds: one more field block, every laminate's stiffness adjoint [21 N]
+__host__ __device__ inline size_t grad_fields_tangent(int N, int L) { return grad_fields(N, L) + (size_t)21 * N; }
 
 // CMP: the tree is walked by its compressed-traversal tables.
 template <bool CMP>
@@ -823,11 +828,14 @@ __global__ void __launch_bounds__(256) k_grad_reduce(TreeDev t, int64_t nc, cons
   if (threadIdx.x == 0) *out += red[0];
 }
 
-// Tangent seeds (trees of elastic phases): one thread per point of a chunk, in the work
-// layout of k_grad.  After k_grad (stress seeds) the normals and shape-function values are
-// in the work array and the tangent's terms are added; alone (init) the kernel computes
-// them and starts the per-laminate and per-leaf terms at zero.  The weight gradient is
-// then (re)assembled from all terms.
+// Tangent seeds (trees of elastic phases): one warp per point of a chunk, in the work layout
+// of k_grad plus the stiffness adjoints (grad_fields_tangent).  The lanes share each level of
+// the tree (tangent_level_fwd / _rev), with a warp barrier between levels: the batches of the
+// offline training (a few thousand samples) then keep the GPU's FP64 pipes busy, where one
+// thread per point left most of them idle.  After k_grad (stress seeds) the normals and
+// shape-function values are in the work array and the tangent's terms are added; alone (init)
+// the kernel computes them and starts the per-laminate and per-leaf terms at zero.  The weight
+// gradient is then (re)assembled from all terms by lane 0.
 struct GradTParams {
   TreeDev t;
   int64_t n, n0, nc;
@@ -839,15 +847,17 @@ struct GradTParams {
 
 template <bool CMP>
 __global__ void __launch_bounds__(128) k_grad_tangent(GradTParams P) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= P.nc) return;
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;   // this warp's point
+  const int lane = threadIdx.x & 31;
+  if (i >= P.nc) return;   // the whole warp
   const int64_t pt = P.n0 + i;
   const TreeDev& t = P.t;
   const int N = t.N, L = t.L;
   const size_t ws = (size_t)P.nc;
   double* w = P.work + i;
   double* nrm = w;
-  double* Cst = w + (size_t)(6 * N) * ws;      // the g, H field of k_grad: every laminate's tangent
+  double* Cst = w + (size_t)(6 * N) * ws;                       // the g, H field of k_grad: stiffnesses
+  double* Gst = w + grad_fields(N, L) * ws;                     // stiffness adjoints
   AdjWork Wk;
   Wk.H = nullptr; Wk.hs = ws;
   Wk.mu = w + (size_t)(27 * N) * ws;
@@ -859,61 +869,64 @@ __global__ void __launch_bounds__(128) k_grad_tangent(GradTParams P) {
   double* phv = w + (size_t)(33 * N + 2 * L) * ws;   // shape-function values (k_grad writes them too)
   if (P.init) {
     const double l1 = P.lam[2 * pt], l2 = P.lam[2 * pt + 1];
-    point_normals(t, l1, l2, nrm, ws);
-    double ph[6];
-    const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
-#pragma unroll
-    for (int m = 0; m < 6; ++m) ph[m] = 0.0;
-    if (t.M == 3) {
-      ph[0] = v[0]; ph[1] = v[1]; ph[2] = v[2];
-    } else if (t.M == 4) {
-      const double b = v[0] * v[1] * v[2];
-      ph[0] = v[0] - 9.0 * b; ph[1] = v[1] - 9.0 * b; ph[2] = v[2] - 9.0 * b; ph[3] = 27.0 * b;
-    } else {
-      ph[0] = v[0] * (2.0 * v[0] - 1.0); ph[1] = v[1] * (2.0 * v[1] - 1.0); ph[2] = v[2] * (2.0 * v[2] - 1.0);
-      ph[3] = 4.0 * v[0] * v[1]; ph[4] = 4.0 * v[0] * v[2]; ph[5] = 4.0 * v[1] * v[2];
+    point_normals(t, l1, l2, nrm, ws, lane, 32);
+    if (lane == 0) {
+      const double v[3] = {l1 - l2, 3.0 * (1.0 - l1 - l2), 2.0 * l1 + 4.0 * l2 - 2.0};
+      double ph[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      if (t.M == 3) {
+        ph[0] = v[0]; ph[1] = v[1]; ph[2] = v[2];
+      } else if (t.M == 4) {
+        const double b = v[0] * v[1] * v[2];
+        ph[0] = v[0] - 9.0 * b; ph[1] = v[1] - 9.0 * b; ph[2] = v[2] - 9.0 * b; ph[3] = 27.0 * b;
+      } else {
+        ph[0] = v[0] * (2.0 * v[0] - 1.0); ph[1] = v[1] * (2.0 * v[1] - 1.0); ph[2] = v[2] * (2.0 * v[2] - 1.0);
+        ph[3] = 4.0 * v[0] * v[1]; ph[4] = 4.0 * v[0] * v[2]; ph[5] = 4.0 * v[1] * v[2];
+      }
+      for (int m = 0; m < 6; ++m) phv[(size_t)m * ws] = ph[m];
+      if (P.g_E)   // the tangent of elastic phases does not depend on the macro strain
+        for (int I = 0; I < 6; ++I) P.g_E[6 * pt + I] = 0.0;
     }
-    for (int m = 0; m < 6; ++m) phv[(size_t)m * ws] = ph[m];
-    for (int k = 0; k < 2 * N; ++k) Wk.gab[(size_t)k * ws] = 0.0;
-    for (int k = 0; k < N; ++k) Wk.xi[(size_t)k * ws] = 0.0;
-    for (int l = 0; l < L; ++l) Wk.direct[(size_t)l * ws] = 0.0;
-    if (P.g_E)   // the tangent of elastic phases does not depend on the macro strain
-      for (int I = 0; I < 6; ++I) P.g_E[6 * pt + I] = 0.0;
+    for (int k = lane; k < 2 * N; k += 32) Wk.gab[(size_t)k * ws] = 0.0;
+    for (int k = lane; k < N; k += 32) Wk.xi[(size_t)k * ws] = 0.0;
+    for (int l = lane; l < L; l += 32) Wk.direct[(size_t)l * ws] = 0.0;
   }
-  // the seed in the local frame: C_glob = R C_loc R^T  =>  Gb_loc = R^T G R, symmetrised
-  double R[6][6];
-  mandel_rotation(P.Q + 9 * pt, R);
-  const double* G = P.g_tangent + 36 * pt;
-  double RG[6][6];
-#pragma unroll
-  for (int P2 = 0; P2 < 6; ++P2)
-#pragma unroll
-    for (int J = 0; J < 6; ++J) {
-      double v = 0.0;
-#pragma unroll
-      for (int I = 0; I < 6; ++I) v += R[I][P2] * G[6 * I + J];
-      RG[P2][J] = v;
-    }
-  double Gl[6][6];
-#pragma unroll
-  for (int P2 = 0; P2 < 6; ++P2)
-#pragma unroll
-    for (int Q2 = 0; Q2 < 6; ++Q2) {
-      double v = 0.0;
-#pragma unroll
-      for (int J = 0; J < 6; ++J) v += RG[P2][J] * R[J][Q2];
-      Gl[P2][Q2] = v;
-    }
-  double Gb[21];
-#pragma unroll
-  for (int I = 0; I < 6; ++I)
-#pragma unroll
-    for (int J = I; J < 6; ++J) Gb[sidx(I, J)] = 0.5 * (Gl[I][J] + Gl[J][I]);
+  if (lane == 0) {
+    // the seed in the local frame: C_glob = R C_loc R^T  =>  Gb_loc = R^T G R, symmetrised
+    double R[6][6];
+    mandel_rotation(P.Q + 9 * pt, R);
+    const double* G = P.g_tangent + 36 * pt;
+    double RG[6][6];
+    for (int P2 = 0; P2 < 6; ++P2)
+      for (int J = 0; J < 6; ++J) {
+        double v = 0.0;
+        for (int I = 0; I < 6; ++I) v += R[I][P2] * G[6 * I + J];
+        RG[P2][J] = v;
+      }
+    const int root = tangent_root(t, CMP);
+    for (int I = 0; I < 6; ++I)
+      for (int J = I; J < 6; ++J) {
+        double a = 0.0, b = 0.0;
+        for (int K2 = 0; K2 < 6; ++K2) { a += RG[I][K2] * R[K2][J]; b += RG[J][K2] * R[K2][I]; }
+        Gst[(size_t)(21 * root + sidx(I, J)) * ws] = 0.5 * (a + b);
+      }
+  }
+  double Cph[2][21];
+  phase_stiffnesses(t, Cph);
   PointArrays A{};
   A.nrm = nrm; A.ns = ws;
-  tangent_adjoint_pass(t, CMP, phv, ws, A, Gb, Cst, Wk);
-  if (CMP) adjoint_weights_c(t, t.wl, t.wsum, Wk, gw, ws);
-  else adjoint_weights(t, t.wl, t.wsum, Wk, gw, ws);
+  __syncwarp();
+  for (int lvl = t.K; lvl >= 1; --lvl) {
+    tangent_level_fwd(t, CMP, lvl, lane, 32, A, Cph, Cst, ws);
+    __syncwarp();
+  }
+  for (int lvl = 1; lvl <= t.K; ++lvl) {
+    tangent_level_rev(t, CMP, lvl, lane, 32, phv, ws, A, Cph, Cst, Gst, Wk);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (CMP) adjoint_weights_c(t, t.wl, t.wsum, Wk, gw, ws);
+    else adjoint_weights(t, t.wl, t.wsum, Wk, gw, ws);
+  }
 }
 
 int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -956,7 +969,8 @@ struct CmpTree {
   int N = 0, Lc = 0, nz = 0;
   std::vector<double> p, q, c;   // p, q [N][M]; c = c1 [N], c2 [N], sc [N], leaf weights [L]
   std::vector<float> cf;         // c1f [N], c2f [N], c12f [N]
-  std::vector<int> tab;          // lf [Lc] (4 ints each), pre [N], post [N], paper index [N], children [2 N]
+  std::vector<int> tab;          // lf [Lc] (4 ints each), pre [N], post [N], paper index [N], children [2 N],
+                                 // the laminate at each heap position [2^K - 1]
 };
 
 void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& B) {
@@ -1036,6 +1050,7 @@ void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& 
   for (int h = 1; h <= N; ++h)
     if (cid[h] >= 0) { kids[2 * cid[h]] = stand_in(2 * h); kids[2 * cid[h] + 1] = stand_in(2 * h + 1); }
   B.tab.insert(B.tab.end(), kids.begin(), kids.end());
+  for (int h = 1; h <= N; ++h) B.tab.push_back(cid[h]);   // heap position h - 1: its laminate or -1
 }
 
 bool has_zero_weight(const dmn_tree_desc& d) {
@@ -1592,14 +1607,15 @@ int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam
     return fail(h, DMN_ERR_ARG, "dmn_grad: NULL array");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t chunk = std::min<int64_t>(n, 65536);   // few points per chunk leave the adjoint latency-bound
-  const size_t fields = grad_fields(T.N, T.L);
+  const size_t fields = g_tangent ? grad_fields_tangent(T.N, T.L) : grad_fields(T.N, T.L);
+  const int64_t need = (int64_t)(fields * (size_t)chunk);   // doubles
   cudaError_t e;
-  if (chunk > h->gwork_cap) {
+  if (need > h->gwork_cap) {
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) { cudaFree(h->gwork); h->gwork = nullptr; h->gwork_cap = 0; }
-    if (e == cudaSuccess) e = cudaMalloc(&h->gwork, sizeof(double) * fields * chunk);
+    if (e == cudaSuccess) e = cudaMalloc(&h->gwork, sizeof(double) * (size_t)need);
     if (e != cudaSuccess) return cuda_fail(h, e, "dmn_grad: work buffer");
-    h->gwork_cap = chunk;
+    h->gwork_cap = need;
   }
   const int n_params = 2 * T.N * T.M + T.L;
   for (int64_t n0 = 0; n0 < n; n0 += chunk) {
@@ -1612,8 +1628,9 @@ int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam
     }
     if (g_tangent) {
       GradTParams P{td, n, n0, nc, lam, Q, g_tangent, g_E, h->gwork, g_stress ? 0 : 1};
-      if (h->cmp) k_grad_tangent<true><<<grid, 128, 0, s>>>(P);
-      else k_grad_tangent<false><<<grid, 128, 0, s>>>(P);
+      const unsigned wgrid = (unsigned)div_up(32 * nc, 128);   // a warp per point
+      if (h->cmp) k_grad_tangent<true><<<wgrid, 128, 0, s>>>(P);
+      else k_grad_tangent<false><<<wgrid, 128, 0, s>>>(P);
     }
     k_grad_reduce<<<n_params, 256, 0, s>>>(td, nc, h->gwork, g_p, g_q, g_w);
   }

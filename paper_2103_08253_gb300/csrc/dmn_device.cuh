@@ -73,6 +73,7 @@ struct TreeDev {
   const int* post;   // [N] laminates in completion (post-) order
   const int* pidx;   // [N] the paper's index of each laminate (in the uncompressed tree)
   const int* kid;    // [2 N] children of each laminate: >= 0 a laminate, -1 - phase a leaf
+  const int* hcid;   // [2^K - 1] the laminate standing at each heap position, -1 for none (compressed trees)
 };
 
 // fields of TreeDev::lf .w
@@ -1540,15 +1541,18 @@ __device__ __forceinline__ void lam_kids(const TreeDev& t, bool cmp, int node, i
   }
 }
 
-// Per point: the tangent's adjoint for the seed Gb_root (local frame, symmetric, packed),
-// added to the per-laminate angle gradients and weight terms of AdjWork.  Cst [21 N]
-// (stride Wk.ws) receives every laminate's tangent.  ph: the point's shape-function values,
-// ph[m * phs] (the work array's copy in the kernel).
-__device__ void tangent_adjoint_pass(const TreeDev& t, bool cmp, const double* ph, size_t phs, const PointArrays& P,
-                                     const double Gb_root[21], double* Cst, const AdjWork& Wk) {
-  const size_t ws = Wk.ws;
-  const int N = t.N;
-  double Cph[2][21];
+// The tangent's adjoint of one point, level by level of the full tree's heap positions, so
+// that the lanes of a warp share a level: lane `lane` of `nl` takes every nl-th position of the
+// level (the laminate standing there, if any; compressed trees skip passed-through and dead
+// positions).  A laminate's children stand at deeper positions, so the forward pass (the
+// children's stiffnesses to the laminate's, stored in Cst [21 N]) runs from level K up, and the
+// reverse pass (the laminate's adjoint, read from Gst [21 N], to its children's adjoints, its
+// normal's and its volume fraction's) from the root down; the caller orders the levels (a warp
+// barrier between them).  Cph: the leaf stiffnesses of the two phases; ph[m * phs]: the point's
+// shape-function values; strides Wk.ws.
+__device__ __forceinline__ int heap_to_lam(const TreeDev& t, int h) { return t.hcid ? __ldg(t.hcid + h) : h; }
+
+__device__ __forceinline__ void phase_stiffnesses(const TreeDev& t, double Cph[2][21]) {
 #pragma unroll
   for (int f = 0; f < 2; ++f)
 #pragma unroll
@@ -1556,9 +1560,14 @@ __device__ void tangent_adjoint_pass(const TreeDev& t, bool cmp, const double* p
 #pragma unroll
       for (int J = I; J < 6; ++J)
         Cph[f][sidx(I, J)] = ((I < 3 && J < 3) ? t.ph[f].lam : 0.0) + (I == J ? 2.0 * t.ph[f].G : 0.0);
-  // forward: children before parents (heap: descending index; compressed: the paper's order)
-  for (int x = 0; x < N; ++x) {
-    const int node = cmp ? x : N - 1 - x;
+}
+
+__device__ void tangent_level_fwd(const TreeDev& t, bool cmp, int lvl, int lane, int nl, const PointArrays& P,
+                                  const double Cph[2][21], double* Cst, size_t ws) {
+  const int h0 = (1 << (lvl - 1)) - 1, nh = 1 << (lvl - 1);
+  for (int x = lane; x < nh; x += nl) {
+    const int node = heap_to_lam(t, h0 + x);
+    if (node < 0) continue;
     int k1, k2;
     lam_kids(t, cmp, node, k1, k2);
     double CL[21], CR[21], C[21], nd[3];
@@ -1573,22 +1582,24 @@ __device__ void tangent_adjoint_pass(const TreeDev& t, bool cmp, const double* p
 #pragma unroll
     for (int k = 0; k < 21; ++k) Cst[(size_t)(21 * node + k) * ws] = C[k];
   }
-  // reverse: depth first from the root, pending left subtrees on a stack
-  double stG[KMAX + 1][21];
-  int stN[KMAX + 1];
-  int sp = 0;
-  int node = cmp ? N - 1 : 0;
-  double G[21];
-#pragma unroll
-  for (int k = 0; k < 21; ++k) G[k] = Gb_root[k];
-  for (int guard = 0; guard < N; ++guard) {
+}
+
+__device__ void tangent_level_rev(const TreeDev& t, bool cmp, int lvl, int lane, int nl, const double* ph, size_t phs,
+                                  const PointArrays& P, const double Cph[2][21], const double* Cst, double* Gst,
+                                  const AdjWork& Wk) {
+  const size_t ws = Wk.ws;
+  const int h0 = (1 << (lvl - 1)) - 1, nh = 1 << (lvl - 1);
+  for (int x = lane; x < nh; x += nl) {
+    const int node = heap_to_lam(t, h0 + x);
+    if (node < 0) continue;
     int k1, k2;
     lam_kids(t, cmp, node, k1, k2);
-    double CL[21], CR[21], GL[21], GR[21], nd[3], nb[3], c1b;
+    double CL[21], CR[21], G[21], GL[21], GR[21], nd[3], nb[3], c1b;
 #pragma unroll
     for (int k = 0; k < 21; ++k) {
       CL[k] = k1 >= 0 ? Cst[(size_t)(21 * k1 + k) * ws] : Cph[-1 - k1][k];
       CR[k] = k2 >= 0 ? Cst[(size_t)(21 * k2 + k) * ws] : Cph[-1 - k2][k];
+      G[k] = Gst[(size_t)(21 * node + k) * ws];
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) nd[c] = P.nrm[(3 * node + c) * P.ns];
@@ -1599,32 +1610,20 @@ __device__ void tangent_adjoint_pass(const TreeDev& t, bool cmp, const double* p
     sincos(al, &sa, &ca);
     sincos(be, &sbeta, &cbeta);
     Wk.gab[(size_t)node * ws] += nb[0] * ca * cbeta + nb[1] * ca * sbeta - nb[2] * sa;
-    Wk.gab[(size_t)(N + node) * ws] += -nb[0] * sa * sbeta + nb[1] * sa * cbeta;
+    Wk.gab[(size_t)(t.N + node) * ws] += -nb[0] * sa * sbeta + nb[1] * sa * cbeta;
     const double W = __ldg(t.sc + node) / (c1 * c2);
     Wk.xi[(size_t)node * ws] += c1b / (W * W);   // c1 = W_L / W: d/dW_L = W_R Xi, d/dW_R = -W_L Xi
-    if (k2 >= 0) {
-      if (k1 >= 0 && sp <= KMAX) {
+    if (k1 >= 0)
 #pragma unroll
-        for (int k = 0; k < 21; ++k) stG[sp][k] = GL[k];
-        stN[sp++] = k1;
-      }
-      node = k2;
+      for (int k = 0; k < 21; ++k) Gst[(size_t)(21 * k1 + k) * ws] = GL[k];
+    if (k2 >= 0)
 #pragma unroll
-      for (int k = 0; k < 21; ++k) G[k] = GR[k];
-    } else if (k1 >= 0) {
-      node = k1;
-#pragma unroll
-      for (int k = 0; k < 21; ++k) G[k] = GL[k];
-    } else if (sp > 0) {
-      --sp;
-      node = stN[sp];
-#pragma unroll
-      for (int k = 0; k < 21; ++k) G[k] = stG[sp][k];
-    } else {
-      break;
-    }
+      for (int k = 0; k < 21; ++k) Gst[(size_t)(21 * k2 + k) * ws] = GR[k];
   }
 }
+
+// the laminate at the root: the whole tree's root, or the topmost one kept by compression
+__device__ __forceinline__ int tangent_root(const TreeDev& t, bool cmp) { return cmp ? t.N - 1 : 0; }
 
 // ---------------------------------------------------------------------------
 // Mandel rotation R_IJ = (w_I w_J / 2)(Q_ia Q_jb + Q_ib Q_ja) for index pairs

@@ -192,10 +192,12 @@ struct Tree {
       }
     }
     tab.insert(tab.end(), kid.begin(), kid.end());
+    for (int h = 1; h <= N; ++h) tab.push_back(cid[h]);   // the laminate at each heap position, or -1
     N = Nc;
     t.N = Nc; t.Lc = Lc; t.nz = nz; t.z_both = 0;
     t.lf = reinterpret_cast<const int4*>(tab.data());
     t.pre = tab.data() + 4 * Lc; t.post = t.pre + Nc; t.pidx = t.post + Nc; t.kid = t.pidx + Nc;
+    t.hcid = t.kid + 2 * Nc;
     t.p = hp.data(); t.q = hq.data();
     t.c1 = c.data(); t.c2 = c.data() + Nc; t.sc = c.data() + 2 * Nc; t.wl = c.data() + 3 * Nc;
     t.c1f = cf.data(); t.c2f = cf.data() + Nc; t.c12f = cf.data() + 2 * Nc;
@@ -391,7 +393,9 @@ static int run_grad_tangent(FILE* in, FILE* out, int K, int M, long n) {
   rd(lam.data(), 2 * n, in); rd(Q.data(), 9 * n, in); rd(G.data(), 36 * n, in);
   const int Nfull = L - 1;
   std::vector<double> gp(Nfull * M, 0.0), gq(Nfull * M, 0.0), gwt(L, 0.0);
-  std::vector<double> nrm(3 * N), Cst(21 * N), mu(3 * N), xi(N), gab(2 * N), direct(L), gw(L);
+  std::vector<double> nrm(3 * N), Cst(21 * N), Gst(21 * N), mu(3 * N), xi(N), gab(2 * N), direct(L), gw(L);
+  double Cph[2][21];
+  phase_stiffnesses(t, Cph);
   const double zero6[6] = {0, 0, 0, 0, 0, 0};
   for (long pt = 0; pt < n; ++pt) {
     double f[6], R[6][6], Eloc[6];
@@ -412,7 +416,14 @@ static int run_grad_tangent(FILE* in, FILE* out, int K, int M, long n) {
     AdjWork Wk;
     Wk.H = nullptr; Wk.hs = 1; Wk.mu = mu.data(); Wk.xi = xi.data(); Wk.gab = gab.data();
     Wk.direct = direct.data(); Wk.ws = 1;
-    tangent_adjoint_pass(t, tr.cmp, f, 1, A, Gb, Cst.data(), Wk);
+    // the level-synchronous passes of a warp, its 32 lanes taken one after another within a level
+    const int root = tangent_root(t, tr.cmp);
+    for (int k = 0; k < 21; ++k) Gst[21 * root + k] = Gb[k];
+    for (int lvl = K; lvl >= 1; --lvl)
+      for (int lane = 0; lane < 32; ++lane) tangent_level_fwd(t, tr.cmp, lvl, lane, 32, A, Cph, Cst.data(), 1);
+    for (int lvl = 1; lvl <= K; ++lvl)
+      for (int lane = 0; lane < 32; ++lane)
+        tangent_level_rev(t, tr.cmp, lvl, lane, 32, f, 1, A, Cph, Cst.data(), Gst.data(), Wk);
     if (tr.cmp) adjoint_weights_c(t, t.wl, t.wsum, Wk, gw.data(), 1);
     else adjoint_weights(t, t.wl, t.wsum, Wk, gw.data(), 1);
     for (int node = 0; node < N; ++node) {
