@@ -326,11 +326,18 @@ def rel_rows(a, b):
 
 
 def form_opts(form):
-    """(precision, extrapolated start) of a form name such as "f64" or "mixed-f32-tangent/extrap"."""
+    """(precision, extrapolated start) of a form name such as "f64", "mixed-f32-tangent/extrap" or
+    "mixed/no-stage" (the mixed iteration without its all-FP32 first stage)."""
     prec, _, start = form.partition("/")
-    if start not in ("", "extrap"):
+    if start not in ("", "extrap", "no-stage"):
         raise ValueError("unknown start in form %r" % form)
     return prec, start == "extrap"
+
+
+def form_stage(form):
+    """Whether the form runs the mixed forms' all-FP32 first stage."""
+    prec, pred = form_opts(form)
+    return prec != "f64" and not pred and not form.endswith("/no-stage")
 
 
 def tune_shape(form, ctx, args):
@@ -369,7 +376,7 @@ def run_form(form, ctx, args, dist):
     shape = tune_shape(form, ctx, args) if args.autotune else None
     prec, pred = form_opts(form)
     m = dmn.DMN(ctx["tree"], precision=prec, block=shape["block"] if shape else 0,
-                ctas_per_sm=shape["ctas_per_sm"] if shape else 0, predictor=pred)
+                ctas_per_sm=shape["ctas_per_sm"] if shape else 0, predictor=pred, first_stage=form_stage(form))
     S = m.state_size
     st = [torch.zeros((S, n), dtype=torch.float64, device=dev), torch.zeros((S, n), dtype=torch.float64, device=dev)]
     lam = torch.empty((n, 2), dtype=torch.float64, device=dev)
@@ -409,11 +416,14 @@ def run_form(form, ctx, args, dist):
     if dist:
         dist.barrier()
     clk = clocks.stop() if clocks else None
-    kms, cnt = m.profile_read()
+    kms, passes, cnt = m.profile_read_stages()
     m.profile(False)
+    if not form_stage(form):
+        kms.pop("stage")
     its = iters_steps.to(torch.int64).sum().item()
     hist = torch.bincount(iters_steps.reshape(-1).to(torch.int64), minlength=1).cpu().numpy()
     res = dict(t_ms=t_ms, kms=kms, updates=cnt, clocks=clk, iters_sum=int(its), iters_hist=hist.tolist(),
+               passes=passes,
                launch=(dict(block=shape["block"], ctas_per_sm=shape["ctas_per_sm"], tuned_on_points=shape["points"],
                             table=shape["table"]) if shape else "defaults"),
                stress=out["stress"], tangent=out["tangent"], status=out["status"], state=st[cur],
@@ -509,23 +519,45 @@ def roofline_f64(r, n, steps, w=None, peaks=None):
             "frac_of_derived_peak": ach / PEAK_F64_GFLOPS, "peak_note": pk["note"]}
 
 
+def stage_flops(K, passes, npts, w=None):
+    """FP32 flops of the all-FP32 first stage over npts points and `passes` tree passes: the Newton
+    pass's FP64 and FP32 parts, and the jump corrections, all in FP32."""
+    f64, ft = pass_flops(K, w, t_is_f64=False)
+    c64, ct = corr_flops(K, w)
+    corr = passes - npts
+    return passes * (f64 + ft) + corr * (c64 + ct)
+
+
 def roofline_mixed(r, n, steps, w=None, sweep=True, peaks=None):
-    """Mixed forms: the Newton kernel against F64/P64 + F32/P32; the final kernel (with the FP64 sweep,
-    or only the state pass and rotation in the form with an FP32 tangent) against the FP64 peak."""
+    """Mixed forms: the Newton kernel against F64/P64 + F32/P32; the first stage (all FP32) against the
+    FP32 peak; the final kernel (with the FP64 sweep, or only the state pass and rotation in the form
+    with an FP32 tangent) against the FP64 peak.  Pass counts come from the kernels' counters."""
     pk = peaks or PEAKS_DERIVED
     P64, P32 = pk["f64"], pk["f32"]
-    F64, F32 = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=True, w=w)
+    npts = n * steps
+    passes = r.get("passes") or {}
+    newton_corr = passes["newton"] - npts if passes.get("newton") else r["iters_sum"]
+    F64, F32 = newton_flops(K_DEPTH, newton_corr, npts, mixed=True, w=w)
     t = r["kms"]["newton"] * 1e-3
     tb = F64 / (P64 * 1e9) + F32 / (P32 * 1e9)
     Ff = final_flops(K_DEPTH, n * steps, sweep=sweep, w=w)
     tf = r["kms"]["final"] * 1e-3
     fin = {"kernel": "k_final<sweep>" if sweep else "k_final", "achieved": Ff / tf / 1e9, "peak": P64,
            "unit": "GFLOP/s (FP64)", "frac": Ff / tf / 1e9 / P64, "launch_ms": r["kms"]["final"] / steps}
-    return {"bound": "alu", "kernel": "k_newton<float>", "achieved": tb / t * P64,
-            "peak": P64, "unit": "GFLOP/s (FP64-equivalent: F64/P64 + F32/P32)", "frac": tb / t, "peak_note": pk["note"],
-            "traffic": ncu_traffic("k_newton_mixed" + ("_compressed" if w is not None and (np.asarray(w) == 0).any()
-                                                       else ""), n), "flops_f64_per_launch": F64 / steps,
-            "flops_f32_per_launch": F32 / steps, "launch_ms": r["kms"]["newton"] / steps, "final_kernel": fin}
+    out = {"bound": "alu", "kernel": "k_newton<float>", "achieved": tb / t * P64,
+           "peak": P64, "unit": "GFLOP/s (FP64-equivalent: F64/P64 + F32/P32)", "frac": tb / t, "peak_note": pk["note"],
+           "traffic": ncu_traffic("k_newton_mixed" + ("_compressed" if w is not None and (np.asarray(w) == 0).any()
+                                                      else ""), n), "flops_f64_per_launch": F64 / steps,
+           "flops_f32_per_launch": F32 / steps, "launch_ms": r["kms"]["newton"] / steps,
+           "passes_per_update": (newton_corr + npts) / npts, "final_kernel": fin}
+    if "stage" in r["kms"]:
+        Fs = stage_flops(K_DEPTH, passes["stage"], npts, w=w)
+        ts = r["kms"]["stage"] * 1e-3
+        out["stage_kernel"] = {"kernel": "k_stage32", "achieved": Fs / ts / 1e9, "peak": P32,
+                               "unit": "GFLOP/s (FP32)", "frac": Fs / ts / 1e9 / P32,
+                               "flops_per_launch": Fs / steps, "launch_ms": r["kms"]["stage"] / steps,
+                               "passes_per_update": passes["stage"] / npts}
+    return out
 
 
 # ---------------------------------------------------------------------------------------------

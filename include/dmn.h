@@ -143,6 +143,15 @@ typedef struct {
                         * (up to the stopping criterion) in fewer Newton steps on smooth load
                         * paths.  The state then carries 3 fields per laminate and 6 more (see
                         * the state layout above). */
+  int32_t first_stage; /* the mixed forms: 0 (default) or 1 starts each point's Newton iteration with an
+                        * all-FP32 stage -- jumps, strains, the leaf return mapping, the residual and the
+                        * condensation in FP32 -- until its FP32 residual meets
+                        * ||A^T W sigma|| <= 1e-8 (2^K - 1) ||sigma_bar|| or min(12, max_iter - 1)
+                        * corrections; the FP64-residual iteration above then continues from its jumps
+                        * to tol.  iters counts the corrections of both, and both together stay within
+                        * max_iter.  The FP32 passes cost a small fraction of an FP64-residual pass, so
+                        * the update needs fewer of the latter.  -1: no first stage.  Not run with
+                        * line_search or predictor, nor in the FP64 form. */
 } dmn_options;
 
 /* Create a handle for n_trees DMNs (1 <= n_trees <= DMN_MAX_TREES; trees may
@@ -287,11 +296,17 @@ int dmn_grad(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* lam
 int dmn_profile_enable(dmn_handle* h, int32_t enable);
 
 /* Totals since dmn_profile_enable(h, 1): ms[0] orientation normals kernel,
- * ms[1] Newton kernel, ms[2] final-sweep kernel (milliseconds, summed over
+ * ms[1] Newton kernel (with the first stage), ms[2] final-sweep kernel (milliseconds, summed over
  * the timed updates), *updates = number of timed updates.  Waits for the
  * recorded events.  Errors: DMN_ERR_ARG for NULL arguments, DMN_ERR_CUDA if
  * an event query fails. */
 int dmn_profile_read(dmn_handle* h, double ms[3], int64_t* updates);
+
+/* The same totals with the mixed forms' first stage apart: ms[0] normals, ms[1] first stage (0 when it
+ * did not run), ms[2] Newton kernel, ms[3] final sweep; passes (may be NULL): passes[0] tree passes of
+ * the first stage, passes[1] of the Newton kernel, summed over points and timed updates (waits for the
+ * device).  Errors as dmn_profile_read. */
+int dmn_profile_read_stages(dmn_handle* h, double ms[4], int64_t passes[2], int64_t* updates);
 
 /* The same FP64 update as dmn_update, for callers that cannot allocate device
  * memory -- for example code whose device memory is all handed out by an

@@ -45,7 +45,7 @@ struct Tree {
   double* d_p = nullptr;
   double* d_q = nullptr;
   double* d_c = nullptr;   // c1 [N], c2 [N], sc [N], normalised leaf weights [L]
-  float* d_cf = nullptr;   // c1f [N], c2f [N], c12f [N]
+  float* d_cf = nullptr;   // c1f [N], c2f [N], c12f [N], scf [N]
   double wsum = 1.0;       // sum of the leaf weights as given
   PhaseDev ph[2];
   // compressed trees (some leaf weight zero): N laminates left, Lc leaves left,
@@ -92,7 +92,8 @@ struct dmn_handle {
   double* gwork = nullptr;      // dmn_grad per-point work, one chunk
   int64_t gwork_cap = 0;
   bool profiling = false;
-  std::vector<std::array<cudaEvent_t, 4>> events;  // per timed update: before/after each kernel
+  std::vector<std::array<cudaEvent_t, 5>> events;  // per timed update: before/after each kernel
+  unsigned long long* d_passes = nullptr;          // profiling: tree passes of the first stage and of k_newton
   size_t events_used = 0;
   std::string err;
 };
@@ -113,7 +114,7 @@ TreeDev tree_dev(const Tree& t) {
   d.K = t.K; d.M = t.M; d.N = t.N; d.L = t.L; d.nz = t.nz; d.z_both = t.z_both;
   d.p = t.d_p; d.q = t.d_q;
   d.c1 = t.d_c; d.c2 = t.d_c + t.N; d.sc = t.d_c + 2 * t.N;
-  d.c1f = t.d_cf; d.c2f = t.d_cf + t.N; d.c12f = t.d_cf + 2 * t.N;
+  d.c1f = t.d_cf; d.c2f = t.d_cf + t.N; d.c12f = t.d_cf + 2 * t.N; d.scf = t.d_cf + 3 * t.N;
   d.wl = t.d_c + 3 * t.N; d.wsum = t.wsum;
   d.ph[0] = t.ph[0]; d.ph[1] = t.ph[1];
   d.Lc = t.Lc;
@@ -124,6 +125,13 @@ TreeDev tree_dev(const Tree& t) {
   d.kid = t.d_tab ? t.d_tab + 4 * t.Lc + 3 * t.N : nullptr;
   d.hcid = t.d_tab ? t.d_tab + 4 * t.Lc + 5 * t.N : nullptr;
   return d;
+}
+
+// The FP32 copies of a phase's constants (the mixed forms' all-FP32 first stage).
+void phase_f32(PhaseDev& o) {
+  o.f.K = (float)o.K; o.f.G = (float)o.G; o.f.s0 = (float)o.s0; o.f.H = (float)o.H; o.f.lam = (float)o.lam;
+  o.f.inv_den = (float)o.inv_den; o.f.thb0 = (float)o.thb0;
+  o.f.ds = (float)o.ds; o.f.dk = (float)o.dk; o.f.rate = (float)o.rate;
 }
 
 // Checks one phase of a tree description and derives its device constants.
@@ -156,6 +164,7 @@ const char* make_phase(const dmn_phase& p, PhaseDev& out) {
   out.Gf = (float)out.G;
   out.inv_den = 1.0 / (2.0 * out.G + 2.0 * p.H / 3.0);
   out.thb0 = 1.0 / (1.0 + p.H / (3.0 * out.G));
+  phase_f32(out);
   return nullptr;
 }
 
@@ -187,6 +196,7 @@ __global__ void k_setup_tree(int K, const double* w_raw, double* c, float* cf) {
     cf[h - 1] = (float)c1;
     cf[N + h - 1] = (float)c2;
     cf[2 * N + h - 1] = (float)(c1 * c2);
+    cf[3 * N + h - 1] = (float)(W[h - 1] * c1 * c2);
   }
   for (int l = 0; l < L; ++l) c[3 * N + l] = w_raw[l] / s;
 }
@@ -424,6 +434,9 @@ struct NewtonParams {
   int write_outputs;  // no final sweep: stress and tangent (local frame) come from the converged Newton pass
   int predictor;      // extrapolated start; the state carries the last jump change and strain increment
   const double* dE;   // [n][6] strain increments (global frame), read with the extrapolated start
+  const double* a_start;  // the jumps to start from (state layout), or NULL for those of state_in; with the
+                          // first stage these are its jumps in state_out, and iters holds its corrections
+  unsigned long long* passes;  // profiling: tree passes of all points added here, or NULL
 };
 
 // MINB: resident CTAs per SM the register allocation is sized for (255, 170 or
@@ -459,6 +472,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   int64_t pt = -1;   // point of this lane; -1: needs work; >= n: no work left
   int tr = 0;        // its tree
   int it = 0;
+  int it0 = 0;       // corrections of the first stage (they count against max_iter)
   int cur = 0;       // buffer holding the accepted jumps and g, H
   bool first = true; // the next pass evaluates the starting jumps
   T step = (T)1;     // line search: scale of the trial step
@@ -468,6 +482,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   double rn_acc = 0.0;
   Sub<T> root_acc;   // line search: results at the accepted iterate
   double Eloc[6];
+  unsigned long long npass = 0;
   // the extrapolated start failed: continue from the stored jumps a^n, as a new point would
   auto restart = [&](const TreeDev& t) {
     const int nzf = 6 * t.nz;
@@ -532,7 +547,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
               // heap node -> paper index of its jumps
               const int lvl = 32 - __clz(node + 1);
               const int j = CMP ? node : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
-              double a0 = P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt];
+              double a0 = (P.a_start ? P.a_start : P.state_in)[(size_t)(nzf + 3 * j + c) * P.n + pt];
               if (PRED) a0 += rho * P.state_in[(size_t)(pf0 + 3 * j + c) * P.n + pt];
               abuf[0][(size_t)f * ns] = a0;
               const double nv = P.nbuf[(size_t)f * P.n + pt];
@@ -541,6 +556,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
             }
             A.z = P.state_in + pt;
             it = 0;
+            it0 = P.a_start ? P.iters[pt] : 0;
             first = true;
             step = (T)1;
             halvings = 0;
@@ -555,6 +571,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
     }
     if (!active) continue;
     const TreeDev& t = P.F.t[tr];
+    ++npass;
     A.a = abuf[cur];
     A.a_out = abuf[LS ? 1 - cur : cur];
     GH<T> gh{gbuf[cur], ns, gbuf[LS ? 1 - cur : cur]};
@@ -572,7 +589,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
       first = false;
       if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
       else if (rn <= P.tol * (double)t.N * sn) st = DMN_STATUS_OK;
-      else if (it >= (PRED ? lim : P.max_iter)) st = DMN_STATUS_MAXITER;
+      else if (it >= (PRED ? lim : P.max_iter - it0)) st = DMN_STATUS_MAXITER;
       if (st < 0) { ++it; continue; }
     } else {
       bool accepted = first || rn < rn_acc;
@@ -617,7 +634,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
 #pragma unroll
       for (int c = 0; c < 6; ++c) P.state_out[(size_t)(nzf + 6 * t.N + c) * P.n + pt] = P.dE[6 * pt + c];
     }
-    P.iters[pt] = it;
+    P.iters[pt] = it + it0;
     P.status[pt] = st;
     if (P.write_outputs) {
 #pragma unroll
@@ -627,6 +644,122 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
     }
     pt = -1;
   }
+  if (P.passes && npass) atomicAdd(P.passes, npass);
+}
+
+// The mixed forms' first stage (Sec. 3.2's Newton iteration with every quantity in FP32: jumps,
+// strains, leaf return mapping, residual and condensation).  Persistent like k_newton, with its own
+// work counter; per slot the FP32 scratch g, H [21 N], normals [3 N], jumps [3 N].  A point iterates
+// until its FP32 residual meets ||A^T W sigma|| <= tol (2^K - 1) ||sigma_bar|| or max_iter
+// corrections, then writes its jumps (widened) to the jump fields of state_out and the corrections
+// to iters; k_newton continues from there with the FP64 residual.  A point whose FP32 iterates are
+// not finite hands on a^n and zero corrections.  Points of unknown trees are left to k_newton.
+struct StageParams {
+  Forest F;
+  int64_t n, nslots;
+  int N_max;
+  const int32_t* tid;
+  const int64_t* perm;
+  const double* state_in;
+  double* state_out;
+  int32_t* iters;
+  const double* nbuf;
+  float* scr;
+  unsigned long long* counter;
+  float tol;
+  int max_iter;
+  unsigned long long* passes;  // profiling: tree passes of all points added here, or NULL
+};
+
+template <int MINB, bool CMP>
+__global__ void __launch_bounds__(128, MINB) k_stage32(StageParams P) {
+  const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int NM = P.N_max;
+  const size_t ns = (size_t)P.nslots;
+  float* gh = P.scr + slot;
+  float* nrmf = P.scr + (size_t)(21 * NM) * ns + slot;
+  float* af = P.scr + (size_t)(24 * NM) * ns + slot;
+  PointArrays A{};
+  A.ns = ns; A.nrmf = nrmf;
+  A.as = ns; A.paper = false;
+  A.af = af; A.af_out = af;
+  A.zs = (size_t)P.n;
+  int64_t pt = -1;
+  int tr = 0, it = 0;
+  bool first = true;
+  float E32[6];
+  unsigned long long npass = 0;
+  for (;;) {
+    const bool need = pt < 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, need);
+    if (mask) {
+      const int leader = __ffs(mask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(P.counter, (unsigned long long)__popc(mask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const int64_t i = (int64_t)(base + __popc(mask & ((1u << lane) - 1u)));
+        if (i >= P.n) {
+          pt = P.n;
+        } else {
+          point_of(P.perm, P.tid, P.F.n, i, pt, tr);
+          if (tr >= P.F.n) {
+            pt = -1;
+          } else {
+            const TreeDev& t = P.F.t[tr];
+            const int nzf = 6 * t.nz;
+#pragma unroll
+            for (int I = 0; I < 6; ++I) E32[I] = narrow_rn(P.nbuf[(size_t)(3 * NM + I) * P.n + pt]);
+            for (int f = 0; f < 3 * t.N; ++f) {
+              const int node = f / 3, c = f - 3 * node;
+              const int lvl = 32 - __clz(node + 1);
+              const int j = CMP ? node : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+              af[(size_t)f * ns] = narrow_rn(P.state_in[(size_t)(nzf + 3 * j + c) * P.n + pt]);
+              nrmf[(size_t)f * ns] = narrow_rn(P.nbuf[(size_t)f * P.n + pt]);
+            }
+            A.z = P.state_in + pt;
+            it = 0;
+            first = true;
+          }
+        }
+      }
+    }
+    const bool active = pt >= 0 && pt < P.n;
+    if (!__any_sync(0xffffffffu, active)) {
+      if (!__any_sync(0xffffffffu, pt < 0)) break;
+      continue;
+    }
+    if (!active) continue;
+    const TreeDev& t = P.F.t[tr];
+    ++npass;
+    GH<float> g{gh, ns, gh};
+    Sub<float, float> root;
+    float r2;
+    if (CMP) tree_pass_c<float, true, float>(t, E32, A, g, !first, 1.0f, root, r2, nullptr);
+    else tree_pass<float, true, float>(t, E32, A, g, !first, 1.0f, root, r2, nullptr);
+    first = false;
+    float sn2 = 0.0f;
+#pragma unroll
+    for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
+    const float rn = sqrtf(r2), sn = sqrtf(sn2);
+    const bool bad = !isfinite(rn) || !isfinite(sn);
+    if (!bad && rn > P.tol * (float)t.N * sn && it < P.max_iter) {
+      ++it;
+      continue;
+    }
+    const int nzf = 6 * t.nz;
+    for (int f = 0; f < 3 * t.N; ++f) {
+      const int node = f / 3, c = f - 3 * node;
+      const int lvl = 32 - __clz(node + 1);
+      const int j = CMP ? node : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+      const size_t at = (size_t)(nzf + 3 * j + c) * P.n + pt;
+      P.state_out[at] = bad ? P.state_in[at] : widen(af[(size_t)f * ns]);
+    }
+    P.iters[pt] = bad ? 0 : it;
+    pt = -1;
+  }
+  if (P.passes && npass) atomicAdd(P.passes, npass);
 }
 
 struct FinalParams {
@@ -968,7 +1101,7 @@ const char* check_tree(const dmn_tree_desc& d, bool allow_zero = false) {
 struct CmpTree {
   int N = 0, Lc = 0, nz = 0;
   std::vector<double> p, q, c;   // p, q [N][M]; c = c1 [N], c2 [N], sc [N], leaf weights [L]
-  std::vector<float> cf;         // c1f [N], c2f [N], c12f [N]
+  std::vector<float> cf;         // c1f [N], c2f [N], c12f [N], scf [N]
   std::vector<int> tab;          // lf [Lc] (4 ints each), pre [N], post [N], paper index [N], children [2 N],
                                  // the laminate at each heap position [2^K - 1]
 };
@@ -994,7 +1127,7 @@ void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& 
   const int Nc = (int)paper_of.size();
   B.N = Nc;
   B.p.resize((size_t)Nc * M); B.q.resize((size_t)Nc * M);
-  B.c.assign(3 * (size_t)Nc + L, 0.0); B.cf.assign(3 * (size_t)Nc, 0.0f);
+  B.c.assign(3 * (size_t)Nc + L, 0.0); B.cf.assign(4 * (size_t)Nc, 0.0f);
   for (int c = 0; c < Nc; ++c)
     for (int m = 0; m < M; ++m) { B.p[c * M + m] = d.p[paper_of[c] * M + m]; B.q[c * M + m] = d.q[paper_of[c] * M + m]; }
   for (int h = 1; h <= N; ++h) {
@@ -1003,6 +1136,7 @@ void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& 
     const double c1 = W[2 * h] / W[h], c2 = 1.0 - c1;
     B.c[c] = c1; B.c[Nc + c] = c2; B.c[2 * Nc + c] = W[h] * c1 * c2;
     B.cf[c] = (float)c1; B.cf[Nc + c] = (float)c2; B.cf[2 * Nc + c] = (float)(c1 * c2);
+    B.cf[3 * Nc + c] = (float)B.c[2 * Nc + c];
   }
   for (int l = 0; l < L; ++l) B.c[3 * Nc + l] = W[N + 1 + l];
   std::vector<int> lf, pre, post;
@@ -1103,6 +1237,19 @@ void launch_newton_p(const NewtonParams<T>& P, bool ls, int minb, unsigned grid,
   else if (minb == 3) k_newton<T, 3, false, CMP, PRED><<<grid, block, 0, s>>>(P);
   else k_newton<T, 4, false, CMP, PRED><<<grid, block, 0, s>>>(P);
 }
+template <bool CMP>
+void launch_stage(const StageParams& P, int minb, unsigned grid, int block, cudaStream_t s) {
+  if (minb == 2) k_stage32<2, CMP><<<grid, block, 0, s>>>(P);
+  else if (minb == 3) k_stage32<3, CMP><<<grid, block, 0, s>>>(P);
+  else k_stage32<4, CMP><<<grid, block, 0, s>>>(P);
+}
+
+// the mixed forms run the all-FP32 first stage unless the options turn it off or ask for the
+// line search or the extrapolated start
+bool first_stage_on(const dmn_options& o) {
+  return o.precision != DMN_PREC_F64 && o.first_stage >= 0 && !o.line_search && !o.predictor;
+}
+
 template <typename T, bool CMP>
 void launch_newton(const NewtonParams<T>& P, bool ls, int minb, unsigned grid, int block, cudaStream_t s) {
   if (P.predictor) launch_newton_p<T, CMP, true>(P, ls, minb, grid, block, s);
@@ -1134,7 +1281,7 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, cons
   cudaEvent_t* ev = nullptr;
   if (h->profiling) {
     if (h->events_used == h->events.size()) {
-      std::array<cudaEvent_t, 4> a;
+      std::array<cudaEvent_t, 5> a;
       for (auto& x : a) {
         e = cudaEventCreate(&x);
         if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: profiling event");
@@ -1163,20 +1310,31 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, cons
   const int minb = threads_per_sm > 384 ? 4 : threads_per_sm > 256 ? 3 : 2;
   const bool ls = h->opt.line_search != 0;
   const int block = h->opt.block;
+  const bool stage = first_stage_on(h->opt);
+  unsigned long long* passes = h->profiling ? h->d_passes : nullptr;
+  if (stage) {   // counter [19]: the first stage's work counter
+    // its corrections count against max_iter: the FP64-residual iteration keeps at least one
+    const int max32 = std::max(0, std::min(STAGE_MAX_ITER, h->opt.max_iter - 1));
+    StageParams SP{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, iters, w.nbuf, (float*)w.scr_t,
+                   w.counter + 19, STAGE_TOL, max32, passes};
+    if (h->cmp) launch_stage<true>(SP, minb, grid, block, s);
+    else launch_stage<false>(SP, minb, grid, block, s);
+  }
+  if (ev) cudaEventRecord(ev[2], s);
   if (!mixed) {
     NewtonParams<double> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                            w.nbuf, w.scr_d, (double*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 1,
-                           h->opt.predictor, dE};
+                           h->opt.predictor, dE, nullptr, passes ? passes + 1 : nullptr};
     if (h->cmp) launch_newton<double, true>(P, ls, minb, grid, block, s);
     else launch_newton<double, false>(P, ls, minb, grid, block, s);
   } else {
     NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                           w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, sweep ? 0 : 1,
-                          h->opt.predictor, dE};
+                          h->opt.predictor, dE, stage ? state_out : nullptr, passes ? passes + 1 : nullptr};
     if (h->cmp) launch_newton<float, true>(P, ls, minb, grid, block, s);
     else launch_newton<float, false>(P, ls, minb, grid, block, s);
   }
-  if (ev) cudaEventRecord(ev[2], s);
+  if (ev) cudaEventRecord(ev[3], s);
   FinalParams FP{F, n, NM, tree_id, perm, Q, state_in, state_out, stress, tangent, status, w.nbuf};
   if (sweep) {
     if (h->cmp) k_final<true, true><<<g1, 128, 0, s>>>(FP);
@@ -1185,7 +1343,7 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, cons
     if (h->cmp) k_final<false, true><<<g1, 128, 0, s>>>(FP);
     else k_final<false, false><<<g1, 128, 0, s>>>(FP);
   }
-  if (ev) cudaEventRecord(ev[3], s);
+  if (ev) cudaEventRecord(ev[4], s);
   e = cudaGetLastError();
   return e == cudaSuccess ? DMN_OK : cuda_fail(h, e, "dmn_update: launch");
 }
@@ -1302,7 +1460,7 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
 
   dmn_options o;
   o.tol = 1e-12; o.max_iter = 50; o.precision = DMN_PREC_F64; o.block = 128; o.ctas_per_sm = 0; o.line_search = 0;
-  o.predictor = 0;
+  o.predictor = 0; o.first_stage = 0;
   if (opt) {
     if (opt->tol > 0.0) o.tol = opt->tol;
     if (opt->max_iter > 0) o.max_iter = opt->max_iter;
@@ -1311,7 +1469,10 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     if (opt->ctas_per_sm > 0) o.ctas_per_sm = opt->ctas_per_sm;
     o.line_search = opt->line_search;
     o.predictor = opt->predictor;
+    o.first_stage = opt->first_stage;
   }
+  if (o.first_stage < -1 || o.first_stage > 1)
+    return fail(nullptr, DMN_ERR_ARG, "dmn_create: first_stage must be -1, 0 or 1");
   if (o.line_search != 0 && o.line_search != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: line_search must be 0 or 1");
   if (o.predictor != 0 && o.predictor != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: predictor must be 0 or 1");
   if (o.predictor) {   // the last update's jump change and strain increment follow the jumps
@@ -1375,7 +1536,7 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     e = cudaMalloc(&T.d_p, sizeof(double) * N * M);
     if (e == cudaSuccess) e = cudaMalloc(&T.d_q, sizeof(double) * N * M);
     if (e == cudaSuccess) e = cudaMalloc(&T.d_c, sizeof(double) * (3 * N + L));
-    if (e == cudaSuccess) e = cudaMalloc(&T.d_cf, sizeof(float) * 3 * N);
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_cf, sizeof(float) * 4 * N);
     if (e == cudaSuccess) e = cudaMemcpy(T.d_p, ph.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(T.d_q, qh.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_w, d.w, sizeof(double) * L, cudaMemcpyHostToDevice);
@@ -1405,6 +1566,7 @@ void dmn_destroy(dmn_handle* h) {
   for (auto& w : h->ws) free_ws(w);
   free_pipe(h->hp);
   cudaFree(h->gwork);
+  cudaFree(h->d_passes);
   delete h;
 }
 
@@ -1417,27 +1579,53 @@ int64_t dmn_state_size(const dmn_handle* h, int32_t tree_id) {
 
 int dmn_profile_enable(dmn_handle* h, int32_t enable) {
   if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_profile_enable: NULL handle");
+  if (enable) {
+    cudaError_t e = cudaSuccess;
+    if (!h->d_passes) e = cudaMalloc(&h->d_passes, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_passes, 0, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_profile_enable");
+    h->events_used = 0;
+  }
   h->profiling = enable != 0;
-  if (enable) h->events_used = 0;
+  return DMN_OK;
+}
+
+int dmn_profile_read_stages(dmn_handle* h, double ms[4], int64_t passes[2], int64_t* updates) {
+  if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_profile_read_stages: NULL handle");
+  if (!ms || !updates) return fail(h, DMN_ERR_ARG, "dmn_profile_read_stages: NULL output");
+  ms[0] = ms[1] = ms[2] = ms[3] = 0.0;
+  for (size_t i = 0; i < h->events_used; ++i) {
+    const auto& a = h->events[i];
+    cudaError_t e = cudaEventSynchronize(a[4]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_profile_read_stages");
+    for (int k = 0; k < 4; ++k) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, a[k], a[k + 1]);
+      if (e != cudaSuccess) return cuda_fail(h, e, "dmn_profile_read_stages");
+      ms[k] += t;
+    }
+  }
+  if (passes) {
+    unsigned long long c[2] = {0, 0};
+    if (h->d_passes) {
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e == cudaSuccess) e = cudaMemcpy(c, h->d_passes, sizeof c, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(h, e, "dmn_profile_read_stages");
+    }
+    passes[0] = (int64_t)c[0];
+    passes[1] = (int64_t)c[1];
+  }
+  *updates = (int64_t)h->events_used;
   return DMN_OK;
 }
 
 int dmn_profile_read(dmn_handle* h, double ms[3], int64_t* updates) {
   if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_profile_read: NULL handle");
   if (!ms || !updates) return fail(h, DMN_ERR_ARG, "dmn_profile_read: NULL output");
-  ms[0] = ms[1] = ms[2] = 0.0;
-  for (size_t i = 0; i < h->events_used; ++i) {
-    const auto& a = h->events[i];
-    cudaError_t e = cudaEventSynchronize(a[3]);
-    if (e != cudaSuccess) return cuda_fail(h, e, "dmn_profile_read");
-    for (int k = 0; k < 3; ++k) {
-      float t = 0.f;
-      e = cudaEventElapsedTime(&t, a[k], a[k + 1]);
-      if (e != cudaSuccess) return cuda_fail(h, e, "dmn_profile_read");
-      ms[k] += t;
-    }
-  }
-  *updates = (int64_t)h->events_used;
+  double m4[4];
+  const int rc = dmn_profile_read_stages(h, m4, nullptr, updates);
+  if (rc != DMN_OK) return rc;
+  ms[0] = m4[0]; ms[1] = m4[1] + m4[2]; ms[2] = m4[3];
   return DMN_OK;
 }
 
@@ -1806,7 +1994,7 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   td.z_both = n_inel == 2;
   td.nz = n_inel * (L / 2);
   // sizes against the fixed work space: parameters, then whole CTAs of lane scratch
-  const size_t param_doubles = (size_t)2 * N * M + (size_t)L + 3 * (size_t)N + (size_t)L + (3 * (size_t)N + 1) / 2;
+  const size_t param_doubles = (size_t)2 * N * M + (size_t)L + 3 * (size_t)N + (size_t)L + 2 * (size_t)N;
   const size_t lane_bytes = sizeof(double) * (size_t)27 * N;
   const size_t avail = DMN_NOALLOC_BYTES - 256 - sizeof(double) * NOALLOC_PARAM_DOUBLES;
   const int64_t nslots = (int64_t)(avail / lane_bytes) / NOALLOC_BLOCK * NOALLOC_BLOCK;
@@ -1847,7 +2035,7 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "dmn_update_noalloc: counter reset");
   td.p = d_p; td.q = d_q;
   td.c1 = d_c; td.c2 = d_c + N; td.sc = d_c + 2 * N;
-  td.c1f = d_cf; td.c2f = d_cf + N; td.c12f = d_cf + 2 * N;
+  td.c1f = d_cf; td.c2f = d_cf + N; td.c12f = d_cf + 2 * N; td.scf = d_cf + 3 * N;
   td.wl = d_c + 3 * N;
   td.wsum = 0.0;
   for (int l = 0; l < L; ++l) td.wsum += d.w[l];

@@ -26,6 +26,11 @@ constexpr int KMAX = 8;
 constexpr int NMAX = (1 << KMAX) - 1;
 constexpr double RS2 = 0.70710678118654752440;   // 1/sqrt(2)
 constexpr double SQ23 = 0.81649658092772603273;  // sqrt(2/3)
+// The mixed forms' all-FP32 first stage: Newton passes in FP32 until
+// ||A^T W sigma|| <= STAGE_TOL (2^K - 1) ||sigma_bar|| (its FP32 residual) or STAGE_MAX_ITER
+// corrections; the FP64-residual iteration continues from its jumps.
+constexpr float STAGE_TOL = 1e-8f;
+constexpr int STAGE_MAX_ITER = 12;
 
 // Isotropic phase: elastic (kind 0), J2 with linear isotropic hardening
 // (kind 1) or with exponential-linear hardening (kind 2, Sec. 4.1):
@@ -41,6 +46,10 @@ struct PhaseDev {
   double inv_den;    // 1 / (2G + 2H/3): plastic multiplier per unit overstress (kind 1)
   double thb0;       // 1 / (1 + H / (3G)) (kind 1)
   double ds, dk, rate;  // kind 2: sigma_inf - s0, k0 - H, (k0 - H) / (sigma_inf - s0)
+  // FP32 copies of the constants above, for the all-FP32 passes of the mixed forms' first stage
+  struct {
+    float K, G, s0, H, lam, inv_den, thb0, ds, dk, rate;
+  } f;
 };
 
 // Per-laminate constants, heap order.
@@ -56,6 +65,7 @@ struct TreeDev {
   const float* c1f;  // [N] FP32 copies of c1, c2, c1 c2
   const float* c2f;
   const float* c12f;
+  const float* scf;  // [N] FP32 copy of sc
   const double* wl;  // [L] normalised leaf weights
   double wsum;       // sum of the leaf weights as given
   PhaseDev ph[2];
@@ -185,6 +195,49 @@ __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <>
 __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
+// x converted to T: exact or by narrow_rn / widen (integer instructions), never by a hardware conversion
+template <typename T, typename S>
+struct Cvt;
+template <>
+struct Cvt<double, double> { __host__ __device__ static double f(double x) { return x; } };
+template <>
+struct Cvt<float, double> { __host__ __device__ static float f(double x) { return narrow_rn(x); } };
+template <>
+struct Cvt<float, float> { __host__ __device__ static float f(float x) { return x; } };
+template <>
+struct Cvt<double, float> { __host__ __device__ static double f(float x) { return widen(x); } };
+template <typename T, typename S>
+__device__ __forceinline__ T cvt(S x) { return Cvt<T, S>::f(x); }
+
+// a parameter type that takes no part in template argument deduction (a NULL argument then fits)
+template <typename X>
+struct NoDeduce { using type = X; };
+
+// the math functions in precision S (float: the FP32 versions, so that nothing runs on the FP64 pipe)
+__device__ __forceinline__ double rsqrt_s(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_s(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double sqrt_s(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_s(float x) { return sqrtf(x); }
+__device__ __forceinline__ double exp_s(double x) { return exp(x); }
+__device__ __forceinline__ float exp_s(float x) { return expf(x); }
+__device__ __forceinline__ double fabs_s(double x) { return fabs(x); }
+__device__ __forceinline__ float fabs_s(float x) { return fabsf(x); }
+__device__ __forceinline__ double fmax_s(double x, double y) { return fmax(x, y); }
+__device__ __forceinline__ float fmax_s(float x, float y) { return fmaxf(x, y); }
+// smallest squared norm taken as non-zero, and a value above any relative yield gap
+template <typename S>
+__device__ __forceinline__ S tiny_s();
+template <>
+__device__ __forceinline__ double tiny_s<double>() { return 1e-300; }
+template <>
+__device__ __forceinline__ float tiny_s<float>() { return 1e-36f; }
+template <typename S>
+__device__ __forceinline__ S huge_s();
+template <>
+__device__ __forceinline__ double huge_s<double>() { return 1e300; }
+template <>
+__device__ __forceinline__ float huge_s<float>() { return 1e30f; }
+
 // packed symmetric 6x6: upper triangle row by row
 __host__ __device__ constexpr int sidx(int i, int j) {
   return i <= j ? i * 6 - (i * (i - 1)) / 2 + (j - i) : j * 6 - (j * (j - 1)) / 2 + (i - j);
@@ -196,9 +249,10 @@ __host__ __device__ constexpr int sidx(int i, int j) {
 // residual), ds the change that the inner Newton corrections add (precision
 // T), C the condensed tangent (T).  Keeping sb apart in FP64 lets the FP32
 // form see the residual, a small difference of large stresses, exactly.
-template <typename T>
+// The all-FP32 passes (S = float) keep sb in FP32 as well.
+template <typename T, typename S = double>
 struct Sub {
-  double sb[6];
+  S sb[6];
   T ds[6];
   T C[21];
 };
@@ -220,13 +274,16 @@ struct LeafTan {
 //          D = K 1(x)1 + 2G th Idev - 2G thb n(x)n, th = 1 - k2,
 //          thb = 1/(1 + sigma_Y'/(3G)) - (1 - th).
 // Written without branches: an elastic step is the plastic formula with dg = 0.
-template <typename T>
-__device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], const double z[6], double sig[6],
-                                         LeafTan<T>* D, double* znew, double* gap) {
-  const double tr = e[0] + e[1] + e[2];
-  const double twoG = 2.0 * ph.G;
+// S: the precision of strains, state and stress (double; float in the mixed forms' all-FP32
+// first stage, whose constants are the phase's FP32 copies).
+template <typename T, typename S = double>
+__device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const S e[6], const S z[6], S sig[6], LeafTan<T>* D,
+                                         typename NoDeduce<S>::type* znew, typename NoDeduce<S>::type* gap) {
+  const S K = pick<S>(ph.K, ph.f.K), G = pick<S>(ph.G, ph.f.G), lam = pick<S>(ph.lam, ph.f.lam);
+  const S tr = e[0] + e[1] + e[2];
+  const S twoG = (S)2 * G;
   if (ph.kind == 0) {
-    const double lt = ph.lam * tr;
+    const S lt = lam * tr;
 #pragma unroll
     for (int I = 0; I < 6; ++I) sig[I] = twoG * e[I];
     sig[0] += lt; sig[1] += lt; sig[2] += lt;
@@ -235,68 +292,74 @@ __device__ __forceinline__ void leaf_iso(const PhaseDev& ph, const double e[6], 
 #pragma unroll
       for (int I = 0; I < 6; ++I) D->m[I] = (T)0;
     }
-    if (gap) *gap = 1e300;
+    if (gap) *gap = huge_s<S>();
     return;
   }
-  const double m3 = tr * (1.0 / 3.0);
-  const double ep2 = -(z[1] + z[2]);
-  const double xi[6] = {e[0] - m3 - z[1], e[1] - m3 - z[2], e[2] - m3 - ep2, e[3] - z[3], e[4] - z[4], e[5] - z[5]};
-  double n2 = 0.0;
+  const S s0 = pick<S>(ph.s0, ph.f.s0), H = pick<S>(ph.H, ph.f.H);
+  const S sq23 = (S)SQ23;
+  const S m3 = tr * (S)(1.0 / 3.0);
+  const S ep2 = -(z[1] + z[2]);
+  const S xi[6] = {e[0] - m3 - z[1], e[1] - m3 - z[2], e[2] - m3 - ep2, e[3] - z[3], e[4] - z[4], e[5] - z[5]};
+  S n2 = (S)0;
 #pragma unroll
   for (int I = 0; I < 6; ++I) n2 += xi[I] * xi[I];
-  const double inx = rsqrt(fmax(n2, 1e-300));   // 1 / |xi|
-  const double ns = twoG * (n2 * inx);          // |s_tr|
+  const S inx = rsqrt_s(fmax_s(n2, tiny_s<S>()));   // 1 / |xi|
+  const S ns = twoG * (n2 * inx);                    // |s_tr|
   const bool explin = ph.kind == 2;
-  const double e_n = explin ? exp(-ph.rate * z[0]) : 1.0;
-  const double sy = ph.s0 + ph.H * z[0] + (explin ? ph.ds * (1.0 - e_n) : 0.0);
-  const double f = ns - SQ23 * sy;
-  const bool plastic = f > 0.0;
-  if (gap) *gap = fabs(f) / sy;
-  double dg = plastic ? f * ph.inv_den : 0.0;
-  double thb0 = ph.thb0;
+  const S rate = pick<S>(ph.rate, ph.f.rate), dsat = pick<S>(ph.ds, ph.f.ds), dk = pick<S>(ph.dk, ph.f.dk);
+  const S e_n = explin ? exp_s(-rate * z[0]) : (S)1;
+  const S sy = s0 + H * z[0] + (explin ? dsat * ((S)1 - e_n) : (S)0);
+  const S f = ns - sq23 * sy;
+  const bool plastic = f > (S)0;
+  if (gap) *gap = fabs_s(f) / sy;
+  S dg = plastic ? f * pick<S>(ph.inv_den, ph.f.inv_den) : (S)0;
+  S thb0 = pick<S>(ph.thb0, ph.f.thb0);
   if (explin && plastic) {
     // scalar Newton on r(dg) = |s_tr| - 2G dg - sqrt(2/3) sigma_Y(a_n + sqrt(2/3) dg).  r is convex and
     // decreasing, so from dg = 0 the iterates rise monotonically to the root; the first iterate,
     // f / (2G + 2/3 sigma_Y'(a_n)), needs no new exponential.  Convergence is quadratic, so once a
-    // step is below 1e-10 dg the next would be below the rounding of dg: stop there.
-    double slope = ph.H + ph.dk * e_n, e = e_n, step = 0.0;
-    dg = f / (twoG + (2.0 / 3.0) * slope);
+    // step is below 1e-10 dg the next would be below the rounding of dg: stop there.  In FP32 the
+    // residual's rounding bounds a step from below by about 1e-7 |xi|: stop at 1e-6 dg + 2e-7 |xi|.
+    S slope = H + dk * e_n, ex = e_n, step = (S)0;
+    dg = f / (twoG + (S)(2.0 / 3.0) * slope);
+    const S floor_abs = sizeof(S) == 8 ? (S)0 : (S)2e-7f * (n2 * inx);
+    const S rel = sizeof(S) == 8 ? (S)1e-10 : (S)1e-6f;
     for (int it = 0; it < 40; ++it) {
-      const double a = z[0] + SQ23 * dg;
-      e = exp(-ph.rate * a);
-      slope = ph.H + ph.dk * e;
-      const double r = ns - twoG * dg - SQ23 * (ph.s0 + ph.H * a + ph.ds * (1.0 - e));
-      step = r / (twoG + (2.0 / 3.0) * slope);
+      const S a = z[0] + sq23 * dg;
+      ex = exp_s(-rate * a);
+      slope = H + dk * ex;
+      const S r = ns - twoG * dg - sq23 * (s0 + H * a + dsat * ((S)1 - ex));
+      step = r / (twoG + (S)(2.0 / 3.0) * slope);
       dg += step;
-      if (fabs(step) <= 1e-10 * dg) break;
+      if (sizeof(S) == 8 ? fabs_s(step) <= rel * dg : fabs_s(step) <= rel * dg + floor_abs) break;
     }
     // hardening slope at the new a: the last one was taken one step earlier; its first-order
     // correction -rate dk e sqrt(2/3) step leaves an error of order (rate step)^2
-    slope -= ph.rate * ph.dk * e * SQ23 * step;
-    thb0 = 1.0 / (1.0 + slope / (3.0 * ph.G));
+    slope -= rate * dk * ex * sq23 * step;
+    thb0 = (S)1 / ((S)1 + slope / ((S)3 * G));
   }
-  const double k2 = dg * inx;          // 2G dg / |s_tr| = 1 - th
-  const double Kt = ph.K * tr;
-  const double g2 = twoG - twoG * k2;  // 2G th
+  const S k2 = dg * inx;          // 2G dg / |s_tr| = 1 - th
+  const S Kt = K * tr;
+  const S g2 = twoG - twoG * k2;  // 2G th
 #pragma unroll
   for (int I = 0; I < 6; ++I) sig[I] = g2 * xi[I];
   sig[0] += Kt; sig[1] += Kt; sig[2] += Kt;
   if (D) {
-    const double mu = ph.G * (1.0 - k2);
-    D->mu = narrow<T>(mu);
-    D->lam = narrow<T>(ph.K - (2.0 / 3.0) * mu);
-    D->c = narrow<T>(plastic ? twoG * (thb0 - k2) : 0.0);
-    if (sizeof(T) == 8) {
+    const S mu = G * ((S)1 - k2);
+    D->mu = cvt<T>(mu);
+    D->lam = cvt<T>(K - (S)(2.0 / 3.0) * mu);
+    D->c = cvt<T>(plastic ? twoG * (thb0 - k2) : (S)0);
+    if (sizeof(T) == sizeof(S)) {
 #pragma unroll
-      for (int I = 0; I < 6; ++I) D->m[I] = narrow<T>(xi[I] * inx);
+      for (int I = 0; I < 6; ++I) D->m[I] = cvt<T>(xi[I] * inx);
     } else {   // the FP32 tangent's flow direction, normalised in FP32
-      const T it = narrow<T>(inx);
+      const T it = cvt<T>(inx);
 #pragma unroll
-      for (int I = 0; I < 6; ++I) D->m[I] = narrow<T>(xi[I]) * it;
+      for (int I = 0; I < 6; ++I) D->m[I] = cvt<T>(xi[I]) * it;
     }
   }
   if (znew) {
-    znew[0] = z[0] + SQ23 * dg;         // ep += dg n = k2 xi
+    znew[0] = z[0] + sq23 * dg;         // ep += dg n = k2 xi
     znew[1] = z[1] + k2 * xi[0]; znew[2] = z[2] + k2 * xi[1];
     znew[3] = z[3] + k2 * xi[3]; znew[4] = z[4] + k2 * xi[4]; znew[5] = z[5] + k2 * xi[5];
   }
@@ -360,13 +423,15 @@ __device__ __forceinline__ void inv3_sym(T k00, T k01, T k02, T k11, T k12, T k2
 
 // The laminate's FP64 residual share (A^T W sigma)_j = W c1 c2 N^T (sb_R - sb_L),
 // added to r2, the plain average sb = c1 sb_L + c2 sb_R, and t = N^T (sb_R - sb_L).
-__device__ __forceinline__ void residual_share(const double nd[3], double c1, double c2, double sc, const double sL[6],
-                                               const double sR[6], double sb[6], double t[3], double& r2) {
-  double d[6];
+// (In the all-FP32 first stage, S = float, it is the FP32 residual of that stage.)
+template <typename S>
+__device__ __forceinline__ void residual_share(const S nd[3], S c1, S c2, S sc, const S sL[6], const S sR[6], S sb[6],
+                                               S t[3], S& r2) {
+  S d[6];
 #pragma unroll
   for (int I = 0; I < 6; ++I) d[I] = sR[I] - sL[I];
-  const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
-  Nt_apply<double>(nd, ndr, d, t);
+  const S ndr[3] = {nd[0] * (S)RS2, nd[1] * (S)RS2, nd[2] * (S)RS2};
+  Nt_apply<S>(nd, ndr, d, t);
   r2 += sc * sc * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
 #pragma unroll
   for (int I = 0; I < 6; ++I) sb[I] = sL[I] + c2 * d[I];   // c1 sL + c2 sR with c1 = 1 - c2
@@ -387,15 +452,15 @@ __device__ __forceinline__ void residual_share(const double nd[3], double c1, do
 // For constant child tangents this is the laminate homogenisation of Sec. 3.1;
 // eliminating laminates leaves-to-root is Gaussian elimination of the Newton
 // system A^T W D A da = -A^T W sigma of Sec. 3.2 (no fill in that order).
-template <typename T, bool STORE>
-__device__ __forceinline__ void condense(const double nd[3], const T n[3], double c1d, double c2d, double sc,
-                                         NodeC<T> cc, const Sub<T>& L, const Sub<T>& R, Sub<T>& out, T* gp,
-                                         size_t gstride, double& r2) {
+template <typename T, bool STORE, typename S = double>
+__device__ __forceinline__ void condense(const S nd[3], const T n[3], S c1d, S c2d, S sc, NodeC<T> cc,
+                                         const Sub<T, S>& L, const Sub<T, S>& R, Sub<T, S>& out, T* gp,
+                                         size_t gstride, S& r2) {
   T u[3];
   {
-    double t[3];
-    residual_share(nd, c1d, c2d, sc, L.sb, R.sb, out.sb, t, r2);
-    u[0] = narrow<T>(t[0]); u[1] = narrow<T>(t[1]); u[2] = narrow<T>(t[2]);
+    S t[3];
+    residual_share<S>(nd, c1d, c2d, sc, L.sb, R.sb, out.sb, t, r2);
+    u[0] = cvt<T>(t[0]); u[1] = cvt<T>(t[1]); u[2] = cvt<T>(t[2]);
   }
   const T c1 = cc.c1, c2 = cc.c2, c12 = cc.c12;
   const T nr[3] = {n[0] * (T)RS2, n[1] * (T)RS2, n[2] * (T)RS2};
@@ -470,19 +535,19 @@ __device__ __forceinline__ void condense(const double nd[3], const T n[3], doubl
 // A leaf of an elastic phase has c_X = 0 in every pass: elL / elR (the phases of the
 // tree's left and right leaves, the same for every lane) drop its rank-one terms in the
 // FP64 condensation, which leaves every non-zero result unchanged.
-template <typename T, bool STORE>
-__device__ __forceinline__ void condense_bottom(const double nd[3], const T n[3], double c1d, double c2d, double sc,
-                                                NodeC<T> cc, const double sL[6], const LeafTan<T>& DL,
-                                                const double sR[6], const LeafTan<T>& DR, Sub<T>& out, T* gp,
-                                                size_t gstride, double& r2, bool elL, bool elR) {
+template <typename T, bool STORE, typename S = double>
+__device__ __forceinline__ void condense_bottom(const S nd[3], const T n[3], S c1d, S c2d, S sc, NodeC<T> cc,
+                                                const S sL[6], const LeafTan<T>& DL, const S sR[6],
+                                                const LeafTan<T>& DR, Sub<T, S>& out, T* gp, size_t gstride, S& r2,
+                                                bool elL, bool elR) {
   // the FP32 condensation runs beside the FP64 work at no cost of its own: it keeps the general
   // form, whose register use the shortcut would raise
   if (sizeof(T) == 4) { elL = false; elR = false; }
   T u[3];
   {
-    double t[3];
-    residual_share(nd, c1d, c2d, sc, sL, sR, out.sb, t, r2);
-    u[0] = narrow<T>(t[0]); u[1] = narrow<T>(t[1]); u[2] = narrow<T>(t[2]);
+    S t[3];
+    residual_share<S>(nd, c1d, c2d, sc, sL, sR, out.sb, t, r2);
+    u[0] = cvt<T>(t[0]); u[1] = cvt<T>(t[1]); u[2] = cvt<T>(t[2]);
   }
   const T c1 = cc.c1, c2 = cc.c2, c12 = cc.c12;
   const T nr[3] = {n[0] * (T)RS2, n[1] * (T)RS2, n[2] * (T)RS2};
@@ -604,6 +669,30 @@ struct PointArrays {
   double* a_out;                 // where corrected jumps are written (same indexing; == a: in place)
   bool paper;                    // jumps stored in the paper's ordering (level K first, root last)
   const double* z; size_t zs;    // leaf state z^n of the inelastic slots: z[(6*slot+c)*zs]
+  float* af;                     // the all-FP32 passes: jumps in FP32 (indexing of a)
+  float* af_out;
+};
+
+// Per-laminate and per-leaf inputs of a pass in its state precision S: the FP32 passes read the
+// FP32 copies (normals, volume fractions) or narrow the FP64 values with integer instructions
+// (leaf states).
+template <typename S>
+struct PassIn;
+template <>
+struct PassIn<double> {
+  __device__ static double* a(const PointArrays& P) { return P.a; }
+  __device__ static double* a_out(const PointArrays& P) { return P.a_out; }
+  __device__ static double c1(const TreeDev& t, int j) { return __ldg(t.c1 + j); }
+  __device__ static double c2(const TreeDev& t, int j) { return __ldg(t.c2 + j); }
+  __device__ static double sc(const TreeDev& t, int j) { return __ldg(t.sc + j); }
+};
+template <>
+struct PassIn<float> {
+  __device__ static float* a(const PointArrays& P) { return P.af; }
+  __device__ static float* a_out(const PointArrays& P) { return P.af_out; }
+  __device__ static float c1(const TreeDev& t, int j) { return __ldg(t.c1f + j); }
+  __device__ static float c2(const TreeDev& t, int j) { return __ldg(t.c2f + j); }
+  __device__ static float sc(const TreeDev& t, int j) { return __ldg(t.scf + j); }
 };
 
 // array index of the jumps of heap node `node` at level lvl
@@ -630,15 +719,27 @@ __device__ __forceinline__ void load_n<float>(const PointArrays& P, int node, do
   for (int c = 0; c < 3; ++c) { nd[c] = P.nrm[(3 * node + c) * P.ns]; n[c] = P.nrmf[(3 * node + c) * P.ns]; }
 }
 
-__device__ __forceinline__ void load_z(const TreeDev& t, const PointArrays& P, int leaf, int phase, double z[6]) {
+// normals in the state precision S and in the working precision T
+template <typename T, typename S>
+__device__ __forceinline__ void load_ns(const PointArrays& P, int node, S nd[3], T n[3]) {
+  if (sizeof(S) == 8) {
+    load_n<T>(P, node, reinterpret_cast<double*>(nd), n);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { n[c] = (T)P.nrmf[(3 * node + c) * P.ns]; nd[c] = (S)n[c]; }
+  }
+}
+
+template <typename S>
+__device__ __forceinline__ void load_z(const TreeDev& t, const PointArrays& P, int leaf, int phase, S z[6]) {
   if (t.ph[phase].kind != 0) {
     const int slot = t.z_both ? leaf : (leaf >> 1);
     const double* b = P.z + (size_t)(6 * slot) * P.zs;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) z[c] = b[c * P.zs];
+    for (int c = 0; c < 6; ++c) z[c] = cvt<S>(b[c * P.zs]);
   } else {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) z[c] = 0.0;
+    for (int c = 0; c < 6; ++c) z[c] = (S)0;
   }
 }
 
@@ -651,18 +752,22 @@ __device__ __forceinline__ void load_z(const TreeDev& t, const PointArrays& P, i
 //   !STORE: evaluation at the given jumps only (final sweep).
 // Returns the root's subtree result (sb = effective stress, C = tangent of the
 // linearised DMN) and the squared norm of A^T W sigma at the (updated) jumps.
-template <typename T, bool STORE>
-__device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArrays& P, GH<T> gh, bool apply,
-                          T step, Sub<T>& root, double& r2, double* gap_min) {
+// S: the precision of strains, jumps, leaf stresses and residual (double; float in the mixed
+// forms' all-FP32 first stage, which reads and writes the FP32 jumps af).
+template <typename T, bool STORE, typename S = double>
+__device__ void tree_pass(const TreeDev& t, const S Eloc[6], const PointArrays& P, GH<T> gh, bool apply, T step,
+                          Sub<T, S>& root, S& r2, typename NoDeduce<S>::type* gap_min) {
   const int K = t.K;
-  double epsR[KMAX + 1][6];
+  S epsR[KMAX + 1][6];
   T depsR[KMAX + 1][6];
-  Sub<T> pend[KMAX + 1];
-  r2 = 0.0;
+  Sub<T, S> pend[KMAX + 1];
+  r2 = (S)0;
+  S* const a_in = PassIn<S>::a(P);
+  S* const a_wr = PassIn<S>::a_out(P);
   const int nbottom = 1 << (K - 1);
   for (int m = 0; m < nbottom; ++m) {
     const int top = (m == 0) ? 1 : K - __ffs(m) + 1;
-    double e[6];
+    S e[6];
     T de[6];
     if (m == 0) {
 #pragma unroll
@@ -671,16 +776,16 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
 #pragma unroll
       for (int I = 0; I < 6; ++I) { e[I] = epsR[top][I]; de[I] = depsR[top][I]; }
     }
-    double eL[6], eR[6];
+    S eL[6], eR[6];
     for (int lvl = top; lvl <= K; ++lvl) {
       const int node = (1 << (lvl - 1)) + (m >> (K - lvl)) - 1;
-      double nd[3];
+      S nd[3];
       T nt[3];
-      load_n<T>(P, node, nd, nt);
-      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+      load_ns<T, S>(P, node, nd, nt);
+      const S c1 = PassIn<S>::c1(t, node), c2 = PassIn<S>::c2(t, node);
       const size_t aoff = (size_t)(3 * jump_index(P, K, lvl, node)) * P.as;
-      const double* ap = P.a + aoff;
-      double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
+      const S* ap = a_in + aoff;
+      S a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
       T da[3] = {(T)0, (T)0, (T)0};
       if (STORE) {   // only the Newton kernel corrects jumps; `apply` is false on a point's first pass
         const T* gp = gh.p + (size_t)(21 * node) * gh.s;
@@ -691,13 +796,13 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
           for (int I = 0; I < 6; ++I) v += gp[(3 + 6 * c + I) * gh.s] * de[I];
           da[c] = apply ? v : (T)0;
         }
-        double* aw = P.a_out + aoff;
+        S* aw = a_wr + aoff;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) { a[c] += widen(da[c]); aw[c * P.as] = a[c]; }
+        for (int c = 0; c < 3; ++c) { a[c] += cvt<S>(da[c]); aw[c * P.as] = a[c]; }
       }
-      const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
-      double Na[6];
-      N_apply<double>(nd, ndr, a, Na);
+      const S ndr[3] = {nd[0] * (S)RS2, nd[1] * (S)RS2, nd[2] * (S)RS2};
+      S Na[6];
+      N_apply<S>(nd, ndr, a, Na);
 #pragma unroll
       for (int I = 0; I < 6; ++I) { eL[I] = e[I] - c2 * Na[I]; eR[I] = e[I] + c1 * Na[I]; }
       if (lvl < K) {
@@ -718,24 +823,24 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
       }
     }
     // leaves 2m (phase 1) and 2m + 1 (phase 2), condensed by their bottom laminate
-    Sub<T> res;
+    Sub<T, S> res;
     {
       const int node = nbottom + m - 1;
-      double z[6], g, sL[6], sR[6];
+      S z[6], g, sL[6], sR[6];
       LeafTan<T> DL, DR;
-      load_z(t, P, 2 * m, 0, z);
-      leaf_iso<T>(t.ph[0], eL, z, sL, &DL, nullptr, gap_min ? &g : nullptr);
+      load_z<S>(t, P, 2 * m, 0, z);
+      leaf_iso<T, S>(t.ph[0], eL, z, sL, &DL, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
-      load_z(t, P, 2 * m + 1, 1, z);
-      leaf_iso<T>(t.ph[1], eR, z, sR, &DR, nullptr, gap_min ? &g : nullptr);
+      load_z<S>(t, P, 2 * m + 1, 1, z);
+      leaf_iso<T, S>(t.ph[1], eR, z, sR, &DR, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
-      double nd[3];
+      S nd[3];
       T nt[3];
-      load_n<T>(P, node, nd, nt);
+      load_ns<T, S>(P, node, nd, nt);
       T* gp = STORE ? gh.q + (size_t)(21 * node) * gh.s : nullptr;
-      condense_bottom<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node),
-                                node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2, t.ph[0].kind == 0,
-                                t.ph[1].kind == 0);
+      condense_bottom<T, STORE, S>(nd, nt, PassIn<S>::c1(t, node), PassIn<S>::c2(t, node), PassIn<S>::sc(t, node),
+                                   node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2, t.ph[0].kind == 0,
+                                   t.ph[1].kind == 0);
     }
     // condense upwards while the finished laminate is a right child
     int lvl = K, idx = m;
@@ -745,20 +850,20 @@ __device__ void tree_pass(const TreeDev& t, const double Eloc[6], const PointArr
       idx >>= 1;
       --lvl;
       const int node = (1 << (lvl - 1)) + idx - 1;
-      double nd[3];
+      S nd[3];
       T nt[3];
-      load_n<T>(P, node, nd, nt);
+      load_ns<T, S>(P, node, nd, nt);
       T* gp = STORE ? gh.q + (size_t)(21 * node) * gh.s : nullptr;
-      const Sub<T> B = res;
-      condense<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node), node_c<T>(t, node),
-                         pend[lvl + 1], B, res, gp, gh.s, r2);
+      const Sub<T, S> B = res;
+      condense<T, STORE, S>(nd, nt, PassIn<S>::c1(t, node), PassIn<S>::c2(t, node), PassIn<S>::sc(t, node),
+                            node_c<T>(t, node), pend[lvl + 1], B, res, gp, gh.s, r2);
     }
   }
 }
 
 // Tangent and stress of one leaf as a subtree result (no inner jumps).
-template <typename T>
-__device__ __forceinline__ void leaf_sub(const LeafTan<T>& D, const double sig[6], Sub<T>& s) {
+template <typename T, typename S = double>
+__device__ __forceinline__ void leaf_sub(const LeafTan<T>& D, const S sig[6], Sub<T, S>& s) {
 #pragma unroll
   for (int I = 0; I < 6; ++I) { s.sb[I] = sig[I]; s.ds[I] = (T)0; }
 #pragma unroll
@@ -772,14 +877,15 @@ __device__ __forceinline__ void leaf_sub(const LeafTan<T>& D, const double sig[6
     }
 }
 
-__device__ __forceinline__ void load_z_slot(const PointArrays& P, int slot, double z[6]) {
+template <typename S>
+__device__ __forceinline__ void load_z_slot(const PointArrays& P, int slot, S z[6]) {
   if (slot >= 0) {
     const double* b = P.z + (size_t)(6 * slot) * P.zs;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) z[c] = b[c * P.zs];
+    for (int c = 0; c < 6; ++c) z[c] = cvt<S>(b[c * P.zs]);
   } else {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) z[c] = 0.0;
+    for (int c = 0; c < 6; ++c) z[c] = (S)0;
   }
 }
 
@@ -788,19 +894,21 @@ __device__ __forceinline__ void load_z_slot(const PointArrays& P, int slot, doub
 // the scratch and the state).  Same arithmetic per laminate and leaf; a leaf
 // whose sibling is a laminate enters the condensation as a subtree with the
 // leaf's tangent, two sibling leaves use the structured bottom condensation.
-template <typename T, bool STORE>
-__device__ void tree_pass_c(const TreeDev& t, const double Eloc[6], const PointArrays& P, GH<T> gh, bool apply,
-                            T step, Sub<T>& root, double& r2, double* gap_min) {
-  double epsR[KMAX + 1][6];
+template <typename T, bool STORE, typename S = double>
+__device__ void tree_pass_c(const TreeDev& t, const S Eloc[6], const PointArrays& P, GH<T> gh, bool apply, T step,
+                            Sub<T, S>& root, S& r2, typename NoDeduce<S>::type* gap_min) {
+  S epsR[KMAX + 1][6];
   T depsR[KMAX + 1][6];
-  Sub<T> pend[KMAX + 1];
-  r2 = 0.0;
+  Sub<T, S> pend[KMAX + 1];
+  r2 = (S)0;
+  S* const a_in = PassIn<S>::a(P);
+  S* const a_wr = PassIn<S>::a_out(P);
   int ipre = 0, ipost = 0;
   for (int l = 0; l < t.Lc;) {
     const int4 f = __ldg(t.lf + l);
     const bool pair = f.w & 1;
     int d = f.x;
-    double e[6];
+    S e[6];
     T de[6];
     if (l == 0) {
 #pragma unroll
@@ -811,12 +919,12 @@ __device__ void tree_pass_c(const TreeDev& t, const double Eloc[6], const PointA
     }
     for (int s = 0; s < f.y; ++s, ++d) {
       const int node = __ldg(t.pre + ipre++);
-      double nd[3];
+      S nd[3];
       T nt[3];
-      load_n<T>(P, node, nd, nt);
-      const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
-      const double* ap = P.a + (size_t)(3 * node) * P.as;
-      double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
+      load_ns<T, S>(P, node, nd, nt);
+      const S c1 = PassIn<S>::c1(t, node), c2 = PassIn<S>::c2(t, node);
+      const S* ap = a_in + (size_t)(3 * node) * P.as;
+      S a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
       T da[3] = {(T)0, (T)0, (T)0};
       if (STORE) {
         const T* gp = gh.p + (size_t)(21 * node) * gh.s;
@@ -827,13 +935,13 @@ __device__ void tree_pass_c(const TreeDev& t, const double Eloc[6], const PointA
           for (int I = 0; I < 6; ++I) v += gp[(3 + 6 * c + I) * gh.s] * de[I];
           da[c] = apply ? v : (T)0;
         }
-        double* aw = P.a_out + (size_t)(3 * node) * P.as;
+        S* aw = a_wr + (size_t)(3 * node) * P.as;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) { a[c] += widen(da[c]); aw[c * P.as] = a[c]; }
+        for (int c = 0; c < 3; ++c) { a[c] += cvt<S>(da[c]); aw[c * P.as] = a[c]; }
       }
-      const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
-      double Na[6];
-      N_apply<double>(nd, ndr, a, Na);
+      const S ndr[3] = {nd[0] * (S)RS2, nd[1] * (S)RS2, nd[2] * (S)RS2};
+      S Na[6];
+      N_apply<S>(nd, ndr, a, Na);
       T dR[6];
       if (STORE && !(pair && s == f.y - 1)) {   // children that are laminates need strain corrections
         const NodeC<T> cc = node_c<T>(t, node);
@@ -853,51 +961,51 @@ __device__ void tree_pass_c(const TreeDev& t, const double Eloc[6], const PointA
         e[I] = e[I] - c2 * Na[I];
       }
     }
-    Sub<T> res;
+    Sub<T, S> res;
     int nup;
     const int ph0 = lf_phase(f.w);
-    double z[6], g;
+    S z[6], g;
     if (pair) {
       const int4 f2 = __ldg(t.lf + l + 1);
       const int ph1 = lf_phase(f2.w);
-      double sL[6], sR[6];
+      S sL[6], sR[6];
       LeafTan<T> DL, DR;
-      load_z_slot(P, lf_slot(f.w), z);
-      leaf_iso<T>(t.ph[ph0], e, z, sL, &DL, nullptr, gap_min ? &g : nullptr);
+      load_z_slot<S>(P, lf_slot(f.w), z);
+      leaf_iso<T, S>(t.ph[ph0], e, z, sL, &DL, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
-      load_z_slot(P, lf_slot(f2.w), z);
-      leaf_iso<T>(t.ph[ph1], epsR[d], z, sR, &DR, nullptr, gap_min ? &g : nullptr);
+      load_z_slot<S>(P, lf_slot(f2.w), z);
+      leaf_iso<T, S>(t.ph[ph1], epsR[d], z, sR, &DR, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
       const int node = __ldg(t.post + ipost++);
-      double nd[3];
+      S nd[3];
       T nt[3];
-      load_n<T>(P, node, nd, nt);
+      load_ns<T, S>(P, node, nd, nt);
       T* gp = STORE ? gh.q + (size_t)(21 * node) * gh.s : nullptr;
-      condense_bottom<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node),
-                                node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2, t.ph[ph0].kind == 0,
-                                t.ph[ph1].kind == 0);
+      condense_bottom<T, STORE, S>(nd, nt, PassIn<S>::c1(t, node), PassIn<S>::c2(t, node), PassIn<S>::sc(t, node),
+                                   node_c<T>(t, node), sL, DL, sR, DR, res, gp, gh.s, r2, t.ph[ph0].kind == 0,
+                                   t.ph[ph1].kind == 0);
       --d;
       nup = f2.z - 1;
       l += 2;
     } else {
-      double sg[6];
+      S sg[6];
       LeafTan<T> D;
-      load_z_slot(P, lf_slot(f.w), z);
-      leaf_iso<T>(t.ph[ph0], e, z, sg, &D, nullptr, gap_min ? &g : nullptr);
+      load_z_slot<S>(P, lf_slot(f.w), z);
+      leaf_iso<T, S>(t.ph[ph0], e, z, sg, &D, nullptr, gap_min ? &g : nullptr);
       if (gap_min) *gap_min = fmin(*gap_min, g);
-      leaf_sub<T>(D, sg, res);
+      leaf_sub<T, S>(D, sg, res);
       nup = f.z;
       l += 1;
     }
     for (int u = 0; u < nup; ++u) {
       const int node = __ldg(t.post + ipost++);
-      double nd[3];
+      S nd[3];
       T nt[3];
-      load_n<T>(P, node, nd, nt);
+      load_ns<T, S>(P, node, nd, nt);
       T* gp = STORE ? gh.q + (size_t)(21 * node) * gh.s : nullptr;
-      const Sub<T> B = res;
-      condense<T, STORE>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node), node_c<T>(t, node),
-                         pend[d], B, res, gp, gh.s, r2);
+      const Sub<T, S> B = res;
+      condense<T, STORE, S>(nd, nt, PassIn<S>::c1(t, node), PassIn<S>::c2(t, node), PassIn<S>::sc(t, node),
+                            node_c<T>(t, node), pend[d], B, res, gp, gh.s, r2);
       --d;
     }
     if (d == 0) root = res;

@@ -17,7 +17,8 @@ _lib = None
 
 # ABI symbols declared in include/dmn.h
 EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_interp_orientation", "dmn_update",
-           "dmn_set_params", "dmn_grad", "dmn_profile_enable", "dmn_profile_read", "dmn_update_noalloc",
+           "dmn_set_params", "dmn_grad", "dmn_profile_enable", "dmn_profile_read", "dmn_profile_read_stages",
+           "dmn_update_noalloc",
            "dmn_update_host", "dmn_last_error")
 
 PHASE_ELASTIC, PHASE_J2_LINEAR, PHASE_J2_EXPLIN = 0, 1, 2
@@ -44,7 +45,7 @@ class TreeDesc_(ctypes.Structure):
 class Options_(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("line_search", ctypes.c_int32),
-                ("predictor", ctypes.c_int32)]
+                ("predictor", ctypes.c_int32), ("first_stage", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -85,6 +86,9 @@ def load_library(build_if_missing: bool = True):
     lib.dmn_profile_enable.restype = ctypes.c_int
     lib.dmn_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.dmn_profile_read.restype = ctypes.c_int
+    lib.dmn_profile_read_stages.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                            ctypes.POINTER(i64)]
+    lib.dmn_profile_read_stages.restype = ctypes.c_int
     lib.dmn_update_noalloc.argtypes = [ctypes.POINTER(TreeDesc_), ctypes.POINTER(Options_), i64,
                                        vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.dmn_update_noalloc.restype = ctypes.c_int
@@ -233,10 +237,13 @@ class DMN:
     sweep); "mixed-f32-tangent" (the mixed iteration, tangent from its last
     FP32 condensation).  predictor: start each Newton iteration from the last update's jumps
     extrapolated along the new strain increment (the state then holds the last jump change
-    and strain increment too).  The other options are those of dmn_options."""
+    and strain increment too).  first_stage (mixed forms): True (default) starts every point
+    with the all-FP32 Newton stage, False goes straight to the FP64-residual iteration.  The
+    other options are those of dmn_options."""
 
     def __init__(self, tree, precision: str = "f64", tol: float = 1e-12, max_iter: int = 50, block: int = 0,
-                 ctas_per_sm: int = 0, line_search: bool = False, predictor: bool = False):
+                 ctas_per_sm: int = 0, line_search: bool = False, predictor: bool = False,
+                 first_stage: bool = True):
         import torch
         self._lib = load_library()
         if not torch.cuda.is_available():
@@ -256,8 +263,9 @@ class DMN:
         if precision not in PRECISIONS:
             raise ValueError("precision must be one of %s" % (tuple(PRECISIONS),))
         opt = Options_(float(tol), int(max_iter), PRECISIONS[precision], int(block),
-                       int(ctas_per_sm), int(bool(line_search)), int(bool(predictor)))
+                       int(ctas_per_sm), int(bool(line_search)), int(bool(predictor)), 0 if first_stage else -1)
         self.precision = precision
+        self.first_stage = bool(first_stage) and precision != "f64" and not line_search and not predictor
         self.predictor = bool(predictor)
         h = ctypes.c_void_p()
         rc = self._lib.dmn_create(descs, len(trees), ctypes.byref(opt), ctypes.byref(h))
@@ -384,6 +392,19 @@ class DMN:
         if rc != 0:
             self._err("dmn_profile_read", rc)
         return dict(normals=ms[0], newton=ms[1], final=ms[2]), int(cnt.value)
+
+    def profile_read_stages(self):
+        """(ms of the normals, first-stage, Newton and final kernels, tree passes of the first stage and of
+        the Newton kernel, number of updates), summed over the timed updates."""
+        ms = (ctypes.c_double * 4)()
+        ps = (ctypes.c_int64 * 2)()
+        cnt = ctypes.c_int64()
+        with self._on_device():
+            rc = self._lib.dmn_profile_read_stages(self._h, ms, ps, ctypes.byref(cnt))
+        if rc != 0:
+            self._err("dmn_profile_read_stages", rc)
+        return (dict(normals=ms[0], stage=ms[1], newton=ms[2], final=ms[3]),
+                dict(stage=int(ps[0]), newton=int(ps[1])), int(cnt.value))
 
     def alloc_outputs(self, n, device):
         import torch

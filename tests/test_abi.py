@@ -118,6 +118,17 @@ def test_predictor_option_is_checked_without_touching_the_gpu():
     assert rc == -1 and "extrapolated start" in lib.dmn_last_error(None).decode()
 
 
+def test_first_stage_option_is_checked_without_touching_the_gpu():
+    lib = dmn.load_library()
+    d, keep = _desc()
+    for bad in (2, -2):
+        h = ctypes.c_void_p(123)
+        o = dmn.Options_(1e-12, 50, dmn.PREC_MIXED, 0, 0, 0, 0, bad)
+        assert lib.dmn_create(ctypes.byref(d), 1, ctypes.byref(o), ctypes.byref(h)) == -1
+        assert h.value is None and "first_stage must be -1, 0 or 1" in lib.dmn_last_error(None).decode()
+    assert [f[0] for f in dmn.Options_._fields_][-1] == "first_stage"
+
+
 def _noalloc(d, o, n=8, arrays=None):
     lib = dmn.load_library()
     arrays = arrays if arrays is not None else [None] * 10

@@ -80,3 +80,21 @@ def test_roofline_arithmetic():
     f32 = (iters / steps + n) * (127 * 717 + 128 * 595) + iters / steps * 255 * 39
     t_bound = f64 / (peak * 1e9) + f32 / (152 * 128 * 2 * 2.07 * 1e9)
     assert abs(mx["frac"] - t_bound / 1.2456054931640624) <= 1e-9 * mx["frac"]
+    # with the all-FP32 first stage: the Newton kernel's corrections from its pass counter, the stage's
+    # flops (every part of its passes in FP32) against the FP32 peak
+    rs = dict(r, passes={"stage": int(3.4 * n * steps), "newton": int(2.4 * n * steps)},
+              kms={"newton": 600.0 * steps, "stage": 80.0 * steps, "final": 22.67 * steps})
+    ms = bench.roofline_mixed(rs, n, steps, sweep=True)
+    cn = 1.4 * n
+    f64 = (cn + n) * 31548 + cn * 255 * 3
+    f32 = (cn + n) * (127 * 717 + 128 * 595) + cn * 255 * 39
+    t_bound = f64 / (peak * 1e9) + f32 / (152 * 128 * 2 * 2.07 * 1e9)
+    assert abs(ms["frac"] - t_bound / 0.6) <= 1e-6 * ms["frac"]
+    assert abs(ms["passes_per_update"] - 2.4) <= 1e-9
+    cs = 2.4 * n
+    fs = (cs + n) * (31548 + 127 * 717 + 128 * 595) + cs * (255 * 3 + 255 * 39)
+    st = ms["stage_kernel"]
+    assert abs(st["flops_per_launch"] - fs) <= 1e-6 * fs
+    assert st["peak"] == 152 * 128 * 2 * 2.07 and abs(st["achieved"] - fs / 0.08 / 1e9) <= 1e-6 * st["achieved"]
+    assert bench.form_stage("mixed") and not bench.form_stage("mixed/no-stage")
+    assert not bench.form_stage("f64") and not bench.form_stage("mixed/extrap")

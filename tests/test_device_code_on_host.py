@@ -40,6 +40,7 @@ HARNESS = r'''
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 using std::isfinite;
 struct int4 { int x, y, z, w; };
@@ -50,6 +51,7 @@ inline long long __double_as_longlong(double d) { long long v; std::memcpy(&v, &
 inline float __uint_as_float(unsigned u) { float f; std::memcpy(&f, &u, 4); return f; }
 inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f, 4); return u; }
 inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
+inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
 #include "dmn_device.cuh"
 using namespace dmn;
 
@@ -73,6 +75,9 @@ static PhaseDev make_phase(const double* r) {
   o.lamf = (float)o.lam; o.Gf = (float)o.G;
   o.inv_den = 1.0 / (2.0 * o.G + 2.0 * H / 3.0);
   o.thb0 = 1.0 / (1.0 + H / (3.0 * o.G));
+  o.f.K = (float)o.K; o.f.G = (float)o.G; o.f.s0 = (float)o.s0; o.f.H = (float)o.H; o.f.lam = (float)o.lam;
+  o.f.inv_den = (float)o.inv_den; o.f.thb0 = (float)o.thb0;
+  o.f.ds = (float)o.ds; o.f.dk = (float)o.dk; o.f.rate = (float)o.rate;
   return o;
 }
 
@@ -102,7 +107,7 @@ struct Tree {
         const int j = L - (1 << k) + (i - 1), hn = (1 << (k - 1)) + i - 2;
         for (int m = 0; m < M; ++m) { hp[hn * M + m] = p[j * M + m]; hq[hn * M + m] = q[j * M + m]; }
       }
-    c.resize(3 * N + L); cf.resize(3 * N);
+    c.resize(3 * N + L); cf.resize(4 * N);
     std::vector<double> Wsub(N);
     double s = 0.0;
     for (int l = 0; l < L; ++l) s += w[l];
@@ -114,11 +119,12 @@ struct Tree {
       const double c1 = wl / (wl + wr), c2 = 1.0 - c1;
       c[h - 1] = c1; c[N + h - 1] = c2; c[2 * N + h - 1] = Wsub[h - 1] * c1 * c2;
       cf[h - 1] = (float)c1; cf[N + h - 1] = (float)c2; cf[2 * N + h - 1] = (float)(c1 * c2);
+      cf[3 * N + h - 1] = (float)c[2 * N + h - 1];
     }
     for (int l = 0; l < L; ++l) c[3 * N + l] = w[l] / s;
     t.p = hp.data(); t.q = hq.data();
     t.c1 = c.data(); t.c2 = c.data() + N; t.sc = c.data() + 2 * N; t.wl = c.data() + 3 * N;
-    t.c1f = cf.data(); t.c2f = cf.data() + N; t.c12f = cf.data() + 2 * N;
+    t.c1f = cf.data(); t.c2f = cf.data() + N; t.c12f = cf.data() + 2 * N; t.scf = cf.data() + 3 * N;
     t.wsum = s;
     S = 6L * t.nz + 3L * N;
   }
@@ -142,7 +148,7 @@ struct Tree {
       }
     const int Nc = (int)paper.size();
     hp.assign((size_t)std::max(Nc, 1) * M, 0.0); hq.assign((size_t)std::max(Nc, 1) * M, 0.0);
-    c.assign(3 * (size_t)Nc + L, 0.0); cf.assign(3 * (size_t)std::max(Nc, 1), 0.0f);
+    c.assign(3 * (size_t)Nc + L, 0.0); cf.assign(4 * (size_t)std::max(Nc, 1), 0.0f);
     for (int k = 0; k < Nc; ++k)
       for (int m = 0; m < M; ++m) { hp[k * M + m] = p[paper[k] * M + m]; hq[k * M + m] = q[paper[k] * M + m]; }
     for (int h = 1; h <= N; ++h) {
@@ -151,6 +157,7 @@ struct Tree {
       const double c1 = Wh[2 * h] / Wh[h], c2 = 1.0 - c1;
       c[k] = c1; c[Nc + k] = c2; c[2 * Nc + k] = Wh[h] * c1 * c2;
       cf[k] = (float)c1; cf[Nc + k] = (float)c2; cf[2 * Nc + k] = (float)(c1 * c2);
+      cf[3 * Nc + k] = (float)c[2 * Nc + k];
     }
     for (int l = 0; l < L; ++l) c[3 * Nc + l] = Wh[N + 1 + l];
     std::vector<int> lf, pre, post;
@@ -200,7 +207,7 @@ struct Tree {
     t.hcid = t.kid + 2 * Nc;
     t.p = hp.data(); t.q = hq.data();
     t.c1 = c.data(); t.c2 = c.data() + Nc; t.sc = c.data() + 2 * Nc; t.wl = c.data() + 3 * Nc;
-    t.c1f = cf.data(); t.c2f = cf.data() + Nc; t.c12f = cf.data() + 2 * Nc;
+    t.c1f = cf.data(); t.c2f = cf.data() + Nc; t.c12f = cf.data() + 2 * Nc; t.scf = cf.data() + 3 * Nc;
     t.wsum = s;
     S = 6L * nz + 3L * Nc;
   }
@@ -231,8 +238,11 @@ struct Tree {
 
 // sweep: the mixed form's final FP64 pass at the converged jumps gives stress and tangent
 // ls: the backtracking line search with its two buffers of jumps and of g, H (accepted / trial)
+// stage: the mixed forms' all-FP32 first stage before the Newton loop (tol32, max32: its criterion and
+// its corrections; the FP64-residual loop then starts from its jumps)
 template <typename T>
-static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double tol, bool sweep, bool ls) {
+static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double tol, bool sweep, bool ls,
+               bool stage = false, float tol32 = STAGE_TOL, int max32 = STAGE_MAX_ITER) {
   const Tree tr(in, K, M);
   const TreeDev& t = tr.t;
   const int N = tr.N;
@@ -253,6 +263,31 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
     A.nrm = nrm.data(); A.ns = 1; A.nrmf = nrmf.data();
     A.as = 1; A.paper = !tr.cmp;
     A.z = st.data() + pt; A.zs = (size_t)n;
+    int it32 = 0;
+    if (stage) {   // the stage kernel's loop for one point: FP32 jumps, strains, stresses and residual
+      std::vector<float> af(3 * N), g32(21 * N);
+      for (int k = 0; k < 3 * N; ++k) af[k] = narrow_rn(abuf[0][k]);
+      float E32[6];
+      for (int I = 0; I < 6; ++I) E32[I] = narrow_rn(Eloc[I]);
+      A.af = af.data(); A.af_out = af.data();
+      bool first32 = true, bad = false;
+      for (;;) {
+        GH<float> gh{g32.data(), 1, g32.data()};
+        Sub<float, float> r32;
+        float r2;
+        if (tr.cmp) tree_pass_c<float, true, float>(t, E32, A, gh, !first32, 1.0f, r32, r2, nullptr);
+        else tree_pass<float, true, float>(t, E32, A, gh, !first32, 1.0f, r32, r2, nullptr);
+        first32 = false;
+        float sn2 = 0.0f;
+        for (int I = 0; I < 6; ++I) sn2 += r32.sb[I] * r32.sb[I];
+        const float rn = std::sqrt(r2), sn = std::sqrt(sn2);
+        if (!std::isfinite(rn) || !std::isfinite(sn)) { bad = true; break; }
+        if (rn <= tol32 * (float)N * sn || it32 >= max32) break;
+        ++it32;
+      }
+      if (bad) it32 = 0;   // the FP64-residual loop starts from a^n
+      else for (int k = 0; k < 3 * N; ++k) abuf[0][k] = widen(af[k]);
+    }
     // the persistent kernel's Newton loop for one point
     int it = 0, stt = -1, halvings = 0;
     bool first = true;
@@ -278,14 +313,14 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
       first = false;
       if (!std::isfinite(rn) || !std::isfinite(sn)) stt = 2;
       else if (rn <= tol * (double)N * sn) stt = 0;
-      else if (it >= max_iter) stt = 1;
+      else if (it >= max_iter - it32) stt = 1;
       if (stt < 0) { ++it; continue; }
       break;
     }
     A.a = abuf[cur].data();
     A.a_out = A.a;
     std::vector<double>& a = abuf[cur];
-    iters[pt] = it; status[pt] = stt;
+    iters[pt] = it + it32; status[pt] = stt;
     double Cl[6][6], sl[6];
     if (sweep) {
       Sub<double> fin;
@@ -441,15 +476,19 @@ int main(int argc, char** argv) {
   FILE* in = argc == 3 ? fopen(argv[1], "rb") : nullptr;
   FILE* out = argc == 3 ? fopen(argv[2], "wb") : nullptr;
   if (argc != 3 || !in || !out) return 2;
-  double hdr[6];
-  rd(hdr, 6, in);
+  double hdr[8];
+  rd(hdr, 8, in);   // hdr[6], hdr[7] > 0: the first stage's criterion and corrections (else the library's)
   const int K = (int)hdr[0], M = (int)hdr[1], mode = (int)hdr[3], max_iter = (int)hdr[4];
   const long n = (long)hdr[2];
   // mode: 0 FP64, 1 mixed with the FP32 tangent, 2 mixed with the FP64 final sweep, 3 adjoint (FP64),
-  //       4 FP64 with the line search, 5 adjoint of the tangent (elastic phases)
+  //       4 FP64 with the line search, 5 adjoint of the tangent (elastic phases),
+  //       6 / 7 modes 1 / 2 after the all-FP32 first stage
+  const float tol32 = hdr[6] > 0.0 ? (float)hdr[6] : STAGE_TOL;
+  const int max32 = hdr[7] > 0.0 ? (int)hdr[7] : std::max(0, std::min(STAGE_MAX_ITER, max_iter - 1));
   const int rc = mode == 0 || mode == 4 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false, mode == 4)
                : mode == 3 ? run_grad(in, out, K, M, n)
                : mode == 5 ? run_grad_tangent(in, out, K, M, n)
+               : mode >= 6 ? run<float>(in, out, K, M, n, max_iter, hdr[5], mode == 7, false, true, tol32, max32)
                            : run<float>(in, out, K, M, n, max_iter, hdr[5], mode == 2, false);
   fclose(in); fclose(out);
   return rc;
@@ -471,11 +510,11 @@ def harness(tmp_path_factory):
     return str(exe), d
 
 
-def run_harness(harness, tree, lam, Q, En, dE, state, prec, max_iter=50):
+def run_harness(harness, tree, lam, Q, En, dE, state, prec, max_iter=50, tol32=0.0, max32=0):
     exe, d = harness
     n = lam.shape[0]
     rows = [oracle.phases_array(tree.phases).ravel()]
-    hdr = np.array([tree.K, tree.M, n, prec, max_iter, 1e-12], dtype=np.float64)
+    hdr = np.array([tree.K, tree.M, n, prec, max_iter, 1e-12, tol32, max32], dtype=np.float64)
     blob = np.concatenate([hdr, np.ravel(tree.p), np.ravel(tree.q), np.ravel(tree.w), rows[0],
                            lam.ravel(), Q.ravel(), En.ravel(), dE.ravel(), state.ravel()]).astype(np.float64)
     fin, fout = d / "in.bin", d / "out.bin"
@@ -505,7 +544,10 @@ PHASE_SETS = {"linear": (W.FIBER, W.MATRIX), "explin": (W.FIBER, W.MATRIX_EXPLIN
 
 @pytest.mark.parametrize("K,M,matrix,prec", [(4, 3, "linear", 0), (6, 3, "explin", 0), (5, 6, "linear", 0),
                                              (6, 3, "linear", 1), (6, 3, "explin", 2), (5, 3, "both-inelastic", 0),
-                                             (5, 3, "inelastic-left", 0), (5, 3, "both-inelastic", 1)])
+                                             (5, 3, "inelastic-left", 0), (5, 3, "both-inelastic", 1),
+                                             # the mixed forms after the all-FP32 first stage
+                                             (6, 3, "linear", 6), (6, 3, "explin", 7), (5, 3, "both-inelastic", 7),
+                                             (5, 6, "inelastic-left", 6)])
 def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
     phases = PHASE_SETS[matrix]
     tree = (W.tree_d10_fit(K, seed=30 + K, phases=phases) if M == 3
@@ -515,7 +557,7 @@ def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
     Ef = W.random6_path_final(n, 0.03, seed=50 + K)
     S = W.state_size(K, tree.phases)
     sh, so = np.zeros((S, n)), np.zeros((S, n))
-    tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6)}[prec]
+    tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6), 6: (1e-6, 1e-4), 7: (1e-6, 1e-6)}[prec]
     alive = np.ones(n, dtype=bool)
     for s in range(1, 9):
         En, dE = W.proportional_increment(Ef, s, 20)
@@ -535,7 +577,7 @@ def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
 def run_grad_harness(harness, tree, lam, Q, En, dE, state_in, state_out, g):
     exe, d = harness
     n = lam.shape[0]
-    hdr = np.array([tree.K, tree.M, n, 3, 0, 0.0], dtype=np.float64)
+    hdr = np.array([tree.K, tree.M, n, 3, 0, 0.0, 0.0, 0.0], dtype=np.float64)
     blob = np.concatenate([hdr, np.ravel(tree.p), np.ravel(tree.q), np.ravel(tree.w),
                            oracle.phases_array(tree.phases).ravel(), lam.ravel(), Q.ravel(), En.ravel(), dE.ravel(),
                            state_in.ravel(), state_out.ravel(), g.ravel()]).astype(np.float64)
@@ -608,7 +650,7 @@ def test_device_line_search_matches_the_oracle(harness):
     assert differs > 0          # the search was active on this path
 
 
-@pytest.mark.parametrize("K,prec", [(5, 0), (7, 0), (7, 1), (7, 2)])
+@pytest.mark.parametrize("K,prec", [(5, 0), (7, 0), (7, 1), (7, 2), (7, 6), (7, 7)])
 def test_device_compressed_traversal_matches_the_oracle(harness, K, prec):
     """Trees with weightless leaves, walked by the compression tables (restated in the harness from
     their documented format), against the oracle's compression."""
@@ -619,7 +661,7 @@ def test_device_compressed_traversal_matches_the_oracle(harness, K, prec):
     S = oracle.state_size(K, tree.phases, tree.w)
     assert S < W.state_size(K)
     sh, so = np.zeros((S, n)), np.zeros((S, n))
-    tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6)}[prec]
+    tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6), 6: (1e-6, 1e-4), 7: (1e-6, 1e-6)}[prec]
     alive = np.ones(n, dtype=bool)
     for s in range(1, 9):
         En, dE = W.proportional_increment(Ef, s, 20)
@@ -673,7 +715,7 @@ def test_device_tangent_adjoint_matches_the_oracle(harness, K, compressed):
     A2, lam, Q = W.orientation_field(n, seed=111 + K)
     G = np.random.default_rng(112 + K).standard_normal((n, 36))
     exe, d = harness
-    hdr = np.array([K, tree.M, n, 5, 0, 0.0], dtype=np.float64)
+    hdr = np.array([K, tree.M, n, 5, 0, 0.0, 0.0, 0.0], dtype=np.float64)
     blob = np.concatenate([hdr, np.ravel(tree.p), np.ravel(tree.q), np.ravel(tree.w),
                            oracle.phases_array(tree.phases).ravel(), lam.ravel(), Q.ravel(), G.ravel()])
     fin, fout = d / "gt_in.bin", d / "gt_out.bin"

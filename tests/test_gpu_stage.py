@@ -1,0 +1,118 @@
+"""The mixed forms' all-FP32 first stage, through the C ABI, against the oracle.
+
+The stage runs Sec. 3.2's Newton iteration with every quantity in FP32 until its own residual is
+small, and the FP64-residual iteration of the mixed forms continues from its jumps to the FP64
+criterion.  So the results must meet the mixed forms' tolerances against the FP64 oracle (stress
+<= 1e-6, tangent <= 1e-6 with the FP64 final sweep) on plastic paths, on full and compressed trees,
+and agree with the same forms without the stage to the accuracy the common FP64 criterion leaves.
+The pass counters must show the FP64-residual passes that the stage saves.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2103_08253_gb300 import dmn, workloads as W
+from test_gpu_parity import d, rel, run_path
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("prec,matrix", [("mixed", "linear"), ("mixed-f32-tangent", "linear"), ("mixed", "explin")])
+def test_first_stage_matches_the_oracle_at_depth_8(prec, matrix):
+    phases = (W.FIBER, W.MATRIX_EXPLIN if matrix == "explin" else W.MATRIX)
+    tree = W.tree_d10_fit(8, seed=301, phases=phases)
+    n = 192
+    A2, lam, Q = W.orientation_field(n, seed=302)
+    Ef = W.random6_path_final(n, 0.03, seed=303)
+    worst, out, _ = run_path(tree, lam, Q, Ef, 20, prec, upto=8, first_stage=True)
+    assert worst["stress"] <= 1e-6
+    assert worst["tangent"] <= (1e-6 if prec == "mixed" else 1e-4)
+    assert worst["state"] <= 1e-5
+
+
+def test_first_stage_on_a_compressed_tree():
+    tree = W.tree_with_zero_weights(7, seed=311)
+    n = 160
+    A2, lam, Q = W.orientation_field(n, seed=312)
+    Ef = W.random6_path_final(n, 0.03, seed=313)
+    S = W.state_size(tree.K, tree.phases)
+    m_on = dmn.DMN(tree, precision="mixed")
+    m_off = dmn.DMN(tree, precision="mixed", first_stage=False)
+    assert m_on.first_stage and not m_off.first_stage
+    import oracle
+    S = oracle.state_size(tree.K, tree.phases, tree.w)
+    st_on = torch.zeros((m_on.state_size, n), dtype=torch.float64, device=DEV)
+    st_off = st_on.clone()
+    st_o = np.zeros((S, n))
+    for s in range(1, 9):
+        En, dE = W.proportional_increment(Ef, s, 20)
+        a = m_on.update(d(lam), d(Q), d(En), d(dE), st_on)
+        b = m_off.update(d(lam), d(Q), d(En), d(dE), st_off)
+        st_o, sig_o, C_o, it_o, stat_o, gap = oracle.update(tree, lam, Q, En, dE, st_o)
+        st_on, st_off = a["state_out"], b["state_out"]
+        ok = (stat_o == 0) & (a["status"].cpu().numpy() == 0)
+        assert ok.mean() > 0.95
+        assert rel(a["stress"].cpu().numpy()[ok], sig_o[ok]).max() <= 1e-6
+        tie = gap < 1e-9
+        assert rel(a["tangent"].cpu().numpy()[ok & ~tie], C_o[ok & ~tie]).max() <= 1e-6
+        # the same fixed point as the mixed iteration without the stage, to its stopping criterion
+        assert rel(a["stress"].cpu().numpy()[ok], b["stress"].cpu().numpy()[ok]).max() <= 1e-8
+    m_on.close()
+    m_off.close()
+
+
+def test_first_stage_saves_fp64_passes_and_the_counters_add_up():
+    """Profiling counters: with the stage the Newton kernel runs fewer FP64-residual passes; the stage's
+    and the Newton kernel's passes per point are each (corrections + 1), their corrections add up to
+    the iteration counts; without the stage (or in the FP64 form) the stage counter stays zero."""
+    tree = W.tree_d10_fit(8, seed=321)
+    n = 4096
+    A2, lam, Q = W.orientation_field(n, seed=322)
+    Ef = W.random6_path_final(n, 0.03, seed=323)
+    res = {}
+    for key, prec, stage in (("on", "mixed", True), ("off", "mixed", False), ("f64", "f64", True)):
+        m = dmn.DMN(tree, precision=prec, first_stage=stage)
+        st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+        for s in range(1, 6):
+            En, dE = W.proportional_increment(Ef, s, 20)
+            st = m.update(d(lam), d(Q), d(En), d(dE), st)["state_out"]
+        En, dE = W.proportional_increment(Ef, 6, 20)
+        m.profile(True)
+        out = m.update(d(lam), d(Q), d(En), d(dE), st)
+        ms, passes, upd = m.profile_read_stages()
+        m.profile(False)
+        assert upd == 1
+        assert (out["status"] == 0).all()
+        it = int(out["iters"].to(torch.int64).sum().item())
+        if key == "on":
+            assert ms["stage"] > 0.0 and passes["stage"] >= n
+            # corrections of both kernels = the reported iterations
+            assert (passes["stage"] - n) + (passes["newton"] - n) == it
+        else:
+            assert passes["stage"] == 0
+            assert passes["newton"] - n == it
+        res[key] = (passes, it, out["stress"].cpu().numpy())
+        m.close()
+    assert res["on"][0]["newton"] < 0.75 * res["off"][0]["newton"]
+    assert rel(res["on"][2], res["f64"][2]).max() <= 1e-8
+
+
+def test_first_stage_within_max_iter():
+    """With a small max_iter the stage's corrections count against it: no point reports more."""
+    tree = W.tree_d10_fit(6, seed=331)
+    n = 512
+    A2, lam, Q = W.orientation_field(n, seed=332)
+    Ef = W.random6_path_final(n, 0.03, seed=333)
+    m = dmn.DMN(tree, precision="mixed", max_iter=3)
+    st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
+    for s in range(1, 5):
+        En, dE = W.proportional_increment(Ef, s, 20)
+        out = m.update(d(lam), d(Q), d(En), d(dE), st)
+        st = out["state_out"]
+        it = out["iters"].cpu().numpy()
+        stat = out["status"].cpu().numpy()
+        assert it.max() <= 3
+        assert set(np.unique(stat)) <= {dmn.STATUS_OK, dmn.STATUS_MAXITER}
+        assert (it[stat == dmn.STATUS_MAXITER] == 3).all()
+    m.close()
