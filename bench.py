@@ -326,18 +326,21 @@ def rel_rows(a, b):
 
 
 def form_opts(form):
-    """(precision, extrapolated start) of a form name such as "f64", "mixed-f32-tangent/extrap" or
-    "mixed/no-stage" (the mixed iteration without its all-FP32 first stage)."""
+    """(precision, extrapolated start) of a form name such as "f64", "mixed-f32-tangent/extrap",
+    "mixed/no-stage" (the mixed iteration without its all-FP32 first stage) or "f64/stage" (the FP64
+    iteration after that stage)."""
     prec, _, start = form.partition("/")
-    if start not in ("", "extrap", "no-stage"):
+    if start not in ("", "extrap", "no-stage", "stage"):
         raise ValueError("unknown start in form %r" % form)
     return prec, start == "extrap"
 
 
 def form_stage(form):
-    """Whether the form runs the mixed forms' all-FP32 first stage."""
+    """Whether the form runs the all-FP32 first stage (the mixed forms' default; "/stage" in the FP64 form)."""
     prec, pred = form_opts(form)
-    return prec != "f64" and not pred and not form.endswith("/no-stage")
+    if pred or form.endswith("/no-stage"):
+        return False
+    return prec != "f64" or form.endswith("/stage")
 
 
 def tune_shape(form, ctx, args):
@@ -377,6 +380,7 @@ def run_form(form, ctx, args, dist):
     prec, pred = form_opts(form)
     m = dmn.DMN(ctx["tree"], precision=prec, block=shape["block"] if shape else 0,
                 ctas_per_sm=shape["ctas_per_sm"] if shape else 0, predictor=pred, first_stage=form_stage(form))
+    assert m.first_stage == form_stage(form)
     S = m.state_size
     st = [torch.zeros((S, n), dtype=torch.float64, device=dev), torch.zeros((S, n), dtype=torch.float64, device=dev)]
     lam = torch.empty((n, 2), dtype=torch.float64, device=dev)
@@ -506,17 +510,34 @@ def run_e2e(r, ctx, args, dist):
             "status_ok": int((out_h["status"] == 0).sum().item())}
 
 
+def stage_roofline(r, n, steps, w, P32):
+    """The all-FP32 first stage against the FP32 peak, from its pass counter and event time."""
+    npts = n * steps
+    Fs = stage_flops(K_DEPTH, r["passes"]["stage"], npts, w=w)
+    ts = r["kms"]["stage"] * 1e-3
+    return {"kernel": "k_stage32", "achieved": Fs / ts / 1e9, "peak": P32, "unit": "GFLOP/s (FP32)",
+            "frac": Fs / ts / 1e9 / P32, "flops_per_launch": Fs / steps, "launch_ms": r["kms"]["stage"] / steps,
+            "passes_per_update": r["passes"]["stage"] / npts}
+
+
 def roofline_f64(r, n, steps, w=None, peaks=None):
     pk = peaks or PEAKS_DERIVED
     P64 = pk["f64"]
-    F, _ = newton_flops(K_DEPTH, r["iters_sum"], n * steps, mixed=False, w=w)
+    npts = n * steps
+    passes = r.get("passes") or {}
+    corr = passes["newton"] - npts if passes.get("newton") else r["iters_sum"]
+    F, _ = newton_flops(K_DEPTH, corr, npts, mixed=False, w=w)
     t = r["kms"]["newton"] * 1e-3
     ach = F / t / 1e9
     tr = ncu_traffic("k_newton_f64" + ("_compressed" if w is not None and (np.asarray(w) == 0).any() else ""), n)
-    return {"bound": "alu", "kernel": "k_newton<double>", "achieved": ach, "peak": P64,
-            "unit": "GFLOP/s (FP64)", "frac": ach / P64, "traffic": tr,
-            "flops_per_launch": F / steps, "launch_ms": r["kms"]["newton"] / steps,
-            "frac_of_derived_peak": ach / PEAK_F64_GFLOPS, "peak_note": pk["note"]}
+    out = {"bound": "alu", "kernel": "k_newton<double>", "achieved": ach, "peak": P64,
+           "unit": "GFLOP/s (FP64)", "frac": ach / P64, "traffic": tr,
+           "flops_per_launch": F / steps, "launch_ms": r["kms"]["newton"] / steps,
+           "frac_of_derived_peak": ach / PEAK_F64_GFLOPS, "peak_note": pk["note"],
+           "passes_per_update": (corr + npts) / npts}
+    if "stage" in r["kms"]:
+        out["stage_kernel"] = stage_roofline(r, n, steps, w, pk["f32"])
+    return out
 
 
 def stage_flops(K, passes, npts, w=None):
@@ -551,12 +572,7 @@ def roofline_mixed(r, n, steps, w=None, sweep=True, peaks=None):
            "flops_f32_per_launch": F32 / steps, "launch_ms": r["kms"]["newton"] / steps,
            "passes_per_update": (newton_corr + npts) / npts, "final_kernel": fin}
     if "stage" in r["kms"]:
-        Fs = stage_flops(K_DEPTH, passes["stage"], npts, w=w)
-        ts = r["kms"]["stage"] * 1e-3
-        out["stage_kernel"] = {"kernel": "k_stage32", "achieved": Fs / ts / 1e9, "peak": P32,
-                               "unit": "GFLOP/s (FP32)", "frac": Fs / ts / 1e9 / P32,
-                               "flops_per_launch": Fs / steps, "launch_ms": r["kms"]["stage"] / steps,
-                               "passes_per_update": passes["stage"] / npts}
+        out["stage_kernel"] = stage_roofline(r, n, steps, w, P32)
     return out
 
 
@@ -792,7 +808,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--points", type=int, default=1 << 20)
-    ap.add_argument("--forms", default="f64,mixed,mixed-f32-tangent",
+    ap.add_argument("--forms", default="f64,mixed,mixed-f32-tangent,f64/stage",
                     help="precisions, each optionally with /extrap: the Newton iteration starts from the last "
                          "update's jumps extrapolated along the strain increment instead of the paper's a^n")
     ap.add_argument("--e2e-chunk", type=int, default=0,
@@ -919,9 +935,9 @@ def run_gpu(args):
             "gpu_launches": 4 * steps, "clocks": mr["clocks"],
             "peaks": {"fp64_gflops": peaks["f64"], "fp32_gflops": peaks["f32"], "note": peaks["note"]}}
     # the other forms side by side with the headline: value, roofline and error against the oracle
-    for form in ("mixed", "mixed-f32-tangent"):
+    for form in ("mixed", "mixed-f32-tangent", "f64/stage"):
         if form in forms_out and form != main_form:
-            key = form.replace("-", "_")
+            key = form.replace("-", "_").replace("/", "_")
             line["value_" + key] = forms_out[form]["value"]
             line["roofline_" + key] = forms_out[form]["roofline"]
             line["parity_" + key] = forms_out[form]["parity_vs_oracle"]

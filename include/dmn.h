@@ -143,15 +143,19 @@ typedef struct {
                         * (up to the stopping criterion) in fewer Newton steps on smooth load
                         * paths.  The state then carries 3 fields per laminate and 6 more (see
                         * the state layout above). */
-  int32_t first_stage; /* the mixed forms: 0 (default) or 1 starts each point's Newton iteration with an
-                        * all-FP32 stage -- jumps, strains, the leaf return mapping, the residual and the
-                        * condensation in FP32 -- until its FP32 residual meets
-                        * ||A^T W sigma|| <= 1e-8 (2^K - 1) ||sigma_bar|| or min(12, max_iter - 1)
-                        * corrections; the FP64-residual iteration above then continues from its jumps
-                        * to tol.  iters counts the corrections of both, and both together stay within
-                        * max_iter.  The FP32 passes cost a small fraction of an FP64-residual pass, so
-                        * the update needs fewer of the latter.  -1: no first stage.  Not run with
-                        * line_search or predictor, nor in the FP64 form. */
+  int32_t first_stage; /* 1 starts each point's Newton iteration with an all-FP32 stage -- jumps,
+                        * strains, the leaf return mapping, the residual and the condensation in FP32 --
+                        * until its FP32 residual meets ||A^T W sigma|| <= 1e-8 (2^K - 1) ||sigma_bar||
+                        * or min(12, max_iter - 1) corrections; the iteration of the chosen precision
+                        * then continues from its jumps to tol, so the results are those of that form
+                        * (its residual, criterion, Newton matrix and tangent; the FP64 form takes at
+                        * least one FP64 Newton step after the stage).  iters counts the
+                        * corrections of both, and both together stay within max_iter.  An FP32 pass
+                        * costs about half an FP64-residual pass, and the update needs fewer of the
+                        * latter.  0 (default): on in the mixed forms, off in the FP64 form.  -1: off.
+                        * Not run with line_search or predictor. */
+  int32_t stage_ctas_per_sm; /* resident CTAs of 128 threads per SM of the first stage's persistent kernel:
+                              * 2, 3, 4, 6 or 8 (registers capped to fit); 0 selects the default */
 } dmn_options;
 
 /* Create a handle for n_trees DMNs (1 <= n_trees <= DMN_MAX_TREES; trees may

@@ -64,6 +64,9 @@ struct WorkSet {
   double* scr_d = nullptr;      // per slot: normals [3N] + jumps [3N] (FP64)
   void* scr_t = nullptr;        // per slot: g, H [21N] (FP64 or FP32) + FP32 normals [3N]
   unsigned long long* counter = nullptr;  // [0] work counter, [1..9] points per tree, [10..18] cursors
+  float* scr_s = nullptr;       // the mixed forms' first stage, per slot of its kernel: g, H [21N], normals [3N],
+                                // jumps [3N] (FP32)
+  int64_t nslots_s = 0;         // slots of the first stage's kernel
   double* nbuf = nullptr;       // per point: normals [3N] + local macro strain [6], field-major
   int64_t* perm = nullptr;      // points sorted by tree (several trees)
   int64_t nbuf_cap = 0;
@@ -437,6 +440,9 @@ struct NewtonParams {
   const double* a_start;  // the jumps to start from (state layout), or NULL for those of state_in; with the
                           // first stage these are its jumps in state_out, and iters holds its corrections
   unsigned long long* passes;  // profiling: tree passes of all points added here, or NULL
+  int min_corr;       // corrections before the criterion may end the iteration (1 for the FP64 form after
+                      // the first stage: one quadratic step from the FP32 iterate, so that the accepted
+                      // iterate is as far inside the criterion as in the plain FP64 iteration)
 };
 
 // MINB: resident CTAs per SM the register allocation is sized for (255, 170 or
@@ -588,7 +594,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
     if (!LS) {
       first = false;
       if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
-      else if (rn <= P.tol * (double)t.N * sn) st = DMN_STATUS_OK;
+      else if (rn <= P.tol * (double)t.N * sn && it >= P.min_corr) st = DMN_STATUS_OK;
       else if (it >= (PRED ? lim : P.max_iter - it0)) st = DMN_STATUS_MAXITER;
       if (st < 0) { ++it; continue; }
     } else {
@@ -649,11 +655,14 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
 
 // The mixed forms' first stage (Sec. 3.2's Newton iteration with every quantity in FP32: jumps,
 // strains, leaf return mapping, residual and condensation).  Persistent like k_newton, with its own
-// work counter; per slot the FP32 scratch g, H [21 N], normals [3 N], jumps [3 N].  A point iterates
-// until its FP32 residual meets ||A^T W sigma|| <= tol (2^K - 1) ||sigma_bar|| or max_iter
-// corrections, then writes its jumps (widened) to the jump fields of state_out and the corrections
-// to iters; k_newton continues from there with the FP64 residual.  A point whose FP32 iterates are
-// not finite hands on a^n and zero corrections.  Points of unknown trees are left to k_newton.
+// work counter and launch shape; per slot the FP32 scratch g, H [21 N], normals [3 N], jumps
+// [3 N].  A point iterates until its FP32 residual meets ||A^T W sigma|| <= tol (2^K - 1)
+// ||sigma_bar|| or max_iter corrections, then writes its jumps (widened) to the jump fields of
+// state_out and the corrections to iters; k_newton continues from there with the FP64 residual.
+// A point whose FP32 iterates are not finite hands on a^n and zero corrections.  Points of
+// unknown trees are left to k_newton.
+constexpr int STAGE_CTAS_DEFAULT = 4;   // resident CTAs of 128 threads per SM
+
 struct StageParams {
   Forest F;
   int64_t n, nslots;
@@ -1200,6 +1209,13 @@ bool has_zero_weight(const dmn_tree_desc& d) {
 
 namespace {
 
+// the all-FP32 first stage: on by default in the mixed forms, on request in the FP64 form; never
+// with the line search or the extrapolated start
+bool first_stage_on(const dmn_options& o) {
+  const bool want = o.first_stage == 1 || (o.first_stage == 0 && o.precision != DMN_PREC_F64);
+  return want && !o.line_search && !o.predictor;
+}
+
 // Per-slot scratch and counters of one work set (per-point buffers come with the first update).
 cudaError_t alloc_ws(const dmn_handle* h, WorkSet& w) {
   // per slot: normals + one or two jump buffers (FP64); one or two g, H buffers + FP32 normals
@@ -1207,11 +1223,15 @@ cudaError_t alloc_ws(const dmn_handle* h, WorkSet& w) {
   cudaError_t e = cudaMalloc(&w.scr_d, sizeof(double) * (size_t)(sd * h->N_max) * h->nslots);
   if (e == cudaSuccess) e = cudaMalloc(&w.scr_t, sizeof(double) * (size_t)(stt * h->N_max) * h->nslots);
   if (e == cudaSuccess) e = cudaMalloc(&w.counter, sizeof(unsigned long long) * 32);
+  if (e == cudaSuccess && first_stage_on(h->opt)) {
+    w.nslots_s = (int64_t)h->n_sm * h->opt.stage_ctas_per_sm * 128;
+    e = cudaMalloc(&w.scr_s, sizeof(float) * (size_t)(27 * h->N_max) * w.nslots_s);
+  }
   return e;
 }
 
 void free_ws(WorkSet& w) {
-  cudaFree(w.scr_d); cudaFree(w.scr_t); cudaFree(w.counter); cudaFree(w.nbuf); cudaFree(w.perm);
+  cudaFree(w.scr_d); cudaFree(w.scr_t); cudaFree(w.scr_s); cudaFree(w.counter); cudaFree(w.nbuf); cudaFree(w.perm);
   w = WorkSet();
 }
 
@@ -1237,17 +1257,14 @@ void launch_newton_p(const NewtonParams<T>& P, bool ls, int minb, unsigned grid,
   else if (minb == 3) k_newton<T, 3, false, CMP, PRED><<<grid, block, 0, s>>>(P);
   else k_newton<T, 4, false, CMP, PRED><<<grid, block, 0, s>>>(P);
 }
+// the first stage's kernel: ctas resident CTAs of 128 threads per SM (registers capped to fit)
 template <bool CMP>
-void launch_stage(const StageParams& P, int minb, unsigned grid, int block, cudaStream_t s) {
-  if (minb == 2) k_stage32<2, CMP><<<grid, block, 0, s>>>(P);
-  else if (minb == 3) k_stage32<3, CMP><<<grid, block, 0, s>>>(P);
-  else k_stage32<4, CMP><<<grid, block, 0, s>>>(P);
-}
-
-// the mixed forms run the all-FP32 first stage unless the options turn it off or ask for the
-// line search or the extrapolated start
-bool first_stage_on(const dmn_options& o) {
-  return o.precision != DMN_PREC_F64 && o.first_stage >= 0 && !o.line_search && !o.predictor;
+void launch_stage(const StageParams& P, int ctas, unsigned grid, cudaStream_t s) {
+  if (ctas <= 2) k_stage32<2, CMP><<<grid, 128, 0, s>>>(P);
+  else if (ctas == 3) k_stage32<3, CMP><<<grid, 128, 0, s>>>(P);
+  else if (ctas == 4) k_stage32<4, CMP><<<grid, 128, 0, s>>>(P);
+  else if (ctas <= 6) k_stage32<6, CMP><<<grid, 128, 0, s>>>(P);
+  else k_stage32<8, CMP><<<grid, 128, 0, s>>>(P);
 }
 
 template <typename T, bool CMP>
@@ -1315,22 +1332,24 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, cons
   if (stage) {   // counter [19]: the first stage's work counter
     // its corrections count against max_iter: the FP64-residual iteration keeps at least one
     const int max32 = std::max(0, std::min(STAGE_MAX_ITER, h->opt.max_iter - 1));
-    StageParams SP{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, iters, w.nbuf, (float*)w.scr_t,
+    StageParams SP{F, n, w.nslots_s, NM, tree_id, perm, state_in, state_out, iters, w.nbuf, w.scr_s,
                    w.counter + 19, STAGE_TOL, max32, passes};
-    if (h->cmp) launch_stage<true>(SP, minb, grid, block, s);
-    else launch_stage<false>(SP, minb, grid, block, s);
+    const unsigned sgrid = (unsigned)(h->n_sm * h->opt.stage_ctas_per_sm);
+    if (h->cmp) launch_stage<true>(SP, h->opt.stage_ctas_per_sm, sgrid, s);
+    else launch_stage<false>(SP, h->opt.stage_ctas_per_sm, sgrid, s);
   }
   if (ev) cudaEventRecord(ev[2], s);
   if (!mixed) {
     NewtonParams<double> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                            w.nbuf, w.scr_d, (double*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 1,
-                           h->opt.predictor, dE, nullptr, passes ? passes + 1 : nullptr};
+                           h->opt.predictor, dE, stage ? state_out : nullptr, passes ? passes + 1 : nullptr,
+                           stage ? 1 : 0};
     if (h->cmp) launch_newton<double, true>(P, ls, minb, grid, block, s);
     else launch_newton<double, false>(P, ls, minb, grid, block, s);
   } else {
     NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                           w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, sweep ? 0 : 1,
-                          h->opt.predictor, dE, stage ? state_out : nullptr, passes ? passes + 1 : nullptr};
+                          h->opt.predictor, dE, stage ? state_out : nullptr, passes ? passes + 1 : nullptr, 0};
     if (h->cmp) launch_newton<float, true>(P, ls, minb, grid, block, s);
     else launch_newton<float, false>(P, ls, minb, grid, block, s);
   }
@@ -1460,7 +1479,7 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
 
   dmn_options o;
   o.tol = 1e-12; o.max_iter = 50; o.precision = DMN_PREC_F64; o.block = 128; o.ctas_per_sm = 0; o.line_search = 0;
-  o.predictor = 0; o.first_stage = 0;
+  o.predictor = 0; o.first_stage = 0; o.stage_ctas_per_sm = 0;
   if (opt) {
     if (opt->tol > 0.0) o.tol = opt->tol;
     if (opt->max_iter > 0) o.max_iter = opt->max_iter;
@@ -1470,9 +1489,14 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     o.line_search = opt->line_search;
     o.predictor = opt->predictor;
     o.first_stage = opt->first_stage;
+    o.stage_ctas_per_sm = opt->stage_ctas_per_sm;
   }
   if (o.first_stage < -1 || o.first_stage > 1)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: first_stage must be -1, 0 or 1");
+  if (o.stage_ctas_per_sm == 0) o.stage_ctas_per_sm = STAGE_CTAS_DEFAULT;
+  if (o.stage_ctas_per_sm != 2 && o.stage_ctas_per_sm != 3 && o.stage_ctas_per_sm != 4 && o.stage_ctas_per_sm != 6 &&
+      o.stage_ctas_per_sm != 8)
+    return fail(nullptr, DMN_ERR_ARG, "dmn_create: stage_ctas_per_sm must be 0, 2, 3, 4, 6 or 8");
   if (o.line_search != 0 && o.line_search != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: line_search must be 0 or 1");
   if (o.predictor != 0 && o.predictor != 1) return fail(nullptr, DMN_ERR_ARG, "dmn_create: predictor must be 0 or 1");
   if (o.predictor) {   // the last update's jump change and strain increment follow the jumps

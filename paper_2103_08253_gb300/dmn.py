@@ -45,7 +45,8 @@ class TreeDesc_(ctypes.Structure):
 class Options_(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("line_search", ctypes.c_int32),
-                ("predictor", ctypes.c_int32), ("first_stage", ctypes.c_int32)]
+                ("predictor", ctypes.c_int32), ("first_stage", ctypes.c_int32),
+                ("stage_ctas_per_sm", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -237,13 +238,13 @@ class DMN:
     sweep); "mixed-f32-tangent" (the mixed iteration, tangent from its last
     FP32 condensation).  predictor: start each Newton iteration from the last update's jumps
     extrapolated along the new strain increment (the state then holds the last jump change
-    and strain increment too).  first_stage (mixed forms): True (default) starts every point
-    with the all-FP32 Newton stage, False goes straight to the FP64-residual iteration.  The
-    other options are those of dmn_options."""
+    and strain increment too).  first_stage: True starts every point with the all-FP32 Newton
+    stage, False goes straight to the iteration of the chosen precision; None (default) runs it
+    in the mixed forms only.  The other options are those of dmn_options."""
 
     def __init__(self, tree, precision: str = "f64", tol: float = 1e-12, max_iter: int = 50, block: int = 0,
                  ctas_per_sm: int = 0, line_search: bool = False, predictor: bool = False,
-                 first_stage: bool = True):
+                 first_stage=None, stage_ctas_per_sm: int = 0):
         import torch
         self._lib = load_library()
         if not torch.cuda.is_available():
@@ -263,9 +264,11 @@ class DMN:
         if precision not in PRECISIONS:
             raise ValueError("precision must be one of %s" % (tuple(PRECISIONS),))
         opt = Options_(float(tol), int(max_iter), PRECISIONS[precision], int(block),
-                       int(ctas_per_sm), int(bool(line_search)), int(bool(predictor)), 0 if first_stage else -1)
+                       int(ctas_per_sm), int(bool(line_search)), int(bool(predictor)),
+                       0 if first_stage is None else (1 if first_stage else -1), int(stage_ctas_per_sm))
         self.precision = precision
-        self.first_stage = bool(first_stage) and precision != "f64" and not line_search and not predictor
+        want = precision != "f64" if first_stage is None else bool(first_stage)
+        self.first_stage = want and not line_search and not predictor
         self.predictor = bool(predictor)
         h = ctypes.c_void_p()
         rc = self._lib.dmn_create(descs, len(trees), ctypes.byref(opt), ctypes.byref(h))

@@ -126,7 +126,12 @@ def test_first_stage_option_is_checked_without_touching_the_gpu():
         o = dmn.Options_(1e-12, 50, dmn.PREC_MIXED, 0, 0, 0, 0, bad)
         assert lib.dmn_create(ctypes.byref(d), 1, ctypes.byref(o), ctypes.byref(h)) == -1
         assert h.value is None and "first_stage must be -1, 0 or 1" in lib.dmn_last_error(None).decode()
-    assert [f[0] for f in dmn.Options_._fields_][-1] == "first_stage"
+    for bad in (1, 5, 9):
+        h = ctypes.c_void_p(123)
+        o = dmn.Options_(1e-12, 50, dmn.PREC_MIXED, 0, 0, 0, 0, 0, bad)
+        assert lib.dmn_create(ctypes.byref(d), 1, ctypes.byref(o), ctypes.byref(h)) == -1
+        assert h.value is None and "stage_ctas_per_sm must be" in lib.dmn_last_error(None).decode()
+    assert [f[0] for f in dmn.Options_._fields_][-2:] == ["first_stage", "stage_ctas_per_sm"]
 
 
 def _noalloc(d, o, n=8, arrays=None):

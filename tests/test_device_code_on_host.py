@@ -312,7 +312,7 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
       if (ls) { cur = 1 - cur; rn_acc = rn; root_acc = root; step = (T)1; halvings = 0; }
       first = false;
       if (!std::isfinite(rn) || !std::isfinite(sn)) stt = 2;
-      else if (rn <= tol * (double)N * sn) stt = 0;
+      else if (rn <= tol * (double)N * sn && (it >= 1 || !stage || sizeof(T) == 4)) stt = 0;
       else if (it >= max_iter - it32) stt = 1;
       if (stt < 0) { ++it; continue; }
       break;
@@ -482,10 +482,11 @@ int main(int argc, char** argv) {
   const long n = (long)hdr[2];
   // mode: 0 FP64, 1 mixed with the FP32 tangent, 2 mixed with the FP64 final sweep, 3 adjoint (FP64),
   //       4 FP64 with the line search, 5 adjoint of the tangent (elastic phases),
-  //       6 / 7 modes 1 / 2 after the all-FP32 first stage
+  //       6 / 7 / 8 modes 1 / 2 / 0 after the all-FP32 first stage
   const float tol32 = hdr[6] > 0.0 ? (float)hdr[6] : STAGE_TOL;
   const int max32 = hdr[7] > 0.0 ? (int)hdr[7] : std::max(0, std::min(STAGE_MAX_ITER, max_iter - 1));
   const int rc = mode == 0 || mode == 4 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false, mode == 4)
+               : mode == 8 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false, false, true, tol32, max32)
                : mode == 3 ? run_grad(in, out, K, M, n)
                : mode == 5 ? run_grad_tangent(in, out, K, M, n)
                : mode >= 6 ? run<float>(in, out, K, M, n, max_iter, hdr[5], mode == 7, false, true, tol32, max32)
@@ -547,7 +548,9 @@ PHASE_SETS = {"linear": (W.FIBER, W.MATRIX), "explin": (W.FIBER, W.MATRIX_EXPLIN
                                              (5, 3, "inelastic-left", 0), (5, 3, "both-inelastic", 1),
                                              # the mixed forms after the all-FP32 first stage
                                              (6, 3, "linear", 6), (6, 3, "explin", 7), (5, 3, "both-inelastic", 7),
-                                             (5, 6, "inelastic-left", 6)])
+                                             (5, 6, "inelastic-left", 6),
+                                             # the FP64 form after the first stage
+                                             (6, 3, "linear", 8), (6, 3, "explin", 8), (5, 3, "both-inelastic", 8)])
 def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
     phases = PHASE_SETS[matrix]
     tree = (W.tree_d10_fit(K, seed=30 + K, phases=phases) if M == 3
@@ -557,7 +560,11 @@ def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
     Ef = W.random6_path_final(n, 0.03, seed=50 + K)
     S = W.state_size(K, tree.phases)
     sh, so = np.zeros((S, n)), np.zeros((S, n))
-    tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6), 6: (1e-6, 1e-4), 7: (1e-6, 1e-6)}[prec]
+    # 8: the FP64 iteration from the first stage's jumps and the oracle's from a^n stop at the same
+    # criterion, ||A^T W sigma|| <= 1e-12 (2^K - 1) ||sigma_bar||, at different iterates: they agree to
+    # that criterion's reach (the oracle itself moves by up to ~1e-9 when converged further), not to rounding
+    tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6), 6: (1e-6, 1e-4), 7: (1e-6, 1e-6),
+                    8: (3e-9, 3e-9)}[prec]
     alive = np.ones(n, dtype=bool)
     for s in range(1, 9):
         En, dE = W.proportional_increment(Ef, s, 20)
@@ -650,7 +657,7 @@ def test_device_line_search_matches_the_oracle(harness):
     assert differs > 0          # the search was active on this path
 
 
-@pytest.mark.parametrize("K,prec", [(5, 0), (7, 0), (7, 1), (7, 2), (7, 6), (7, 7)])
+@pytest.mark.parametrize("K,prec", [(5, 0), (7, 0), (7, 1), (7, 2), (7, 6), (7, 7), (7, 8)])
 def test_device_compressed_traversal_matches_the_oracle(harness, K, prec):
     """Trees with weightless leaves, walked by the compression tables (restated in the harness from
     their documented format), against the oracle's compression."""
@@ -661,7 +668,11 @@ def test_device_compressed_traversal_matches_the_oracle(harness, K, prec):
     S = oracle.state_size(K, tree.phases, tree.w)
     assert S < W.state_size(K)
     sh, so = np.zeros((S, n)), np.zeros((S, n))
-    tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6), 6: (1e-6, 1e-4), 7: (1e-6, 1e-6)}[prec]
+    # 8: the FP64 iteration from the first stage's jumps and the oracle's from a^n stop at the same
+    # criterion, ||A^T W sigma|| <= 1e-12 (2^K - 1) ||sigma_bar||, at different iterates: they agree to
+    # that criterion's reach (the oracle itself moves by up to ~1e-9 when converged further), not to rounding
+    tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6), 6: (1e-6, 1e-4), 7: (1e-6, 1e-6),
+                    8: (3e-9, 3e-9)}[prec]
     alive = np.ones(n, dtype=bool)
     for s in range(1, 9):
         En, dE = W.proportional_increment(Ef, s, 20)

@@ -1,4 +1,5 @@
-"""The mixed forms' all-FP32 first stage, through the C ABI, against the oracle.
+"""The all-FP32 first Newton stage (the mixed forms' default, the FP64 form's option), through the C ABI,
+against the oracle.
 
 The stage runs Sec. 3.2's Newton iteration with every quantity in FP32 until its own residual is
 small, and the FP64-residual iteration of the mixed forms continues from its jumps to the FP64
@@ -65,13 +66,13 @@ def test_first_stage_on_a_compressed_tree():
 def test_first_stage_saves_fp64_passes_and_the_counters_add_up():
     """Profiling counters: with the stage the Newton kernel runs fewer FP64-residual passes; the stage's
     and the Newton kernel's passes per point are each (corrections + 1), their corrections add up to
-    the iteration counts; without the stage (or in the FP64 form) the stage counter stays zero."""
+    the iteration counts; without the stage (or in the FP64 form by default) the stage counter stays zero."""
     tree = W.tree_d10_fit(8, seed=321)
     n = 4096
     A2, lam, Q = W.orientation_field(n, seed=322)
     Ef = W.random6_path_final(n, 0.03, seed=323)
     res = {}
-    for key, prec, stage in (("on", "mixed", True), ("off", "mixed", False), ("f64", "f64", True)):
+    for key, prec, stage in (("on", "mixed", True), ("off", "mixed", False), ("f64", "f64", None)):
         m = dmn.DMN(tree, precision=prec, first_stage=stage)
         st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
         for s in range(1, 6):
@@ -116,3 +117,42 @@ def test_first_stage_within_max_iter():
         assert set(np.unique(stat)) <= {dmn.STATUS_OK, dmn.STATUS_MAXITER}
         assert (it[stat == dmn.STATUS_MAXITER] == 3).all()
     m.close()
+
+
+def test_fp64_form_after_the_first_stage():
+    """The FP64 form with the first stage on request: at least one FP64 Newton step after the stage, the
+    FP64 criterion, FP64 tangent.  It stops at the same criterion as the oracle from another start, so it
+    agrees with the oracle to that criterion's reach (||A^T W sigma|| <= 1e-12 x 255 ||sigma_bar|| leaves
+    some 1e-9 of the stress open at depth 8; the oracle itself moves that much when converged further),
+    not to rounding as the plain FP64 form does; and it needs far fewer FP64 passes."""
+    import oracle
+    tree = W.tree_d10_fit(8, seed=341)
+    n = 256
+    A2, lam, Q = W.orientation_field(n, seed=342)
+    Ef = W.random6_path_final(n, 0.03, seed=343)
+    S = W.state_size(8, tree.phases)
+    m = dmn.DMN(tree, precision="f64", first_stage=True)
+    plain = dmn.DMN(tree, precision="f64")
+    assert m.first_stage and not plain.first_stage
+    st, st_p = (torch.zeros((S, n), dtype=torch.float64, device=DEV) for _ in range(2))
+    st_o = np.zeros((S, n))
+    for s in range(1, 7):
+        En, dE = W.proportional_increment(Ef, s, 20)
+        m.profile(True)
+        plain.profile(True)
+        out = m.update(d(lam), d(Q), d(En), d(dE), st)
+        ref = plain.update(d(lam), d(Q), d(En), d(dE), st_p)
+        _, ps, _ = m.profile_read_stages()
+        _, pp, _ = plain.profile_read_stages()
+        st, st_p = out["state_out"], ref["state_out"]
+        st_o, sig_o, C_o, it_o, stat_o, gap = oracle.update(tree, lam, Q, En, dE, st_o)
+        assert (out["status"] == 0).all() and (stat_o == 0).all()
+        tie = gap < 1e-9
+        assert rel(out["stress"].cpu().numpy(), sig_o).max() <= 1e-8
+        assert rel(out["tangent"].cpu().numpy()[~tie], C_o[~tie]).max() <= 1e-8
+        assert ps["stage"] >= n and pp["stage"] == 0
+        assert ps["newton"] >= 2 * n            # one FP64 step at least: two FP64 passes per point
+        if s > 1:
+            assert ps["newton"] < 0.7 * pp["newton"]
+    m.close()
+    plain.close()
