@@ -529,7 +529,8 @@ def roofline_f64(r, n, steps, w=None, peaks=None):
     F, _ = newton_flops(K_DEPTH, corr, npts, mixed=False, w=w)
     t = r["kms"]["newton"] * 1e-3
     ach = F / t / 1e9
-    tr = ncu_traffic("k_newton_f64" + ("_compressed" if w is not None and (np.asarray(w) == 0).any() else ""), n)
+    cmp = "_compressed" if w is not None and (np.asarray(w) == 0).any() else ""
+    tr = ncu_traffic("k_newton_f64" + cmp + ("_stage" if "stage" in r["kms"] else ""), n)
     out = {"bound": "alu", "kernel": "k_newton<double>", "achieved": ach, "peak": P64,
            "unit": "GFLOP/s (FP64)", "frac": ach / P64, "traffic": tr,
            "flops_per_launch": F / steps, "launch_ms": r["kms"]["newton"] / steps,
@@ -537,6 +538,7 @@ def roofline_f64(r, n, steps, w=None, peaks=None):
            "passes_per_update": (corr + npts) / npts}
     if "stage" in r["kms"]:
         out["stage_kernel"] = stage_roofline(r, n, steps, w, pk["f32"])
+        out["stage_kernel"]["traffic"] = ncu_traffic("k_stage32" + cmp, n)
     return out
 
 
@@ -565,14 +567,17 @@ def roofline_mixed(r, n, steps, w=None, sweep=True, peaks=None):
     tf = r["kms"]["final"] * 1e-3
     fin = {"kernel": "k_final<sweep>" if sweep else "k_final", "achieved": Ff / tf / 1e9, "peak": P64,
            "unit": "GFLOP/s (FP64)", "frac": Ff / tf / 1e9 / P64, "launch_ms": r["kms"]["final"] / steps}
+    cmp = "_compressed" if w is not None and (np.asarray(w) == 0).any() else ""
+    stg = "stage" in r["kms"]
     out = {"bound": "alu", "kernel": "k_newton<float>", "achieved": tb / t * P64,
            "peak": P64, "unit": "GFLOP/s (FP64-equivalent: F64/P64 + F32/P32)", "frac": tb / t, "peak_note": pk["note"],
-           "traffic": ncu_traffic("k_newton_mixed" + ("_compressed" if w is not None and (np.asarray(w) == 0).any()
-                                                      else ""), n), "flops_f64_per_launch": F64 / steps,
+           "traffic": ncu_traffic("k_newton_mixed" + cmp + ("_stage" if stg else ""), n),
+           "flops_f64_per_launch": F64 / steps,
            "flops_f32_per_launch": F32 / steps, "launch_ms": r["kms"]["newton"] / steps,
            "passes_per_update": (newton_corr + npts) / npts, "final_kernel": fin}
-    if "stage" in r["kms"]:
+    if stg:
         out["stage_kernel"] = stage_roofline(r, n, steps, w, P32)
+        out["stage_kernel"]["traffic"] = ncu_traffic("k_stage32" + cmp, n)
     return out
 
 
@@ -616,7 +621,8 @@ def run_mixed_depth(args):
     for form in [f for f in args.forms.split(",") if f]:
         # autotuned shape on 2^18 points of the batch at the first timed increment
         prec, pred = form_opts(form)
-        m0 = dmn.DMN(trees, precision=prec)
+        stage = form_stage(form)
+        m0 = dmn.DMN(trees, precision=prec, first_stage=stage)
         msub = min(n, 1 << 18)
         lam_s, Q_s = m0.interp_orientation(A2_d[:msub].contiguous())
         st = torch.zeros((m0.state_size, msub), dtype=torch.float64, device=dev)
@@ -628,11 +634,11 @@ def run_mixed_depth(args):
         # the project's autotuner on the handle of four trees, on this sub-batch
         En, dE = inputs(first)
         tuned = autotune.tune(trees, prec, lam_s, Q_s, En[:msub].contiguous(), dE[:msub].contiguous(), st, reps=1,
-                              tree_id=tid_d[:msub].contiguous())
+                              tree_id=tid_d[:msub].contiguous(), first_stage=stage)
         best = (tuned["block"], tuned["ctas_per_sm"], tuned["newton_ms"])
         del st
         torch.cuda.empty_cache()
-        m = dmn.DMN(trees, precision=prec, block=best[0], ctas_per_sm=best[1], predictor=pred)
+        m = dmn.DMN(trees, precision=prec, block=best[0], ctas_per_sm=best[1], predictor=pred, first_stage=stage)
         lam, Q = m.interp_orientation(A2_d)
         S = m.state_size
         bufs = [torch.zeros((S, n), dtype=torch.float64, device=dev) for _ in range(2)]

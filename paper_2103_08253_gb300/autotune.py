@@ -48,17 +48,19 @@ def cached(tree, precision, device=None):
     return (int(e["block"]), int(e["ctas_per_sm"])) if e else None
 
 
-def tune(tree, precision, lam, Q, E_n, dE, state_in, reps=2, candidates=CANDIDATES, save=True, tree_id=None):
+def tune(tree, precision, lam, Q, E_n, dE, state_in, reps=2, candidates=CANDIDATES, save=True, tree_id=None,
+         first_stage=None):
     """Time the Newton kernel of every candidate shape on this batch; returns
     dict(block, ctas_per_sm, newton_ms, table).  tree may be a list of trees (one handle with
     several trees, as dmn.DMN takes it), with tree_id [n] (int32, device) selecting each
-    point's tree."""
+    point's tree.  first_stage as in dmn.DMN; with the first stage the time is that of the stage
+    and the Newton kernel together (the stage keeps its own launch shape)."""
     import torch
     dev = lam.device
     n = lam.shape[0]
     table = []
     for block, cps in candidates:
-        m = dmn.DMN(tree, precision=precision, block=block, ctas_per_sm=cps)
+        m = dmn.DMN(tree, precision=precision, block=block, ctas_per_sm=cps, first_stage=first_stage)
         out = m.alloc_outputs(n, dev)
         m.update(lam, Q, E_n, dE, state_in, out=out, tree_id=tree_id)
         torch.cuda.synchronize()
@@ -76,7 +78,7 @@ def tune(tree, precision, lam, Q, E_n, dE, state_in, reps=2, candidates=CANDIDAT
                table=[dict(block=b, ctas_per_sm=c, newton_ms=t) for b, c, t in table])
     if save:
         data = _load()
-        data[_key(tree, precision, dev)] = res
+        data[_key(tree, precision, dev) + ("" if first_stage is None else "|stage%d" % int(bool(first_stage)))] = res
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)
         tmp = CACHE + ".tmp%d" % os.getpid()
         with open(tmp, "w") as f:
