@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   float* my_nrmf = (float*)(P.scr_t + (size_t)((LS ? 42 : 21) * NM) * ns) + slot;
   double* abuf[2] = {P.scr_d + (size_t)(3 * NM) * ns + slot, P.scr_d + (size_t)((LS ? 6 : 3) * NM) * ns + slot};
   T* gbuf[2] = {P.scr_t + slot, P.scr_t + (size_t)((LS ? 21 : 0) * NM) * ns + slot};
-  PointArrays A;
+  PointArrays A{};
   A.nrm = my_nrm; A.ns = ns;
   A.nrmf = my_nrmf;
   A.as = ns;
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(128) k_final(FinalParams P) {
   double Eloc[6];
 #pragma unroll
   for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * P.N_max + I) * P.n + pt];
-  PointArrays A;
+  PointArrays A{};
   A.nrm = P.nbuf + pt; A.ns = (size_t)P.n;
   A.nrmf = nullptr;
   A.a = P.state_out + (size_t)(6 * t.nz) * P.n + pt; A.as = (size_t)P.n;
@@ -807,7 +807,7 @@ __global__ void __launch_bounds__(128) k_final(FinalParams P) {
     const double qnan = __longlong_as_double(0x7ff8000000000000LL);
     for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
     for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
-  } else if (SWEEP) {
+  } else if (SWEEP) {   // stress and tangent from one FP64 pass at the converged jumps
     Sub<double> root;
     double r2;
     GH<double> gh{nullptr, 0, nullptr};
@@ -889,7 +889,7 @@ __global__ void __launch_bounds__(128) k_grad(GradParams P) {
   }
   double Eloc[6];
   local_strain(P.Q + 9 * pt, P.En + 6 * pt, P.dE + 6 * pt, Eloc);
-  PointArrays A;
+  PointArrays A{};
   A.nrm = nrm; A.ns = ws; A.nrmf = nullptr;
   A.a = a; A.a_out = a; A.as = ws; A.paper = false;
   A.z = P.state_in + pt; A.zs = (size_t)P.n;
@@ -1910,7 +1910,7 @@ __global__ void __launch_bounds__(NOALLOC_BLOCK) k_newton_noalloc(NoAllocParams 
   const TreeDev& t = P.t;
   const int N = t.N;
   double* my_nrm = P.slots + slot;
-  PointArrays A;
+  PointArrays A{};
   A.nrm = my_nrm; A.ns = (size_t)P.nslots;
   A.nrmf = nullptr;
   A.a = P.slots + (size_t)(3 * N) * P.nslots + slot; A.as = (size_t)P.nslots;

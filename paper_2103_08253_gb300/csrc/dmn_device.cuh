@@ -437,6 +437,14 @@ __device__ __forceinline__ void residual_share(const S nd[3], S c1, S c2, S sc, 
   for (int I = 0; I < 6; ++I) sb[I] = sL[I] + c2 * d[I];   // c1 sL + c2 sR with c1 = 1 - c2
 }
 
+// The plain average alone, sb = c1 sb_L + c2 sb_R (as residual_share forms it): the final sweep,
+// which needs the stress and the tangent but neither the residual nor a Newton step.
+template <typename S>
+__device__ __forceinline__ void stress_average(S c2, const S sL[6], const S sR[6], S sb[6]) {
+#pragma unroll
+  for (int I = 0; I < 6; ++I) sb[I] = sL[I] + c2 * (sR[I] - sL[I]);
+}
+
 // ---------------------------------------------------------------------------
 // Condensation of one laminate with children L (fraction c1) and R (c2) and
 // normal n.  Jumps perturb the children as d_eps_L = d_eps - c2 N da,
@@ -456,11 +464,14 @@ template <typename T, bool STORE, typename S = double>
 __device__ __forceinline__ void condense(const S nd[3], const T n[3], S c1d, S c2d, S sc, NodeC<T> cc,
                                          const Sub<T, S>& L, const Sub<T, S>& R, Sub<T, S>& out, T* gp,
                                          size_t gstride, S& r2) {
-  T u[3];
-  {
+  // without STORE (the final sweep) only sb and C: no residual, no Newton step g, no ds
+  T u[3] = {(T)0, (T)0, (T)0};
+  if (STORE) {
     S t[3];
     residual_share<S>(nd, c1d, c2d, sc, L.sb, R.sb, out.sb, t, r2);
     u[0] = cvt<T>(t[0]); u[1] = cvt<T>(t[1]); u[2] = cvt<T>(t[2]);
+  } else {
+    stress_average<S>(c2d, L.sb, R.sb, out.sb);
   }
   const T c1 = cc.c1, c2 = cc.c2, c12 = cc.c12;
   const T nr[3] = {n[0] * (T)RS2, n[1] * (T)RS2, n[2] * (T)RS2};
@@ -492,16 +503,21 @@ __device__ __forceinline__ void condense(const S nd[3], const T n[3], S c1d, S c
   for (int I = 0; I < 6; ++I)
 #pragma unroll
     for (int m = 0; m < 3; ++m) B12[I][m] = c12 * B[I][m];
+  if (STORE) {
 #pragma unroll
-  for (int I = 0; I < 6; ++I) dds[I] = R.ds[I] - L.ds[I];
-  Nt_apply<T>(n, nr, dds, v);
+    for (int I = 0; I < 6; ++I) dds[I] = R.ds[I] - L.ds[I];
+    Nt_apply<T>(n, nr, dds, v);
 #pragma unroll
-  for (int m = 0; m < 3; ++m) u[m] += v[m];
+    for (int m = 0; m < 3; ++m) u[m] += v[m];
 #pragma unroll
-  for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
+    for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
 #pragma unroll
-  for (int I = 0; I < 6; ++I)
-    out.ds[I] = L.ds[I] + c2 * dds[I] + B12[I][0] * g[0] + B12[I][1] * g[1] + B12[I][2] * g[2];
+    for (int I = 0; I < 6; ++I)
+      out.ds[I] = L.ds[I] + c2 * dds[I] + B12[I][0] * g[0] + B12[I][1] * g[1] + B12[I][2] * g[2];
+  } else {
+#pragma unroll
+    for (int I = 0; I < 6; ++I) out.ds[I] = (T)0;
+  }
 #pragma unroll
   for (int I = 0; I < 6; ++I)
 #pragma unroll
@@ -543,11 +559,13 @@ __device__ __forceinline__ void condense_bottom(const S nd[3], const T n[3], S c
   // the FP32 condensation runs beside the FP64 work at no cost of its own: it keeps the general
   // form, whose register use the shortcut would raise
   if (sizeof(T) == 4) { elL = false; elR = false; }
-  T u[3];
-  {
+  T u[3] = {(T)0, (T)0, (T)0};
+  if (STORE) {
     S t[3];
     residual_share<S>(nd, c1d, c2d, sc, sL, sR, out.sb, t, r2);
     u[0] = cvt<T>(t[0]); u[1] = cvt<T>(t[1]); u[2] = cvt<T>(t[2]);
+  } else {
+    stress_average<S>(c2d, sL, sR, out.sb);
   }
   const T c1 = cc.c1, c2 = cc.c2, c12 = cc.c12;
   const T nr[3] = {n[0] * (T)RS2, n[1] * (T)RS2, n[2] * (T)RS2};
@@ -608,12 +626,17 @@ __device__ __forceinline__ void condense_bottom(const S nd[3], const T n[3], S c
   for (int m = 0; m < 3; ++m)
 #pragma unroll
     for (int I = 0; I < 6; ++I) H[m][I] = -(Ki[m][0] * B[I][0] + Ki[m][1] * B[I][1] + Ki[m][2] * B[I][2]);
-  T g[3];
+  T g[3] = {(T)0, (T)0, (T)0};
+  if (STORE) {
 #pragma unroll
-  for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
-  const T g12[3] = {c12 * g[0], c12 * g[1], c12 * g[2]};
+    for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
+    const T g12[3] = {c12 * g[0], c12 * g[1], c12 * g[2]};
 #pragma unroll
-  for (int I = 0; I < 6; ++I) out.ds[I] = B[I][0] * g12[0] + B[I][1] * g12[1] + B[I][2] * g12[2];
+    for (int I = 0; I < 6; ++I) out.ds[I] = B[I][0] * g12[0] + B[I][1] * g12[1] + B[I][2] * g12[2];
+  } else {
+#pragma unroll
+    for (int I = 0; I < 6; ++I) out.ds[I] = (T)0;
+  }
   const T lamC = c1 * DL.lam + c2 * DR.lam, mu2C = (T)2 * (c1 * DL.mu + c2 * DR.mu);
   T H12[3][6];
 #pragma unroll

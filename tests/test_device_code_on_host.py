@@ -259,7 +259,7 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
     tr.point(lam[2 * pt], lam[2 * pt + 1], &Q[9 * pt], &En[6 * pt], &dE[6 * pt], f, nrm.data(), nrmf.data(), R, Eloc);
     int cur = 0;
     for (int k = 0; k < 3 * N; ++k) abuf[0][k] = st[(6L * t.nz + k) * n + pt];
-    PointArrays A;
+    PointArrays A{};
     A.nrm = nrm.data(); A.ns = 1; A.nrmf = nrmf.data();
     A.as = 1; A.paper = !tr.cmp;
     A.z = st.data() + pt; A.zs = (size_t)n;
@@ -322,7 +322,7 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
     std::vector<double>& a = abuf[cur];
     iters[pt] = it + it32; status[pt] = stt;
     double Cl[6][6], sl[6];
-    if (sweep) {
+    if (sweep) {   // the final kernel's FP64 pass: stress and tangent of the converged jumps
       Sub<double> fin;
       double r2;
       GH<double> none{nullptr, 0, nullptr};
@@ -370,7 +370,7 @@ static int run_grad(FILE* in, FILE* out, int K, int M, long n) {
     double f[6], R[6][6], Eloc[6];
     tr.point(lam[2 * pt], lam[2 * pt + 1], &Q[9 * pt], &En[6 * pt], &dE[6 * pt], f, nrm.data(), nullptr, R, Eloc);
     for (int k = 0; k < 3 * N; ++k) a[k] = st_out[(6L * t.nz + k) * n + pt];
-    PointArrays A;
+    PointArrays A{};
     A.nrm = nrm.data(); A.ns = 1; A.nrmf = nullptr;
     A.a = a.data(); A.as = 1; A.a_out = a.data(); A.paper = !tr.cmp;
     A.z = st_in.data() + pt; A.zs = (size_t)n;
