@@ -365,6 +365,10 @@ def tune_shape(form, ctx, args):
     s = args.warmup + 1
     res = autotune.tune(ctx["tree"], form, lam, Q, ctx["En"][s - 1][:m].contiguous(),
                         ctx["dE"][s - 1][:m].contiguous(), st, reps=1)
+    # the first stage's own launch shape, at the Newton kernel's tuned one
+    ts = autotune.tune_stage(ctx["tree"], form, lam, Q, ctx["En"][s - 1][:m].contiguous(),
+                             ctx["dE"][s - 1][:m].contiguous(), st, block=res["block"], ctas_per_sm=res["ctas_per_sm"])
+    res["stage_ctas_per_sm"], res["stage_table"] = ts["stage_ctas_per_sm"], ts["table"]
     del st
     torch.cuda.empty_cache()
     cache[form] = res
@@ -379,7 +383,8 @@ def run_form(form, ctx, args, dist):
     shape = tune_shape(form, ctx, args) if args.autotune else None
     prec, pred = form_opts(form)
     m = dmn.DMN(ctx["tree"], precision=prec, block=shape["block"] if shape else 0,
-                ctas_per_sm=shape["ctas_per_sm"] if shape else 0, predictor=pred, first_stage=form_stage(form))
+                ctas_per_sm=shape["ctas_per_sm"] if shape else 0, predictor=pred, first_stage=form_stage(form),
+                stage_ctas_per_sm=shape["stage_ctas_per_sm"] if shape else 0)
     assert m.first_stage == form_stage(form)
     S = m.state_size
     st = [torch.zeros((S, n), dtype=torch.float64, device=dev), torch.zeros((S, n), dtype=torch.float64, device=dev)]
@@ -429,7 +434,8 @@ def run_form(form, ctx, args, dist):
     res = dict(t_ms=t_ms, kms=kms, updates=cnt, clocks=clk, iters_sum=int(its), iters_hist=hist.tolist(),
                passes=passes,
                launch=(dict(block=shape["block"], ctas_per_sm=shape["ctas_per_sm"], tuned_on_points=shape["points"],
-                            table=shape["table"]) if shape else "defaults"),
+                            table=shape["table"], stage_ctas_per_sm=shape["stage_ctas_per_sm"],
+                            stage_table=shape["stage_table"]) if shape else "defaults"),
                stress=out["stress"], tangent=out["tangent"], status=out["status"], state=st[cur],
                host_state=host_state, m=m, lam=lam, Q=Q, S=S, st=st)
     return res

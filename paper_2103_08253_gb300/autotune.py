@@ -7,9 +7,10 @@ key of their own.  The FP64 form is
 bound by the FP64 pipe once each SM holds a few warps, the FP32 form hides
 latency with more resident warps, and both trade occupancy against registers.
 `tune` times every candidate shape on a caller-provided batch through the C ABI
-(per-kernel CUDA events of the Newton kernel) and returns the fastest; results
-are cached per (GPU, SM count, depth, shape functions, phases, precision) in
-`_build/autotune.json` next to this file.
+(per-kernel CUDA events of the Newton kernel) and returns the fastest;
+`tune_stage` does the same for the first stage's kernel, which has a launch
+shape of its own.  Results are cached per (GPU, SM count, depth, shape
+functions, phases, precision) in `_build/autotune.json` next to this file.
 """
 from __future__ import annotations
 
@@ -19,6 +20,7 @@ import os
 from . import dmn
 
 CANDIDATES = ((128, 2), (128, 3), (128, 4), (64, 4), (64, 6), (64, 8), (96, 4), (32, 12), (32, 16))
+STAGE_CANDIDATES = (2, 3, 4, 6, 8)   # resident CTAs of 128 threads per SM of the first stage's kernel
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
@@ -79,6 +81,44 @@ def tune(tree, precision, lam, Q, E_n, dE, state_in, reps=2, candidates=CANDIDAT
     if save:
         data = _load()
         data[_key(tree, precision, dev) + ("" if first_stage is None else "|stage%d" % int(bool(first_stage)))] = res
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1)
+        os.replace(tmp, CACHE)
+    return res
+
+
+def tune_stage(tree, precision, lam, Q, E_n, dE, state_in, reps=1, candidates=STAGE_CANDIDATES, save=True,
+               tree_id=None, block=0, ctas_per_sm=0):
+    """Time the first stage's kernel at every candidate number of resident CTAs per SM on this batch
+    (the Newton kernel at the given shape); returns dict(stage_ctas_per_sm, stage_ms, table).  The
+    stage computes every point in one thread whatever the shape, so the results do not depend on it."""
+    import torch
+    dev = lam.device
+    n = lam.shape[0]
+    table = []
+    for cps in candidates:
+        m = dmn.DMN(tree, precision=precision, block=block, ctas_per_sm=ctas_per_sm, first_stage=True,
+                    stage_ctas_per_sm=cps)
+        out = m.alloc_outputs(n, dev)
+        m.update(lam, Q, E_n, dE, state_in, out=out, tree_id=tree_id)
+        torch.cuda.synchronize()
+        m.profile(True)
+        for _ in range(reps):
+            m.update(lam, Q, E_n, dE, state_in, out=out, tree_id=tree_id)
+        kms, _, cnt = m.profile_read_stages()
+        m.profile(False)
+        m.close()
+        del out
+        table.append((cps, kms["stage"] / cnt))
+    torch.cuda.empty_cache()
+    cps, ms = min(table, key=lambda r: r[1])
+    res = dict(stage_ctas_per_sm=cps, stage_ms=ms, points=n,
+               table=[dict(stage_ctas_per_sm=c, stage_ms=t) for c, t in table])
+    if save:
+        data = _load()
+        data[_key(tree, precision, dev) + "|stage_shape"] = res
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)
         tmp = CACHE + ".tmp%d" % os.getpid()
         with open(tmp, "w") as f:

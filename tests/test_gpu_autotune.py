@@ -55,3 +55,28 @@ def test_autotune_of_a_handle_with_several_trees(tmp_path, monkeypatch):
     assert (res["block"], res["ctas_per_sm"]) in cands and len(res["table"]) == 2
     assert autotune.cached(trees, "f64", DEV) == (res["block"], res["ctas_per_sm"])
     assert autotune.cached(trees[0], "f64", DEV) is None
+
+
+def test_stage_shape_tuner(tmp_path, monkeypatch):
+    """The first stage's launch shape: the tuner times the candidates and picks one.  Each shape is its
+    own instantiation (register cap), so the FP32 stage's rounding may differ between shapes; the FP64
+    iteration then ends at the same criterion, and the results agree to that criterion's reach."""
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
+    K, n = 6, 3000
+    tree = W.tree_d10_fit(K, seed=13)
+    A2, lam, Q = W.orientation_field(n, seed=14)
+    Ef = W.random6_path_final(n, 0.03, seed=15)
+    En, dE = W.proportional_increment(Ef, 8, 20)
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+    st = torch.zeros((W.state_size(K), n), dtype=torch.float64, device=DEV)
+    res = autotune.tune_stage(tree, "mixed-f32-tangent", d(lam), d(Q), d(En), d(dE), st, candidates=(2, 4, 8))
+    assert res["stage_ctas_per_sm"] in (2, 4, 8)
+    assert len(res["table"]) == 3 and all(r["stage_ms"] > 0 for r in res["table"])
+    outs = [dmn.DMN(tree, precision="mixed", stage_ctas_per_sm=c).update(d(lam), d(Q), d(En), d(dE), st)
+            for c in (2, 8)]
+    assert torch.equal(outs[0]["status"], outs[1]["status"])
+    ok = (outs[0]["status"] == 0).cpu().numpy()
+    assert ok.mean() > 0.9      # one increment to 40 % of the path from the virgin state: a few points end at MAXITER
+    for k in ("stress", "tangent"):
+        a, b = (o[k].reshape(n, -1).cpu().numpy()[ok] for o in outs)
+        assert (np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)).max() <= 1e-8, k
