@@ -44,8 +44,8 @@ struct Tree {
   int K, M, N, L, nz, z_both, S;
   double* d_p = nullptr;
   double* d_q = nullptr;
-  double* d_c = nullptr;   // c1 [N], c2 [N], sc [N], normalised leaf weights [L]
-  float* d_cf = nullptr;   // c1f [N], c2f [N], c12f [N], scf [N]
+  double* d_c = nullptr;   // c1 [N], c2 [N], sc [N], normalised leaf weights [L], 1 / (c1 c2) [N]
+  float* d_cf = nullptr;   // c1f [N], c2f [N], c12f [N], scf [N], 1 / (c1 c2) [N]
   double wsum = 1.0;       // sum of the leaf weights as given
   PhaseDev ph[2];
   // compressed trees (some leaf weight zero): N laminates left, Lc leaves left,
@@ -119,6 +119,7 @@ TreeDev tree_dev(const Tree& t) {
   d.c1 = t.d_c; d.c2 = t.d_c + t.N; d.sc = t.d_c + 2 * t.N;
   d.c1f = t.d_cf; d.c2f = t.d_cf + t.N; d.c12f = t.d_cf + 2 * t.N; d.scf = t.d_cf + 3 * t.N;
   d.wl = t.d_c + 3 * t.N; d.wsum = t.wsum;
+  d.ic12 = t.d_c + 3 * t.N + t.L; d.ic12f = t.d_cf + 4 * t.N;
   d.ph[0] = t.ph[0]; d.ph[1] = t.ph[1];
   d.Lc = t.Lc;
   d.lf = reinterpret_cast<const int4*>(t.d_tab);
@@ -200,6 +201,8 @@ __global__ void k_setup_tree(int K, const double* w_raw, double* c, float* cf) {
     cf[N + h - 1] = (float)c2;
     cf[2 * N + h - 1] = (float)(c1 * c2);
     cf[3 * N + h - 1] = (float)(W[h - 1] * c1 * c2);
+    c[3 * N + L + h - 1] = 1.0 / (c1 * c2);
+    cf[4 * N + h - 1] = (float)(1.0 / (c1 * c2));
   }
   for (int l = 0; l < L; ++l) c[3 * N + l] = w_raw[l] / s;
 }
@@ -1109,8 +1112,8 @@ const char* check_tree(const dmn_tree_desc& d, bool allow_zero = false) {
 // weights positive the result is the full tree in table form.
 struct CmpTree {
   int N = 0, Lc = 0, nz = 0;
-  std::vector<double> p, q, c;   // p, q [N][M]; c = c1 [N], c2 [N], sc [N], leaf weights [L]
-  std::vector<float> cf;         // c1f [N], c2f [N], c12f [N], scf [N]
+  std::vector<double> p, q, c;   // p, q [N][M]; c = c1 [N], c2 [N], sc [N], leaf weights [L], 1 / (c1 c2) [N]
+  std::vector<float> cf;         // c1f [N], c2f [N], c12f [N], scf [N], 1 / (c1 c2) [N]
   std::vector<int> tab;          // lf [Lc] (4 ints each), pre [N], post [N], paper index [N], children [2 N],
                                  // the laminate at each heap position [2^K - 1]
 };
@@ -1136,7 +1139,7 @@ void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& 
   const int Nc = (int)paper_of.size();
   B.N = Nc;
   B.p.resize((size_t)Nc * M); B.q.resize((size_t)Nc * M);
-  B.c.assign(3 * (size_t)Nc + L, 0.0); B.cf.assign(4 * (size_t)Nc, 0.0f);
+  B.c.assign(4 * (size_t)Nc + L, 0.0); B.cf.assign(5 * (size_t)Nc, 0.0f);
   for (int c = 0; c < Nc; ++c)
     for (int m = 0; m < M; ++m) { B.p[c * M + m] = d.p[paper_of[c] * M + m]; B.q[c * M + m] = d.q[paper_of[c] * M + m]; }
   for (int h = 1; h <= N; ++h) {
@@ -1146,6 +1149,8 @@ void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& 
     B.c[c] = c1; B.c[Nc + c] = c2; B.c[2 * Nc + c] = W[h] * c1 * c2;
     B.cf[c] = (float)c1; B.cf[Nc + c] = (float)c2; B.cf[2 * Nc + c] = (float)(c1 * c2);
     B.cf[3 * Nc + c] = (float)B.c[2 * Nc + c];
+    B.c[3 * Nc + L + c] = 1.0 / (c1 * c2);
+    B.cf[4 * Nc + c] = (float)(1.0 / (c1 * c2));
   }
   for (int l = 0; l < L; ++l) B.c[3 * Nc + l] = W[N + 1 + l];
   std::vector<int> lf, pre, post;
@@ -1559,8 +1564,8 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     heap_params(d, ph.data(), qh.data());
     e = cudaMalloc(&T.d_p, sizeof(double) * N * M);
     if (e == cudaSuccess) e = cudaMalloc(&T.d_q, sizeof(double) * N * M);
-    if (e == cudaSuccess) e = cudaMalloc(&T.d_c, sizeof(double) * (3 * N + L));
-    if (e == cudaSuccess) e = cudaMalloc(&T.d_cf, sizeof(float) * 4 * N);
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_c, sizeof(double) * (4 * N + L));
+    if (e == cudaSuccess) e = cudaMalloc(&T.d_cf, sizeof(float) * 5 * N);
     if (e == cudaSuccess) e = cudaMemcpy(T.d_p, ph.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(T.d_q, qh.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_w, d.w, sizeof(double) * L, cudaMemcpyHostToDevice);
@@ -2018,7 +2023,7 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   td.z_both = n_inel == 2;
   td.nz = n_inel * (L / 2);
   // sizes against the fixed work space: parameters, then whole CTAs of lane scratch
-  const size_t param_doubles = (size_t)2 * N * M + (size_t)L + 3 * (size_t)N + (size_t)L + 2 * (size_t)N;
+  const size_t param_doubles = (size_t)2 * N * M + (size_t)L + 4 * (size_t)N + (size_t)L + (5 * (size_t)N + 1) / 2;
   const size_t lane_bytes = sizeof(double) * (size_t)27 * N;
   const size_t avail = DMN_NOALLOC_BYTES - 256 - sizeof(double) * NOALLOC_PARAM_DOUBLES;
   const int64_t nslots = (int64_t)(avail / lane_bytes) / NOALLOC_BLOCK * NOALLOC_BLOCK;
@@ -2042,7 +2047,7 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   double* d_q = d_p + N * M;
   double* d_w = d_q + N * M;
   double* d_c = d_w + L;
-  float* d_cf = (float*)(d_c + 3 * N + L);
+  float* d_cf = (float*)(d_c + 4 * N + L);
   double* slots = (double*)(base + 256 + sizeof(double) * NOALLOC_PARAM_DOUBLES);
 
   // parameters in heap order, handed to the device by value as a kernel argument
@@ -2061,6 +2066,7 @@ extern "C" int dmn_update_noalloc(const dmn_tree_desc* tree, const dmn_options* 
   td.c1 = d_c; td.c2 = d_c + N; td.sc = d_c + 2 * N;
   td.c1f = d_cf; td.c2f = d_cf + N; td.c12f = d_cf + 2 * N; td.scf = d_cf + 3 * N;
   td.wl = d_c + 3 * N;
+  td.ic12 = d_c + 3 * N + L; td.ic12f = d_cf + 4 * N;
   td.wsum = 0.0;
   for (int l = 0; l < L; ++l) td.wsum += d.w[l];
   NoAllocParams P{td, n, nslots, lam, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status, slots,

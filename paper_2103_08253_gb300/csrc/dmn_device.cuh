@@ -66,6 +66,8 @@ struct TreeDev {
   const float* c2f;
   const float* c12f;
   const float* scf;  // [N] FP32 copy of sc
+  const double* ic12;  // [N] 1 / (c1 c2): the stored Newton step is c1 c2 (g, H), see condense
+  const float* ic12f;  // [N] FP32 copy
   const double* wl;  // [L] normalised leaf weights
   double wsum;       // sum of the leaf weights as given
   PhaseDev ph[2];
@@ -95,6 +97,13 @@ template <typename T>
 struct NodeC {
   T c1, c2, c12;
 };
+// 1 / (c1 c2) of a laminate in precision T
+template <typename T>
+__device__ __forceinline__ T ic12_of(const TreeDev& t, int node);
+template <>
+__device__ __forceinline__ double ic12_of<double>(const TreeDev& t, int node) { return __ldg(t.ic12 + node); }
+template <>
+__device__ __forceinline__ float ic12_of<float>(const TreeDev& t, int node) { return __ldg(t.ic12f + node); }
 template <typename T>
 __device__ __forceinline__ NodeC<T> node_c(const TreeDev& t, int node);
 template <>
@@ -406,16 +415,16 @@ __device__ __forceinline__ T N_entry(const T n[3], const T nr[3], int I, int j) 
   return (T)0;
 }
 
-// Symmetric 3x3 inverse by cofactors (the matrix is positive definite).
+// Symmetric 3x3 inverse by cofactors (the matrix is positive definite), times s.
 template <typename T>
-__device__ __forceinline__ void inv3_sym(T k00, T k01, T k02, T k11, T k12, T k22, T Ki[3][3]) {
+__device__ __forceinline__ void inv3_sym(T k00, T k01, T k02, T k11, T k12, T k22, T Ki[3][3], T s = (T)1) {
   const T i00 = k11 * k22 - k12 * k12;
   const T i01 = k02 * k12 - k01 * k22;
   const T i02 = k01 * k12 - k02 * k11;
   const T i11 = k00 * k22 - k02 * k02;
   const T i12 = k01 * k02 - k00 * k12;
   const T i22 = k00 * k11 - k01 * k01;
-  const T idet = (T)1 / (k00 * i00 + k01 * i01 + k02 * i02);
+  const T idet = s / (k00 * i00 + k01 * i01 + k02 * i02);
   Ki[0][0] = i00 * idet; Ki[0][1] = i01 * idet; Ki[0][2] = i02 * idet;
   Ki[1][0] = Ki[0][1];   Ki[1][1] = i11 * idet; Ki[1][2] = i12 * idet;
   Ki[2][0] = Ki[0][2];   Ki[2][1] = Ki[1][2];   Ki[2][2] = i22 * idet;
@@ -490,19 +499,16 @@ __device__ __forceinline__ void condense(const S nd[3], const T n[3], S c1d, S c
   const T k11 = n[1] * ChN[1][1] + nr[2] * ChN[3][1] + nr[0] * ChN[5][1];
   const T k21 = n[2] * ChN[2][1] + nr[1] * ChN[3][1] + nr[0] * ChN[4][1];
   const T k22 = n[2] * ChN[2][2] + nr[1] * ChN[3][2] + nr[0] * ChN[4][2];
+  // the inverse times c1 c2: H and g come out as c1 c2 H, c1 c2 g, so that the condensed outputs
+  // are multiply-add chains; the descent multiplies the step by 1 / (c1 c2)
   T Ki[3][3];
-  inv3_sym<T>(k00, k10, k20, k11, k21, k22, Ki);
-  T H[3][6];
+  inv3_sym<T>(k00, k10, k20, k11, k21, k22, Ki, c12);
+  T H[3][6];   // c1 c2 H
 #pragma unroll
   for (int m = 0; m < 3; ++m)
 #pragma unroll
     for (int I = 0; I < 6; ++I) H[m][I] = -(Ki[m][0] * B[I][0] + Ki[m][1] * B[I][1] + Ki[m][2] * B[I][2]);
-  T dds[6], v[3], g[3];
-  T B12[6][3];   // c1 c2 B: the condensed outputs then take pure multiply-add chains
-#pragma unroll
-  for (int I = 0; I < 6; ++I)
-#pragma unroll
-    for (int m = 0; m < 3; ++m) B12[I][m] = c12 * B[I][m];
+  T dds[6], v[3], g[3];   // g: c1 c2 g
   if (STORE) {
 #pragma unroll
     for (int I = 0; I < 6; ++I) dds[I] = R.ds[I] - L.ds[I];
@@ -513,7 +519,7 @@ __device__ __forceinline__ void condense(const S nd[3], const T n[3], S c1d, S c
     for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
 #pragma unroll
     for (int I = 0; I < 6; ++I)
-      out.ds[I] = L.ds[I] + c2 * dds[I] + B12[I][0] * g[0] + B12[I][1] * g[1] + B12[I][2] * g[2];
+      out.ds[I] = L.ds[I] + c2 * dds[I] + B[I][0] * g[0] + B[I][1] * g[1] + B[I][2] * g[2];
   } else {
 #pragma unroll
     for (int I = 0; I < 6; ++I) out.ds[I] = (T)0;
@@ -524,9 +530,9 @@ __device__ __forceinline__ void condense(const S nd[3], const T n[3], S c1d, S c
     for (int J = I; J < 6; ++J) {
       const int s = sidx(I, J);
       T v = L.C[s] + c2 * dC[s];
-      v += B12[I][0] * H[0][J];
-      v += B12[I][1] * H[1][J];
-      v += B12[I][2] * H[2][J];
+      v += B[I][0] * H[0][J];
+      v += B[I][1] * H[1][J];
+      v += B[I][2] * H[2][J];
       out.C[s] = v;
     }
   if (STORE) {
@@ -598,8 +604,8 @@ __device__ __forceinline__ void condense_bottom(const S nd[3], const T n[3], S c
 #pragma unroll
     for (int I = 0; I < 6; ++I) cmR[I] = DR.c * DR.m[I];
   }
-  T Ki[3][3];
-  inv3_sym<T>(k[0][0], k[0][1], k[0][2], k[1][1], k[1][2], k[2][2], Ki);
+  T Ki[3][3];   // times c1 c2, as in condense
+  inv3_sym<T>(k[0][0], k[0][1], k[0][2], k[1][1], k[1][2], k[2][2], Ki, c12);
   // (lam_R - lam_L) 1 (x) n + 2 (mu_R - mu_L) N: entry (I, j) is dlam n_j (I < 3, j != I),
   // (dlam + dmu2) n_j (I = j) or dmu2 N_Ij (shear rows)
   const T dlam = DR.lam - DL.lam, dmu2 = (T)2 * (DR.mu - DL.mu), dld = dlam + dmu2;
@@ -621,34 +627,28 @@ __device__ __forceinline__ void condense_bottom(const S nd[3], const T n[3], S c
 #pragma unroll
       for (int j = 0; j < 3; ++j) B[I][j] -= cmR[I] * uR[j];
   }
-  T H[3][6];
+  T H[3][6];   // c1 c2 H
 #pragma unroll
   for (int m = 0; m < 3; ++m)
 #pragma unroll
     for (int I = 0; I < 6; ++I) H[m][I] = -(Ki[m][0] * B[I][0] + Ki[m][1] * B[I][1] + Ki[m][2] * B[I][2]);
-  T g[3] = {(T)0, (T)0, (T)0};
+  T g[3] = {(T)0, (T)0, (T)0};   // c1 c2 g
   if (STORE) {
 #pragma unroll
     for (int m = 0; m < 3; ++m) g[m] = -(Ki[m][0] * u[0] + Ki[m][1] * u[1] + Ki[m][2] * u[2]);
-    const T g12[3] = {c12 * g[0], c12 * g[1], c12 * g[2]};
 #pragma unroll
-    for (int I = 0; I < 6; ++I) out.ds[I] = B[I][0] * g12[0] + B[I][1] * g12[1] + B[I][2] * g12[2];
+    for (int I = 0; I < 6; ++I) out.ds[I] = B[I][0] * g[0] + B[I][1] * g[1] + B[I][2] * g[2];
   } else {
 #pragma unroll
     for (int I = 0; I < 6; ++I) out.ds[I] = (T)0;
   }
   const T lamC = c1 * DL.lam + c2 * DR.lam, mu2C = (T)2 * (c1 * DL.mu + c2 * DR.mu);
-  T H12[3][6];
-#pragma unroll
-  for (int m = 0; m < 3; ++m)
-#pragma unroll
-    for (int I = 0; I < 6; ++I) H12[m][I] = c12 * H[m][I];
   T Cb[21];
 #pragma unroll
   for (int I = 0; I < 6; ++I)
 #pragma unroll
     for (int J = I; J < 6; ++J) {
-      T v = B[I][0] * H12[0][J] + B[I][1] * H12[1][J] + B[I][2] * H12[2][J];
+      T v = B[I][0] * H[0][J] + B[I][1] * H[1][J] + B[I][2] * H[2][J];
       if (I < 3 && J < 3) v += lamC;
       if (I == J) v += mu2C;
       Cb[sidx(I, J)] = v;
@@ -725,7 +725,7 @@ __device__ __forceinline__ int jump_index(const PointArrays& P, int K, int lvl, 
 
 template <typename T>
 struct GH {
-  T* p; size_t s;  // g and H of laminate node read by a pass: p[(21*node + c)*s], c = 0..2 g, 3..20 H
+  T* p; size_t s;  // c1 c2 g and c1 c2 H of laminate node read by a pass: p[(21*node + c)*s], c = 0..2 g, 3..20 H
   T* q;            // where the pass stores the new g and H (== p: in place)
 };
 
@@ -771,7 +771,8 @@ __device__ __forceinline__ void load_z(const TreeDev& t, const PointArrays& P, i
 //           step scaled by `step` on the way down, da = step g + H d_eps with the
 //           g, H stored by the previous pass, a_out = a + da (top-down
 //           redistribution; the scaled step is the same linear map applied to
-//           step g); then store this pass's g, H for the next step.
+//           step g); then store this pass's g, H for the next step (both times c1 c2: the
+//           descent applies 1 / (c1 c2) to the step).
 //   !STORE: evaluation at the given jumps only (final sweep).
 // Returns the root's subtree result (sb = effective stress, C = tangent of the
 // linearised DMN) and the squared norm of A^T W sigma at the (updated) jumps.
@@ -812,12 +813,13 @@ __device__ void tree_pass(const TreeDev& t, const S Eloc[6], const PointArrays& 
       T da[3] = {(T)0, (T)0, (T)0};
       if (STORE) {   // only the Newton kernel corrects jumps; `apply` is false on a point's first pass
         const T* gp = gh.p + (size_t)(21 * node) * gh.s;
+        const T ic = ic12_of<T>(t, node);   // the stored step is c1 c2 (g, H)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           T v = step * gp[c * gh.s];
 #pragma unroll
           for (int I = 0; I < 6; ++I) v += gp[(3 + 6 * c + I) * gh.s] * de[I];
-          da[c] = apply ? v : (T)0;
+          da[c] = apply ? v * ic : (T)0;
         }
         S* aw = a_wr + aoff;
 #pragma unroll
@@ -951,12 +953,13 @@ __device__ void tree_pass_c(const TreeDev& t, const S Eloc[6], const PointArrays
       T da[3] = {(T)0, (T)0, (T)0};
       if (STORE) {
         const T* gp = gh.p + (size_t)(21 * node) * gh.s;
+        const T ic = ic12_of<T>(t, node);   // the stored step is c1 c2 (g, H)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           T v = step * gp[c * gh.s];
 #pragma unroll
           for (int I = 0; I < 6; ++I) v += gp[(3 + 6 * c + I) * gh.s] * de[I];
-          da[c] = apply ? v : (T)0;
+          da[c] = apply ? v * ic : (T)0;
         }
         S* aw = a_wr + (size_t)(3 * node) * P.as;
 #pragma unroll
@@ -1177,13 +1180,15 @@ __device__ void adjoint_pass(const TreeDev& t, const double Eloc[6], const doubl
       const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
       const double* ap = P.a + (size_t)(3 * jump_index(P, K, lvl, node)) * P.as;
       const double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
-      const double* Hp = Wk.H + (size_t)(21 * node + 3) * Wk.hs;
+      const double* Hp = Wk.H + (size_t)(21 * node + 3) * Wk.hs;   // c1 c2 H, as the pass stores it
+      const double ic = __ldg(t.ic12 + node);
       double mu[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         double v = 0.0;
 #pragma unroll
         for (int I = 0; I < 6; ++I) v += Hp[(6 * c + I) * Wk.hs] * ge[I];
+        v *= ic;
         mu[c] = v;
         Wk.mu[(size_t)(3 * node + c) * ws] = v;
       }
@@ -1340,13 +1345,15 @@ __device__ void adjoint_pass_c(const TreeDev& t, const double Eloc[6], const dou
       const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
       const double* ap = P.a + (size_t)(3 * node) * P.as;
       const double a[3] = {ap[0], ap[P.as], ap[2 * P.as]};
-      const double* Hp = Wk.H + (size_t)(21 * node + 3) * Wk.hs;
+      const double* Hp = Wk.H + (size_t)(21 * node + 3) * Wk.hs;   // c1 c2 H, as the pass stores it
+      const double ic = __ldg(t.ic12 + node);
       double mu[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         double v = 0.0;
 #pragma unroll
         for (int I = 0; I < 6; ++I) v += Hp[(6 * c + I) * Wk.hs] * ge[I];
+        v *= ic;
         mu[c] = v;
         Wk.mu[(size_t)(3 * node + c) * ws] = v;
       }

@@ -107,7 +107,7 @@ struct Tree {
         const int j = L - (1 << k) + (i - 1), hn = (1 << (k - 1)) + i - 2;
         for (int m = 0; m < M; ++m) { hp[hn * M + m] = p[j * M + m]; hq[hn * M + m] = q[j * M + m]; }
       }
-    c.resize(3 * N + L); cf.resize(4 * N);
+    c.resize(4 * N + L); cf.resize(5 * N);
     std::vector<double> Wsub(N);
     double s = 0.0;
     for (int l = 0; l < L; ++l) s += w[l];
@@ -120,11 +120,13 @@ struct Tree {
       c[h - 1] = c1; c[N + h - 1] = c2; c[2 * N + h - 1] = Wsub[h - 1] * c1 * c2;
       cf[h - 1] = (float)c1; cf[N + h - 1] = (float)c2; cf[2 * N + h - 1] = (float)(c1 * c2);
       cf[3 * N + h - 1] = (float)c[2 * N + h - 1];
+      c[3 * N + L + h - 1] = 1.0 / (c1 * c2); cf[4 * N + h - 1] = (float)(1.0 / (c1 * c2));
     }
     for (int l = 0; l < L; ++l) c[3 * N + l] = w[l] / s;
     t.p = hp.data(); t.q = hq.data();
     t.c1 = c.data(); t.c2 = c.data() + N; t.sc = c.data() + 2 * N; t.wl = c.data() + 3 * N;
     t.c1f = cf.data(); t.c2f = cf.data() + N; t.c12f = cf.data() + 2 * N; t.scf = cf.data() + 3 * N;
+    t.ic12 = c.data() + 3 * N + L; t.ic12f = cf.data() + 4 * N;
     t.wsum = s;
     S = 6L * t.nz + 3L * N;
   }
@@ -148,7 +150,7 @@ struct Tree {
       }
     const int Nc = (int)paper.size();
     hp.assign((size_t)std::max(Nc, 1) * M, 0.0); hq.assign((size_t)std::max(Nc, 1) * M, 0.0);
-    c.assign(3 * (size_t)Nc + L, 0.0); cf.assign(4 * (size_t)std::max(Nc, 1), 0.0f);
+    c.assign(4 * (size_t)Nc + L, 0.0); cf.assign(5 * (size_t)std::max(Nc, 1), 0.0f);
     for (int k = 0; k < Nc; ++k)
       for (int m = 0; m < M; ++m) { hp[k * M + m] = p[paper[k] * M + m]; hq[k * M + m] = q[paper[k] * M + m]; }
     for (int h = 1; h <= N; ++h) {
@@ -158,6 +160,7 @@ struct Tree {
       c[k] = c1; c[Nc + k] = c2; c[2 * Nc + k] = Wh[h] * c1 * c2;
       cf[k] = (float)c1; cf[Nc + k] = (float)c2; cf[2 * Nc + k] = (float)(c1 * c2);
       cf[3 * Nc + k] = (float)c[2 * Nc + k];
+      c[3 * Nc + L + k] = 1.0 / (c1 * c2); cf[4 * Nc + k] = (float)(1.0 / (c1 * c2));
     }
     for (int l = 0; l < L; ++l) c[3 * Nc + l] = Wh[N + 1 + l];
     std::vector<int> lf, pre, post;
@@ -208,6 +211,7 @@ struct Tree {
     t.p = hp.data(); t.q = hq.data();
     t.c1 = c.data(); t.c2 = c.data() + Nc; t.sc = c.data() + 2 * Nc; t.wl = c.data() + 3 * Nc;
     t.c1f = cf.data(); t.c2f = cf.data() + Nc; t.c12f = cf.data() + 2 * Nc; t.scf = cf.data() + 3 * Nc;
+    t.ic12 = c.data() + 3 * Nc + L; t.ic12f = cf.data() + 4 * Nc;
     t.wsum = s;
     S = 6L * nz + 3L * Nc;
   }
