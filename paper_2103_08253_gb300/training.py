@@ -123,7 +123,9 @@ class Trainer:
         self.pl_phases = None if plastic is None else (W.FIBER, plastic)
         start = W.TreeParams(K, M, self.p.detach().cpu().numpy(), self.q.detach().cpu().numpy(), v0 / v0.sum(),
                              el_phases)
-        self.m_el = dmn.DMN(start, precision=elastic_precision)
+        # the stiffness samples' update at zero strain meets the criterion at its first evaluation: an
+        # all-FP32 first stage would only add a pass
+        self.m_el = dmn.DMN(start, precision=elastic_precision, first_stage=False)
         self.pattern = v0 > 0
         tgt_el = dmn.DMN(W.TreeParams(K, M, target.p, target.q, target.w, el_phases))
         A2, lam, Q = W.orientation_field(n_stiff, seed=seed + 1)
@@ -165,7 +167,8 @@ class Trainer:
         self.rebuilds += 1
         p, q, wn = (x.detach().cpu().numpy() for x in (self.p, self.q, w))
         self.m_el.close()
-        self.m_el = dmn.DMN(W.TreeParams(self.K, 3, p, q, wn, self.el_phases), precision=self.el_prec)
+        self.m_el = dmn.DMN(W.TreeParams(self.K, 3, p, q, wn, self.el_phases), precision=self.el_prec,
+                            first_stage=False)
         if self.m_pl is not None:
             self.m_pl.close()
             self.m_pl = dmn.DMN(W.TreeParams(self.K, 3, p, q, wn, self.pl_phases), line_search=True,

@@ -156,3 +156,26 @@ def test_fp64_form_after_the_first_stage():
             assert ps["newton"] < 0.7 * pp["newton"]
     m.close()
     plain.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "mixed-f32-tangent"])
+def test_first_stage_ragged_sizes_and_depths(prec):
+    """The stage at depths 1..8 and batch sizes that are not multiples of a warp or a CTA (one point
+    included), against the oracle; and no launch at all for an empty batch."""
+    for K, n in ((1, 1), (2, 33), (3, 129), (5, 257), (8, 37)):
+        tree = W.tree_d10_fit(K, seed=350 + K)
+        A2, lam, Q = W.orientation_field(n, seed=360 + K)
+        Ef = W.random6_path_final(n, 0.025, seed=370 + K)
+        worst, out, _ = run_path(tree, lam, Q, Ef, 4, prec, first_stage=True)
+        assert worst["stress"] <= 1e-6, (K, n, worst)
+        assert worst["tangent"] <= (1e-6 if prec == "mixed" else 1e-4), (K, n, worst)
+    tree = W.tree_d10_fit(4, seed=380)
+    m = dmn.DMN(tree, precision=prec)
+    S = m.state_size
+    m.profile(True)
+    out = m.update(d(np.zeros((0, 2))), d(np.zeros((0, 9))), d(np.zeros((0, 6))), d(np.zeros((0, 6))),
+                   torch.zeros((S, 0), dtype=torch.float64, device=DEV))
+    assert out["stress"].shape == (0, 6)
+    _, passes, upd = m.profile_read_stages()
+    assert passes == {"stage": 0, "newton": 0} and upd == 0
+    m.close()
