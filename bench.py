@@ -343,6 +343,13 @@ def form_stage(form):
     return prec != "f64" or form.endswith("/stage")
 
 
+def form_stage_option(form):
+    """The handle's first_stage argument for the form: explicit only where the form names it ("/stage",
+    "/no-stage"), else the library default (on in the mixed forms; a small call, which runs one warp
+    per point, goes without it)."""
+    return True if form.endswith("/stage") else False if form.endswith("/no-stage") else None
+
+
 def tune_shape(form, ctx, args):
     """Launch shape of the Newton kernel from the autotuner, tuned on the first 2^18 points at the
     first timed increment (after the warm-up increments).  Forms that differ only in the start
@@ -383,7 +390,8 @@ def run_form(form, ctx, args, dist):
     shape = tune_shape(form, ctx, args) if args.autotune else None
     prec, pred = form_opts(form)
     m = dmn.DMN(ctx["tree"], precision=prec, block=shape["block"] if shape else 0,
-                ctas_per_sm=shape["ctas_per_sm"] if shape else 0, predictor=pred, first_stage=form_stage(form),
+                ctas_per_sm=shape["ctas_per_sm"] if shape else 0, predictor=pred,
+                first_stage=form_stage_option(form),
                 stage_ctas_per_sm=shape["stage_ctas_per_sm"] if shape else 0)
     assert m.first_stage == form_stage(form)
     S = m.state_size
@@ -427,13 +435,15 @@ def run_form(form, ctx, args, dist):
     clk = clocks.stop() if clocks else None
     kms, passes, cnt = m.profile_read_stages()
     m.profile(False)
-    if not form_stage(form):
+    warp = m.warp_per_point_for(n)   # a small call runs one warp per point, without the first stage
+    if not form_stage(form) or warp:
         kms.pop("stage")
     its = iters_steps.to(torch.int64).sum().item()
     hist = torch.bincount(iters_steps.reshape(-1).to(torch.int64), minlength=1).cpu().numpy()
     res = dict(t_ms=t_ms, kms=kms, updates=cnt, clocks=clk, iters_sum=int(its), iters_hist=hist.tolist(),
-               passes=passes,
-               launch=(dict(block=shape["block"], ctas_per_sm=shape["ctas_per_sm"], tuned_on_points=shape["points"],
+               passes=passes, warp=warp,
+               launch=("one warp per point (k_newton_warp, 2 CTAs of 4 warps per SM)" if warp else
+                       dict(block=shape["block"], ctas_per_sm=shape["ctas_per_sm"], tuned_on_points=shape["points"],
                             table=shape["table"], stage_ctas_per_sm=shape["stage_ctas_per_sm"],
                             stage_table=shape["stage_table"]) if shape else "defaults"),
                stress=out["stress"], tangent=out["tangent"], status=out["status"], state=st[cur],
@@ -487,17 +497,18 @@ def run_e2e(r, ctx, args, dist):
     # untimed call (its own state_out): allocates the library's stage buffers and second work set
     m.update_host(lam_h, Q_h, En_h[0], dE_h[0], st_h, out=out_h, chunk=args.e2e_chunk)
     out_h["state_out"] = st_h
-    # copy bandwidth of this process's pinned state buffer (1 GiB each way), for the record; the
-    # device-to-host copy writes back the bytes the host-to-device copy just read
-    probe = torch.empty(1 << 27, dtype=torch.float64, device=ctx["dev"])
-    flat = st_h.view(-1)[: 1 << 27]
+    # copy bandwidth of this process's pinned state buffer (up to 1 GiB each way), for the record;
+    # the device-to-host copy writes back the bytes the host-to-device copy just read
+    cnt = min(1 << 27, st_h.numel())
+    probe = torch.empty(cnt, dtype=torch.float64, device=ctx["dev"])
+    flat = st_h.view(-1)[:cnt]
     bw = {}
     for name, dst, src in (("h2d_GBps", probe, flat), ("d2h_GBps", flat, probe)):
         torch.cuda.synchronize()
         c0 = time.perf_counter()
         dst.copy_(src, non_blocking=True)
         torch.cuda.synchronize()
-        bw[name] = round(8 * (1 << 27) / (time.perf_counter() - c0) / 1e9, 1)
+        bw[name] = round(8 * cnt / (time.perf_counter() - c0) / 1e9, 1)
     del probe
     h2d = lam_h.nbytes + Q_h.nbytes + En_h[0].nbytes + dE_h[0].nbytes + st_h.nbytes
     d2h = (out_h["stress"].nbytes + out_h["tangent"].nbytes + st_h.nbytes + out_h["iters"].nbytes
@@ -536,8 +547,10 @@ def roofline_f64(r, n, steps, w=None, peaks=None):
     t = r["kms"]["newton"] * 1e-3
     ach = F / t / 1e9
     cmp = "_compressed" if w is not None and (np.asarray(w) == 0).any() else ""
-    tr = ncu_traffic("k_newton_f64" + cmp + ("_stage" if "stage" in r["kms"] else ""), n)
-    out = {"bound": "alu", "kernel": "k_newton<double>", "achieved": ach, "peak": P64,
+    org = "_warp" if r.get("warp") else ""
+    tr = ncu_traffic("k_newton" + org + "_f64" + cmp + ("_stage" if "stage" in r["kms"] else ""), n)
+    out = {"bound": "alu", "kernel": "k_newton_warp<double>" if org else "k_newton<double>", "achieved": ach,
+           "peak": P64,
            "unit": "GFLOP/s (FP64)", "frac": ach / P64, "traffic": tr,
            "flops_per_launch": F / steps, "launch_ms": r["kms"]["newton"] / steps,
            "frac_of_derived_peak": ach / PEAK_F64_GFLOPS, "peak_note": pk["note"],
@@ -575,9 +588,10 @@ def roofline_mixed(r, n, steps, w=None, sweep=True, peaks=None):
            "unit": "GFLOP/s (FP64)", "frac": Ff / tf / 1e9 / P64, "launch_ms": r["kms"]["final"] / steps}
     cmp = "_compressed" if w is not None and (np.asarray(w) == 0).any() else ""
     stg = "stage" in r["kms"]
-    out = {"bound": "alu", "kernel": "k_newton<float>", "achieved": tb / t * P64,
+    org = "_warp" if r.get("warp") else ""
+    out = {"bound": "alu", "kernel": "k_newton_warp<float>" if org else "k_newton<float>", "achieved": tb / t * P64,
            "peak": P64, "unit": "GFLOP/s (FP64-equivalent: F64/P64 + F32/P32)", "frac": tb / t, "peak_note": pk["note"],
-           "traffic": ncu_traffic("k_newton_mixed" + cmp + ("_stage" if stg else ""), n),
+           "traffic": ncu_traffic("k_newton" + org + "_mixed" + cmp + ("_stage" if stg else ""), n),
            "flops_f64_per_launch": F64 / steps,
            "flops_f32_per_launch": F32 / steps, "launch_ms": r["kms"]["newton"] / steps,
            "passes_per_update": (newton_corr + npts) / npts, "final_kernel": fin}
@@ -627,7 +641,7 @@ def run_mixed_depth(args):
     for form in [f for f in args.forms.split(",") if f]:
         # autotuned shape on 2^18 points of the batch at the first timed increment
         prec, pred = form_opts(form)
-        stage = form_stage(form)
+        stage = form_stage_option(form)
         m0 = dmn.DMN(trees, precision=prec, first_stage=stage)
         msub = min(n, 1 << 18)
         lam_s, Q_s = m0.interp_orientation(A2_d[:msub].contiguous())

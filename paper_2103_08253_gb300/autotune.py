@@ -62,7 +62,8 @@ def tune(tree, precision, lam, Q, E_n, dE, state_in, reps=2, candidates=CANDIDAT
     n = lam.shape[0]
     table = []
     for block, cps in candidates:
-        m = dmn.DMN(tree, precision=precision, block=block, ctas_per_sm=cps, first_stage=first_stage)
+        m = dmn.DMN(tree, precision=precision, block=block, ctas_per_sm=cps, first_stage=first_stage,
+                    warp_per_point=-1)
         out = m.alloc_outputs(n, dev)
         m.update(lam, Q, E_n, dE, state_in, out=out, tree_id=tree_id)
         torch.cuda.synchronize()

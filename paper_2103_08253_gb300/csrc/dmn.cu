@@ -67,6 +67,8 @@ struct WorkSet {
   float* scr_s = nullptr;       // the mixed forms' first stage, per slot of its kernel: g, H [21N], normals [3N],
                                 // jumps [3N] (FP32)
   int64_t nslots_s = 0;         // slots of the first stage's kernel
+  double* scr_w = nullptr;      // small batches, one warp per point: a block of scratch per warp
+  int64_t nwarps_w = 0;
   double* nbuf = nullptr;       // per point: normals [3N] + local macro strain [6], field-major
   int64_t* perm = nullptr;      // points sorted by tree (several trees)
   int64_t nbuf_cap = 0;
@@ -656,6 +658,144 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   if (P.passes && npass) atomicAdd(P.passes, npass);
 }
 
+// Small batches: one warp per point (heap trees, the paper's start), the lanes sharing each level
+// of the tree (warp_tree_pass).  The Newton loop is k_newton's, warp-uniform; each warp owns a
+// block of scratch (WARP_SLOT_DOUBLES<T>(N) doubles) holding its point's jumps, g, H, level hand-over
+// and subtree results in two buffers where the line search needs them.  Points are taken one per
+// warp from the work counter.
+template <typename T>
+__host__ __device__ inline size_t warp_slot_doubles(int N) {
+  // jumps 2 x 3N, ein 6N, sb 6N, normals 3N (FP64); g, H 2 x 21N, dein 6N, ds + C 27N (T); FP32 normals 3N
+  const size_t d = (size_t)21 * N, tt = (size_t)75 * N * sizeof(T), f = (size_t)3 * N * sizeof(float);
+  return d + (tt + f + sizeof(double) - 1) / sizeof(double);
+}
+constexpr int WARP_CTAS_PER_SM = 2;   // 128-thread CTAs: 8 point warps per SM
+
+template <typename T, bool LS>
+__global__ void __launch_bounds__(128) k_newton_warp(NewtonParams<T> P, double* scratch) {
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int NM = P.N_max;
+  double* base = scratch + (size_t)gw * warp_slot_doubles<T>(NM);
+  double* abuf[2] = {base, base + 3 * NM};
+  double* ein = base + 6 * NM;
+  double* sbv = base + 12 * NM;
+  double* nrm = base + 18 * NM;
+  T* tb = reinterpret_cast<T*>(base + 21 * NM);
+  T* gbuf[2] = {tb, tb + 21 * NM};
+  T* dein = tb + 42 * NM;
+  T* dcv = tb + 48 * NM;
+  float* nrmf = reinterpret_cast<float*>(tb + 75 * NM);
+  PointArrays A{};
+  A.nrm = nrm; A.ns = 1; A.nrmf = nrmf;
+  A.as = 1; A.paper = false;
+  A.zs = (size_t)P.n;
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  unsigned long long npass = 0;
+  for (;;) {
+    unsigned long long i = 0;
+    if (lane == 0) i = atomicAdd(P.counter, 1ull);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= (unsigned long long)P.n) break;
+    int64_t pt;
+    int tr;
+    point_of(P.perm, P.tid, P.F.n, (int64_t)i, pt, tr);
+    if (tr >= P.F.n) {   // unknown tree: report and take the next point
+      if (lane == 0) {
+        P.iters[pt] = 0;
+        P.status[pt] = DMN_STATUS_BAD_TREE;
+        for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
+        for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
+      }
+      continue;
+    }
+    const TreeDev& t = P.F.t[tr];
+    const int nzf = 6 * t.nz;
+    double Eloc[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * NM + I) * P.n + pt];
+    for (int f = lane; f < 3 * t.N; f += 32) {
+      const int node = f / 3, c = f - 3 * node;
+      const int lvl = 32 - __clz(node + 1);
+      const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+      abuf[0][f] = (P.a_start ? P.a_start : P.state_in)[(size_t)(nzf + 3 * j + c) * P.n + pt];
+      const double nv = P.nbuf[(size_t)f * P.n + pt];
+      nrm[f] = nv;
+      if (sizeof(T) == 4) nrmf[f] = narrow_rn(nv);
+    }
+    A.z = P.state_in + pt;
+    const int it0 = P.a_start ? P.iters[pt] : 0;
+    int it = 0, cur = 0, halvings = 0, st = -1;
+    bool first = true;
+    T step = (T)1;
+    double rn_acc = 0.0;
+    Sub<T> root, root_acc;
+    __syncwarp();
+    for (;;) {
+      WarpSlot<T> W{abuf[cur], abuf[LS ? 1 - cur : cur], gbuf[cur], gbuf[LS ? 1 - cur : cur], ein, dein, sbv, dcv, NM};
+      ++npass;
+      double r2 = warp_tree_pass<T>(t, Eloc, A, W, !first, step, lane);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+      warp_sub_load<T>(W, 0, root);
+      __syncwarp();
+      const double rn = sqrt(r2);
+      double sn2 = 0.0;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
+      const double sn = sqrt(sn2);
+      if (!LS) {
+        first = false;
+        if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
+        else if (rn <= P.tol * (double)t.N * sn && it >= P.min_corr) st = DMN_STATUS_OK;
+        else if (it >= P.max_iter - it0) st = DMN_STATUS_MAXITER;
+        if (st < 0) { ++it; continue; }
+      } else {
+        const bool accepted = first || rn < rn_acc;
+        if (accepted) {
+          first = false;
+          cur = 1 - cur;
+          rn_acc = rn;
+          root_acc = root;
+          step = (T)1;
+          halvings = 0;
+          if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
+          else if (rn <= P.tol * (double)t.N * sn && it >= P.min_corr) st = DMN_STATUS_OK;
+          else if (it >= P.max_iter - it0) st = DMN_STATUS_MAXITER;
+          if (st < 0) { ++it; continue; }
+        } else if (++halvings > 8) {
+          st = DMN_STATUS_LINESEARCH;   // no halving lowered the residual: keep the accepted iterate
+          ++it;
+          root = root_acc;
+        } else {
+          step *= (T)0.5;
+          continue;
+        }
+      }
+      break;
+    }
+    // finished point: jumps (paper ordering), counters, and without a final sweep the local-frame
+    // stress and packed tangent for k_final to rotate
+    const double* afin = abuf[cur];
+    for (int f = lane; f < 3 * t.N; f += 32) {
+      const int node = f / 3, c = f - 3 * node;
+      const int lvl = 32 - __clz(node + 1);
+      const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+      P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt] = st == DMN_STATUS_NONFINITE ? qnan : afin[f];
+    }
+    if (lane == 0) {
+      P.iters[pt] = it + it0;
+      P.status[pt] = st;
+      if (P.write_outputs) {
+        for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = root.sb[I];
+        for (int k = 0; k < 21; ++k) P.tangent[36 * pt + k] = widen(root.C[k]);
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && P.passes && npass) atomicAdd(P.passes, npass);
+}
+
 // The mixed forms' first stage (Sec. 3.2's Newton iteration with every quantity in FP32: jumps,
 // strains, leaf return mapping, residual and condensation).  Persistent like k_newton, with its own
 // work counter and launch shape; per slot the FP32 scratch g, H [21 N], normals [3 N], jumps
@@ -1221,6 +1361,17 @@ bool first_stage_on(const dmn_options& o) {
   return want && !o.line_search && !o.predictor;
 }
 
+// one warp per point: for heap trees with the paper's start, always on request, by default (unless
+// the first stage was asked for) for batches of at most WARP_AUTO_POINTS_PER_SM points per SM.  Below that the thread-per-point
+// kernel leaves SMs idle or nearly so; at depth 8 on 152 SMs the warp kernel is 12x faster at
+// 1024 points, 1.4x at 32768, even at about 45000 and slower above.
+constexpr int64_t WARP_AUTO_POINTS_PER_SM = 256;
+bool warp_possible(const dmn_handle* h) { return h->opt.warp_per_point >= 0 && !h->cmp && !h->opt.predictor; }
+bool warp_on(const dmn_handle* h, int64_t n) {
+  return warp_possible(h) && (h->opt.warp_per_point == 1 ||
+                              (h->opt.first_stage != 1 && n <= WARP_AUTO_POINTS_PER_SM * h->n_sm));
+}
+
 // Per-slot scratch and counters of one work set (per-point buffers come with the first update).
 cudaError_t alloc_ws(const dmn_handle* h, WorkSet& w) {
   // per slot: normals + one or two jump buffers (FP64); one or two g, H buffers + FP32 normals
@@ -1232,11 +1383,18 @@ cudaError_t alloc_ws(const dmn_handle* h, WorkSet& w) {
     w.nslots_s = (int64_t)h->n_sm * h->opt.stage_ctas_per_sm * 128;
     e = cudaMalloc(&w.scr_s, sizeof(float) * (size_t)(27 * h->N_max) * w.nslots_s);
   }
+  if (e == cudaSuccess && warp_possible(h)) {
+    w.nwarps_w = (int64_t)h->n_sm * WARP_CTAS_PER_SM * 4;
+    const size_t per = h->opt.precision == DMN_PREC_F64 ? warp_slot_doubles<double>(h->N_max)
+                                                        : warp_slot_doubles<float>(h->N_max);
+    e = cudaMalloc(&w.scr_w, sizeof(double) * per * (size_t)w.nwarps_w);
+  }
   return e;
 }
 
 void free_ws(WorkSet& w) {
-  cudaFree(w.scr_d); cudaFree(w.scr_t); cudaFree(w.scr_s); cudaFree(w.counter); cudaFree(w.nbuf); cudaFree(w.perm);
+  cudaFree(w.scr_d); cudaFree(w.scr_t); cudaFree(w.scr_s); cudaFree(w.scr_w); cudaFree(w.counter); cudaFree(w.nbuf);
+  cudaFree(w.perm);
   w = WorkSet();
 }
 
@@ -1279,9 +1437,12 @@ void launch_newton(const NewtonParams<T>& P, bool ls, int minb, unsigned grid, i
 }
 
 // One update on work set w and stream s (the body of dmn_update; arguments checked by the caller).
-int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, const double* lam, const double* Q,
-              const double* E_n, const double* dE, const double* state_in, double* state_out, double* stress,
-              double* tangent, int32_t* iters, int32_t* status, cudaStream_t s) {
+// n_call is the size of the whole call (the sum of its chunks for dmn_update_host): it alone
+// chooses between the warp and the thread-per-point organisation, so that a call's points get
+// the same kernel whatever its chunks.
+int update_on(dmn_handle* h, WorkSet& w, int64_t n, int64_t n_call, const int32_t* tree_id, const double* lam,
+              const double* Q, const double* E_n, const double* dE, const double* state_in, double* state_out,
+              double* stress, double* tangent, int32_t* iters, int32_t* status, cudaStream_t s) {
   cudaError_t e;
   const int NM = h->N_max;
   const bool sort = tree_id && h->trees.size() > 1;
@@ -1332,7 +1493,9 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, cons
   const int minb = threads_per_sm > 384 ? 4 : threads_per_sm > 256 ? 3 : 2;
   const bool ls = h->opt.line_search != 0;
   const int block = h->opt.block;
-  const bool stage = first_stage_on(h->opt);
+  const bool warp = warp_on(h, n_call) && w.scr_w;
+  const bool stage = first_stage_on(h->opt) && !warp;   // a small batch goes straight to the warp kernel
+  const unsigned wgrid = (unsigned)(h->n_sm * WARP_CTAS_PER_SM);
   unsigned long long* passes = h->profiling ? h->d_passes : nullptr;
   if (stage) {   // counter [19]: the first stage's work counter
     // its corrections count against max_iter: the FP64-residual iteration keeps at least one
@@ -1349,13 +1512,17 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, const int32_t* tree_id, cons
                            w.nbuf, w.scr_d, (double*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 1,
                            h->opt.predictor, dE, stage ? state_out : nullptr, passes ? passes + 1 : nullptr,
                            stage ? 1 : 0};
-    if (h->cmp) launch_newton<double, true>(P, ls, minb, grid, block, s);
+    if (warp && ls) k_newton_warp<double, true><<<wgrid, 128, 0, s>>>(P, w.scr_w);
+    else if (warp) k_newton_warp<double, false><<<wgrid, 128, 0, s>>>(P, w.scr_w);
+    else if (h->cmp) launch_newton<double, true>(P, ls, minb, grid, block, s);
     else launch_newton<double, false>(P, ls, minb, grid, block, s);
   } else {
     NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                           w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, sweep ? 0 : 1,
                           h->opt.predictor, dE, stage ? state_out : nullptr, passes ? passes + 1 : nullptr, 0};
-    if (h->cmp) launch_newton<float, true>(P, ls, minb, grid, block, s);
+    if (warp && ls) k_newton_warp<float, true><<<wgrid, 128, 0, s>>>(P, w.scr_w);
+    else if (warp) k_newton_warp<float, false><<<wgrid, 128, 0, s>>>(P, w.scr_w);
+    else if (h->cmp) launch_newton<float, true>(P, ls, minb, grid, block, s);
     else launch_newton<float, false>(P, ls, minb, grid, block, s);
   }
   if (ev) cudaEventRecord(ev[3], s);
@@ -1484,7 +1651,7 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
 
   dmn_options o;
   o.tol = 1e-12; o.max_iter = 50; o.precision = DMN_PREC_F64; o.block = 128; o.ctas_per_sm = 0; o.line_search = 0;
-  o.predictor = 0; o.first_stage = 0; o.stage_ctas_per_sm = 0;
+  o.predictor = 0; o.first_stage = 0; o.stage_ctas_per_sm = 0; o.warp_per_point = 0;
   if (opt) {
     if (opt->tol > 0.0) o.tol = opt->tol;
     if (opt->max_iter > 0) o.max_iter = opt->max_iter;
@@ -1495,7 +1662,10 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     o.predictor = opt->predictor;
     o.first_stage = opt->first_stage;
     o.stage_ctas_per_sm = opt->stage_ctas_per_sm;
+    o.warp_per_point = opt->warp_per_point;
   }
+  if (o.warp_per_point < -1 || o.warp_per_point > 1)
+    return fail(nullptr, DMN_ERR_ARG, "dmn_create: warp_per_point must be -1, 0 or 1");
   if (o.first_stage < -1 || o.first_stage > 1)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: first_stage must be -1, 0 or 1");
   if (o.stage_ctas_per_sm == 0) o.stage_ctas_per_sm = STAGE_CTAS_DEFAULT;
@@ -1606,6 +1776,11 @@ int64_t dmn_state_size(const dmn_handle* h, int32_t tree_id) {
   return h->trees[tree_id].S;
 }
 
+int dmn_update_warp_per_point(const dmn_handle* h, int64_t n) {
+  if (!h || n < 0) return -1;
+  return warp_on(h, n) ? 1 : 0;
+}
+
 int dmn_profile_enable(dmn_handle* h, int32_t enable) {
   if (!h) return fail(nullptr, DMN_ERR_ARG, "dmn_profile_enable: NULL handle");
   if (enable) {
@@ -1680,7 +1855,7 @@ int dmn_update(dmn_handle* h, int64_t n, const int32_t* tree_id, const double* l
   if (!lam || !Q || !E_n || !dE || !state_in || !state_out || !stress || !tangent || !iters || !status)
     return fail(h, DMN_ERR_ARG, "dmn_update: NULL array");
   if (state_in == state_out) return fail(h, DMN_ERR_ARG, "dmn_update: state_in and state_out must differ");
-  return update_on(h, h->ws[0], n, tree_id, lam, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status,
+  return update_on(h, h->ws[0], n, n, tree_id, lam, Q, E_n, dE, state_in, state_out, stress, tangent, iters, status,
                    (cudaStream_t)stream);
 }
 
@@ -1737,7 +1912,7 @@ int dmn_update_host(dmn_handle* h, int64_t n, const int32_t* tree_id, const doub
     if (e == cudaSuccess && tree_id)
       e = cudaMemcpyAsync(V.state_out, V.state_in, c8 * (size_t)S, cudaMemcpyDeviceToDevice, P.comp[b]);
     if (e != cudaSuccess) { rc = cuda_fail(h, e, "dmn_update_host: copy in"); break; }
-    rc = update_on(h, h->ws[b], c, tree_id ? V.tid : nullptr, V.lam, V.Q, V.E_n, V.dE, V.state_in, V.state_out,
+    rc = update_on(h, h->ws[b], c, n, tree_id ? V.tid : nullptr, V.lam, V.Q, V.E_n, V.dE, V.state_in, V.state_out,
                    V.stress, V.tangent, V.iters, V.status, P.comp[b]);
     if (rc != DMN_OK) break;
     e = cudaEventRecord(P.done[b], P.comp[b]);

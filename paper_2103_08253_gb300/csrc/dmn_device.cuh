@@ -1764,6 +1764,153 @@ __device__ void tangent_level_rev(const TreeDev& t, bool cmp, int lvl, int lane,
 __device__ __forceinline__ int tangent_root(const TreeDev& t, bool cmp) { return cmp ? t.N - 1 : 0; }
 
 // ---------------------------------------------------------------------------
+// One Newton pass of one point by the 32 lanes of a warp, level by level of a heap tree (small
+// batches, where one point per thread leaves most of the GPU idle).  The per-laminate arithmetic
+// is that of tree_pass -- the same functions in the same order -- so a point's iterates are
+// those of the thread-per-point kernel to rounding (the two are compiled apart, and the
+// residual's squares are summed in another order: the lanes' partial sums are reduced at the
+// end).  The lanes share a level's
+// laminates: top-down the jump correction and the children's strains (each laminate hands them
+// to its children through ein / dein), then at the bottom level the leaves and the structured
+// condensation, then bottom-up the condensation of each level from its children's results
+// (sb, dc); a warp barrier separates the levels.
+// Per-point arrays (one block per warp), field-major over the laminates, stride N (the handle's
+// largest tree): jumps a [N][3]; c1 c2 (g, H) [21][N]; ein [6][N] (FP64) and dein [6][N] (T);
+// results sb [6][N] (FP64), ds and C [27][N] (T); normals in P (nrm / nrmf [N][3], stride 1).
+template <typename T>
+struct WarpSlot {
+  const double* a_in; double* a_out;
+  const T* gh_in; T* gh_out;
+  double* ein; T* dein;
+  double* sb; T* dc;
+  int N;
+};
+
+template <typename T>
+__device__ __forceinline__ void warp_sub_store(const WarpSlot<T>& W, int node, const Sub<T>& r) {
+#pragma unroll
+  for (int I = 0; I < 6; ++I) W.sb[I * W.N + node] = r.sb[I];
+#pragma unroll
+  for (int I = 0; I < 6; ++I) W.dc[I * W.N + node] = r.ds[I];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) W.dc[(6 + k) * W.N + node] = r.C[k];
+}
+template <typename T>
+__device__ __forceinline__ void warp_sub_load(const WarpSlot<T>& W, int node, Sub<T>& r) {
+#pragma unroll
+  for (int I = 0; I < 6; ++I) r.sb[I] = W.sb[I * W.N + node];
+#pragma unroll
+  for (int I = 0; I < 6; ++I) r.ds[I] = W.dc[I * W.N + node];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) r.C[k] = W.dc[(6 + k) * W.N + node];
+}
+
+// One level of the descent (lvl = 1 .. K): lane `lane` of 32 takes every 32nd laminate of the level;
+// at the bottom level it also evaluates the laminate's leaves and its structured condensation.
+// Adds the lane's share of the squared residual norm to r2.
+template <typename T>
+__device__ void warp_descend_level(const TreeDev& t, const double Eloc[6], const PointArrays& P, const WarpSlot<T>& W,
+                                   bool apply, T step, int lvl, int lane, double& r2) {
+  const int K = t.K, NS = W.N;
+  const int h0 = (1 << (lvl - 1)) - 1, nh = 1 << (lvl - 1);
+  for (int x = lane; x < nh; x += 32) {
+    const int node = h0 + x;
+    double e[6];
+    T de[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) {
+      e[I] = lvl == 1 ? Eloc[I] : W.ein[I * NS + node];
+      de[I] = lvl == 1 ? (T)0 : W.dein[I * NS + node];
+    }
+    double nd[3];
+    T nt[3];
+    load_n<T>(P, node, nd, nt);
+    const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+    double a[3] = {W.a_in[3 * node], W.a_in[3 * node + 1], W.a_in[3 * node + 2]};
+    T da[3] = {(T)0, (T)0, (T)0};
+    {
+      const T* gp = W.gh_in + node;
+      const T ic = ic12_of<T>(t, node);   // the stored step is c1 c2 (g, H)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T v = step * gp[c * NS];
+#pragma unroll
+        for (int I = 0; I < 6; ++I) v += gp[(3 + 6 * c + I) * NS] * de[I];
+        da[c] = apply ? v * ic : (T)0;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { a[c] += widen(da[c]); W.a_out[3 * node + c] = a[c]; }
+    }
+    const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+    double Na[6], eL[6], eR[6];
+    N_apply<double>(nd, ndr, a, Na);
+#pragma unroll
+    for (int I = 0; I < 6; ++I) { eL[I] = e[I] - c2 * Na[I]; eR[I] = e[I] + c1 * Na[I]; }
+    if (lvl < K) {
+      const NodeC<T> cc = node_c<T>(t, node);
+      const T ntr[3] = {nt[0] * (T)RS2, nt[1] * (T)RS2, nt[2] * (T)RS2};
+      T Nda[6], dR[6];
+      N_apply<T>(nt, ntr, da, Nda);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { dR[I] = de[I] + cc.c1 * Nda[I]; de[I] = de[I] - cc.c2 * Nda[I]; }
+      const int k1 = 2 * node + 1, k2 = 2 * node + 2;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) {
+        W.ein[I * NS + k1] = eL[I]; W.dein[I * NS + k1] = de[I];
+        W.ein[I * NS + k2] = eR[I]; W.dein[I * NS + k2] = dR[I];
+      }
+    } else {   // the bottom laminate's two leaves and its structured condensation
+      double z[6], sL[6], sR[6];
+      LeafTan<T> DL, DR;
+      load_z<double>(t, P, 2 * x, 0, z);
+      leaf_iso<T, double>(t.ph[0], eL, z, sL, &DL, nullptr, nullptr);
+      load_z<double>(t, P, 2 * x + 1, 1, z);
+      leaf_iso<T, double>(t.ph[1], eR, z, sR, &DR, nullptr, nullptr);
+      Sub<T> res;
+      condense_bottom<T, true, double>(nd, nt, c1, c2, __ldg(t.sc + node), node_c<T>(t, node), sL, DL, sR, DR, res,
+                                       W.gh_out + node, (size_t)NS, r2, t.ph[0].kind == 0, t.ph[1].kind == 0);
+      warp_sub_store<T>(W, node, res);
+    }
+  }
+}
+
+// One level of the condensation above the bottom one (lvl = K - 1 .. 1), from the children's results.
+template <typename T>
+__device__ void warp_condense_level(const TreeDev& t, const PointArrays& P, const WarpSlot<T>& W, int lvl, int lane,
+                                    double& r2) {
+  const int h0 = (1 << (lvl - 1)) - 1, nh = 1 << (lvl - 1);
+  for (int x = lane; x < nh; x += 32) {
+    const int node = h0 + x;
+    double nd[3];
+    T nt[3];
+    load_n<T>(P, node, nd, nt);
+    Sub<T> L, R, res;
+    warp_sub_load<T>(W, 2 * node + 1, L);
+    warp_sub_load<T>(W, 2 * node + 2, R);
+    condense<T, true, double>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node), node_c<T>(t, node),
+                              L, R, res, W.gh_out + node, (size_t)W.N, r2);
+    warp_sub_store<T>(W, node, res);
+  }
+}
+
+// The whole pass for a warp: levels in order, a warp barrier between them.  Returns this lane's
+// share of the squared residual norm; the root's result is at node 0 of W.
+template <typename T>
+__device__ double warp_tree_pass(const TreeDev& t, const double Eloc[6], const PointArrays& P, const WarpSlot<T>& W,
+                                 bool apply, T step, int lane) {
+  double r2 = 0.0;
+  for (int lvl = 1; lvl <= t.K; ++lvl) {
+    warp_descend_level<T>(t, Eloc, P, W, apply, step, lvl, lane, r2);
+    __syncwarp();
+  }
+  for (int lvl = t.K - 1; lvl >= 1; --lvl) {
+    warp_condense_level<T>(t, P, W, lvl, lane, r2);
+    __syncwarp();
+  }
+  return r2;
+}
+
+// ---------------------------------------------------------------------------
 // Mandel rotation R_IJ = (w_I w_J / 2)(Q_ia Q_jb + Q_ib Q_ja) for index pairs
 // I = (i, j), J = (a, b), w = 1 (normal) or sqrt 2 (shear): sigma_glob =
 // R sigma_loc, E_loc = R^T E_glob, C_glob = R C_loc R^T.

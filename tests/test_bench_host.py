@@ -98,3 +98,19 @@ def test_roofline_arithmetic():
     assert st["peak"] == 152 * 128 * 2 * 2.07 and abs(st["achieved"] - fs / 0.08 / 1e9) <= 1e-6 * st["achieved"]
     assert bench.form_stage("mixed") and not bench.form_stage("mixed/no-stage")
     assert not bench.form_stage("f64") and not bench.form_stage("mixed/extrap")
+
+
+def test_roofline_names_the_warp_kernel(monkeypatch):
+    """A call that ran one warp per point is reported as k_newton_warp, with the same algorithmic flops,
+    and looks up its own DRAM figure, never the thread kernel's."""
+    keys = []
+    monkeypatch.setattr(bench, "ncu_traffic", lambda k, n: keys.append(k))
+    n, steps = 4096, 10
+    r = {"iters_sum": 3.5 * n * steps, "kms": {"newton": 9.0 * steps, "final": 0.2 * steps}}
+    thread = bench.roofline_f64(r, n, steps)
+    warp = bench.roofline_f64(dict(r, warp=True), n, steps)
+    assert thread["kernel"] == "k_newton<double>" and warp["kernel"] == "k_newton_warp<double>"
+    assert warp["flops_per_launch"] == thread["flops_per_launch"]
+    mw = bench.roofline_mixed(dict(r, warp=True), n, steps)
+    assert mw["kernel"] == "k_newton_warp<float>"
+    assert keys == ["k_newton_f64", "k_newton_warp_f64", "k_newton_warp_mixed"]

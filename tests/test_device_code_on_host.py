@@ -52,6 +52,7 @@ inline float __uint_as_float(unsigned u) { float f; std::memcpy(&f, &u, 4); retu
 inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f, 4); return u; }
 inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
 inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+inline void __syncwarp(unsigned = 0xffffffffu) {}   // the harness runs a warp's lanes one after another
 #include "dmn_device.cuh"
 using namespace dmn;
 
@@ -356,6 +357,109 @@ static int run(FILE* in, FILE* out, int K, int M, long n, int max_iter, double t
   return 0;
 }
 
+// the small-batch kernel's Newton loop, one warp per point (heap trees): every pass runs the levels in
+// order, the 32 lanes of a level one after another; the lanes' residual shares are added as the
+// warp's butterfly does (v[l] + v[l ^ o] for o = 16, 8, 4, 2, 1)
+template <typename T>
+static int run_warp(FILE* in, FILE* out, int K, int M, long n, int max_iter, double tol, bool sweep, bool ls) {
+  const Tree tr(in, K, M);
+  const TreeDev& t = tr.t;
+  const int N = tr.N;
+  const long S = tr.S;
+  std::vector<double> lam(2 * n), Q(9 * n), En(6 * n), dE(6 * n), st(S * n), so(S * n);
+  rd(lam.data(), 2 * n, in); rd(Q.data(), 9 * n, in); rd(En.data(), 6 * n, in);
+  rd(dE.data(), 6 * n, in); rd(st.data(), S * n, in);
+  std::vector<double> stress(6 * n), tangent(36 * n), iters(n), status(n);
+  std::vector<double> nrm(3 * N), abuf[2] = {std::vector<double>(3 * N), std::vector<double>(3 * N)};
+  std::vector<float> nrmf(3 * N);
+  std::vector<T> gbuf[2] = {std::vector<T>(21 * N), std::vector<T>(21 * N)}, dein(6 * N), dc(27 * N);
+  std::vector<double> ein(6 * N), sb(6 * N);
+  auto paper = [&](int node) {
+    const int lvl = 32 - __builtin_clz(node + 1);
+    return (1 << K) - 3 * (1 << (lvl - 1)) + node + 1;
+  };
+  for (long pt = 0; pt < n; ++pt) {
+    double f[6], R[6][6], Eloc[6];
+    tr.point(lam[2 * pt], lam[2 * pt + 1], &Q[9 * pt], &En[6 * pt], &dE[6 * pt], f, nrm.data(), nrmf.data(), R, Eloc);
+    for (int node = 0; node < N; ++node)
+      for (int c = 0; c < 3; ++c) abuf[0][3 * node + c] = st[(6L * t.nz + 3 * paper(node) + c) * n + pt];
+    PointArrays A{};
+    A.nrm = nrm.data(); A.ns = 1; A.nrmf = nrmf.data();
+    A.as = 1; A.paper = false;
+    A.z = st.data() + pt; A.zs = (size_t)n;
+    int it = 0, cur = 0, halvings = 0, stt = -1;
+    bool first = true;
+    T step = (T)1;
+    double rn_acc = 0.0;
+    Sub<T> root, root_acc;
+    for (;;) {
+      WarpSlot<T> W{abuf[cur].data(), abuf[ls ? 1 - cur : cur].data(), gbuf[cur].data(), gbuf[ls ? 1 - cur : cur].data(),
+                    ein.data(), dein.data(), sb.data(), dc.data(), N};
+      double v[32] = {0.0};
+      for (int lvl = 1; lvl <= K; ++lvl)
+        for (int lane = 0; lane < 32; ++lane) warp_descend_level<T>(t, Eloc, A, W, !first, step, lvl, lane, v[lane]);
+      for (int lvl = K - 1; lvl >= 1; --lvl)
+        for (int lane = 0; lane < 32; ++lane) warp_condense_level<T>(t, A, W, lvl, lane, v[lane]);
+      for (int o = 16; o > 0; o >>= 1) {
+        double w2[32];
+        for (int l = 0; l < 32; ++l) w2[l] = v[l] + v[l ^ o];
+        for (int l = 0; l < 32; ++l) v[l] = w2[l];
+      }
+      const double r2 = v[0];
+      warp_sub_load<T>(W, 0, root);
+      double sn2 = 0.0;
+      for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
+      const double rn = std::sqrt(r2), sn = std::sqrt(sn2);
+      if (ls && !(first || rn < rn_acc)) {
+        if (++halvings > 8) { stt = 3; ++it; root = root_acc; break; }
+        step *= (T)0.5;
+        continue;
+      }
+      if (ls) { cur = 1 - cur; rn_acc = rn; root_acc = root; step = (T)1; halvings = 0; }
+      first = false;
+      if (!std::isfinite(rn) || !std::isfinite(sn)) stt = 2;
+      else if (rn <= tol * (double)N * sn) stt = 0;
+      else if (it >= max_iter) stt = 1;
+      if (stt < 0) { ++it; continue; }
+      break;
+    }
+    iters[pt] = it; status[pt] = stt;
+    // the jumps back in the paper's ordering; stress, tangent and state as in run()
+    std::vector<double> a(3 * N);
+    for (int node = 0; node < N; ++node)
+      for (int c = 0; c < 3; ++c) a[3 * paper(node) + c] = abuf[cur][3 * node + c];
+    PointArrays B{};
+    B.nrm = nrm.data(); B.ns = 1; B.nrmf = nrmf.data();
+    B.a = a.data(); B.a_out = a.data(); B.as = 1; B.paper = true;
+    B.z = st.data() + pt; B.zs = (size_t)n;
+    double Cl[6][6], sl[6];
+    if (sweep) {
+      Sub<double> fin;
+      double r2;
+      GH<double> none{nullptr, 0, nullptr};
+      tree_pass<double, false>(t, Eloc, B, none, false, 1.0, fin, r2, nullptr);
+      for (int I = 0; I < 6; ++I) { sl[I] = fin.sb[I]; for (int J = 0; J < 6; ++J) Cl[I][J] = fin.C[sidx(I, J)]; }
+    } else {
+      for (int I = 0; I < 6; ++I) { sl[I] = root.sb[I]; for (int J = 0; J < 6; ++J) Cl[I][J] = widen(root.C[sidx(I, J)]); }
+    }
+    for (int I = 0; I < 6; ++I) {
+      double acc = 0.0;
+      for (int J = 0; J < 6; ++J) acc += R[I][J] * sl[J];
+      stress[6 * pt + I] = acc;
+      for (int J = 0; J < 6; ++J) {
+        double cc = 0.0;
+        for (int P2 = 0; P2 < 6; ++P2) for (int Q2 = 0; Q2 < 6; ++Q2) cc += R[I][P2] * Cl[P2][Q2] * R[J][Q2];
+        tangent[36 * pt + 6 * I + J] = cc;
+      }
+    }
+    for (int k = 0; k < 3 * N; ++k) so[(6L * t.nz + k) * n + pt] = a[k];
+    write_leaf_states(t, Eloc, B, so.data() + pt, (size_t)n, stt == 2);
+  }
+  fwrite(so.data(), 8, S * n, out); fwrite(stress.data(), 8, 6 * n, out); fwrite(tangent.data(), 8, 36 * n, out);
+  fwrite(iters.data(), 8, n, out); fwrite(status.data(), 8, n, out);
+  return 0;
+}
+
 // the adjoint of a converged update (the per-point work of the gradient kernel, then the sum over points):
 // inputs lam, Q, E_n, dE, the state before and after the update and the loss gradient g (global frame);
 // outputs dL/dp, dL/dq (paper ordering), dL/dw and dL/dE
@@ -486,10 +590,14 @@ int main(int argc, char** argv) {
   const long n = (long)hdr[2];
   // mode: 0 FP64, 1 mixed with the FP32 tangent, 2 mixed with the FP64 final sweep, 3 adjoint (FP64),
   //       4 FP64 with the line search, 5 adjoint of the tangent (elastic phases),
-  //       6 / 7 / 8 modes 1 / 2 / 0 after the all-FP32 first stage
+  //       6 / 7 / 8 modes 1 / 2 / 0 after the all-FP32 first stage,
+  //       9 / 10 / 11 modes 0 / 2 / 4 with one warp per point (heap trees)
   const float tol32 = hdr[6] > 0.0 ? (float)hdr[6] : STAGE_TOL;
   const int max32 = hdr[7] > 0.0 ? (int)hdr[7] : std::max(0, std::min(STAGE_MAX_ITER, max_iter - 1));
-  const int rc = mode == 0 || mode == 4 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false, mode == 4)
+  const int rc = mode == 9 ? run_warp<double>(in, out, K, M, n, max_iter, hdr[5], false, false)
+               : mode == 10 ? run_warp<float>(in, out, K, M, n, max_iter, hdr[5], true, false)
+               : mode == 11 ? run_warp<double>(in, out, K, M, n, max_iter, hdr[5], false, true)
+               : mode == 0 || mode == 4 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false, mode == 4)
                : mode == 8 ? run<double>(in, out, K, M, n, max_iter, hdr[5], false, false, true, tol32, max32)
                : mode == 3 ? run_grad(in, out, K, M, n)
                : mode == 5 ? run_grad_tangent(in, out, K, M, n)
@@ -554,7 +662,10 @@ PHASE_SETS = {"linear": (W.FIBER, W.MATRIX), "explin": (W.FIBER, W.MATRIX_EXPLIN
                                              (6, 3, "linear", 6), (6, 3, "explin", 7), (5, 3, "both-inelastic", 7),
                                              (5, 6, "inelastic-left", 6),
                                              # the FP64 form after the first stage
-                                             (6, 3, "linear", 8), (6, 3, "explin", 8), (5, 3, "both-inelastic", 8)])
+                                             (6, 3, "linear", 8), (6, 3, "explin", 8), (5, 3, "both-inelastic", 8),
+                                             # one warp per point: FP64, mixed with the FP64 sweep
+                                             (6, 3, "linear", 9), (5, 6, "explin", 9), (5, 3, "both-inelastic", 10),
+                                             (6, 3, "linear", 10)])
 def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
     phases = PHASE_SETS[matrix]
     tree = (W.tree_d10_fit(K, seed=30 + K, phases=phases) if M == 3
@@ -568,7 +679,7 @@ def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
     # criterion, ||A^T W sigma|| <= 1e-12 (2^K - 1) ||sigma_bar||, at different iterates: they agree to
     # that criterion's reach (the oracle itself moves by up to ~1e-9 when converged further), not to rounding
     tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6), 6: (1e-6, 1e-4), 7: (1e-6, 1e-6),
-                    8: (3e-9, 3e-9)}[prec]
+                    8: (3e-9, 3e-9), 9: (1e-10, 1e-10), 10: (1e-6, 1e-6)}[prec]
     alive = np.ones(n, dtype=bool)
     for s in range(1, 9):
         En, dE = W.proportional_increment(Ef, s, 20)
@@ -580,8 +691,8 @@ def test_device_arithmetic_matches_the_oracle(harness, K, M, matrix, prec):
         ok = alive & (gap > 1e-9)
         assert rel(C_h[ok], C_o[ok]).max() <= tol_c, s
         scale = np.abs(so[:, alive]).max(axis=1, keepdims=True) + 1e-300
-        assert (np.abs(sh[:, alive] - so[:, alive]) / scale).max() <= (1e-9 if prec == 0 else 1e-5), s
-        if prec == 0:
+        assert (np.abs(sh[:, alive] - so[:, alive]) / scale).max() <= (1e-9 if prec in (0, 9) else 1e-5), s
+        if prec in (0, 9):
             assert np.abs(it_h[alive] - it_o[alive]).max() <= 1
 
 
@@ -635,9 +746,11 @@ def test_device_adjoint_matches_the_oracle_gradient(harness, K, matrix, steps):
     np.testing.assert_allclose(gE, np.einsum("nij,nj->ni", C, g), rtol=1e-9, atol=1e-9 * np.abs(gE).max())
 
 
-def test_device_line_search_matches_the_oracle(harness):
+@pytest.mark.parametrize("mode", [4, 11])
+def test_device_line_search_matches_the_oracle(harness, mode):
     """The line search's two buffers (accepted and trial jumps, g and H) on large cyclic steps against
-    the oracle's line search; plain Newton takes other iterates there (the search halves steps)."""
+    the oracle's line search, one thread per point (4) and one warp per point (11); plain Newton takes
+    other iterates there (the search halves steps)."""
     K, n, n_steps = 6, 100, 8
     tree = W.tree_d10_fit(K, seed=80)
     A2, lam, Q = W.orientation_field(n, seed=81)
@@ -649,7 +762,7 @@ def test_device_line_search_matches_the_oracle(harness):
     for s in range(1, n_steps + 1):
         En, dE = W.cyclic_increment(amp, s, n_steps)
         _, _, _, it_plain, stat_plain, _ = oracle.update(tree, lam, Q, En, dE, so)
-        sh, sig_h, C_h, it_h, stat_h = run_harness(harness, tree, lam, Q, En, dE, sh, 4)
+        sh, sig_h, C_h, it_h, stat_h = run_harness(harness, tree, lam, Q, En, dE, sh, mode)
         so, sig_o, C_o, it_o, stat_o, gap = oracle.update(tree, lam, Q, En, dE, so, line_search=True)
         differs += int(((it_plain != it_o) | (stat_plain != stat_o)).sum())
         alive &= (stat_o == 0) & (stat_h == 0)
@@ -676,7 +789,7 @@ def test_device_compressed_traversal_matches_the_oracle(harness, K, prec):
     # criterion, ||A^T W sigma|| <= 1e-12 (2^K - 1) ||sigma_bar||, at different iterates: they agree to
     # that criterion's reach (the oracle itself moves by up to ~1e-9 when converged further), not to rounding
     tol_s, tol_c = {0: (1e-10, 1e-10), 1: (1e-6, 1e-4), 2: (1e-6, 1e-6), 6: (1e-6, 1e-4), 7: (1e-6, 1e-6),
-                    8: (3e-9, 3e-9)}[prec]
+                    8: (3e-9, 3e-9), 9: (1e-10, 1e-10), 10: (1e-6, 1e-6)}[prec]
     alive = np.ones(n, dtype=bool)
     for s in range(1, 9):
         En, dE = W.proportional_increment(Ef, s, 20)
@@ -688,8 +801,8 @@ def test_device_compressed_traversal_matches_the_oracle(harness, K, prec):
         ok = alive & (gap > 1e-9)
         assert rel(C_h[ok], C_o[ok]).max() <= tol_c, s
         scale = np.abs(so[:, alive]).max(axis=1, keepdims=True) + 1e-300
-        assert (np.abs(sh[:, alive] - so[:, alive]) / scale).max() <= (1e-9 if prec == 0 else 1e-5), s
-        if prec == 0:
+        assert (np.abs(sh[:, alive] - so[:, alive]) / scale).max() <= (1e-9 if prec in (0, 9) else 1e-5), s
+        if prec in (0, 9):
             assert np.abs(it_h[alive] - it_o[alive]).max() <= 1
 
 

@@ -27,9 +27,11 @@ def test_autotune_picks_a_candidate_and_caches_it(tmp_path, monkeypatch):
     assert autotune.cached(tree, "mixed", DEV) == (res["block"], res["ctas_per_sm"])
     data = json.load(open(autotune.CACHE))
     assert len(data) == 1
-    # a tuned handle computes the same result as a default one, bit for bit
-    a = dmn.DMN(tree, precision="f64").update(d(lam), d(Q), d(En), d(dE), st)
-    b = dmn.DMN(tree, precision="f64", block=64, ctas_per_sm=6).update(d(lam), d(Q), d(En), d(dE), st)
+    # a tuned handle computes the same result as a default one, bit for bit (the launch shape is the
+    # thread-per-point kernel's; at this size the default would take the warp kernel)
+    a = dmn.DMN(tree, precision="f64", warp_per_point=-1).update(d(lam), d(Q), d(En), d(dE), st)
+    b = dmn.DMN(tree, precision="f64", block=64, ctas_per_sm=6, warp_per_point=-1).update(d(lam), d(Q), d(En),
+                                                                                         d(dE), st)
     for k in a:
         assert torch.equal(a[k], b[k]), k
 

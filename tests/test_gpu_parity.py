@@ -111,8 +111,8 @@ def test_depth8_interpolated_random_paths(prec):
 
 
 def test_ragged_sizes_depths_and_launch_shapes():
-    """n not a multiple of a warp or a CTA; depths 1..8; several CTA shapes give
-    bit-identical FP64 results."""
+    """n not a multiple of a warp or a CTA; depths 1..8; several CTA shapes of the thread-per-point
+    kernel give bit-identical FP64 results."""
     for K, n in ((1, 1), (2, 33), (3, 129), (5, 257), (8, 37)):
         tree = W.tree_d10_fit(K, seed=10 + K)
         A2, lam, Q = W.orientation_field(n, seed=20 + K)
@@ -125,7 +125,8 @@ def test_ragged_sizes_depths_and_launch_shapes():
     Ef = W.random6_path_final(n, 0.03, seed=42)
     outs = []
     for block, cps in ((128, 2), (64, 1), (32, 3), (128, 2)):
-        _, out, _ = run_path(tree, lam, Q, Ef, 3, "f64", compare=False, block=block, ctas_per_sm=cps)
+        _, out, _ = run_path(tree, lam, Q, Ef, 3, "f64", compare=False, block=block, ctas_per_sm=cps,
+                             warp_per_point=-1)
         outs.append({k: v.cpu().numpy() for k, v in out.items()})
     for o in outs[1:]:
         for k in o:
@@ -313,12 +314,13 @@ def test_interp_orientation_at_the_triangle_corners():
 def test_points_are_independent_of_the_batch(prec):
     """Every point's update depends on that point alone: 65,537 points at depth 6 (more than one
     point per lane of the persistent kernel) give bit for bit the results of the same points
-    updated as two uneven parts in the reverse order."""
+    updated as two uneven parts in the reverse order, in the thread-per-point organisation (the
+    warp organisation, which small calls get by default, rounds differently)."""
     K, n, cut = 6, 65537, 40001
     tree = W.tree_d10_fit(K, seed=97)
     A2, lam, Q = W.orientation_field(n, seed=98)
     Ef = W.random6_path_final(n, 0.03, seed=99)
-    m = dmn.DMN(tree, precision=prec)
+    m = dmn.DMN(tree, precision=prec, warp_per_point=-1)
     lam_d, Q_d = d(lam), d(Q)
     st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
     for s in range(1, 4):

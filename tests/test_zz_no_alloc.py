@@ -56,7 +56,7 @@ def test_noalloc_update_matches_dmn_update_on_two_calls_in_a_row():
     Ef = W.random6_path_final(n, 0.03, seed=125)
     S = W.state_size(K)
     d, keep = _desc(tree)
-    m = dmn.DMN(tree, precision="f64")
+    m = dmn.DMN(tree, precision="f64", warp_per_point=-1)   # the organisation of the allocation-free call
     lam_d = torch.from_numpy(lam).to(DEV)
     Q_d = torch.from_numpy(Q).to(DEV)
     st_ref = torch.zeros((S, n), dtype=torch.float64, device=DEV)
@@ -119,7 +119,7 @@ def test_python_binding_matches_dmn_update():
     tree = W.tree_d10_fit(K, seed=126)
     A2, lam, Q = W.orientation_field(n, seed=127)
     Ef = W.random6_path_final(n, 0.03, seed=128)
-    m = dmn.DMN(tree, precision="f64")
+    m = dmn.DMN(tree, precision="f64", warp_per_point=-1)   # the organisation of the allocation-free call
     lam_d, Q_d = torch.from_numpy(lam).to(DEV), torch.from_numpy(Q).to(DEV)
     st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
     for step in range(1, 6):
