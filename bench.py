@@ -195,13 +195,14 @@ def src_hash():
 
 
 def ncu_traffic(kernel, npts_launch):
-    """DRAM bytes per launch from a committed ncu summary of the same sources (scaled by points)."""
+    """DRAM bytes per launch from a committed ncu summary of the same sources: the capture of this
+    batch size ("kernel@points") if there is one, else the kernel's (scaled by points)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
-    e = d.get(kernel)
+    e = d.get("%s@%d" % (kernel, npts_launch)) or d.get(kernel)
     if not e or e.get("src_hash") != src_hash():
         return None
     return e["dram_bytes_per_point"] * npts_launch
@@ -327,10 +328,11 @@ def rel_rows(a, b):
 
 def form_opts(form):
     """(precision, extrapolated start) of a form name such as "f64", "mixed-f32-tangent/extrap",
-    "mixed/no-stage" (the mixed iteration without its all-FP32 first stage) or "f64/stage" (the FP64
-    iteration after that stage)."""
+    "mixed/no-stage" (the mixed iteration without its all-FP32 first stage), "f64/stage" (the FP64
+    iteration after that stage), "f64/thread" (one point per thread whatever the batch size) or
+    "f64/w8" (the warp organisation with 8, 16 or 32 lanes per point whatever the batch size)."""
     prec, _, start = form.partition("/")
-    if start not in ("", "extrap", "no-stage", "stage"):
+    if start not in ("", "extrap", "no-stage", "stage", "thread", "w8", "w16", "w32"):
         raise ValueError("unknown start in form %r" % form)
     return prec, start == "extrap"
 
@@ -348,6 +350,31 @@ def form_stage_option(form):
     "/no-stage"), else the library default (on in the mixed forms; a small call, which runs one warp
     per point, goes without it)."""
     return True if form.endswith("/stage") else False if form.endswith("/no-stage") else None
+
+
+L2_BYTES = 126 << 20
+
+
+def state_fields(tree):
+    """Doubles of state per point (leaf states of the inelastic leaves, jumps) of a tree's handle."""
+    c = tree_counts(tree.w)
+    return 6 * c["j2"] + 3 * c["N"]
+
+
+def l2_flush_needed(S, n):
+    """Whether one step's state (read and written) and strains fit twice into the L2."""
+    return 8 * n * (2 * S + 12 + 11) < 2 * L2_BYTES
+
+
+def form_warp_option(form):
+    """The handle's (warp_per_point, warp_lanes) arguments: (-1, 0) for "/thread", (1, lanes) for "/w8",
+    "/w16", "/w32", else the library default (the warp organisation for small calls, its lanes by size)."""
+    start = form.partition("/")[2]
+    if start == "thread":
+        return -1, 0
+    if start in ("w8", "w16", "w32"):
+        return 1, int(start[1:])
+    return 0, 0
 
 
 def tune_shape(form, ctx, args):
@@ -391,7 +418,8 @@ def run_form(form, ctx, args, dist):
     prec, pred = form_opts(form)
     m = dmn.DMN(ctx["tree"], precision=prec, block=shape["block"] if shape else 0,
                 ctas_per_sm=shape["ctas_per_sm"] if shape else 0, predictor=pred,
-                first_stage=form_stage_option(form),
+                first_stage=form_stage_option(form), warp_per_point=form_warp_option(form)[0],
+                warp_lanes=form_warp_option(form)[1],
                 stage_ctas_per_sm=shape["stage_ctas_per_sm"] if shape else 0)
     assert m.first_stage == form_stage(form)
     S = m.state_size
@@ -401,8 +429,13 @@ def run_form(form, ctx, args, dist):
     out = m.alloc_outputs(n, dev)
     iters_steps = torch.zeros((args.steps, n), dtype=torch.int32, device=dev)
     cur = 0
+    # a step's inputs and state smaller than twice the L2: overwrite the L2 (a 256 MB fill) before
+    # every step, inside the timed region (about 0.05 ms a step)
+    flush = torch.empty(1 << 25, dtype=torch.float64, device=dev) if l2_flush_needed(S, n) else None
 
     def step(s, cur, iters_buf=None):
+        if flush is not None:
+            flush.fill_(float(s))
         m.interp_orientation(ctx["A2"], lam, Q)
         out["state_out"] = st[1 - cur]
         if iters_buf is not None:
@@ -435,14 +468,15 @@ def run_form(form, ctx, args, dist):
     clk = clocks.stop() if clocks else None
     kms, passes, cnt = m.profile_read_stages()
     m.profile(False)
-    warp = m.warp_per_point_for(n)   # a small call runs one warp per point, without the first stage
+    lanes = m.lanes_per_point(n)   # a small call runs the warp organisation, without the first stage
+    warp = lanes > 1
     if not form_stage(form) or warp:
         kms.pop("stage")
     its = iters_steps.to(torch.int64).sum().item()
     hist = torch.bincount(iters_steps.reshape(-1).to(torch.int64), minlength=1).cpu().numpy()
     res = dict(t_ms=t_ms, kms=kms, updates=cnt, clocks=clk, iters_sum=int(its), iters_hist=hist.tolist(),
                passes=passes, warp=warp,
-               launch=("one warp per point (k_newton_warp, 2 CTAs of 4 warps per SM)" if warp else
+               launch=("%d lanes per point (k_newton_warp, 2 CTAs of 4 warps per SM)" % lanes if warp else
                        dict(block=shape["block"], ctas_per_sm=shape["ctas_per_sm"], tuned_on_points=shape["points"],
                             table=shape["table"], stage_ctas_per_sm=shape["stage_ctas_per_sm"],
                             stage_table=shape["stage_table"]) if shape else "defaults"),
@@ -954,11 +988,13 @@ def run_gpu(args):
                        "increments": N_INCREMENTS, "matrix": MATRIX_NOTE[args.matrix],
                        "shape_functions": SHAPE_NOTE[args.shape],
                        "timed_increments": [args.warmup + 1, args.warmup + steps],
-                       "l2": "no flush: per-step inputs (state %.1f GB) exceed L2"
-                             % ((6 * tree_counts(tree.w)["j2"] + 3 * tree_counts(tree.w)["N"]) * n * 8e-9),
+                       "l2": ("flushed before every step (256 MB fill, in the timed region): per-step state "
+                              "%.1f MB" if l2_flush_needed(state_fields(tree), n) else
+                              "no flush: per-step inputs (state %.1f MB) exceed L2")
+                             % (state_fields(tree) * n * 8e-6),
                        "parallelism": "independent point shards per GPU, no collective"},
             "roofline": forms_out[main_form]["roofline"], "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 4 * steps, "clocks": mr["clocks"],
+            "gpu_launches": (4 + ("stage" in mr["kms"])) * steps, "clocks": mr["clocks"],
             "peaks": {"fp64_gflops": peaks["f64"], "fp32_gflops": peaks["f32"], "note": peaks["note"]}}
     # the other forms side by side with the headline: value, roofline and error against the oracle
     for form in ("mixed", "mixed-f32-tangent", "f64/stage"):

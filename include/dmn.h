@@ -156,15 +156,20 @@ typedef struct {
                         * Not run with line_search or predictor. */
   int32_t stage_ctas_per_sm; /* resident CTAs of 128 threads per SM of the first stage's persistent kernel:
                               * 2, 3, 4, 6 or 8 (registers capped to fit); 0 selects the default */
-  int32_t warp_per_point; /* small batches: 0 (default) updates a batch of at most 256 points per SM of
-                           * the device (38912 on 152 SMs) with one warp per point, its lanes sharing
-                           * each level of the tree (the same arithmetic per laminate and the same
-                           * iterates to rounding), where one point per thread would leave SMs idle;
-                           * 1 does so for every batch; -1 never.  The choice is made per call (for
+  int32_t warp_per_point; /* small batches: 0 (default) updates a call of at most 1024 points per SM
+                           * of the device in the FP64 form, 256 in the mixed forms (155648 / 38912 on
+                           * 152 SMs) in the warp organisation: a point per group of 32, 16 or 8 lanes
+                           * of a warp, the group's lanes sharing each level of the tree (the same
+                           * arithmetic per laminate and the same iterates to rounding), where one point
+                           * per thread would leave SMs idle; 1 does so for every call; -1 never.  The choice is made per call (for
                            * dmn_update_host on the whole batch, not per chunk); first_stage = 1 turns
                            * the default off.  Trees with weightless leaves (compressed) and the
                            * extrapolated start always run one point per thread; the first stage is not run
                            * in this organisation. */
+  int32_t warp_lanes;     /* lanes per point in that organisation: 32 (one point per warp), 16 or 8 (two
+                           * or four points per warp, side by side); 0 (default) chooses by the call's
+                           * size: 32 up to 16 points per SM, then 8 in the FP64 form, 16 in the mixed
+                           * forms */
 } dmn_options;
 
 /* Create a handle for n_trees DMNs (1 <= n_trees <= DMN_MAX_TREES; trees may
@@ -191,10 +196,11 @@ void dmn_destroy(dmn_handle* h);
  * dmn_state_size(h, t) of them).  -1 on a bad argument. */
 int64_t dmn_state_size(const dmn_handle* h, int32_t tree_id);
 
-/* The organisation dmn_update (and dmn_update_host) gives a call of n points on this handle:
- * 1 one warp per point (see dmn_options.warp_per_point), 0 one point per thread of the
- * persistent kernel; -1 on a NULL handle or n < 0.  A query only: no device work. */
-int dmn_update_warp_per_point(const dmn_handle* h, int64_t n);
+/* The organisation dmn_update (and dmn_update_host) gives a call of n points on this handle, as
+ * lanes per point: 1 one point per thread of the persistent kernel, 32 / 16 / 8 the warp
+ * organisation with one / two / four points per warp (dmn_options.warp_per_point, warp_lanes);
+ * -1 on a NULL handle or n < 0.  A query only: no device work. */
+int dmn_update_lanes_per_point(const dmn_handle* h, int64_t n);
 
 /* Orientation set-up (Sec. 2.2, Eq. of the eigen decomposition of A2):
  * A2 dev [n][6] (plain components, symmetric positive semi-definite, unit

@@ -658,25 +658,31 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
   if (P.passes && npass) atomicAdd(P.passes, npass);
 }
 
-// Small batches: one warp per point (heap trees, the paper's start), the lanes sharing each level
-// of the tree (warp_tree_pass).  The Newton loop is k_newton's, warp-uniform; each warp owns a
-// block of scratch (WARP_SLOT_DOUBLES<T>(N) doubles) holding its point's jumps, g, H, level hand-over
-// and subtree results in two buffers where the line search needs them.  Points are taken one per
-// warp from the work counter.
+// Small batches: one point per group of G lanes of a warp (G = 32, 16 or 8; heap trees, the
+// paper's start), the group's lanes sharing each level of the tree (warp_tree_pass).  The Newton
+// loop is k_newton's.  The warp's groups run their passes side by side: every iteration of the
+// warp's loop is one pass of every group that holds a point, so the groups' lanes stay together
+// (the pass's instructions are the same for every point); a group whose point is done writes it
+// out and takes the next one from the work counter.  Each group owns a block of scratch
+// (warp_slot_doubles<T>(N) doubles) holding its point's jumps, g, H, level hand-over and subtree
+// results, in two buffers where the line search needs them.
 template <typename T>
 __host__ __device__ inline size_t warp_slot_doubles(int N) {
   // jumps 2 x 3N, ein 6N, sb 6N, normals 3N (FP64); g, H 2 x 21N, dein 6N, ds + C 27N (T); FP32 normals 3N
   const size_t d = (size_t)21 * N, tt = (size_t)75 * N * sizeof(T), f = (size_t)3 * N * sizeof(float);
   return d + (tt + f + sizeof(double) - 1) / sizeof(double);
 }
-constexpr int WARP_CTAS_PER_SM = 2;   // 128-thread CTAs: 8 point warps per SM
+constexpr int WARP_CTAS_PER_SM = 2;   // 128-thread CTAs: 8 warps per SM
+constexpr int WARP_MIN_LANES = 8;     // the smallest group: the scratch holds 32 / 8 = 4 slots per warp
 
-template <typename T, bool LS>
+template <typename T, bool LS, int G>
 __global__ void __launch_bounds__(128) k_newton_warp(NewtonParams<T> P, double* scratch) {
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  static_assert(G == 8 || G == 16 || G == 32, "8, 16 or 32 lanes per point");
+  const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x % G;
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << ((threadIdx.x & 31) / G * G);
   const int NM = P.N_max;
-  double* base = scratch + (size_t)gw * warp_slot_doubles<T>(NM);
+  double* base = scratch + (size_t)grp * warp_slot_doubles<T>(NM);
   double* abuf[2] = {base, base + 3 * NM};
   double* ein = base + 6 * NM;
   double* sbv = base + 12 * NM;
@@ -692,29 +698,35 @@ __global__ void __launch_bounds__(128) k_newton_warp(NewtonParams<T> P, double* 
   A.zs = (size_t)P.n;
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
   unsigned long long npass = 0;
-  for (;;) {
-    unsigned long long i = 0;
-    if (lane == 0) i = atomicAdd(P.counter, 1ull);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= (unsigned long long)P.n) break;
-    int64_t pt;
-    int tr;
-    point_of(P.perm, P.tid, P.F.n, (int64_t)i, pt, tr);
-    if (tr >= P.F.n) {   // unknown tree: report and take the next point
-      if (lane == 0) {
+  // the group's point and its Newton state
+  int64_t pt = -1;
+  int tr = 0, it0 = 0, it = 0, cur = 0, halvings = 0;
+  bool first = true;
+  T step = (T)1;
+  double rn_acc = 0.0, Eloc[6];
+  Sub<T> root, root_acc;
+  // the next point of a known tree for this group (points of unknown trees are reported on the
+  // way); false once the counter is exhausted
+  auto take = [&]() -> bool {
+    for (;;) {
+      unsigned long long i = 0;
+      if (lane == 0) i = atomicAdd(P.counter, 1ull);
+      i = __shfl_sync(gmask, i, 0, G);
+      if (i >= (unsigned long long)P.n) return false;
+      point_of(P.perm, P.tid, P.F.n, (int64_t)i, pt, tr);
+      if (tr < P.F.n) break;
+      if (lane == 0) {   // unknown tree: report and take the next point
         P.iters[pt] = 0;
         P.status[pt] = DMN_STATUS_BAD_TREE;
         for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
         for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
       }
-      continue;
     }
     const TreeDev& t = P.F.t[tr];
     const int nzf = 6 * t.nz;
-    double Eloc[6];
 #pragma unroll
     for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * NM + I) * P.n + pt];
-    for (int f = lane; f < 3 * t.N; f += 32) {
+    for (int f = lane; f < 3 * t.N; f += G) {
       const int node = f / 3, c = f - 3 * node;
       const int lvl = 32 - __clz(node + 1);
       const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
@@ -723,61 +735,62 @@ __global__ void __launch_bounds__(128) k_newton_warp(NewtonParams<T> P, double* 
       nrm[f] = nv;
       if (sizeof(T) == 4) nrmf[f] = narrow_rn(nv);
     }
+    it0 = P.a_start ? P.iters[pt] : 0;
+    it = 0; cur = 0; halvings = 0; first = true; step = (T)1; rn_acc = 0.0;
+    __syncwarp(gmask);
+    return true;
+  };
+  bool have = take();
+  while (__any_sync(0xffffffffu, have)) {
+    if (!have) continue;
+    const TreeDev& t = P.F.t[tr];
     A.z = P.state_in + pt;
-    const int it0 = P.a_start ? P.iters[pt] : 0;
-    int it = 0, cur = 0, halvings = 0, st = -1;
-    bool first = true;
-    T step = (T)1;
-    double rn_acc = 0.0;
-    Sub<T> root, root_acc;
-    __syncwarp();
-    for (;;) {
-      WarpSlot<T> W{abuf[cur], abuf[LS ? 1 - cur : cur], gbuf[cur], gbuf[LS ? 1 - cur : cur], ein, dein, sbv, dcv, NM};
-      ++npass;
-      double r2 = warp_tree_pass<T>(t, Eloc, A, W, !first, step, lane);
+    WarpSlot<T> W{abuf[cur], abuf[LS ? 1 - cur : cur], gbuf[cur], gbuf[LS ? 1 - cur : cur], ein, dein, sbv, dcv, NM};
+    ++npass;
+    double r2 = warp_tree_pass<T>(t, Eloc, A, W, !first, step, lane, G, gmask);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-      warp_sub_load<T>(W, 0, root);
-      __syncwarp();
-      const double rn = sqrt(r2);
-      double sn2 = 0.0;
+    for (int o = G / 2; o > 0; o >>= 1) r2 += __shfl_xor_sync(gmask, r2, o, G);
+    warp_sub_load<T>(W, 0, root);
+    __syncwarp(gmask);
+    const double rn = sqrt(r2);
+    double sn2 = 0.0;
 #pragma unroll
-      for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
-      const double sn = sqrt(sn2);
-      if (!LS) {
+    for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
+    const double sn = sqrt(sn2);
+    int st = -1;
+    if (!LS) {
+      first = false;
+      if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
+      else if (rn <= P.tol * (double)t.N * sn && it >= P.min_corr) st = DMN_STATUS_OK;
+      else if (it >= P.max_iter - it0) st = DMN_STATUS_MAXITER;
+      if (st < 0) { ++it; continue; }
+    } else {
+      const bool accepted = first || rn < rn_acc;
+      if (accepted) {
         first = false;
+        cur = 1 - cur;
+        rn_acc = rn;
+        root_acc = root;
+        step = (T)1;
+        halvings = 0;
         if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
         else if (rn <= P.tol * (double)t.N * sn && it >= P.min_corr) st = DMN_STATUS_OK;
         else if (it >= P.max_iter - it0) st = DMN_STATUS_MAXITER;
         if (st < 0) { ++it; continue; }
+      } else if (++halvings > 8) {
+        st = DMN_STATUS_LINESEARCH;   // no halving lowered the residual: keep the accepted iterate
+        ++it;
+        root = root_acc;
       } else {
-        const bool accepted = first || rn < rn_acc;
-        if (accepted) {
-          first = false;
-          cur = 1 - cur;
-          rn_acc = rn;
-          root_acc = root;
-          step = (T)1;
-          halvings = 0;
-          if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
-          else if (rn <= P.tol * (double)t.N * sn && it >= P.min_corr) st = DMN_STATUS_OK;
-          else if (it >= P.max_iter - it0) st = DMN_STATUS_MAXITER;
-          if (st < 0) { ++it; continue; }
-        } else if (++halvings > 8) {
-          st = DMN_STATUS_LINESEARCH;   // no halving lowered the residual: keep the accepted iterate
-          ++it;
-          root = root_acc;
-        } else {
-          step *= (T)0.5;
-          continue;
-        }
+        step *= (T)0.5;
+        continue;
       }
-      break;
     }
     // finished point: jumps (paper ordering), counters, and without a final sweep the local-frame
     // stress and packed tangent for k_final to rotate
+    const int nzf = 6 * t.nz;
     const double* afin = abuf[cur];
-    for (int f = lane; f < 3 * t.N; f += 32) {
+    for (int f = lane; f < 3 * t.N; f += G) {
       const int node = f / 3, c = f - 3 * node;
       const int lvl = 32 - __clz(node + 1);
       const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
@@ -791,9 +804,24 @@ __global__ void __launch_bounds__(128) k_newton_warp(NewtonParams<T> P, double* 
         for (int k = 0; k < 21; ++k) P.tangent[36 * pt + k] = widen(root.C[k]);
       }
     }
-    __syncwarp();
+    __syncwarp(gmask);
+    have = take();
   }
   if (lane == 0 && P.passes && npass) atomicAdd(P.passes, npass);
+}
+
+template <typename T>
+void launch_warp(const NewtonParams<T>& P, bool ls, int lanes, unsigned grid, double* scr, cudaStream_t s) {
+  if (lanes == 8) {
+    if (ls) k_newton_warp<T, true, 8><<<grid, 128, 0, s>>>(P, scr);
+    else k_newton_warp<T, false, 8><<<grid, 128, 0, s>>>(P, scr);
+  } else if (lanes == 16) {
+    if (ls) k_newton_warp<T, true, 16><<<grid, 128, 0, s>>>(P, scr);
+    else k_newton_warp<T, false, 16><<<grid, 128, 0, s>>>(P, scr);
+  } else {
+    if (ls) k_newton_warp<T, true, 32><<<grid, 128, 0, s>>>(P, scr);
+    else k_newton_warp<T, false, 32><<<grid, 128, 0, s>>>(P, scr);
+  }
 }
 
 // The mixed forms' first stage (Sec. 3.2's Newton iteration with every quantity in FP32: jumps,
@@ -1361,15 +1389,26 @@ bool first_stage_on(const dmn_options& o) {
   return want && !o.line_search && !o.predictor;
 }
 
-// one warp per point: for heap trees with the paper's start, always on request, by default (unless
-// the first stage was asked for) for batches of at most WARP_AUTO_POINTS_PER_SM points per SM.  Below that the thread-per-point
-// kernel leaves SMs idle or nearly so; at depth 8 on 152 SMs the warp kernel is 12x faster at
-// 1024 points, 1.4x at 32768, even at about 45000 and slower above.
-constexpr int64_t WARP_AUTO_POINTS_PER_SM = 256;
+// the warp organisation: for heap trees with the paper's start, always on request, by default
+// (unless the first stage was asked for) for calls of at most warp_auto_points_per_sm points per SM.
+// Below that the thread-per-point kernel leaves SMs idle or nearly so.  At depth 8 on 152 SMs,
+// FP64: one point per warp is 20x faster than one point per thread at 1024 points; four points per
+// warp (8 lanes each) 9.9x at 4096, 1.85x at 32768, 1.36x at 65536, 1.12x at 131072.  FP32
+// condensation: one point per warp 6.2x at 1024, two per warp 4.7x at 4096, 1.48x at 32768, even
+// at about 45000.
+int warp_auto_points_per_sm(const dmn_handle* h) { return h->opt.precision == DMN_PREC_F64 ? 1024 : 256; }
 bool warp_possible(const dmn_handle* h) { return h->opt.warp_per_point >= 0 && !h->cmp && !h->opt.predictor; }
 bool warp_on(const dmn_handle* h, int64_t n) {
   return warp_possible(h) && (h->opt.warp_per_point == 1 ||
-                              (h->opt.first_stage != 1 && n <= WARP_AUTO_POINTS_PER_SM * h->n_sm));
+                              (h->opt.first_stage != 1 && n <= (int64_t)warp_auto_points_per_sm(h) * h->n_sm));
+}
+// lanes per point of the warp organisation: the option's, else by the call's size: 32 while there
+// are few points per SM (latency), then fewer (fewer idle lanes on the upper levels): 8 for the
+// FP64 condensation, 16 for the FP32 one (whose FP64 work is a smaller part)
+int warp_lanes_for(const dmn_handle* h, int64_t n) {
+  if (h->opt.warp_lanes) return h->opt.warp_lanes;
+  if (n <= 16 * (int64_t)h->n_sm) return 32;
+  return h->opt.precision == DMN_PREC_F64 ? 8 : 16;
 }
 
 // Per-slot scratch and counters of one work set (per-point buffers come with the first update).
@@ -1384,7 +1423,8 @@ cudaError_t alloc_ws(const dmn_handle* h, WorkSet& w) {
     e = cudaMalloc(&w.scr_s, sizeof(float) * (size_t)(27 * h->N_max) * w.nslots_s);
   }
   if (e == cudaSuccess && warp_possible(h)) {
-    w.nwarps_w = (int64_t)h->n_sm * WARP_CTAS_PER_SM * 4;
+    // one slot per group of the smallest size the handle may use
+    w.nwarps_w = (int64_t)h->n_sm * WARP_CTAS_PER_SM * 128 / (h->opt.warp_lanes ? h->opt.warp_lanes : WARP_MIN_LANES);
     const size_t per = h->opt.precision == DMN_PREC_F64 ? warp_slot_doubles<double>(h->N_max)
                                                         : warp_slot_doubles<float>(h->N_max);
     e = cudaMalloc(&w.scr_w, sizeof(double) * per * (size_t)w.nwarps_w);
@@ -1496,6 +1536,7 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, int64_t n_call, const int32_
   const bool warp = warp_on(h, n_call) && w.scr_w;
   const bool stage = first_stage_on(h->opt) && !warp;   // a small batch goes straight to the warp kernel
   const unsigned wgrid = (unsigned)(h->n_sm * WARP_CTAS_PER_SM);
+  const int lanes = warp ? warp_lanes_for(h, n_call) : 32;
   unsigned long long* passes = h->profiling ? h->d_passes : nullptr;
   if (stage) {   // counter [19]: the first stage's work counter
     // its corrections count against max_iter: the FP64-residual iteration keeps at least one
@@ -1512,16 +1553,14 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, int64_t n_call, const int32_
                            w.nbuf, w.scr_d, (double*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 1,
                            h->opt.predictor, dE, stage ? state_out : nullptr, passes ? passes + 1 : nullptr,
                            stage ? 1 : 0};
-    if (warp && ls) k_newton_warp<double, true><<<wgrid, 128, 0, s>>>(P, w.scr_w);
-    else if (warp) k_newton_warp<double, false><<<wgrid, 128, 0, s>>>(P, w.scr_w);
+    if (warp) launch_warp<double>(P, ls, lanes, wgrid, w.scr_w, s);
     else if (h->cmp) launch_newton<double, true>(P, ls, minb, grid, block, s);
     else launch_newton<double, false>(P, ls, minb, grid, block, s);
   } else {
     NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                           w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, sweep ? 0 : 1,
                           h->opt.predictor, dE, stage ? state_out : nullptr, passes ? passes + 1 : nullptr, 0};
-    if (warp && ls) k_newton_warp<float, true><<<wgrid, 128, 0, s>>>(P, w.scr_w);
-    else if (warp) k_newton_warp<float, false><<<wgrid, 128, 0, s>>>(P, w.scr_w);
+    if (warp) launch_warp<float>(P, ls, lanes, wgrid, w.scr_w, s);
     else if (h->cmp) launch_newton<float, true>(P, ls, minb, grid, block, s);
     else launch_newton<float, false>(P, ls, minb, grid, block, s);
   }
@@ -1663,9 +1702,12 @@ int dmn_create(const dmn_tree_desc* trees, int32_t n_trees, const dmn_options* o
     o.first_stage = opt->first_stage;
     o.stage_ctas_per_sm = opt->stage_ctas_per_sm;
     o.warp_per_point = opt->warp_per_point;
+    o.warp_lanes = opt->warp_lanes;
   }
   if (o.warp_per_point < -1 || o.warp_per_point > 1)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: warp_per_point must be -1, 0 or 1");
+  if (o.warp_lanes != 0 && o.warp_lanes != 8 && o.warp_lanes != 16 && o.warp_lanes != 32)
+    return fail(nullptr, DMN_ERR_ARG, "dmn_create: warp_lanes must be 0, 8, 16 or 32");
   if (o.first_stage < -1 || o.first_stage > 1)
     return fail(nullptr, DMN_ERR_ARG, "dmn_create: first_stage must be -1, 0 or 1");
   if (o.stage_ctas_per_sm == 0) o.stage_ctas_per_sm = STAGE_CTAS_DEFAULT;
@@ -1776,9 +1818,9 @@ int64_t dmn_state_size(const dmn_handle* h, int32_t tree_id) {
   return h->trees[tree_id].S;
 }
 
-int dmn_update_warp_per_point(const dmn_handle* h, int64_t n) {
+int dmn_update_lanes_per_point(const dmn_handle* h, int64_t n) {
   if (!h || n < 0) return -1;
-  return warp_on(h, n) ? 1 : 0;
+  return warp_on(h, n) ? warp_lanes_for(h, n) : 1;
 }
 
 int dmn_profile_enable(dmn_handle* h, int32_t enable) {

@@ -1764,19 +1764,21 @@ __device__ void tangent_level_rev(const TreeDev& t, bool cmp, int lvl, int lane,
 __device__ __forceinline__ int tangent_root(const TreeDev& t, bool cmp) { return cmp ? t.N - 1 : 0; }
 
 // ---------------------------------------------------------------------------
-// One Newton pass of one point by the 32 lanes of a warp, level by level of a heap tree (small
-// batches, where one point per thread leaves most of the GPU idle).  The per-laminate arithmetic
-// is that of tree_pass -- the same functions in the same order -- so a point's iterates are
-// those of the thread-per-point kernel to rounding (the two are compiled apart, and the
-// residual's squares are summed in another order: the lanes' partial sums are reduced at the
-// end).  The lanes share a level's
-// laminates: top-down the jump correction and the children's strains (each laminate hands them
-// to its children through ein / dein), then at the bottom level the leaves and the structured
+// One Newton pass of one point by a group of lanes of a warp (32, 16 or 8 lanes: one, two or four
+// points per warp), level by level of a heap tree (small batches, where one point per thread
+// leaves most of the GPU idle).  The per-laminate arithmetic is that of tree_pass -- the same
+// functions in the same order -- so a point's iterates are those of the thread-per-point kernel
+// to rounding (the two are compiled apart, and the residual's squares are summed in another
+// order: the lanes' partial sums are reduced at the end).  The lanes share a level's laminates:
+// top-down the jump correction and the children's strains (each laminate hands them to its
+// children through ein / dein), then at the bottom level the leaves and the structured
 // condensation, then bottom-up the condensation of each level from its children's results
-// (sb, dc); a warp barrier separates the levels.
-// Per-point arrays (one block per warp), field-major over the laminates, stride N (the handle's
-// largest tree): jumps a [N][3]; c1 c2 (g, H) [21][N]; ein [6][N] (FP64) and dein [6][N] (T);
-// results sb [6][N] (FP64), ds and C [27][N] (T); normals in P (nrm / nrmf [N][3], stride 1).
+// (sb, dc); a barrier of the group separates the levels.  Fewer lanes per point leave fewer
+// lanes idle on the upper levels (at depth 8 levels 1-5 hold 31 laminates) at the price of more
+// points in flight.
+// Per-point arrays (one block per group), field-major over the laminates, stride N (the
+// handle's largest tree): jumps a [N][3]; c1 c2 (g, H) [21][N]; ein [6][N] (FP64) and dein [6][N]
+// (T); results sb [6][N] (FP64), ds and C [27][N] (T); normals in P (nrm / nrmf [N][3], stride 1).
 template <typename T>
 struct WarpSlot {
   const double* a_in; double* a_out;
@@ -1805,15 +1807,15 @@ __device__ __forceinline__ void warp_sub_load(const WarpSlot<T>& W, int node, Su
   for (int k = 0; k < 21; ++k) r.C[k] = W.dc[(6 + k) * W.N + node];
 }
 
-// One level of the descent (lvl = 1 .. K): lane `lane` of 32 takes every 32nd laminate of the level;
-// at the bottom level it also evaluates the laminate's leaves and its structured condensation.
-// Adds the lane's share of the squared residual norm to r2.
+// One level of the descent (lvl = 1 .. K): lane `lane` of the point's `lanes` lanes takes every
+// lanes-th laminate of the level; at the bottom level it also evaluates the laminate's leaves and
+// its structured condensation.  Adds the lane's share of the squared residual norm to r2.
 template <typename T>
 __device__ void warp_descend_level(const TreeDev& t, const double Eloc[6], const PointArrays& P, const WarpSlot<T>& W,
-                                   bool apply, T step, int lvl, int lane, double& r2) {
+                                   bool apply, T step, int lvl, int lane, int lanes, double& r2) {
   const int K = t.K, NS = W.N;
   const int h0 = (1 << (lvl - 1)) - 1, nh = 1 << (lvl - 1);
-  for (int x = lane; x < nh; x += 32) {
+  for (int x = lane; x < nh; x += lanes) {
     const int node = h0 + x;
     double e[6];
     T de[6];
@@ -1877,9 +1879,9 @@ __device__ void warp_descend_level(const TreeDev& t, const double Eloc[6], const
 // One level of the condensation above the bottom one (lvl = K - 1 .. 1), from the children's results.
 template <typename T>
 __device__ void warp_condense_level(const TreeDev& t, const PointArrays& P, const WarpSlot<T>& W, int lvl, int lane,
-                                    double& r2) {
+                                    int lanes, double& r2) {
   const int h0 = (1 << (lvl - 1)) - 1, nh = 1 << (lvl - 1);
-  for (int x = lane; x < nh; x += 32) {
+  for (int x = lane; x < nh; x += lanes) {
     const int node = h0 + x;
     double nd[3];
     T nt[3];
@@ -1893,19 +1895,20 @@ __device__ void warp_condense_level(const TreeDev& t, const PointArrays& P, cons
   }
 }
 
-// The whole pass for a warp: levels in order, a warp barrier between them.  Returns this lane's
-// share of the squared residual norm; the root's result is at node 0 of W.
+// The whole pass for the point of a group of `lanes` lanes (gmask: the group's lanes in the warp):
+// levels in order, a barrier of the group between them.  Returns this lane's share of the squared
+// residual norm; the root's result is at node 0 of W.
 template <typename T>
 __device__ double warp_tree_pass(const TreeDev& t, const double Eloc[6], const PointArrays& P, const WarpSlot<T>& W,
-                                 bool apply, T step, int lane) {
+                                 bool apply, T step, int lane, int lanes, unsigned gmask) {
   double r2 = 0.0;
   for (int lvl = 1; lvl <= t.K; ++lvl) {
-    warp_descend_level<T>(t, Eloc, P, W, apply, step, lvl, lane, r2);
-    __syncwarp();
+    warp_descend_level<T>(t, Eloc, P, W, apply, step, lvl, lane, lanes, r2);
+    __syncwarp(gmask);
   }
   for (int lvl = t.K - 1; lvl >= 1; --lvl) {
-    warp_condense_level<T>(t, P, W, lvl, lane, r2);
-    __syncwarp();
+    warp_condense_level<T>(t, P, W, lvl, lane, lanes, r2);
+    __syncwarp(gmask);
   }
   return r2;
 }

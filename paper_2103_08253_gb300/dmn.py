@@ -16,7 +16,7 @@ from . import build as _build
 _lib = None
 
 # ABI symbols declared in include/dmn.h
-EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_update_warp_per_point", "dmn_interp_orientation",
+EXPORTS = ("dmn_create", "dmn_destroy", "dmn_state_size", "dmn_update_lanes_per_point", "dmn_interp_orientation",
            "dmn_update",
            "dmn_set_params", "dmn_grad", "dmn_profile_enable", "dmn_profile_read", "dmn_profile_read_stages",
            "dmn_update_noalloc",
@@ -47,7 +47,8 @@ class Options_(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("line_search", ctypes.c_int32),
                 ("predictor", ctypes.c_int32), ("first_stage", ctypes.c_int32),
-                ("stage_ctas_per_sm", ctypes.c_int32), ("warp_per_point", ctypes.c_int32)]
+                ("stage_ctas_per_sm", ctypes.c_int32), ("warp_per_point", ctypes.c_int32),
+                ("warp_lanes", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -73,8 +74,8 @@ def load_library(build_if_missing: bool = True):
     lib.dmn_destroy.restype = None
     lib.dmn_state_size.argtypes = [vp, i32]
     lib.dmn_state_size.restype = i64
-    lib.dmn_update_warp_per_point.restype = ctypes.c_int
-    lib.dmn_update_warp_per_point.argtypes = [ctypes.c_void_p, i64]
+    lib.dmn_update_lanes_per_point.restype = ctypes.c_int
+    lib.dmn_update_lanes_per_point.argtypes = [ctypes.c_void_p, i64]
     lib.dmn_interp_orientation.argtypes = [vp, i64, vp, vp, vp, vp]
     lib.dmn_interp_orientation.restype = ctypes.c_int
     lib.dmn_update.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -243,13 +244,13 @@ class DMN:
     extrapolated along the new strain increment (the state then holds the last jump change
     and strain increment too).  first_stage: True starts every point with the all-FP32 Newton
     stage, False goes straight to the iteration of the chosen precision; None (default) runs it
-    in the mixed forms only.  warp_per_point: 0 (default) one warp per point for batches of at most
-    256 points per SM, 1 always, -1 never (heap trees, the paper's start).  The other options are those of
-    dmn_options."""
+    in the mixed forms only.  warp_per_point: 0 (default) the warp organisation for calls of at most
+    1024 points per SM in the FP64 form, 256 in the mixed forms; 1 always, -1 never (heap trees, the
+    paper's start); warp_lanes: lanes per point there (32, 16, 8; 0 chooses by the call's size).  The other options are those of dmn_options."""
 
     def __init__(self, tree, precision: str = "f64", tol: float = 1e-12, max_iter: int = 50, block: int = 0,
                  ctas_per_sm: int = 0, line_search: bool = False, predictor: bool = False,
-                 first_stage=None, stage_ctas_per_sm: int = 0, warp_per_point: int = 0):
+                 first_stage=None, stage_ctas_per_sm: int = 0, warp_per_point: int = 0, warp_lanes: int = 0):
         import torch
         self._lib = load_library()
         if not torch.cuda.is_available():
@@ -271,7 +272,7 @@ class DMN:
         opt = Options_(float(tol), int(max_iter), PRECISIONS[precision], int(block),
                        int(ctas_per_sm), int(bool(line_search)), int(bool(predictor)),
                        0 if first_stage is None else (1 if first_stage else -1), int(stage_ctas_per_sm),
-                       int(warp_per_point))
+                       int(warp_per_point), int(warp_lanes))
         self.precision = precision
         want = precision != "f64" if first_stage is None else bool(first_stage)
         self.first_stage = want and not line_search and not predictor
@@ -285,13 +286,13 @@ class DMN:
         self.state_size = int(self._lib.dmn_state_size(h, -1))
         self.tree_state_sizes = [int(self._lib.dmn_state_size(h, k)) for k in range(len(trees))]
 
-    def warp_per_point_for(self, n: int) -> bool:
-        """dmn_update_warp_per_point: whether a call of n points runs one warp per point (else one
-        point per thread of the persistent kernel)."""
-        r = self._lib.dmn_update_warp_per_point(self._h, int(n))
+    def lanes_per_point(self, n: int) -> int:
+        """dmn_update_lanes_per_point: the organisation of a call of n points, as lanes per point (1
+        one point per thread of the persistent kernel; 32, 16 or 8 the warp organisation)."""
+        r = self._lib.dmn_update_lanes_per_point(self._h, int(n))
         if r < 0:
-            raise ValueError("warp_per_point_for: n must be >= 0 on an open handle")
-        return bool(r)
+            raise ValueError("lanes_per_point: n must be >= 0 on an open handle")
+        return int(r)
 
     def close(self):
         if getattr(self, "_h", None):

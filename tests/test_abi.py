@@ -136,7 +136,13 @@ def test_first_stage_option_is_checked_without_touching_the_gpu():
         o = dmn.Options_(1e-12, 50, dmn.PREC_F64, 0, 0, 0, 0, 0, 0, bad)
         assert lib.dmn_create(ctypes.byref(d), 1, ctypes.byref(o), ctypes.byref(h)) == -1
         assert h.value is None and "warp_per_point must be -1, 0 or 1" in lib.dmn_last_error(None).decode()
-    assert [f[0] for f in dmn.Options_._fields_][-3:] == ["first_stage", "stage_ctas_per_sm", "warp_per_point"]
+    for bad in (4, 24, 64, -8):
+        h = ctypes.c_void_p(123)
+        o = dmn.Options_(1e-12, 50, dmn.PREC_F64, 0, 0, 0, 0, 0, 0, 0, bad)
+        assert lib.dmn_create(ctypes.byref(d), 1, ctypes.byref(o), ctypes.byref(h)) == -1
+        assert h.value is None and "warp_lanes must be 0, 8, 16 or 32" in lib.dmn_last_error(None).decode()
+    assert [f[0] for f in dmn.Options_._fields_][-4:] == ["first_stage", "stage_ctas_per_sm", "warp_per_point",
+                                                          "warp_lanes"]
 
 
 def _noalloc(d, o, n=8, arrays=None):
@@ -175,7 +181,7 @@ def test_calls_on_null_handle_are_argument_errors():
     assert lib.dmn_update_host(None, 4, *([None] * 11), 0, None) == -1
     assert lib.dmn_interp_orientation(None, 4, None, None, None, None) == -1
     assert lib.dmn_state_size(None, 0) == -1
-    assert lib.dmn_update_warp_per_point(None, 16) == -1
+    assert lib.dmn_update_lanes_per_point(None, 16) == -1
     lib.dmn_destroy(None)
 
 

@@ -114,3 +114,16 @@ def test_roofline_names_the_warp_kernel(monkeypatch):
     mw = bench.roofline_mixed(dict(r, warp=True), n, steps)
     assert mw["kernel"] == "k_newton_warp<float>"
     assert keys == ["k_newton_f64", "k_newton_warp_f64", "k_newton_warp_mixed"]
+
+
+def test_form_options_and_l2_flush_rule():
+    """Forms name the start, the first stage and the organisation; a step whose state fits twice into
+    the L2 gets an L2 flush (depth 8: 1533 fields, so 4096 points do and 2^20 do not)."""
+    assert bench.form_opts("f64/thread") == ("f64", False) and bench.form_warp_option("f64/thread") == (-1, 0)
+    assert bench.form_warp_option("mixed") == (0, 0) and bench.form_stage_option("mixed") is None
+    assert bench.form_warp_option("f64/w8") == (1, 8) and bench.form_warp_option("mixed/w16") == (1, 16)
+    assert bench.form_stage_option("f64/stage") is True and bench.form_stage_option("mixed/no-stage") is False
+    tree = W.tree_d10_fit(8, seed=0)
+    S = bench.state_fields(tree)
+    assert S == 1533
+    assert bench.l2_flush_needed(S, 4096) and not bench.l2_flush_needed(S, 1 << 20)

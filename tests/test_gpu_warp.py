@@ -1,7 +1,8 @@
-"""One warp per point for small batches (heap trees), through the C ABI.
+"""The warp organisation for small batches (heap trees): a point per group of 32, 16 or 8 lanes of a
+warp, through the C ABI.
 
 The warp kernel runs the same per-laminate functions as the thread-per-point kernel, level by level
-with the lanes sharing a level; the residual's sum of squares is added in another order, and the two
+with the group's lanes sharing a level; the residual's sum of squares is added in another order, and the two
 kernels are compiled separately, so their roundings differ.  Its iterates must be those of the
 thread-per-point kernel to rounding (the same statuses, the same correction counts except where the
 criterion ties within rounding) and it must meet the oracle's tolerances in every form, with and
@@ -18,15 +19,17 @@ pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
 
 
-@pytest.mark.parametrize("prec", ["f64", "mixed", "mixed-f32-tangent"])
-def test_warp_kernel_reproduces_the_thread_kernel(prec):
+@pytest.mark.parametrize("prec,lanes", [("f64", 32), ("mixed", 32), ("mixed-f32-tangent", 32), ("f64", 16),
+                                        ("f64", 8), ("mixed", 8)])
+def test_warp_kernel_reproduces_the_thread_kernel(prec, lanes):
     K, n = 8, 1000
     tree = W.tree_d10_fit(K, seed=401)
     A2, lam, Q = W.orientation_field(n, seed=402)
     Ef = W.random6_path_final(n, 0.03, seed=403)
     outs = {}
     for mode in (1, -1):
-        m = dmn.DMN(tree, precision=prec, warp_per_point=mode, first_stage=False)
+        m = dmn.DMN(tree, precision=prec, warp_per_point=mode, first_stage=False,
+                    warp_lanes=lanes if mode == 1 else 0)
         st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
         for s in range(1, 6):
             En, dE = W.proportional_increment(Ef, s, 20)
@@ -44,19 +47,21 @@ def test_warp_kernel_reproduces_the_thread_kernel(prec):
     assert rel(a["stress"], b["stress"]).max() <= 1e-9
 
 
-@pytest.mark.parametrize("prec", ["f64", "mixed", "mixed-f32-tangent"])
-def test_warp_kernel_against_the_oracle_ragged(prec):
+@pytest.mark.parametrize("prec,lanes", [("f64", 32), ("mixed", 32), ("mixed-f32-tangent", 32), ("f64", 8),
+                                        ("mixed-f32-tangent", 16)])
+def test_warp_kernel_against_the_oracle_ragged(prec, lanes):
     tol_t = {"f64": 1e-10, "mixed": 1e-6, "mixed-f32-tangent": 1e-4}[prec]
     tol_s = {"f64": 1e-10, "mixed": 1e-6, "mixed-f32-tangent": 1e-6}[prec]
     for K, n in ((1, 1), (2, 33), (3, 129), (5, 257), (8, 37)):
         tree = W.tree_d10_fit(K, seed=410 + K)
         A2, lam, Q = W.orientation_field(n, seed=420 + K)
         Ef = W.random6_path_final(n, 0.025, seed=430 + K)
-        worst, out, _ = run_path(tree, lam, Q, Ef, 4, prec, warp_per_point=1)
+        worst, out, _ = run_path(tree, lam, Q, Ef, 4, prec, warp_per_point=1, warp_lanes=lanes)
         assert worst["stress"] <= tol_s and worst["tangent"] <= tol_t, (K, n, worst)
 
 
-def test_warp_kernel_with_the_line_search():
+@pytest.mark.parametrize("lanes", [32, 8])
+def test_warp_kernel_with_the_line_search(lanes):
     """Large cyclic steps, where the line search halves steps: the warp kernel's two buffers (accepted and
     trial) against the thread kernel's, and the oracle's line search."""
     import oracle
@@ -65,7 +70,8 @@ def test_warp_kernel_with_the_line_search():
     A2, lam, Q = W.orientation_field(n, seed=441)
     amp = W.random6_path_final(n, 0.025, seed=442)
     S = W.state_size(K)
-    ms = {mode: dmn.DMN(tree, precision="f64", line_search=True, warp_per_point=mode) for mode in (1, -1)}
+    ms = {mode: dmn.DMN(tree, precision="f64", line_search=True, warp_per_point=mode,
+                        warp_lanes=lanes if mode == 1 else 0) for mode in (1, -1)}
     st = {mode: torch.zeros((S, n), dtype=torch.float64, device=DEV) for mode in ms}
     so = np.zeros((S, n))
     for s in range(1, n_steps + 1):
@@ -84,7 +90,8 @@ def test_warp_kernel_with_the_line_search():
         m.close()
 
 
-def test_warp_kernel_unknown_tree_and_several_depths():
+@pytest.mark.parametrize("lanes", [32, 16])
+def test_warp_kernel_unknown_tree_and_several_depths(lanes):
     """Several heap trees of different depths in one handle, points selected by tree_id, one of them out
     of range: the warp kernel reports it and updates the others as the thread kernel does."""
     trees = [W.tree_d10_fit(K, seed=450 + K) for K in (5, 8)]
@@ -96,7 +103,7 @@ def test_warp_kernel_unknown_tree_and_several_depths():
     En, dE = W.proportional_increment(Ef, 6, 20)
     outs = {}
     for mode in (1, -1):
-        m = dmn.DMN(trees, precision="f64", warp_per_point=mode)
+        m = dmn.DMN(trees, precision="f64", warp_per_point=mode, warp_lanes=lanes if mode == 1 else 0)
         st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
         outs[mode] = {k: v.cpu().numpy() for k, v in m.update(d(lam), d(Q), d(En), d(dE), st,
                                                                tree_id=d(tid)).items()}
@@ -109,14 +116,15 @@ def test_warp_kernel_unknown_tree_and_several_depths():
     assert rel(a["stress"][same], b["stress"][same]).max() <= 1e-11
 
 
-def test_warp_kernel_points_are_independent_of_the_batch():
+@pytest.mark.parametrize("lanes", [32, 8])
+def test_warp_kernel_points_are_independent_of_the_batch(lanes):
     """In the warp organisation too a point's update depends on that point alone: the same points as
     two uneven parts in the reverse order give the whole batch's results bit for bit."""
     K, n, cut = 7, 3000, 1801
     tree = W.tree_d10_fit(K, seed=470)
     A2, lam, Q = W.orientation_field(n, seed=471)
     Ef = W.random6_path_final(n, 0.03, seed=472)
-    m = dmn.DMN(tree, precision="mixed", warp_per_point=1)
+    m = dmn.DMN(tree, precision="mixed", warp_per_point=1, warp_lanes=lanes)
     lam_d, Q_d = d(lam), d(Q)
     st = torch.zeros((m.state_size, n), dtype=torch.float64, device=DEV)
     for s in range(1, 4):
@@ -134,16 +142,19 @@ def test_warp_kernel_points_are_independent_of_the_batch():
     m.close()
 
 
-def test_the_default_organisation_is_chosen_per_call():
-    """By default a call of at most 256 points per SM runs the warp kernel and a larger one the thread
-    kernel (bit for bit the results of warp_per_point = 1 and -1); dmn_update_host decides on the
-    whole call, so its chunks get the kernel of the device call; first_stage = True keeps the thread
-    kernel with its stage."""
+@pytest.mark.parametrize("prec,per_sm,lanes", [("f64", 1024, 8), ("mixed", 256, 16)])
+def test_the_default_organisation_is_chosen_per_call(prec, per_sm, lanes):
+    """By default a call of at most 1024 points per SM (FP64 form) or 256 (mixed forms) runs the warp
+    kernel, with 32 lanes per point up to 16 points per SM and 8 (FP64) or 16 (mixed) above, and a
+    larger call the thread kernel: bit for bit the results of warp_per_point = 1 and -1.
+    dmn_update_host decides on the whole call, so its chunks get the kernel of the device call;
+    first_stage = True keeps the thread kernel with its stage."""
     K = 5
     n_sm = torch.cuda.get_device_properties(DEV).multi_processor_count
-    limit = 256 * n_sm
+    limit = per_sm * n_sm
     tree = W.tree_d10_fit(K, seed=480)
-    handles = {mode: dmn.DMN(tree, precision="f64", warp_per_point=mode) for mode in (0, 1, -1)}
+    handles = {mode: dmn.DMN(tree, precision=prec, warp_per_point=mode) for mode in (0, 1, -1)}
+    assert handles[0].lanes_per_point(16 * n_sm) == 32 and handles[0].lanes_per_point(16 * n_sm + 1) == lanes
     for n in (limit, limit + 1):
         A2, lam, Q = W.orientation_field(n, seed=481)
         Ef = W.random6_path_final(n, 0.03, seed=482)
@@ -152,8 +163,8 @@ def test_the_default_organisation_is_chosen_per_call():
         st = torch.zeros((S, n), dtype=torch.float64, device=DEV)
         outs = {mode: m.update(d(lam), d(Q), d(En), d(dE), st) for mode, m in handles.items()}
         ref = outs[1] if n <= limit else outs[-1]
-        assert handles[0].warp_per_point_for(n) == (n <= limit)
-        assert handles[1].warp_per_point_for(n) and not handles[-1].warp_per_point_for(n)
+        assert handles[0].lanes_per_point(n) == (lanes if n <= limit else 1)
+        assert handles[1].lanes_per_point(n) == lanes and handles[-1].lanes_per_point(n) == 1
         for k in outs[0]:
             assert torch.equal(outs[0][k], ref[k]), (n, k)
         # the same call from host arrays in chunks smaller than the limit
@@ -165,7 +176,7 @@ def test_the_default_organisation_is_chosen_per_call():
         m.close()
     m = dmn.DMN(tree, precision="f64", first_stage=True)
     n = 512
-    assert not m.warp_per_point_for(n)
+    assert m.lanes_per_point(n) == 1
     A2, lam, Q = W.orientation_field(n, seed=483)
     Ef = W.random6_path_final(n, 0.03, seed=484)
     En, dE = W.proportional_increment(Ef, 6, 20)
