@@ -189,7 +189,8 @@ def final_flops(K, npts, sweep, w=None):
 # ---------------------------------------------------------------------------------------------
 def src_hash():
     h = hashlib.sha256()
-    for f in ("paper_2103_08253_gb300/csrc/dmn.cu", "paper_2103_08253_gb300/csrc/dmn_device.cuh"):
+    for f in ("paper_2103_08253_gb300/csrc/dmn.cu", "paper_2103_08253_gb300/csrc/dmn_device.cuh",
+              "paper_2103_08253_gb300/csrc/dmn_warp.cu", "paper_2103_08253_gb300/csrc/dmn_launch.cuh"):
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -163,9 +163,9 @@ typedef struct {
                            * arithmetic per laminate and the same iterates to rounding), where one point
                            * per thread would leave SMs idle; 1 does so for every call; -1 never.  The choice is made per call (for
                            * dmn_update_host on the whole batch, not per chunk); first_stage = 1 turns
-                           * the default off.  Trees with weightless leaves (compressed) and the
-                           * extrapolated start always run one point per thread; the first stage is not run
-                           * in this organisation. */
+                           * the default off.  The extrapolated start always runs one point per thread; the
+                           * first stage is not run in this organisation.  Compressed trees (weightless
+                           * leaves) run it level by level of the full tree's heap positions. */
   int32_t warp_lanes;     /* lanes per point in that organisation: 32 (one point per warp), 16 or 8 (two
                            * or four points per warp, side by side); 0 (default) chooses by the call's
                            * size: 32 up to 16 points per SM, then 8 in the FP64 form, 16 in the mixed

@@ -1,9 +1,10 @@
 """Build of the CUDA library (in-tree, sm_103a only).
 
 ``python -m paper_2103_08253_gb300.build`` compiles ``csrc/dmn.cu`` (the DMN
-update), ``csrc/fe.cu`` (the hexahedral FE operator and PCG) and ``csrc/peak.cu``
-(the measured FMA peaks of the rooflines) with nvcc, in parallel, and links them
-into ``_build/libdmn.so`` next to this file.
+update: C ABI and the thread-per-point kernels), ``csrc/dmn_warp.cu`` (its warp
+organisation for small calls), ``csrc/fe.cu`` (the hexahedral FE operator and
+PCG) and ``csrc/peak.cu`` (the measured FMA peaks of the rooflines) with nvcc, in
+parallel, and links them into ``_build/libdmn.so`` next to this file.
 """
 from __future__ import annotations
 
@@ -14,9 +15,10 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = [os.path.join(HERE, "csrc", "dmn.cu"), os.path.join(HERE, "csrc", "fe.cu"),
-           os.path.join(HERE, "csrc", "peak.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "dmn_device.cuh"), os.path.join(ROOT, "include", "dmn.h"),
+SOURCES = [os.path.join(HERE, "csrc", "dmn.cu"), os.path.join(HERE, "csrc", "dmn_warp.cu"),
+           os.path.join(HERE, "csrc", "fe.cu"), os.path.join(HERE, "csrc", "peak.cu")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", "dmn_device.cuh"), os.path.join(HERE, "csrc", "dmn_launch.cuh"),
+                  os.path.join(ROOT, "include", "dmn.h"),
                   os.path.join(ROOT, "include", "fe.h"), os.path.join(ROOT, "include", "dmn_peak.h")]
 LIB = os.path.join(HERE, "_build", "libdmn.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

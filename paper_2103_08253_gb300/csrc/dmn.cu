@@ -26,6 +26,7 @@
 
 #include "../../include/dmn.h"
 #include "dmn_device.cuh"
+#include "dmn_launch.cuh"
 
 using namespace dmn;
 
@@ -130,6 +131,7 @@ TreeDev tree_dev(const Tree& t) {
   d.pidx = t.d_tab ? t.d_tab + 4 * t.Lc + 2 * t.N : nullptr;
   d.kid = t.d_tab ? t.d_tab + 4 * t.Lc + 3 * t.N : nullptr;
   d.hcid = t.d_tab ? t.d_tab + 4 * t.Lc + 5 * t.N : nullptr;
+  d.kslot = t.d_tab ? t.d_tab + 4 * t.Lc + 5 * t.N + ((1 << t.K) - 1) : nullptr;
   return d;
 }
 
@@ -319,20 +321,6 @@ __device__ __forceinline__ void local_strain(const double* Q, const double* En, 
   }
 }
 
-// All trees of a handle, passed by value to the kernels.
-struct Forest {
-  TreeDev t[DMN_MAX_TREES];
-  int n;
-};
-
-// point handled by thread/work item i and its tree (n_trees = invalid)
-__device__ __forceinline__ void point_of(const int64_t* perm, const int32_t* tid, int n_trees, int64_t i,
-                                         int64_t& p, int& tree) {
-  p = perm ? perm[i] : i;
-  const int t = tid ? tid[p] : 0;
-  tree = (t >= 0 && t < n_trees) ? t : n_trees;
-}
-
 // Sorting points by tree (several trees): count per tree, exclusive offsets,
 // scatter.  Lanes of a warp with the same tree share one atomic.  The order
 // inside a tree is not deterministic; results do not depend on it.
@@ -422,33 +410,6 @@ __device__ __forceinline__ void write_stress_tangent(const double* Q, const doub
       tangent[6 * I + J] = s;
     }
 }
-
-template <typename T>
-struct NewtonParams {
-  Forest F;
-  int64_t n, nslots;
-  int N_max;
-  const int32_t* tid;
-  const int64_t* perm;
-  const double* state_in;
-  double *state_out, *stress, *tangent;
-  int32_t *iters, *status;
-  const double* nbuf;
-  double* scr_d;
-  T* scr_t;
-  unsigned long long* counter;
-  double tol;
-  int max_iter;
-  int write_outputs;  // no final sweep: stress and tangent (local frame) come from the converged Newton pass
-  int predictor;      // extrapolated start; the state carries the last jump change and strain increment
-  const double* dE;   // [n][6] strain increments (global frame), read with the extrapolated start
-  const double* a_start;  // the jumps to start from (state layout), or NULL for those of state_in; with the
-                          // first stage these are its jumps in state_out, and iters holds its corrections
-  unsigned long long* passes;  // profiling: tree passes of all points added here, or NULL
-  int min_corr;       // corrections before the criterion may end the iteration (1 for the FP64 form after
-                      // the first stage: one quadratic step from the FP32 iterate, so that the accepted
-                      // iterate is as far inside the criterion as in the plain FP64 iteration)
-};
 
 // MINB: resident CTAs per SM the register allocation is sized for (255, 170 or
 // 128 registers per thread at 2, 3 or 4 CTAs of 128 threads).
@@ -656,172 +617,6 @@ __global__ void __launch_bounds__(128, MINB) k_newton(NewtonParams<T> P) {
     pt = -1;
   }
   if (P.passes && npass) atomicAdd(P.passes, npass);
-}
-
-// Small batches: one point per group of G lanes of a warp (G = 32, 16 or 8; heap trees, the
-// paper's start), the group's lanes sharing each level of the tree (warp_tree_pass).  The Newton
-// loop is k_newton's.  The warp's groups run their passes side by side: every iteration of the
-// warp's loop is one pass of every group that holds a point, so the groups' lanes stay together
-// (the pass's instructions are the same for every point); a group whose point is done writes it
-// out and takes the next one from the work counter.  Each group owns a block of scratch
-// (warp_slot_doubles<T>(N) doubles) holding its point's jumps, g, H, level hand-over and subtree
-// results, in two buffers where the line search needs them.
-template <typename T>
-__host__ __device__ inline size_t warp_slot_doubles(int N) {
-  // jumps 2 x 3N, ein 6N, sb 6N, normals 3N (FP64); g, H 2 x 21N, dein 6N, ds + C 27N (T); FP32 normals 3N
-  const size_t d = (size_t)21 * N, tt = (size_t)75 * N * sizeof(T), f = (size_t)3 * N * sizeof(float);
-  return d + (tt + f + sizeof(double) - 1) / sizeof(double);
-}
-constexpr int WARP_CTAS_PER_SM = 2;   // 128-thread CTAs: 8 warps per SM
-constexpr int WARP_MIN_LANES = 8;     // the smallest group: the scratch holds 32 / 8 = 4 slots per warp
-
-template <typename T, bool LS, int G>
-__global__ void __launch_bounds__(128) k_newton_warp(NewtonParams<T> P, double* scratch) {
-  static_assert(G == 8 || G == 16 || G == 32, "8, 16 or 32 lanes per point");
-  const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
-  const int lane = threadIdx.x % G;
-  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << ((threadIdx.x & 31) / G * G);
-  const int NM = P.N_max;
-  double* base = scratch + (size_t)grp * warp_slot_doubles<T>(NM);
-  double* abuf[2] = {base, base + 3 * NM};
-  double* ein = base + 6 * NM;
-  double* sbv = base + 12 * NM;
-  double* nrm = base + 18 * NM;
-  T* tb = reinterpret_cast<T*>(base + 21 * NM);
-  T* gbuf[2] = {tb, tb + 21 * NM};
-  T* dein = tb + 42 * NM;
-  T* dcv = tb + 48 * NM;
-  float* nrmf = reinterpret_cast<float*>(tb + 75 * NM);
-  PointArrays A{};
-  A.nrm = nrm; A.ns = 1; A.nrmf = nrmf;
-  A.as = 1; A.paper = false;
-  A.zs = (size_t)P.n;
-  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-  unsigned long long npass = 0;
-  // the group's point and its Newton state
-  int64_t pt = -1;
-  int tr = 0, it0 = 0, it = 0, cur = 0, halvings = 0;
-  bool first = true;
-  T step = (T)1;
-  double rn_acc = 0.0, Eloc[6];
-  Sub<T> root, root_acc;
-  // the next point of a known tree for this group (points of unknown trees are reported on the
-  // way); false once the counter is exhausted
-  auto take = [&]() -> bool {
-    for (;;) {
-      unsigned long long i = 0;
-      if (lane == 0) i = atomicAdd(P.counter, 1ull);
-      i = __shfl_sync(gmask, i, 0, G);
-      if (i >= (unsigned long long)P.n) return false;
-      point_of(P.perm, P.tid, P.F.n, (int64_t)i, pt, tr);
-      if (tr < P.F.n) break;
-      if (lane == 0) {   // unknown tree: report and take the next point
-        P.iters[pt] = 0;
-        P.status[pt] = DMN_STATUS_BAD_TREE;
-        for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = qnan;
-        for (int I = 0; I < 36; ++I) P.tangent[36 * pt + I] = qnan;
-      }
-    }
-    const TreeDev& t = P.F.t[tr];
-    const int nzf = 6 * t.nz;
-#pragma unroll
-    for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * NM + I) * P.n + pt];
-    for (int f = lane; f < 3 * t.N; f += G) {
-      const int node = f / 3, c = f - 3 * node;
-      const int lvl = 32 - __clz(node + 1);
-      const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
-      abuf[0][f] = (P.a_start ? P.a_start : P.state_in)[(size_t)(nzf + 3 * j + c) * P.n + pt];
-      const double nv = P.nbuf[(size_t)f * P.n + pt];
-      nrm[f] = nv;
-      if (sizeof(T) == 4) nrmf[f] = narrow_rn(nv);
-    }
-    it0 = P.a_start ? P.iters[pt] : 0;
-    it = 0; cur = 0; halvings = 0; first = true; step = (T)1; rn_acc = 0.0;
-    __syncwarp(gmask);
-    return true;
-  };
-  bool have = take();
-  while (__any_sync(0xffffffffu, have)) {
-    if (!have) continue;
-    const TreeDev& t = P.F.t[tr];
-    A.z = P.state_in + pt;
-    WarpSlot<T> W{abuf[cur], abuf[LS ? 1 - cur : cur], gbuf[cur], gbuf[LS ? 1 - cur : cur], ein, dein, sbv, dcv, NM};
-    ++npass;
-    double r2 = warp_tree_pass<T>(t, Eloc, A, W, !first, step, lane, G, gmask);
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) r2 += __shfl_xor_sync(gmask, r2, o, G);
-    warp_sub_load<T>(W, 0, root);
-    __syncwarp(gmask);
-    const double rn = sqrt(r2);
-    double sn2 = 0.0;
-#pragma unroll
-    for (int I = 0; I < 6; ++I) sn2 += root.sb[I] * root.sb[I];
-    const double sn = sqrt(sn2);
-    int st = -1;
-    if (!LS) {
-      first = false;
-      if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
-      else if (rn <= P.tol * (double)t.N * sn && it >= P.min_corr) st = DMN_STATUS_OK;
-      else if (it >= P.max_iter - it0) st = DMN_STATUS_MAXITER;
-      if (st < 0) { ++it; continue; }
-    } else {
-      const bool accepted = first || rn < rn_acc;
-      if (accepted) {
-        first = false;
-        cur = 1 - cur;
-        rn_acc = rn;
-        root_acc = root;
-        step = (T)1;
-        halvings = 0;
-        if (!isfinite(rn) || !isfinite(sn)) st = DMN_STATUS_NONFINITE;
-        else if (rn <= P.tol * (double)t.N * sn && it >= P.min_corr) st = DMN_STATUS_OK;
-        else if (it >= P.max_iter - it0) st = DMN_STATUS_MAXITER;
-        if (st < 0) { ++it; continue; }
-      } else if (++halvings > 8) {
-        st = DMN_STATUS_LINESEARCH;   // no halving lowered the residual: keep the accepted iterate
-        ++it;
-        root = root_acc;
-      } else {
-        step *= (T)0.5;
-        continue;
-      }
-    }
-    // finished point: jumps (paper ordering), counters, and without a final sweep the local-frame
-    // stress and packed tangent for k_final to rotate
-    const int nzf = 6 * t.nz;
-    const double* afin = abuf[cur];
-    for (int f = lane; f < 3 * t.N; f += G) {
-      const int node = f / 3, c = f - 3 * node;
-      const int lvl = 32 - __clz(node + 1);
-      const int j = (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
-      P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt] = st == DMN_STATUS_NONFINITE ? qnan : afin[f];
-    }
-    if (lane == 0) {
-      P.iters[pt] = it + it0;
-      P.status[pt] = st;
-      if (P.write_outputs) {
-        for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = root.sb[I];
-        for (int k = 0; k < 21; ++k) P.tangent[36 * pt + k] = widen(root.C[k]);
-      }
-    }
-    __syncwarp(gmask);
-    have = take();
-  }
-  if (lane == 0 && P.passes && npass) atomicAdd(P.passes, npass);
-}
-
-template <typename T>
-void launch_warp(const NewtonParams<T>& P, bool ls, int lanes, unsigned grid, double* scr, cudaStream_t s) {
-  if (lanes == 8) {
-    if (ls) k_newton_warp<T, true, 8><<<grid, 128, 0, s>>>(P, scr);
-    else k_newton_warp<T, false, 8><<<grid, 128, 0, s>>>(P, scr);
-  } else if (lanes == 16) {
-    if (ls) k_newton_warp<T, true, 16><<<grid, 128, 0, s>>>(P, scr);
-    else k_newton_warp<T, false, 16><<<grid, 128, 0, s>>>(P, scr);
-  } else {
-    if (ls) k_newton_warp<T, true, 32><<<grid, 128, 0, s>>>(P, scr);
-    else k_newton_warp<T, false, 32><<<grid, 128, 0, s>>>(P, scr);
-  }
 }
 
 // The mixed forms' first stage (Sec. 3.2's Newton iteration with every quantity in FP32: jumps,
@@ -1283,7 +1078,7 @@ struct CmpTree {
   std::vector<double> p, q, c;   // p, q [N][M]; c = c1 [N], c2 [N], sc [N], leaf weights [L], 1 / (c1 c2) [N]
   std::vector<float> cf;         // c1f [N], c2f [N], c12f [N], scf [N], 1 / (c1 c2) [N]
   std::vector<int> tab;          // lf [Lc] (4 ints each), pre [N], post [N], paper index [N], children [2 N],
-                                 // the laminate at each heap position [2^K - 1]
+                                 // the laminate at each heap position [2^K - 1], leaf children's state slots [2 N]
 };
 
 void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& B) {
@@ -1367,6 +1162,17 @@ void build_compressed(const dmn_tree_desc& d, const bool inelastic[2], CmpTree& 
     if (cid[h] >= 0) { kids[2 * cid[h]] = stand_in(2 * h); kids[2 * cid[h] + 1] = stand_in(2 * h + 1); }
   B.tab.insert(B.tab.end(), kids.begin(), kids.end());
   for (int h = 1; h <= N; ++h) B.tab.push_back(cid[h]);   // heap position h - 1: its laminate or -1
+  // the state slot of every child that is a leaf (the slots of the leaf table, in leaf order)
+  std::vector<int> slot_of(L, -1), kslot(2 * (size_t)Nc, -1);
+  for (int l = 0; l < Lc; ++l) slot_of[lf[4 * l + 3] >> 12] = ((lf[4 * l + 3] >> 2) & 1023) - 1;
+  for (int h = 1; h <= N; ++h)
+    if (cid[h] >= 0)
+      for (int side = 0; side < 2; ++side) {
+        int x = 2 * h + side;
+        while (x <= N && cid[x] < 0) x = W[2 * x] > 0.0 ? 2 * x : 2 * x + 1;
+        if (x > N) kslot[2 * cid[h] + side] = slot_of[x - N - 1];
+      }
+  B.tab.insert(B.tab.end(), kslot.begin(), kslot.end());
 }
 
 bool has_zero_weight(const dmn_tree_desc& d) {
@@ -1397,7 +1203,12 @@ bool first_stage_on(const dmn_options& o) {
 // condensation: one point per warp 6.2x at 1024, two per warp 4.7x at 4096, 1.48x at 32768, even
 // at about 45000.
 int warp_auto_points_per_sm(const dmn_handle* h) { return h->opt.precision == DMN_PREC_F64 ? 1024 : 256; }
-bool warp_possible(const dmn_handle* h) { return h->opt.warp_per_point >= 0 && !h->cmp && !h->opt.predictor; }
+bool warp_possible(const dmn_handle* h) {
+  if (h->opt.warp_per_point < 0 || h->opt.predictor) return false;
+  for (const Tree& t : h->trees)
+    if (t.N < 1) return false;   // a compressed tree reduced to one leaf: no laminate to hold the result
+  return true;
+}
 bool warp_on(const dmn_handle* h, int64_t n) {
   return warp_possible(h) && (h->opt.warp_per_point == 1 ||
                               (h->opt.first_stage != 1 && n <= (int64_t)warp_auto_points_per_sm(h) * h->n_sm));
@@ -1553,14 +1364,16 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, int64_t n_call, const int32_
                            w.nbuf, w.scr_d, (double*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, 1,
                            h->opt.predictor, dE, stage ? state_out : nullptr, passes ? passes + 1 : nullptr,
                            stage ? 1 : 0};
-    if (warp) launch_warp<double>(P, ls, lanes, wgrid, w.scr_w, s);
+    if (warp && h->cmp) launch_warp<double, true>(P, ls, lanes, wgrid, w.scr_w, s);
+    else if (warp) launch_warp<double, false>(P, ls, lanes, wgrid, w.scr_w, s);
     else if (h->cmp) launch_newton<double, true>(P, ls, minb, grid, block, s);
     else launch_newton<double, false>(P, ls, minb, grid, block, s);
   } else {
     NewtonParams<float> P{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
                           w.nbuf, w.scr_d, (float*)w.scr_t, w.counter, h->opt.tol, h->opt.max_iter, sweep ? 0 : 1,
                           h->opt.predictor, dE, stage ? state_out : nullptr, passes ? passes + 1 : nullptr, 0};
-    if (warp) launch_warp<float>(P, ls, lanes, wgrid, w.scr_w, s);
+    if (warp && h->cmp) launch_warp<float, true>(P, ls, lanes, wgrid, w.scr_w, s);
+    else if (warp) launch_warp<float, false>(P, ls, lanes, wgrid, w.scr_w, s);
     else if (h->cmp) launch_newton<float, true>(P, ls, minb, grid, block, s);
     else launch_newton<float, false>(P, ls, minb, grid, block, s);
   }

@@ -86,6 +86,7 @@ struct TreeDev {
   const int* pidx;   // [N] the paper's index of each laminate (in the uncompressed tree)
   const int* kid;    // [2 N] children of each laminate: >= 0 a laminate, -1 - phase a leaf
   const int* hcid;   // [2^K - 1] the laminate standing at each heap position, -1 for none (compressed trees)
+  const int* kslot;  // [2 N] the state slot of each child that is a leaf (-1: elastic, or a laminate child)
 };
 
 // fields of TreeDev::lf .w
@@ -1155,7 +1156,7 @@ __device__ __forceinline__ void node_angles(const TreeDev& t, int node, const do
   }
 }
 
-__device__ void adjoint_pass(const TreeDev& t, const double Eloc[6], const double gl[6], const double* ph, size_t phs,
+static __device__ void adjoint_pass(const TreeDev& t, const double Eloc[6], const double gl[6], const double* ph, size_t phs,
                              const PointArrays& P, const AdjWork& Wk) {
   const int K = t.K;
   double epsR[KMAX + 1][6], gR[KMAX + 1][6];
@@ -1290,7 +1291,7 @@ __device__ void adjoint_pass(const TreeDev& t, const double Eloc[6], const doubl
 // Leaf-weight gradient: each leaf collects the direct term and, from every
 // laminate above it, +W_R Xi (left subtree) or -W_L Xi (right subtree); then the
 // normalisation w~ = w / S is undone: dL/dw_k = (G_k - sum_l G_l w~_l) / S.
-__device__ void adjoint_weights(const TreeDev& t, const double* wl, double S, const AdjWork& Wk, double* gw,
+static __device__ void adjoint_weights(const TreeDev& t, const double* wl, double S, const AdjWork& Wk, double* gw,
                                 size_t gws) {
   const int K = t.K, L = t.L;
   const size_t ws = Wk.ws;
@@ -1321,7 +1322,7 @@ __device__ void adjoint_weights(const TreeDev& t, const double* wl, double S, co
 
 // adjoint_pass over a compressed tree (tables of TreeDev): the same per-laminate and
 // per-leaf terms, leaves one at a time, laminates numbered as in the state.
-__device__ void adjoint_pass_c(const TreeDev& t, const double Eloc[6], const double gl[6], const double* ph,
+static __device__ void adjoint_pass_c(const TreeDev& t, const double Eloc[6], const double gl[6], const double* ph,
                                size_t phs, const PointArrays& P, const AdjWork& Wk) {
   double epsR[KMAX + 1][6], gR[KMAX + 1][6];
   double pend_s[KMAX + 1][6], pend_t[KMAX + 1][6];
@@ -1440,7 +1441,7 @@ __device__ void adjoint_pass_c(const TreeDev& t, const double Eloc[6], const dou
 // adjoint_weights over a compressed tree.  Leaves of weight zero get no gradient: the
 // compressed tree holds nothing of them, and the weights' Macaulay bracket (Sec. 3.1)
 // passes none below zero.
-__device__ void adjoint_weights_c(const TreeDev& t, const double* wl, double S, const AdjWork& Wk, double* gw,
+static __device__ void adjoint_weights_c(const TreeDev& t, const double* wl, double S, const AdjWork& Wk, double* gw,
                                   size_t gws) {
   const size_t ws = Wk.ws;
   double accR[KMAX + 2];
@@ -1500,7 +1501,7 @@ __device__ __forceinline__ void n_matrix(const double n[3], double Nm[6][3]) {
 }
 
 // the laminate's tangent C (packed) from its children's
-__device__ void lam_tangent(const double n[3], double c1, double c2, const double CL[21], const double CR[21],
+static __device__ void lam_tangent(const double n[3], double c1, double c2, const double CL[21], const double CR[21],
                             double C[21]) {
   double Nm[6][3];
   n_matrix(n, Nm);
@@ -1546,7 +1547,7 @@ __device__ void lam_tangent(const double n[3], double c1, double c2, const doubl
     }
 }
 
-__device__ void lam_tangent_adjoint(const double n[3], double c1, double c2, const double CL[21], const double CR[21],
+static __device__ void lam_tangent_adjoint(const double n[3], double c1, double c2, const double CL[21], const double CR[21],
                                     const double Gbp[21], double GL[21], double GR[21], double nb[3], double& c1b) {
   double Nm[6][3];
   n_matrix(n, Nm);
@@ -1700,7 +1701,7 @@ __device__ __forceinline__ void phase_stiffnesses(const TreeDev& t, double Cph[2
         Cph[f][sidx(I, J)] = ((I < 3 && J < 3) ? t.ph[f].lam : 0.0) + (I == J ? 2.0 * t.ph[f].G : 0.0);
 }
 
-__device__ void tangent_level_fwd(const TreeDev& t, bool cmp, int lvl, int lane, int nl, const PointArrays& P,
+static __device__ void tangent_level_fwd(const TreeDev& t, bool cmp, int lvl, int lane, int nl, const PointArrays& P,
                                   const double Cph[2][21], double* Cst, size_t ws) {
   const int h0 = (1 << (lvl - 1)) - 1, nh = 1 << (lvl - 1);
   for (int x = lane; x < nh; x += nl) {
@@ -1722,7 +1723,7 @@ __device__ void tangent_level_fwd(const TreeDev& t, bool cmp, int lvl, int lane,
   }
 }
 
-__device__ void tangent_level_rev(const TreeDev& t, bool cmp, int lvl, int lane, int nl, const double* ph, size_t phs,
+static __device__ void tangent_level_rev(const TreeDev& t, bool cmp, int lvl, int lane, int nl, const double* ph, size_t phs,
                                   const PointArrays& P, const double Cph[2][21], const double* Cst, double* Gst,
                                   const AdjWork& Wk) {
   const size_t ws = Wk.ws;
@@ -1778,7 +1779,8 @@ __device__ __forceinline__ int tangent_root(const TreeDev& t, bool cmp) { return
 // points in flight.
 // Per-point arrays (one block per group), field-major over the laminates, stride N (the
 // handle's largest tree): jumps a [N][3]; c1 c2 (g, H) [21][N]; ein [6][N] (FP64) and dein [6][N]
-// (T); results sb [6][N] (FP64), ds and C [27][N] (T); normals in P (nrm / nrmf [N][3], stride 1).
+// (T); results sb [6][N] (FP64), ds and C [27][N] (T); normals in P (nrm / nrmf [N][3], stride 1);
+// compressed trees also le [6][N] (FP64).
 template <typename T>
 struct WarpSlot {
   const double* a_in; double* a_out;
@@ -1786,6 +1788,7 @@ struct WarpSlot {
   double* ein; T* dein;
   double* sb; T* dc;
   int N;
+  double* le;   // compressed trees: the strain of a laminate's leaf child beside a laminate child [6][N]
 };
 
 template <typename T>
@@ -1895,19 +1898,135 @@ __device__ void warp_condense_level(const TreeDev& t, const PointArrays& P, cons
   }
 }
 
+// Compressed trees (the tables of TreeDev): the same pass level by level of the full tree's heap
+// positions.  A kept laminate keeps its heap position; its children (kid) may stand several levels
+// deeper, or be leaves.  A laminate whose children are two leaves condenses them on the way down
+// (structured condensation); a leaf beside a laminate is evaluated when its parent condenses, from
+// the strain the parent handed it (le).  The root is the last laminate.
+template <typename T>
+__device__ void warp_descend_level_c(const TreeDev& t, const double Eloc[6], const PointArrays& P,
+                                     const WarpSlot<T>& W, bool apply, T step, int lvl, int lane, int lanes,
+                                     double& r2) {
+  const int NS = W.N, root = t.N - 1;
+  const int h0 = (1 << (lvl - 1)) - 1, nh = 1 << (lvl - 1);
+  for (int x = lane; x < nh; x += lanes) {
+    const int node = __ldg(t.hcid + h0 + x);
+    if (node < 0) continue;
+    double e[6];
+    T de[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) {
+      e[I] = node == root ? Eloc[I] : W.ein[I * NS + node];
+      de[I] = node == root ? (T)0 : W.dein[I * NS + node];
+    }
+    double nd[3];
+    T nt[3];
+    load_n<T>(P, node, nd, nt);
+    const double c1 = __ldg(t.c1 + node), c2 = __ldg(t.c2 + node);
+    double a[3] = {W.a_in[3 * node], W.a_in[3 * node + 1], W.a_in[3 * node + 2]};
+    T da[3] = {(T)0, (T)0, (T)0};
+    {
+      const T* gp = W.gh_in + node;
+      const T ic = ic12_of<T>(t, node);   // the stored step is c1 c2 (g, H)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T v = step * gp[c * NS];
+#pragma unroll
+        for (int I = 0; I < 6; ++I) v += gp[(3 + 6 * c + I) * NS] * de[I];
+        da[c] = apply ? v * ic : (T)0;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { a[c] += widen(da[c]); W.a_out[3 * node + c] = a[c]; }
+    }
+    const double ndr[3] = {nd[0] * RS2, nd[1] * RS2, nd[2] * RS2};
+    double Na[6], eL[6], eR[6];
+    N_apply<double>(nd, ndr, a, Na);
+#pragma unroll
+    for (int I = 0; I < 6; ++I) { eL[I] = e[I] - c2 * Na[I]; eR[I] = e[I] + c1 * Na[I]; }
+    const int k1 = __ldg(t.kid + 2 * node), k2 = __ldg(t.kid + 2 * node + 1);
+    if (k1 >= 0 || k2 >= 0) {   // a laminate child: hand the strains and their corrections down
+      const NodeC<T> cc = node_c<T>(t, node);
+      const T ntr[3] = {nt[0] * (T)RS2, nt[1] * (T)RS2, nt[2] * (T)RS2};
+      T Nda[6], dR[6];
+      N_apply<T>(nt, ntr, da, Nda);
+#pragma unroll
+      for (int I = 0; I < 6; ++I) { dR[I] = de[I] + cc.c1 * Nda[I]; de[I] = de[I] - cc.c2 * Nda[I]; }
+#pragma unroll
+      for (int I = 0; I < 6; ++I) {
+        if (k1 >= 0) { W.ein[I * NS + k1] = eL[I]; W.dein[I * NS + k1] = de[I]; }
+        else W.le[I * NS + node] = eL[I];
+        if (k2 >= 0) { W.ein[I * NS + k2] = eR[I]; W.dein[I * NS + k2] = dR[I]; }
+        else W.le[I * NS + node] = eR[I];
+      }
+    } else {   // two leaves and their structured condensation
+      const int p1 = -1 - k1, p2 = -1 - k2;
+      double z[6], sL[6], sR[6];
+      LeafTan<T> DL, DR;
+      load_z_slot<double>(P, __ldg(t.kslot + 2 * node), z);
+      leaf_iso<T, double>(t.ph[p1], eL, z, sL, &DL, nullptr, nullptr);
+      load_z_slot<double>(P, __ldg(t.kslot + 2 * node + 1), z);
+      leaf_iso<T, double>(t.ph[p2], eR, z, sR, &DR, nullptr, nullptr);
+      Sub<T> res;
+      condense_bottom<T, true, double>(nd, nt, c1, c2, __ldg(t.sc + node), node_c<T>(t, node), sL, DL, sR, DR, res,
+                                       W.gh_out + node, (size_t)NS, r2, t.ph[p1].kind == 0, t.ph[p2].kind == 0);
+      warp_sub_store<T>(W, node, res);
+    }
+  }
+}
+
+// the subtree result of laminate `node`'s child on `side`: a laminate's from W, or the leaf's
+// (evaluated at the strain in le)
+template <typename T>
+__device__ __forceinline__ void warp_child_c(const TreeDev& t, const PointArrays& P, const WarpSlot<T>& W, int node,
+                                             int side, Sub<T>& r) {
+  const int k = __ldg(t.kid + 2 * node + side);
+  if (k >= 0) {
+    warp_sub_load<T>(W, k, r);
+    return;
+  }
+  double e[6], z[6], sg[6];
+#pragma unroll
+  for (int I = 0; I < 6; ++I) e[I] = W.le[I * W.N + node];
+  LeafTan<T> D;
+  load_z_slot<double>(P, __ldg(t.kslot + 2 * node + side), z);
+  leaf_iso<T, double>(t.ph[-1 - k], e, z, sg, &D, nullptr, nullptr);
+  leaf_sub<T, double>(D, sg, r);
+}
+
+template <typename T>
+__device__ void warp_condense_level_c(const TreeDev& t, const PointArrays& P, const WarpSlot<T>& W, int lvl,
+                                      int lane, int lanes, double& r2) {
+  const int h0 = (1 << (lvl - 1)) - 1, nh = 1 << (lvl - 1);
+  for (int x = lane; x < nh; x += lanes) {
+    const int node = __ldg(t.hcid + h0 + x);
+    if (node < 0 || (__ldg(t.kid + 2 * node) < 0 && __ldg(t.kid + 2 * node + 1) < 0)) continue;
+    double nd[3];
+    T nt[3];
+    load_n<T>(P, node, nd, nt);
+    Sub<T> L, R, res;
+    warp_child_c<T>(t, P, W, node, 0, L);
+    warp_child_c<T>(t, P, W, node, 1, R);
+    condense<T, true, double>(nd, nt, __ldg(t.c1 + node), __ldg(t.c2 + node), __ldg(t.sc + node), node_c<T>(t, node),
+                              L, R, res, W.gh_out + node, (size_t)W.N, r2);
+    warp_sub_store<T>(W, node, res);
+  }
+}
+
 // The whole pass for the point of a group of `lanes` lanes (gmask: the group's lanes in the warp):
 // levels in order, a barrier of the group between them.  Returns this lane's share of the squared
-// residual norm; the root's result is at node 0 of W.
-template <typename T>
+// residual norm; the root's result is at node 0 of W (heap trees) or at its last laminate (CMP).
+template <typename T, bool CMP>
 __device__ double warp_tree_pass(const TreeDev& t, const double Eloc[6], const PointArrays& P, const WarpSlot<T>& W,
                                  bool apply, T step, int lane, int lanes, unsigned gmask) {
   double r2 = 0.0;
   for (int lvl = 1; lvl <= t.K; ++lvl) {
-    warp_descend_level<T>(t, Eloc, P, W, apply, step, lvl, lane, lanes, r2);
+    if (CMP) warp_descend_level_c<T>(t, Eloc, P, W, apply, step, lvl, lane, lanes, r2);
+    else warp_descend_level<T>(t, Eloc, P, W, apply, step, lvl, lane, lanes, r2);
     __syncwarp(gmask);
   }
   for (int lvl = t.K - 1; lvl >= 1; --lvl) {
-    warp_condense_level<T>(t, P, W, lvl, lane, lanes, r2);
+    if (CMP) warp_condense_level_c<T>(t, P, W, lvl, lane, lanes, r2);
+    else warp_condense_level<T>(t, P, W, lvl, lane, lanes, r2);
     __syncwarp(gmask);
   }
   return r2;

@@ -245,8 +245,8 @@ class DMN:
     and strain increment too).  first_stage: True starts every point with the all-FP32 Newton
     stage, False goes straight to the iteration of the chosen precision; None (default) runs it
     in the mixed forms only.  warp_per_point: 0 (default) the warp organisation for calls of at most
-    1024 points per SM in the FP64 form, 256 in the mixed forms; 1 always, -1 never (heap trees, the
-    paper's start); warp_lanes: lanes per point there (32, 16, 8; 0 chooses by the call's size).  The other options are those of dmn_options."""
+    1024 points per SM in the FP64 form, 256 in the mixed forms; 1 always, -1 never (the paper's
+    start); warp_lanes: lanes per point there (32, 16, 8; 0 chooses by the call's size).  The other options are those of dmn_options."""
 
     def __init__(self, tree, precision: str = "f64", tol: float = 1e-12, max_iter: int = 50, block: int = 0,
                  ctas_per_sm: int = 0, line_search: bool = False, predictor: bool = False,

@@ -88,8 +88,9 @@ def test_table_traversal_equals_the_heap_traversal(prec):
     other = W.tree_with_zero_weights(4, seed=31)
     A2, lam, Q = W.orientation_field(n, seed=32)
     Ef = W.random6_path_final(n, 0.03, seed=33)
-    heap = dmn.DMN(full, precision=prec, warp_per_point=-1)   # heap arithmetic of the thread-per-point kernel
-    table = dmn.DMN([full, other], precision=prec)
+    # the thread-per-point kernel's heap and table arithmetic
+    heap = dmn.DMN(full, precision=prec, warp_per_point=-1)
+    table = dmn.DMN([full, other], precision=prec, warp_per_point=-1)
     assert table.tree_state_sizes[0] == heap.state_size
     a = gpu_path(heap, lam, Q, Ef, 4, 10)
     b = gpu_path(table, lam, Q, Ef, 4, 10, tree_id=d(np.zeros(n, dtype=np.int32)))

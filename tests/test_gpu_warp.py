@@ -185,3 +185,72 @@ def test_the_default_organisation_is_chosen_per_call(prec, per_sm, lanes):
     _, passes, _ = m.profile_read_stages()
     assert passes["stage"] >= n
     m.close()
+
+
+@pytest.mark.parametrize("prec,lanes", [("f64", 8), ("f64", 32), ("mixed", 16), ("mixed-f32-tangent", 16)])
+def test_warp_kernel_on_compressed_trees(prec, lanes):
+    """Trees with weightless leaves in the warp organisation (level by level of the full tree's heap
+    positions, kept laminates at their positions, leaves beside laminates evaluated by their parent)
+    against the oracle's compression, and against the thread kernel's table traversal to rounding."""
+    import oracle
+    tol_s = {"f64": 1e-10, "mixed": 1e-6, "mixed-f32-tangent": 1e-6}[prec]
+    tol_t = {"f64": 1e-10, "mixed": 1e-6, "mixed-f32-tangent": 1e-4}[prec]
+    for K, n in ((5, 65), (7, 300), (8, 129)):
+        tree = W.tree_with_zero_weights(K, seed=490 + K)
+        A2, lam, Q = W.orientation_field(n, seed=500 + K)
+        Ef = W.random6_path_final(n, 0.03, seed=510 + K)
+        S = oracle.state_size(K, tree.phases, tree.w)
+        ms = {mode: dmn.DMN(tree, precision=prec, warp_per_point=mode, warp_lanes=lanes if mode == 1 else 0)
+              for mode in (1, -1)}
+        assert ms[1].lanes_per_point(n) == lanes and ms[-1].lanes_per_point(n) == 1
+        st = {mode: torch.zeros((S, n), dtype=torch.float64, device=DEV) for mode in ms}
+        so = np.zeros((S, n))
+        for s in range(1, 7):
+            En, dE = W.proportional_increment(Ef, s, 20)
+            outs = {}
+            for mode, m in ms.items():
+                outs[mode] = {k: v.cpu().numpy() for k, v in m.update(d(lam), d(Q), d(En), d(dE), st[mode]).items()}
+                st[mode] = torch.from_numpy(outs[mode]["state_out"]).to(DEV)
+            so, sig_o, C_o, it_o, stat_o, gap = oracle.update(tree, lam, Q, En, dE, so)
+            a, b = outs[1], outs[-1]
+            ok = (stat_o == 0) & (a["status"] == 0)
+            assert ok.mean() > 0.95, (K, s)
+            assert rel(a["stress"][ok], sig_o[ok]).max() <= tol_s, (K, s)
+            tie = gap < 1e-9
+            assert rel(a["tangent"][ok & ~tie], C_o[ok & ~tie]).max() <= tol_t, (K, s)
+            scale = np.abs(so[:, ok]).max(axis=1, keepdims=True) + 1e-300
+            if prec == "f64":
+                assert (np.abs(a["state_out"][:, ok] - so[:, ok]) / scale).max() <= 1e-9, (K, s)
+            np.testing.assert_array_equal(a["status"], b["status"])
+            assert rel(a["stress"], b["stress"]).max() <= (1e-10 if prec == "f64" else 1e-8), (K, s)
+        for m in ms.values():
+            m.close()
+
+
+def test_warp_kernel_on_a_compressed_tree_with_the_line_search():
+    """The line search's two buffers on a compressed tree, large cyclic steps, against the oracle's line
+    search; the same statuses as the thread kernel."""
+    import oracle
+    K, n, n_steps = 7, 200, 8
+    tree = W.tree_with_zero_weights(K, seed=520)
+    A2, lam, Q = W.orientation_field(n, seed=521)
+    amp = W.random6_path_final(n, 0.025, seed=522)
+    S = oracle.state_size(K, tree.phases, tree.w)
+    ms = {mode: dmn.DMN(tree, precision="f64", line_search=True, warp_per_point=mode) for mode in (0, -1)}
+    assert ms[0].lanes_per_point(n) == 32 and ms[0].lanes_per_point(4096) == 8
+    st = {mode: torch.zeros((S, n), dtype=torch.float64, device=DEV) for mode in ms}
+    so = np.zeros((S, n))
+    for s in range(1, n_steps + 1):
+        En, dE = W.cyclic_increment(amp, s, n_steps)
+        outs = {}
+        for mode, m in ms.items():
+            outs[mode] = m.update(d(lam), d(Q), d(En), d(dE), st[mode])
+            st[mode] = outs[mode]["state_out"]
+        so, sig_o, C_o, it_o, stat_o, gap = oracle.update(tree, lam, Q, En, dE, so, line_search=True)
+        a, b = ({k: v.cpu().numpy() for k, v in outs[mode].items()} for mode in (0, -1))
+        ok = (stat_o == 0) & (a["status"] == 0) & (b["status"] == 0)
+        assert ok.mean() > 0.95
+        assert rel(a["stress"][ok], sig_o[ok]).max() <= 1e-10
+        assert rel(a["stress"][ok], b["stress"][ok]).max() <= 1e-10
+    for m in ms.values():
+        m.close()
