@@ -218,7 +218,9 @@ def test_warp_kernel_on_compressed_trees(prec, lanes):
             assert rel(a["stress"][ok], sig_o[ok]).max() <= tol_s, (K, s)
             tie = gap < 1e-9
             assert rel(a["tangent"][ok & ~tie], C_o[ok & ~tie]).max() <= tol_t, (K, s)
-            scale = np.abs(so[:, ok]).max(axis=1, keepdims=True) + 1e-300
+            # per-field scale, floored at 1e-5 of the largest field: some fields of these trees are zero
+            # to rounding (a jump of a laminate whose children still deform alike)
+            scale = np.maximum(np.abs(so[:, ok]).max(axis=1, keepdims=True), 1e-5 * np.abs(so[:, ok]).max())
             if prec == "f64":
                 assert (np.abs(a["state_out"][:, ok] - so[:, ok]) / scale).max() <= 1e-9, (K, s)
             np.testing.assert_array_equal(a["status"], b["status"])
