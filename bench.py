@@ -995,7 +995,8 @@ def run_gpu(args):
                              % (state_fields(tree) * n * 8e-6),
                        "parallelism": "independent point shards per GPU, no collective"},
             "roofline": forms_out[main_form]["roofline"], "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": (4 + ("stage" in mr["kms"])) * steps, "clocks": mr["clocks"],
+            "gpu_launches": (4 + ("stage" in mr["kms"]) + (bool(mr.get("warp")) and main_form.split("/")[0] == "mixed"))
+                            * steps, "clocks": mr["clocks"],
             "peaks": {"fp64_gflops": peaks["f64"], "fp32_gflops": peaks["f32"], "note": peaks["note"]}}
     # the other forms side by side with the headline: value, roofline and error against the oracle
     for form in ("mixed", "mixed-f32-tangent", "f64/stage"):

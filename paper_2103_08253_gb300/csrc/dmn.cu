@@ -1236,8 +1236,9 @@ cudaError_t alloc_ws(const dmn_handle* h, WorkSet& w) {
   if (e == cudaSuccess && warp_possible(h)) {
     // one slot per group of the smallest size the handle may use
     w.nwarps_w = (int64_t)h->n_sm * WARP_CTAS_PER_SM * 128 / (h->opt.warp_lanes ? h->opt.warp_lanes : WARP_MIN_LANES);
-    const size_t per = h->opt.precision == DMN_PREC_F64 ? warp_slot_doubles<double>(h->N_max)
-                                                        : warp_slot_doubles<float>(h->N_max);
+    // FP64 slots where an FP64 pass runs in them (the FP64 form's Newton, the mixed form's final sweep)
+    const size_t per = h->opt.precision == DMN_PREC_MIXED_F32_TANGENT ? warp_slot_doubles<float>(h->N_max)
+                                                                     : warp_slot_doubles<double>(h->N_max);
     e = cudaMalloc(&w.scr_w, sizeof(double) * per * (size_t)w.nwarps_w);
   }
   return e;
@@ -1325,7 +1326,7 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, int64_t n_call, const int32_
     ev = h->events[h->events_used++].data();
     cudaEventRecord(ev[0], s);
   }
-  // counters: [0] work, [1..9] points per tree, [10..18] cursors
+  // counters: [0] work, [1..9] points per tree, [10..18] cursors, [19] first stage, [20] warp sweep
   e = cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long) * 32, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "dmn_update: counter reset");
   const int64_t* perm = nullptr;
@@ -1379,7 +1380,16 @@ int update_on(dmn_handle* h, WorkSet& w, int64_t n, int64_t n_call, const int32_
   }
   if (ev) cudaEventRecord(ev[3], s);
   FinalParams FP{F, n, NM, tree_id, perm, Q, state_in, state_out, stress, tangent, status, w.nbuf};
-  if (sweep) {
+  if (sweep && warp) {   // the FP64 sweep in the warp organisation (counter [20]), then k_final rotates
+    NewtonParams<double> SP{F, n, h->nslots, NM, tree_id, perm, state_in, state_out, stress, tangent, iters, status,
+                            w.nbuf, w.scr_d, (double*)w.scr_t, w.counter + 20, h->opt.tol, h->opt.max_iter, 1, 0,
+                            dE, nullptr, nullptr, 0};
+    const int swl = h->opt.warp_lanes ? h->opt.warp_lanes : (n_call <= 16 * (int64_t)h->n_sm ? 32 : 8);
+    if (h->cmp) launch_sweep_warp<true>(SP, swl, wgrid, w.scr_w, s);
+    else launch_sweep_warp<false>(SP, swl, wgrid, w.scr_w, s);
+    if (h->cmp) k_final<false, true><<<g1, 128, 0, s>>>(FP);
+    else k_final<false, false><<<g1, 128, 0, s>>>(FP);
+  } else if (sweep) {
     if (h->cmp) k_final<true, true><<<g1, 128, 0, s>>>(FP);
     else k_final<true, false><<<g1, 128, 0, s>>>(FP);
   } else {

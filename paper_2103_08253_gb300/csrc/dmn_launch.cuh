@@ -74,5 +74,9 @@ constexpr int WARP_MIN_LANES = 8;     // the smallest group: the scratch holds 3
 // grid * 128 / lanes slots of warp_slot_doubles<T>(P.N_max) doubles
 template <typename T, bool CMP>
 void launch_warp(const NewtonParams<T>& P, bool ls, int lanes, unsigned grid, double* scr, cudaStream_t s);
+// k_sweep_warp<CMP, lanes>: the mixed form's FP64 final sweep in the warp organisation (csrc/dmn_warp.cu);
+// `scr` holds grid * 128 / lanes slots of warp_slot_doubles<double>(P.N_max) doubles
+template <bool CMP>
+void launch_sweep_warp(const NewtonParams<double>& P, int lanes, unsigned grid, double* scr, cudaStream_t s);
 
 }  // namespace dmn

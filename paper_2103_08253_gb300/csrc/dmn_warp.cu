@@ -160,6 +160,84 @@ void launch_warp(const NewtonParams<T>& P, bool ls, int lanes, unsigned grid, do
   }
 }
 
+// The mixed form's FP64 final sweep in the warp organisation: one FP64 pass per point at its converged
+// jumps (state_out), no correction applied, the root's stress and packed tangent (local frame) written
+// for k_final<false> to rotate; that kernel then writes the leaf states.  Points whose Newton iteration
+// was not finite, or whose tree is unknown, are left to k_final and to the Newton kernel's report.  The
+// groups run side by side as in k_newton_warp; the scratch slots are sized for FP64.
+template <bool CMP, int G>
+__global__ void __launch_bounds__(128) k_sweep_warp(NewtonParams<double> P, double* scratch) {
+  const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x % G;
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << ((threadIdx.x & 31) / G * G);
+  const int NM = P.N_max;
+  double* base = scratch + (size_t)grp * warp_slot_doubles<double>(NM);
+  double* av = base;
+  double* ein = base + 6 * NM;
+  double* sbv = base + 12 * NM;
+  double* nrm = base + 18 * NM;
+  double* le = base + 21 * NM;
+  double* tb = base + 27 * NM;
+  double* gbuf = tb;             // written by the pass, not read: no correction is applied
+  double* dein = tb + 42 * NM;
+  double* dcv = tb + 48 * NM;
+  PointArrays A{};
+  A.nrm = nrm; A.ns = 1; A.nrmf = nullptr;
+  A.as = 1; A.paper = false;
+  A.zs = (size_t)P.n;
+  int64_t pt = -1;
+  int tr = 0;
+  double Eloc[6];
+  auto take = [&]() -> bool {
+    for (;;) {
+      unsigned long long i = 0;
+      if (lane == 0) i = atomicAdd(P.counter, 1ull);
+      i = __shfl_sync(gmask, i, 0, G);
+      if (i >= (unsigned long long)P.n) return false;
+      point_of(P.perm, P.tid, P.F.n, (int64_t)i, pt, tr);
+      if (tr < P.F.n && P.status[pt] != DMN_STATUS_NONFINITE) break;
+    }
+    const TreeDev& t = P.F.t[tr];
+    const int nzf = 6 * t.nz;
+#pragma unroll
+    for (int I = 0; I < 6; ++I) Eloc[I] = P.nbuf[(size_t)(3 * NM + I) * P.n + pt];
+    for (int f = lane; f < 3 * t.N; f += G) {   // jumps: heap order here, paper order in the state
+      const int node = f / 3, c = f - 3 * node;
+      const int lvl = 32 - __clz(node + 1);
+      const int j = CMP ? node : (1 << t.K) - 3 * (1 << (lvl - 1)) + node + 1;
+      av[f] = P.state_out[(size_t)(nzf + 3 * j + c) * P.n + pt];
+      nrm[f] = P.nbuf[(size_t)f * P.n + pt];
+    }
+    __syncwarp(gmask);
+    return true;
+  };
+  bool have = take();
+  while (__any_sync(0xffffffffu, have)) {
+    if (!have) continue;
+    const TreeDev& t = P.F.t[tr];
+    A.z = P.state_in + pt;
+    WarpSlot<double> W{av, av, gbuf, gbuf, ein, dein, sbv, dcv, NM, le};
+    warp_tree_pass<double, CMP>(t, Eloc, A, W, false, 1.0, lane, G, gmask);
+    Sub<double> root;
+    warp_sub_load<double>(W, CMP ? t.N - 1 : 0, root);
+    if (lane == 0) {
+      for (int I = 0; I < 6; ++I) P.stress[6 * pt + I] = root.sb[I];
+      for (int k = 0; k < 21; ++k) P.tangent[36 * pt + k] = root.C[k];
+    }
+    __syncwarp(gmask);
+    have = take();
+  }
+}
+
+template <bool CMP>
+void launch_sweep_warp(const NewtonParams<double>& P, int lanes, unsigned grid, double* scr, cudaStream_t s) {
+  if (lanes == 8) k_sweep_warp<CMP, 8><<<grid, 128, 0, s>>>(P, scr);
+  else if (lanes == 16) k_sweep_warp<CMP, 16><<<grid, 128, 0, s>>>(P, scr);
+  else k_sweep_warp<CMP, 32><<<grid, 128, 0, s>>>(P, scr);
+}
+
+template void launch_sweep_warp<false>(const NewtonParams<double>&, int, unsigned, double*, cudaStream_t);
+template void launch_sweep_warp<true>(const NewtonParams<double>&, int, unsigned, double*, cudaStream_t);
 template void launch_warp<double, false>(const NewtonParams<double>&, bool, int, unsigned, double*, cudaStream_t);
 template void launch_warp<double, true>(const NewtonParams<double>&, bool, int, unsigned, double*, cudaStream_t);
 template void launch_warp<float, false>(const NewtonParams<float>&, bool, int, unsigned, double*, cudaStream_t);

@@ -456,12 +456,26 @@ static int run_warp(FILE* in, FILE* out, int K, int M, long n, int max_iter, dou
     B.a = a.data(); B.a_out = a.data(); B.as = 1; B.paper = !tr.cmp;
     B.z = st.data() + pt; B.zs = (size_t)n;
     double Cl[6][6], sl[6];
-    if (sweep) {
+    if (sweep) {   // the warp sweep: one FP64 pass of the group's lanes at the converged jumps, no correction
+      std::vector<double> aw(abuf[cur].begin(), abuf[cur].end()), gd(21 * N), deind(6 * N), dcd(27 * N);
+      std::vector<double> eind(6 * N), sbd(6 * N), led(6 * N);
+      WarpSlot<double> Wd{aw.data(), aw.data(), gd.data(), gd.data(), eind.data(), deind.data(), sbd.data(),
+                          dcd.data(), N, led.data()};
+      PointArrays Ad = A;
+      Ad.nrmf = nullptr;
+      double v[32] = {0.0};
+      for (int lvl = 1; lvl <= K; ++lvl)
+        for (int lane = 0; lane < G; ++lane) {
+          if (tr.cmp) warp_descend_level_c<double>(t, Eloc, Ad, Wd, false, 1.0, lvl, lane, G, v[lane]);
+          else warp_descend_level<double>(t, Eloc, Ad, Wd, false, 1.0, lvl, lane, G, v[lane]);
+        }
+      for (int lvl = K - 1; lvl >= 1; --lvl)
+        for (int lane = 0; lane < G; ++lane) {
+          if (tr.cmp) warp_condense_level_c<double>(t, Ad, Wd, lvl, lane, G, v[lane]);
+          else warp_condense_level<double>(t, Ad, Wd, lvl, lane, G, v[lane]);
+        }
       Sub<double> fin;
-      double r2;
-      GH<double> none{nullptr, 0, nullptr};
-      if (tr.cmp) tree_pass_c<double, false>(t, Eloc, B, none, false, 1.0, fin, r2, nullptr);
-      else tree_pass<double, false>(t, Eloc, B, none, false, 1.0, fin, r2, nullptr);
+      warp_sub_load<double>(Wd, tr.cmp ? N - 1 : 0, fin);
       for (int I = 0; I < 6; ++I) { sl[I] = fin.sb[I]; for (int J = 0; J < 6; ++J) Cl[I][J] = fin.C[sidx(I, J)]; }
     } else {
       for (int I = 0; I < 6; ++I) { sl[I] = root.sb[I]; for (int J = 0; J < 6; ++J) Cl[I][J] = widen(root.C[sidx(I, J)]); }
