@@ -33,6 +33,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -187,11 +188,23 @@ def final_flops(K, npts, sweep, w=None):
 
 
 # ---------------------------------------------------------------------------------------------
+SRC_FILES = ("paper_2103_08253_gb300/csrc/dmn.cu", "paper_2103_08253_gb300/csrc/dmn_device.cuh",
+             "paper_2103_08253_gb300/csrc/dmn_warp.cu", "paper_2103_08253_gb300/csrc/dmn_launch.cuh")
+
+
+def code_only(text):
+    """A CUDA source without its comments and blank lines, each line stripped: what a change must touch
+    for the compiled kernels (and so their DRAM figures) to change."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", line).strip() for line in text.split("\n"))
+    return "\n".join(line for line in lines if line)
+
+
 def src_hash():
+    """Hash of the DMN kernels' sources, comments and layout left out (the key of profiles/traffic.json)."""
     h = hashlib.sha256()
-    for f in ("paper_2103_08253_gb300/csrc/dmn.cu", "paper_2103_08253_gb300/csrc/dmn_device.cuh",
-              "paper_2103_08253_gb300/csrc/dmn_warp.cu", "paper_2103_08253_gb300/csrc/dmn_launch.cuh"):
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+    for f in SRC_FILES:
+        h.update(code_only(open(os.path.join(ROOT, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -68,7 +68,7 @@ struct WorkSet {
   float* scr_s = nullptr;       // the mixed forms' first stage, per slot of its kernel: g, H [21N], normals [3N],
                                 // jumps [3N] (FP32)
   int64_t nslots_s = 0;         // slots of the first stage's kernel
-  double* scr_w = nullptr;      // small batches, one warp per point: a block of scratch per warp
+  double* scr_w = nullptr;      // small calls, the warp organisation: a block of scratch per group of lanes
   int64_t nwarps_w = 0;
   double* nbuf = nullptr;       // per point: normals [3N] + local macro strain [6], field-major
   int64_t* perm = nullptr;      // points sorted by tree (several trees)
@@ -1195,7 +1195,7 @@ bool first_stage_on(const dmn_options& o) {
   return want && !o.line_search && !o.predictor;
 }
 
-// the warp organisation: for heap trees with the paper's start, always on request, by default
+// the warp organisation: for the paper's start (heap or compressed trees), always on request, by default
 // (unless the first stage was asked for) for calls of at most warp_auto_points_per_sm points per SM.
 // Below that the thread-per-point kernel leaves SMs idle or nearly so.  At depth 8 on 152 SMs,
 // FP64: one point per warp is 20x faster than one point per thread at 1024 points; four points per

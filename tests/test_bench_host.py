@@ -127,3 +127,12 @@ def test_form_options_and_l2_flush_rule():
     S = bench.state_fields(tree)
     assert S == 1533
     assert bench.l2_flush_needed(S, 4096) and not bench.l2_flush_needed(S, 1 << 20)
+
+
+def test_source_hash_ignores_comments_only():
+    """The key of the committed DRAM figures changes with the code, not with comments or blank lines."""
+    a = "int f(int x) {  // the square\n  return x * x;\n}\n"
+    b = "/* squares */\nint f(int x) {\n\n  return x * x;   // as before\n}\n"
+    c = "int f(int x) {\n  return x * x + 1;\n}\n"
+    assert bench.code_only(a) == bench.code_only(b) != bench.code_only(c)
+    assert len(bench.src_hash()) == 16
